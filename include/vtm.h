@@ -1,0 +1,185 @@
+/*
+ * vtm.h -- C ABI of libvtm, a GB300 (sm_103a) implementation of the Virtual
+ * Transmission Method (VTM) of Wei & Yang, "Transmission Line Inspires A New
+ * Distributed Algorithm to Solve the Linear System of Circuit",
+ * arXiv 0910.0663.
+ *
+ * The library solves the nodal system A x = b of a circuit (Sec. II, Eq. 1).
+ * A is torn into sub-circuits along virtual lossless transmission lines of
+ * characteristic impedance Zc (wire tearing, Sec. V; transmission delay
+ * equations, Eq. 3-5, W = 1/Zc).  Every VTM sweep (Sec. VI, Eq. 11 / Eq. 14)
+ * lets each sub-circuit solve its own system loaded by W at its torn ports
+ * with the incident waves on the right-hand side; the outgoing waves then
+ * cross every line with one sweep of delay, and a residual norm decides
+ * convergence.
+ *
+ * Tearing of a disjoint node partition: every branch between nodes of two
+ * different parts is torn at its midpoint (two 2g conductances in series,
+ * the midpoint split into twin nodes, Sec. V Steps 1-4).  Inside the library
+ * each sub-circuit P is condensed onto its ports through its voltage
+ * reflection matrix T_P = (W - S_P)(W + S_P)^-1 (Sec. VIII), so that a sweep
+ * is w_out = T_P w_in + c_P per sub-circuit followed by the exchange
+ * w_in(s) <- w_out(twin(s)).
+ *
+ * Conventions for every entry point:
+ *  - Array arguments may live in device memory or in host memory (pageable
+ *    or pinned); the library inspects each pointer.  Host arrays are copied
+ *    in and out on the plan's stream.  The caller keeps ownership.
+ *  - Matrices are CSR with int64 row pointers, int32 column indices sorted
+ *    within each row, and float64 values.  Vectors of several right-hand
+ *    sides are n x nrhs column-major (column r starts at r*n).
+ *  - All device work of a plan runs on the CUDA stream given to vtm_plan
+ *    (NULL = the legacy default stream).  Calls on one plan must not
+ *    overlap; distinct plans are independent.
+ *  - Errors are returned as vtm_status; nothing aborts the process and there
+ *    is no CPU fallback.  vtm_strerror gives a message; vtm_last_error_detail
+ *    gives the last detailed message of the calling thread.
+ */
+#ifndef VTM_H
+#define VTM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vtm_plan_s* vtm_plan_t;
+
+typedef enum {
+  VTM_OK = 0,
+  VTM_EINVAL = -1,       /* bad argument: size, range, empty part, pattern change */
+  VTM_ENOMEM = -2,       /* device or host allocation failed */
+  VTM_ESINGULAR = -3,    /* non-positive (Cholesky) or zero (LU) pivot in a local factor */
+  VTM_ENOCONV = -4,      /* tolerance not met within max_sweeps / max_outer; x = last iterate */
+  VTM_EDIVERGED = -5,    /* NaN/Inf or residual growth > 1e6 x initial; x = last iterate */
+  VTM_ETIMEOUT = -6,     /* a bounded device-side wait ran out (persistent kernels) */
+  VTM_ECUDA = -7,        /* a CUDA runtime call failed */
+  VTM_EINTERNAL = -8,    /* an internal consistency check failed */
+  VTM_ENOTFACTORED = -9  /* vtm_solve/vtm_adjoint before vtm_factor (or after vtm_set_values) */
+} vtm_status;
+
+/* Arithmetic of the sub-circuit applies (the reflection-matrix products). */
+enum {
+  VTM_PREC_FP64 = 0, /* plain FP64 VTM */
+  VTM_PREC_FP32 = 1, /* FP32 T_P and waves, FP32 accumulate, inside FP64 iterative refinement */
+  VTM_PREC_BF16 = 2  /* BF16 T_P, FP32 waves and accumulate, inside FP64 iterative refinement */
+};
+
+typedef struct {
+  int precision;     /* VTM_PREC_*; default VTM_PREC_FP64 */
+  int max_sweeps;    /* sweeps per vtm_solve call, all refinement steps together; default 200000 */
+  int check_every;   /* sweeps launched between two host polls of the convergence flag; default 32 */
+  double inner_tol;  /* relative tolerance of each inner solve in the refinement modes;
+                        0 -> 1e-6 (FP32) / 3e-3 (BF16) */
+  int max_outer;     /* refinement steps in the FP32/BF16 modes; default 40 */
+  double* history;   /* optional host array: relative (interface) residual after each
+                        sweep k=1..history_len of the first column; NULL = not recorded */
+  int history_len;
+} vtm_opts;
+
+typedef struct {
+  int sweeps;        /* total sweeps run (all refinement steps) */
+  int outer_steps;   /* refinement steps (1 in FP64 mode) */
+  double relres;     /* max over columns of ||b - A x||_2 / ||b||_2, from an FP64 SpMV of the returned x */
+  double t_solve_ms; /* device time of the call (CUDA events on the plan's stream) */
+  int first_sweep_converged; /* sweep k at which the interface residual first met tol (FP64 mode) */
+  int kernel_launches;       /* kernels libvtm launched during the call */
+  int sweep_launches;        /* sweep-kernel launches (including launches that found the
+                                convergence flag already set and returned at once) */
+  double t_sweeps_ms;        /* device time of the sweep-kernel launches (CUDA events around
+                                each batch of back-to-back launches on the plan's stream) */
+} vtm_info;
+
+typedef struct {
+  int64_t n;
+  int32_t nparts;
+  int64_t nports;        /* two per torn branch */
+  int64_t nlagged;       /* cut entries that are not branches (controlled sources) */
+  int64_t sum_p2;        /* sum over sub-circuits of p_P^2 (reflection-matrix entries) */
+  int32_t max_ports;     /* largest p_P */
+  int32_t max_nodes;     /* largest sub-circuit */
+  int32_t max_band;      /* largest half-bandwidth of a local matrix after reordering */
+  int32_t symmetric;     /* 1: A symmetric -> Cholesky; 0: LU without pivoting */
+  int64_t t_bytes;       /* bytes of the stored reflection matrices (all precisions kept) */
+  int64_t factor_bytes;  /* bytes of the stored local factors */
+} vtm_plan_stats;
+
+/* vtm_plan -- wire tearing (Sec. V) and the port table.
+ * n: unknowns.  rowptr[n+1], colidx[nnz], vals[nnz]: A in CSR (host or device).
+ * partition[n]: sub-circuit of each node, values in [0, nparts); every part
+ * must be non-empty.  Zc > 0: characteristic impedance of every virtual line
+ * (W = 1/Zc, the choice W = alpha I of Sec. VIII).  opts may be NULL.
+ * stream: a cudaStream_t (or NULL).  On success *out owns all device buffers.
+ * Errors: VTM_EINVAL (n <= 0, nparts <= 0, partition out of range, empty
+ * part, Zc <= 0 or not finite, unsorted or out-of-range column indices),
+ * VTM_ENOMEM, VTM_ECUDA. */
+vtm_status vtm_plan(int64_t n, const int64_t* rowptr, const int32_t* colidx, const double* vals,
+                    const int32_t* partition, int32_t nparts, double Zc, const vtm_opts* opts,
+                    void* stream, vtm_plan_t* out);
+
+/* vtm_set_values -- new values for the same sparsity pattern (gradients,
+ * finite differences).  The set of torn branches (cut pairs with a positive
+ * symmetric conductance) must not change: VTM_EINVAL otherwise.  The plan
+ * must be factored again before the next solve. */
+vtm_status vtm_set_values(vtm_plan_t plan, const double* vals);
+
+/* vtm_set_opts -- replace the options of a plan (precision, limits, history). */
+vtm_status vtm_set_opts(vtm_plan_t plan, const vtm_opts* opts);
+
+/* vtm_factor -- per sub-circuit factorisation of the condensed local matrix
+ * K_P = A_PP + sum_s (g_s - 4 g_s^2/(2 g_s + W)) e_l(s) e_l(s)^T (the matrix
+ * of Eq. 11 after eliminating the twin rows) by banded Cholesky (symmetric A)
+ * or banded LU without pivoting, in FP64; then the reflection matrices
+ * T_P = (W - S_P)(W + S_P)^-1 (Sec. VIII) from p_P banded solves each, kept
+ * in FP64 and in the precision selected by opts.  Errors: VTM_ESINGULAR. */
+vtm_status vtm_factor(vtm_plan_t plan);
+
+/* vtm_solve -- solve A x = b by VTM sweeps (Sec. VI, Eq. 11/14) with zero
+ * initial waves, until ||b - A x||_2 <= tol ||b||_2 for every column.
+ * b, x: n x nrhs column-major, host or device; x is output only.  tol > 0.
+ * The convergence test after every sweep uses the residual of the torn
+ * branches (the interior rows of each sub-circuit are solved exactly); the
+ * returned info->relres comes from an FP64 SpMV of the returned x.
+ * Errors: VTM_ENOTFACTORED, VTM_EINVAL, VTM_ENOCONV, VTM_EDIVERGED (x then
+ * holds the last iterate and info is filled). */
+vtm_status vtm_solve(vtm_plan_t plan, const double* b, double* x, int64_t nrhs, double tol,
+                     vtm_info* info);
+
+/* vtm_adjoint -- solve A^T lam = g (same tearing; for a symmetric A the same
+ * operators, otherwise a transposed plan built and factored on first use).
+ * Arguments as vtm_solve. */
+vtm_status vtm_adjoint(vtm_plan_t plan, const double* g, double* lam, int64_t nrhs, double tol,
+                       vtm_info* info);
+
+/* vtm_plan_get_stats -- sizes of the tearing and of the stored operators. */
+vtm_status vtm_plan_get_stats(vtm_plan_t plan, vtm_plan_stats* stats);
+
+/* vtm_get_ports -- the port table (host arrays of length stats.nports):
+ * node = the port's node, remote = the node across the torn branch,
+ * part = owning sub-circuit, twin = the port at the other end of the line.
+ * Ports are grouped by sub-circuit, then ordered by (node, remote).
+ * Any pointer may be NULL. */
+vtm_status vtm_get_ports(vtm_plan_t plan, int32_t* node, int32_t* remote, int32_t* part,
+                         int32_t* twin);
+
+/* vtm_get_reflection -- copy T_P of sub-circuit `part` (p_P x p_P, row-major,
+ * FP64, ports in vtm_get_ports order) into host array T (capacity `cap`
+ * doubles); *p receives p_P.  Requires vtm_factor. */
+vtm_status vtm_get_reflection(vtm_plan_t plan, int32_t part, double* T, int64_t cap, int32_t* p);
+
+/* vtm_residual_norm -- rel[r] = ||b_r - A x_r||_2 / ||b_r||_2 for each of
+ * nrhs columns, in FP64 on the plan's stream (A = the plan's current values).
+ * x, b: n x nrhs column-major (host or device); rel: host array[nrhs]. */
+vtm_status vtm_residual_norm(vtm_plan_t plan, const double* x, const double* b, int64_t nrhs,
+                             double* rel);
+
+void vtm_destroy(vtm_plan_t plan);
+const char* vtm_strerror(vtm_status status);
+const char* vtm_last_error_detail(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VTM_H */

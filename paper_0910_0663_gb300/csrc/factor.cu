@@ -1,0 +1,346 @@
+// Per sub-circuit factorisation and the voltage reflection matrices.
+//
+// K_P (the matrix of Eq. 11 after eliminating the twin rows, see vtm.h) is
+// banded after the planner's reordering.  It is factored in FP64 by a
+// right-looking band Cholesky (symmetric A) or band LU without pivoting,
+// one CTA per sub-circuit, with the active (bw+1) x (bw+1) window in shared
+// memory addressed circularly.  The factors are stored column-wise:
+//   Lc[j][a] = L(j+a, j), a = 1..bw;  Lc[j][0] = 1 / L(j, j)
+//   Uc[j][b] = U(j-b, j), b = 1..bw;  Uc[j][0] = 1 / U(j, j)
+// so that both triangular solves are column sweeps with contiguous reads.
+//
+// The reflection matrix of Sec. VIII, T_P = (W - S_P)(W + S_P)^-1, is built
+// column by column from banded solves: column q of T_P is
+//   T(s, q) = 2 W beta_s y_q(l(s)) + delta_sq (W - 2 g_s)/(W + 2 g_s),
+//   K_P y_q = beta_q e_l(q),  beta = 2 g/(2 g + W).
+// It is stored transposed (row q of the block = column q of T_P) with rows
+// padded to a multiple of 8 elements.
+#include <algorithm>
+
+#include "vtm_internal.h"
+
+namespace vtm {
+
+// ---------------------------------------------------------------------------
+// band factorisation
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int wrap(int x, int B) { return x % B; }
+
+template <bool kLU>
+__global__ void __launch_bounds__(256) band_factor_kernel(const int32_t* __restrict__ node_off,
+                                                          const int32_t* __restrict__ bwv,
+                                                          const int64_t* __restrict__ band_off,
+                                                          double* __restrict__ Lc,
+                                                          double* __restrict__ Uc,
+                                                          double* __restrict__ gwin, int Bmax,
+                                                          int* __restrict__ err) {
+  extern __shared__ double smem[];
+  const int t = blockIdx.x;
+  const int n = node_off[t + 1] - node_off[t];
+  const int bw = bwv[t];
+  const int B = bw + 1;
+  double* lc = Lc + band_off[t];
+  double* uc = Uc + band_off[t];
+  double* win = gwin ? gwin + (size_t)t * Bmax * Bmax : smem;
+  double* lcol = gwin ? smem : smem + (size_t)Bmax * Bmax;
+  double* urow = lcol + Bmax;
+  const int tid = threadIdx.x;
+  // initial window: rows/cols 0..min(bw, n-1)
+  const int r0 = min(B, n);
+  for (int idx = tid; idx < r0 * r0; idx += blockDim.x) {
+    int r = idx / r0, c = idx % r0;
+    double v = 0.0;
+    if (c <= r) v = lc[(size_t)c * B + (r - c)];
+    else if (kLU) v = uc[(size_t)c * B + (c - r)];
+    if (kLU || c <= r) win[wrap(r, B) * B + wrap(c, B)] = v;
+  }
+  __syncthreads();
+  bool bad = false;
+  for (int j = 0; j < n; ++j) {
+    const int jm = wrap(j, B);
+    const int m = min(bw, n - 1 - j);
+    const double piv = win[jm * B + jm];
+    double dinv;
+    if (kLU) {
+      bad = bad || !(fabs(piv) > 0.0) || !isfinite(piv);
+      dinv = 1.0 / piv;
+    } else {
+      bad = bad || !(piv > 0.0) || !isfinite(piv);
+      dinv = rsqrt(piv > 0.0 ? piv : 1.0);
+    }
+    for (int a = tid + 1; a <= m; a += blockDim.x) {
+      lcol[a] = win[wrap(j + a, B) * B + jm] * dinv;
+      if (kLU) urow[a] = win[jm * B + wrap(j + a, B)];
+    }
+    __syncthreads();
+    for (int a = tid; a <= m; a += blockDim.x) {
+      if (a == 0) {
+        lc[(size_t)j * B] = kLU ? 1.0 : dinv;
+        uc[(size_t)j * B] = dinv;
+      } else {
+        lc[(size_t)j * B + a] = lcol[a];
+        uc[(size_t)(j + a) * B + a] = kLU ? urow[a] : lcol[a];
+      }
+    }
+    // rank-1 update of the trailing window
+    if (kLU) {
+      for (int idx = tid; idx < m * m; idx += blockDim.x) {
+        int a = idx / m + 1, b = idx % m + 1;
+        win[wrap(j + a, B) * B + wrap(j + b, B)] -= lcol[a] * urow[b];
+      }
+    } else {
+      for (int idx = tid; idx < m * m; idx += blockDim.x) {
+        int a = idx / m + 1, b = idx % m + 1;
+        if (b <= a) win[wrap(j + a, B) * B + wrap(j + b, B)] -= lcol[a] * lcol[b];
+      }
+    }
+    __syncthreads();
+    // bring in row (and column) r = j + B, which no earlier step touched
+    const int r = j + B;
+    if (r < n) {
+      for (int c = r - bw + tid; c <= r; c += blockDim.x) {
+        win[wrap(r, B) * B + wrap(c, B)] = lc[(size_t)c * B + (r - c)];
+        if (kLU && c < r) win[wrap(c, B) * B + wrap(r, B)] = uc[(size_t)r * B + (r - c)];
+      }
+    }
+    __syncthreads();
+  }
+  if (bad && tid == 0) atomicMax(err, t + 1);
+}
+
+vtm_status factor_tiles(vtm_plan_s* P) {
+  cudaStream_t s = P->stream;
+  const int Bmax = P->max_bw + 1;
+  size_t win_bytes = (size_t)Bmax * Bmax * sizeof(double);
+  size_t vec_bytes = 2 * (size_t)Bmax * sizeof(double);
+  DevBuf gwin;
+  bool use_smem = win_bytes + vec_bytes <= 200 * 1024;
+  size_t smem = use_smem ? win_bytes + vec_bytes : vec_bytes;
+  if (!use_smem) VTM_TRY(dev_alloc(gwin, (size_t)P->nparts * win_bytes));
+  VTM_CUDA_TRY(cudaMemsetAsync(P->d_err.p, 0, sizeof(int), s));
+  int threads = Bmax <= 40 ? 128 : 256;
+  if (P->symmetric) {
+    VTM_CUDA_TRY(cudaFuncSetAttribute(band_factor_kernel<false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    band_factor_kernel<false><<<P->nparts, threads, smem, s>>>(
+        P->tabs.node_off.as<int32_t>(), P->tabs.bw.as<int32_t>(), P->tabs.band_off.as<int64_t>(),
+        P->d_Lc.as<double>(), P->d_Uc.as<double>(), gwin.as<double>(), Bmax, P->d_err.as<int>());
+  } else {
+    VTM_CUDA_TRY(cudaFuncSetAttribute(band_factor_kernel<true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    band_factor_kernel<true><<<P->nparts, threads, smem, s>>>(
+        P->tabs.node_off.as<int32_t>(), P->tabs.bw.as<int32_t>(), P->tabs.band_off.as<int64_t>(),
+        P->d_Lc.as<double>(), P->d_Uc.as<double>(), gwin.as<double>(), Bmax, P->d_err.as<int>());
+  }
+  VTM_CUDA_TRY(cudaGetLastError());
+  int herr = 0;
+  VTM_CUDA_TRY(cudaMemcpyAsync(&herr, P->d_err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  VTM_CUDA_TRY(cudaStreamSynchronize(s));
+  dev_free(gwin);
+  if (herr) {
+    set_detail("vtm_factor: bad pivot in sub-circuit " + std::to_string(herr - 1));
+    return VTM_ESINGULAR;
+  }
+  return VTM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// banded solves (one warp per right-hand side)
+// ---------------------------------------------------------------------------
+
+// Forward sweep L y = v from row `start` (entries above are zero), then
+// backward sweep U x = y; v is overwritten by x.  One warp.
+__device__ __forceinline__ void warp_band_solve(double* v, int n, int bw, const double* __restrict__ lc,
+                                                const double* __restrict__ uc, int start) {
+  const int lane = threadIdx.x & 31;
+  const int B = bw + 1;
+  for (int j = start; j < n; ++j) {
+    const double* col = lc + (size_t)j * B;
+    const double y = v[j] * __ldg(col);
+    const int m = min(bw, n - 1 - j);
+    __syncwarp();
+    if (lane == 0) v[j] = y;
+    for (int a = lane + 1; a <= m; a += 32) v[j + a] -= __ldg(col + a) * y;
+    __syncwarp();
+  }
+  for (int j = n - 1; j >= 0; --j) {
+    const double* col = uc + (size_t)j * B;
+    const double x = v[j] * __ldg(col);
+    const int m = min(bw, j);
+    __syncwarp();
+    if (lane == 0) v[j] = x;
+    for (int b = lane + 1; b <= m; b += 32) v[j - b] -= __ldg(col + b) * x;
+    __syncwarp();
+  }
+}
+
+// Solve K_P x = v for every tile, in place in the permuted vector v
+// (one warp per (tile, column)); columns are `stride` apart.
+__global__ void band_solve_tiles_kernel(const int32_t* __restrict__ node_off,
+                                        const int32_t* __restrict__ bwv,
+                                        const int64_t* __restrict__ band_off,
+                                        const double* __restrict__ Lc, const double* __restrict__ Uc,
+                                        double* __restrict__ v, int64_t stride, int nparts,
+                                        int use_smem) {
+  extern __shared__ double smem[];
+  const int t = blockIdx.x % nparts;
+  const int col = blockIdx.x / nparts;
+  const int off = node_off[t];
+  const int n = node_off[t + 1] - off;
+  double* vg = v + (size_t)col * stride + off;
+  const int lane = threadIdx.x;
+  if (use_smem) {
+    for (int i = lane; i < n; i += 32) smem[i] = vg[i];
+    __syncwarp();
+    warp_band_solve(smem, n, bwv[t], Lc + band_off[t], Uc + band_off[t], 0);
+    for (int i = lane; i < n; i += 32) vg[i] = smem[i];
+  } else {
+    warp_band_solve(vg, n, bwv[t], Lc + band_off[t], Uc + band_off[t], 0);
+  }
+}
+
+void launch_band_solve(vtm_plan_s* P, double* v, int ncols, int64_t stride, cudaStream_t s) {
+  P->launch_count++;
+  size_t smem = (size_t)P->max_nodes * sizeof(double);
+  int use_smem = smem <= 200 * 1024;
+  if (use_smem) {
+    cudaFuncSetAttribute(band_solve_tiles_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+  } else {
+    smem = 0;
+  }
+  band_solve_tiles_kernel<<<P->nparts * ncols, 32, smem, s>>>(
+      P->tabs.node_off.as<int32_t>(), P->tabs.bw.as<int32_t>(), P->tabs.band_off.as<int64_t>(),
+      P->d_Lc.as<double>(), P->d_Uc.as<double>(), v, stride, P->nparts, use_smem);
+}
+
+// ---------------------------------------------------------------------------
+// reflection matrices
+// ---------------------------------------------------------------------------
+
+// One warp per port q: solve K_P y = beta_q e_l(q) and write row q of T_P^T.
+__global__ void build_reflection_kernel(const int32_t* __restrict__ node_off,
+                                        const int32_t* __restrict__ bwv,
+                                        const int64_t* __restrict__ band_off,
+                                        const double* __restrict__ Lc, const double* __restrict__ Uc,
+                                        const int32_t* __restrict__ port_off,
+                                        const int32_t* __restrict__ port_tile,
+                                        const int32_t* __restrict__ port_loc,
+                                        const double* __restrict__ g,
+                                        const double* __restrict__ beta,
+                                        const int64_t* __restrict__ T_off,
+                                        const int32_t* __restrict__ T_ld, double W,
+                                        double* __restrict__ T) {
+  extern __shared__ double y[];
+  const int q = blockIdx.x;
+  const int t = port_tile[q];
+  const int n = node_off[t + 1] - node_off[t];
+  const int p0 = port_off[t];
+  const int p = port_off[t + 1] - p0;
+  const int lane = threadIdx.x;
+  for (int i = lane; i < n; i += 32) y[i] = 0.0;
+  __syncwarp();
+  const int lq = port_loc[q];
+  if (lane == 0) y[lq] = beta[q];
+  __syncwarp();
+  warp_band_solve(y, n, bwv[t], Lc + band_off[t], Uc + band_off[t], lq);
+  double* row = T + T_off[t] + (size_t)(q - p0) * T_ld[t];
+  for (int s = lane; s < p; s += 32) {
+    const int ps = p0 + s;
+    double v = 2.0 * W * beta[ps] * y[port_loc[ps]];
+    if (ps == q) v += (W - 2.0 * g[ps]) / (W + 2.0 * g[ps]);
+    row[s] = v;
+  }
+}
+
+__global__ void convert_f32_kernel(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+__global__ void convert_bf16_kernel(const double* __restrict__ a, __nv_bfloat16* __restrict__ b,
+                                    int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = __float2bfloat16_rn((float)a[i]);
+}
+
+vtm_status build_reflections(vtm_plan_s* P) {
+  cudaStream_t s = P->stream;
+  const int64_t npt = (int64_t)P->port_node.size();
+  const size_t Tbytes = std::max<int64_t>(P->T_elems, 8) * sizeof(double);
+  VTM_TRY(dev_alloc(P->d_T64, Tbytes));
+  VTM_CUDA_TRY(cudaMemsetAsync(P->d_T64.p, 0, Tbytes, s));
+  if (npt > 0) {
+    size_t smem = (size_t)P->max_nodes * sizeof(double);
+    if (smem > 200 * 1024) {
+      set_detail("vtm_factor: a sub-circuit with more than 25600 nodes has ports; use more parts");
+      return VTM_EINVAL;
+    }
+    std::vector<int32_t> port_tile(npt);
+    for (int32_t t = 0; t < P->nparts; ++t)
+      for (int32_t q = P->port_off[t]; q < P->port_off[t + 1]; ++q) port_tile[q] = t;
+    DevBuf d_pt;
+    VTM_TRY(upload(d_pt, port_tile, s));
+    VTM_CUDA_TRY(cudaFuncSetAttribute(build_reflection_kernel,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    build_reflection_kernel<<<(unsigned)npt, 32, smem, s>>>(
+        P->tabs.node_off.as<int32_t>(), P->tabs.bw.as<int32_t>(), P->tabs.band_off.as<int64_t>(),
+        P->d_Lc.as<double>(), P->d_Uc.as<double>(), P->tabs.port_off.as<int32_t>(),
+        d_pt.as<int32_t>(), P->d_port_loc.as<int32_t>(), P->d_g.as<double>(),
+        P->d_beta.as<double>(), P->tabs.T_off.as<int64_t>(), P->tabs.T_ld.as<int32_t>(), P->W,
+        P->d_T64.as<double>());
+    VTM_CUDA_TRY(cudaGetLastError());
+    VTM_CUDA_TRY(cudaStreamSynchronize(s));
+    dev_free(d_pt);
+  }
+  const int64_t ne = std::max<int64_t>(P->T_elems, 8);
+  if (P->opts.precision == VTM_PREC_FP32) {
+    VTM_TRY(dev_alloc(P->d_T32, ne * sizeof(float)));
+    convert_f32_kernel<<<1216, 256, 0, s>>>(P->d_T64.as<double>(), P->d_T32.as<float>(), ne);
+  } else if (P->opts.precision == VTM_PREC_BF16) {
+    VTM_TRY(dev_alloc(P->d_T16, ne * sizeof(__nv_bfloat16)));
+    convert_bf16_kernel<<<1216, 256, 0, s>>>(P->d_T64.as<double>(), P->d_T16.as<__nv_bfloat16>(), ne);
+  }
+  VTM_CUDA_TRY(cudaGetLastError());
+  VTM_CUDA_TRY(cudaStreamSynchronize(s));
+  return VTM_OK;
+}
+
+}  // namespace vtm
+
+using namespace vtm;
+
+extern "C" vtm_status vtm_factor(vtm_plan_t P) {
+  if (!P) return VTM_EINVAL;
+  cudaSetDevice(P->device);
+  P->factored = false;
+  // the band arrays hold K_P before the factorisation: re-assemble if a
+  // previous factorisation overwrote them
+  static_assert(sizeof(double) == 8, "");
+  VTM_TRY(assemble_local(P));
+  VTM_TRY(factor_tiles(P));
+  VTM_TRY(build_reflections(P));
+  P->factored = true;
+  return VTM_OK;
+}
+
+extern "C" vtm_status vtm_get_reflection(vtm_plan_t P, int32_t part, double* T, int64_t cap,
+                                         int32_t* p) {
+  if (!P || part < 0 || part >= P->nparts) return VTM_EINVAL;
+  if (!P->factored) return VTM_ENOTFACTORED;
+  const int32_t pp = P->port_off[part + 1] - P->port_off[part];
+  if (p) *p = pp;
+  if (!T) return VTM_OK;
+  if (cap < (int64_t)pp * pp) return VTM_EINVAL;
+  const int32_t ld = P->T_ld[part];
+  std::vector<double> blk((size_t)pp * ld);
+  if (pp > 0)
+    VTM_CUDA_TRY(cudaMemcpy(blk.data(), P->d_T64.as<double>() + P->T_off[part],
+                            blk.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  for (int32_t q = 0; q < pp; ++q)
+    for (int32_t s = 0; s < pp; ++s) T[(size_t)s * pp + q] = blk[(size_t)q * ld + s];
+  return VTM_OK;
+}

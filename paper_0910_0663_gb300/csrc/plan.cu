@@ -1,0 +1,687 @@
+// Planner of libvtm: wire tearing of a node partition into sub-circuits and
+// the torn-port table (Sec. V, Steps 1-4), band ordering of every
+// sub-circuit, and host assembly of the condensed local matrices K_P.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <queue>
+
+#include "vtm_internal.h"
+
+namespace vtm {
+
+static thread_local std::string g_detail;
+
+void set_detail(const std::string& msg) { g_detail = msg; }
+
+vtm_status dev_alloc(DevBuf& b, size_t bytes) {
+  if (b.p && b.bytes >= bytes) return VTM_OK;
+  dev_free(b);
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    set_detail(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? VTM_ENOMEM : VTM_ECUDA;
+  }
+  b.bytes = bytes;
+  return VTM_OK;
+}
+
+void dev_free(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+static vtm_status fetch(std::vector<T>& h, const T* src, size_t count) {
+  h.resize(count);
+  if (count == 0) return VTM_OK;
+  if (is_device_ptr(src)) {
+    VTM_CUDA_TRY(cudaMemcpy(h.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(h.data(), src, count * sizeof(T));
+  }
+  return VTM_OK;
+}
+
+// Half bandwidth of one tile's local pattern under the ordering `loc`.
+static int tile_bandwidth(const vtm_plan_s* P, const std::vector<int32_t>& nodes,
+                          const std::vector<int32_t>& loc_of, int32_t tile) {
+  int bw = 0;
+  for (size_t a = 0; a < nodes.size(); ++a) {
+    int32_t i = nodes[a];
+    int li = loc_of[i];
+    for (int64_t q = P->h_rowptr[i]; q < P->h_rowptr[i + 1]; ++q) {
+      int32_t j = P->h_colidx[q];
+      if (P->h_part[j] != tile) continue;
+      int d = std::abs(loc_of[j] - li);
+      bw = std::max(bw, d);
+    }
+  }
+  return bw;
+}
+
+// Reverse Cuthill-McKee ordering of one tile (symmetrised pattern).
+static void tile_rcm(const vtm_plan_s* P, const std::vector<int32_t>& nodes, int32_t tile,
+                     std::vector<int32_t>& out, std::vector<int32_t>& mark) {
+  const size_t m = nodes.size();
+  // local adjacency
+  std::vector<int32_t> deg(m, 0);
+  std::vector<std::vector<int32_t>> adj(m);
+  for (size_t a = 0; a < m; ++a) mark[nodes[a]] = (int32_t)a;
+  for (size_t a = 0; a < m; ++a) {
+    int32_t i = nodes[a];
+    for (int64_t q = P->h_rowptr[i]; q < P->h_rowptr[i + 1]; ++q) {
+      int32_t j = P->h_colidx[q];
+      if (j == i || P->h_part[j] != tile) continue;
+      int32_t b = mark[j];
+      adj[a].push_back(b);
+      adj[b].push_back((int32_t)a);
+    }
+  }
+  for (size_t a = 0; a < m; ++a) {
+    std::sort(adj[a].begin(), adj[a].end());
+    adj[a].erase(std::unique(adj[a].begin(), adj[a].end()), adj[a].end());
+    deg[a] = (int32_t)adj[a].size();
+  }
+  std::vector<char> seen(m, 0);
+  std::vector<int32_t> order;
+  order.reserve(m);
+  while (order.size() < m) {
+    // start: unvisited node of minimum degree (ties: lowest local id)
+    int32_t s = -1;
+    for (size_t a = 0; a < m; ++a)
+      if (!seen[a] && (s < 0 || deg[a] < deg[s])) s = (int32_t)a;
+    std::queue<int32_t> q;
+    q.push(s);
+    seen[s] = 1;
+    while (!q.empty()) {
+      int32_t a = q.front();
+      q.pop();
+      order.push_back(a);
+      std::vector<int32_t> nb;
+      for (int32_t b : adj[a])
+        if (!seen[b]) {
+          seen[b] = 1;
+          nb.push_back(b);
+        }
+      std::stable_sort(nb.begin(), nb.end(), [&](int32_t x, int32_t y) { return deg[x] < deg[y]; });
+      for (int32_t b : nb) q.push(b);
+    }
+  }
+  out.resize(m);
+  for (size_t a = 0; a < m; ++a) out[a] = nodes[order[m - 1 - a]];
+}
+
+static int64_t csr_find(const vtm_plan_s* P, int32_t i, int32_t j) {
+  const int32_t* b = P->h_colidx.data() + P->h_rowptr[i];
+  const int32_t* e = P->h_colidx.data() + P->h_rowptr[i + 1];
+  const int32_t* f = std::lower_bound(b, e, j);
+  if (f != e && *f == j) return (int64_t)(f - P->h_colidx.data());
+  return -1;
+}
+
+struct CutPair {
+  int32_t lo, hi;
+  int64_t pos_lohi, pos_hilo;
+  bool wire;
+};
+
+static double val_at(const vtm_plan_s* P, int64_t pos) { return pos >= 0 ? P->h_vals[pos] : 0.0; }
+
+// All structure that depends only on the pattern, the partition and the
+// signs that decide which cut pairs carry a virtual line.
+static vtm_status build_structure(vtm_plan_s* P, std::vector<CutPair>& pairs) {
+  const int64_t n = P->n;
+  const int32_t np = P->nparts;
+  // tiles
+  std::vector<int32_t> count(np + 1, 0);
+  for (int64_t i = 0; i < n; ++i) count[P->h_part[i] + 1]++;
+  for (int32_t t = 0; t < np; ++t) {
+    if (count[t + 1] == 0) {
+      set_detail("vtm_plan: part " + std::to_string(t) + " is empty");
+      return VTM_EINVAL;
+    }
+    count[t + 1] += count[t];
+  }
+  P->node_off = count;
+  std::vector<std::vector<int32_t>> tnodes(np);
+  for (int64_t i = 0; i < n; ++i) tnodes[P->h_part[i]].push_back((int32_t)i);
+  P->perm.assign(n, 0);
+  P->iperm.assign(n, 0);
+  P->bw.assign(np, 0);
+  std::vector<int32_t> loc_of(n, 0), mark(n, 0), rcm;
+  P->max_nodes = 0;
+  P->max_bw = 0;
+  for (int32_t t = 0; t < np; ++t) {
+    auto& nd = tnodes[t];
+    for (size_t a = 0; a < nd.size(); ++a) loc_of[nd[a]] = (int32_t)a;
+    int bw_nat = tile_bandwidth(P, nd, loc_of, t);
+    std::vector<int32_t>* best = &nd;
+    int bw_best = bw_nat;
+    if (bw_nat > 1 && nd.size() > 2) {
+      tile_rcm(P, nd, t, rcm, mark);
+      for (size_t a = 0; a < rcm.size(); ++a) loc_of[rcm[a]] = (int32_t)a;
+      int bw_rcm = tile_bandwidth(P, rcm, loc_of, t);
+      if (bw_rcm < bw_nat) {
+        best = &rcm;
+        bw_best = bw_rcm;
+      }
+    }
+    for (size_t a = 0; a < best->size(); ++a) {
+      int32_t node = (*best)[a];
+      P->perm[P->node_off[t] + a] = node;
+      P->iperm[node] = P->node_off[t] + (int32_t)a;
+    }
+    P->bw[t] = bw_best;
+    P->max_nodes = std::max<int32_t>(P->max_nodes, (int32_t)nd.size());
+    P->max_bw = std::max(P->max_bw, bw_best);
+  }
+  P->band_off.assign(np, 0);
+  int64_t off = 0;
+  for (int32_t t = 0; t < np; ++t) {
+    P->band_off[t] = off;
+    off += (int64_t)(P->node_off[t + 1] - P->node_off[t]) * (P->bw[t] + 1);
+  }
+  P->band_elems = off;
+
+  // cut pairs (Sec. V Step 1: every branch between two parts is torn)
+  pairs.clear();
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t q = P->h_rowptr[i]; q < P->h_rowptr[i + 1]; ++q) {
+      int32_t j = P->h_colidx[q];
+      if (P->h_part[j] == P->h_part[i]) continue;
+      if (i < j) {
+        pairs.push_back({(int32_t)i, j, q, csr_find(P, j, (int32_t)i), false});
+      } else if (csr_find(P, j, (int32_t)i) < 0) {
+        pairs.push_back({j, (int32_t)i, -1, q, false});
+      }
+    }
+  }
+  std::vector<int32_t> pn, pr, pt;
+  std::vector<int64_t> pij, pji;
+  P->lag_i.clear();
+  P->lag_j.clear();
+  P->lag_pos.clear();
+  for (auto& cp : pairs) {
+    double a1 = val_at(P, cp.pos_lohi), a2 = val_at(P, cp.pos_hilo);
+    double g = -(a1 + a2) / 2.0;
+    cp.wire = g > 0;
+    double r1 = cp.wire ? a1 + g : a1;
+    double r2 = cp.wire ? a2 + g : a2;
+    if (r1 != 0.0) {
+      P->lag_i.push_back(cp.lo);
+      P->lag_j.push_back(cp.hi);
+      P->lag_pos.push_back(cp.pos_lohi);
+    }
+    if (r2 != 0.0) {
+      P->lag_i.push_back(cp.hi);
+      P->lag_j.push_back(cp.lo);
+      P->lag_pos.push_back(cp.pos_hilo);
+    }
+    if (cp.wire) {
+      pn.push_back(cp.lo); pr.push_back(cp.hi); pij.push_back(cp.pos_lohi); pji.push_back(cp.pos_hilo);
+      pn.push_back(cp.hi); pr.push_back(cp.lo); pij.push_back(cp.pos_hilo); pji.push_back(cp.pos_lohi);
+    }
+  }
+  // ports: grouped by tile, then (node, remote)
+  const size_t npt = pn.size();
+  std::vector<int64_t> idx(npt);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) {
+    int32_t ta = P->h_part[pn[a]], tb = P->h_part[pn[b]];
+    if (ta != tb) return ta < tb;
+    if (pn[a] != pn[b]) return pn[a] < pn[b];
+    return pr[a] < pr[b];
+  });
+  P->port_node.resize(npt);
+  P->port_remote.resize(npt);
+  P->port_pos_ij.resize(npt);
+  P->port_pos_ji.resize(npt);
+  P->port_loc.resize(npt);
+  P->port_off.assign(np + 1, 0);
+  for (size_t s = 0; s < npt; ++s) {
+    int64_t a = idx[s];
+    P->port_node[s] = pn[a];
+    P->port_remote[s] = pr[a];
+    P->port_pos_ij[s] = pij[a];
+    P->port_pos_ji[s] = pji[a];
+    int32_t t = P->h_part[pn[a]];
+    P->port_loc[s] = P->iperm[pn[a]] - P->node_off[t];
+    P->port_off[t + 1]++;
+  }
+  for (int32_t t = 0; t < np; ++t) P->port_off[t + 1] += P->port_off[t];
+  // twins: the port whose (node, remote) is our (remote, node)
+  std::vector<int64_t> key(npt), srt(npt);
+  for (size_t s = 0; s < npt; ++s) key[s] = (int64_t)P->port_node[s] * n + P->port_remote[s];
+  std::iota(srt.begin(), srt.end(), 0);
+  std::sort(srt.begin(), srt.end(), [&](int64_t a, int64_t b) { return key[a] < key[b]; });
+  P->port_twin.resize(npt);
+  for (size_t s = 0; s < npt; ++s) {
+    int64_t want = (int64_t)P->port_remote[s] * n + P->port_node[s];
+    auto it = std::lower_bound(srt.begin(), srt.end(), want,
+                               [&](int64_t a, int64_t v) { return key[a] < v; });
+    if (it == srt.end() || key[*it] != want) {
+      set_detail("vtm_plan: internal: twin port not found");
+      return VTM_EINTERNAL;
+    }
+    P->port_twin[s] = (int32_t)*it;
+  }
+  // node runs (ports of one node are adjacent)
+  P->port_run.assign(npt, 0);
+  for (size_t s = 0; s < npt;) {
+    size_t e = s + 1;
+    int32_t t = P->h_part[P->port_node[s]];
+    while (e < npt && P->port_node[e] == P->port_node[s] && (int64_t)e < P->port_off[t + 1]) ++e;
+    P->port_run[s] = (uint8_t)std::min<size_t>(e - s, 255);
+    if (e - s > 255) {
+      set_detail("vtm_plan: more than 255 torn branches at one node");
+      return VTM_EINVAL;
+    }
+    s = e;
+  }
+  // reflection-matrix layout: T^T blocks with rows padded to 8 elements
+  P->T_ld.assign(np, 0);
+  P->T_off.assign(np, 0);
+  int64_t toff = 0;
+  P->sum_p2 = 0;
+  P->max_ports = 0;
+  for (int32_t t = 0; t < np; ++t) {
+    int32_t p = P->port_off[t + 1] - P->port_off[t];
+    int32_t ld = (p + 7) / 8 * 8;
+    P->T_ld[t] = ld;
+    P->T_off[t] = toff;
+    toff += (int64_t)p * ld;
+    P->sum_p2 += (int64_t)p * p;
+    P->max_ports = std::max(P->max_ports, p);
+  }
+  P->T_elems = toff;
+  return VTM_OK;
+}
+
+// True if the current values give the same torn lines and the same set of
+// lagged positions as the ones the plan was built with.
+static bool same_cut_structure(const vtm_plan_s* P) {
+  std::vector<int64_t> wires, lags;
+  for (int64_t i = 0; i < P->n; ++i) {
+    for (int64_t q = P->h_rowptr[i]; q < P->h_rowptr[i + 1]; ++q) {
+      int32_t j = P->h_colidx[q];
+      if (P->h_part[j] == P->h_part[i]) continue;
+      int64_t back = csr_find(P, j, (int32_t)i);
+      if (i > j && back >= 0) continue;
+      int64_t p1 = i < j ? q : back, p2 = i < j ? back : q;
+      double a1 = val_at(P, p1), a2 = val_at(P, p2);
+      double g = -(a1 + a2) / 2.0;
+      bool wire = g > 0;
+      if (wire) wires.push_back(p1 >= 0 ? p1 : p2);
+      double r1 = wire ? a1 + g : a1, r2 = wire ? a2 + g : a2;
+      if (r1 != 0.0) lags.push_back(p1);
+      if (r2 != 0.0) lags.push_back(p2);
+    }
+  }
+  std::vector<int64_t> w0, l0;
+  for (size_t s = 0; s < P->port_node.size(); ++s)
+    if (P->port_node[s] < P->port_remote[s])
+      w0.push_back(P->port_pos_ij[s] >= 0 ? P->port_pos_ij[s] : P->port_pos_ji[s]);
+  for (size_t q = 0; q < P->lag_pos.size(); ++q) l0.push_back(P->lag_pos[q]);
+  std::sort(wires.begin(), wires.end());
+  std::sort(lags.begin(), lags.end());
+  std::sort(w0.begin(), w0.end());
+  std::sort(l0.begin(), l0.end());
+  // a lagged entry may vanish (rho = 0) but no new one may appear
+  if (wires != w0) return false;
+  return std::includes(l0.begin(), l0.end(), lags.begin(), lags.end());
+}
+
+// Values: branch conductances, beta, lagged couplings and the band of K_P.
+vtm_status assemble_local(vtm_plan_s* P) {
+  const int32_t np = P->nparts;
+  const double W = P->W;
+  const size_t npt = P->port_node.size();
+  P->port_g.resize(npt);
+  std::vector<double> beta(npt);
+  for (size_t s = 0; s < npt; ++s) {
+    double g = -(val_at(P, P->port_pos_ij[s]) + val_at(P, P->port_pos_ji[s])) / 2.0;
+    if (!(g > 0)) {
+      set_detail("vtm_set_values: a torn branch lost its positive conductance");
+      return VTM_EINVAL;
+    }
+    P->port_g[s] = g;
+    beta[s] = 2 * g / (2 * g + W);
+  }
+  P->lag_rho.resize(P->lag_i.size());
+  for (size_t q = 0; q < P->lag_i.size(); ++q) {
+    // remainder after the branch part (if the pair carries a line)
+    int32_t i = P->lag_i[q], j = P->lag_j[q];
+    int64_t pji = csr_find(P, j, i);
+    double a = val_at(P, P->lag_pos[q]);
+    double g = -(a + val_at(P, pji)) / 2.0;
+    P->lag_rho[q] = g > 0 ? a + g : a;
+  }
+  std::vector<double> Lc(P->band_elems, 0.0), Uc;
+  if (!P->symmetric) Uc.assign(P->band_elems, 0.0);
+  for (int32_t t = 0; t < np; ++t) {
+    const int32_t B = P->bw[t] + 1;
+    const int32_t off = P->node_off[t];
+    const int32_t cnt = P->node_off[t + 1] - off;
+    double* lc = Lc.data() + P->band_off[t];
+    double* uc = P->symmetric ? nullptr : Uc.data() + P->band_off[t];
+    for (int32_t l = 0; l < cnt; ++l) {
+      int32_t i = P->perm[off + l];
+      for (int64_t q = P->h_rowptr[i]; q < P->h_rowptr[i + 1]; ++q) {
+        int32_t j = P->h_colidx[q];
+        if (P->h_part[j] != t) continue;
+        int32_t m = P->iperm[j] - off;
+        if (m <= l) {
+          lc[(int64_t)m * B + (l - m)] += P->h_vals[q];
+        } else if (uc) {
+          uc[(int64_t)m * B + (m - l)] += P->h_vals[q];
+        }
+      }
+    }
+    for (int32_t s = P->port_off[t]; s < P->port_off[t + 1]; ++s) {
+      double g = P->port_g[s];
+      lc[(int64_t)P->port_loc[s] * B] += g - 4 * g * g / (2 * g + W);
+    }
+  }
+  cudaStream_t st = P->stream;
+  VTM_TRY(upload(P->d_Lc, Lc, st));
+  if (!P->symmetric) {
+    VTM_TRY(upload(P->d_Uc, Uc, st));
+  } else {
+    VTM_TRY(dev_alloc(P->d_Uc, std::max<size_t>(16, Lc.size() * sizeof(double))));
+  }
+  VTM_TRY(upload(P->d_g, P->port_g, st));
+  VTM_TRY(upload(P->d_beta, beta, st));
+  VTM_CUDA_TRY(cudaStreamSynchronize(st));
+  return VTM_OK;
+}
+
+}  // namespace vtm
+
+using namespace vtm;
+
+std::vector<DevBuf*> vtm_plan_s::all_bufs() {
+  return {&tabs.node_off, &tabs.bw, &tabs.band_off, &tabs.port_off, &tabs.T_off, &tabs.T_ld,
+          &tabs.order, &d_rowptr, &d_colidx, &d_vals, &d_perm, &d_Lc, &d_Uc, &d_port_loc, &d_port_pos,
+          &d_twin, &d_g, &d_beta, &d_run, &d_T64, &d_T32, &d_T16, &d_c64, &d_c32, &d_state64,
+          &d_state32, &d_v, &d_v2, &d_xacc, &d_r, &d_bcol, &d_partials, &d_ctrl, &d_hist,
+          &d_err, &d_red};
+}
+
+static void fill_default_opts(vtm_opts* o) {
+  if (o->max_sweeps <= 0) o->max_sweeps = 200000;
+  if (o->check_every <= 0) o->check_every = 32;
+  if (o->max_outer <= 0) o->max_outer = 40;
+  if (o->precision < 0 || o->precision > 2) o->precision = 0;
+}
+
+extern "C" vtm_status vtm_set_opts(vtm_plan_t P, const vtm_opts* opts) {
+  if (!P) return VTM_EINVAL;
+  vtm_opts o{};
+  if (opts) o = *opts;
+  if (o.precision < 0 || o.precision > 2 || o.history_len < 0 || (o.history_len > 0 && !o.history)) {
+    set_detail("vtm_set_opts: bad precision or history");
+    return VTM_EINVAL;
+  }
+  bool prec_changed = o.precision != P->opts.precision;
+  fill_default_opts(&o);
+  P->opts = o;
+  if (o.history_len > P->hist_cap) {
+    VTM_TRY(dev_alloc(P->d_hist, sizeof(double) * (size_t)o.history_len));
+    P->hist_cap = o.history_len;
+  }
+  if (prec_changed && P->factored && o.precision != VTM_PREC_FP64) {
+    // low-precision copies are built by vtm_factor
+    P->factored = false;
+  }
+  return VTM_OK;
+}
+
+extern "C" vtm_status vtm_plan(int64_t n, const int64_t* rowptr, const int32_t* colidx,
+                               const double* vals, const int32_t* partition, int32_t nparts,
+                               double Zc, const vtm_opts* opts, void* stream, vtm_plan_t* out) {
+  if (!out) return VTM_EINVAL;
+  *out = nullptr;
+  if (n <= 0 || n > INT32_MAX - 1 || nparts <= 0 || nparts > n || !rowptr || !colidx || !vals ||
+      !partition || !(Zc > 0) || !std::isfinite(Zc)) {
+    set_detail("vtm_plan: bad n, nparts, Zc or NULL array");
+    return VTM_EINVAL;
+  }
+  vtm_plan_s* P = new (std::nothrow) vtm_plan_s();
+  if (!P) return VTM_ENOMEM;
+  P->n = n;
+  P->nparts = nparts;
+  P->Zc = Zc;
+  P->W = 1.0 / Zc;
+  P->stream = static_cast<cudaStream_t>(stream);
+  cudaGetDevice(&P->device);
+  auto fail = [&](vtm_status s) {
+    vtm_destroy(P);
+    return s;
+  };
+  vtm_status st;
+  if ((st = fetch(P->h_rowptr, rowptr, (size_t)n + 1)) != VTM_OK) return fail(st);
+  int64_t nnz = P->h_rowptr[n];
+  if (P->h_rowptr[0] != 0 || nnz < 0) {
+    set_detail("vtm_plan: rowptr[0] must be 0");
+    return fail(VTM_EINVAL);
+  }
+  for (int64_t i = 0; i < n; ++i)
+    if (P->h_rowptr[i + 1] < P->h_rowptr[i]) {
+      set_detail("vtm_plan: rowptr not monotone");
+      return fail(VTM_EINVAL);
+    }
+  P->nnz = nnz;
+  if ((st = fetch(P->h_colidx, colidx, (size_t)nnz)) != VTM_OK) return fail(st);
+  if ((st = fetch(P->h_vals, vals, (size_t)nnz)) != VTM_OK) return fail(st);
+  if ((st = fetch(P->h_part, partition, (size_t)n)) != VTM_OK) return fail(st);
+  for (int64_t i = 0; i < n; ++i) {
+    if (P->h_part[i] < 0 || P->h_part[i] >= nparts) {
+      set_detail("vtm_plan: partition value out of range at node " + std::to_string(i));
+      return fail(VTM_EINVAL);
+    }
+    for (int64_t q = P->h_rowptr[i]; q < P->h_rowptr[i + 1]; ++q) {
+      int32_t j = P->h_colidx[q];
+      if (j < 0 || j >= n || (q > P->h_rowptr[i] && j <= P->h_colidx[q - 1])) {
+        set_detail("vtm_plan: column indices out of range or not strictly increasing in row " +
+                   std::to_string(i));
+        return fail(VTM_EINVAL);
+      }
+      if (!std::isfinite(P->h_vals[q])) {
+        set_detail("vtm_plan: non-finite matrix value");
+        return fail(VTM_EINVAL);
+      }
+    }
+  }
+  // symmetric values -> Cholesky, else LU without pivoting
+  P->symmetric = true;
+  for (int64_t i = 0; i < n && P->symmetric; ++i)
+    for (int64_t q = P->h_rowptr[i]; q < P->h_rowptr[i + 1]; ++q) {
+      int32_t j = P->h_colidx[q];
+      if (j <= i) continue;
+      int64_t t = csr_find(P, j, (int32_t)i);
+      if (t < 0 || P->h_vals[t] != P->h_vals[q]) {
+        P->symmetric = false;
+        break;
+      }
+    }
+  std::vector<CutPair> pairs;
+  if ((st = build_structure(P, pairs)) != VTM_OK) return fail(st);
+
+  vtm_opts o{};
+  if (opts) o = *opts;
+  P->opts.precision = o.precision;
+  if ((st = vtm_set_opts(P, &o)) != VTM_OK) return fail(st);
+
+  cudaStream_t s = P->stream;
+  // device tables
+  if ((st = upload(P->d_rowptr, P->h_rowptr, s)) != VTM_OK) return fail(st);
+  if ((st = upload(P->d_colidx, P->h_colidx, s)) != VTM_OK) return fail(st);
+  if ((st = upload(P->d_vals, P->h_vals, s)) != VTM_OK) return fail(st);
+  if ((st = upload(P->d_perm, P->perm, s)) != VTM_OK) return fail(st);
+  if ((st = upload(P->tabs.node_off, P->node_off, s)) != VTM_OK) return fail(st);
+  if ((st = upload(P->tabs.bw, P->bw, s)) != VTM_OK) return fail(st);
+  if ((st = upload(P->tabs.band_off, P->band_off, s)) != VTM_OK) return fail(st);
+  if ((st = upload(P->tabs.port_off, P->port_off, s)) != VTM_OK) return fail(st);
+  if ((st = upload(P->tabs.T_off, P->T_off, s)) != VTM_OK) return fail(st);
+  if ((st = upload(P->tabs.T_ld, P->T_ld, s)) != VTM_OK) return fail(st);
+  std::vector<int32_t> order(nparts);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return (P->port_off[a + 1] - P->port_off[a]) > (P->port_off[b + 1] - P->port_off[b]);
+  });
+  if ((st = upload(P->tabs.order, order, s)) != VTM_OK) return fail(st);
+  if ((st = upload(P->d_port_loc, P->port_loc, s)) != VTM_OK) return fail(st);
+  std::vector<int32_t> port_pos(P->port_node.size());
+  for (size_t q = 0; q < port_pos.size(); ++q) port_pos[q] = P->iperm[P->port_node[q]];
+  if ((st = upload(P->d_port_pos, port_pos, s)) != VTM_OK) return fail(st);
+  if ((st = upload(P->d_twin, P->port_twin, s)) != VTM_OK) return fail(st);
+  if ((st = upload(P->d_run, P->port_run, s)) != VTM_OK) return fail(st);
+  const size_t npt = std::max<size_t>(P->port_node.size(), 1);
+  if ((st = dev_alloc(P->d_c64, npt * sizeof(double))) != VTM_OK) return fail(st);
+  if ((st = dev_alloc(P->d_state64, 4 * npt * sizeof(double))) != VTM_OK) return fail(st);
+  if ((st = dev_alloc(P->d_v, (size_t)n * sizeof(double))) != VTM_OK) return fail(st);
+  if ((st = dev_alloc(P->d_v2, (size_t)n * sizeof(double))) != VTM_OK) return fail(st);
+  if ((st = dev_alloc(P->d_xacc, (size_t)n * sizeof(double))) != VTM_OK) return fail(st);
+  if ((st = dev_alloc(P->d_r, (size_t)n * sizeof(double))) != VTM_OK) return fail(st);
+  if ((st = dev_alloc(P->d_bcol, (size_t)n * sizeof(double))) != VTM_OK) return fail(st);
+  if ((st = dev_alloc(P->d_partials, sizeof(double) * std::max<size_t>(nparts, 4096))) != VTM_OK)
+    return fail(st);
+  if ((st = dev_alloc(P->d_ctrl, sizeof(SweepCtrl))) != VTM_OK) return fail(st);
+  if ((st = dev_alloc(P->d_err, 64)) != VTM_OK) return fail(st);
+  if ((st = dev_alloc(P->d_red, 256)) != VTM_OK) return fail(st);
+  if (P->hist_cap == 0) {
+    if ((st = dev_alloc(P->d_hist, 16)) != VTM_OK) return fail(st);
+  }
+  if (cudaMallocHost(&P->h_ctrl, sizeof(SweepCtrl)) != cudaSuccess) {
+    P->h_ctrl = nullptr;
+    return fail(VTM_ENOMEM);
+  }
+  if (cudaEventCreate(&P->ev0) != cudaSuccess || cudaEventCreate(&P->ev1) != cudaSuccess ||
+      cudaEventCreate(&P->evs0) != cudaSuccess || cudaEventCreate(&P->evs1) != cudaSuccess)
+    return fail(VTM_ECUDA);
+  if ((st = assemble_local(P)) != VTM_OK) return fail(st);
+  *out = P;
+  return VTM_OK;
+}
+
+extern "C" vtm_status vtm_set_values(vtm_plan_t P, const double* vals) {
+  if (!P || !vals) return VTM_EINVAL;
+  std::vector<double> old = P->h_vals;
+  vtm_status st = fetch(P->h_vals, vals, (size_t)P->nnz);
+  if (st != VTM_OK) return st;
+  for (double v : P->h_vals)
+    if (!std::isfinite(v)) {
+      P->h_vals = old;
+      set_detail("vtm_set_values: non-finite value");
+      return VTM_EINVAL;
+    }
+  if (P->symmetric) {
+    for (int64_t i = 0; i < P->n; ++i)
+      for (int64_t q = P->h_rowptr[i]; q < P->h_rowptr[i + 1]; ++q) {
+        int32_t j = P->h_colidx[q];
+        if (j <= i) continue;
+        int64_t t = csr_find(P, j, (int32_t)i);
+        if (t < 0 || P->h_vals[t] != P->h_vals[q]) {
+          P->h_vals = old;
+          set_detail("vtm_set_values: the plan was made for a symmetric matrix");
+          return VTM_EINVAL;
+        }
+      }
+  }
+  // the torn lines and the lagged couplings must stay the same
+  if (!same_cut_structure(P)) {
+    P->h_vals = old;
+    set_detail("vtm_set_values: the set of torn lines or lagged couplings changed");
+    return VTM_EINVAL;
+  }
+  st = assemble_local(P);
+  if (st != VTM_OK) {
+    P->h_vals = old;
+    assemble_local(P);
+    return st;
+  }
+  VTM_CUDA_TRY(cudaMemcpyAsync(P->d_vals.p, P->h_vals.data(), P->nnz * sizeof(double),
+                               cudaMemcpyHostToDevice, P->stream));
+  VTM_CUDA_TRY(cudaStreamSynchronize(P->stream));
+  P->factored = false;
+  if (P->transposed) {
+    vtm_destroy(P->transposed);
+    P->transposed = nullptr;
+  }
+  return VTM_OK;
+}
+
+extern "C" vtm_status vtm_plan_get_stats(vtm_plan_t P, vtm_plan_stats* s) {
+  if (!P || !s) return VTM_EINVAL;
+  s->n = P->n;
+  s->nparts = P->nparts;
+  s->nports = (int64_t)P->port_node.size();
+  s->nlagged = (int64_t)P->lag_i.size();
+  s->sum_p2 = P->sum_p2;
+  s->max_ports = P->max_ports;
+  s->max_nodes = P->max_nodes;
+  s->max_band = P->max_bw;
+  s->symmetric = P->symmetric ? 1 : 0;
+  s->t_bytes = (int64_t)(P->d_T64.bytes + P->d_T32.bytes + P->d_T16.bytes);
+  s->factor_bytes = (int64_t)(P->d_Lc.bytes + P->d_Uc.bytes);
+  return VTM_OK;
+}
+
+extern "C" vtm_status vtm_get_ports(vtm_plan_t P, int32_t* node, int32_t* remote, int32_t* part,
+                                    int32_t* twin) {
+  if (!P) return VTM_EINVAL;
+  const size_t npt = P->port_node.size();
+  for (size_t s = 0; s < npt; ++s) {
+    if (node) node[s] = P->port_node[s];
+    if (remote) remote[s] = P->port_remote[s];
+    if (part) part[s] = P->h_part[P->port_node[s]];
+    if (twin) twin[s] = P->port_twin[s];
+  }
+  return VTM_OK;
+}
+
+extern "C" void vtm_destroy(vtm_plan_t P) {
+  if (!P) return;
+  if (P->transposed) vtm_destroy(P->transposed);
+  for (DevBuf* b : P->all_bufs()) dev_free(*b);
+  if (P->h_ctrl) cudaFreeHost(P->h_ctrl);
+  if (P->ev0) cudaEventDestroy(P->ev0);
+  if (P->ev1) cudaEventDestroy(P->ev1);
+  if (P->evs0) cudaEventDestroy(P->evs0);
+  if (P->evs1) cudaEventDestroy(P->evs1);
+  delete P;
+}
+
+extern "C" const char* vtm_strerror(vtm_status s) {
+  switch (s) {
+    case VTM_OK: return "success";
+    case VTM_EINVAL: return "invalid argument";
+    case VTM_ENOMEM: return "out of memory";
+    case VTM_ESINGULAR: return "singular local matrix (bad pivot)";
+    case VTM_ENOCONV: return "tolerance not reached within the sweep/refinement limit";
+    case VTM_EDIVERGED: return "iteration diverged";
+    case VTM_ETIMEOUT: return "device-side wait timed out";
+    case VTM_ECUDA: return "CUDA runtime error";
+    case VTM_EINTERNAL: return "internal error";
+    case VTM_ENOTFACTORED: return "plan not factored";
+  }
+  return "unknown status";
+}
+
+extern "C" const char* vtm_last_error_detail(void) { return g_detail.c_str(); }

@@ -1,0 +1,620 @@
+// VTM sweeps, recovery, FP64 residual and the refinement driver.
+//
+// One sweep (Sec. VI, Eq. 11 and Eq. 14 with unit line delay) in condensed
+// form, for every sub-circuit P at once:
+//   w_in(s)  = w_out(twin(s)) of the previous sweep      (zero at sweep 1)
+//   w_out_P  = T_P w_in_P + c_P,  c_P(s) = 2 W beta_s x0(l(s)),  x0 = K_P^-1 b_P
+// where w_in = W u_twin - i_twin is the wave arriving over the virtual line
+// and w_out = W u - i the wave sent back (Eq. 5).  The port voltage of a
+// sweep is u = (w_in + w_out)/(2W) and the node voltage behind it follows
+// from the twin row of Eq. 11, (2g + W) u - 2g x = w_in.
+//
+// Residual.  The interior rows of every sub-circuit are solved exactly, so
+// b - A x^k is non-zero only at nodes with torn branches, where branch e
+// between i (in P) and j (in Q) contributes g (x_i + x_j - 2 u_s); written
+// with the waves of both ends, g (x_i + x_j - 2 u_s) =
+//   ((W - 2g) u_s + (W + 2g) u_t - w_in_s - w_in_t) / 2.
+// The sweep kernel of sweep k evaluates this for sweep k-1 (it reads that
+// sweep's waves anyway), sums the ports of each node, squares, reduces per
+// tile and finally over tiles in a fixed order (deterministic), and raises a
+// device flag when ||r|| <= tol ||b||.  The paper gives no stopping rule;
+// this is the relative 2-norm residual after every sweep.
+//
+// Recovery of the node voltages of the converged sweep:
+//   x_P = K_P^-1 (b_P + sum_s beta_s w_in(s) e_l(s)).
+#include <algorithm>
+#include <cmath>
+#include <type_traits>
+
+#include "vtm_internal.h"
+
+namespace vtm {
+
+// ---------------------------------------------------------------------------
+// small kernels
+// ---------------------------------------------------------------------------
+
+__global__ void gather_perm_kernel(const int32_t* __restrict__ perm, const double* __restrict__ src,
+                                   double* __restrict__ dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[perm[i]];
+}
+
+// dst[perm[i]] (+)= src[i]
+__global__ void scatter_perm_kernel(const int32_t* __restrict__ perm, const double* __restrict__ src,
+                                    double* __restrict__ dst, int64_t n, int accumulate) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (accumulate) dst[perm[i]] += src[i];
+    else dst[perm[i]] = src[i];
+  }
+}
+
+// c(s) = 2 W beta_s x0(l(s)) (permuted position pos(s))
+template <class WT>
+__global__ void port_const_kernel(const int32_t* __restrict__ port_pos, const double* __restrict__ beta,
+                                  const double* __restrict__ x0, double W, WT* __restrict__ c,
+                                  int64_t nports) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nports;
+       s += (int64_t)gridDim.x * blockDim.x)
+    c[s] = (WT)(2.0 * W * beta[s] * x0[port_pos[s]]);
+}
+
+// v(l(s)) += sum over the node's ports of beta_s w_in(s); w_in of the chosen
+// sweep sits in state[slot][s].x
+template <class WT>
+__global__ void inject_kernel(const int32_t* __restrict__ port_pos, const uint8_t* __restrict__ run,
+                              const double* __restrict__ beta, const WT* __restrict__ st,
+                              double* __restrict__ v, int64_t nports) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nports;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    int nr = run[s];
+    if (!nr) continue;
+    double acc = 0.0;
+    for (int q = 0; q < nr; ++q) acc += beta[s + q] * (double)st[2 * (s + q)];
+    v[port_pos[s]] += acc;
+  }
+}
+
+// Fixed-order sum of `count` doubles by one block (result valid in thread 0).
+__device__ double block_sum_fixed(const double* __restrict__ a, int64_t count) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < count; i += blockDim.x) acc += a[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = acc;
+  __syncthreads();
+  double tot = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += red[i];
+  __syncthreads();
+  return tot;
+}
+
+__device__ double block_sum_value(double v) {
+  __shared__ double red2[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red2[w] = v;
+  __syncthreads();
+  double tot = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += red2[i];
+  __syncthreads();
+  return tot;
+}
+
+// r = b - A x (global order, FP64), ||r||^2 and ||b||^2 reduced in a fixed
+// order; out[0] = ||r||^2, out[1] = ||b||^2.  counter must be 0 on entry and
+// is left 0.
+__global__ void __launch_bounds__(256) residual_kernel(const int64_t* __restrict__ rowptr,
+                                                       const int32_t* __restrict__ col,
+                                                       const double* __restrict__ val,
+                                                       const double* __restrict__ x,
+                                                       const double* __restrict__ b,
+                                                       double* __restrict__ r, int64_t n,
+                                                       double* __restrict__ partials,
+                                                       unsigned* __restrict__ counter,
+                                                       double* __restrict__ out) {
+  double rr = 0.0, bb = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = b[i];
+    for (int64_t q = rowptr[i]; q < rowptr[i + 1]; ++q) acc -= val[q] * x[col[q]];
+    if (r) r[i] = acc;
+    rr += acc * acc;
+    bb += b[i] * b[i];
+  }
+  double trr = block_sum_value(rr);
+  double tbb = block_sum_value(bb);
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = trr;
+    partials[gridDim.x + blockIdx.x] = tbb;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    double a = block_sum_fixed(partials, gridDim.x);
+    double c = block_sum_fixed(partials + gridDim.x, gridDim.x);
+    if (threadIdx.x == 0) {
+      out[0] = a;
+      out[1] = c;
+      *counter = 0u;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the sweep
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float load_t(const float* p) { return __ldg(p); }
+__device__ __forceinline__ double load_t(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float load_t(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+template <class TT, class WT>
+__global__ void __launch_bounds__(256) sweep_kernel(
+    const TT* __restrict__ T, const int64_t* __restrict__ T_off, const int32_t* __restrict__ T_ld,
+    const int32_t* __restrict__ port_off, const int32_t* __restrict__ order,
+    const int32_t* __restrict__ twin, const double* __restrict__ g,
+    const uint8_t* __restrict__ run, const WT* __restrict__ c, WT* __restrict__ state,
+    int64_t nports, double W, SweepCtrl* __restrict__ ctrl, double* __restrict__ partials,
+    double* __restrict__ hist, int hist_len, int nparts) {
+  using AT = WT;  // accumulation type: FP64 for FP64 waves, FP32 otherwise
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ int s_k, s_flag;
+  __shared__ bool s_last;
+  if (threadIdx.x == 0) {
+    s_k = *((volatile int*)&ctrl->k);
+    s_flag = *((volatile int*)&ctrl->flag);
+  }
+  __syncthreads();
+  if (s_flag) return;
+  const int k = s_k;
+  const int tile = order[blockIdx.x];
+  const int p0 = port_off[tile];
+  const int p = port_off[tile + 1] - p0;
+  WT* w_in = reinterpret_cast<WT*>(smem_raw);
+  AT* rs = reinterpret_cast<AT*>(smem_raw + sizeof(WT) * ((p + 1) & ~1));
+  const WT* prev = state + (size_t)((k - 1) & 1) * nports * 2;
+  WT* cur = state + (size_t)(k & 1) * nports * 2;
+  const AT hW = (AT)W, inv2W = (AT)(0.5 / W);
+  // gather the incident waves (delay 1) and the residual terms of sweep k-1
+  for (int s = threadIdx.x; s < p; s += blockDim.x) {
+    const int gs = p0 + s;
+    AT wi = 0, rc = 0;
+    if (k > 1) {
+      const int tw = twin[gs];
+      const AT wi_t = (AT)prev[2 * tw], wo_t = (AT)prev[2 * tw + 1];
+      const AT wi_s = (AT)prev[2 * gs], wo_s = (AT)prev[2 * gs + 1];
+      wi = wo_t;
+      const AT gg = (AT)g[gs];
+      const AT us = (wi_s + wo_s) * inv2W, ut = (wi_t + wo_t) * inv2W;
+      rc = (AT)0.5 * ((hW - 2 * gg) * us + (hW + 2 * gg) * ut - wi_s - wi_t);
+    }
+    w_in[s] = (WT)wi;
+    rs[s] = rc;
+  }
+  __syncthreads();
+  double sq = 0.0;
+  if (k > 1) {
+    for (int s = threadIdx.x; s < p; s += blockDim.x) {
+      const int nr = run[p0 + s];
+      if (nr) {
+        double r = 0.0;
+        for (int q = 0; q < nr; ++q) r += (double)rs[s + q];
+        sq += r * r;
+      }
+    }
+  }
+  const double tile_sq = block_sum_value(sq);
+  // apply the reflection matrix: w_out(s) = c(s) + sum_t T(s, t) w_in(t)
+  const TT* Tb = T + T_off[tile];
+  const int ld = T_ld[tile];
+  for (int s = threadIdx.x; s < p; s += blockDim.x) {
+    AT acc = (AT)c[p0 + s];
+    const TT* col = Tb + s;
+#pragma unroll 8
+    for (int t = 0; t < p; ++t) acc += (AT)load_t(col + (size_t)t * ld) * (AT)w_in[t];
+    cur[2 * (p0 + s)] = w_in[s];
+    cur[2 * (p0 + s) + 1] = (WT)acc;
+  }
+  // the last tile to finish reduces the residual of sweep k-1
+  if (threadIdx.x == 0) {
+    partials[tile] = tile_sq;
+    __threadfence();
+    s_last = atomicAdd(&ctrl->counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const double tot = block_sum_fixed(partials, nparts);
+  if (threadIdx.x == 0) {
+    int flag = 0;
+    if (k > 1) {
+      const int ks = k - 1;
+      if (hist && ks <= hist_len) hist[ks - 1] = sqrt(tot / ctrl->bnorm2);
+      if (ks == 1) ctrl->first_res2 = tot;
+      ctrl->last_res2 = tot;
+      if (!isfinite(tot) || (ks > 1 && tot > 1e12 * ctrl->first_res2 && ctrl->first_res2 > 0)) {
+        flag = 3;
+      } else if (tot <= ctrl->tol2) {
+        flag = 1;
+        ctrl->conv_sweep = ks;
+      }
+    }
+    if (!flag && k >= ctrl->k_max) flag = 2;
+    ctrl->counter = 0u;
+    ctrl->k = k + 1;
+    __threadfence();
+    ctrl->flag = flag;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host driver
+// ---------------------------------------------------------------------------
+
+static int grid_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 8));
+}
+
+struct SweepLaunch {
+  const void* T;
+  const void* c;
+  void* state;
+  int prec;
+};
+
+template <class TT, class WT>
+static void launch_sweep(vtm_plan_s* P, const TT* T, const WT* c, WT* state, int threads,
+                         size_t smem, double* hist, int hist_len) {
+  sweep_kernel<TT, WT><<<P->nparts, threads, smem, P->stream>>>(
+      T, P->tabs.T_off.as<int64_t>(), P->tabs.T_ld.as<int32_t>(), P->tabs.port_off.as<int32_t>(),
+      P->tabs.order.as<int32_t>(), P->d_twin.as<int32_t>(), P->d_g.as<double>(),
+      P->d_run.as<uint8_t>(), c, state, (int64_t)P->port_node.size(), P->W,
+      P->d_ctrl.as<SweepCtrl>(), P->d_partials.as<double>(), hist, hist_len, P->nparts);
+}
+
+// Run sweeps from a zero state until the interface residual is below
+// target2 (absolute, squared) or the sweep budget is used.  Returns the
+// sweep whose waves are to be recovered and its flag.
+static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int budget, int prec,
+                             double* hist, int hist_len, int* sweep_out, int* flag_out) {
+  cudaStream_t s = P->stream;
+  const int64_t npt = (int64_t)P->port_node.size();
+  SweepCtrl h{};
+  h.k = 1;
+  h.flag = 0;
+  h.counter = 0;
+  h.conv_sweep = 0;
+  h.k_max = budget;
+  h.tol2 = target2;
+  h.bnorm2 = bnorm2 > 0 ? bnorm2 : 1.0;
+  *P->h_ctrl = h;
+  VTM_CUDA_TRY(cudaMemcpyAsync(P->d_ctrl.p, P->h_ctrl, sizeof(SweepCtrl), cudaMemcpyHostToDevice, s));
+  const int threads = P->max_ports <= 64 ? 64 : (P->max_ports <= 128 ? 128 : 256);
+  size_t wsz = prec == VTM_PREC_FP64 ? sizeof(double) : sizeof(float);
+  size_t smem = (size_t)((P->max_ports + 2) & ~1) * wsz * 2 + 16;
+  if (prec == VTM_PREC_FP64) {
+    VTM_CUDA_TRY(cudaMemsetAsync(P->d_state64.p, 0, 4 * npt * sizeof(double), s));
+  } else {
+    VTM_CUDA_TRY(cudaMemsetAsync(P->d_state32.p, 0, 4 * npt * sizeof(float), s));
+  }
+  int launched = 0;
+  while (true) {
+    const int m = std::min(P->opts.check_every, budget + 1 - launched);
+    VTM_CUDA_TRY(cudaEventRecord(P->evs0, s));
+    for (int i = 0; i < m; ++i) {
+      if (prec == VTM_PREC_FP64)
+        launch_sweep<double, double>(P, P->d_T64.as<double>(), P->d_c64.as<double>(),
+                                     P->d_state64.as<double>(), threads, smem, hist, hist_len);
+      else if (prec == VTM_PREC_FP32)
+        launch_sweep<float, float>(P, P->d_T32.as<float>(), P->d_c32.as<float>(),
+                                   P->d_state32.as<float>(), threads, smem, hist, hist_len);
+      else
+        launch_sweep<__nv_bfloat16, float>(P, P->d_T16.as<__nv_bfloat16>(), P->d_c32.as<float>(),
+                                           P->d_state32.as<float>(), threads, smem, hist, hist_len);
+    }
+    launched += m;
+    VTM_CUDA_TRY(cudaGetLastError());
+    VTM_CUDA_TRY(cudaEventRecord(P->evs1, s));
+    VTM_CUDA_TRY(cudaMemcpyAsync(P->h_ctrl, P->d_ctrl.p, sizeof(SweepCtrl), cudaMemcpyDeviceToHost, s));
+    VTM_CUDA_TRY(cudaStreamSynchronize(s));
+    float bms = 0.f;
+    VTM_CUDA_TRY(cudaEventElapsedTime(&bms, P->evs0, P->evs1));
+    P->sweep_ms += bms;
+    P->sweep_launch_count += m;
+    P->launch_count += m;
+    if (P->h_ctrl->flag || launched > budget) break;
+  }
+  const SweepCtrl& r = *P->h_ctrl;
+  *flag_out = r.flag;
+  if (r.flag == 1) *sweep_out = r.conv_sweep;
+  else *sweep_out = std::min(r.k - 1, budget);
+  return VTM_OK;
+}
+
+static vtm_status norms(vtm_plan_s* P, const double* x, const double* b, double* r, double* rr,
+                        double* bb) {
+  cudaStream_t s = P->stream;
+  const int grid = grid_for(P->n);
+  double* out = P->d_red.as<double>() + 2;
+  unsigned* counter = reinterpret_cast<unsigned*>(P->d_red.p);
+  P->launch_count++;
+  residual_kernel<<<grid, 256, 0, s>>>(P->d_rowptr.as<int64_t>(), P->d_colidx.as<int32_t>(),
+                                       P->d_vals.as<double>(), x, b, r, P->n,
+                                       P->d_partials.as<double>(), counter, out);
+  VTM_CUDA_TRY(cudaGetLastError());
+  double h[2];
+  VTM_CUDA_TRY(cudaMemcpyAsync(h, out, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  VTM_CUDA_TRY(cudaStreamSynchronize(s));
+  *rr = h[0];
+  *bb = h[1];
+  return VTM_OK;
+}
+
+// Solve one column: d_b (global order) -> d_x (global order).
+static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, double tol,
+                            vtm_info* info, bool record_hist) {
+  cudaStream_t s = P->stream;
+  const int64_t n = P->n;
+  const int64_t npt = (int64_t)P->port_node.size();
+  const int prec = P->opts.precision;
+  const int g1 = grid_for(n), g2 = grid_for(std::max<int64_t>(npt, 1));
+  double* v = P->d_v.as<double>();
+  double* xacc = P->d_xacc.as<double>();
+  double* r = P->d_r.as<double>();
+  if (prec != VTM_PREC_FP64) {
+    VTM_TRY(dev_alloc(P->d_c32, std::max<int64_t>(npt, 1) * sizeof(float)));
+    VTM_TRY(dev_alloc(P->d_state32, 4 * std::max<int64_t>(npt, 1) * sizeof(float)));
+  }
+  double rr0, bb;
+  // ||b||^2 (x = 0 gives r = b)
+  VTM_CUDA_TRY(cudaMemsetAsync(xacc, 0, n * sizeof(double), s));
+  VTM_TRY(norms(P, xacc, d_b, r, &rr0, &bb));
+  const double bnorm = std::sqrt(bb);
+  info->sweeps = 0;
+  info->outer_steps = 0;
+  info->relres = 0.0;
+  info->first_sweep_converged = 0;
+  if (bb == 0.0) {
+    VTM_CUDA_TRY(cudaMemsetAsync(d_x, 0, n * sizeof(double), s));
+    return VTM_OK;
+  }
+  const double target = tol * bnorm;
+  double rnorm = bnorm;
+  double inner_tol = P->opts.inner_tol;
+  if (inner_tol <= 0) inner_tol = prec == VTM_PREC_FP32 ? 1e-6 : (prec == VTM_PREC_BF16 ? 3e-3 : 0.0);
+  const int max_outer = prec == VTM_PREC_FP64 ? 4 : P->opts.max_outer;
+  int sweeps_left = P->opts.max_sweeps;
+  vtm_status result = VTM_ENOCONV;
+  for (int outer = 0; outer < max_outer; ++outer) {
+    // inner problem A d = r (r = b at the first step)
+    const double* rhs = outer == 0 ? d_b : r;
+    gather_perm_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, v, n);
+    P->launch_count++;
+    launch_band_solve(P, v, 1, n, s);
+    int kc = 0, flag = 1;
+    if (npt > 0) {
+      if (prec == VTM_PREC_FP64)
+        port_const_kernel<double><<<g2, 256, 0, s>>>(P->d_port_pos.as<int32_t>(), P->d_beta.as<double>(),
+                                                     v, P->W, P->d_c64.as<double>(), npt);
+      else
+        port_const_kernel<float><<<g2, 256, 0, s>>>(P->d_port_pos.as<int32_t>(), P->d_beta.as<double>(),
+                                                    v, P->W, P->d_c32.as<float>(), npt);
+      VTM_CUDA_TRY(cudaGetLastError());
+      P->launch_count++;
+      double t_abs = prec == VTM_PREC_FP64 ? target : std::max(target, inner_tol * rnorm);
+      double* hist = (record_hist && outer == 0 && P->opts.history) ? P->d_hist.as<double>() : nullptr;
+      const int hist_len = hist ? P->opts.history_len : 0;
+      if (hist) VTM_CUDA_TRY(cudaMemsetAsync(hist, 0, hist_len * sizeof(double), s));
+      if (sweeps_left <= 0) break;
+      VTM_TRY(run_sweeps(P, rnorm * rnorm, t_abs * t_abs, sweeps_left, prec, hist, hist_len, &kc, &flag));
+      if (hist) {
+        VTM_CUDA_TRY(cudaMemcpyAsync(P->opts.history, hist, hist_len * sizeof(double),
+                                     cudaMemcpyDeviceToHost, s));
+      }
+      if (outer == 0 && flag == 1) info->first_sweep_converged = kc;
+      info->sweeps += kc;
+      sweeps_left -= kc;
+      // recovery of the sweep kc: x_P = K_P^-1 (rhs_P + B beta w_in)
+      gather_perm_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, v, n);
+      P->launch_count += 2;
+      const int slot = kc & 1;
+      if (prec == VTM_PREC_FP64)
+        inject_kernel<double><<<g2, 256, 0, s>>>(P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(),
+                                                 P->d_beta.as<double>(),
+                                                 P->d_state64.as<double>() + (size_t)slot * npt * 2, v, npt);
+      else
+        inject_kernel<float><<<g2, 256, 0, s>>>(P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(),
+                                                P->d_beta.as<double>(),
+                                                P->d_state32.as<float>() + (size_t)slot * npt * 2, v, npt);
+      launch_band_solve(P, v, 1, n, s);
+    } else {
+      info->sweeps += 1;  // one direct solve per sub-circuit
+      if (outer == 0) info->first_sweep_converged = 1;
+    }
+    scatter_perm_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), v, xacc, n, outer > 0 ? 1 : 0);
+    P->launch_count++;
+    VTM_CUDA_TRY(cudaGetLastError());
+    info->outer_steps = outer + 1;
+    double rr;
+    VTM_TRY(norms(P, xacc, d_b, r, &rr, &bb));
+    rnorm = std::sqrt(rr);
+    info->relres = rnorm / bnorm;
+    if (flag == 3 || !std::isfinite(rnorm)) {
+      result = VTM_EDIVERGED;
+      break;
+    }
+    if (rnorm <= target) {
+      result = VTM_OK;
+      break;
+    }
+    if (flag == 2 || sweeps_left <= 0) {
+      result = VTM_ENOCONV;
+      break;
+    }
+  }
+  VTM_CUDA_TRY(cudaMemcpyAsync(d_x, xacc, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  VTM_CUDA_TRY(cudaStreamSynchronize(s));
+  if (result == VTM_ENOCONV) set_detail("vtm_solve: tolerance not met");
+  if (result == VTM_EDIVERGED) set_detail("vtm_solve: the iteration diverged");
+  return result;
+}
+
+vtm_status solve_columns(vtm_plan_s* P, const double* d_b, double* d_x, int64_t nrhs, double tol,
+                         vtm_info* info) {
+  vtm_info agg{};
+  vtm_status worst = VTM_OK;
+  for (int64_t col = 0; col < nrhs; ++col) {
+    vtm_info one{};
+    vtm_status st = solve_one(P, d_b + col * P->n, d_x + col * P->n, tol, &one, col == 0);
+    if (st != VTM_OK && st != VTM_ENOCONV && st != VTM_EDIVERGED) return st;
+    if (st != VTM_OK && worst == VTM_OK) worst = st;
+    agg.sweeps = std::max(agg.sweeps, one.sweeps);
+    agg.outer_steps = std::max(agg.outer_steps, one.outer_steps);
+    agg.relres = std::max(agg.relres, one.relres);
+    if (col == 0) agg.first_sweep_converged = one.first_sweep_converged;
+  }
+  *info = agg;
+  return worst;
+}
+
+vtm_status residual_norms(vtm_plan_s* P, const double* d_x, const double* d_b, int64_t nrhs,
+                          double* rel) {
+  for (int64_t c = 0; c < nrhs; ++c) {
+    double rr, bb;
+    VTM_TRY(norms(P, d_x + c * P->n, d_b + c * P->n, nullptr, &rr, &bb));
+    rel[c] = bb > 0 ? std::sqrt(rr / bb) : std::sqrt(rr);
+  }
+  return VTM_OK;
+}
+
+}  // namespace vtm
+
+using namespace vtm;
+
+// Host/device staging of the caller's vectors.
+struct Staged {
+  vtm_plan_s* P = nullptr;
+  const double* in_dev = nullptr;
+  double* out_dev = nullptr;
+  DevBuf tmp_in, tmp_out;
+  bool out_host = false;
+  ~Staged() {
+    dev_free(tmp_in);
+    dev_free(tmp_out);
+  }
+};
+
+static vtm_status stage(vtm_plan_s* P, const double* in, double* out, int64_t count, Staged& S) {
+  S.P = P;
+  if (is_device_ptr(in)) {
+    S.in_dev = in;
+  } else {
+    VTM_TRY(dev_alloc(S.tmp_in, count * sizeof(double)));
+    VTM_CUDA_TRY(cudaMemcpyAsync(S.tmp_in.p, in, count * sizeof(double), cudaMemcpyHostToDevice, P->stream));
+    S.in_dev = S.tmp_in.as<double>();
+  }
+  if (out) {
+    if (is_device_ptr(out)) {
+      S.out_dev = out;
+    } else {
+      VTM_TRY(dev_alloc(S.tmp_out, count * sizeof(double)));
+      S.out_dev = S.tmp_out.as<double>();
+      S.out_host = true;
+    }
+  }
+  return VTM_OK;
+}
+
+static vtm_status solve_entry(vtm_plan_s* P, const double* b, double* x, int64_t nrhs, double tol,
+                              vtm_info* info) {
+  if (!P || !b || !x || nrhs <= 0 || !(tol > 0)) return VTM_EINVAL;
+  if (!P->factored) return VTM_ENOTFACTORED;
+  cudaSetDevice(P->device);
+  vtm_info local{};
+  if (!info) info = &local;
+  Staged S;
+  const int64_t count = P->n * nrhs;
+  VTM_TRY(stage(P, b, x, count, S));
+  P->launch_count = 0;
+  P->sweep_launch_count = 0;
+  P->sweep_ms = 0.0;
+  VTM_CUDA_TRY(cudaEventRecord(P->ev0, P->stream));
+  vtm_status st = solve_columns(P, S.in_dev, S.out_dev, nrhs, tol, info);
+  VTM_CUDA_TRY(cudaEventRecord(P->ev1, P->stream));
+  if (S.out_host)
+    VTM_CUDA_TRY(cudaMemcpyAsync(x, S.out_dev, count * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
+  VTM_CUDA_TRY(cudaStreamSynchronize(P->stream));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, P->ev0, P->ev1);
+  info->t_solve_ms = ms;
+  info->kernel_launches = P->launch_count;
+  info->sweep_launches = P->sweep_launch_count;
+  info->t_sweeps_ms = P->sweep_ms;
+  return st;
+}
+
+extern "C" vtm_status vtm_solve(vtm_plan_t P, const double* b, double* x, int64_t nrhs, double tol,
+                                vtm_info* info) {
+  return solve_entry(P, b, x, nrhs, tol, info);
+}
+
+extern "C" vtm_status vtm_adjoint(vtm_plan_t P, const double* g, double* lam, int64_t nrhs,
+                                  double tol, vtm_info* info) {
+  if (!P) return VTM_EINVAL;
+  if (P->symmetric) return solve_entry(P, g, lam, nrhs, tol, info);
+  if (!P->factored) return VTM_ENOTFACTORED;
+  if (!P->transposed) {
+    // A^T in CSR = A in CSC
+    const int64_t n = P->n;
+    std::vector<int64_t> rp(n + 1, 0);
+    std::vector<int32_t> ci(P->nnz);
+    std::vector<double> va(P->nnz);
+    for (int64_t q = 0; q < P->nnz; ++q) rp[P->h_colidx[q] + 1]++;
+    for (int64_t i = 0; i < n; ++i) rp[i + 1] += rp[i];
+    std::vector<int64_t> fill(rp.begin(), rp.end() - 1);
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t q = P->h_rowptr[i]; q < P->h_rowptr[i + 1]; ++q) {
+        int64_t d = fill[P->h_colidx[q]]++;
+        ci[d] = (int32_t)i;
+        va[d] = P->h_vals[q];
+      }
+    vtm_plan_t T = nullptr;
+    VTM_TRY(vtm_plan(n, rp.data(), ci.data(), va.data(), P->h_part.data(), P->nparts, P->Zc, &P->opts,
+                     P->stream, &T));
+    vtm_status st = vtm_factor(T);
+    if (st != VTM_OK) {
+      vtm_destroy(T);
+      return st;
+    }
+    P->transposed = T;
+  }
+  P->transposed->opts = P->opts;
+  return solve_entry(P->transposed, g, lam, nrhs, tol, info);
+}
+
+extern "C" vtm_status vtm_residual_norm(vtm_plan_t P, const double* x, const double* b, int64_t nrhs,
+                                        double* rel) {
+  if (!P || !x || !b || !rel || nrhs <= 0) return VTM_EINVAL;
+  cudaSetDevice(P->device);
+  const int64_t count = P->n * nrhs;
+  Staged Sx, Sb;
+  VTM_TRY(stage(P, x, nullptr, count, Sx));
+  VTM_TRY(stage(P, b, nullptr, count, Sb));
+  vtm_status st = residual_norms(P, Sx.in_dev, Sb.in_dev, nrhs, rel);
+  VTM_CUDA_TRY(cudaStreamSynchronize(P->stream));
+  dev_free(Sx.tmp_in);
+  dev_free(Sb.tmp_in);
+  return st;
+}

@@ -1,0 +1,176 @@
+// Internal declarations shared by the translation units of libvtm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/vtm.h"
+
+namespace vtm {
+
+// Thread-local detail message for vtm_last_error_detail().
+void set_detail(const std::string& msg);
+
+#define VTM_CUDA_TRY(expr)                                                        \
+  do {                                                                            \
+    cudaError_t e_ = (expr);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      ::vtm::set_detail(std::string(#expr) + ": " + cudaGetErrorString(e_));      \
+      return (e_ == cudaErrorMemoryAllocation) ? VTM_ENOMEM : VTM_ECUDA;          \
+    }                                                                             \
+  } while (0)
+
+#define VTM_TRY(expr)                         \
+  do {                                        \
+    vtm_status s_ = (expr);                   \
+    if (s_ != VTM_OK) return s_;              \
+  } while (0)
+
+// A device allocation released by the plan.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// Device-side control block of one solve (one per plan).
+struct SweepCtrl {
+  int k;               // index of the sweep the next launch runs (1-based)
+  int flag;            // 0 running, 1 converged, 2 sweep limit, 3 diverged
+  unsigned counter;    // CTAs of the current launch that finished
+  int conv_sweep;      // sweep whose residual met the tolerance
+  int k_max;           // last sweep allowed
+  int pad0;
+  double tol2;         // (tol * ||b||)^2 for the residual test
+  double bnorm2;       // ||b||^2 of the current right-hand side
+  double first_res2;   // squared residual of sweep 1 (divergence guard)
+  double last_res2;    // squared residual of the last completed sweep
+};
+
+// Offsets and sizes describing one tile-contiguous operator family.
+struct TileTables {
+  DevBuf node_off;   // int32[nparts+1]: first permuted position of each tile
+  DevBuf bw;         // int32[nparts]: half bandwidth
+  DevBuf band_off;   // int64[nparts]: offset (doubles) of the tile's band columns
+  DevBuf port_off;   // int32[nparts+1]
+  DevBuf T_off;      // int64[nparts]: element offset of the tile's T^T block
+  DevBuf T_ld;       // int32[nparts]: padded row length of the T^T block
+  DevBuf order;      // int32[nparts]: launch order of tiles (largest p first)
+};
+
+}  // namespace vtm
+
+struct vtm_plan_s {
+  // problem description
+  int64_t n = 0;
+  int64_t nnz = 0;
+  int32_t nparts = 0;
+  double Zc = 1.0;
+  double W = 1.0;
+  vtm_opts opts{};
+  cudaStream_t stream = nullptr;
+  bool symmetric = true;
+  bool factored = false;
+  int device = 0;
+
+  // host copies of the input (values change with vtm_set_values)
+  std::vector<int64_t> h_rowptr;
+  std::vector<int32_t> h_colidx;
+  std::vector<double> h_vals;
+  std::vector<int32_t> h_part;
+
+  // tiles: permuted (tile-contiguous, band-ordered) numbering
+  std::vector<int32_t> node_off;  // nparts+1
+  std::vector<int32_t> perm;      // perm[pos] = node
+  std::vector<int32_t> iperm;     // iperm[node] = pos
+  std::vector<int32_t> bw;        // half bandwidth per tile
+  std::vector<int64_t> band_off;  // offset (doubles) per tile: n_P * (bw+1)
+  int64_t band_elems = 0;
+  int32_t max_nodes = 0, max_bw = 0, max_ports = 0;
+
+  // ports (two per torn branch), grouped by tile, then by (node, remote)
+  std::vector<int32_t> port_off;     // nparts+1
+  std::vector<int32_t> port_node;    // global node
+  std::vector<int32_t> port_remote;  // node across the branch
+  std::vector<int32_t> port_twin;    // twin port
+  std::vector<int32_t> port_loc;     // permuted position - tile start of the port node
+  std::vector<int64_t> port_pos_ij;  // CSR position of a(node, remote) or -1
+  std::vector<int64_t> port_pos_ji;  // CSR position of a(remote, node) or -1
+  std::vector<double> port_g;        // branch conductance
+  std::vector<uint8_t> port_run;     // ports left in this node's run (>=1) at a run start, else 0
+
+  // lagged couplings (cut entries that are not branches), by row
+  std::vector<int32_t> lag_i, lag_j;
+  std::vector<int64_t> lag_pos;
+  std::vector<double> lag_rho;
+
+  // reflection-matrix layout
+  std::vector<int32_t> T_ld;
+  std::vector<int64_t> T_off;
+  int64_t T_elems = 0;
+  int64_t sum_p2 = 0;
+
+  // device copies
+  vtm::TileTables tabs;
+  vtm::DevBuf d_rowptr, d_colidx, d_vals;  // A for the FP64 residual
+  vtm::DevBuf d_perm;                      // int32[n]
+  vtm::DevBuf d_Lc, d_Uc;                  // band factors (doubles)
+  vtm::DevBuf d_port_loc, d_port_pos, d_twin, d_g, d_beta, d_run;
+  vtm::DevBuf d_T64, d_T32, d_T16;         // reflection matrices (T^T blocks)
+  vtm::DevBuf d_c64, d_c32;                // constant term of the sweep
+  vtm::DevBuf d_state64, d_state32;        // [2][nports] (w_in, w_out) pairs
+  vtm::DevBuf d_v, d_v2;                   // permuted work vectors [n]
+  vtm::DevBuf d_xacc, d_r, d_bcol;         // refinement vectors [n] (global order)
+  vtm::DevBuf d_partials;                  // double[max(nparts, 1024)]
+  vtm::DevBuf d_ctrl;                      // SweepCtrl
+  vtm::DevBuf d_hist;                      // double[history capacity]
+  vtm::DevBuf d_err;                       // int error word of factor kernels
+  vtm::DevBuf d_red;                       // double[2] + unsigned counter for reductions
+  int hist_cap = 0;
+  vtm::SweepCtrl* h_ctrl = nullptr;        // pinned mirror
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evs0 = nullptr, evs1 = nullptr;
+  // per-call accounting (reset by each solve)
+  int launch_count = 0;
+  int sweep_launch_count = 0;
+  double sweep_ms = 0.0;
+
+  // adjoint of an unsymmetric system
+  vtm_plan_s* transposed = nullptr;
+
+  std::vector<vtm::DevBuf*> all_bufs();
+};
+
+namespace vtm {
+
+vtm_status dev_alloc(DevBuf& b, size_t bytes);
+void dev_free(DevBuf& b);
+template <class T>
+vtm_status upload(DevBuf& b, const std::vector<T>& h, cudaStream_t s) {
+  VTM_TRY(dev_alloc(b, h.size() * sizeof(T) > 0 ? h.size() * sizeof(T) : 16));
+  if (!h.empty()) VTM_CUDA_TRY(cudaMemcpyAsync(b.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  return VTM_OK;
+}
+
+bool is_device_ptr(const void* p);
+
+// plan.cu
+vtm_status assemble_local(vtm_plan_s* P);  // host band values of K_P + port tables -> device
+
+// factor.cu
+vtm_status factor_tiles(vtm_plan_s* P);
+vtm_status build_reflections(vtm_plan_s* P);
+
+// solve.cu
+vtm_status solve_columns(vtm_plan_s* P, const double* d_b, double* d_x, int64_t nrhs, double tol,
+                         vtm_info* info);
+vtm_status residual_norms(vtm_plan_s* P, const double* d_x, const double* d_b, int64_t nrhs,
+                          double* rel);
+
+// Launch helpers exported between translation units.
+void launch_band_solve(vtm_plan_s* P, double* v, int ncols, int64_t vec_stride, cudaStream_t s);
+
+}  // namespace vtm

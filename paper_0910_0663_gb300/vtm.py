@@ -1,0 +1,119 @@
+"""User-facing API over libvtm: torch tensors in, torch tensors out.
+
+``Plan`` wraps one ``vtm_plan`` handle (wire tearing + port table), its
+factorisation (``vtm_factor``) and the solves (``vtm_solve`` /
+``vtm_adjoint``).  PyTorch supplies device memory and the CUDA stream; all
+arithmetic runs in libvtm's kernels.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import _vtm as C
+
+
+def _dev(a, dtype, device):
+    if isinstance(a, np.ndarray):
+        a = torch.from_numpy(np.ascontiguousarray(a))
+    return a.to(device=device, dtype=dtype).contiguous()
+
+
+class Plan:
+    """A torn circuit ready for VTM solves.
+
+    indptr/indices/data: CSR of A (int64 / int32 / float64); partition: node
+    -> sub-circuit (int32); Zc: characteristic impedance of the virtual lines
+    (W = 1/Zc).  ``precision`` selects the arithmetic of the sweeps:
+    "fp64", or "fp32"/"bf16" inside FP64 iterative refinement.
+    """
+
+    def __init__(self, indptr, indices, data, partition, nparts, Zc=1.0, precision="fp64",
+                 device="cuda", stream=None, max_sweeps=0, check_every=0, inner_tol=0.0,
+                 max_outer=0, factor=True):
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.n = int(len(indptr) - 1)
+        self.nparts = int(nparts)
+        self._opts = dict(precision=precision, max_sweeps=max_sweeps, check_every=check_every,
+                          inner_tol=inner_tol, max_outer=max_outer)
+        self._history = None
+        rp = _dev(indptr, torch.int64, self.device)
+        ci = _dev(indices, torch.int32, self.device)
+        va = _dev(data, torch.float64, self.device)
+        pa = _dev(partition, torch.int32, self.device)
+        self.handle = C.vtm_plan(self.n, rp, ci, va, pa, self.nparts, float(Zc),
+                                 C.make_opts(**self._opts), self.stream.cuda_stream)
+        if factor:
+            self.factor()
+
+    # -- set-up ------------------------------------------------------------
+    def factor(self):
+        C.vtm_factor(self.handle)
+
+    def set_values(self, data):
+        C.vtm_set_values(self.handle, _dev(data, torch.float64, self.device))
+
+    def set_options(self, history_len=0, **kw):
+        self._opts.update(kw)
+        self._history = np.zeros(history_len, np.float64) if history_len else None
+        C.vtm_set_opts(self.handle, C.make_opts(**self._opts, history=self._history))
+
+    @property
+    def history(self):
+        return None if self._history is None else self._history.copy()
+
+    def stats(self) -> dict:
+        return C.vtm_plan_get_stats(self.handle).as_dict()
+
+    def ports(self):
+        return C.vtm_get_ports(self.handle)
+
+    def reflection(self, part) -> np.ndarray:
+        return C.vtm_get_reflection(self.handle, part)
+
+    # -- solves --------------------------------------------------------------
+    def _run(self, fn, b, tol, check):
+        b = b if torch.is_tensor(b) else torch.from_numpy(np.ascontiguousarray(b))
+        squeeze = b.dim() == 1
+        b2 = b.reshape(1, -1) if squeeze else b
+        if b2.is_cuda:
+            b2 = b2.to(torch.float64).contiguous()
+            x = torch.empty_like(b2)
+        else:
+            b2 = b2.to(torch.float64).contiguous()
+            x = torch.empty_like(b2)
+        st, info = fn(self.handle, b2, x, b2.shape[0], tol, check=check)
+        x = x.reshape(-1) if squeeze else x
+        return x, info.as_dict(), st
+
+    def solve(self, b, tol=1e-10, check=True):
+        """x with A x = b.  b: (n,) or (nrhs, n) tensor (CPU or CUDA)."""
+        x, info, _ = self._run(C.vtm_solve, b, tol, check)
+        return x, info
+
+    def adjoint(self, g, tol=1e-10, check=True):
+        x, info, _ = self._run(C.vtm_adjoint, g, tol, check)
+        return x, info
+
+    def residual(self, x, b):
+        x = x.reshape(-1, self.n).to(torch.float64).contiguous()
+        b = b.reshape(-1, self.n).to(torch.float64).contiguous()
+        return C.vtm_residual_norm(self.handle, x, b, x.shape[0])
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            C.vtm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plan_workload(w, precision="fp64", device="cuda", **kw) -> Plan:
+    """Plan and factor a ``workloads.Workload``."""
+    return Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc, precision=precision,
+                device=device, **kw)

@@ -1,0 +1,208 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Floating-point bars (FP64 path):
+* sweep counts equal to the oracle's (the same linear iteration and the
+  same stopping rule); +-1 is accepted only when the oracle's residual at
+  that sweep is within 1% of the tolerance;
+* node voltages at the same sweep count within 1e-11 relative (the two
+  sides evaluate the same iteration in different orders: the oracle solves
+  the twin-row system of Eq. 11, the library applies the condensed
+  reflection matrices);
+* reflection matrices within 1e-11 of (W - S)(W + S)^-1;
+* the returned relative residual <= tol (checked by the oracle's own SpMV).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import vtm_oracle as O
+from paper_0910_0663_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vtm():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_0910_0663_gb300 import build
+    build.build()
+    from paper_0910_0663_gb300 import vtm as V
+    return V
+
+
+def _match_ports(plan, tear, P):
+    """Permutation from the library's port order of tile P to the oracle's."""
+    node, remote, part, twin = plan.ports()
+    sel = np.flatnonzero(part == P)
+    lib_keys = list(zip(node[sel].tolist(), remote[sel].tolist()))
+    ora = tear.tile_ports[P]
+    ora_keys = list(zip(tear.port_node[ora].tolist(), tear.port_remote[ora].tolist()))
+    pos = {k: i for i, k in enumerate(ora_keys)}
+    return np.array([pos[k] for k in lib_keys])
+
+
+def _check_against_oracle(vtm, w, tol=1e-10, x_rel=1e-11, Zc=None):
+    Zc = w.Zc if Zc is None else Zc
+    A = w.csr()
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=Zc)
+    x, info = plan.solve(torch.from_numpy(w.b).cuda(), tol=tol)
+    ref = O.vtm_midpoint(A, w.partition, w.nparts, w.b, W=1.0 / Zc, tol=tol)
+    assert ref.converged
+    k_gpu, k_ref = info["sweeps"], ref.sweeps
+    if k_gpu != k_ref:
+        assert abs(k_gpu - k_ref) == 1
+        near = ref.history[min(k_gpu, k_ref) - 1].max()
+        assert abs(near - tol) <= 0.01 * tol
+    else:
+        xs = x.cpu().numpy().reshape(w.b.shape)
+        assert np.abs(xs - ref.x).max() <= x_rel * np.abs(ref.x).max()
+    rel = O.residual_norms(A, x.cpu().numpy().reshape(w.b.shape), w.b)
+    assert rel.max() <= tol
+    # both are FP64 norms of a residual that is 1e-10 of b: rounding of the
+    # individual residual entries shows in the 4th-5th digit
+    assert info["relres"] == pytest.approx(rel.max(), rel=1e-3)
+    return plan, info, ref
+
+
+def test_small_grid_fp64_matches_oracle(vtm):
+    w = wl.c1_small_grid()
+    plan, info, ref = _check_against_oracle(vtm, w)
+    assert info["outer_steps"] == 1
+
+
+def test_small_grid_reflection_matrices(vtm):
+    w = wl.c1_small_grid()
+    A = w.csr()
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc)
+    tear = O.tear_midpoint(A, w.partition, w.nparts)
+    for P in range(w.nparts):
+        T_lib = plan.reflection(P)
+        _, T_ref = O.reflection_ops(A, tear, P, 1.0 / w.Zc)
+        perm = _match_ports(plan, tear, P)
+        assert np.abs(T_lib - T_ref[np.ix_(perm, perm)]).max() < 1e-11
+
+
+def test_interface_residual_history_matches_full_residual(vtm):
+    # the library's residual (torn branches only) equals the oracle's full
+    # b - A x^k at every sweep (interior rows are solved exactly)
+    w = wl.grid2d(24, 24, 8, 6, Zc=0.5, seed=21)
+    A = w.csr()
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc)
+    plan.set_options(history_len=60)
+    x, info = plan.solve(torch.from_numpy(w.b).cuda(), tol=1e-10)
+    h = plan.history
+    ref = O.vtm_midpoint(A, w.partition, w.nparts, w.b, W=1 / w.Zc, tol=0, max_sweeps=60)
+    k = min(60, info["sweeps"])
+    assert np.allclose(h[:k], ref.history[:k, 0], rtol=1e-9, atol=1e-13)
+
+
+@pytest.mark.parametrize("Zc", [0.25, 1.0, 4.0])
+def test_power_grid_zc_sweep(vtm, Zc):
+    w = wl.power_grid(128, 128, 32, 32, Zc=Zc, seed=2)
+    _check_against_oracle(vtm, w)
+
+
+def test_ragged_tiles_and_random_partition(vtm):
+    w = wl.grid2d(21, 26, 6, 7, Zc=0.7, seed=5, ground=0.01)
+    _check_against_oracle(vtm, w)
+    rng = np.random.default_rng(7)
+    part = rng.integers(0, 7, w.n).astype(np.int32)
+    part[:7] = np.arange(7)
+    w2 = wl.Workload("rand", w.n, w.indptr, w.indices, w.data, part, 7, w.b, 1.3)
+    _check_against_oracle(vtm, w2)
+
+
+def test_thermal_boxes_small(vtm):
+    w = wl.thermal3d(6, 12, 12, 12, nrhs=3, seed=1, min_box=20, max_box=400)
+    _check_against_oracle(vtm, w)
+
+
+def test_single_partition_is_one_direct_solve(vtm):
+    w = wl.grid2d(20, 20, 20, 20, seed=3)
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, 1, Zc=1.0)
+    x, info = plan.solve(torch.from_numpy(w.b[0]).cuda(), tol=1e-12)
+    assert info["sweeps"] == 1
+    x_star = np.linalg.solve(w.csr().toarray(), w.b[0])
+    assert np.abs(x.cpu().numpy() - x_star).max() <= 1e-12 * np.abs(x_star).max()
+
+
+def test_fixed_point_is_direct_solution(vtm):
+    w = wl.c1_small_grid()
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=4.0)
+    x, info = plan.solve(torch.from_numpy(w.b[0]).cuda(), tol=1e-13)
+    x_star = np.linalg.solve(w.csr().toarray(), w.b[0])
+    assert np.abs(x.cpu().numpy() - x_star).max() <= 1e-9 * np.abs(x_star).max()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_mixed_precision_reaches_fp64_tolerance(vtm, precision):
+    w = wl.power_grid(256, 256, 32, 32, Zc=1.0, seed=4)
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc, precision=precision)
+    x, info = plan.solve(torch.from_numpy(w.b[0]).cuda(), tol=1e-10)
+    rel = O.residual_norms(w.csr(), x.cpu().numpy()[None], w.b)
+    assert rel.max() <= 1e-10
+    assert info["outer_steps"] >= 2
+
+
+def test_host_and_device_buffers_agree(vtm):
+    w = wl.grid2d(16, 16, 4, 8, seed=6)
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=1.0)
+    xd, _ = plan.solve(torch.from_numpy(w.b[0]).cuda(), tol=1e-10)
+    xh, _ = plan.solve(torch.from_numpy(w.b[0]), tol=1e-10)
+    assert not xh.is_cuda
+    assert torch.equal(xd.cpu(), xh)
+    # reruns are bit-identical (fixed-order reductions)
+    xd2, _ = plan.solve(torch.from_numpy(w.b[0]).cuda(), tol=1e-10)
+    assert torch.equal(xd, xd2)
+
+
+def test_multiple_columns(vtm):
+    w = wl.grid2d(16, 16, 8, 8, seed=8, nrhs=3)
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=1.0)
+    x, info = plan.solve(torch.from_numpy(w.b).cuda(), tol=1e-10)
+    for r in range(3):
+        xr, _ = plan.solve(torch.from_numpy(w.b[r]).cuda(), tol=1e-10)
+        assert torch.equal(xr, x[r])
+
+
+def test_zero_rhs_and_errors(vtm):
+    from paper_0910_0663_gb300 import _vtm as C
+    w = wl.grid2d(8, 8, 4, 4, seed=9)
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=1.0)
+    x, info = plan.solve(torch.zeros(w.n, dtype=torch.float64, device="cuda"))
+    assert torch.count_nonzero(x) == 0
+    bad = w.partition.copy()
+    bad[3] = 99
+    with pytest.raises(C.VTMError) as e:
+        vtm.Plan(w.indptr, w.indices, w.data, bad, w.nparts, Zc=1.0)
+    assert e.value.status == C.VTM_EINVAL
+    empty = np.zeros(w.n, np.int32)
+    with pytest.raises(C.VTMError) as e:
+        vtm.Plan(w.indptr, w.indices, w.data, empty, 2, Zc=1.0)
+    assert e.value.status == C.VTM_EINVAL
+    with pytest.raises(C.VTMError) as e:
+        vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=-1.0)
+    assert e.value.status == C.VTM_EINVAL
+    p2 = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=1.0, factor=False)
+    with pytest.raises(C.VTMError) as e:
+        p2.solve(torch.from_numpy(w.b[0]).cuda())
+    assert e.value.status == C.VTM_ENOTFACTORED
+    # sweep limit -> ENOCONV with the last iterate
+    p3 = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=1.0, max_sweeps=5)
+    x, info = p3.solve(torch.from_numpy(w.b[0]).cuda(), check=False)
+    assert info["sweeps"] == 5 and info["relres"] > 1e-10
+
+
+def test_set_values_then_refactor(vtm):
+    w = wl.grid2d(16, 16, 8, 8, seed=10)
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=1.0)
+    g2 = w.g * 1.3
+    ip, ix, d2 = wl.assemble_nodal(w.n, w.edges, g2, w.ground)
+    assert np.array_equal(ip, w.indptr) and np.array_equal(ix, w.indices)
+    plan.set_values(d2)
+    plan.factor()
+    x, info = plan.solve(torch.from_numpy(w.b[0]).cuda(), tol=1e-11)
+    A2 = O.csr_matrix(ip, ix, d2, w.n)
+    x_star = np.linalg.solve(A2.toarray(), w.b[0])
+    assert np.abs(x.cpu().numpy() - x_star).max() <= 1e-8 * np.abs(x_star).max()
