@@ -71,7 +71,9 @@ typedef struct {
   int max_sweeps;    /* sweeps per vtm_solve call, all refinement steps together; default 200000 */
   int check_every;   /* sweeps launched between two host polls of the convergence flag; default 32 */
   double inner_tol;  /* relative tolerance of each inner solve in the refinement modes;
-                        0 -> 1e-6 (FP32) / 3e-3 (BF16) */
+                        0 -> 1e-5 (FP32) / 1e-2 (BF16).  An inner solve also ends when
+                        its residual has not dropped by 10% within 64 sweeps (its
+                        rounding floor); the FP64 refinement then continues. */
   int max_outer;     /* refinement steps in the FP32/BF16 modes; default 40 */
   double* history;   /* optional host array: relative (interface) residual after each
                         sweep k=1..history_len of the first column; NULL = not recorded */

@@ -565,6 +565,7 @@ extern "C" vtm_status vtm_plan(int64_t n, const int64_t* rowptr, const int32_t* 
   if ((st = dev_alloc(P->d_ctrl, sizeof(SweepCtrl))) != VTM_OK) return fail(st);
   if ((st = dev_alloc(P->d_err, 64)) != VTM_OK) return fail(st);
   if ((st = dev_alloc(P->d_red, 256)) != VTM_OK) return fail(st);
+  if (cudaMemsetAsync(P->d_red.p, 0, 256, s) != cudaSuccess) return fail(VTM_ECUDA);  // counters start at 0
   if (P->hist_cap == 0) {
     if ((st = dev_alloc(P->d_hist, 16)) != VTM_OK) return fail(st);
   }

@@ -243,10 +243,17 @@ __global__ void __launch_bounds__(256) sweep_kernel(
       if (hist && ks <= hist_len) hist[ks - 1] = sqrt(tot / ctrl->bnorm2);
       if (ks == 1) ctrl->first_res2 = tot;
       ctrl->last_res2 = tot;
+      if (ks == 1 || tot < 0.81 * ctrl->best_res2) {
+        ctrl->best_res2 = tot;
+        ctrl->best_k = ks;
+      }
       if (!isfinite(tot) || (ks > 1 && tot > 1e12 * ctrl->first_res2 && ctrl->first_res2 > 0)) {
         flag = 3;
       } else if (tot <= ctrl->tol2) {
         flag = 1;
+        ctrl->conv_sweep = ks;
+      } else if (ctrl->stall > 0 && ks - ctrl->best_k >= ctrl->stall) {
+        flag = 4;  // rounding floor of a low-precision inner solve
         ctrl->conv_sweep = ks;
       }
     }
@@ -288,7 +295,7 @@ static void launch_sweep(vtm_plan_s* P, const TT* T, const WT* c, WT* state, int
 // target2 (absolute, squared) or the sweep budget is used.  Returns the
 // sweep whose waves are to be recovered and its flag.
 static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int budget, int prec,
-                             double* hist, int hist_len, int* sweep_out, int* flag_out) {
+                             double* hist, int hist_len, int stall, int* sweep_out, int* flag_out) {
   cudaStream_t s = P->stream;
   const int64_t npt = (int64_t)P->port_node.size();
   SweepCtrl h{};
@@ -297,6 +304,9 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   h.counter = 0;
   h.conv_sweep = 0;
   h.k_max = budget;
+  h.stall = stall;
+  h.best_k = 0;
+  h.best_res2 = 0.0;
   h.tol2 = target2;
   h.bnorm2 = bnorm2 > 0 ? bnorm2 : 1.0;
   *P->h_ctrl = h;
@@ -338,7 +348,7 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   }
   const SweepCtrl& r = *P->h_ctrl;
   *flag_out = r.flag;
-  if (r.flag == 1) *sweep_out = r.conv_sweep;
+  if (r.flag == 1 || r.flag == 4) *sweep_out = r.conv_sweep;
   else *sweep_out = std::min(r.k - 1, budget);
   return VTM_OK;
 }
@@ -393,7 +403,7 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
   const double target = tol * bnorm;
   double rnorm = bnorm;
   double inner_tol = P->opts.inner_tol;
-  if (inner_tol <= 0) inner_tol = prec == VTM_PREC_FP32 ? 1e-6 : (prec == VTM_PREC_BF16 ? 3e-3 : 0.0);
+  if (inner_tol <= 0) inner_tol = prec == VTM_PREC_FP32 ? 1e-5 : (prec == VTM_PREC_BF16 ? 1e-2 : 0.0);
   const int max_outer = prec == VTM_PREC_FP64 ? 4 : P->opts.max_outer;
   int sweeps_left = P->opts.max_sweeps;
   vtm_status result = VTM_ENOCONV;
@@ -418,7 +428,10 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
       const int hist_len = hist ? P->opts.history_len : 0;
       if (hist) VTM_CUDA_TRY(cudaMemsetAsync(hist, 0, hist_len * sizeof(double), s));
       if (sweeps_left <= 0) break;
-      VTM_TRY(run_sweeps(P, rnorm * rnorm, t_abs * t_abs, sweeps_left, prec, hist, hist_len, &kc, &flag));
+      // low-precision inner solves stop at their rounding floor as well
+      const int stall = prec == VTM_PREC_FP64 ? 0 : 64;
+      VTM_TRY(run_sweeps(P, rnorm * rnorm, t_abs * t_abs, sweeps_left, prec, hist, hist_len, stall,
+                         &kc, &flag));
       if (hist) {
         VTM_CUDA_TRY(cudaMemcpyAsync(P->opts.history, hist, hist_len * sizeof(double),
                                      cudaMemcpyDeviceToHost, s));

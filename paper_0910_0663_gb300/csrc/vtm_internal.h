@@ -40,11 +40,14 @@ struct DevBuf {
 // Device-side control block of one solve (one per plan).
 struct SweepCtrl {
   int k;               // index of the sweep the next launch runs (1-based)
-  int flag;            // 0 running, 1 converged, 2 sweep limit, 3 diverged
+  int flag;            // 0 running, 1 converged, 2 sweep limit, 3 diverged, 4 stalled
   unsigned counter;    // CTAs of the current launch that finished
   int conv_sweep;      // sweep whose residual met the tolerance
   int k_max;           // last sweep allowed
+  int best_k;          // sweep with the smallest residual so far
+  int stall;           // sweeps without a 10% improvement that end the run (0 = never)
   int pad0;
+  double best_res2;    // smallest squared residual so far
   double tol2;         // (tol * ||b||)^2 for the residual test
   double bnorm2;       // ||b||^2 of the current right-hand side
   double first_res2;   // squared residual of sweep 1 (divergence guard)
