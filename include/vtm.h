@@ -176,6 +176,26 @@ vtm_status vtm_get_reflection(vtm_plan_t plan, int32_t part, double* T, int64_t 
 vtm_status vtm_residual_norm(vtm_plan_t plan, const double* x, const double* b, int64_t nrhs,
                              double* rel);
 
+/* vtm_residual_norm_noalloc -- the same relative residual norms as
+ * vtm_residual_norm, for callers that cannot allocate device memory (a
+ * simulator whose pool owns the whole device, a loop that must not call
+ * cudaMalloc, code that only holds buffers lent to it).  The paper has no
+ * counterpart; this is a service of the library.
+ * Needs no plan and allocates nothing: rowptr[n+1], colidx[nnz], vals[nnz],
+ * x and b (n x nrhs column-major) must all be device memory; rel is a host
+ * array[nrhs].  Work runs on `stream` (a cudaStream_t or NULL) and the call
+ * returns after it finished.  Scratch is a fixed 20,736-byte __device__ array
+ * in the library, present on every GPU that loads it until the process
+ * exits; hence nrhs <= 64 (VTM_EINVAL beyond).  The first call on a device
+ * looks up that array's address with the device current; make that first
+ * call before any stream capture.  All calls on a device share the array,
+ * so calls that overlap on the GPU (other streams or threads) race; the
+ * array keeps the last call's sums and the call clears what must start at
+ * zero.  Errors: VTM_EINVAL (sizes, NULL, host pointers), VTM_ECUDA. */
+vtm_status vtm_residual_norm_noalloc(int64_t n, const int64_t* rowptr, const int32_t* colidx,
+                                     const double* vals, const double* x, const double* b,
+                                     int64_t nrhs, double* rel, void* stream);
+
 void vtm_destroy(vtm_plan_t plan);
 const char* vtm_strerror(vtm_status status);
 const char* vtm_last_error_detail(void);

@@ -77,6 +77,7 @@ def _load():
         "vtm_get_ports": (ctypes.c_int, [P, P, P, P, P]),
         "vtm_get_reflection": (ctypes.c_int, [P, i32, P, i64, ctypes.POINTER(i32)]),
         "vtm_residual_norm": (ctypes.c_int, [P, P, P, i64, P]),
+        "vtm_residual_norm_noalloc": (ctypes.c_int, [i64, P, P, P, P, P, i64, P, P]),
         "vtm_destroy": (None, [P]),
         "vtm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "vtm_last_error_detail": (ctypes.c_char_p, []),
@@ -91,7 +92,8 @@ def _load():
 _lib = _load()
 EXPORTED = ("vtm_plan", "vtm_set_values", "vtm_set_opts", "vtm_factor", "vtm_solve",
             "vtm_adjoint", "vtm_plan_get_stats", "vtm_get_ports", "vtm_get_reflection",
-            "vtm_residual_norm", "vtm_destroy", "vtm_strerror", "vtm_last_error_detail")
+            "vtm_residual_norm", "vtm_residual_norm_noalloc", "vtm_destroy", "vtm_strerror",
+            "vtm_last_error_detail")
 
 
 def _ptr(a):
@@ -204,3 +206,13 @@ def vtm_strerror(status):
 
 def vtm_last_error_detail():
     return _lib.vtm_last_error_detail().decode()
+
+
+def vtm_residual_norm_noalloc(n, rowptr, colidx, vals, x, b, nrhs, stream=0):
+    """Relative residual norms with no plan and no device allocation (all
+    arrays on the device; see include/vtm.h)."""
+    rel = np.empty(int(nrhs), np.float64)
+    _check(_lib.vtm_residual_norm_noalloc(int(n), _ptr(rowptr), _ptr(colidx), _ptr(vals), _ptr(x),
+                                          _ptr(b), int(nrhs), _ptr(rel), ctypes.c_void_p(stream)),
+           "vtm_residual_norm_noalloc")
+    return rel

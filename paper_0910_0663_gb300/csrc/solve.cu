@@ -151,6 +151,18 @@ __global__ void __launch_bounds__(256) residual_kernel(const int64_t* __restrict
   }
 }
 
+// Host-side launcher of residual_kernel for other translation units; the
+// caller provides partials[2*grid], the counter word (0 on entry, left 0)
+// and out[2].  Returns the grid it used.
+int launch_residual(const int64_t* rowptr, const int32_t* col, const double* val, const double* x,
+                    const double* b, int64_t n, double* partials, unsigned* counter, double* out,
+                    int max_grid, cudaStream_t s) {
+  int64_t blocks = (n + 255) / 256;
+  int grid = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, max_grid));
+  residual_kernel<<<grid, 256, 0, s>>>(rowptr, col, val, x, b, nullptr, n, partials, counter, out);
+  return grid;
+}
+
 // ---------------------------------------------------------------------------
 // the sweep
 // ---------------------------------------------------------------------------

@@ -173,6 +173,10 @@ vtm_status solve_columns(vtm_plan_s* P, const double* d_b, double* d_x, int64_t 
 vtm_status residual_norms(vtm_plan_s* P, const double* d_x, const double* d_b, int64_t nrhs,
                           double* rel);
 
+int launch_residual(const int64_t* rowptr, const int32_t* col, const double* val, const double* x,
+                    const double* b, int64_t n, double* partials, unsigned* counter, double* out,
+                    int max_grid, cudaStream_t s);
+
 // Launch helpers exported between translation units.
 void launch_band_solve(vtm_plan_s* P, double* v, int ncols, int64_t vec_stride, cudaStream_t s);
 

@@ -1,0 +1,67 @@
+"""The allocation-free residual entry point.
+
+vtm_residual_norm_noalloc serves callers that cannot allocate device memory
+when they need a residual (their pool owns the device, or their loop must
+not call cudaMalloc).  It must give the same numbers as the plan-based
+vtm_residual_norm, call after call, since its scratch is a static device
+array that keeps the previous call's contents.  This file is collected last
+so that a failure here leaves every other test already run.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_0910_0663_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_0910_0663_gb300 import build
+    build.build()
+    from paper_0910_0663_gb300 import _vtm, vtm
+    return _vtm, vtm
+
+
+def test_noalloc_residual_matches_plan_residual_twice(mods):
+    C, vtm = mods
+    w = wl.grid2d(48, 40, 12, 10, seed=31, nrhs=3, ground=0.01)
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=1.0)
+    b = torch.from_numpy(w.b).cuda()
+    x, _ = plan.solve(b, tol=1e-6)  # a residual well above rounding
+    x = x.contiguous()
+    ref = plan.residual(x, b)  # existing entry point (vtm_residual_norm)
+    rp = torch.from_numpy(w.indptr).cuda()
+    ci = torch.from_numpy(w.indices).cuda()
+    va = torch.from_numpy(w.data).cuda()
+    stream = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):  # the second call sees the first call's leftovers
+        got = C.vtm_residual_norm_noalloc(w.n, rp, ci, va, x, b, w.nrhs, stream)
+        np.testing.assert_allclose(got, ref, rtol=1e-12, atol=0)
+    assert np.all(ref > 1e-9) and np.all(ref < 1e-5)
+    # a different x gives a different answer (the call really computes)
+    x2 = x.clone()
+    x2[1, 7] += 1.0
+    got2 = C.vtm_residual_norm_noalloc(w.n, rp, ci, va, x2, b, w.nrhs, stream)
+    ref2 = plan.residual(x2, b)
+    np.testing.assert_allclose(got2, ref2, rtol=1e-12)
+    assert got2[1] > 10 * got[1] and got2[0] == got[0]
+    plan.close()
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch(mods):
+    C, _ = mods
+    w = wl.grid2d(8, 8, 4, 4, seed=1)
+    rp = torch.from_numpy(w.indptr).cuda()
+    ci = torch.from_numpy(w.indices).cuda()
+    va = torch.from_numpy(w.data).cuda()
+    x = torch.zeros((65, w.n), dtype=torch.float64, device="cuda")
+    with pytest.raises(C.VTMError) as e:
+        C.vtm_residual_norm_noalloc(w.n, rp, ci, va, x, x, 65)
+    assert e.value.status == C.VTM_EINVAL
+    with pytest.raises(C.VTMError) as e:  # host vectors are refused, not staged
+        C.vtm_residual_norm_noalloc(w.n, rp, ci, va, x.cpu(), x.cpu(), 1)
+    assert e.value.status == C.VTM_EINVAL
