@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--grid", type=int, default=2048)
     ap.add_argument("--zc", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep-kernel", type=int, default=0, choices=[0, 1, 2],
+                    help="0: automatic, 1: direct-load sweep kernel, 2: bulk-copy staged kernel")
     return ap.parse_args()
 
 
@@ -249,7 +251,8 @@ def run_mode(args, prec, w, dev, stream, b_dev, b_host, x_host, flush, world):
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
             plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc,
-                            precision=prec, device=dev, stream=stream, factor=False)
+                            precision=prec, device=dev, stream=stream, factor=False,
+                            sweep_kernel=args.sweep_kernel)
             t1 = time.perf_counter()
             plan.factor()
         torch.cuda.synchronize()

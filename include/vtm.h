@@ -66,6 +66,13 @@ enum {
   VTM_PREC_BF16 = 2  /* BF16 T_P, FP32 waves and accumulate, inside FP64 iterative refinement */
 };
 
+/* Iteration run by a plan. */
+enum {
+  VTM_METHOD_VTM = 0, /* virtual transmission lines on the torn branches (Sec. VI) */
+  VTM_METHOD_BJ = 1   /* block Jacobi over the same sub-circuits (the comparison method of
+                         Sec. X): every cut entry is applied with one sweep of delay */
+};
+
 typedef struct {
   int precision;     /* VTM_PREC_*; default VTM_PREC_FP64 */
   int max_sweeps;    /* sweeps per vtm_solve call, all refinement steps together; default 200000 */
@@ -75,6 +82,9 @@ typedef struct {
                         its residual has not dropped by 10% within 64 sweeps (its
                         rounding floor); the FP64 refinement then continues. */
   int max_outer;     /* refinement steps in the FP32/BF16 modes; default 40 */
+  int method;        /* VTM_METHOD_VTM (default) or VTM_METHOD_BJ; read by vtm_plan only */
+  int sweep_kernel;  /* 0 (default): automatic (direct-load for FP64, bulk-copy staged
+                        otherwise); 1: direct-load kernel; 2: bulk-copy staged kernel */
   double* history;   /* optional host array: relative (interface) residual after each
                         sweep k=1..history_len of the first column; NULL = not recorded */
   int history_len;
@@ -175,6 +185,36 @@ vtm_status vtm_get_reflection(vtm_plan_t plan, int32_t part, double* T, int64_t 
  * x, b: n x nrhs column-major (host or device); rel: host array[nrhs]. */
 vtm_status vtm_residual_norm(vtm_plan_t plan, const double* x, const double* b, int64_t nrhs,
                              double* rel);
+
+/* ---- resistor networks: branch map and gradients (adjoint of Eq. 1) ----
+ * A netmap ties a branch list (e: i -- j, conductance g_e) and node-to-ground
+ * conductances to the CSR pattern of A = sum_e g_e (e_i - e_j)(e_i - e_j)^T
+ * + diag(ground) (nodal analysis, Sec. II, Eq. 1; Lemma 1). */
+typedef struct vtm_netmap_s* vtm_netmap_t;
+
+/* vtm_netmap_create -- rowptr[n+1], colidx[nnz] (host or device): the CSR
+ * pattern, which must hold every diagonal and both (i,j), (j,i) of every
+ * branch; ei[nedges], ej[nedges] (int64, host or device): branch ends, no
+ * self-loops, no parallel branches.  Work of the map runs on `stream`.
+ * Errors: VTM_EINVAL. */
+vtm_status vtm_netmap_create(int64_t n, const int64_t* rowptr, const int32_t* colidx,
+                             int64_t nedges, const int64_t* ei, const int64_t* ej, void* stream,
+                             vtm_netmap_t* out);
+
+/* vtm_netmap_values -- vals[nnz] = values of A for branch conductances
+ * g[nedges] and ground[n] (NULL = no ground); all device arrays; each
+ * diagonal is summed in a fixed order (deterministic).  Stream-ordered. */
+vtm_status vtm_netmap_values(vtm_netmap_t map, const int64_t* rowptr, const double* g,
+                             const double* ground, double* vals);
+
+/* vtm_netmap_gradient -- for lam = A^-T dL/dx (vtm_adjoint) and x (n x nrhs,
+ * column-major, device): grad_g[e] = -sum_r (lam_i - lam_j)(x_i - x_j) and,
+ * if grad_ground is not NULL, grad_ground[i] = -sum_r lam_i x_i.  dL/db is
+ * lam itself.  Device arrays; stream-ordered. */
+vtm_status vtm_netmap_gradient(vtm_netmap_t map, const double* lam, const double* x, int64_t nrhs,
+                               double* grad_g, double* grad_ground);
+
+void vtm_netmap_destroy(vtm_netmap_t map);
 
 /* vtm_residual_norm_noalloc -- the same relative residual norms as
  * vtm_residual_norm, for callers that cannot allocate device memory (a

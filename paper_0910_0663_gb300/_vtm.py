@@ -20,12 +20,14 @@ LIB_PATH = os.path.join(_HERE, "libvtm.so")
 VTM_OK, VTM_EINVAL, VTM_ENOMEM, VTM_ESINGULAR, VTM_ENOCONV = 0, -1, -2, -3, -4
 VTM_EDIVERGED, VTM_ETIMEOUT, VTM_ECUDA, VTM_EINTERNAL, VTM_ENOTFACTORED = -5, -6, -7, -8, -9
 PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
+METHOD = {"vtm": 0, "bj": 1}
 
 
 class vtm_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_sweeps", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("max_outer", ctypes.c_int), ("history", ctypes.POINTER(ctypes.c_double)),
+                ("max_outer", ctypes.c_int), ("method", ctypes.c_int), ("sweep_kernel", ctypes.c_int),
+                ("history", ctypes.POINTER(ctypes.c_double)),
                 ("history_len", ctypes.c_int)]
 
 
@@ -78,6 +80,10 @@ def _load():
         "vtm_get_reflection": (ctypes.c_int, [P, i32, P, i64, ctypes.POINTER(i32)]),
         "vtm_residual_norm": (ctypes.c_int, [P, P, P, i64, P]),
         "vtm_residual_norm_noalloc": (ctypes.c_int, [i64, P, P, P, P, P, i64, P, P]),
+        "vtm_netmap_create": (ctypes.c_int, [i64, P, P, i64, P, P, P, ctypes.POINTER(P)]),
+        "vtm_netmap_values": (ctypes.c_int, [P, P, P, P, P]),
+        "vtm_netmap_gradient": (ctypes.c_int, [P, P, P, i64, P, P]),
+        "vtm_netmap_destroy": (None, [P]),
         "vtm_destroy": (None, [P]),
         "vtm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "vtm_last_error_detail": (ctypes.c_char_p, []),
@@ -92,8 +98,9 @@ def _load():
 _lib = _load()
 EXPORTED = ("vtm_plan", "vtm_set_values", "vtm_set_opts", "vtm_factor", "vtm_solve",
             "vtm_adjoint", "vtm_plan_get_stats", "vtm_get_ports", "vtm_get_reflection",
-            "vtm_residual_norm", "vtm_residual_norm_noalloc", "vtm_destroy", "vtm_strerror",
-            "vtm_last_error_detail")
+            "vtm_residual_norm", "vtm_residual_norm_noalloc", "vtm_netmap_create",
+            "vtm_netmap_values", "vtm_netmap_gradient", "vtm_netmap_destroy", "vtm_destroy",
+            "vtm_strerror", "vtm_last_error_detail")
 
 
 def _ptr(a):
@@ -117,13 +124,15 @@ def _check(status, where):
 
 
 def make_opts(precision="fp64", max_sweeps=0, check_every=0, inner_tol=0.0, max_outer=0,
-              history=None):
+              history=None, sweep_kernel=0, method="vtm"):
     o = vtm_opts()
     o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
     o.max_sweeps = max_sweeps
     o.check_every = check_every
     o.inner_tol = inner_tol
     o.max_outer = max_outer
+    o.sweep_kernel = sweep_kernel
+    o.method = METHOD[method] if isinstance(method, str) else int(method)
     if history is not None:
         assert history.dtype == np.float64 and history.flags["C_CONTIGUOUS"]
         o.history = history.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
@@ -216,3 +225,24 @@ def vtm_residual_norm_noalloc(n, rowptr, colidx, vals, x, b, nrhs, stream=0):
                                           _ptr(b), int(nrhs), _ptr(rel), ctypes.c_void_p(stream)),
            "vtm_residual_norm_noalloc")
     return rel
+
+
+def vtm_netmap_create(n, rowptr, colidx, nedges, ei, ej, stream=0):
+    h = ctypes.c_void_p()
+    _check(_lib.vtm_netmap_create(int(n), _ptr(rowptr), _ptr(colidx), int(nedges), _ptr(ei), _ptr(ej),
+                                  ctypes.c_void_p(stream), ctypes.byref(h)), "vtm_netmap_create")
+    return h
+
+
+def vtm_netmap_values(netmap, rowptr, g, ground, vals):
+    _check(_lib.vtm_netmap_values(netmap, _ptr(rowptr), _ptr(g), _ptr(ground), _ptr(vals)),
+           "vtm_netmap_values")
+
+
+def vtm_netmap_gradient(netmap, lam, x, nrhs, grad_g, grad_ground=None):
+    _check(_lib.vtm_netmap_gradient(netmap, _ptr(lam), _ptr(x), int(nrhs), _ptr(grad_g),
+                                    _ptr(grad_ground)), "vtm_netmap_gradient")
+
+
+def vtm_netmap_destroy(netmap):
+    _lib.vtm_netmap_destroy(netmap)

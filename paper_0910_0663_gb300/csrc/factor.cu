@@ -5,9 +5,10 @@
 // right-looking band Cholesky (symmetric A) or band LU without pivoting,
 // one CTA per sub-circuit, with the active (bw+1) x (bw+1) window in shared
 // memory addressed circularly.  The factors are stored column-wise:
-//   Lc[j][a] = L(j+a, j), a = 1..bw;  Lc[j][0] = 1 / L(j, j)
-//   Uc[j][b] = U(j-b, j), b = 1..bw;  Uc[j][0] = 1 / U(j, j)
-// so that both triangular solves are column sweeps with contiguous reads.
+//   Lc[j][a] = L(j+a, j) / L(j, j), a = 1..bw;  Lc[j][0] = 1 / L(j, j)
+//   Uc[j][b] = U(j-b, j) / U(j, j), b = 1..bw;  Uc[j][0] = 1 / U(j, j)
+// (multipliers divided by the pivot: see band.cuh) so that both triangular
+// solves are column sweeps with contiguous reads and one FMA per step.
 //
 // The reflection matrix of Sec. VIII, T_P = (W - S_P)(W + S_P)^-1, is built
 // column by column from banded solves: column q of T_P is
@@ -17,6 +18,7 @@
 // padded to a multiple of 8 elements.
 #include <algorithm>
 
+#include "band.cuh"
 #include "vtm_internal.h"
 
 namespace vtm {
@@ -74,15 +76,18 @@ __global__ void __launch_bounds__(256) band_factor_kernel(const int32_t* __restr
       if (kLU) urow[a] = win[jm * B + wrap(j + a, B)];
     }
     __syncthreads();
+    // column j of the factors, multipliers divided by the pivot (see band.cuh);
+    // column j of U was filled unscaled by the earlier steps and is scaled now
     for (int a = tid; a <= m; a += blockDim.x) {
       if (a == 0) {
         lc[(size_t)j * B] = kLU ? 1.0 : dinv;
         uc[(size_t)j * B] = dinv;
       } else {
-        lc[(size_t)j * B + a] = lcol[a];
+        lc[(size_t)j * B + a] = kLU ? lcol[a] : lcol[a] * dinv;
         uc[(size_t)(j + a) * B + a] = kLU ? urow[a] : lcol[a];
       }
     }
+    for (int b = tid + 1; b <= min(bw, j); b += blockDim.x) uc[(size_t)j * B + b] *= dinv;
     // rank-1 update of the trailing window
     if (kLU) {
       for (int idx = tid; idx < m * m; idx += blockDim.x) {
@@ -149,32 +154,6 @@ vtm_status factor_tiles(vtm_plan_s* P) {
 // banded solves (one warp per right-hand side)
 // ---------------------------------------------------------------------------
 
-// Forward sweep L y = v from row `start` (entries above are zero), then
-// backward sweep U x = y; v is overwritten by x.  One warp.
-__device__ __forceinline__ void warp_band_solve(double* v, int n, int bw, const double* __restrict__ lc,
-                                                const double* __restrict__ uc, int start) {
-  const int lane = threadIdx.x & 31;
-  const int B = bw + 1;
-  for (int j = start; j < n; ++j) {
-    const double* col = lc + (size_t)j * B;
-    const double y = v[j] * __ldg(col);
-    const int m = min(bw, n - 1 - j);
-    __syncwarp();
-    if (lane == 0) v[j] = y;
-    for (int a = lane + 1; a <= m; a += 32) v[j + a] -= __ldg(col + a) * y;
-    __syncwarp();
-  }
-  for (int j = n - 1; j >= 0; --j) {
-    const double* col = uc + (size_t)j * B;
-    const double x = v[j] * __ldg(col);
-    const int m = min(bw, j);
-    __syncwarp();
-    if (lane == 0) v[j] = x;
-    for (int b = lane + 1; b <= m; b += 32) v[j - b] -= __ldg(col + b) * x;
-    __syncwarp();
-  }
-}
-
 // Solve K_P x = v for every tile, in place in the permuted vector v
 // (one warp per (tile, column)); columns are `stride` apart.
 __global__ void band_solve_tiles_kernel(const int32_t* __restrict__ node_off,
@@ -193,10 +172,10 @@ __global__ void band_solve_tiles_kernel(const int32_t* __restrict__ node_off,
   if (use_smem) {
     for (int i = lane; i < n; i += 32) smem[i] = vg[i];
     __syncwarp();
-    warp_band_solve(smem, n, bwv[t], Lc + band_off[t], Uc + band_off[t], 0);
+    warp_band_solve_any(smem, n, bwv[t], Lc + band_off[t], Uc + band_off[t], 0);
     for (int i = lane; i < n; i += 32) vg[i] = smem[i];
   } else {
-    warp_band_solve(vg, n, bwv[t], Lc + band_off[t], Uc + band_off[t], 0);
+    warp_band_solve_any(vg, n, bwv[t], Lc + band_off[t], Uc + band_off[t], 0);
   }
 }
 
@@ -244,7 +223,7 @@ __global__ void build_reflection_kernel(const int32_t* __restrict__ node_off,
   const int lq = port_loc[q];
   if (lane == 0) y[lq] = beta[q];
   __syncwarp();
-  warp_band_solve(y, n, bwv[t], Lc + band_off[t], Uc + band_off[t], lq);
+  warp_band_solve_any(y, n, bwv[t], Lc + band_off[t], Uc + band_off[t], lq);
   double* row = T + T_off[t] + (size_t)(q - p0) * T_ld[t];
   for (int s = lane; s < p; s += 32) {
     const int ps = p0 + s;
@@ -322,7 +301,11 @@ extern "C" vtm_status vtm_factor(vtm_plan_t P) {
   static_assert(sizeof(double) == 8, "");
   VTM_TRY(assemble_local(P));
   VTM_TRY(factor_tiles(P));
-  VTM_TRY(build_reflections(P));
+  if (P->general) {
+    VTM_TRY(build_general_operators(P));
+  } else {
+    VTM_TRY(build_reflections(P));
+  }
   P->factored = true;
   return VTM_OK;
 }
@@ -331,6 +314,11 @@ extern "C" vtm_status vtm_get_reflection(vtm_plan_t P, int32_t part, double* T, 
                                          int32_t* p) {
   if (!P || part < 0 || part >= P->nparts) return VTM_EINVAL;
   if (!P->factored) return VTM_ENOTFACTORED;
+  if (P->general) {
+    set_detail("vtm_get_reflection: this plan carries lagged couplings; its tile operators "
+               "include them and are not plain reflection matrices");
+    return VTM_EINVAL;
+  }
   const int32_t pp = P->port_off[part + 1] - P->port_off[part];
   if (p) *p = pp;
   if (!T) return VTM_OK;

@@ -220,7 +220,7 @@ static vtm_status build_structure(vtm_plan_s* P, std::vector<CutPair>& pairs) {
   for (auto& cp : pairs) {
     double a1 = val_at(P, cp.pos_lohi), a2 = val_at(P, cp.pos_hilo);
     double g = -(a1 + a2) / 2.0;
-    cp.wire = g > 0;
+    cp.wire = P->method == VTM_METHOD_VTM && g > 0;
     double r1 = cp.wire ? a1 + g : a1;
     double r2 = cp.wire ? a2 + g : a2;
     if (r1 != 0.0) {
@@ -326,7 +326,7 @@ static bool same_cut_structure(const vtm_plan_s* P) {
       int64_t p1 = i < j ? q : back, p2 = i < j ? back : q;
       double a1 = val_at(P, p1), a2 = val_at(P, p2);
       double g = -(a1 + a2) / 2.0;
-      bool wire = g > 0;
+      bool wire = P->method == VTM_METHOD_VTM && g > 0;
       if (wire) wires.push_back(p1 >= 0 ? p1 : p2);
       double r1 = wire ? a1 + g : a1, r2 = wire ? a2 + g : a2;
       if (r1 != 0.0) lags.push_back(p1);
@@ -370,7 +370,7 @@ vtm_status assemble_local(vtm_plan_s* P) {
     int64_t pji = csr_find(P, j, i);
     double a = val_at(P, P->lag_pos[q]);
     double g = -(a + val_at(P, pji)) / 2.0;
-    P->lag_rho[q] = g > 0 ? a + g : a;
+    P->lag_rho[q] = (P->method == VTM_METHOD_VTM && g > 0) ? a + g : a;
   }
   std::vector<double> Lc(P->band_elems, 0.0), Uc;
   if (!P->symmetric) Uc.assign(P->band_elems, 0.0);
@@ -407,6 +407,188 @@ vtm_status assemble_local(vtm_plan_s* P) {
   }
   VTM_TRY(upload(P->d_g, P->port_g, st));
   VTM_TRY(upload(P->d_beta, beta, st));
+  if (P->general) {
+    // per input: residual coefficient (g or rho) and right-hand-side weight
+    // (beta or -rho); per output: scale (2 W beta or 1) and the diagonal
+    // reflection term of a port
+    std::vector<double> coef(P->n_in), sigma(P->n_in), scale(P->n_out), diag(P->n_out, 0.0);
+    for (int64_t a = 0; a < P->n_in; ++a) {
+      const int32_t it = P->in_item[a];
+      if (P->in_kind[a] == 0) {
+        coef[a] = P->port_g[it];
+        sigma[a] = beta[it];
+      } else {
+        coef[a] = P->lag_rho[it];
+        sigma[a] = -P->lag_rho[it];
+      }
+    }
+    for (int64_t o = 0; o < P->n_out; ++o) {
+      const int32_t it = P->out_item[o];
+      if (it >= 0) {
+        const double g = P->port_g[it];
+        scale[o] = 2.0 * W * beta[it];
+        diag[o] = (W - 2.0 * g) / (W + 2.0 * g);
+      } else {
+        scale[o] = 1.0;
+      }
+    }
+    VTM_TRY(upload(P->d_in_coef, coef, st));
+    VTM_TRY(upload(P->d_in_sigma, sigma, st));
+    VTM_TRY(upload(P->d_out_scale, scale, st));
+    VTM_TRY(upload(P->d_out_diag, diag, st));
+  }
+  VTM_CUDA_TRY(cudaStreamSynchronize(st));
+  return VTM_OK;
+}
+
+// Channel tables of the general form (see vtm_internal.h).
+static vtm_status build_general(vtm_plan_s* P) {
+  const int32_t np = P->nparts;
+  const int64_t nl = (int64_t)P->lag_i.size();
+  // lagged entries grouped by the tile of their row, ordered by (row, column)
+  std::vector<int64_t> lag_order(nl);
+  std::iota(lag_order.begin(), lag_order.end(), 0);
+  std::sort(lag_order.begin(), lag_order.end(), [&](int64_t a, int64_t b) {
+    int32_t ta = P->h_part[P->lag_i[a]], tb = P->h_part[P->lag_i[b]];
+    if (ta != tb) return ta < tb;
+    if (P->lag_i[a] != P->lag_i[b]) return P->lag_i[a] < P->lag_i[b];
+    return P->lag_j[a] < P->lag_j[b];
+  });
+  // probes: distinct columns of lagged entries, grouped by their tile
+  std::vector<int32_t> probe_nodes;
+  for (int64_t q = 0; q < nl; ++q) probe_nodes.push_back(P->lag_j[q]);
+  std::sort(probe_nodes.begin(), probe_nodes.end(), [&](int32_t a, int32_t b) {
+    int32_t ta = P->h_part[a], tb = P->h_part[b];
+    return ta != tb ? ta < tb : a < b;
+  });
+  probe_nodes.erase(std::unique(probe_nodes.begin(), probe_nodes.end()), probe_nodes.end());
+  std::vector<int32_t> nlag(np, 0), nprobe(np, 0);
+  for (int64_t q = 0; q < nl; ++q) nlag[P->h_part[P->lag_i[q]]]++;
+  for (int32_t v : probe_nodes) nprobe[P->h_part[v]]++;
+  P->in_off.assign(np + 1, 0);
+  P->out_off.assign(np + 1, 0);
+  for (int32_t t = 0; t < np; ++t) {
+    const int32_t p = P->port_off[t + 1] - P->port_off[t];
+    P->in_off[t + 1] = P->in_off[t] + p + nlag[t];
+    P->out_off[t + 1] = P->out_off[t] + p + nprobe[t];
+  }
+  P->n_in = P->in_off[np];
+  P->n_out = P->out_off[np];
+  // output slot of each probe node
+  std::vector<int32_t> probe_slot(P->n, -1);
+  {
+    std::vector<int32_t> fill(np, 0);
+    for (int32_t v : probe_nodes) {
+      const int32_t t = P->h_part[v];
+      const int32_t p = P->port_off[t + 1] - P->port_off[t];
+      probe_slot[v] = P->out_off[t] + p + fill[t]++;
+    }
+  }
+  P->in_src.assign(P->n_in, -1);
+  P->in_kind.assign(P->n_in, 0);
+  P->in_twin.assign(P->n_in, -1);
+  P->in_own_out.assign(P->n_in, -1);
+  P->in_loc.assign(P->n_in, 0);
+  P->in_item.assign(P->n_in, -1);
+  P->out_loc.assign(P->n_out, 0);
+  P->out_item.assign(P->n_out, -1);
+  // global input / output id of a port
+  auto port_in = [&](int32_t s) {
+    const int32_t t = P->h_part[P->port_node[s]];
+    return P->in_off[t] + (s - P->port_off[t]);
+  };
+  auto port_out = [&](int32_t s) {
+    const int32_t t = P->h_part[P->port_node[s]];
+    return P->out_off[t] + (s - P->port_off[t]);
+  };
+  for (int32_t s = 0; s < (int32_t)P->port_node.size(); ++s) {
+    const int32_t a = port_in(s), o = port_out(s);
+    const int32_t tw = P->port_twin[s];
+    P->in_kind[a] = 0;
+    P->in_src[a] = port_out(tw);
+    P->in_twin[a] = port_in(tw);
+    P->in_own_out[a] = o;
+    P->in_loc[a] = P->port_loc[s];
+    P->in_item[a] = s;
+    P->out_loc[o] = P->port_loc[s];
+    P->out_item[o] = s;
+  }
+  {
+    std::vector<int32_t> fill(np, 0);
+    for (int64_t k = 0; k < nl; ++k) {
+      const int64_t q = lag_order[k];
+      const int32_t i = P->lag_i[q], j = P->lag_j[q];
+      const int32_t t = P->h_part[i];
+      const int32_t p = P->port_off[t + 1] - P->port_off[t];
+      const int32_t a = P->in_off[t] + p + fill[t]++;
+      P->in_kind[a] = 1;
+      P->in_src[a] = probe_slot[j];
+      P->in_loc[a] = P->iperm[i] - P->node_off[t];
+      P->in_item[a] = (int32_t)q;
+    }
+  }
+  for (int32_t v : probe_nodes) {
+    const int32_t o = probe_slot[v];
+    const int32_t t = P->h_part[v];
+    P->out_loc[o] = P->iperm[v] - P->node_off[t];
+    P->out_item[o] = -1;
+  }
+  // residual runs: inputs of each tile sorted by their row node
+  P->res_perm.assign(P->n_in, 0);
+  P->res_run.assign(P->n_in, 0);
+  P->max_in = P->max_out = 0;
+  for (int32_t t = 0; t < np; ++t) {
+    const int32_t a0 = P->in_off[t], ni = P->in_off[t + 1] - a0;
+    P->max_in = std::max(P->max_in, ni);
+    P->max_out = std::max(P->max_out, P->out_off[t + 1] - P->out_off[t]);
+    std::vector<int32_t> idx(ni);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(),
+                     [&](int32_t x, int32_t y) { return P->in_loc[a0 + x] < P->in_loc[a0 + y]; });
+    for (int32_t k = 0; k < ni;) {
+      int32_t e = k + 1;
+      while (e < ni && P->in_loc[a0 + idx[e]] == P->in_loc[a0 + idx[k]]) ++e;
+      if (e - k > 255) {
+        set_detail("vtm_plan: more than 255 cut couplings in one row");
+        return VTM_EINVAL;
+      }
+      P->res_run[a0 + k] = (uint8_t)(e - k);
+      k = e;
+    }
+    for (int32_t k = 0; k < ni; ++k) P->res_perm[a0 + k] = idx[k];
+  }
+  // operator layout: per tile, one row of E^T per input, rows padded to 8
+  P->E_ld.assign(np, 0);
+  P->E_off.assign(np, 0);
+  int64_t off = 0;
+  for (int32_t t = 0; t < np; ++t) {
+    const int32_t ni = P->in_off[t + 1] - P->in_off[t];
+    const int32_t no = P->out_off[t + 1] - P->out_off[t];
+    P->E_ld[t] = (no + 7) / 8 * 8;
+    P->E_off[t] = off;
+    off += (int64_t)ni * P->E_ld[t];
+  }
+  P->E_elems = off;
+  cudaStream_t st = P->stream;
+  std::vector<int32_t> in_tile(P->n_in);
+  for (int32_t t = 0; t < np; ++t)
+    for (int32_t a = P->in_off[t]; a < P->in_off[t + 1]; ++a) in_tile[a] = t;
+  VTM_TRY(upload(P->d_in_off, P->in_off, st));
+  VTM_TRY(upload(P->d_out_off, P->out_off, st));
+  VTM_TRY(upload(P->d_in_src, P->in_src, st));
+  VTM_TRY(upload(P->d_in_kind, P->in_kind, st));
+  VTM_TRY(upload(P->d_in_twin, P->in_twin, st));
+  VTM_TRY(upload(P->d_in_own_out, P->in_own_out, st));
+  VTM_TRY(upload(P->d_in_loc, P->in_loc, st));
+  VTM_TRY(upload(P->d_res_perm, P->res_perm, st));
+  VTM_TRY(upload(P->d_res_run, P->res_run, st));
+  VTM_TRY(upload(P->d_out_loc, P->out_loc, st));
+  VTM_TRY(upload(P->d_E_off, P->E_off, st));
+  VTM_TRY(upload(P->d_E_ld, P->E_ld, st));
+  VTM_TRY(upload(P->d_in_tile, in_tile, st));
+  VTM_TRY(dev_alloc(P->d_cg, std::max<int64_t>(P->n_out, 1) * sizeof(double)));
+  VTM_TRY(dev_alloc(P->d_gin, 2 * std::max<int64_t>(P->n_in, 1) * sizeof(double)));
+  VTM_TRY(dev_alloc(P->d_gout, 2 * std::max<int64_t>(P->n_out, 1) * sizeof(double)));
   VTM_CUDA_TRY(cudaStreamSynchronize(st));
   return VTM_OK;
 }
@@ -420,7 +602,10 @@ std::vector<DevBuf*> vtm_plan_s::all_bufs() {
           &tabs.order, &d_rowptr, &d_colidx, &d_vals, &d_perm, &d_Lc, &d_Uc, &d_port_loc, &d_port_pos,
           &d_twin, &d_g, &d_beta, &d_run, &d_T64, &d_T32, &d_T16, &d_c64, &d_c32, &d_state64,
           &d_state32, &d_v, &d_v2, &d_xacc, &d_r, &d_bcol, &d_partials, &d_ctrl, &d_hist,
-          &d_err, &d_red};
+          &d_err, &d_red, &d_in_off, &d_out_off, &d_in_src, &d_in_kind, &d_in_twin,
+          &d_in_own_out, &d_in_loc, &d_res_perm, &d_res_run, &d_out_loc, &d_in_coef,
+          &d_in_sigma, &d_out_scale, &d_out_diag, &d_E_off, &d_E_ld, &d_E, &d_cg, &d_gin,
+          &d_gout, &d_in_tile};
 }
 
 static void fill_default_opts(vtm_opts* o) {
@@ -520,11 +705,18 @@ extern "C" vtm_status vtm_plan(int64_t n, const int64_t* rowptr, const int32_t* 
         break;
       }
     }
-  std::vector<CutPair> pairs;
-  if ((st = build_structure(P, pairs)) != VTM_OK) return fail(st);
-
   vtm_opts o{};
   if (opts) o = *opts;
+  if (o.method != VTM_METHOD_VTM && o.method != VTM_METHOD_BJ) {
+    set_detail("vtm_plan: unknown method");
+    return fail(VTM_EINVAL);
+  }
+  P->method = o.method;
+  std::vector<CutPair> pairs;
+  if ((st = build_structure(P, pairs)) != VTM_OK) return fail(st);
+  P->general = !P->lag_i.empty() || P->method == VTM_METHOD_BJ;
+  if (P->general && (st = build_general(P)) != VTM_OK) return fail(st);
+
   P->opts.precision = o.precision;
   if ((st = vtm_set_opts(P, &o)) != VTM_OK) return fail(st);
 
@@ -639,7 +831,7 @@ extern "C" vtm_status vtm_plan_get_stats(vtm_plan_t P, vtm_plan_stats* s) {
   s->max_nodes = P->max_nodes;
   s->max_band = P->max_bw;
   s->symmetric = P->symmetric ? 1 : 0;
-  s->t_bytes = (int64_t)(P->d_T64.bytes + P->d_T32.bytes + P->d_T16.bytes);
+  s->t_bytes = (int64_t)(P->d_T64.bytes + P->d_T32.bytes + P->d_T16.bytes + P->d_E.bytes);
   s->factor_bytes = (int64_t)(P->d_Lc.bytes + P->d_Uc.bytes);
   return VTM_OK;
 }

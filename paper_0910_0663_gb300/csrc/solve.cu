@@ -26,6 +26,7 @@
 #include <cmath>
 #include <type_traits>
 
+#include "ptx.h"
 #include "vtm_internal.h"
 
 namespace vtm {
@@ -278,6 +279,266 @@ __global__ void __launch_bounds__(256) sweep_kernel(
 }
 
 // ---------------------------------------------------------------------------
+// the sweep with the reflection matrix staged by the bulk-copy engine
+// ---------------------------------------------------------------------------
+//
+// Same arithmetic as sweep_kernel, persistent over tiles: each CTA handles
+// the tiles order[blockIdx.x + m gridDim.x].  Thread 0 streams the T_P^T
+// blocks of those tiles, in sequence and across tile boundaries, through a
+// ring of kStages shared-memory stages of `ch` rows with cp.async.bulk
+// (completion on one mbarrier per stage), so the next tile's matrix is
+// already in flight while a tile gathers its incident waves and residual
+// terms.  The apply reads T from shared memory with 16-byte vector loads;
+// thread (g, l) accumulates VEC consecutive outputs of vector column l over
+// the rows t = g (mod G), and the G partial sums are added in a fixed order.
+
+constexpr int kStages = 4;
+constexpr uint32_t kWaitPolls = 1u << 24;  // bounded mbarrier wait
+
+template <class TT, int VEC> struct VecLoad;
+template <> struct VecLoad<double, 2> {
+  __device__ static void load(const double* p, double (&o)[2]) {
+    double2 v = *reinterpret_cast<const double2*>(p);
+    o[0] = v.x; o[1] = v.y;
+  }
+};
+template <> struct VecLoad<float, 4> {
+  __device__ static void load(const float* p, float (&o)[4]) {
+    float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+};
+template <> struct VecLoad<__nv_bfloat16, 8> {
+  __device__ static void load(const __nv_bfloat16* p, float (&o)[8]) {
+    uint4 v = *reinterpret_cast<const uint4*>(p);
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float2 f = __bfloat1622float2(h[i]);
+      o[2 * i] = f.x;
+      o[2 * i + 1] = f.y;
+    }
+  }
+};
+
+template <class TT, class WT, int VEC, int MAXV>
+__global__ void __launch_bounds__(256) sweep_staged_kernel(
+    const TT* __restrict__ T, const int64_t* __restrict__ T_off, const int32_t* __restrict__ T_ld,
+    const int32_t* __restrict__ port_off, const int32_t* __restrict__ order,
+    const int32_t* __restrict__ twin, const double* __restrict__ g,
+    const uint8_t* __restrict__ run, const WT* __restrict__ c, WT* __restrict__ state,
+    int64_t nports, double W, SweepCtrl* __restrict__ ctrl, double* __restrict__ partials,
+    double* __restrict__ hist, int hist_len, int nparts, int ch, int ld_max) {
+  using AT = WT;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ uint64_t bars[kStages];
+  __shared__ int s_k, s_flag, s_timeout;
+  __shared__ bool s_last;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    s_k = *((volatile int*)&ctrl->k);
+    s_flag = *((volatile int*)&ctrl->flag);
+    s_timeout = 0;
+  }
+  __syncthreads();
+  if (s_flag) return;
+  const int k = s_k;
+  // shared memory: ring | w_in (ld_max) | rs (ld_max) | red (256 * VEC: one
+  // partial per thread and vector element)
+  TT* ring = reinterpret_cast<TT*>(smem_raw);
+  const size_t stage_elems = (size_t)ch * ld_max;
+  WT* w_in = reinterpret_cast<WT*>(smem_raw + kStages * stage_elems * sizeof(TT));
+  AT* rs = w_in + ld_max;
+  AT* red = rs + ld_max;
+  // Producer (thread 0): the chunks of this CTA's tiles (order[blockIdx.x +
+  // m gridDim.x], m = 0, 1, ...) in sequence, chunk q into stage q % kStages.
+  int pit = blockIdx.x, pc = 0;
+  uint32_t issued = 0;
+  auto issue_next = [&]() {
+    while (pit < nparts) {
+      const int tl = order[pit];
+      const int pp = port_off[tl + 1] - port_off[tl];
+      if (pc * ch < pp) {
+        const int ldt = T_ld[tl];
+        const int rows = min(ch, pp - pc * ch);
+        const uint32_t bytes = (uint32_t)rows * ldt * sizeof(TT);
+        uint64_t* bar = &bars[issued % kStages];
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_copy_g2s(ring + (size_t)(issued % kStages) * stage_elems,
+                      T + T_off[tl] + (size_t)pc * ch * ldt, bytes, bar);
+        ++pc;
+        ++issued;
+        return;
+      }
+      pit += gridDim.x;
+      pc = 0;
+    }
+  };
+  if (tid == 0) {
+    for (int i = 0; i < kStages; ++i) mbar_init(&bars[i], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int i = 0; i < kStages; ++i) issue_next();
+  const WT* prev = state + (size_t)((k - 1) & 1) * nports * 2;
+  WT* cur = state + (size_t)(k & 1) * nports * 2;
+  const AT hW = (AT)W, inv2W = (AT)(0.5 / W);
+  uint32_t consumed = 0;
+  for (int it = blockIdx.x; it < nparts; it += gridDim.x) {
+    const int tile = order[it];
+    const int p0 = port_off[tile];
+    const int p = port_off[tile + 1] - p0;
+    const int ld = T_ld[tile];
+    // incident waves (delay 1) and residual terms of sweep k-1; the chunks
+    // of this tile are already streaming in
+    for (int s = tid; s < p; s += blockDim.x) {
+      const int gs = p0 + s;
+      AT wi = 0, rc = 0;
+      if (k > 1) {
+        const int tw = twin[gs];
+        const AT wi_t = (AT)prev[2 * tw], wo_t = (AT)prev[2 * tw + 1];
+        const AT wi_s = (AT)prev[2 * gs], wo_s = (AT)prev[2 * gs + 1];
+        wi = wo_t;
+        const AT gg = (AT)g[gs];
+        const AT us = (wi_s + wo_s) * inv2W, ut = (wi_t + wo_t) * inv2W;
+        rc = (AT)0.5 * ((hW - 2 * gg) * us + (hW + 2 * gg) * ut - wi_s - wi_t);
+      }
+      w_in[s] = (WT)wi;
+      rs[s] = rc;
+    }
+    __syncthreads();
+    double sq = 0.0;
+    if (k > 1) {
+      for (int s = tid; s < p; s += blockDim.x) {
+        const int nr = run[p0 + s];
+        if (nr) {
+          double r = 0.0;
+          for (int q = 0; q < nr; ++q) r += (double)rs[s + q];
+          sq += r * r;
+        }
+      }
+    }
+    const double tile_sq = block_sum_value(sq);
+    if (tid == 0) partials[tile] = tile_sq;
+    // apply the reflection matrix from the staged chunks
+    const int nv = (p + VEC - 1) / VEC;
+    const int L = max(1, min(nv, (int)blockDim.x));
+    const int G = blockDim.x / L;
+    const int gi = tid / L, li = tid % L;
+    AT acc[MAXV][VEC];
+#pragma unroll
+    for (int m = 0; m < MAXV; ++m)
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) acc[m][e] = 0;
+    const int nchunks = (p + ch - 1) / ch;
+    for (int ci = 0; ci < nchunks; ++ci, ++consumed) {
+      if (tid == 0 &&
+          !mbar_wait_bounded(&bars[consumed % kStages], (consumed / kStages) & 1, kWaitPolls))
+        s_timeout = 1;
+      __syncthreads();
+      if (s_timeout) break;
+      const TT* st = ring + (size_t)(consumed % kStages) * stage_elems;
+      const int r0 = ci * ch, r1 = min(p, r0 + ch);
+      if (gi < G) {
+        for (int t = r0 + gi; t < r1; t += G) {
+          const AT wt = (AT)w_in[t];
+          const TT* row = st + (size_t)(t - r0) * ld;
+#pragma unroll
+          for (int m = 0; m < MAXV; ++m) {
+            const int v = li + m * L;
+            if (v < nv) {
+              AT val[VEC];
+              VecLoad<TT, VEC>::load(row + v * VEC, val);
+#pragma unroll
+              for (int e = 0; e < VEC; ++e) acc[m][e] += val[e] * wt;
+            }
+          }
+        }
+      }
+      __syncthreads();
+      if (tid == 0) issue_next();
+    }
+    if (s_timeout) break;
+    // fixed-order sum over the G row groups (G > 1 only when every thread
+    // owns a single vector column, i.e. m = 0)
+    if (G > 1) {
+      const int cols = L * VEC;
+      if (gi < G && li < nv)
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) red[gi * cols + li * VEC + e] = acc[0][e];
+      __syncthreads();
+      for (int s = tid; s < p; s += blockDim.x) {
+        AT a = (AT)c[p0 + s];
+        for (int gg = 0; gg < G; ++gg) a += red[gg * cols + s];
+        cur[2 * (p0 + s)] = w_in[s];
+        cur[2 * (p0 + s) + 1] = (WT)a;
+      }
+    } else if (gi == 0) {  // threads past the L vector columns hold no sums
+#pragma unroll
+      for (int m = 0; m < MAXV; ++m) {
+        const int v = li + m * L;
+        if (v < nv) {
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) {
+            const int s = v * VEC + e;
+            if (s < p) {
+              cur[2 * (p0 + s)] = w_in[s];
+              cur[2 * (p0 + s) + 1] = (WT)(acc[m][e] + (AT)c[p0 + s]);
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();  // w_in, rs and red are reused by the next tile
+  }
+  if (s_timeout) {
+    // wait (bounded) for this CTA's copies still in flight, then report
+    if (tid == 0) {
+      for (uint32_t q = consumed; q < issued; ++q)
+        mbar_wait_bounded(&bars[q % kStages], (q / kStages) & 1, kWaitPolls);
+      atomicExch(&ctrl->flag, 5);
+    }
+    return;
+  }
+  if (tid == 0) {
+    __threadfence();
+    s_last = atomicAdd(&ctrl->counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const double tot = block_sum_fixed(partials, nparts);
+  if (tid == 0) {
+    int flag = 0;
+    if (k > 1) {
+      const int ks = k - 1;
+      if (hist && ks <= hist_len) hist[ks - 1] = sqrt(tot / ctrl->bnorm2);
+      if (ks == 1) ctrl->first_res2 = tot;
+      ctrl->last_res2 = tot;
+      if (ks == 1 || tot < 0.81 * ctrl->best_res2) {
+        ctrl->best_res2 = tot;
+        ctrl->best_k = ks;
+      }
+      if (!isfinite(tot) || (ks > 1 && tot > 1e12 * ctrl->first_res2 && ctrl->first_res2 > 0)) {
+        flag = 3;
+      } else if (tot <= ctrl->tol2) {
+        flag = 1;
+        ctrl->conv_sweep = ks;
+      } else if (ctrl->stall > 0 && ks - ctrl->best_k >= ctrl->stall) {
+        flag = 4;
+        ctrl->conv_sweep = ks;
+      }
+    }
+    if (!flag && k >= ctrl->k_max) flag = 2;
+    ctrl->counter = 0u;
+    ctrl->k = k + 1;
+    __threadfence();
+    if (ctrl->flag == 0) ctrl->flag = flag;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
 
@@ -331,11 +592,65 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   } else {
     VTM_CUDA_TRY(cudaMemsetAsync(P->d_state32.p, 0, 4 * npt * sizeof(float), s));
   }
+  // staged kernel: ring of kStages stages of `ch` rows, at most 16 KB per stage
+  int ld_max = 8;
+  for (int32_t v : P->T_ld) ld_max = std::max(ld_max, v);
+  const size_t s_t = prec == VTM_PREC_FP64 ? 8 : (prec == VTM_PREC_FP32 ? 4 : 2);
+  const int vec = prec == VTM_PREC_FP64 ? 2 : (prec == VTM_PREC_FP32 ? 4 : 8);
+  int ch = (int)std::max<size_t>(1, (16 * 1024) / (ld_max * s_t));
+  ch = std::min(ch, std::max(1, P->max_ports));
+  const size_t st_smem = kStages * (size_t)ch * ld_max * s_t + 2 * (size_t)ld_max * wsz +
+                         256 * (size_t)vec * wsz + 128;
+  const int nv_max = (P->max_ports + vec - 1) / vec;
+  // auto: the FP64 sweep is bound by GB300's FP64 pipe, where the direct-load
+  // kernel does best; FP32/BF16 stream their matrices through the bulk-copy ring
+  const int choice = P->opts.sweep_kernel ? P->opts.sweep_kernel : (prec == VTM_PREC_FP64 ? 1 : 2);
+  const bool staged = choice == 2 && nv_max <= 4 * 256 && st_smem <= 200 * 1024;
+  if (staged) {
+    if (prec == VTM_PREC_FP64)
+      VTM_CUDA_TRY(cudaFuncSetAttribute(sweep_staged_kernel<double, double, 2, 4>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st_smem));
+    else if (prec == VTM_PREC_FP32)
+      VTM_CUDA_TRY(cudaFuncSetAttribute(sweep_staged_kernel<float, float, 4, 4>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st_smem));
+    else
+      VTM_CUDA_TRY(cudaFuncSetAttribute(sweep_staged_kernel<__nv_bfloat16, float, 8, 4>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st_smem));
+  }
+  const int st_threads = 256;
+  const int64_t npt_ = npt;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
+  int st_grid = 0;
+  auto launch_staged = [&](auto* kern, const auto* T, const auto* c, auto* state) {
+    if (!st_grid) {
+      int per_sm = 1;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, st_threads, st_smem);
+      st_grid = std::max(1, std::min(P->nparts, std::max(per_sm, 1) * sms));
+    }
+    kern<<<st_grid, st_threads, st_smem, s>>>(
+        T, P->tabs.T_off.as<int64_t>(), P->tabs.T_ld.as<int32_t>(), P->tabs.port_off.as<int32_t>(),
+        P->tabs.order.as<int32_t>(), P->d_twin.as<int32_t>(), P->d_g.as<double>(),
+        P->d_run.as<uint8_t>(), c, state, npt_, P->W, P->d_ctrl.as<SweepCtrl>(),
+        P->d_partials.as<double>(), hist, hist_len, P->nparts, ch, ld_max);
+  };
   int launched = 0;
   while (true) {
     const int m = std::min(P->opts.check_every, budget + 1 - launched);
     VTM_CUDA_TRY(cudaEventRecord(P->evs0, s));
     for (int i = 0; i < m; ++i) {
+      if (staged) {
+        if (prec == VTM_PREC_FP64)
+          launch_staged(sweep_staged_kernel<double, double, 2, 4>, P->d_T64.as<double>(),
+                        P->d_c64.as<double>(), P->d_state64.as<double>());
+        else if (prec == VTM_PREC_FP32)
+          launch_staged(sweep_staged_kernel<float, float, 4, 4>, P->d_T32.as<float>(),
+                        P->d_c32.as<float>(), P->d_state32.as<float>());
+        else
+          launch_staged(sweep_staged_kernel<__nv_bfloat16, float, 8, 4>, P->d_T16.as<__nv_bfloat16>(),
+                        P->d_c32.as<float>(), P->d_state32.as<float>());
+        continue;
+      }
       if (prec == VTM_PREC_FP64)
         launch_sweep<double, double>(P, P->d_T64.as<double>(), P->d_c64.as<double>(),
                                      P->d_state64.as<double>(), threads, smem, hist, hist_len);
@@ -359,6 +674,10 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
     if (P->h_ctrl->flag || launched > budget) break;
   }
   const SweepCtrl& r = *P->h_ctrl;
+  if (r.flag == 5) {
+    set_detail("vtm_solve: a bounded wait for a bulk copy ran out");
+    return VTM_ETIMEOUT;
+  }
   *flag_out = r.flag;
   if (r.flag == 1 || r.flag == 4) *sweep_out = r.conv_sweep;
   else *sweep_out = std::min(r.k - 1, budget);
@@ -416,7 +735,7 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
   double rnorm = bnorm;
   double inner_tol = P->opts.inner_tol;
   if (inner_tol <= 0) inner_tol = prec == VTM_PREC_FP32 ? 1e-5 : (prec == VTM_PREC_BF16 ? 1e-2 : 0.0);
-  const int max_outer = prec == VTM_PREC_FP64 ? 4 : P->opts.max_outer;
+  const int max_outer = (prec == VTM_PREC_FP64 || P->general) ? 4 : P->opts.max_outer;
   int sweeps_left = P->opts.max_sweeps;
   vtm_status result = VTM_ENOCONV;
   for (int outer = 0; outer < max_outer; ++outer) {
@@ -426,7 +745,25 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
     P->launch_count++;
     launch_band_solve(P, v, 1, n, s);
     int kc = 0, flag = 1;
-    if (npt > 0) {
+    if (P->general && P->n_in > 0) {
+      // channel form (lagged couplings / block Jacobi), FP64 sweeps
+      VTM_TRY(general_const(P, v));
+      double* hist = (record_hist && outer == 0 && P->opts.history) ? P->d_hist.as<double>() : nullptr;
+      const int hist_len = hist ? P->opts.history_len : 0;
+      if (hist) VTM_CUDA_TRY(cudaMemsetAsync(hist, 0, hist_len * sizeof(double), s));
+      if (sweeps_left <= 0) break;
+      VTM_TRY(general_sweeps(P, rnorm * rnorm, target * target, sweeps_left, hist, hist_len, &kc, &flag));
+      if (hist)
+        VTM_CUDA_TRY(cudaMemcpyAsync(P->opts.history, hist, hist_len * sizeof(double),
+                                     cudaMemcpyDeviceToHost, s));
+      if (outer == 0 && flag == 1) info->first_sweep_converged = kc;
+      info->sweeps += kc;
+      sweeps_left -= kc;
+      gather_perm_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, v, n);
+      P->launch_count++;
+      VTM_TRY(general_inject(P, kc, v));
+      launch_band_solve(P, v, 1, n, s);
+    } else if (!P->general && npt > 0) {
       if (prec == VTM_PREC_FP64)
         port_const_kernel<double><<<g2, 256, 0, s>>>(P->d_port_pos.as<int32_t>(), P->d_beta.as<double>(),
                                                      v, P->W, P->d_c64.as<double>(), npt);

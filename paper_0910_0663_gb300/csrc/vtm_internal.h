@@ -141,6 +141,32 @@ struct vtm_plan_s {
   int sweep_launch_count = 0;
   double sweep_ms = 0.0;
 
+  // channel form for cut entries that are not branches (controlled sources)
+  // and for block Jacobi: per tile, inputs = [ports | lagged entries of its
+  // rows], outputs = [ports | probes (its nodes read by lagged entries of
+  // other tiles)]; the tile operator maps inputs to outputs.
+  int method = VTM_METHOD_VTM;
+  bool general = false;
+  std::vector<int32_t> in_off, out_off;  // nparts+1
+  std::vector<int32_t> in_src;           // global output feeding each input (delay 1)
+  std::vector<uint8_t> in_kind;          // 0 port, 1 lagged entry
+  std::vector<int32_t> in_twin;          // port input: twin's global input, else -1
+  std::vector<int32_t> in_own_out;       // port input: own global output, else -1
+  std::vector<int32_t> in_loc;           // local position of the input's row node
+  std::vector<int32_t> in_item;          // port id or lagged-entry id
+  std::vector<int32_t> res_perm;         // per tile: local input ids sorted by row node
+  std::vector<uint8_t> res_run;          // run length at each run start of res_perm, else 0
+  std::vector<int32_t> out_loc;          // local position of each output's node
+  std::vector<int32_t> out_item;         // port id of a port output, -1 for a probe
+  std::vector<int32_t> E_ld;
+  std::vector<int64_t> E_off;
+  int64_t E_elems = 0;
+  int32_t max_in = 0, max_out = 0;
+  int64_t n_in = 0, n_out = 0;
+  vtm::DevBuf d_in_off, d_out_off, d_in_src, d_in_kind, d_in_twin, d_in_own_out, d_in_loc,
+      d_res_perm, d_res_run, d_out_loc, d_in_coef, d_in_sigma, d_out_scale, d_out_diag, d_E_off,
+      d_E_ld, d_E, d_cg, d_gin, d_gout, d_in_tile;
+
   // adjoint of an unsymmetric system
   vtm_plan_s* transposed = nullptr;
 
@@ -162,6 +188,13 @@ bool is_device_ptr(const void* p);
 
 // plan.cu
 vtm_status assemble_local(vtm_plan_s* P);  // host band values of K_P + port tables -> device
+
+// general.cu (channel form: lagged couplings and block Jacobi)
+vtm_status build_general_operators(vtm_plan_s* P);
+vtm_status general_const(vtm_plan_s* P, const double* x0_perm);
+vtm_status general_sweeps(vtm_plan_s* P, double bnorm2, double target2, int budget, double* hist,
+                          int hist_len, int* sweep_out, int* flag_out);
+vtm_status general_inject(vtm_plan_s* P, int sweep, double* v);
 
 // factor.cu
 vtm_status factor_tiles(vtm_plan_s* P);

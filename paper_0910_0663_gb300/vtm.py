@@ -30,13 +30,14 @@ class Plan:
 
     def __init__(self, indptr, indices, data, partition, nparts, Zc=1.0, precision="fp64",
                  device="cuda", stream=None, max_sweeps=0, check_every=0, inner_tol=0.0,
-                 max_outer=0, factor=True):
+                 max_outer=0, sweep_kernel=0, method="vtm", factor=True):
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.n = int(len(indptr) - 1)
         self.nparts = int(nparts)
         self._opts = dict(precision=precision, max_sweeps=max_sweeps, check_every=check_every,
-                          inner_tol=inner_tol, max_outer=max_outer)
+                          inner_tol=inner_tol, max_outer=max_outer, sweep_kernel=sweep_kernel,
+                          method=method)
         self._history = None
         rp = _dev(indptr, torch.int64, self.device)
         ci = _dev(indices, torch.int32, self.device)
@@ -117,3 +118,89 @@ def plan_workload(w, precision="fp64", device="cuda", **kw) -> Plan:
     """Plan and factor a ``workloads.Workload``."""
     return Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc, precision=precision,
                 device=device, **kw)
+
+
+class Network:
+    """A resistor network: branches (ei, ej) and the CSR pattern of its nodal
+    matrix, with a VTM plan over a node partition.  ``solve(g, ground, b)``
+    is differentiable in g, ground and b (``VTMSolve``)."""
+
+    def __init__(self, n, edges, indptr, indices, partition, nparts, Zc=1.0, precision="fp64",
+                 device="cuda", g0=None, ground0=None, **plan_kw):
+        self.device = torch.device(device)
+        self.n = int(n)
+        self.stream = torch.cuda.current_stream(self.device)
+        self.rowptr = _dev(indptr, torch.int64, self.device)
+        self.colidx = _dev(indices, torch.int32, self.device)
+        self.ei = _dev(np.asarray(edges)[:, 0], torch.int64, self.device)
+        self.ej = _dev(np.asarray(edges)[:, 1], torch.int64, self.device)
+        self.nedges = int(self.ei.numel())
+        self.netmap = C.vtm_netmap_create(self.n, self.rowptr, self.colidx, self.nedges, self.ei,
+                                          self.ej, self.stream.cuda_stream)
+        g0 = torch.ones(self.nedges, dtype=torch.float64, device=self.device) if g0 is None else \
+            _dev(g0, torch.float64, self.device)
+        gr0 = None if ground0 is None else _dev(ground0, torch.float64, self.device)
+        vals = self.values(g0, gr0)
+        self.plan = Plan(self.rowptr, self.colidx, vals, partition, nparts, Zc=Zc,
+                         precision=precision, device=self.device, stream=self.stream,
+                         factor=False, **plan_kw)
+        self._key = None
+        self._set(g0, gr0, vals)
+
+    def values(self, g, ground=None):
+        vals = torch.empty(int(self.colidx.numel()), dtype=torch.float64, device=self.device)
+        C.vtm_netmap_values(self.netmap, self.rowptr, g.contiguous(),
+                            None if ground is None else ground.contiguous(), vals)
+        return vals
+
+    def _set(self, g, ground, vals=None):
+        key = (g.data_ptr(), g._version, None if ground is None else (ground.data_ptr(), ground._version))
+        if key == self._key:
+            return
+        if vals is None:
+            vals = self.values(g, ground)
+        self.plan.set_values(vals)
+        self.plan.factor()
+        self._key = key
+
+    def gradient(self, lam, x):
+        nrhs = 1 if x.dim() == 1 else x.shape[0]
+        gg = torch.empty(self.nedges, dtype=torch.float64, device=self.device)
+        gr = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        C.vtm_netmap_gradient(self.netmap, lam.contiguous(), x.contiguous(), nrhs, gg, gr)
+        return gg, gr
+
+    def solve(self, g, ground, b, tol=1e-10):
+        return VTMSolve.apply(g, ground, b, self, tol)
+
+    def close(self):
+        if getattr(self, "netmap", None) is not None:
+            C.vtm_netmap_destroy(self.netmap)
+            self.netmap = None
+        self.plan.close()
+
+
+class VTMSolve(torch.autograd.Function):
+    """x = A(g, ground)^-1 b by VTM; backward by one adjoint VTM solve:
+    dL/db = lam, dL/dg_e = -(lam_i - lam_j)(x_i - x_j), dL/dground = -lam x,
+    with A^T lam = dL/dx."""
+
+    @staticmethod
+    def forward(ctx, g, ground, b, net, tol):
+        g = g.detach().to(torch.float64).contiguous()
+        gr = None if ground is None else ground.detach().to(torch.float64).contiguous()
+        net._set(g, gr)
+        x, info = net.plan.solve(b.detach().to(torch.float64).contiguous(), tol=tol)
+        ctx.net, ctx.tol = net, tol
+        ctx.has_ground = ground is not None
+        ctx.save_for_backward(x)
+        ctx.info = info
+        return x
+
+    @staticmethod
+    def backward(ctx, grad_x):
+        (x,) = ctx.saved_tensors
+        net = ctx.net
+        lam, _ = net.plan.adjoint(grad_x.to(torch.float64).contiguous(), tol=ctx.tol)
+        gg, gr = net.gradient(lam, x)
+        return gg, (gr if ctx.has_ground else None), lam, None, None
