@@ -41,19 +41,36 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="vtm", choices=["vtm", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "fp32", "bf16"])
+    ap.add_argument("--workload", default="power_grid", choices=["power_grid", "thermal", "vccs", "grad"],
+                    help="power_grid: the headline 2048^2 grid; thermal: 128x128x32 RC grid, 400 boxes, "
+                         "64 RHS; vccs: 1024^2 grid with controlled sources, VTM and block Jacobi; "
+                         "grad: 1024^2 grid, forward + adjoint solve + branch gradients")
     ap.add_argument("--grid", type=int, default=2048)
     ap.add_argument("--zc", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--sweep-kernel", type=int, default=0, choices=[0, 1, 2],
-                    help="0: automatic, 1: direct-load sweep kernel, 2: bulk-copy staged kernel")
+    ap.add_argument("--l2-persist", type=int, default=0, choices=[0, 1],
+                    help="0: reflection matrices persisting in L2 during low-precision sweeps, 1: off")
+    ap.add_argument("--sweep-kernel", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="0: automatic, 1: direct-load, 2: bulk-copy staged, 3: vector-load")
     return ap.parse_args()
 
 
 def workload_config(args):
+    l2 = "flushed (512 MB write) between timed steps"
+    if args.workload == "thermal":
+        return {"workload": "RC thermal grid 128x128x32 (524288 unknowns), G + C/h, 400 random boxes "
+                            "(200-3000 nodes), Zc=1 ohm, 64 RHS", "n": 524288, "nrhs": 64, "tol": TOL,
+                "seed": 0, "l2": l2}
+    if args.workload == "vccs":
+        return {"workload": "1024x1024 resistor grid + VCCS at 5% of nodes (unsymmetric), 256 tiles of 64x64, "
+                            "Zc=1 ohm, 1 RHS", "n": 1048576, "nrhs": 1, "tol": TOL, "seed": 0, "l2": l2}
+    if args.workload == "grad":
+        return {"workload": "1024x1024 SPD grid, 256 tiles of 64x64, Zc=1 ohm; step = forward solve + adjoint "
+                            "solve + branch/injection gradients of sum(x^2)", "n": 1048576, "nrhs": 1,
+                "tol": TOL, "seed": 0, "l2": l2}
     return {"workload": f"power grid {args.grid}x{args.grid} (5-point, {args.grid * args.grid} unknowns), "
                         f"32x32-node tiles ({(args.grid // 32) ** 2} sub-circuits), Zc={args.zc} ohm, 1 RHS",
-            "n": args.grid * args.grid, "nrhs": 1, "tol": TOL, "seed": 0,
-            "l2": "flushed (512 MB write) between timed steps"}
+            "n": args.grid * args.grid, "nrhs": 1, "tol": TOL, "seed": 0, "l2": l2}
 
 
 # ---------------------------------------------------------------------------
@@ -176,14 +193,24 @@ def measured_peaks():
     return 6800.0, "of fallback"
 
 
-def sweep_bytes(stats, prec):
+def sweep_bytes(stats, prec, nrhs=1):
     """Algorithmic bytes of one sweep launch: the reflection matrices once,
-    and per port the twin's (w_in, w_out), its own (w_in, w_out) of the
-    previous sweep, c, the new (w_in, w_out), plus g (8 B), twin index (4 B)
-    and node-run byte (1 B)."""
+    and per port and right-hand side the twin's (w_in, w_out), its own
+    (w_in, w_out) of the previous sweep, c, the new (w_in, w_out); per port
+    g (8 B), twin index (4 B) and node-run byte (1 B)."""
     s_t = {0: 8, 1: 4, 2: 2}[prec]
     s_w = 8 if prec == 0 else 4
-    return stats["sum_p2"] * s_t + stats["nports"] * (7 * s_w + 13)
+    return stats["sum_p2"] * s_t + stats["nports"] * (7 * s_w * nrhs + 13)
+
+
+def plan_rowptr(w, dev):
+    import torch
+    return torch.from_numpy(w.indptr).to(dev)
+
+
+def plan_colidx(w, dev):
+    import torch
+    return torch.from_numpy(w.indices).to(dev)
 
 
 def traffic_record(prec):
@@ -216,14 +243,27 @@ def gpu_arm(args):
     build.build()
     from paper_0910_0663_gb300 import vtm, workloads as wl
 
-    w = wl.c2_power_grid(Zc=args.zc, ny=args.grid, nx=args.grid)
+    if args.workload == "thermal":
+        w = wl.c3_thermal(nrhs=64)
+    elif args.workload == "vccs":
+        w = wl.c4_vccs()
+    elif args.workload == "grad":
+        w = wl.c5_grad_grid()
+    else:
+        w = wl.c2_power_grid(Zc=args.zc, ny=args.grid, nx=args.grid)
     stream = torch.cuda.Stream(dev)
-    b_dev = torch.from_numpy(w.b[0]).to(dev)
-    b_host = torch.from_numpy(w.b[0]).pin_memory()
+    bsrc = w.b if args.workload == "thermal" else w.b[0]
+    b_dev = torch.from_numpy(bsrc).to(dev)
+    b_host = torch.from_numpy(bsrc).pin_memory()
     x_host = torch.empty_like(b_host).pin_memory()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    precs = ["fp64", "fp32", "bf16"] if args.precision == "auto" else [args.precision]
+    if args.workload == "vccs":
+        precs = ["fp64", "bj_fp64"]
+    elif args.precision == "auto":
+        precs = ["fp64", "fp32", "bf16"] if args.workload != "grad" else ["fp64", "fp32"]
+    else:
+        precs = [args.precision]
     results = {}
     plans = {}
     errors = {}
@@ -247,20 +287,42 @@ def run_mode(args, prec, w, dev, stream, b_dev, b_host, x_host, flush, world):
     import torch
     import torch.distributed as dist
     from paper_0910_0663_gb300 import vtm
+    method = "bj" if prec.startswith("bj_") else "vtm"
+    prec_name = prec.split("_")[-1]
+    nrhs = 1 if b_dev.dim() == 1 else b_dev.shape[0]
+    grad = args.workload == "grad"
     if True:
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
             plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc,
-                            precision=prec, device=dev, stream=stream, factor=False,
-                            sweep_kernel=args.sweep_kernel)
+                            precision=prec_name, device=dev, stream=stream, factor=False,
+                            sweep_kernel=args.sweep_kernel, l2_persist=args.l2_persist, method=method)
             t1 = time.perf_counter()
             plan.factor()
         torch.cuda.synchronize()
+        if grad:
+            netmap = vtm.C.vtm_netmap_create(w.n, plan_rowptr(w, dev), plan_colidx(w, dev),
+                                             len(w.edges), torch.from_numpy(w.edges[:, 0]).to(dev),
+                                             torch.from_numpy(w.edges[:, 1]).to(dev), stream.cuda_stream)
+            ei = torch.from_numpy(w.edges[:, 0]).to(dev)
+            gg = torch.empty(len(w.edges), dtype=torch.float64, device=dev)
+            gr = torch.empty(w.n, dtype=torch.float64, device=dev)
+
+        def step():
+            x, info = plan.solve(b_dev, tol=TOL)
+            if grad:
+                lam, info2 = plan.adjoint(2.0 * x, tol=TOL)
+                vtm.C.vtm_netmap_gradient(netmap, lam, x, 1, gg, gr)
+                info = dict(info)
+                for key in ("sweeps", "kernel_launches", "sweep_launches", "t_sweeps_ms"):
+                    info[key] = info[key] + info2[key]
+                info["relres"] = max(info["relres"], info2["relres"])
+            return x, info
         t2 = time.perf_counter()
         # warm-up
         for _ in range(args.warmup):
             with torch.cuda.stream(stream):
-                x, info = plan.solve(b_dev, tol=TOL)
+                x, info = step()
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -274,7 +336,7 @@ def run_mode(args, prec, w, dev, stream, b_dev, b_host, x_host, flush, world):
                 torch.cuda.synchronize()
                 with torch.cuda.stream(stream):
                     ev0.record(stream)
-                    x, info = plan.solve(b_dev, tol=TOL)
+                    x, info = step()
                     ev1.record(stream)
                 torch.cuda.synchronize()
                 times.append(ev0.elapsed_time(ev1))
@@ -292,18 +354,20 @@ def run_mode(args, prec, w, dev, stream, b_dev, b_host, x_host, flush, world):
             torch.cuda.synchronize()
             h0 = time.perf_counter()
             with torch.cuda.stream(stream):
-                C.vtm_solve(plan.handle, b_host, x_host, 1, TOL)
+                C.vtm_solve(plan.handle, b_host, x_host, nrhs, TOL)
             h1 = time.perf_counter()
             e2e.append(h1 - h0)
         st = plan.stats()
         inf = infos[-1]
-        bytes_sweep = sweep_bytes(st, {"fp64": 0, "fp32": 1, "bf16": 2}[prec])
+        bytes_sweep = sweep_bytes(st, {"fp64": 0, "fp32": 1, "bf16": 2}[prec_name], nrhs)
         sweeps_eff = inf["sweeps"]
         t_sweep_launch = inf["t_sweeps_ms"] / max(1, inf["sweep_launches"])
         achieved = bytes_sweep * sweeps_eff / (inf["t_sweeps_ms"] * 1e-3) / 1e9
+        if grad:
+            vtm.C.vtm_netmap_destroy(netmap)
         return dict(t_step_ms=t_step, t_plan_s=t1 - t0, t_factor_s=t2 - t1,
-                             value=w.n * world / (t_step * 1e-3),
-                             e2e_value=w.n * world / float(np.mean(e2e)), info=inf, stats=st,
+                             value=w.n * nrhs * world / (t_step * 1e-3), nrhs=nrhs,
+                             e2e_value=w.n * nrhs * world / float(np.mean(e2e)), info=inf, stats=st,
                              bytes_sweep=bytes_sweep, achieved_gbs=achieved,
                              t_sweep_ms=t_sweep_launch, clocks=sampler.summary(),
                              relres=max(i["relres"] for i in infos)), plan
@@ -312,12 +376,12 @@ def run_mode(args, prec, w, dev, stream, b_dev, b_host, x_host, flush, world):
 def emit(args, results, errors, best, w, world, rank):
     R = results[best]
     peak, peak_src = measured_peaks()
-    prec_id = {"fp64": 0, "fp32": 1, "bf16": 2}[best]
+    prec_id = {"fp64": 0, "fp32": 1, "bf16": 2}[best.split("_")[-1]]
     line = {
         "metric": METRIC, "value": R["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": R["t_step_ms"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64", "fp32": "f32+f64 refinement", "bf16": "bf16+f64 refinement"}[best],
+        "dtype": {"fp64": "f64", "fp32": "f32+f64 refinement", "bf16": "bf16+f64 refinement"}[best.split("_")[-1]],
         "data": "synthetic", "config": dict(workload_config(args), precision=best),
         "roofline": {"bound": "hbm", "kernel": "sweep_kernel",
                      "achieved": R["achieved_gbs"], "peak": peak, "unit": "GB/s",
@@ -325,8 +389,8 @@ def emit(args, results, errors, best, w, world, rank):
                      "traffic": traffic_record(prec_id),
                      "algorithmic_bytes_per_launch": R["bytes_sweep"],
                      "avg_launch_ms": R["t_sweep_ms"]},
-        "e2e": {"value": R["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": w.n * 8,
-                "d2h_bytes_per_step": w.n * 8},
+        "e2e": {"value": R["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": w.n * 8 * R["nrhs"],
+                "d2h_bytes_per_step": w.n * 8 * R["nrhs"]},
         "gpu_launches": R["info"]["kernel_launches"],
         "clocks": R["clocks"],
         "sweeps": R["info"]["sweeps"], "outer_steps": R["info"]["outer_steps"],
@@ -341,7 +405,7 @@ def emit(args, results, errors, best, w, world, rank):
         line["mode_errors"] = errors
     if "fp64" in results:
         line["vs_plain_fp64"] = R["value"] / results["fp64"]["value"]
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "power_grid":
         v, dt, sweeps = oracle_sample(args)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": sample_text(sweeps), "seconds": dt}

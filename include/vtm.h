@@ -83,8 +83,16 @@ typedef struct {
                         rounding floor); the FP64 refinement then continues. */
   int max_outer;     /* refinement steps in the FP32/BF16 modes; default 40 */
   int method;        /* VTM_METHOD_VTM (default) or VTM_METHOD_BJ; read by vtm_plan only */
-  int sweep_kernel;  /* 0 (default): automatic (direct-load for FP64, bulk-copy staged
-                        otherwise); 1: direct-load kernel; 2: bulk-copy staged kernel */
+  int batch;         /* several right-hand sides: 0 (default) one batched iteration over
+                        up to 64 columns at a time; 1: one column after the other */
+  int l2_persist;    /* 0 (default): during FP32/BF16 sweeps, mark the reflection matrices
+                        persisting in L2 (access-policy window on the plan's stream; the
+                        context's persisting carve-out is set and restored around the
+                        sweeps); 1: off.  Needs a non-default stream. */
+  int sweep_kernel;  /* 0 (default): automatic (FP64: direct-load; FP32/BF16: vector-load
+                        when every tile has p <= 256 VEC ports, else bulk-copy staged);
+                        1: direct-load kernel; 2: bulk-copy staged kernel;
+                        3: 16-byte vector-load kernel */
   double* history;   /* optional host array: relative (interface) residual after each
                         sweep k=1..history_len of the first column; NULL = not recorded */
   int history_len;

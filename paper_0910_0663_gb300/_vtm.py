@@ -26,7 +26,8 @@ METHOD = {"vtm": 0, "bj": 1}
 class vtm_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_sweeps", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("max_outer", ctypes.c_int), ("method", ctypes.c_int), ("sweep_kernel", ctypes.c_int),
+                ("max_outer", ctypes.c_int), ("method", ctypes.c_int), ("batch", ctypes.c_int),
+                ("l2_persist", ctypes.c_int), ("sweep_kernel", ctypes.c_int),
                 ("history", ctypes.POINTER(ctypes.c_double)),
                 ("history_len", ctypes.c_int)]
 
@@ -124,7 +125,7 @@ def _check(status, where):
 
 
 def make_opts(precision="fp64", max_sweeps=0, check_every=0, inner_tol=0.0, max_outer=0,
-              history=None, sweep_kernel=0, method="vtm"):
+              history=None, sweep_kernel=0, method="vtm", batch=0, l2_persist=0):
     o = vtm_opts()
     o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
     o.max_sweeps = max_sweeps
@@ -133,6 +134,8 @@ def make_opts(precision="fp64", max_sweeps=0, check_every=0, inner_tol=0.0, max_
     o.max_outer = max_outer
     o.sweep_kernel = sweep_kernel
     o.method = METHOD[method] if isinstance(method, str) else int(method)
+    o.batch = int(batch)
+    o.l2_persist = int(l2_persist)
     if history is not None:
         assert history.dtype == np.float64 and history.flags["C_CONTIGUOUS"]
         o.history = history.ctypes.data_as(ctypes.POINTER(ctypes.c_double))

@@ -1,0 +1,761 @@
+// Many right-hand sides at once (backward-Euler time steps of an RC grid).
+//
+// The same VTM sweep (Sec. VI, Eq. 11/14) for R right-hand sides: per
+// sub-circuit the wave update is a dense product W_out = T_P W_in + C_P with
+// W_in = the R incident waves of every port (p x R).  Vectors are kept
+// row-major, [port][R] and [node][R], so that the exchange moves one
+// contiguous row per port.
+//
+// Kernels:
+//  * batch_band_solve_kernel: K_P^-1 V for a block of RG right-hand sides,
+//    one thread per band offset (each thread updates its row for RG
+//    columns), factor columns prefetched D steps ahead;
+//  * batch_sweep_kernel: one CTA per (tile, block of 64 outputs); each
+//    thread owns a 4 x 4 block of (output, RHS); T and the gathered incident
+//    waves pass through shared memory in chunks of 16 inputs; the residual of
+//    the previous sweep (per RHS) is reduced per item and then over items in
+//    a fixed order;
+//  * batch_sweep_mma_kernel: the same with BF16 T and BF16 incident waves on
+//    the tensor cores (mma.sync m16n8k16, FP32 accumulate).
+#include <algorithm>
+#include <cmath>
+
+#include "vtm_internal.h"
+
+namespace vtm {
+
+struct BatchCtrl {
+  int k;
+  int flag;  // 0 running, 1 converged, 2 sweep limit, 3 diverged, 4 stalled
+  unsigned counter;
+  int conv_sweep;
+  int k_max;
+  int best_k;
+  int stall;
+  int R;
+  double best_ratio;  // max over columns of res2 / tol2 at best_k
+  double first_ratio;
+};
+
+// ---------------------------------------------------------------------------
+// permutation between the caller's column-major n x R and [pos][R]
+// ---------------------------------------------------------------------------
+
+template <class FT>
+__global__ void batch_gather_kernel(const int32_t* __restrict__ perm, const double* __restrict__ src,
+                                    FT* __restrict__ dst, int64_t n, int R) {
+  const int64_t total = n * R;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pos = i / R;
+    const int r = (int)(i % R);
+    dst[i] = (FT)src[(int64_t)r * n + perm[pos]];
+  }
+}
+
+template <class FT>
+__global__ void batch_scatter_kernel(const int32_t* __restrict__ perm, const FT* __restrict__ src,
+                                     double* __restrict__ dst, int64_t n, int R, int accumulate) {
+  const int64_t total = n * R;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pos = i / R;
+    const int r = (int)(i % R);
+    double* d = dst + (int64_t)r * n + perm[pos];
+    if (accumulate) *d += (double)src[i];
+    else *d = (double)src[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// band solves for RG right-hand sides per CTA
+// ---------------------------------------------------------------------------
+//
+// V[pos][R] in global memory, the tile's block of RG columns staged in
+// shared memory ([n_P][RG]).  Thread a (1..bw) owns band offset a: at step j
+// it updates row j + a with multiplier Lc[j][a] (forward) or row j - a with
+// Uc[j][a] (backward); one barrier per step.  Each thread prefetches its
+// multiplier D columns ahead.
+
+template <class FT, int RG, int D>
+__global__ void batch_band_solve_kernel(const int32_t* __restrict__ node_off,
+                                        const int32_t* __restrict__ bwv,
+                                        const int64_t* __restrict__ band_off,
+                                        const FT* __restrict__ Lc, const FT* __restrict__ Uc,
+                                        FT* __restrict__ V, int R) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  FT* v = reinterpret_cast<FT*>(smem_raw);  // [n][RG]
+  const int ngroups = (R + RG - 1) / RG;
+  const int t = blockIdx.x / ngroups;
+  const int r0 = (blockIdx.x % ngroups) * RG;
+  const int rg = min(RG, R - r0);
+  const int base = node_off[t];
+  const int n = node_off[t + 1] - base;
+  const int bw = bwv[t];
+  const int B = bw + 1;
+  const FT* lc = Lc + band_off[t];
+  const FT* uc = Uc + band_off[t];
+  const int tid = threadIdx.x;
+  for (int i = tid; i < n * RG; i += blockDim.x) {
+    const int row = i / RG, c = i % RG;
+    v[i] = c < rg ? V[(int64_t)(base + row) * R + r0 + c] : FT(0);
+  }
+  __syncthreads();
+  const int a = tid + 1;  // band offset of this thread
+  const bool act = a <= bw;
+  FT pf[D];
+  // forward sweep (scaled multipliers, see band.cuh)
+#pragma unroll
+  for (int d = 0; d < D; ++d) pf[d] = (act && d < n && a <= n - 1 - d) ? lc[(size_t)d * B + a] : FT(0);
+  for (int j0 = 0; j0 < n; j0 += D) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const int j = j0 + d;
+      if (j < n) {
+        if (act && a <= n - 1 - j) {
+          const FT m = pf[d];
+          FT* dst = v + (size_t)(j + a) * RG;
+          const FT* src = v + (size_t)j * RG;
+#pragma unroll
+          for (int c = 0; c < RG; ++c) dst[c] -= m * src[c];
+        }
+        const int jn = j + D;
+        pf[d] = (act && jn < n && a <= n - 1 - jn) ? lc[(size_t)jn * B + a] : FT(0);
+        __syncthreads();
+      }
+    }
+  }
+  for (int i = tid; i < n * RG; i += blockDim.x) v[i] *= lc[(size_t)(i / RG) * B];
+  __syncthreads();
+  // backward sweep
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const int j = n - 1 - d;
+    pf[d] = (act && j >= 0 && a <= j) ? uc[(size_t)j * B + a] : FT(0);
+  }
+  for (int j0 = n - 1; j0 >= 0; j0 -= D) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const int j = j0 - d;
+      if (j >= 0) {
+        if (act && a <= j) {
+          const FT m = pf[d];
+          FT* dst = v + (size_t)(j - a) * RG;
+          const FT* src = v + (size_t)j * RG;
+#pragma unroll
+          for (int c = 0; c < RG; ++c) dst[c] -= m * src[c];
+        }
+        const int jn = j - D;
+        pf[d] = (act && jn >= 0 && a <= jn) ? uc[(size_t)jn * B + a] : FT(0);
+        __syncthreads();
+      }
+    }
+  }
+  for (int i = tid; i < n * RG; i += blockDim.x) {
+    const int row = i / RG, c = i % RG;
+    const FT x = v[i] * uc[(size_t)row * B];
+    if (c < rg) V[(int64_t)(base + row) * R + r0 + c] = x;
+  }
+}
+
+// c[s][r] = 2 W beta_s x0[pos(s)][r]
+template <class FT, class WT>
+__global__ void batch_const_kernel(const int32_t* __restrict__ port_pos, const double* __restrict__ beta,
+                                   const FT* __restrict__ x0, double W, WT* __restrict__ c,
+                                   int64_t nports, int R) {
+  const int64_t total = nports * R;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = i / R;
+    const int r = (int)(i % R);
+    c[i] = (WT)(2.0 * W * beta[s] * (double)x0[(int64_t)port_pos[s] * R + r]);
+  }
+}
+
+// V[pos(node)][r] += sum over the node's ports of beta_s w_in[s][r]
+template <class FT, class WT>
+__global__ void batch_inject_kernel(const int32_t* __restrict__ port_pos, const uint8_t* __restrict__ run,
+                                    const double* __restrict__ beta, const WT* __restrict__ st,
+                                    FT* __restrict__ V, int64_t nports, int R) {
+  const int64_t total = nports * R;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = i / R;
+    const int r = (int)(i % R);
+    const int nr = run[s];
+    if (!nr) continue;
+    double acc = 0.0;
+    for (int q = 0; q < nr; ++q) acc += beta[s + q] * (double)st[(s + q) * 2 * R + r];
+    V[(int64_t)port_pos[s] * R + r] += (FT)acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the batched sweep
+// ---------------------------------------------------------------------------
+
+constexpr int kMB = 64;  // outputs per work item
+constexpr int kKC = 16;  // inputs per chunk
+
+__device__ __forceinline__ float to_acc(float v) { return v; }
+__device__ __forceinline__ double to_acc(double v) { return v; }
+__device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// Residual terms of the previous sweep for the node runs that start in
+// [m0, m1) of the tile starting at port p0 (a run may reach past m1), per
+// RHS: the square of each node's residual goes to rsq[run][r] (shared), and
+// red[r] receives the column sums in a fixed order.  State layout:
+// [port][2][R] = (w_in, w_out).
+template <class WT>
+__device__ void batch_residual(const int32_t* __restrict__ twin, const double* __restrict__ g,
+                               const uint8_t* __restrict__ run, const WT* __restrict__ prev,
+                               int p0, int m0, int m1, int R, double W, double (*rsq)[64],
+                               double* red) {
+  const double inv2W = 0.5 / W;
+  for (int i = threadIdx.x; i < (m1 - m0) * R; i += blockDim.x) {
+    const int sl = i / R;
+    const int r = i % R;
+    const int gs = p0 + m0 + sl;
+    const int nr = run[gs];
+    double rsum = 0.0;
+    for (int q = 0; q < nr; ++q) {
+      const int ps = gs + q;
+      const int tw = twin[ps];
+      const double wi_s = (double)prev[(size_t)ps * 2 * R + r];
+      const double wo_s = (double)prev[(size_t)ps * 2 * R + R + r];
+      const double wi_t = (double)prev[(size_t)tw * 2 * R + r];
+      const double wo_t = (double)prev[(size_t)tw * 2 * R + R + r];
+      const double gg = g[ps];
+      const double us = (wi_s + wo_s) * inv2W, ut = (wi_t + wo_t) * inv2W;
+      rsum += 0.5 * ((W - 2 * gg) * us + (W + 2 * gg) * ut - wi_s - wi_t);
+    }
+    rsq[sl][r] = rsum * rsum;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    double a = 0.0;
+    for (int sl = 0; sl < m1 - m0; ++sl) a += rsq[sl][r];
+    red[r] = a;
+  }
+}
+
+// Last-CTA reduction over work items per RHS and the convergence decision.
+__device__ void batch_finish(BatchCtrl* __restrict__ ctrl, const double* __restrict__ partials,
+                             int nitems, int R, const double* __restrict__ tol2,
+                             double* __restrict__ hist, int hist_len, int k) {
+  __shared__ double worst;
+  __shared__ int any_bad;
+  if (threadIdx.x == 0) {
+    worst = 0.0;
+    any_bad = 0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    double tot = 0.0;
+    for (int w = 0; w < nitems; ++w) tot += partials[(size_t)w * R + r];
+    if (!isfinite(tot)) atomicExch(&any_bad, 1);
+    const double ratio = tot / tol2[r];
+    // max over columns (atomicMax on the bit pattern of a non-negative double)
+    atomicMax(reinterpret_cast<unsigned long long*>(&worst), __double_as_longlong(ratio));
+    if (r == 0 && hist && k - 1 >= 1 && k - 1 <= hist_len) hist[k - 2] = tot;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int flag = 0;
+    if (k > 1) {
+      const int ks = k - 1;
+      const double ratio = worst;
+      if (ks == 1) ctrl->first_ratio = ratio;
+      if (ks == 1 || ratio < 0.81 * ctrl->best_ratio) {
+        ctrl->best_ratio = ratio;
+        ctrl->best_k = ks;
+      }
+      if (any_bad || (ks > 1 && ratio > 1e12 * ctrl->first_ratio && ctrl->first_ratio > 0)) {
+        flag = 3;
+      } else if (ratio <= 1.0) {
+        flag = 1;
+        ctrl->conv_sweep = ks;
+      } else if (ctrl->stall > 0 && ks - ctrl->best_k >= ctrl->stall) {
+        flag = 4;
+        ctrl->conv_sweep = ks;
+      }
+    }
+    if (!flag && k >= ctrl->k_max) flag = 2;
+    ctrl->counter = 0u;
+    ctrl->k = k + 1;
+    __threadfence();
+    ctrl->flag = flag;
+  }
+}
+
+// CUDA-core version: thread (ty, tx) owns outputs m0 + 4 ty .. +3 and RHS
+// 4 tx .. +3.  TT: stored T type; WT: wave type; AT: accumulate type.
+template <class TT, class WT, class AT>
+__global__ void __launch_bounds__(256) batch_sweep_kernel(
+    const TT* __restrict__ T, const int64_t* __restrict__ T_off, const int32_t* __restrict__ T_ld,
+    const int32_t* __restrict__ port_off, const int32_t* __restrict__ item_tile,
+    const int32_t* __restrict__ item_m0, int nitems, const int32_t* __restrict__ twin,
+    const double* __restrict__ g, const uint8_t* __restrict__ run, const WT* __restrict__ c,
+    WT* __restrict__ state, int64_t nports, int R, double W, BatchCtrl* __restrict__ ctrl,
+    double* __restrict__ partials, const double* __restrict__ tol2, double* __restrict__ hist,
+    int hist_len) {
+  __shared__ AT Ts[kKC][kMB];
+  __shared__ AT Ws[kKC][64];
+  __shared__ double red[64];
+  __shared__ double rsq[kMB][64];
+  __shared__ int s_k, s_flag;
+  __shared__ bool s_last;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    s_k = *((volatile int*)&ctrl->k);
+    s_flag = *((volatile int*)&ctrl->flag);
+  }
+  if (tid < 64) red[tid] = 0.0;
+  __syncthreads();
+  if (s_flag) return;
+  const int k = s_k;
+  const int item = blockIdx.x;
+  const int tile = item_tile[item];
+  const int m0 = item_m0[item];
+  const int p0 = port_off[tile];
+  const int p = port_off[tile + 1] - p0;
+  const int m1 = min(p, m0 + kMB);
+  const int ld = T_ld[tile];
+  const TT* Tb = T + T_off[tile];
+  const WT* prev = state + (size_t)((k - 1) & 1) * nports * 2 * R;
+  WT* cur = state + (size_t)(k & 1) * nports * 2 * R;
+  if (k > 1) batch_residual<WT>(twin, g, run, prev, p0, m0, m1, R, W, rsq, red);
+  const int tx = tid % 16, ty = tid / 16;
+  AT acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+  if (k > 1) {
+    for (int t0 = 0; t0 < p; t0 += kKC) {
+      for (int i = tid; i < kKC * kMB; i += blockDim.x) {
+        const int kk = i / kMB, mm = i % kMB;
+        const int t = t0 + kk, s = m0 + mm;
+        Ts[kk][mm] = (t < p && s < m1) ? to_acc(Tb[(size_t)t * ld + s]) : AT(0);
+      }
+      for (int i = tid; i < kKC * 64; i += blockDim.x) {
+        const int kk = i / 64, r = i % 64;
+        const int t = t0 + kk;
+        Ws[kk][r] = (t < p && r < R) ? (AT)prev[(size_t)twin[p0 + t] * 2 * R + R + r] : AT(0);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < kKC; ++kk) {
+        AT a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = Ts[kk][4 * ty + i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = Ws[kk][4 * tx + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+      }
+      __syncthreads();
+    }
+  }
+  // epilogue: w_out = acc + c, and this sweep's incident waves
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int s = m0 + 4 * ty + i;
+    if (s >= m1) continue;
+    const size_t ps = (size_t)(p0 + s);
+    const int tw = twin[p0 + s];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = 4 * tx + j;
+      if (r >= R) continue;
+      const WT wi = k > 1 ? prev[(size_t)tw * 2 * R + R + r] : WT(0);
+      cur[ps * 2 * R + r] = wi;
+      cur[ps * 2 * R + R + r] = (WT)(acc[i][j] + (AT)c[ps * R + r]);
+    }
+  }
+  __syncthreads();
+  for (int r = tid; r < R; r += blockDim.x) partials[(size_t)item * R + r] = red[r];
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    s_last = atomicAdd(&ctrl->counter, 1u) == (unsigned)nitems - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  batch_finish(ctrl, partials, nitems, R, tol2, hist, hist_len, k);
+}
+
+// ---------------------------------------------------------------------------
+// tensor-core version (BF16 T and incident waves, FP32 accumulate)
+// ---------------------------------------------------------------------------
+//
+// CTA = 4 warps; warp w computes outputs m0 + 16 w .. +15 for all R (<= 64)
+// RHS with mma.sync.m16n8k16 (A = T(s, t) read transposed from the stored
+// T^T rows with ldmatrix.trans, B = W_in(t, r) read transposed from its
+// row-major chunk).  Shared rows are padded by 8 elements (16 bytes) so the
+// eight row addresses of each 8x8 ldmatrix fall in distinct bank groups.
+
+constexpr int kAPad = kMB + 8;
+constexpr int kBPad = 64 + 8;
+
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3,
+                                              const void* p) {
+  const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(a));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(128) batch_sweep_mma_kernel(
+    const __nv_bfloat16* __restrict__ T, const int64_t* __restrict__ T_off,
+    const int32_t* __restrict__ T_ld, const int32_t* __restrict__ port_off,
+    const int32_t* __restrict__ item_tile, const int32_t* __restrict__ item_m0, int nitems,
+    const int32_t* __restrict__ twin, const double* __restrict__ g,
+    const uint8_t* __restrict__ run, const float* __restrict__ c, float* __restrict__ state,
+    int64_t nports, int R, double W, BatchCtrl* __restrict__ ctrl, double* __restrict__ partials,
+    const double* __restrict__ tol2, double* __restrict__ hist, int hist_len) {
+  __shared__ __align__(16) __nv_bfloat16 As[kKC][kAPad];  // T^T chunk: [t][s]
+  __shared__ __align__(16) __nv_bfloat16 Bs[kKC][kBPad];  // W_in chunk: [t][r]
+  __shared__ double red[64];
+  __shared__ double rsq[kMB][64];
+  __shared__ int s_k, s_flag;
+  __shared__ bool s_last;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    s_k = *((volatile int*)&ctrl->k);
+    s_flag = *((volatile int*)&ctrl->flag);
+  }
+  if (tid < 64) red[tid] = 0.0;
+  __syncthreads();
+  if (s_flag) return;
+  const int k = s_k;
+  const int item = blockIdx.x;
+  const int tile = item_tile[item];
+  const int m0 = item_m0[item];
+  const int p0 = port_off[tile];
+  const int p = port_off[tile + 1] - p0;
+  const int m1 = min(p, m0 + kMB);
+  const int ld = T_ld[tile];
+  const __nv_bfloat16* Tb = T + T_off[tile];
+  const float* prev = state + (size_t)((k - 1) & 1) * nports * 2 * R;
+  float* cur = state + (size_t)(k & 1) * nports * 2 * R;
+  if (k > 1) batch_residual<float>(twin, g, run, prev, p0, m0, m1, R, W, rsq, red);
+  float acc[8][4];
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc[nt][e] = 0.f;
+  const int ntiles = (R + 7) / 8;
+  if (k > 1) {
+    for (int t0 = 0; t0 < p; t0 += kKC) {
+      // A chunk: 16 rows x 64 outputs (8 x 16-byte pieces per row)
+      for (int i = tid; i < kKC * 8; i += blockDim.x) {
+        const int kk = i / 8, piece = i % 8;
+        const int t = t0 + kk, s = m0 + piece * 8;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (t < p && s < m1) v = __ldcs(reinterpret_cast<const uint4*>(Tb + (size_t)t * ld + s));
+        *reinterpret_cast<uint4*>(&As[kk][piece * 8]) = v;
+      }
+      // B chunk: 16 rows x R incident waves, gathered and rounded to BF16
+      for (int i = tid; i < kKC * 16; i += blockDim.x) {
+        const int kk = i / 16, q = i % 16;
+        const int t = t0 + kk, r = q * 4;
+        float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (t < p && r < R)
+          w = *reinterpret_cast<const float4*>(prev + (size_t)twin[p0 + t] * 2 * R + R + r);
+        __nv_bfloat162 lo = __floats2bfloat162_rn(w.x, w.y);
+        __nv_bfloat162 hi = __floats2bfloat162_rn(w.z, w.w);
+        *reinterpret_cast<__nv_bfloat162*>(&Bs[kk][r]) = lo;
+        *reinterpret_cast<__nv_bfloat162*>(&Bs[kk][r + 2]) = hi;
+      }
+      __syncthreads();
+      // A fragment (16 outputs x 16 inputs) of this warp
+      uint32_t a0, a1, a2, a3;
+      {
+        const int mat = lane >> 3, row = lane & 7;
+        const int kk = row + ((mat >> 1) << 3);       // matrices 2,3: inputs 8..15
+        const int mm = warp * 16 + ((mat & 1) << 3);  // matrices 1,3: outputs 8..15
+        ldsm_x4_trans(a0, a1, a2, a3, &As[kk][mm]);
+      }
+#pragma unroll
+      for (int np = 0; np < 4; ++np) {  // pairs of 8-wide RHS tiles
+        if (2 * np >= ntiles) break;
+        uint32_t b0, b1, b2, b3;
+        const int mat = lane >> 3, row = lane & 7;
+        const int kk = row + ((mat & 1) << 3);              // matrices 1,3: inputs 8..15
+        const int nn = np * 16 + ((mat >> 1) << 3);         // matrices 2,3: next RHS tile
+        ldsm_x4_trans(b0, b1, b2, b3, &Bs[kk][nn]);
+        mma_bf16(acc[2 * np], a0, a1, a2, a3, b0, b1);
+        mma_bf16(acc[2 * np + 1], a0, a1, a2, a3, b2, b3);
+      }
+      __syncthreads();
+    }
+  }
+  // epilogue: fragment element e of tile nt sits at output row
+  // warp*16 + lane/4 (+8 for e >= 2) and RHS column nt*8 + 2*(lane%4) + (e&1)
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    if (nt >= ntiles) break;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int s = m0 + warp * 16 + (lane >> 2) + ((e >> 1) << 3);
+      const int r = nt * 8 + 2 * (lane & 3) + (e & 1);
+      if (s < m1 && r < R) {
+        const size_t ps = (size_t)(p0 + s);
+        const float wi = k > 1 ? prev[(size_t)twin[p0 + s] * 2 * R + R + r] : 0.f;
+        cur[ps * 2 * R + r] = wi;
+        cur[ps * 2 * R + R + r] = acc[nt][e] + c[ps * R + r];
+      }
+    }
+  }
+  __syncthreads();
+  for (int r = tid; r < R; r += blockDim.x) partials[(size_t)item * R + r] = red[r];
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    s_last = atomicAdd(&ctrl->counter, 1u) == (unsigned)nitems - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  batch_finish(ctrl, partials, nitems, R, tol2, hist, hist_len, k);
+}
+
+// ---------------------------------------------------------------------------
+// host driver for a batch of right-hand sides
+// ---------------------------------------------------------------------------
+
+static int grid_n(int64_t work) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 152 * 16));
+}
+
+template <class FT>
+static vtm_status batch_band_solve(vtm_plan_s* P, FT* V, int R, const FT* Lc, const FT* Uc) {
+  constexpr int RG = 8;
+  constexpr int D = 8;
+  const int ngroups = (R + RG - 1) / RG;
+  const int threads = std::max(32, (P->max_bw + 31) / 32 * 32);
+  const size_t smem = (size_t)P->max_nodes * RG * sizeof(FT);
+  if (threads > 1024 || smem > 200 * 1024) {
+    set_detail("batched solve: sub-circuit too large for the batched band solve");
+    return VTM_EINVAL;
+  }
+  VTM_CUDA_TRY(cudaFuncSetAttribute(batch_band_solve_kernel<FT, RG, D>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  batch_band_solve_kernel<FT, RG, D><<<P->nparts * ngroups, threads, smem, P->stream>>>(
+      P->tabs.node_off.as<int32_t>(), P->tabs.bw.as<int32_t>(), P->tabs.band_off.as<int64_t>(), Lc,
+      Uc, V, R);
+  P->launch_count++;
+  VTM_CUDA_TRY(cudaGetLastError());
+  return VTM_OK;
+}
+
+vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, double tol,
+                         vtm_info* info) {
+  cudaStream_t s = P->stream;
+  const int64_t n = P->n;
+  const int64_t npt = (int64_t)P->port_node.size();
+  const int prec = P->opts.precision;
+  if (R > 64) {
+    set_detail("batched solve: at most 64 right-hand sides per call");
+    return VTM_EINVAL;
+  }
+  // work items: (tile, block of 64 outputs)
+  if (P->item_tile.empty()) {
+    for (int32_t t = 0; t < P->nparts; ++t) {
+      const int32_t pp = P->port_off[t + 1] - P->port_off[t];
+      for (int32_t m = 0; m < pp; m += kMB) {
+        P->item_tile.push_back(t);
+        P->item_m0.push_back(m);
+      }
+    }
+    VTM_TRY(upload(P->d_item_tile, P->item_tile, s));
+    VTM_TRY(upload(P->d_item_m0, P->item_m0, s));
+  }
+  const int nitems = (int)P->item_tile.size();
+  const bool lowp = prec != VTM_PREC_FP64;
+  const size_t wsz = lowp ? sizeof(float) : sizeof(double);
+  VTM_TRY(dev_alloc(P->d_bV, (size_t)n * R * sizeof(double)));
+  VTM_TRY(dev_alloc(P->d_bstate, 4 * (size_t)std::max<int64_t>(npt, 1) * R * wsz));
+  VTM_TRY(dev_alloc(P->d_bc, (size_t)std::max<int64_t>(npt, 1) * R * wsz));
+  VTM_TRY(dev_alloc(P->d_bpart, (size_t)std::max(nitems, 1) * R * sizeof(double)));
+  VTM_TRY(dev_alloc(P->d_btol2, 64 * sizeof(double)));
+  VTM_TRY(dev_alloc(P->d_bctrl, sizeof(BatchCtrl)));
+  VTM_TRY(dev_alloc(P->d_xacc, (size_t)n * R * sizeof(double)));
+  VTM_TRY(dev_alloc(P->d_r, (size_t)n * R * sizeof(double)));
+  double* V = P->d_bV.as<double>();
+  double* xacc = P->d_xacc.as<double>();
+  double* r = P->d_r.as<double>();
+  // ||b_r||
+  std::vector<double> bnorm(R), rnorm(R), rel(R);
+  VTM_CUDA_TRY(cudaMemsetAsync(xacc, 0, (size_t)n * R * sizeof(double), s));
+  for (int c = 0; c < R; ++c) {
+    double rr, bb;
+    VTM_TRY(residual_pair(P, xacc + (size_t)c * n, d_b + (size_t)c * n, r + (size_t)c * n, &rr, &bb));
+    bnorm[c] = std::sqrt(bb);
+    rnorm[c] = bnorm[c];
+  }
+  info->sweeps = 0;
+  info->outer_steps = 0;
+  info->relres = 0.0;
+  info->first_sweep_converged = 0;
+  double inner_tol = P->opts.inner_tol;
+  if (inner_tol <= 0) inner_tol = prec == VTM_PREC_FP32 ? 1e-5 : (prec == VTM_PREC_BF16 ? 1e-2 : 0.0);
+  const int max_outer = prec == VTM_PREC_FP64 ? 4 : P->opts.max_outer;
+  int sweeps_left = P->opts.max_sweeps;
+  vtm_status result = VTM_ENOCONV;
+  const int g1 = grid_n(n * R), g2 = grid_n(npt * R);
+  for (int outer = 0; outer < max_outer; ++outer) {
+    const double* rhs = outer == 0 ? d_b : r;
+    batch_gather_kernel<double><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, V, n, R);
+    P->launch_count++;
+    VTM_TRY(batch_band_solve<double>(P, V, R, P->d_Lc.as<double>(), P->d_Uc.as<double>()));
+    int kc = 0, flag = 1;
+    if (npt > 0) {
+      if (lowp)
+        batch_const_kernel<double, float><<<g2, 256, 0, s>>>(P->d_port_pos.as<int32_t>(),
+                                                            P->d_beta.as<double>(), V, P->W,
+                                                            P->d_bc.as<float>(), npt, R);
+      else
+        batch_const_kernel<double, double><<<g2, 256, 0, s>>>(P->d_port_pos.as<int32_t>(),
+                                                             P->d_beta.as<double>(), V, P->W,
+                                                             P->d_bc.as<double>(), npt, R);
+      P->launch_count++;
+      std::vector<double> t2(64, 1.0);
+      for (int c = 0; c < R; ++c) {
+        const double target = tol * bnorm[c];
+        const double t_abs = prec == VTM_PREC_FP64 ? target : std::max(target, inner_tol * rnorm[c]);
+        t2[c] = std::max(t_abs * t_abs, 1e-300);
+      }
+      VTM_CUDA_TRY(cudaMemcpyAsync(P->d_btol2.p, t2.data(), 64 * sizeof(double), cudaMemcpyHostToDevice, s));
+      BatchCtrl h{};
+      h.k = 1;
+      h.k_max = sweeps_left;
+      h.stall = lowp ? 64 : 0;
+      h.R = R;
+      VTM_CUDA_TRY(cudaMemcpyAsync(P->d_bctrl.p, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+      VTM_CUDA_TRY(cudaMemsetAsync(P->d_bstate.p, 0, 4 * (size_t)npt * R * wsz, s));
+      VTM_CUDA_TRY(cudaStreamSynchronize(s));
+      if (sweeps_left <= 0) break;
+      int launched = 0;
+      BatchCtrl hc{};
+      while (true) {
+        const int m = std::min(P->opts.check_every, sweeps_left + 1 - launched);
+        VTM_CUDA_TRY(cudaEventRecord(P->evs0, s));
+        for (int i = 0; i < m; ++i) {
+          if (prec == VTM_PREC_BF16 && R % 8 != 0)
+            batch_sweep_kernel<__nv_bfloat16, float, float><<<nitems, 256, 0, s>>>(
+                P->d_T16.as<__nv_bfloat16>(), P->tabs.T_off.as<int64_t>(), P->tabs.T_ld.as<int32_t>(),
+                P->tabs.port_off.as<int32_t>(), P->d_item_tile.as<int32_t>(),
+                P->d_item_m0.as<int32_t>(), nitems, P->d_twin.as<int32_t>(), P->d_g.as<double>(),
+                P->d_run.as<uint8_t>(), P->d_bc.as<float>(), P->d_bstate.as<float>(), npt, R, P->W,
+                P->d_bctrl.as<BatchCtrl>(), P->d_bpart.as<double>(), P->d_btol2.as<double>(),
+                nullptr, 0);
+          else if (prec == VTM_PREC_BF16)
+            batch_sweep_mma_kernel<<<nitems, 128, 0, s>>>(
+                P->d_T16.as<__nv_bfloat16>(), P->tabs.T_off.as<int64_t>(), P->tabs.T_ld.as<int32_t>(),
+                P->tabs.port_off.as<int32_t>(), P->d_item_tile.as<int32_t>(),
+                P->d_item_m0.as<int32_t>(), nitems, P->d_twin.as<int32_t>(), P->d_g.as<double>(),
+                P->d_run.as<uint8_t>(), P->d_bc.as<float>(), P->d_bstate.as<float>(), npt, R, P->W,
+                P->d_bctrl.as<BatchCtrl>(), P->d_bpart.as<double>(), P->d_btol2.as<double>(),
+                nullptr, 0);
+          else if (prec == VTM_PREC_FP32)
+            batch_sweep_kernel<float, float, float><<<nitems, 256, 0, s>>>(
+                P->d_T32.as<float>(), P->tabs.T_off.as<int64_t>(), P->tabs.T_ld.as<int32_t>(),
+                P->tabs.port_off.as<int32_t>(), P->d_item_tile.as<int32_t>(),
+                P->d_item_m0.as<int32_t>(), nitems, P->d_twin.as<int32_t>(), P->d_g.as<double>(),
+                P->d_run.as<uint8_t>(), P->d_bc.as<float>(), P->d_bstate.as<float>(), npt, R, P->W,
+                P->d_bctrl.as<BatchCtrl>(), P->d_bpart.as<double>(), P->d_btol2.as<double>(),
+                nullptr, 0);
+          else
+            batch_sweep_kernel<double, double, double><<<nitems, 256, 0, s>>>(
+                P->d_T64.as<double>(), P->tabs.T_off.as<int64_t>(), P->tabs.T_ld.as<int32_t>(),
+                P->tabs.port_off.as<int32_t>(), P->d_item_tile.as<int32_t>(),
+                P->d_item_m0.as<int32_t>(), nitems, P->d_twin.as<int32_t>(), P->d_g.as<double>(),
+                P->d_run.as<uint8_t>(), P->d_bc.as<double>(), P->d_bstate.as<double>(), npt, R,
+                P->W, P->d_bctrl.as<BatchCtrl>(), P->d_bpart.as<double>(), P->d_btol2.as<double>(),
+                nullptr, 0);
+        }
+        VTM_CUDA_TRY(cudaGetLastError());
+        launched += m;
+        VTM_CUDA_TRY(cudaEventRecord(P->evs1, s));
+        VTM_CUDA_TRY(cudaMemcpyAsync(&hc, P->d_bctrl.p, sizeof(hc), cudaMemcpyDeviceToHost, s));
+        VTM_CUDA_TRY(cudaStreamSynchronize(s));
+        float bms = 0.f;
+        VTM_CUDA_TRY(cudaEventElapsedTime(&bms, P->evs0, P->evs1));
+        P->sweep_ms += bms;
+        P->sweep_launch_count += m;
+        P->launch_count += m;
+        if (hc.flag || launched > sweeps_left) break;
+      }
+      flag = hc.flag;
+      kc = (flag == 1 || flag == 4) ? hc.conv_sweep : std::min(hc.k - 1, sweeps_left);
+      if (outer == 0 && flag == 1) info->first_sweep_converged = kc;
+      info->sweeps += kc;
+      sweeps_left -= kc;
+      batch_gather_kernel<double><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, V, n, R);
+      P->launch_count += 2;
+      const int slot = kc & 1;
+      if (lowp)
+        batch_inject_kernel<double, float><<<g2, 256, 0, s>>>(
+            P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(), P->d_beta.as<double>(),
+            P->d_bstate.as<float>() + (size_t)slot * npt * 2 * R, V, npt, R);
+      else
+        batch_inject_kernel<double, double><<<g2, 256, 0, s>>>(
+            P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(), P->d_beta.as<double>(),
+            P->d_bstate.as<double>() + (size_t)slot * npt * 2 * R, V, npt, R);
+      VTM_TRY(batch_band_solve<double>(P, V, R, P->d_Lc.as<double>(), P->d_Uc.as<double>()));
+    } else {
+      info->sweeps += 1;
+      if (outer == 0) info->first_sweep_converged = 1;
+    }
+    batch_scatter_kernel<double><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), V, xacc, n, R, outer > 0);
+    P->launch_count++;
+    VTM_CUDA_TRY(cudaGetLastError());
+    info->outer_steps = outer + 1;
+    bool all_ok = true, bad = false;
+    double worst = 0.0;
+    for (int c = 0; c < R; ++c) {
+      double rr, bb;
+      VTM_TRY(residual_pair(P, xacc + (size_t)c * n, d_b + (size_t)c * n, r + (size_t)c * n, &rr, &bb));
+      rnorm[c] = std::sqrt(rr);
+      rel[c] = bnorm[c] > 0 ? rnorm[c] / bnorm[c] : rnorm[c];
+      worst = std::max(worst, rel[c]);
+      if (!std::isfinite(rr)) bad = true;
+      if (rnorm[c] > tol * bnorm[c]) all_ok = false;
+    }
+    info->relres = worst;
+    if (flag == 3 || bad) {
+      result = VTM_EDIVERGED;
+      break;
+    }
+    if (all_ok) {
+      result = VTM_OK;
+      break;
+    }
+    if (flag == 2 || sweeps_left <= 0) {
+      result = VTM_ENOCONV;
+      break;
+    }
+  }
+  VTM_CUDA_TRY(cudaMemcpyAsync(d_x, xacc, (size_t)n * R * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  VTM_CUDA_TRY(cudaStreamSynchronize(s));
+  if (result == VTM_ENOCONV) set_detail("vtm_solve (batched): tolerance not met");
+  if (result == VTM_EDIVERGED) set_detail("vtm_solve (batched): the iteration diverged");
+  return result;
+}
+
+}  // namespace vtm

@@ -605,7 +605,8 @@ std::vector<DevBuf*> vtm_plan_s::all_bufs() {
           &d_err, &d_red, &d_in_off, &d_out_off, &d_in_src, &d_in_kind, &d_in_twin,
           &d_in_own_out, &d_in_loc, &d_res_perm, &d_res_run, &d_out_loc, &d_in_coef,
           &d_in_sigma, &d_out_scale, &d_out_diag, &d_E_off, &d_E_ld, &d_E, &d_cg, &d_gin,
-          &d_gout, &d_in_tile};
+          &d_gout, &d_in_tile, &d_item_tile, &d_item_m0, &d_bV, &d_bstate, &d_bc, &d_bpart,
+          &d_btol2, &d_bctrl};
 }
 
 static void fill_default_opts(vtm_opts* o) {

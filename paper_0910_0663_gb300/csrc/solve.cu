@@ -408,18 +408,18 @@ __global__ void __launch_bounds__(256) sweep_staged_kernel(
       rs[s] = rc;
     }
     __syncthreads();
-    double sq = 0.0;
+    AT sq = 0;
     if (k > 1) {
       for (int s = tid; s < p; s += blockDim.x) {
         const int nr = run[p0 + s];
         if (nr) {
-          double r = 0.0;
-          for (int q = 0; q < nr; ++q) r += (double)rs[s + q];
+          AT r = 0;
+          for (int q = 0; q < nr; ++q) r += rs[s + q];
           sq += r * r;
         }
       }
     }
-    const double tile_sq = block_sum_value(sq);
+    const double tile_sq = block_sum_value((double)sq);
     if (tid == 0) partials[tile] = tile_sq;
     // apply the reflection matrix from the staged chunks
     const int nv = (p + VEC - 1) / VEC;
@@ -539,6 +539,195 @@ __global__ void __launch_bounds__(256) sweep_staged_kernel(
 }
 
 // ---------------------------------------------------------------------------
+// the sweep with 16-byte vector loads straight from HBM
+// ---------------------------------------------------------------------------
+//
+// One CTA per tile; thread (g, l) owns VEC consecutive outputs of vector
+// column l and loads its rows t = g (mod G) of T_P^T with 16-byte
+// non-allocating loads, all issued before the first FMA of a batch, so each
+// thread keeps kBatch loads in flight and the short tiles of a power grid
+// need no shared-memory staging.
+
+template <class TT, int VEC> struct VecLoadG;
+template <> struct VecLoadG<double, 2> {
+  using raw = double2;
+  __device__ static raw load(const double* p) { return __ldcs(reinterpret_cast<const double2*>(p)); }
+  __device__ static void unpack(const raw& v, double (&o)[2]) { o[0] = v.x; o[1] = v.y; }
+};
+template <> struct VecLoadG<float, 4> {
+  using raw = float4;
+  __device__ static raw load(const float* p) { return __ldcs(reinterpret_cast<const float4*>(p)); }
+  __device__ static void unpack(const raw& v, float (&o)[4]) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
+};
+template <> struct VecLoadG<__nv_bfloat16, 8> {
+  using raw = uint4;
+  __device__ static raw load(const __nv_bfloat16* p) { return __ldcs(reinterpret_cast<const uint4*>(p)); }
+  __device__ static void unpack(const raw& v, float (&o)[8]) {
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float2 f = __bfloat1622float2(h[i]);
+      o[2 * i] = f.x;
+      o[2 * i + 1] = f.y;
+    }
+  }
+};
+
+template <class TT, class WT, int VEC>
+__global__ void __launch_bounds__(256) sweep_vec_kernel(
+    const TT* __restrict__ T, const int64_t* __restrict__ T_off, const int32_t* __restrict__ T_ld,
+    const int32_t* __restrict__ port_off, const int32_t* __restrict__ order,
+    const int32_t* __restrict__ twin, const double* __restrict__ g,
+    const uint8_t* __restrict__ run, const WT* __restrict__ c, WT* __restrict__ state,
+    int64_t nports, double W, SweepCtrl* __restrict__ ctrl, double* __restrict__ partials,
+    double* __restrict__ hist, int hist_len, int nparts, int ld_max) {
+  using AT = WT;
+  using LD = VecLoadG<TT, VEC>;
+  constexpr int kBatch = 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_k, s_flag;
+  __shared__ bool s_last;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    s_k = *((volatile int*)&ctrl->k);
+    s_flag = *((volatile int*)&ctrl->flag);
+  }
+  __syncthreads();
+  if (s_flag) return;
+  const int k = s_k;
+  const int tile = order[blockIdx.x];
+  const int p0 = port_off[tile];
+  const int p = port_off[tile + 1] - p0;
+  const int ld = T_ld[tile];
+  const TT* Tb = T + T_off[tile];
+  WT* w_in = reinterpret_cast<WT*>(smem_raw);
+  AT* rs = w_in + ld_max;
+  AT* red = rs + ld_max;
+  const int nv = (p + VEC - 1) / VEC;
+  const int L = max(1, min(nv, (int)blockDim.x));
+  const int G = blockDim.x / L;
+  const int gi = tid / L, li = tid % L;
+  // first batch of T loads goes out before the gather (it needs no waves)
+  typename LD::raw buf[kBatch];
+  const bool active = gi < G && li < nv;
+#pragma unroll
+  for (int b = 0; b < kBatch; ++b) {
+    const int t = gi + b * G;
+    if (active && t < p) buf[b] = LD::load(Tb + (size_t)t * ld + li * VEC);
+  }
+  const WT* prev = state + (size_t)((k - 1) & 1) * nports * 2;
+  WT* cur = state + (size_t)(k & 1) * nports * 2;
+  const AT hW = (AT)W, inv2W = (AT)(0.5 / W);
+  for (int s = tid; s < p; s += blockDim.x) {
+    const int gs = p0 + s;
+    AT wi = 0, rc = 0;
+    if (k > 1) {
+      const int tw = twin[gs];
+      const AT wi_t = (AT)prev[2 * tw], wo_t = (AT)prev[2 * tw + 1];
+      const AT wi_s = (AT)prev[2 * gs], wo_s = (AT)prev[2 * gs + 1];
+      wi = wo_t;
+      const AT gg = (AT)g[gs];
+      const AT us = (wi_s + wo_s) * inv2W, ut = (wi_t + wo_t) * inv2W;
+      rc = (AT)0.5 * ((hW - 2 * gg) * us + (hW + 2 * gg) * ut - wi_s - wi_t);
+    }
+    w_in[s] = (WT)wi;
+    rs[s] = rc;
+  }
+  __syncthreads();
+  // node residuals in the wave precision (GB300's FP64 pipe is narrow)
+  AT sq = 0;
+  if (k > 1) {
+    for (int s = tid; s < p; s += blockDim.x) {
+      const int nr = run[p0 + s];
+      if (nr) {
+        AT r = 0;
+        for (int q = 0; q < nr; ++q) r += rs[s + q];
+        sq += r * r;
+      }
+    }
+  }
+  const double tile_sq = block_sum_value((double)sq);
+  AT acc[VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) acc[e] = 0;
+  if (active) {
+    for (int t0 = 0; t0 < p; t0 += kBatch * G) {
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b) {
+        const int t = gi + t0 + b * G;
+        if (t < p) {
+          AT val[VEC];
+          LD::unpack(buf[b], val);
+          const AT wt = (AT)w_in[t];
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) acc[e] += val[e] * wt;
+          const int tn = t + kBatch * G;
+          if (tn < p) buf[b] = LD::load(Tb + (size_t)tn * ld + li * VEC);
+        }
+      }
+    }
+  }
+  if (G > 1) {
+    const int cols = L * VEC;
+    if (active)
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) red[gi * cols + li * VEC + e] = acc[e];
+    __syncthreads();
+    for (int s = tid; s < p; s += blockDim.x) {
+      AT a = (AT)c[p0 + s];
+      for (int gg = 0; gg < G; ++gg) a += red[gg * cols + s];
+      cur[2 * (p0 + s)] = w_in[s];
+      cur[2 * (p0 + s) + 1] = (WT)a;
+    }
+  } else if (active) {
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+      const int s = li * VEC + e;
+      if (s < p) {
+        cur[2 * (p0 + s)] = w_in[s];
+        cur[2 * (p0 + s) + 1] = (WT)(acc[e] + (AT)c[p0 + s]);
+      }
+    }
+  }
+  if (tid == 0) {
+    partials[tile] = tile_sq;
+    __threadfence();
+    s_last = atomicAdd(&ctrl->counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const double tot = block_sum_fixed(partials, nparts);
+  if (tid == 0) {
+    int flag = 0;
+    if (k > 1) {
+      const int ks = k - 1;
+      if (hist && ks <= hist_len) hist[ks - 1] = sqrt(tot / ctrl->bnorm2);
+      if (ks == 1) ctrl->first_res2 = tot;
+      ctrl->last_res2 = tot;
+      if (ks == 1 || tot < 0.81 * ctrl->best_res2) {
+        ctrl->best_res2 = tot;
+        ctrl->best_k = ks;
+      }
+      if (!isfinite(tot) || (ks > 1 && tot > 1e12 * ctrl->first_res2 && ctrl->first_res2 > 0)) {
+        flag = 3;
+      } else if (tot <= ctrl->tol2) {
+        flag = 1;
+        ctrl->conv_sweep = ks;
+      } else if (ctrl->stall > 0 && ks - ctrl->best_k >= ctrl->stall) {
+        flag = 4;
+        ctrl->conv_sweep = ks;
+      }
+    }
+    if (!flag && k >= ctrl->k_max) flag = 2;
+    ctrl->counter = 0u;
+    ctrl->k = k + 1;
+    __threadfence();
+    ctrl->flag = flag;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
 
@@ -563,6 +752,61 @@ static void launch_sweep(vtm_plan_s* P, const TT* T, const WT* c, WT* state, int
       P->d_run.as<uint8_t>(), c, state, (int64_t)P->port_node.size(), P->W,
       P->d_ctrl.as<SweepCtrl>(), P->d_partials.as<double>(), hist, hist_len, P->nparts);
 }
+
+// Scoped access-policy window on the plan's stream over the FP32/BF16
+// reflection matrices: a persisting L2 carve-out of up to the device's
+// maximum is requested for this context and released (with the stream
+// attribute and the previous limit) when the sweeps end.
+struct L2Window {
+  cudaStream_t s = nullptr;
+  size_t old_limit = 0;
+  bool active = false;
+  L2Window(vtm_plan_s* P, int prec) {
+    if (prec == VTM_PREC_FP64 || P->opts.l2_persist == 1 || !P->stream) return;
+    const void* base = prec == VTM_PREC_FP32 ? P->d_T32.p : P->d_T16.p;
+    const size_t bytes = prec == VTM_PREC_FP32 ? P->d_T32.bytes : P->d_T16.bytes;
+    int maxp = 0, maxw = 0;
+    if (cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, P->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, P->device) != cudaSuccess ||
+        maxp <= 0 || maxw <= 0 || !base) {
+      cudaGetLastError();
+      return;
+    }
+    if (cudaDeviceGetLimit(&old_limit, cudaLimitPersistingL2CacheSize) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    const size_t carve = std::min<size_t>((size_t)maxp, bytes);
+    const size_t win = std::min<size_t>((size_t)maxw, bytes);
+    if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, carve) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    cudaStreamAttrValue a{};
+    a.accessPolicyWindow.base_ptr = const_cast<void*>(base);
+    a.accessPolicyWindow.num_bytes = win;
+    a.accessPolicyWindow.hitRatio = (float)std::min(1.0, (double)carve / (double)win);
+    a.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    a.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    if (cudaStreamSetAttribute(P->stream, cudaStreamAttributeAccessPolicyWindow, &a) != cudaSuccess) {
+      cudaGetLastError();
+      cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, old_limit);
+      return;
+    }
+    s = P->stream;
+    active = true;
+  }
+  ~L2Window() {
+    if (!active) return;
+    cudaStreamAttrValue a{};
+    a.accessPolicyWindow.num_bytes = 0;
+    cudaStreamSetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &a);
+    cudaStreamSynchronize(s);
+    cudaCtxResetPersistingL2Cache();
+    cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, old_limit);
+    cudaGetLastError();
+  }
+};
 
 // Run sweeps from a zero state until the interface residual is below
 // target2 (absolute, squared) or the sweep budget is used.  Returns the
@@ -604,8 +848,13 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   const int nv_max = (P->max_ports + vec - 1) / vec;
   // auto: the FP64 sweep is bound by GB300's FP64 pipe, where the direct-load
   // kernel does best; FP32/BF16 stream their matrices through the bulk-copy ring
-  const int choice = P->opts.sweep_kernel ? P->opts.sweep_kernel : (prec == VTM_PREC_FP64 ? 1 : 2);
+  const int choice = P->opts.sweep_kernel
+                         ? P->opts.sweep_kernel
+                         : (prec == VTM_PREC_FP64 ? 1 : (nv_max <= 256 ? 3 : 2));
   const bool staged = choice == 2 && nv_max <= 4 * 256 && st_smem <= 200 * 1024;
+  // vector-load kernel: every thread owns one vector column (nv <= 256)
+  const bool vecload = choice == 3 && nv_max <= 256;
+  const size_t vec_smem = 2 * (size_t)ld_max * wsz + 256 * (size_t)vec * wsz + 16;
   if (staged) {
     if (prec == VTM_PREC_FP64)
       VTM_CUDA_TRY(cudaFuncSetAttribute(sweep_staged_kernel<double, double, 2, 4>,
@@ -634,11 +883,34 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
         P->d_run.as<uint8_t>(), c, state, npt_, P->W, P->d_ctrl.as<SweepCtrl>(),
         P->d_partials.as<double>(), hist, hist_len, P->nparts, ch, ld_max);
   };
+  // keep as much of the low-precision reflection matrices in L2 as the
+  // persisting carve-out allows (restored after the sweeps)
+  L2Window l2win(P, prec);
   int launched = 0;
   while (true) {
     const int m = std::min(P->opts.check_every, budget + 1 - launched);
     VTM_CUDA_TRY(cudaEventRecord(P->evs0, s));
     for (int i = 0; i < m; ++i) {
+      if (vecload) {
+        auto launch_vec = [&](auto* kern, const auto* T, const auto* c, auto* state) {
+          kern<<<P->nparts, 256, vec_smem, s>>>(
+              T, P->tabs.T_off.as<int64_t>(), P->tabs.T_ld.as<int32_t>(),
+              P->tabs.port_off.as<int32_t>(), P->tabs.order.as<int32_t>(), P->d_twin.as<int32_t>(),
+              P->d_g.as<double>(), P->d_run.as<uint8_t>(), c, state, npt_, P->W,
+              P->d_ctrl.as<SweepCtrl>(), P->d_partials.as<double>(), hist, hist_len, P->nparts,
+              ld_max);
+        };
+        if (prec == VTM_PREC_FP64)
+          launch_vec(sweep_vec_kernel<double, double, 2>, P->d_T64.as<double>(), P->d_c64.as<double>(),
+                     P->d_state64.as<double>());
+        else if (prec == VTM_PREC_FP32)
+          launch_vec(sweep_vec_kernel<float, float, 4>, P->d_T32.as<float>(), P->d_c32.as<float>(),
+                     P->d_state32.as<float>());
+        else
+          launch_vec(sweep_vec_kernel<__nv_bfloat16, float, 8>, P->d_T16.as<__nv_bfloat16>(),
+                     P->d_c32.as<float>(), P->d_state32.as<float>());
+        continue;
+      }
       if (staged) {
         if (prec == VTM_PREC_FP64)
           launch_staged(sweep_staged_kernel<double, double, 2, 4>, P->d_T64.as<double>(),
@@ -684,8 +956,15 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   return VTM_OK;
 }
 
+vtm_status residual_pair(vtm_plan_s* P, const double* x, const double* b, double* r, double* rr,
+                         double* bb);
 static vtm_status norms(vtm_plan_s* P, const double* x, const double* b, double* r, double* rr,
                         double* bb) {
+  return residual_pair(P, x, b, r, rr, bb);
+}
+
+vtm_status residual_pair(vtm_plan_s* P, const double* x, const double* b, double* r, double* rr,
+                         double* bb) {
   cudaStream_t s = P->stream;
   const int grid = grid_for(P->n);
   double* out = P->d_red.as<double>() + 2;
@@ -835,6 +1114,25 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
 
 vtm_status solve_columns(vtm_plan_s* P, const double* d_b, double* d_x, int64_t nrhs, double tol,
                          vtm_info* info) {
+  // several right-hand sides: one batched iteration (up to 64 per pass)
+  const bool batch = P->opts.batch != 1 && nrhs >= 2 && !P->general && !P->port_node.empty();
+  if (batch) {
+    vtm_status worst = VTM_OK;
+    vtm_info agg{};
+    for (int64_t c0 = 0; c0 < nrhs; c0 += 64) {
+      const int R = (int)std::min<int64_t>(64, nrhs - c0);
+      vtm_info one{};
+      vtm_status st = solve_batched(P, d_b + c0 * P->n, d_x + c0 * P->n, R, tol, &one);
+      if (st != VTM_OK && st != VTM_ENOCONV && st != VTM_EDIVERGED) return st;
+      if (st != VTM_OK && worst == VTM_OK) worst = st;
+      agg.sweeps = std::max(agg.sweeps, one.sweeps);
+      agg.outer_steps = std::max(agg.outer_steps, one.outer_steps);
+      agg.relres = std::max(agg.relres, one.relres);
+      if (c0 == 0) agg.first_sweep_converged = one.first_sweep_converged;
+    }
+    *info = agg;
+    return worst;
+  }
   vtm_info agg{};
   vtm_status worst = VTM_OK;
   for (int64_t col = 0; col < nrhs; ++col) {

@@ -167,6 +167,10 @@ struct vtm_plan_s {
       d_res_perm, d_res_run, d_out_loc, d_in_coef, d_in_sigma, d_out_scale, d_out_diag, d_E_off,
       d_E_ld, d_E, d_cg, d_gin, d_gout, d_in_tile;
 
+  // batched right-hand sides (batch.cu)
+  std::vector<int32_t> item_tile, item_m0;
+  vtm::DevBuf d_item_tile, d_item_m0, d_bV, d_bstate, d_bc, d_bpart, d_btol2, d_bctrl;
+
   // adjoint of an unsymmetric system
   vtm_plan_s* transposed = nullptr;
 
@@ -206,6 +210,10 @@ vtm_status solve_columns(vtm_plan_s* P, const double* d_b, double* d_x, int64_t 
 vtm_status residual_norms(vtm_plan_s* P, const double* d_x, const double* d_b, int64_t nrhs,
                           double* rel);
 
+vtm_status residual_pair(vtm_plan_s* P, const double* x, const double* b, double* r, double* rr,
+                         double* bb);
+vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, double tol,
+                         vtm_info* info);
 int launch_residual(const int64_t* rowptr, const int32_t* col, const double* val, const double* x,
                     const double* b, int64_t n, double* partials, unsigned* counter, double* out,
                     int max_grid, cudaStream_t s);

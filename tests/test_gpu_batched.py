@@ -1,0 +1,92 @@
+"""Many right-hand sides in one batched VTM iteration (RC thermal grid,
+backward-Euler time-step vectors), against the oracle's multi-RHS VTM.
+
+The batched iteration stops when every column meets the tolerance, exactly
+like the oracle's multi-RHS run, so the sweep counts and the iterates agree.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import vtm_oracle as O
+from paper_0910_0663_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vtm():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_0910_0663_gb300 import build
+    build.build()
+    from paper_0910_0663_gb300 import vtm as V
+    return V
+
+
+def _thermal_small(nrhs, seed=1):
+    return wl.thermal3d(8, 24, 24, 12, nrhs=nrhs, seed=seed, min_box=100, max_box=1200)
+
+
+def test_batched_fp64_matches_oracle(vtm):
+    w = _thermal_small(8)
+    A = w.csr()
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc)
+    x, info = plan.solve(torch.from_numpy(w.b).cuda(), tol=1e-10)
+    ref = O.vtm_midpoint(A, w.partition, w.nparts, w.b, W=1 / w.Zc, tol=1e-10)
+    assert ref.converged
+    xs = x.cpu().numpy()
+    if info["sweeps"] == ref.sweeps:
+        assert np.abs(xs - ref.x).max() <= 1e-11 * np.abs(ref.x).max()
+    else:
+        assert abs(info["sweeps"] - ref.sweeps) == 1
+    assert O.residual_norms(A, xs, w.b).max() <= 1e-10
+
+
+def test_batched_equals_column_by_column_at_equal_sweeps(vtm):
+    # with the batched count forced on every column, the same iterate results
+    w = _thermal_small(4, seed=2)
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc)
+    xb, info = plan.solve(torch.from_numpy(w.b).cuda(), tol=1e-10)
+    K = info["sweeps"]
+    plan1 = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc, batch=1,
+                     max_sweeps=K)
+    for r in range(4):
+        xr, inf = plan1.solve(torch.from_numpy(w.b[r]).cuda(), tol=1e-300, check=False)
+        assert inf["sweeps"] == K
+        assert torch.allclose(xr, xb[r], rtol=1e-12, atol=1e-14 * float(xb[r].abs().max()))
+
+
+@pytest.mark.parametrize("precision,nrhs", [("bf16", 16), ("fp32", 5), ("bf16", 6)])
+def test_batched_low_precision_reaches_tolerance(vtm, precision, nrhs):
+    w = _thermal_small(nrhs, seed=3)
+    A = w.csr()
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc,
+                    precision=precision)
+    x, info = plan.solve(torch.from_numpy(w.b).cuda(), tol=1e-10)
+    rel = O.residual_norms(A, x.cpu().numpy(), w.b)
+    assert rel.max() <= 1e-10
+    assert info["outer_steps"] >= 2
+
+
+def test_thermal_full_size_64_rhs_bf16(vtm):
+    # the 128x128x32 grid in 400 boxes with 64 right-hand sides, as timed
+    w = wl.c3_thermal(nrhs=64)
+    A = w.csr()
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc, precision="bf16")
+    st = plan.stats()
+    assert st["nparts"] == 400
+    x, info = plan.solve(torch.from_numpy(w.b).cuda(), tol=1e-10)
+    rel = O.residual_norms(A, x.cpu().numpy(), w.b)
+    assert rel.max() <= 1e-10
+    # sampled reflection matrices of three boxes against (W - S)(W + S)^-1
+    tear = O.tear_midpoint(A, w.partition, w.nparts)
+    node, remote, part, _ = plan.ports()
+    for P in (0, 137, 399):
+        T_lib = plan.reflection(P)
+        _, T_ref = O.reflection_ops(A, tear, P, 1.0 / w.Zc)
+        sel = np.flatnonzero(part == P)
+        keys = {k: i for i, k in enumerate(zip(tear.port_node[tear.tile_ports[P]].tolist(),
+                                                 tear.port_remote[tear.tile_ports[P]].tolist()))}
+        perm = np.array([keys[k] for k in zip(node[sel].tolist(), remote[sel].tolist())])
+        assert np.abs(T_lib - T_ref[np.ix_(perm, perm)]).max() < 1e-10
