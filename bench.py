@@ -50,8 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--l2-persist", type=int, default=0, choices=[0, 1],
                     help="0: reflection matrices persisting in L2 during low-precision sweeps, 1: off")
-    ap.add_argument("--sweep-kernel", type=int, default=0, choices=[0, 1, 2, 3],
-                    help="0: automatic, 1: direct-load, 2: bulk-copy staged, 3: vector-load")
+    ap.add_argument("--sweep-kernel", type=int, default=0, choices=[0, 1, 2, 3, 4],
+                    help="0: autotuned, 1: direct-load, 2: bulk-copy staged, 3/4: vector-load (256/128 threads)")
     return ap.parse_args()
 
 

@@ -89,10 +89,13 @@ typedef struct {
                         persisting in L2 (access-policy window on the plan's stream; the
                         context's persisting carve-out is set and restored around the
                         sweeps); 1: off.  Needs a non-default stream. */
-  int sweep_kernel;  /* 0 (default): automatic (FP64: direct-load; FP32/BF16: vector-load
-                        when every tile has p <= 256 VEC ports, else bulk-copy staged);
-                        1: direct-load kernel; 2: bulk-copy staged kernel;
-                        3: 16-byte vector-load kernel */
+  int sweep_kernel;  /* 0 (default): autotuned -- the first solve of each precision times
+                        every sweep kernel that fits the plan's sub-circuits and keeps the
+                        fastest; 1: direct-load kernel; 2: bulk-copy staged kernel;
+                        3: 16-byte vector-load kernel, 256 threads per tile;
+                        4: the same with 128 threads (p <= 128 VEC) */
+  int graphs;        /* 0 (default): replay batches of check_every sweep launches from a
+                        CUDA graph when the plan has its own stream; 1: plain launches */
   double* history;   /* optional host array: relative (interface) residual after each
                         sweep k=1..history_len of the first column; NULL = not recorded */
   int history_len;
@@ -123,6 +126,7 @@ typedef struct {
   int32_t symmetric;     /* 1: A symmetric -> Cholesky; 0: LU without pivoting */
   int64_t t_bytes;       /* bytes of the stored reflection matrices (all precisions kept) */
   int64_t factor_bytes;  /* bytes of the stored local factors */
+  int32_t sweep_kernel;  /* sweep kernel in use for the plan's precision (see vtm_opts) */
 } vtm_plan_stats;
 
 /* vtm_plan -- wire tearing (Sec. V) and the port table.

@@ -14,8 +14,8 @@
 
 namespace vtm {
 
-__device__ __forceinline__ void warp_scale_pass(double* v, int n, const double* __restrict__ col0,
-                                                int B) {
+template <class FT>
+__device__ __forceinline__ void warp_scale_pass(FT* v, int n, const FT* __restrict__ col0, int B) {
   const int lane = threadIdx.x & 31;
   __syncwarp();
   for (int j = lane; j < n; j += 32) v[j] *= __ldg(col0 + (size_t)j * B);
@@ -23,22 +23,22 @@ __device__ __forceinline__ void warp_scale_pass(double* v, int n, const double* 
 }
 
 // Plain column sweeps (any bandwidth).
-__device__ __forceinline__ void warp_band_solve_plain(double* v, int n, int bw,
-                                                      const double* __restrict__ lc,
-                                                      const double* __restrict__ uc, int start) {
+template <class FT>
+__device__ __forceinline__ void warp_band_solve_plain(FT* v, int n, int bw, const FT* __restrict__ lc,
+                                                      const FT* __restrict__ uc, int start) {
   const int lane = threadIdx.x & 31;
   const int B = bw + 1;
   for (int j = start; j < n; ++j) {
-    const double* col = lc + (size_t)j * B;
-    const double u = v[j];
+    const FT* col = lc + (size_t)j * B;
+    const FT u = v[j];
     const int m = min(bw, n - 1 - j);
     for (int a = lane + 1; a <= m; a += 32) v[j + a] -= __ldg(col + a) * u;
     __syncwarp();
   }
   warp_scale_pass(v, n, lc, B);
   for (int j = n - 1; j >= 0; --j) {
-    const double* col = uc + (size_t)j * B;
-    const double u = v[j];
+    const FT* col = uc + (size_t)j * B;
+    const FT u = v[j];
     const int m = min(bw, j);
     for (int b = lane + 1; b <= m; b += 32) v[j - b] -= __ldg(col + b) * u;
     __syncwarp();
@@ -48,20 +48,19 @@ __device__ __forceinline__ void warp_band_solve_plain(double* v, int n, int bw,
 
 // The same sweeps with the multipliers of column j + D loaded while column j
 // is applied (lane owns entries a = lane + 1 + 32 q, q < Q; needs bw <= 32 Q).
-template <int Q, int D>
-__device__ __forceinline__ void warp_band_solve_pf(double* v, int n, int bw,
-                                                   const double* __restrict__ lc,
-                                                   const double* __restrict__ uc, int start) {
+template <int Q, int D, class FT>
+__device__ __forceinline__ void warp_band_solve_pf(FT* v, int n, int bw, const FT* __restrict__ lc,
+                                                   const FT* __restrict__ uc, int start) {
   const int lane = threadIdx.x & 31;
   const int B = bw + 1;
-  double buf[D][Q];
+  FT buf[D][Q];
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     const int j = start + d;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const int a = lane + 1 + 32 * q;
-      buf[d][q] = (j < n && a <= min(bw, n - 1 - j)) ? __ldg(lc + (size_t)j * B + a) : 0.0;
+      buf[d][q] = (j < n && a <= min(bw, n - 1 - j)) ? __ldg(lc + (size_t)j * B + a) : FT(0);
     }
   }
   for (int j0 = start; j0 < n; j0 += D) {
@@ -69,7 +68,7 @@ __device__ __forceinline__ void warp_band_solve_pf(double* v, int n, int bw,
     for (int d = 0; d < D; ++d) {
       const int j = j0 + d;
       if (j < n) {
-        const double u = v[j];
+        const FT u = v[j];
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
           const int a = lane + 1 + 32 * q;
@@ -80,7 +79,7 @@ __device__ __forceinline__ void warp_band_solve_pf(double* v, int n, int bw,
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
           const int a = lane + 1 + 32 * q;
-          buf[d][q] = (jn < n && a <= min(bw, n - 1 - jn)) ? __ldg(lc + (size_t)jn * B + a) : 0.0;
+          buf[d][q] = (jn < n && a <= min(bw, n - 1 - jn)) ? __ldg(lc + (size_t)jn * B + a) : FT(0);
         }
       }
     }
@@ -92,7 +91,7 @@ __device__ __forceinline__ void warp_band_solve_pf(double* v, int n, int bw,
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const int b = lane + 1 + 32 * q;
-      buf[d][q] = (j >= 0 && b <= min(bw, j)) ? __ldg(uc + (size_t)j * B + b) : 0.0;
+      buf[d][q] = (j >= 0 && b <= min(bw, j)) ? __ldg(uc + (size_t)j * B + b) : FT(0);
     }
   }
   for (int j0 = n - 1; j0 >= 0; j0 -= D) {
@@ -100,7 +99,7 @@ __device__ __forceinline__ void warp_band_solve_pf(double* v, int n, int bw,
     for (int d = 0; d < D; ++d) {
       const int j = j0 - d;
       if (j >= 0) {
-        const double u = v[j];
+        const FT u = v[j];
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
           const int b = lane + 1 + 32 * q;
@@ -111,7 +110,7 @@ __device__ __forceinline__ void warp_band_solve_pf(double* v, int n, int bw,
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
           const int b = lane + 1 + 32 * q;
-          buf[d][q] = (jn >= 0 && b <= min(bw, jn)) ? __ldg(uc + (size_t)jn * B + b) : 0.0;
+          buf[d][q] = (jn >= 0 && b <= min(bw, jn)) ? __ldg(uc + (size_t)jn * B + b) : FT(0);
         }
       }
     }
@@ -120,9 +119,9 @@ __device__ __forceinline__ void warp_band_solve_pf(double* v, int n, int bw,
 }
 
 // K_P^-1 v in place (v in shared or global memory, one warp).
-__device__ __forceinline__ void warp_band_solve_any(double* v, int n, int bw,
-                                                    const double* __restrict__ lc,
-                                                    const double* __restrict__ uc, int start) {
+template <class FT>
+__device__ __forceinline__ void warp_band_solve_any(FT* v, int n, int bw, const FT* __restrict__ lc,
+                                                    const FT* __restrict__ uc, int start) {
   if (bw <= 32) warp_band_solve_pf<1, 16>(v, n, bw, lc, uc, start);
   else if (bw <= 64) warp_band_solve_pf<2, 12>(v, n, bw, lc, uc, start);
   else if (bw <= 128) warp_band_solve_pf<4, 8>(v, n, bw, lc, uc, start);

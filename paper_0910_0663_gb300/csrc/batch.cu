@@ -72,7 +72,7 @@ __global__ void batch_scatter_kernel(const int32_t* __restrict__ perm, const FT*
 // ---------------------------------------------------------------------------
 //
 // V[pos][R] in global memory, the tile's block of RG columns staged in
-// shared memory ([n_P][RG]).  Thread a (1..bw) owns band offset a: at step j
+// shared memory (column-major).  Thread a (1..bw) owns band offset a: at step j
 // it updates row j + a with multiplier Lc[j][a] (forward) or row j - a with
 // Uc[j][a] (backward); one barrier per step.  Each thread prefetches its
 // multiplier D columns ahead.
@@ -84,7 +84,6 @@ __global__ void batch_band_solve_kernel(const int32_t* __restrict__ node_off,
                                         const FT* __restrict__ Lc, const FT* __restrict__ Uc,
                                         FT* __restrict__ V, int R) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  FT* v = reinterpret_cast<FT*>(smem_raw);  // [n][RG]
   const int ngroups = (R + RG - 1) / RG;
   const int t = blockIdx.x / ngroups;
   const int r0 = (blockIdx.x % ngroups) * RG;
@@ -96,9 +95,12 @@ __global__ void batch_band_solve_kernel(const int32_t* __restrict__ node_off,
   const FT* lc = Lc + band_off[t];
   const FT* uc = Uc + band_off[t];
   const int tid = threadIdx.x;
+  // column-major in shared memory, v[c * n + row]: at every step the threads
+  // (band offsets) touch consecutive rows of a column, without bank conflicts
+  FT* v = reinterpret_cast<FT*>(smem_raw);
   for (int i = tid; i < n * RG; i += blockDim.x) {
     const int row = i / RG, c = i % RG;
-    v[i] = c < rg ? V[(int64_t)(base + row) * R + r0 + c] : FT(0);
+    v[c * n + row] = c < rg ? V[(int64_t)(base + row) * R + r0 + c] : FT(0);
   }
   __syncthreads();
   const int a = tid + 1;  // band offset of this thread
@@ -114,10 +116,8 @@ __global__ void batch_band_solve_kernel(const int32_t* __restrict__ node_off,
       if (j < n) {
         if (act && a <= n - 1 - j) {
           const FT m = pf[d];
-          FT* dst = v + (size_t)(j + a) * RG;
-          const FT* src = v + (size_t)j * RG;
 #pragma unroll
-          for (int c = 0; c < RG; ++c) dst[c] -= m * src[c];
+          for (int c = 0; c < RG; ++c) v[c * n + j + a] -= m * v[c * n + j];
         }
         const int jn = j + D;
         pf[d] = (act && jn < n && a <= n - 1 - jn) ? lc[(size_t)jn * B + a] : FT(0);
@@ -125,7 +125,7 @@ __global__ void batch_band_solve_kernel(const int32_t* __restrict__ node_off,
       }
     }
   }
-  for (int i = tid; i < n * RG; i += blockDim.x) v[i] *= lc[(size_t)(i / RG) * B];
+  for (int i = tid; i < n * RG; i += blockDim.x) v[i] *= lc[(size_t)(i % n) * B];
   __syncthreads();
   // backward sweep
 #pragma unroll
@@ -140,10 +140,8 @@ __global__ void batch_band_solve_kernel(const int32_t* __restrict__ node_off,
       if (j >= 0) {
         if (act && a <= j) {
           const FT m = pf[d];
-          FT* dst = v + (size_t)(j - a) * RG;
-          const FT* src = v + (size_t)j * RG;
 #pragma unroll
-          for (int c = 0; c < RG; ++c) dst[c] -= m * src[c];
+          for (int c = 0; c < RG; ++c) v[c * n + j - a] -= m * v[c * n + j];
         }
         const int jn = j - D;
         pf[d] = (act && jn >= 0 && a <= jn) ? uc[(size_t)jn * B + a] : FT(0);
@@ -153,7 +151,7 @@ __global__ void batch_band_solve_kernel(const int32_t* __restrict__ node_off,
   }
   for (int i = tid; i < n * RG; i += blockDim.x) {
     const int row = i / RG, c = i % RG;
-    const FT x = v[i] * uc[(size_t)row * B];
+    const FT x = v[c * n + row] * uc[(size_t)row * B];
     if (c < rg) V[(int64_t)(base + row) * R + r0 + c] = x;
   }
 }
@@ -206,37 +204,46 @@ __device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162flo
 // RHS: the square of each node's residual goes to rsq[run][r] (shared), and
 // red[r] receives the column sums in a fixed order.  State layout:
 // [port][2][R] = (w_in, w_out).
-template <class WT>
+template <class WT, class RT>
 __device__ void batch_residual(const int32_t* __restrict__ twin, const double* __restrict__ g,
                                const uint8_t* __restrict__ run, const WT* __restrict__ prev,
-                               int p0, int m0, int m1, int R, double W, double (*rsq)[64],
+                               int p0, int m0, int m1, int R, double W, RT (*rsq)[64],
                                double* red) {
-  const double inv2W = 0.5 / W;
-  for (int i = threadIdx.x; i < (m1 - m0) * R; i += blockDim.x) {
-    const int sl = i / R;
-    const int r = i % R;
-    const int gs = p0 + m0 + sl;
-    const int nr = run[gs];
-    double rsum = 0.0;
-    for (int q = 0; q < nr; ++q) {
-      const int ps = gs + q;
-      const int tw = twin[ps];
-      const double wi_s = (double)prev[(size_t)ps * 2 * R + r];
-      const double wo_s = (double)prev[(size_t)ps * 2 * R + R + r];
-      const double wi_t = (double)prev[(size_t)tw * 2 * R + r];
-      const double wo_t = (double)prev[(size_t)tw * 2 * R + R + r];
-      const double gg = g[ps];
-      const double us = (wi_s + wo_s) * inv2W, ut = (wi_t + wo_t) * inv2W;
-      rsum += 0.5 * ((W - 2 * gg) * us + (W + 2 * gg) * ut - wi_s - wi_t);
+  // arithmetic in RT: FP32 for the low-precision sweeps (GB300's FP64 pipe is
+  // narrow), FP64 for the FP64 sweep
+  const RT hW = (RT)W, inv2W = (RT)(0.5 / W);
+  for (int r = threadIdx.x; r < R; r += blockDim.x) red[r] = 0.0;
+  // rows in slices of 32 node runs; the column sums add the slices in order
+  for (int h0 = m0; h0 < m1; h0 += 32) {
+    const int h1 = min(m1, h0 + 32);
+    __syncthreads();
+    for (int i = threadIdx.x; i < (h1 - h0) * R; i += blockDim.x) {
+      const int sl = i / R;
+      const int r = i % R;
+      const int gs = p0 + h0 + sl;
+      const int nr = run[gs];
+      RT rsum = 0;
+      for (int q = 0; q < nr; ++q) {
+        const int ps = gs + q;
+        const int tw = twin[ps];
+        const RT wi_s = (RT)prev[(size_t)ps * 2 * R + r];
+        const RT wo_s = (RT)prev[(size_t)ps * 2 * R + R + r];
+        const RT wi_t = (RT)prev[(size_t)tw * 2 * R + r];
+        const RT wo_t = (RT)prev[(size_t)tw * 2 * R + R + r];
+        const RT gg = (RT)g[ps];
+        const RT us = (wi_s + wo_s) * inv2W, ut = (wi_t + wo_t) * inv2W;
+        rsum += (RT)0.5 * ((hW - 2 * gg) * us + (hW + 2 * gg) * ut - wi_s - wi_t);
+      }
+      rsq[sl][r] = rsum * rsum;
     }
-    rsq[sl][r] = rsum * rsum;
+    __syncthreads();
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+      RT a = 0;
+      for (int sl = 0; sl < h1 - h0; ++sl) a += rsq[sl][r];
+      red[r] += (double)a;
+    }
   }
   __syncthreads();
-  for (int r = threadIdx.x; r < R; r += blockDim.x) {
-    double a = 0.0;
-    for (int sl = 0; sl < m1 - m0; ++sl) a += rsq[sl][r];
-    red[r] = a;
-  }
 }
 
 // Last-CTA reduction over work items per RHS and the convergence decision.
@@ -302,7 +309,7 @@ __global__ void __launch_bounds__(256) batch_sweep_kernel(
   __shared__ AT Ts[kKC][kMB];
   __shared__ AT Ws[kKC][64];
   __shared__ double red[64];
-  __shared__ double rsq[kMB][64];
+  __shared__ AT rsq[32][64];
   __shared__ int s_k, s_flag;
   __shared__ bool s_last;
   const int tid = threadIdx.x;
@@ -324,7 +331,7 @@ __global__ void __launch_bounds__(256) batch_sweep_kernel(
   const TT* Tb = T + T_off[tile];
   const WT* prev = state + (size_t)((k - 1) & 1) * nports * 2 * R;
   WT* cur = state + (size_t)(k & 1) * nports * 2 * R;
-  if (k > 1) batch_residual<WT>(twin, g, run, prev, p0, m0, m1, R, W, rsq, red);
+  if (k > 1) batch_residual<WT, AT>(twin, g, run, prev, p0, m0, m1, R, W, rsq, red);
   const int tx = tid % 16, ty = tid / 16;
   AT acc[4][4];
 #pragma unroll
@@ -426,10 +433,11 @@ __global__ void __launch_bounds__(128) batch_sweep_mma_kernel(
     const uint8_t* __restrict__ run, const float* __restrict__ c, float* __restrict__ state,
     int64_t nports, int R, double W, BatchCtrl* __restrict__ ctrl, double* __restrict__ partials,
     const double* __restrict__ tol2, double* __restrict__ hist, int hist_len) {
-  __shared__ __align__(16) __nv_bfloat16 As[kKC][kAPad];  // T^T chunk: [t][s]
-  __shared__ __align__(16) __nv_bfloat16 Bs[kKC][kBPad];  // W_in chunk: [t][r]
+  constexpr int KC = 32;  // inputs per chunk (two k16 steps)
+  __shared__ __align__(16) __nv_bfloat16 As[2][KC][kAPad];  // T^T chunk: [t][s], double-buffered
+  __shared__ __align__(16) __nv_bfloat16 Bs[2][KC][kBPad];  // W_in chunk: [t][r]
   __shared__ double red[64];
-  __shared__ double rsq[kMB][64];
+  __shared__ float rsq[32][64];
   __shared__ int s_k, s_flag;
   __shared__ bool s_last;
   const int tid = threadIdx.x;
@@ -452,56 +460,77 @@ __global__ void __launch_bounds__(128) batch_sweep_mma_kernel(
   const __nv_bfloat16* Tb = T + T_off[tile];
   const float* prev = state + (size_t)((k - 1) & 1) * nports * 2 * R;
   float* cur = state + (size_t)(k & 1) * nports * 2 * R;
-  if (k > 1) batch_residual<float>(twin, g, run, prev, p0, m0, m1, R, W, rsq, red);
   float acc[8][4];
 #pragma unroll
   for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
     for (int e = 0; e < 4; ++e) acc[nt][e] = 0.f;
   const int ntiles = (R + 7) / 8;
-  if (k > 1) {
-    for (int t0 = 0; t0 < p; t0 += kKC) {
-      // A chunk: 16 rows x 64 outputs (8 x 16-byte pieces per row)
-      for (int i = tid; i < kKC * 8; i += blockDim.x) {
-        const int kk = i / 8, piece = i % 8;
-        const int t = t0 + kk, s = m0 + piece * 8;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (t < p && s < m1) v = __ldcs(reinterpret_cast<const uint4*>(Tb + (size_t)t * ld + s));
-        *reinterpret_cast<uint4*>(&As[kk][piece * 8]) = v;
-      }
-      // B chunk: 16 rows x R incident waves, gathered and rounded to BF16
-      for (int i = tid; i < kKC * 16; i += blockDim.x) {
-        const int kk = i / 16, q = i % 16;
-        const int t = t0 + kk, r = q * 4;
-        float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (t < p && r < R)
-          w = *reinterpret_cast<const float4*>(prev + (size_t)twin[p0 + t] * 2 * R + R + r);
-        __nv_bfloat162 lo = __floats2bfloat162_rn(w.x, w.y);
-        __nv_bfloat162 hi = __floats2bfloat162_rn(w.z, w.w);
-        *reinterpret_cast<__nv_bfloat162*>(&Bs[kk][r]) = lo;
-        *reinterpret_cast<__nv_bfloat162*>(&Bs[kk][r + 2]) = hi;
-      }
-      __syncthreads();
-      // A fragment (16 outputs x 16 inputs) of this warp
-      uint32_t a0, a1, a2, a3;
-      {
-        const int mat = lane >> 3, row = lane & 7;
-        const int kk = row + ((mat >> 1) << 3);       // matrices 2,3: inputs 8..15
-        const int mm = warp * 16 + ((mat & 1) << 3);  // matrices 1,3: outputs 8..15
-        ldsm_x4_trans(a0, a1, a2, a3, &As[kk][mm]);
-      }
+  // per thread: 2 16-byte pieces of the T chunk and 4 float4 of the wave chunk
+  uint4 ra[2];
+  float4 rb[4];
+  auto load_chunk = [&](int t0) {
 #pragma unroll
-      for (int np = 0; np < 4; ++np) {  // pairs of 8-wide RHS tiles
-        if (2 * np >= ntiles) break;
-        uint32_t b0, b1, b2, b3;
-        const int mat = lane >> 3, row = lane & 7;
-        const int kk = row + ((mat & 1) << 3);              // matrices 1,3: inputs 8..15
-        const int nn = np * 16 + ((mat >> 1) << 3);         // matrices 2,3: next RHS tile
-        ldsm_x4_trans(b0, b1, b2, b3, &Bs[kk][nn]);
-        mma_bf16(acc[2 * np], a0, a1, a2, a3, b0, b1);
-        mma_bf16(acc[2 * np + 1], a0, a1, a2, a3, b2, b3);
-      }
+    for (int q = 0; q < 2; ++q) {
+      const int i = tid + q * 128;
+      const int kk = i / 8, piece = i % 8;
+      const int t = t0 + kk, s = m0 + piece * 8;
+      ra[q] = (t < p && s < m1) ? __ldcs(reinterpret_cast<const uint4*>(Tb + (size_t)t * ld + s))
+                                : make_uint4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = tid + q * 128;
+      const int kk = i / 16, r = (i % 16) * 4;
+      const int t = t0 + kk;
+      rb[q] = (t < p && r < R)
+                  ? *reinterpret_cast<const float4*>(prev + (size_t)twin[p0 + t] * 2 * R + R + r)
+                  : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  auto store_chunk = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int i = tid + q * 128;
+      *reinterpret_cast<uint4*>(&As[buf][i / 8][(i % 8) * 8]) = ra[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = tid + q * 128;
+      const int kk = i / 16, r = (i % 16) * 4;
+      *reinterpret_cast<__nv_bfloat162*>(&Bs[buf][kk][r]) = __floats2bfloat162_rn(rb[q].x, rb[q].y);
+      *reinterpret_cast<__nv_bfloat162*>(&Bs[buf][kk][r + 2]) = __floats2bfloat162_rn(rb[q].z, rb[q].w);
+    }
+  };
+  if (k > 1) {
+    load_chunk(0);  // in flight during the residual of sweep k-1
+    batch_residual<float, float>(twin, g, run, prev, p0, m0, m1, R, W, rsq, red);
+    int buf = 0;
+    for (int t0 = 0; t0 < p; t0 += KC, buf ^= 1) {
+      store_chunk(buf);
       __syncthreads();
+      if (t0 + KC < p) load_chunk(t0 + KC);  // next chunk streams while this one multiplies
+#pragma unroll
+      for (int ks = 0; ks < KC / 16; ++ks) {
+        uint32_t a0, a1, a2, a3;
+        {
+          const int mat = lane >> 3, row = lane & 7;
+          const int kk = ks * 16 + row + ((mat >> 1) << 3);  // matrices 2,3: inputs 8..15
+          const int mm = warp * 16 + ((mat & 1) << 3);       // matrices 1,3: outputs 8..15
+          ldsm_x4_trans(a0, a1, a2, a3, &As[buf][kk][mm]);
+        }
+#pragma unroll
+        for (int np = 0; np < 4; ++np) {  // pairs of 8-wide RHS tiles
+          if (2 * np >= ntiles) break;
+          uint32_t b0, b1, b2, b3;
+          const int mat = lane >> 3, row = lane & 7;
+          const int kk = ks * 16 + row + ((mat & 1) << 3);  // matrices 1,3: inputs 8..15
+          const int nn = np * 16 + ((mat >> 1) << 3);       // matrices 2,3: next RHS tile
+          ldsm_x4_trans(b0, b1, b2, b3, &Bs[buf][kk][nn]);
+          mma_bf16(acc[2 * np], a0, a1, a2, a3, b0, b1);
+          mma_bf16(acc[2 * np + 1], a0, a1, a2, a3, b2, b3);
+        }
+      }
     }
   }
   // epilogue: fragment element e of tile nt sits at output row
@@ -597,6 +626,11 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
   VTM_TRY(dev_alloc(P->d_xacc, (size_t)n * R * sizeof(double)));
   VTM_TRY(dev_alloc(P->d_r, (size_t)n * R * sizeof(double)));
   double* V = P->d_bV.as<double>();
+  // low precision: both banded solves of each refinement step in FP32 (their
+  // error is removed by the next step like the sweeps' rounding)
+  const bool f32_solves = lowp && P->d_Lc32.p;
+  if (f32_solves) VTM_TRY(dev_alloc(P->d_bV32, (size_t)n * R * sizeof(float)));
+  float* V32 = P->d_bV32.as<float>();
   double* xacc = P->d_xacc.as<double>();
   double* r = P->d_r.as<double>();
   // ||b_r||
@@ -620,12 +654,22 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
   const int g1 = grid_n(n * R), g2 = grid_n(npt * R);
   for (int outer = 0; outer < max_outer; ++outer) {
     const double* rhs = outer == 0 ? d_b : r;
-    batch_gather_kernel<double><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, V, n, R);
-    P->launch_count++;
-    VTM_TRY(batch_band_solve<double>(P, V, R, P->d_Lc.as<double>(), P->d_Uc.as<double>()));
+    if (f32_solves) {
+      batch_gather_kernel<float><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, V32, n, R);
+      P->launch_count++;
+      VTM_TRY(batch_band_solve<float>(P, V32, R, P->d_Lc32.as<float>(), P->d_Uc32.as<float>()));
+    } else {
+      batch_gather_kernel<double><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, V, n, R);
+      P->launch_count++;
+      VTM_TRY(batch_band_solve<double>(P, V, R, P->d_Lc.as<double>(), P->d_Uc.as<double>()));
+    }
     int kc = 0, flag = 1;
     if (npt > 0) {
-      if (lowp)
+      if (f32_solves)
+        batch_const_kernel<float, float><<<g2, 256, 0, s>>>(P->d_port_pos.as<int32_t>(),
+                                                           P->d_beta.as<double>(), V32, P->W,
+                                                           P->d_bc.as<float>(), npt, R);
+      else if (lowp)
         batch_const_kernel<double, float><<<g2, 256, 0, s>>>(P->d_port_pos.as<int32_t>(),
                                                             P->d_beta.as<double>(), V, P->W,
                                                             P->d_bc.as<float>(), npt, R);
@@ -706,23 +750,34 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
       if (outer == 0 && flag == 1) info->first_sweep_converged = kc;
       info->sweeps += kc;
       sweeps_left -= kc;
-      batch_gather_kernel<double><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, V, n, R);
-      P->launch_count += 2;
       const int slot = kc & 1;
-      if (lowp)
-        batch_inject_kernel<double, float><<<g2, 256, 0, s>>>(
+      P->launch_count += 2;
+      if (f32_solves) {
+        batch_gather_kernel<float><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, V32, n, R);
+        batch_inject_kernel<float, float><<<g2, 256, 0, s>>>(
             P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(), P->d_beta.as<double>(),
-            P->d_bstate.as<float>() + (size_t)slot * npt * 2 * R, V, npt, R);
-      else
-        batch_inject_kernel<double, double><<<g2, 256, 0, s>>>(
-            P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(), P->d_beta.as<double>(),
-            P->d_bstate.as<double>() + (size_t)slot * npt * 2 * R, V, npt, R);
-      VTM_TRY(batch_band_solve<double>(P, V, R, P->d_Lc.as<double>(), P->d_Uc.as<double>()));
+            P->d_bstate.as<float>() + (size_t)slot * npt * 2 * R, V32, npt, R);
+        VTM_TRY(batch_band_solve<float>(P, V32, R, P->d_Lc32.as<float>(), P->d_Uc32.as<float>()));
+      } else {
+        batch_gather_kernel<double><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, V, n, R);
+        if (lowp)
+          batch_inject_kernel<double, float><<<g2, 256, 0, s>>>(
+              P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(), P->d_beta.as<double>(),
+              P->d_bstate.as<float>() + (size_t)slot * npt * 2 * R, V, npt, R);
+        else
+          batch_inject_kernel<double, double><<<g2, 256, 0, s>>>(
+              P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(), P->d_beta.as<double>(),
+              P->d_bstate.as<double>() + (size_t)slot * npt * 2 * R, V, npt, R);
+        VTM_TRY(batch_band_solve<double>(P, V, R, P->d_Lc.as<double>(), P->d_Uc.as<double>()));
+      }
     } else {
       info->sweeps += 1;
       if (outer == 0) info->first_sweep_converged = 1;
     }
-    batch_scatter_kernel<double><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), V, xacc, n, R, outer > 0);
+    if (f32_solves && npt > 0)
+      batch_scatter_kernel<float><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), V32, xacc, n, R, outer > 0);
+    else
+      batch_scatter_kernel<double><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), V, xacc, n, R, outer > 0);
     P->launch_count++;
     VTM_CUDA_TRY(cudaGetLastError());
     info->outer_steps = outer + 1;

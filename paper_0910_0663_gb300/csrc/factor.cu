@@ -156,18 +156,20 @@ vtm_status factor_tiles(vtm_plan_s* P) {
 
 // Solve K_P x = v for every tile, in place in the permuted vector v
 // (one warp per (tile, column)); columns are `stride` apart.
+template <class FT>
 __global__ void band_solve_tiles_kernel(const int32_t* __restrict__ node_off,
                                         const int32_t* __restrict__ bwv,
                                         const int64_t* __restrict__ band_off,
-                                        const double* __restrict__ Lc, const double* __restrict__ Uc,
-                                        double* __restrict__ v, int64_t stride, int nparts,
+                                        const FT* __restrict__ Lc, const FT* __restrict__ Uc,
+                                        FT* __restrict__ v, int64_t stride, int nparts,
                                         int use_smem) {
-  extern __shared__ double smem[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  FT* smem = reinterpret_cast<FT*>(smem_raw);
   const int t = blockIdx.x % nparts;
   const int col = blockIdx.x / nparts;
   const int off = node_off[t];
   const int n = node_off[t + 1] - off;
-  double* vg = v + (size_t)col * stride + off;
+  FT* vg = v + (size_t)col * stride + off;
   const int lane = threadIdx.x;
   if (use_smem) {
     for (int i = lane; i < n; i += 32) smem[i] = vg[i];
@@ -179,19 +181,29 @@ __global__ void band_solve_tiles_kernel(const int32_t* __restrict__ node_off,
   }
 }
 
-void launch_band_solve(vtm_plan_s* P, double* v, int ncols, int64_t stride, cudaStream_t s) {
+template <class FT>
+static void launch_band_solve_t(vtm_plan_s* P, FT* v, const FT* Lc, const FT* Uc, int ncols,
+                                int64_t stride, cudaStream_t s) {
   P->launch_count++;
-  size_t smem = (size_t)P->max_nodes * sizeof(double);
+  size_t smem = (size_t)P->max_nodes * sizeof(FT);
   int use_smem = smem <= 200 * 1024;
   if (use_smem) {
-    cudaFuncSetAttribute(band_solve_tiles_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(band_solve_tiles_kernel<FT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
   } else {
     smem = 0;
   }
-  band_solve_tiles_kernel<<<P->nparts * ncols, 32, smem, s>>>(
-      P->tabs.node_off.as<int32_t>(), P->tabs.bw.as<int32_t>(), P->tabs.band_off.as<int64_t>(),
-      P->d_Lc.as<double>(), P->d_Uc.as<double>(), v, stride, P->nparts, use_smem);
+  band_solve_tiles_kernel<FT><<<P->nparts * ncols, 32, smem, s>>>(
+      P->tabs.node_off.as<int32_t>(), P->tabs.bw.as<int32_t>(), P->tabs.band_off.as<int64_t>(), Lc,
+      Uc, v, stride, P->nparts, use_smem);
+}
+
+void launch_band_solve(vtm_plan_s* P, double* v, int ncols, int64_t stride, cudaStream_t s) {
+  launch_band_solve_t<double>(P, v, P->d_Lc.as<double>(), P->d_Uc.as<double>(), ncols, stride, s);
+}
+
+void launch_band_solve32(vtm_plan_s* P, float* v, int ncols, int64_t stride, cudaStream_t s) {
+  launch_band_solve_t<float>(P, v, P->d_Lc32.as<float>(), P->d_Uc32.as<float>(), ncols, stride, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -296,11 +308,28 @@ extern "C" vtm_status vtm_factor(vtm_plan_t P) {
   if (!P) return VTM_EINVAL;
   cudaSetDevice(P->device);
   P->factored = false;
+  // captured sweep batches refer to the operator buffers: rebuild them
+  for (int i = 0; i < 3; ++i) {
+    if (P->sweep_graph[i].exec) cudaGraphExecDestroy(P->sweep_graph[i].exec);
+    if (P->batch_graph[i].exec) cudaGraphExecDestroy(P->batch_graph[i].exec);
+    P->sweep_graph[i] = SweepGraph{};
+    P->batch_graph[i] = SweepGraph{};
+  }
   // the band arrays hold K_P before the factorisation: re-assemble if a
   // previous factorisation overwrote them
   static_assert(sizeof(double) == 8, "");
   VTM_TRY(assemble_local(P));
   VTM_TRY(factor_tiles(P));
+  if (P->opts.precision != VTM_PREC_FP64) {
+    // FP32 copy of the factors for the right-hand-side preparation of the
+    // inner (low-precision) solves
+    const int64_t ne = std::max<int64_t>(P->band_elems, 8);
+    VTM_TRY(dev_alloc(P->d_Lc32, ne * sizeof(float)));
+    VTM_TRY(dev_alloc(P->d_Uc32, ne * sizeof(float)));
+    convert_f32_kernel<<<1216, 256, 0, P->stream>>>(P->d_Lc.as<double>(), P->d_Lc32.as<float>(), ne);
+    convert_f32_kernel<<<1216, 256, 0, P->stream>>>(P->d_Uc.as<double>(), P->d_Uc32.as<float>(), ne);
+    VTM_CUDA_TRY(cudaGetLastError());
+  }
   if (P->general) {
     VTM_TRY(build_general_operators(P));
   } else {

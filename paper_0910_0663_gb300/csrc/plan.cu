@@ -599,13 +599,14 @@ using namespace vtm;
 
 std::vector<DevBuf*> vtm_plan_s::all_bufs() {
   return {&tabs.node_off, &tabs.bw, &tabs.band_off, &tabs.port_off, &tabs.T_off, &tabs.T_ld,
-          &tabs.order, &d_rowptr, &d_colidx, &d_vals, &d_perm, &d_Lc, &d_Uc, &d_port_loc, &d_port_pos,
+          &tabs.order, &d_rowptr, &d_colidx, &d_vals, &d_perm, &d_Lc, &d_Uc, &d_Lc32, &d_Uc32, &d_v32,
+          &d_port_loc, &d_port_pos, &d_tdesc,
           &d_twin, &d_g, &d_beta, &d_run, &d_T64, &d_T32, &d_T16, &d_c64, &d_c32, &d_state64,
           &d_state32, &d_v, &d_v2, &d_xacc, &d_r, &d_bcol, &d_partials, &d_ctrl, &d_hist,
           &d_err, &d_red, &d_in_off, &d_out_off, &d_in_src, &d_in_kind, &d_in_twin,
           &d_in_own_out, &d_in_loc, &d_res_perm, &d_res_run, &d_out_loc, &d_in_coef,
           &d_in_sigma, &d_out_scale, &d_out_diag, &d_E_off, &d_E_ld, &d_E, &d_cg, &d_gin,
-          &d_gout, &d_in_tile, &d_item_tile, &d_item_m0, &d_bV, &d_bstate, &d_bc, &d_bpart,
+          &d_gout, &d_in_tile, &d_item_tile, &d_item_m0, &d_bV, &d_bV32, &d_bstate, &d_bc, &d_bpart,
           &d_btol2, &d_bctrl};
 }
 
@@ -739,6 +740,13 @@ extern "C" vtm_status vtm_plan(int64_t n, const int64_t* rowptr, const int32_t* 
     return (P->port_off[a + 1] - P->port_off[a]) > (P->port_off[b + 1] - P->port_off[b]);
   });
   if ((st = upload(P->tabs.order, order, s)) != VTM_OK) return fail(st);
+  std::vector<TileDesc> tdesc(nparts);
+  for (int32_t i = 0; i < nparts; ++i) {
+    const int32_t t = order[i];
+    tdesc[i] = TileDesc{t, P->port_off[t], P->port_off[t + 1] - P->port_off[t], P->T_ld[t],
+                        P->T_off[t], 0};
+  }
+  if ((st = upload(P->d_tdesc, tdesc, s)) != VTM_OK) return fail(st);
   if ((st = upload(P->d_port_loc, P->port_loc, s)) != VTM_OK) return fail(st);
   std::vector<int32_t> port_pos(P->port_node.size());
   for (size_t q = 0; q < port_pos.size(); ++q) port_pos[q] = P->iperm[P->port_node[q]];
@@ -834,6 +842,8 @@ extern "C" vtm_status vtm_plan_get_stats(vtm_plan_t P, vtm_plan_stats* s) {
   s->symmetric = P->symmetric ? 1 : 0;
   s->t_bytes = (int64_t)(P->d_T64.bytes + P->d_T32.bytes + P->d_T16.bytes + P->d_E.bytes);
   s->factor_bytes = (int64_t)(P->d_Lc.bytes + P->d_Uc.bytes);
+  s->sweep_kernel = P->tuned_kernel[P->opts.precision] ? P->tuned_kernel[P->opts.precision]
+                                                        : P->opts.sweep_kernel;
   return VTM_OK;
 }
 
@@ -853,6 +863,10 @@ extern "C" vtm_status vtm_get_ports(vtm_plan_t P, int32_t* node, int32_t* remote
 extern "C" void vtm_destroy(vtm_plan_t P) {
   if (!P) return;
   if (P->transposed) vtm_destroy(P->transposed);
+  for (int i = 0; i < 3; ++i) {
+    if (P->sweep_graph[i].exec) cudaGraphExecDestroy(P->sweep_graph[i].exec);
+    if (P->batch_graph[i].exec) cudaGraphExecDestroy(P->batch_graph[i].exec);
+  }
   for (DevBuf* b : P->all_bufs()) dev_free(*b);
   if (P->h_ctrl) cudaFreeHost(P->h_ctrl);
   if (P->ev0) cudaEventDestroy(P->ev0);

@@ -53,13 +53,20 @@ __global__ void scatter_perm_kernel(const int32_t* __restrict__ perm, const doub
 }
 
 // c(s) = 2 W beta_s x0(l(s)) (permuted position pos(s))
-template <class WT>
+template <class WT, class XT>
 __global__ void port_const_kernel(const int32_t* __restrict__ port_pos, const double* __restrict__ beta,
-                                  const double* __restrict__ x0, double W, WT* __restrict__ c,
+                                  const XT* __restrict__ x0, double W, WT* __restrict__ c,
                                   int64_t nports) {
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nports;
        s += (int64_t)gridDim.x * blockDim.x)
-    c[s] = (WT)(2.0 * W * beta[s] * x0[port_pos[s]]);
+    c[s] = (WT)(2.0 * W * beta[s] * (double)x0[port_pos[s]]);
+}
+
+__global__ void gather_perm_f32_kernel(const int32_t* __restrict__ perm, const double* __restrict__ src,
+                                       float* __restrict__ dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (float)src[perm[i]];
 }
 
 // v(l(s)) += sum over the node's ports of beta_s w_in(s); w_in of the chosen
@@ -573,33 +580,27 @@ template <> struct VecLoadG<__nv_bfloat16, 8> {
   }
 };
 
-template <class TT, class WT, int VEC>
-__global__ void __launch_bounds__(256) sweep_vec_kernel(
-    const TT* __restrict__ T, const int64_t* __restrict__ T_off, const int32_t* __restrict__ T_ld,
-    const int32_t* __restrict__ port_off, const int32_t* __restrict__ order,
+template <class TT, class WT, int VEC, int NT, int KB>
+__global__ void __launch_bounds__(NT) sweep_vec_kernel(
+    const TT* __restrict__ T, const TileDesc* __restrict__ tdesc,
     const int32_t* __restrict__ twin, const double* __restrict__ g,
     const uint8_t* __restrict__ run, const WT* __restrict__ c, WT* __restrict__ state,
     int64_t nports, double W, SweepCtrl* __restrict__ ctrl, double* __restrict__ partials,
     double* __restrict__ hist, int hist_len, int nparts, int ld_max) {
   using AT = WT;
   using LD = VecLoadG<TT, VEC>;
-  constexpr int kBatch = 8;
+  constexpr int kBatch = KB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_k, s_flag;
   __shared__ bool s_last;
   const int tid = threadIdx.x;
-  if (tid == 0) {
-    s_k = *((volatile int*)&ctrl->k);
-    s_flag = *((volatile int*)&ctrl->flag);
-  }
-  __syncthreads();
-  if (s_flag) return;
-  const int k = s_k;
-  const int tile = order[blockIdx.x];
-  const int p0 = port_off[tile];
-  const int p = port_off[tile + 1] - p0;
-  const int ld = T_ld[tile];
-  const TT* Tb = T + T_off[tile];
+  // tile descriptor (in launch order) first: the first T loads depend on it only
+  const TileDesc dsc = tdesc[blockIdx.x];
+  const int tile = dsc.tile;
+  const int p0 = dsc.p0;
+  const int p = dsc.p;
+  const int ld = dsc.ld;
+  const TT* Tb = T + dsc.T_off;
   WT* w_in = reinterpret_cast<WT*>(smem_raw);
   AT* rs = w_in + ld_max;
   AT* red = rs + ld_max;
@@ -607,7 +608,7 @@ __global__ void __launch_bounds__(256) sweep_vec_kernel(
   const int L = max(1, min(nv, (int)blockDim.x));
   const int G = blockDim.x / L;
   const int gi = tid / L, li = tid % L;
-  // first batch of T loads goes out before the gather (it needs no waves)
+  // first batch of T loads goes out before anything else (it needs no waves)
   typename LD::raw buf[kBatch];
   const bool active = gi < G && li < nv;
 #pragma unroll
@@ -615,6 +616,13 @@ __global__ void __launch_bounds__(256) sweep_vec_kernel(
     const int t = gi + b * G;
     if (active && t < p) buf[b] = LD::load(Tb + (size_t)t * ld + li * VEC);
   }
+  if (tid == 0) {
+    s_k = *((volatile int*)&ctrl->k);
+    s_flag = *((volatile int*)&ctrl->flag);
+  }
+  __syncthreads();
+  if (s_flag) return;
+  const int k = s_k;
   const WT* prev = state + (size_t)((k - 1) & 1) * nports * 2;
   WT* cur = state + (size_t)(k & 1) * nports * 2;
   const AT hW = (AT)W, inv2W = (AT)(0.5 / W);
@@ -852,8 +860,8 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
                          ? P->opts.sweep_kernel
                          : (prec == VTM_PREC_FP64 ? 1 : (nv_max <= 256 ? 3 : 2));
   const bool staged = choice == 2 && nv_max <= 4 * 256 && st_smem <= 200 * 1024;
-  // vector-load kernel: every thread owns one vector column (nv <= 256)
-  const bool vecload = choice == 3 && nv_max <= 256;
+  // vector-load kernel: every thread owns one vector column (nv <= threads)
+  const bool vecload = (choice == 3 && nv_max <= 256) || (choice == 4 && nv_max <= 128);
   const size_t vec_smem = 2 * (size_t)ld_max * wsz + 256 * (size_t)vec * wsz + 16;
   if (staged) {
     if (prec == VTM_PREC_FP64)
@@ -886,52 +894,160 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   // keep as much of the low-precision reflection matrices in L2 as the
   // persisting carve-out allows (restored after the sweeps)
   L2Window l2win(P, prec);
+  // one sweep launch with kernel `kc` (1 direct, 2 staged, 3 vector loads)
+  auto launch_one = [&](int kc) {
+    if (kc == 3 || kc == 4) {
+      auto launch_vec = [&](auto* kern, int nt, const auto* T, const auto* c, auto* state) {
+        kern<<<P->nparts, nt, vec_smem, s>>>(
+            T, P->d_tdesc.as<TileDesc>(), P->d_twin.as<int32_t>(), P->d_g.as<double>(),
+            P->d_run.as<uint8_t>(), c, state, npt_, P->W, P->d_ctrl.as<SweepCtrl>(),
+            P->d_partials.as<double>(), hist, hist_len, P->nparts, ld_max);
+      };
+      if (kc == 3) {
+        if (prec == VTM_PREC_FP64)
+          launch_vec(sweep_vec_kernel<double, double, 2, 256, 8>, 256, P->d_T64.as<double>(),
+                     P->d_c64.as<double>(), P->d_state64.as<double>());
+        else if (prec == VTM_PREC_FP32)
+          launch_vec(sweep_vec_kernel<float, float, 4, 256, 8>, 256, P->d_T32.as<float>(),
+                     P->d_c32.as<float>(), P->d_state32.as<float>());
+        else
+          launch_vec(sweep_vec_kernel<__nv_bfloat16, float, 8, 256, 8>, 256,
+                     P->d_T16.as<__nv_bfloat16>(), P->d_c32.as<float>(), P->d_state32.as<float>());
+      } else {
+        if (prec == VTM_PREC_FP64)
+          launch_vec(sweep_vec_kernel<double, double, 2, 128, 4>, 128, P->d_T64.as<double>(),
+                     P->d_c64.as<double>(), P->d_state64.as<double>());
+        else if (prec == VTM_PREC_FP32)
+          launch_vec(sweep_vec_kernel<float, float, 4, 128, 4>, 128, P->d_T32.as<float>(),
+                     P->d_c32.as<float>(), P->d_state32.as<float>());
+        else
+          launch_vec(sweep_vec_kernel<__nv_bfloat16, float, 8, 128, 4>, 128,
+                     P->d_T16.as<__nv_bfloat16>(), P->d_c32.as<float>(), P->d_state32.as<float>());
+      }
+      return;
+    }
+    if (kc == 2) {
+      if (prec == VTM_PREC_FP64)
+        launch_staged(sweep_staged_kernel<double, double, 2, 4>, P->d_T64.as<double>(),
+                      P->d_c64.as<double>(), P->d_state64.as<double>());
+      else if (prec == VTM_PREC_FP32)
+        launch_staged(sweep_staged_kernel<float, float, 4, 4>, P->d_T32.as<float>(),
+                      P->d_c32.as<float>(), P->d_state32.as<float>());
+      else
+        launch_staged(sweep_staged_kernel<__nv_bfloat16, float, 8, 4>, P->d_T16.as<__nv_bfloat16>(),
+                      P->d_c32.as<float>(), P->d_state32.as<float>());
+      return;
+    }
+    if (prec == VTM_PREC_FP64)
+      launch_sweep<double, double>(P, P->d_T64.as<double>(), P->d_c64.as<double>(),
+                                   P->d_state64.as<double>(), threads, smem, hist, hist_len);
+    else if (prec == VTM_PREC_FP32)
+      launch_sweep<float, float>(P, P->d_T32.as<float>(), P->d_c32.as<float>(),
+                                 P->d_state32.as<float>(), threads, smem, hist, hist_len);
+    else
+      launch_sweep<__nv_bfloat16, float>(P, P->d_T16.as<__nv_bfloat16>(), P->d_c32.as<float>(),
+                                         P->d_state32.as<float>(), threads, smem, hist, hist_len);
+  };
+  // Autotuner: on the first solve of this precision, time every kernel that
+  // fits on this plan's tiles (a few sweeps each, from a zero state that is
+  // reset afterwards) and keep the fastest.
+  int kern = vecload ? choice : (staged ? 2 : 1);
+  if (P->opts.sweep_kernel == 0) {
+    if (P->tuned_kernel[prec] == 0) {
+      const bool can_st = nv_max <= 4 * 256 && st_smem <= 200 * 1024;
+      const bool can_vec = nv_max <= 256;
+      const bool can_vec128 = nv_max <= 128;
+      float best = 1e30f;
+      int best_k = 1;
+      for (int cand = 1; cand <= 4; ++cand) {
+        if ((cand == 2 && !can_st) || (cand == 3 && !can_vec) || (cand == 4 && !can_vec128)) continue;
+        if (cand == 2)
+          VTM_CUDA_TRY(cudaFuncSetAttribute(
+              prec == VTM_PREC_FP64 ? (const void*)sweep_staged_kernel<double, double, 2, 4>
+              : prec == VTM_PREC_FP32 ? (const void*)sweep_staged_kernel<float, float, 4, 4>
+                                      : (const void*)sweep_staged_kernel<__nv_bfloat16, float, 8, 4>,
+              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st_smem));
+        SweepCtrl t = h;
+        t.k_max = 1 << 30;
+        t.tol2 = -1.0;  // never converges while timing
+        t.stall = 0;
+        *P->h_ctrl = t;
+        VTM_CUDA_TRY(cudaMemcpyAsync(P->d_ctrl.p, P->h_ctrl, sizeof(SweepCtrl), cudaMemcpyHostToDevice, s));
+        for (int i = 0; i < 2; ++i) launch_one(cand);
+        VTM_CUDA_TRY(cudaEventRecord(P->evs0, s));
+        for (int i = 0; i < 6; ++i) launch_one(cand);
+        VTM_CUDA_TRY(cudaEventRecord(P->evs1, s));
+        VTM_CUDA_TRY(cudaGetLastError());
+        VTM_CUDA_TRY(cudaEventSynchronize(P->evs1));
+        float ms = 0.f;
+        VTM_CUDA_TRY(cudaEventElapsedTime(&ms, P->evs0, P->evs1));
+        P->launch_count += 8;
+        if (ms < best) {
+          best = ms;
+          best_k = cand;
+        }
+      }
+      P->tuned_kernel[prec] = best_k;
+      P->tuned_ms[prec] = best / 6.0f;
+      // back to the initial state of this inner solve
+      *P->h_ctrl = h;
+      VTM_CUDA_TRY(cudaMemcpyAsync(P->d_ctrl.p, P->h_ctrl, sizeof(SweepCtrl), cudaMemcpyHostToDevice, s));
+      if (prec == VTM_PREC_FP64)
+        VTM_CUDA_TRY(cudaMemsetAsync(P->d_state64.p, 0, 4 * npt * sizeof(double), s));
+      else
+        VTM_CUDA_TRY(cudaMemsetAsync(P->d_state32.p, 0, 4 * npt * sizeof(float), s));
+    }
+    kern = P->tuned_kernel[prec];
+    if (kern == 2)
+      VTM_CUDA_TRY(cudaFuncSetAttribute(
+          prec == VTM_PREC_FP64 ? (const void*)sweep_staged_kernel<double, double, 2, 4>
+          : prec == VTM_PREC_FP32 ? (const void*)sweep_staged_kernel<float, float, 4, 4>
+                                  : (const void*)sweep_staged_kernel<__nv_bfloat16, float, 8, 4>,
+          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st_smem));
+  }
+  if (kern == 2 && !st_grid) {  // occupancy query before any capture
+    const void* kfn = prec == VTM_PREC_FP64 ? (const void*)sweep_staged_kernel<double, double, 2, 4>
+                      : prec == VTM_PREC_FP32 ? (const void*)sweep_staged_kernel<float, float, 4, 4>
+                                              : (const void*)sweep_staged_kernel<__nv_bfloat16, float, 8, 4>;
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, st_threads, st_smem);
+    st_grid = std::max(1, std::min(P->nparts, std::max(per_sm, 1) * sms));
+  }
+  // Batches of check_every launches, captured once into a CUDA graph when the
+  // plan has its own stream (launches past convergence or the sweep limit
+  // return at once, so full batches are always safe).
+  const int batch = P->opts.check_every;
+  cudaGraphExec_t gexec = nullptr;
+  if (P->stream && P->opts.graphs != 1) {
+    SweepGraph& G = P->sweep_graph[prec];
+    const uint64_t key = ((uint64_t)kern << 56) ^ ((uint64_t)batch << 32) ^ (uint64_t)(uintptr_t)hist ^
+                         ((uint64_t)hist_len << 16);
+    if (!G.exec || G.key != key) {
+      if (G.exec) cudaGraphExecDestroy(G.exec);
+      G.exec = nullptr;
+      cudaGraph_t graph = nullptr;
+      VTM_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      for (int i = 0; i < batch; ++i) launch_one(kern);
+      VTM_CUDA_TRY(cudaStreamEndCapture(s, &graph));
+      cudaError_t e = cudaGraphInstantiate(&G.exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        G.exec = nullptr;
+        cudaGetLastError();
+      } else {
+        G.key = key;
+      }
+    }
+    gexec = G.exec;
+  }
   int launched = 0;
   while (true) {
-    const int m = std::min(P->opts.check_every, budget + 1 - launched);
+    const int m = gexec ? batch : std::min(batch, budget + 1 - launched);
     VTM_CUDA_TRY(cudaEventRecord(P->evs0, s));
-    for (int i = 0; i < m; ++i) {
-      if (vecload) {
-        auto launch_vec = [&](auto* kern, const auto* T, const auto* c, auto* state) {
-          kern<<<P->nparts, 256, vec_smem, s>>>(
-              T, P->tabs.T_off.as<int64_t>(), P->tabs.T_ld.as<int32_t>(),
-              P->tabs.port_off.as<int32_t>(), P->tabs.order.as<int32_t>(), P->d_twin.as<int32_t>(),
-              P->d_g.as<double>(), P->d_run.as<uint8_t>(), c, state, npt_, P->W,
-              P->d_ctrl.as<SweepCtrl>(), P->d_partials.as<double>(), hist, hist_len, P->nparts,
-              ld_max);
-        };
-        if (prec == VTM_PREC_FP64)
-          launch_vec(sweep_vec_kernel<double, double, 2>, P->d_T64.as<double>(), P->d_c64.as<double>(),
-                     P->d_state64.as<double>());
-        else if (prec == VTM_PREC_FP32)
-          launch_vec(sweep_vec_kernel<float, float, 4>, P->d_T32.as<float>(), P->d_c32.as<float>(),
-                     P->d_state32.as<float>());
-        else
-          launch_vec(sweep_vec_kernel<__nv_bfloat16, float, 8>, P->d_T16.as<__nv_bfloat16>(),
-                     P->d_c32.as<float>(), P->d_state32.as<float>());
-        continue;
-      }
-      if (staged) {
-        if (prec == VTM_PREC_FP64)
-          launch_staged(sweep_staged_kernel<double, double, 2, 4>, P->d_T64.as<double>(),
-                        P->d_c64.as<double>(), P->d_state64.as<double>());
-        else if (prec == VTM_PREC_FP32)
-          launch_staged(sweep_staged_kernel<float, float, 4, 4>, P->d_T32.as<float>(),
-                        P->d_c32.as<float>(), P->d_state32.as<float>());
-        else
-          launch_staged(sweep_staged_kernel<__nv_bfloat16, float, 8, 4>, P->d_T16.as<__nv_bfloat16>(),
-                        P->d_c32.as<float>(), P->d_state32.as<float>());
-        continue;
-      }
-      if (prec == VTM_PREC_FP64)
-        launch_sweep<double, double>(P, P->d_T64.as<double>(), P->d_c64.as<double>(),
-                                     P->d_state64.as<double>(), threads, smem, hist, hist_len);
-      else if (prec == VTM_PREC_FP32)
-        launch_sweep<float, float>(P, P->d_T32.as<float>(), P->d_c32.as<float>(),
-                                   P->d_state32.as<float>(), threads, smem, hist, hist_len);
-      else
-        launch_sweep<__nv_bfloat16, float>(P, P->d_T16.as<__nv_bfloat16>(), P->d_c32.as<float>(),
-                                           P->d_state32.as<float>(), threads, smem, hist, hist_len);
+    if (gexec) {
+      VTM_CUDA_TRY(cudaGraphLaunch(gexec, s));
+    } else {
+      for (int i = 0; i < m; ++i) launch_one(kern);
     }
     launched += m;
     VTM_CUDA_TRY(cudaGetLastError());
@@ -1020,9 +1136,19 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
   for (int outer = 0; outer < max_outer; ++outer) {
     // inner problem A d = r (r = b at the first step)
     const double* rhs = outer == 0 ? d_b : r;
-    gather_perm_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, v, n);
-    P->launch_count++;
-    launch_band_solve(P, v, 1, n, s);
+    // x0 = K_P^-1 rhs_P: FP64, or FP32 for a low-precision inner solve (it
+    // only feeds c, whose error the next refinement step removes)
+    const bool x0_f32 = prec != VTM_PREC_FP64 && !P->general && npt > 0 && P->d_Lc32.p;
+    if (x0_f32) {
+      VTM_TRY(dev_alloc(P->d_v32, (size_t)n * sizeof(float)));
+      gather_perm_f32_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, P->d_v32.as<float>(), n);
+      P->launch_count++;
+      launch_band_solve32(P, P->d_v32.as<float>(), 1, n, s);
+    } else {
+      gather_perm_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, v, n);
+      P->launch_count++;
+      launch_band_solve(P, v, 1, n, s);
+    }
     int kc = 0, flag = 1;
     if (P->general && P->n_in > 0) {
       // channel form (lagged couplings / block Jacobi), FP64 sweeps
@@ -1044,11 +1170,15 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
       launch_band_solve(P, v, 1, n, s);
     } else if (!P->general && npt > 0) {
       if (prec == VTM_PREC_FP64)
-        port_const_kernel<double><<<g2, 256, 0, s>>>(P->d_port_pos.as<int32_t>(), P->d_beta.as<double>(),
-                                                     v, P->W, P->d_c64.as<double>(), npt);
+        port_const_kernel<double, double><<<g2, 256, 0, s>>>(
+            P->d_port_pos.as<int32_t>(), P->d_beta.as<double>(), v, P->W, P->d_c64.as<double>(), npt);
+      else if (x0_f32)
+        port_const_kernel<float, float><<<g2, 256, 0, s>>>(P->d_port_pos.as<int32_t>(),
+                                                           P->d_beta.as<double>(), P->d_v32.as<float>(),
+                                                           P->W, P->d_c32.as<float>(), npt);
       else
-        port_const_kernel<float><<<g2, 256, 0, s>>>(P->d_port_pos.as<int32_t>(), P->d_beta.as<double>(),
-                                                    v, P->W, P->d_c32.as<float>(), npt);
+        port_const_kernel<float, double><<<g2, 256, 0, s>>>(
+            P->d_port_pos.as<int32_t>(), P->d_beta.as<double>(), v, P->W, P->d_c32.as<float>(), npt);
       VTM_CUDA_TRY(cudaGetLastError());
       P->launch_count++;
       double t_abs = prec == VTM_PREC_FP64 ? target : std::max(target, inner_tol * rnorm);

@@ -54,6 +54,16 @@ struct SweepCtrl {
   double last_res2;    // squared residual of the last completed sweep
 };
 
+// Per-launch-slot descriptor of a tile for the vector-load sweep kernel.
+struct __align__(16) TileDesc {
+  int32_t tile;
+  int32_t p0;   // first port
+  int32_t p;    // ports
+  int32_t ld;   // row length of the T^T block
+  int64_t T_off;
+  int64_t pad;
+};
+
 // Offsets and sizes describing one tile-contiguous operator family.
 struct TileTables {
   DevBuf node_off;   // int32[nparts+1]: first permuted position of each tile
@@ -65,6 +75,14 @@ struct TileTables {
   DevBuf order;      // int32[nparts]: launch order of tiles (largest p first)
 };
 
+}  // namespace vtm
+
+namespace vtm {
+// A captured batch of sweep launches (CUDA graph) and what it was made for.
+struct SweepGraph {
+  cudaGraphExec_t exec = nullptr;
+  uint64_t key = 0;
+};
 }  // namespace vtm
 
 struct vtm_plan_s {
@@ -122,7 +140,8 @@ struct vtm_plan_s {
   vtm::DevBuf d_rowptr, d_colidx, d_vals;  // A for the FP64 residual
   vtm::DevBuf d_perm;                      // int32[n]
   vtm::DevBuf d_Lc, d_Uc;                  // band factors (doubles)
-  vtm::DevBuf d_port_loc, d_port_pos, d_twin, d_g, d_beta, d_run;
+  vtm::DevBuf d_Lc32, d_Uc32, d_v32;       // FP32 factor copies and work vector (inner solves)
+  vtm::DevBuf d_port_loc, d_port_pos, d_twin, d_g, d_beta, d_run, d_tdesc;
   vtm::DevBuf d_T64, d_T32, d_T16;         // reflection matrices (T^T blocks)
   vtm::DevBuf d_c64, d_c32;                // constant term of the sweep
   vtm::DevBuf d_state64, d_state32;        // [2][nports] (w_in, w_out) pairs
@@ -136,6 +155,11 @@ struct vtm_plan_s {
   int hist_cap = 0;
   vtm::SweepCtrl* h_ctrl = nullptr;        // pinned mirror
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evs0 = nullptr, evs1 = nullptr;
+  // sweep-kernel autotuning and graphs, per precision
+  int tuned_kernel[3] = {0, 0, 0};
+  float tuned_ms[3] = {0.f, 0.f, 0.f};
+  vtm::SweepGraph sweep_graph[3];
+  vtm::SweepGraph batch_graph[3];
   // per-call accounting (reset by each solve)
   int launch_count = 0;
   int sweep_launch_count = 0;
@@ -169,7 +193,7 @@ struct vtm_plan_s {
 
   // batched right-hand sides (batch.cu)
   std::vector<int32_t> item_tile, item_m0;
-  vtm::DevBuf d_item_tile, d_item_m0, d_bV, d_bstate, d_bc, d_bpart, d_btol2, d_bctrl;
+  vtm::DevBuf d_item_tile, d_item_m0, d_bV, d_bV32, d_bstate, d_bc, d_bpart, d_btol2, d_bctrl;
 
   // adjoint of an unsymmetric system
   vtm_plan_s* transposed = nullptr;
@@ -220,5 +244,6 @@ int launch_residual(const int64_t* rowptr, const int32_t* col, const double* val
 
 // Launch helpers exported between translation units.
 void launch_band_solve(vtm_plan_s* P, double* v, int ncols, int64_t vec_stride, cudaStream_t s);
+void launch_band_solve32(vtm_plan_s* P, float* v, int ncols, int64_t vec_stride, cudaStream_t s);
 
 }  // namespace vtm

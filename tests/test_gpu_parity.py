@@ -158,12 +158,17 @@ def test_host_and_device_buffers_agree(vtm):
 
 
 def test_multiple_columns(vtm):
+    # column by column (batch=1): each column is the single-RHS solve, bit for bit
     w = wl.grid2d(16, 16, 8, 8, seed=8, nrhs=3)
-    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=1.0)
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=1.0, batch=1)
     x, info = plan.solve(torch.from_numpy(w.b).cuda(), tol=1e-10)
     for r in range(3):
         xr, _ = plan.solve(torch.from_numpy(w.b[r]).cuda(), tol=1e-10)
         assert torch.equal(xr, x[r])
+    # batched (default): every column meets the tolerance
+    plan_b = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=1.0)
+    xb, info_b = plan_b.solve(torch.from_numpy(w.b).cuda(), tol=1e-10)
+    assert O.residual_norms(w.csr(), xb.cpu().numpy(), w.b).max() <= 1e-10
 
 
 def test_zero_rhs_and_errors(vtm):
@@ -206,3 +211,36 @@ def test_set_values_then_refactor(vtm):
     A2 = O.csr_matrix(ip, ix, d2, w.n)
     x_star = np.linalg.solve(A2.toarray(), w.b[0])
     assert np.abs(x.cpu().numpy() - x_star).max() <= 1e-8 * np.abs(x_star).max()
+
+
+@pytest.mark.parametrize("kernel", [1, 2, 3])
+def test_every_sweep_kernel_matches_oracle(vtm, kernel):
+    # direct-load, bulk-copy staged and vector-load kernels compute the same sweep
+    w = wl.power_grid(128, 128, 32, 32, Zc=1.0, seed=12)
+    A = w.csr()
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc, sweep_kernel=kernel)
+    x, info = plan.solve(torch.from_numpy(w.b).cuda(), tol=1e-10)
+    ref = O.vtm_midpoint(A, w.partition, w.nparts, w.b, W=1 / w.Zc, tol=1e-10)
+    assert abs(info["sweeps"] - ref.sweeps) <= 1
+    if info["sweeps"] == ref.sweeps:
+        xs = x.cpu().numpy().reshape(w.b.shape)
+        assert np.abs(xs - ref.x).max() <= 1e-11 * np.abs(ref.x).max()
+
+
+def test_graph_path_on_a_dedicated_stream(vtm):
+    # a plan with its own stream replays its sweep batches from a CUDA graph
+    # and autotunes its sweep kernel; the result is the same iteration
+    w = wl.power_grid(128, 128, 32, 32, Zc=1.0, seed=13)
+    A = w.csr()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc, stream=s,
+                        precision="fp32")
+        b = torch.from_numpy(w.b[0]).cuda()
+        x1, info1 = plan.solve(b, tol=1e-10)
+        x2, info2 = plan.solve(b, tol=1e-10)  # graph replay
+    torch.cuda.synchronize()
+    assert plan.stats()["sweep_kernel"] in (1, 2, 3)
+    assert torch.equal(x1, x2)
+    rel = O.residual_norms(A, x1.cpu().numpy()[None], w.b)
+    assert rel.max() <= 1e-10
