@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--l2-persist", type=int, default=0, choices=[0, 1],
                     help="0: reflection matrices persisting in L2 during low-precision sweeps, 1: off")
-    ap.add_argument("--sweep-kernel", type=int, default=0, choices=[0, 1, 2, 3, 4],
+    ap.add_argument("--sweep-kernel", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6],
                     help="0: autotuned, 1: direct-load, 2: bulk-copy staged, 3/4: vector-load (256/128 threads)")
     return ap.parse_args()
 
@@ -184,6 +184,21 @@ def reference_arm(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def job_value(units_local, t_local_ms, world, device=None):
+    """Whole-job throughput of N replicas: the units all ranks processed
+    divided by the slowest rank's time (max over ranks).  Returns (value,
+    max_ms).  For world == 1 no collective is used."""
+    if world <= 1:
+        return units_local / (t_local_ms * 1e-3), t_local_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(t_local_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return u.item() / (t.item() * 1e-3), t.item()
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -200,7 +215,9 @@ def sweep_bytes(stats, prec, nrhs=1):
     g (8 B), twin index (4 B) and node-run byte (1 B)."""
     s_t = {0: 8, 1: 4, 2: 2}[prec]
     s_w = 8 if prec == 0 else 4
-    return stats["sum_p2"] * s_t + stats["nports"] * (7 * s_w * nrhs + 13)
+    # the packed symmetric kernels need only the entries on and above the diagonal
+    entries = stats["sum_tri"] if stats.get("sweep_kernel") in (5, 6) and nrhs == 1 else stats["sum_p2"]
+    return entries * s_t + stats["nports"] * (7 * s_w * nrhs + 13)
 
 
 def plan_rowptr(w, dev):
@@ -342,10 +359,7 @@ def run_mode(args, prec, w, dev, stream, b_dev, b_host, x_host, flush, world):
                 times.append(ev0.elapsed_time(ev1))
                 infos.append(info)
         t_step = float(np.mean(times))
-        if world > 1:
-            tt = torch.tensor([t_step], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_step = float(tt.item())
+        value, t_step = job_value(w.n * nrhs, t_step, world, dev)
         # end to end through the C ABI with host buffers (copies inside)
         from paper_0910_0663_gb300 import _vtm as C
         e2e = []
@@ -366,7 +380,7 @@ def run_mode(args, prec, w, dev, stream, b_dev, b_host, x_host, flush, world):
         if grad:
             vtm.C.vtm_netmap_destroy(netmap)
         return dict(t_step_ms=t_step, t_plan_s=t1 - t0, t_factor_s=t2 - t1,
-                             value=w.n * nrhs * world / (t_step * 1e-3), nrhs=nrhs,
+                             value=value, nrhs=nrhs,
                              e2e_value=w.n * nrhs * world / float(np.mean(e2e)), info=inf, stats=st,
                              bytes_sweep=bytes_sweep, achieved_gbs=achieved,
                              t_sweep_ms=t_sweep_launch, clocks=sampler.summary(),
@@ -398,7 +412,9 @@ def emit(args, results, errors, best, w, world, rank):
         "setup": {"t_plan_s": R["t_plan_s"], "t_factor_s": R["t_factor_s"]},
         "modes": {p: {"value": r["value"], "ms_per_step": r["t_step_ms"], "sweeps": r["info"]["sweeps"],
                       "outer_steps": r["info"]["outer_steps"], "relres": r["relres"],
-                      "sweep_gbs": r["achieved_gbs"], "t_factor_s": r["t_factor_s"]}
+                      "sweep_gbs": r["achieved_gbs"], "t_factor_s": r["t_factor_s"],
+                      "sweep_ms_per_launch": r["t_sweep_ms"], "sweep_kernel": r["stats"].get("sweep_kernel"),
+                      "gpu_launches": r["info"]["kernel_launches"]}
                   for p, r in results.items()},
     }
     if errors:

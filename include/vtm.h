@@ -85,6 +85,8 @@ typedef struct {
   int method;        /* VTM_METHOD_VTM (default) or VTM_METHOD_BJ; read by vtm_plan only */
   int batch;         /* several right-hand sides: 0 (default) one batched iteration over
                         up to 64 columns at a time; 1: one column after the other */
+  int batch_solve;   /* batched FP32 band solves: 0 (default) row window in shared memory;
+                        1: whole column block in shared memory */
   int l2_persist;    /* 0 (default): during FP32/BF16 sweeps, mark the reflection matrices
                         persisting in L2 (access-policy window on the plan's stream; the
                         context's persisting carve-out is set and restored around the
@@ -93,7 +95,12 @@ typedef struct {
                         every sweep kernel that fits the plan's sub-circuits and keeps the
                         fastest; 1: direct-load kernel; 2: bulk-copy staged kernel;
                         3: 16-byte vector-load kernel, 256 threads per tile;
-                        4: the same with 128 threads (p <= 128 VEC) */
+                        4: the same with 128 threads (p <= 128 VEC);
+                        5, 6: packed symmetric kernel, 128 / 256 threads per tile --
+                        FP32/BF16 plans of a symmetric A whose sub-circuits have at
+                        most 256 ports keep only the 16x16 blocks of T_P on and above
+                        the diagonal (T_P is symmetric for scalar W, Sec. VIII), about
+                        half the bytes per sweep; elsewhere 5, 6 fall back to kernel 1 */
   int graphs;        /* 0 (default): replay batches of check_every sweep launches from a
                         CUDA graph when the plan has its own stream; 1: plain launches */
   double* history;   /* optional host array: relative (interface) residual after each
@@ -127,6 +134,9 @@ typedef struct {
   int64_t t_bytes;       /* bytes of the stored reflection matrices (all precisions kept) */
   int64_t factor_bytes;  /* bytes of the stored local factors */
   int32_t sweep_kernel;  /* sweep kernel in use for the plan's precision (see vtm_opts) */
+  int64_t sum_tri;       /* sum over sub-circuits of p_P (p_P + 1) / 2: the entries of the
+                            symmetric reflection matrices on and above the diagonal */
+  int64_t packed_bytes;  /* bytes of the packed symmetric copies (0 if none) */
 } vtm_plan_stats;
 
 /* vtm_plan -- wire tearing (Sec. V) and the port table.
@@ -148,7 +158,10 @@ vtm_status vtm_plan(int64_t n, const int64_t* rowptr, const int32_t* colidx, con
  * must be factored again before the next solve. */
 vtm_status vtm_set_values(vtm_plan_t plan, const double* vals);
 
-/* vtm_set_opts -- replace the options of a plan (precision, limits, history). */
+/* vtm_set_opts -- replace the options of a plan (precision, limits, history).
+ * VTM_EINVAL for a precision outside 0..2, a negative history_len, a history
+ * length without an array, or a sweep_kernel outside 0..6; the plan keeps its
+ * previous options then. */
 vtm_status vtm_set_opts(vtm_plan_t plan, const vtm_opts* opts);
 
 /* vtm_factor -- per sub-circuit factorisation of the condensed local matrix

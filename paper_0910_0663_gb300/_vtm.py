@@ -27,6 +27,7 @@ class vtm_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_sweeps", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("max_outer", ctypes.c_int), ("method", ctypes.c_int), ("batch", ctypes.c_int),
+                ("batch_solve", ctypes.c_int),
                 ("l2_persist", ctypes.c_int), ("sweep_kernel", ctypes.c_int), ("graphs", ctypes.c_int),
                 ("history", ctypes.POINTER(ctypes.c_double)),
                 ("history_len", ctypes.c_int)]
@@ -48,7 +49,8 @@ class vtm_plan_stats(ctypes.Structure):
                 ("max_ports", ctypes.c_int32), ("max_nodes", ctypes.c_int32),
                 ("max_band", ctypes.c_int32), ("symmetric", ctypes.c_int32),
                 ("t_bytes", ctypes.c_int64), ("factor_bytes", ctypes.c_int64),
-                ("sweep_kernel", ctypes.c_int32)]
+                ("sweep_kernel", ctypes.c_int32), ("sum_tri", ctypes.c_int64),
+                ("packed_bytes", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -126,7 +128,8 @@ def _check(status, where):
 
 
 def make_opts(precision="fp64", max_sweeps=0, check_every=0, inner_tol=0.0, max_outer=0,
-              history=None, sweep_kernel=0, method="vtm", batch=0, l2_persist=0, graphs=0):
+              history=None, sweep_kernel=0, method="vtm", batch=0, l2_persist=0, graphs=0,
+              batch_solve=0):
     o = vtm_opts()
     o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
     o.max_sweeps = max_sweeps
@@ -138,6 +141,7 @@ def make_opts(precision="fp64", max_sweeps=0, check_every=0, inner_tol=0.0, max_
     o.batch = int(batch)
     o.l2_persist = int(l2_persist)
     o.graphs = int(graphs)
+    o.batch_solve = int(batch_solve)
     if history is not None:
         assert history.dtype == np.float64 and history.flags["C_CONTIGUOUS"]
         o.history = history.ctypes.data_as(ctypes.POINTER(ctypes.c_double))

@@ -28,6 +28,7 @@ struct BatchCtrl {
   int k;
   int flag;  // 0 running, 1 converged, 2 sweep limit, 3 diverged, 4 stalled
   unsigned counter;
+  unsigned work;   // next entry of the work list (persistent CTAs)
   int conv_sweep;
   int k_max;
   int best_k;
@@ -41,15 +42,16 @@ struct BatchCtrl {
 // permutation between the caller's column-major n x R and [pos][R]
 // ---------------------------------------------------------------------------
 
+// Permuted vectors are column-major too, V[r * n + pos], so both sides of
+// the permutation are read and written along a column.
 template <class FT>
 __global__ void batch_gather_kernel(const int32_t* __restrict__ perm, const double* __restrict__ src,
                                     FT* __restrict__ dst, int64_t n, int R) {
   const int64_t total = n * R;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t pos = i / R;
-    const int r = (int)(i % R);
-    dst[i] = (FT)src[(int64_t)r * n + perm[pos]];
+    const int64_t r = i / n, pos = i % n;
+    dst[i] = (FT)src[r * n + perm[pos]];
   }
 }
 
@@ -59,12 +61,83 @@ __global__ void batch_scatter_kernel(const int32_t* __restrict__ perm, const FT*
   const int64_t total = n * R;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t pos = i / R;
-    const int r = (int)(i % R);
-    double* d = dst + (int64_t)r * n + perm[pos];
+    const int64_t r = i / n, pos = i % n;
+    double* d = dst + r * n + perm[pos];
     if (accumulate) *d += (double)src[i];
     else *d = (double)src[i];
   }
+}
+
+// r = b - A x for R columns at once (column-major), with ||r_c||^2 and
+// ||b_c||^2 per column: block (bx, by) covers rows bx, bx + gx, ... of the
+// columns 8 by .. 8 by + 7; per-block partial sums, then the last block of
+// each column group adds them in a fixed order.  counters[by] start at 0 and
+// are left at 0; out[2 c] = ||r_c||^2, out[2 c + 1] = ||b_c||^2.
+__global__ void __launch_bounds__(256) batch_residual_norms_kernel(
+    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+    const double* __restrict__ val, const double* __restrict__ x, const double* __restrict__ b,
+    double* __restrict__ r, int64_t n, int R, double* __restrict__ partials,
+    unsigned* __restrict__ counters, double* __restrict__ out) {
+  constexpr int CG = 8;
+  __shared__ double red[2 * CG][8];
+  __shared__ bool last;
+  const int c0 = blockIdx.y * CG;
+  const int nc = min(CG, R - c0);
+  double rr[CG], bb[CG];
+#pragma unroll
+  for (int c = 0; c < CG; ++c) rr[c] = bb[c] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q0 = rowptr[i], q1 = rowptr[i + 1];
+#pragma unroll
+    for (int c = 0; c < CG; ++c) {
+      if (c < nc) {
+        const double* xc = x + (int64_t)(c0 + c) * n;
+        const double bi = b[(int64_t)(c0 + c) * n + i];
+        double acc = bi;
+        for (int64_t q = q0; q < q1; ++q) acc -= val[q] * xc[col[q]];
+        if (r) r[(int64_t)(c0 + c) * n + i] = acc;
+        rr[c] += acc * acc;
+        bb[c] += bi * bi;
+      }
+    }
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int c = 0; c < CG; ++c) {
+    double a = rr[c], e = bb[c];
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      e += __shfl_down_sync(0xffffffffu, e, o);
+    }
+    if (l == 0) {
+      red[c][w] = a;
+      red[CG + c][w] = e;
+    }
+  }
+  __syncthreads();
+  const size_t pb = ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 2 * CG;
+  if (threadIdx.x < 2 * CG) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[threadIdx.x][k];
+    partials[pb + threadIdx.x] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&counters[blockIdx.y], 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x < 2 * CG) {
+    double t = 0.0;
+    for (unsigned bx = 0; bx < gridDim.x; ++bx)
+      t += partials[((size_t)blockIdx.y * gridDim.x + bx) * 2 * CG + threadIdx.x];
+    const int c = threadIdx.x % CG;
+    if (c < nc) out[2 * (c0 + c) + (threadIdx.x >= CG ? 1 : 0)] = t;
+  }
+  if (threadIdx.x == 0) counters[blockIdx.y] = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -98,9 +171,10 @@ __global__ void batch_band_solve_kernel(const int32_t* __restrict__ node_off,
   // column-major in shared memory, v[c * n + row]: at every step the threads
   // (band offsets) touch consecutive rows of a column, without bank conflicts
   FT* v = reinterpret_cast<FT*>(smem_raw);
+  const int64_t ntot = (int64_t)node_off[gridDim.x / ngroups];  // all nodes (column stride)
   for (int i = tid; i < n * RG; i += blockDim.x) {
-    const int row = i / RG, c = i % RG;
-    v[c * n + row] = c < rg ? V[(int64_t)(base + row) * R + r0 + c] : FT(0);
+    const int c = i / n, row = i % n;
+    v[i] = c < rg ? V[(int64_t)(r0 + c) * ntot + base + row] : FT(0);
   }
   __syncthreads();
   const int a = tid + 1;  // band offset of this thread
@@ -150,23 +224,145 @@ __global__ void batch_band_solve_kernel(const int32_t* __restrict__ node_off,
     }
   }
   for (int i = tid; i < n * RG; i += blockDim.x) {
-    const int row = i / RG, c = i % RG;
-    const FT x = v[c * n + row] * uc[(size_t)row * B];
-    if (c < rg) V[(int64_t)(base + row) * R + r0 + c] = x;
+    const int c = i / n, row = i % n;
+    if (c < rg) V[(int64_t)(r0 + c) * ntot + base + row] = v[i] * uc[(size_t)row * B];
   }
+}
+
+// The same solve with only a window of WB = bw + 1 + PF rows of the tile's
+// column block in shared memory (rows enter PF steps before their first use
+// through 4-byte cp.async copies, finished rows are stored as they leave), so
+// many CTAs fit on an SM and hide each other's per-row latency.
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int RG, int D, int PF>
+__global__ void batch_band_solve_win_kernel(const int32_t* __restrict__ node_off,
+                                            const int32_t* __restrict__ bwv,
+                                            const int64_t* __restrict__ band_off,
+                                            const float* __restrict__ Lc, const float* __restrict__ Uc,
+                                            float* __restrict__ V, int R) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ngroups = (R + RG - 1) / RG;
+  const int t = blockIdx.x / ngroups;
+  const int r0 = (blockIdx.x % ngroups) * RG;
+  const int rg = min(RG, R - r0);
+  const int base = node_off[t];
+  const int n = node_off[t + 1] - base;
+  const int bw = bwv[t];
+  const int B = bw + 1;
+  const int WB = bw + 1 + PF;  // window rows
+  const float* lc = Lc + band_off[t];
+  const float* uc = Uc + band_off[t];
+  const int64_t ntot = (int64_t)node_off[gridDim.x / ngroups];
+  const int tid = threadIdx.x;
+  float* win = reinterpret_cast<float*>(smem_raw);  // win[c * WB + row % WB]
+  const int a = tid + 1;
+  const bool act = a <= bw;
+  const bool loader = tid < RG;  // thread c moves column c in and out
+  const int c = tid;
+  float* Vc = V + (int64_t)(r0 + min(c, RG - 1)) * ntot + base;
+  // ---- forward: rows [j, j + WB) in the window ----
+  for (int i = tid; i < min(WB, n) * RG; i += blockDim.x) {
+    const int cc = i / min(WB, n), row = i % min(WB, n);
+    win[cc * WB + row] = cc < rg ? V[(int64_t)(r0 + cc) * ntot + base + row] : 0.f;
+  }
+  float pf[D], dg[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    pf[d] = (act && d < n && a <= n - 1 - d) ? lc[(size_t)d * B + a] : 0.f;
+    dg[d] = (loader && d < n) ? lc[(size_t)d * B] : 0.f;
+  }
+  __syncthreads();
+  for (int j0 = 0; j0 < n; j0 += D) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const int j = j0 + d;
+      if (j < n) {
+        if (act && a <= n - 1 - j) {
+          const float m = pf[d];
+          const int dst = (j + a) % WB, src = j % WB;
+#pragma unroll
+          for (int q = 0; q < RG; ++q) win[q * WB + dst] -= m * win[q * WB + src];
+        }
+        const int jn = j + D;
+        pf[d] = (act && jn < n && a <= n - 1 - jn) ? lc[(size_t)jn * B + a] : 0.f;
+        __syncthreads();
+        if (loader) {
+          // row j is final: store y_j; bring row j + WB into its slot (first
+          // used PF steps from now)
+          const int slot = j % WB;
+          if (c < rg) Vc[j] = win[c * WB + slot] * dg[d];
+          if (j + WB < n && c < rg) cp_async4(&win[c * WB + slot], Vc + j + WB);
+          cp_async_commit();
+          dg[d] = jn < n ? lc[(size_t)jn * B] : 0.f;
+          cp_async_wait<PF - 1>();
+        }
+        __syncthreads();
+      }
+    }
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  // ---- backward: rows (j - WB, j] in the window, y read back ----
+  for (int i = tid; i < min(WB, n) * RG; i += blockDim.x) {
+    const int cc = i / min(WB, n), k = i % min(WB, n);
+    const int row = n - 1 - k;
+    win[cc * WB + row % WB] = cc < rg ? V[(int64_t)(r0 + cc) * ntot + base + row] : 0.f;
+  }
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const int j = n - 1 - d;
+    pf[d] = (act && j >= 0 && a <= j) ? uc[(size_t)j * B + a] : 0.f;
+    dg[d] = (loader && j >= 0) ? uc[(size_t)j * B] : 0.f;
+  }
+  __syncthreads();
+  for (int j0 = n - 1; j0 >= 0; j0 -= D) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const int j = j0 - d;
+      if (j >= 0) {
+        if (act && a <= j) {
+          const float m = pf[d];
+          const int dst = (j - a) % WB, src = j % WB;
+#pragma unroll
+          for (int q = 0; q < RG; ++q) win[q * WB + dst] -= m * win[q * WB + src];
+        }
+        const int jn = j - D;
+        pf[d] = (act && jn >= 0 && a <= jn) ? uc[(size_t)jn * B + a] : 0.f;
+        __syncthreads();
+        if (loader) {
+          const int slot = j % WB;
+          if (c < rg) Vc[j] = win[c * WB + slot] * dg[d];
+          if (j - WB >= 0 && c < rg) cp_async4(&win[c * WB + slot], Vc + j - WB);
+          cp_async_commit();
+          dg[d] = jn >= 0 ? uc[(size_t)jn * B] : 0.f;
+          cp_async_wait<PF - 1>();
+        }
+        __syncthreads();
+      }
+    }
+  }
+  cp_async_wait<0>();
 }
 
 // c[s][r] = 2 W beta_s x0[pos(s)][r]
 template <class FT, class WT>
 __global__ void batch_const_kernel(const int32_t* __restrict__ port_pos, const double* __restrict__ beta,
                                    const FT* __restrict__ x0, double W, WT* __restrict__ c,
-                                   int64_t nports, int R) {
+                                   int64_t nports, int R, int64_t n) {
   const int64_t total = nports * R;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s = i / R;
     const int r = (int)(i % R);
-    c[i] = (WT)(2.0 * W * beta[s] * (double)x0[(int64_t)port_pos[s] * R + r]);
+    c[i] = (WT)(2.0 * W * beta[s] * (double)x0[(int64_t)r * n + port_pos[s]]);
   }
 }
 
@@ -174,7 +370,7 @@ __global__ void batch_const_kernel(const int32_t* __restrict__ port_pos, const d
 template <class FT, class WT>
 __global__ void batch_inject_kernel(const int32_t* __restrict__ port_pos, const uint8_t* __restrict__ run,
                                     const double* __restrict__ beta, const WT* __restrict__ st,
-                                    FT* __restrict__ V, int64_t nports, int R) {
+                                    FT* __restrict__ V, int64_t nports, int R, int64_t n) {
   const int64_t total = nports * R;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -184,7 +380,7 @@ __global__ void batch_inject_kernel(const int32_t* __restrict__ port_pos, const 
     if (!nr) continue;
     double acc = 0.0;
     for (int q = 0; q < nr; ++q) acc += beta[s + q] * (double)st[(s + q) * 2 * R + r];
-    V[(int64_t)port_pos[s] * R + r] += (FT)acc;
+    V[(int64_t)r * n + port_pos[s]] += (FT)acc;
   }
 }
 
@@ -289,6 +485,7 @@ __device__ void batch_finish(BatchCtrl* __restrict__ ctrl, const double* __restr
     }
     if (!flag && k >= ctrl->k_max) flag = 2;
     ctrl->counter = 0u;
+    ctrl->work = 0u;
     ctrl->k = k + 1;
     __threadfence();
     ctrl->flag = flag;
@@ -301,7 +498,7 @@ template <class TT, class WT, class AT>
 __global__ void __launch_bounds__(256) batch_sweep_kernel(
     const TT* __restrict__ T, const int64_t* __restrict__ T_off, const int32_t* __restrict__ T_ld,
     const int32_t* __restrict__ port_off, const int32_t* __restrict__ item_tile,
-    const int32_t* __restrict__ item_m0, int nitems, const int32_t* __restrict__ twin,
+    const int32_t* __restrict__ item_m0, const int32_t* __restrict__ item_order, int nitems, const int32_t* __restrict__ twin,
     const double* __restrict__ g, const uint8_t* __restrict__ run, const WT* __restrict__ c,
     WT* __restrict__ state, int64_t nports, int R, double W, BatchCtrl* __restrict__ ctrl,
     double* __restrict__ partials, const double* __restrict__ tol2, double* __restrict__ hist,
@@ -321,7 +518,13 @@ __global__ void __launch_bounds__(256) batch_sweep_kernel(
   __syncthreads();
   if (s_flag) return;
   const int k = s_k;
-  const int item = blockIdx.x;
+  // persistent: items of the longest-first work list until it is exhausted
+  __shared__ int s_item;
+  for (;;) {
+  if (tid == 0) s_item = (int)atomicAdd(&ctrl->work, 1u);
+  __syncthreads();
+  if (s_item >= nitems) break;
+  const int item = item_order[s_item];
   const int tile = item_tile[item];
   const int m0 = item_m0[item];
   const int p0 = port_off[tile];
@@ -383,11 +586,12 @@ __global__ void __launch_bounds__(256) batch_sweep_kernel(
     }
   }
   __syncthreads();
-  for (int r = tid; r < R; r += blockDim.x) partials[(size_t)item * R + r] = red[r];
+  for (int r = tid; r < R; r += blockDim.x) partials[(size_t)item * R + r] = k > 1 ? red[r] : 0.0;
   __syncthreads();
+  }  // work list
   if (tid == 0) {
     __threadfence();
-    s_last = atomicAdd(&ctrl->counter, 1u) == (unsigned)nitems - 1;
+    s_last = atomicAdd(&ctrl->counter, 1u) == gridDim.x - 1;
   }
   __syncthreads();
   if (!s_last) return;
@@ -428,7 +632,7 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
 __global__ void __launch_bounds__(128) batch_sweep_mma_kernel(
     const __nv_bfloat16* __restrict__ T, const int64_t* __restrict__ T_off,
     const int32_t* __restrict__ T_ld, const int32_t* __restrict__ port_off,
-    const int32_t* __restrict__ item_tile, const int32_t* __restrict__ item_m0, int nitems,
+    const int32_t* __restrict__ item_tile, const int32_t* __restrict__ item_m0, const int32_t* __restrict__ item_order, int nitems,
     const int32_t* __restrict__ twin, const double* __restrict__ g,
     const uint8_t* __restrict__ run, const float* __restrict__ c, float* __restrict__ state,
     int64_t nports, int R, double W, BatchCtrl* __restrict__ ctrl, double* __restrict__ partials,
@@ -450,7 +654,13 @@ __global__ void __launch_bounds__(128) batch_sweep_mma_kernel(
   __syncthreads();
   if (s_flag) return;
   const int k = s_k;
-  const int item = blockIdx.x;
+  // persistent: items of the longest-first work list until it is exhausted
+  __shared__ int s_item;
+  for (;;) {
+  if (tid == 0) s_item = (int)atomicAdd(&ctrl->work, 1u);
+  __syncthreads();
+  if (s_item >= nitems) break;
+  const int item = item_order[s_item];
   const int tile = item_tile[item];
   const int m0 = item_m0[item];
   const int p0 = port_off[tile];
@@ -551,11 +761,12 @@ __global__ void __launch_bounds__(128) batch_sweep_mma_kernel(
     }
   }
   __syncthreads();
-  for (int r = tid; r < R; r += blockDim.x) partials[(size_t)item * R + r] = red[r];
+  for (int r = tid; r < R; r += blockDim.x) partials[(size_t)item * R + r] = k > 1 ? red[r] : 0.0;
   __syncthreads();
+  }  // work list
   if (tid == 0) {
     __threadfence();
-    s_last = atomicAdd(&ctrl->counter, 1u) == (unsigned)nitems - 1;
+    s_last = atomicAdd(&ctrl->counter, 1u) == gridDim.x - 1;
   }
   __syncthreads();
   if (!s_last) return;
@@ -571,8 +782,32 @@ static int grid_n(int64_t work) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 152 * 16));
 }
 
+static vtm_status batch_band_solve_win(vtm_plan_s* P, float* V, int R, const float* Lc,
+                                       const float* Uc) {
+  constexpr int RG = 16, D = 8, PF = 8;
+  const int ngroups = (R + RG - 1) / RG;
+  const int threads = std::max(32, (std::max(P->max_bw, RG) + 31) / 32 * 32);
+  const size_t smem = (size_t)(P->max_bw + 1 + PF) * RG * sizeof(float);
+  if (threads > 1024 || smem > 200 * 1024) {
+    set_detail("batched solve: band too wide for the windowed batched band solve");
+    return VTM_EINVAL;
+  }
+  if (smem > 48 * 1024)
+    VTM_CUDA_TRY(cudaFuncSetAttribute(batch_band_solve_win_kernel<RG, D, PF>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  batch_band_solve_win_kernel<RG, D, PF><<<P->nparts * ngroups, threads, smem, P->stream>>>(
+      P->tabs.node_off.as<int32_t>(), P->tabs.bw.as<int32_t>(), P->tabs.band_off.as<int64_t>(), Lc,
+      Uc, V, R);
+  P->launch_count++;
+  VTM_CUDA_TRY(cudaGetLastError());
+  return VTM_OK;
+}
+
 template <class FT>
 static vtm_status batch_band_solve(vtm_plan_s* P, FT* V, int R, const FT* Lc, const FT* Uc) {
+  if constexpr (sizeof(FT) == 4) {
+    if (P->opts.batch_solve != 1) return batch_band_solve_win(P, V, R, Lc, Uc);
+  }
   constexpr int RG = 8;
   constexpr int D = 8;
   const int ngroups = (R + RG - 1) / RG;
@@ -589,6 +824,37 @@ static vtm_status batch_band_solve(vtm_plan_s* P, FT* V, int R, const FT* Lc, co
       Uc, V, R);
   P->launch_count++;
   VTM_CUDA_TRY(cudaGetLastError());
+  return VTM_OK;
+}
+
+// ||b_c - A x_c||^2 and ||b_c||^2 for every column (r: residuals out, may be NULL)
+static vtm_status batch_norms(vtm_plan_s* P, const double* x, const double* b, double* r, int R,
+                              std::vector<double>& rr, std::vector<double>& bb) {
+  const int gx = (int)std::max<int64_t>(1, std::min<int64_t>((P->n + 255) / 256, 152 * 2));
+  const int gy = (R + 7) / 8;
+  // fixed layout for up to 8 column groups: partials | out[128] | counters
+  VTM_TRY(dev_alloc(P->d_bres, ((size_t)gx * 8 * 16 + 2 * 64 + 64) * sizeof(double)));
+  double* partials = P->d_bres.as<double>();
+  double* out = partials + (size_t)gx * 8 * 16;
+  unsigned* counters = reinterpret_cast<unsigned*>(out + 2 * 64);
+  if (!P->bres_init) {
+    VTM_CUDA_TRY(cudaMemsetAsync(counters, 0, 64 * sizeof(double), P->stream));
+    P->bres_init = true;
+  }
+  batch_residual_norms_kernel<<<dim3(gx, gy), 256, 0, P->stream>>>(
+      P->d_rowptr.as<int64_t>(), P->d_colidx.as<int32_t>(), P->d_vals.as<double>(), x, b, r, P->n, R,
+      partials, counters, out);
+  P->launch_count++;
+  VTM_CUDA_TRY(cudaGetLastError());
+  std::vector<double> h(2 * R);
+  VTM_CUDA_TRY(cudaMemcpyAsync(h.data(), out, 2 * R * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
+  VTM_CUDA_TRY(cudaStreamSynchronize(P->stream));
+  rr.resize(R);
+  bb.resize(R);
+  for (int c = 0; c < R; ++c) {
+    rr[c] = h[2 * c];
+    bb[c] = h[2 * c + 1];
+  }
   return VTM_OK;
 }
 
@@ -613,6 +879,16 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
     }
     VTM_TRY(upload(P->d_item_tile, P->item_tile, s));
     VTM_TRY(upload(P->d_item_m0, P->item_m0, s));
+    // longest first: cost of an item ~ p_P * (outputs in the item)
+    std::vector<int32_t> order(P->item_tile.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int32_t)i;
+    auto cost = [&](int32_t i) {
+      const int32_t t = P->item_tile[i];
+      const int64_t pp = P->port_off[t + 1] - P->port_off[t];
+      return pp * std::min<int64_t>(kMB, pp - P->item_m0[i]);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cost(a) > cost(b); });
+    VTM_TRY(upload(P->d_item_order, order, s));
   }
   const int nitems = (int)P->item_tile.size();
   const bool lowp = prec != VTM_PREC_FP64;
@@ -636,10 +912,10 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
   // ||b_r||
   std::vector<double> bnorm(R), rnorm(R), rel(R);
   VTM_CUDA_TRY(cudaMemsetAsync(xacc, 0, (size_t)n * R * sizeof(double), s));
+  std::vector<double> rr2, bb2;
+  VTM_TRY(batch_norms(P, xacc, d_b, r, R, rr2, bb2));
   for (int c = 0; c < R; ++c) {
-    double rr, bb;
-    VTM_TRY(residual_pair(P, xacc + (size_t)c * n, d_b + (size_t)c * n, r + (size_t)c * n, &rr, &bb));
-    bnorm[c] = std::sqrt(bb);
+    bnorm[c] = std::sqrt(bb2[c]);
     rnorm[c] = bnorm[c];
   }
   info->sweeps = 0;
@@ -668,15 +944,15 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
       if (f32_solves)
         batch_const_kernel<float, float><<<g2, 256, 0, s>>>(P->d_port_pos.as<int32_t>(),
                                                            P->d_beta.as<double>(), V32, P->W,
-                                                           P->d_bc.as<float>(), npt, R);
+                                                           P->d_bc.as<float>(), npt, R, n);
       else if (lowp)
         batch_const_kernel<double, float><<<g2, 256, 0, s>>>(P->d_port_pos.as<int32_t>(),
                                                             P->d_beta.as<double>(), V, P->W,
-                                                            P->d_bc.as<float>(), npt, R);
+                                                            P->d_bc.as<float>(), npt, R, n);
       else
         batch_const_kernel<double, double><<<g2, 256, 0, s>>>(P->d_port_pos.as<int32_t>(),
                                                              P->d_beta.as<double>(), V, P->W,
-                                                             P->d_bc.as<double>(), npt, R);
+                                                             P->d_bc.as<double>(), npt, R, n);
       P->launch_count++;
       std::vector<double> t2(64, 1.0);
       for (int c = 0; c < R; ++c) {
@@ -694,44 +970,110 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
       VTM_CUDA_TRY(cudaMemsetAsync(P->d_bstate.p, 0, 4 * (size_t)npt * R * wsz, s));
       VTM_CUDA_TRY(cudaStreamSynchronize(s));
       if (sweeps_left <= 0) break;
+      // one launch of kernel variant kv (0: CUDA cores, 1: tensor cores) on a
+      // persistent grid of at most (SMs x resident CTAs) over the work list
+      // variant kv: bit 0 = tensor cores, bit 1 = one work item per CTA instead
+      // of a persistent grid (SMs x resident CTAs) over the work list
+      // (dry = true: only size the grid, before any graph capture)
+      auto launch_batch = [&](int kv, bool dry = false) {
+        auto go = [&](auto* kern, int threads, const auto* T, const auto* cc, auto* st) {
+          const int key = prec * 4 + kv;
+          if (P->batch_grid[key] == 0) {
+            int per_sm = 1;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+            int sms = 152;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
+            P->batch_grid[key] = (kv & 2) ? nitems
+                                          : std::max(1, std::min(nitems, std::max(per_sm, 1) * sms));
+          }
+          if (dry) return;
+          kern<<<P->batch_grid[key], threads, 0, s>>>(
+              T, P->tabs.T_off.as<int64_t>(), P->tabs.T_ld.as<int32_t>(), P->tabs.port_off.as<int32_t>(),
+              P->d_item_tile.as<int32_t>(), P->d_item_m0.as<int32_t>(), P->d_item_order.as<int32_t>(),
+              nitems, P->d_twin.as<int32_t>(), P->d_g.as<double>(), P->d_run.as<uint8_t>(), cc, st, npt,
+              R, P->W, P->d_bctrl.as<BatchCtrl>(), P->d_bpart.as<double>(), P->d_btol2.as<double>(),
+              nullptr, 0);
+        };
+        if (prec == VTM_PREC_BF16 && (kv & 1))
+          go(batch_sweep_mma_kernel, 128, P->d_T16.as<__nv_bfloat16>(), P->d_bc.as<float>(),
+             P->d_bstate.as<float>());
+        else if (prec == VTM_PREC_BF16)
+          go(batch_sweep_kernel<__nv_bfloat16, float, float>, 256, P->d_T16.as<__nv_bfloat16>(),
+             P->d_bc.as<float>(), P->d_bstate.as<float>());
+        else if (prec == VTM_PREC_FP32)
+          go(batch_sweep_kernel<float, float, float>, 256, P->d_T32.as<float>(), P->d_bc.as<float>(),
+             P->d_bstate.as<float>());
+        else
+          go(batch_sweep_kernel<double, double, double>, 256, P->d_T64.as<double>(), P->d_bc.as<double>(),
+             P->d_bstate.as<double>());
+      };
+      // autotune the variant once per plan and precision (tensor cores: BF16
+      // with R % 8 == 0)
+      int kv = 0;
+      {
+        if (P->batch_tuned[prec] == 0 || P->batch_tuned_R[prec] != R) {
+          float best = 1e30f;
+          for (int cand = 0; cand <= 3; ++cand) {
+            if ((cand & 1) && !(prec == VTM_PREC_BF16 && R % 8 == 0)) continue;
+            BatchCtrl tt = h;
+            tt.k_max = 1 << 30;
+            tt.stall = 0;
+            VTM_CUDA_TRY(cudaMemcpyAsync(P->d_bctrl.p, &tt, sizeof(tt), cudaMemcpyHostToDevice, s));
+            launch_batch(cand);
+            VTM_CUDA_TRY(cudaEventRecord(P->evs0, s));
+            for (int i = 0; i < 3; ++i) launch_batch(cand);
+            VTM_CUDA_TRY(cudaEventRecord(P->evs1, s));
+            VTM_CUDA_TRY(cudaGetLastError());
+            VTM_CUDA_TRY(cudaEventSynchronize(P->evs1));
+            float ms = 0.f;
+            VTM_CUDA_TRY(cudaEventElapsedTime(&ms, P->evs0, P->evs1));
+            P->launch_count += 4;
+            if (ms < best) {
+              best = ms;
+              P->batch_tuned[prec] = cand + 1;
+            }
+          }
+          P->batch_tuned_R[prec] = R;
+          VTM_CUDA_TRY(cudaMemcpyAsync(P->d_bctrl.p, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+          VTM_CUDA_TRY(cudaMemsetAsync(P->d_bstate.p, 0, 4 * (size_t)npt * R * wsz, s));
+        }
+        kv = P->batch_tuned[prec] - 1;
+      }
+      // batches of check_every launches replayed from a CUDA graph when the
+      // plan has its own stream
+      const int nb = P->opts.check_every;
+      launch_batch(kv, true);
+      cudaGraphExec_t gexec = nullptr;
+      if (P->stream && P->opts.graphs != 1) {
+        SweepGraph& G = P->batch_graph[prec];
+        const uint64_t key = ((uint64_t)kv << 56) ^ ((uint64_t)nb << 32) ^ ((uint64_t)R << 8) ^
+                             (uint64_t)(uintptr_t)P->d_bstate.p;
+        if (!G.exec || G.key != key) {
+          if (G.exec) cudaGraphExecDestroy(G.exec);
+          G.exec = nullptr;
+          cudaGraph_t graph = nullptr;
+          VTM_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+          for (int i = 0; i < nb; ++i) launch_batch(kv);
+          VTM_CUDA_TRY(cudaStreamEndCapture(s, &graph));
+          if (cudaGraphInstantiate(&G.exec, graph, 0) != cudaSuccess) {
+            G.exec = nullptr;
+            cudaGetLastError();
+          } else {
+            G.key = key;
+          }
+          cudaGraphDestroy(graph);
+        }
+        gexec = G.exec;
+      }
       int launched = 0;
       BatchCtrl hc{};
       while (true) {
-        const int m = std::min(P->opts.check_every, sweeps_left + 1 - launched);
+        const int m = gexec ? nb : std::min(nb, sweeps_left + 1 - launched);
         VTM_CUDA_TRY(cudaEventRecord(P->evs0, s));
-        for (int i = 0; i < m; ++i) {
-          if (prec == VTM_PREC_BF16 && R % 8 != 0)
-            batch_sweep_kernel<__nv_bfloat16, float, float><<<nitems, 256, 0, s>>>(
-                P->d_T16.as<__nv_bfloat16>(), P->tabs.T_off.as<int64_t>(), P->tabs.T_ld.as<int32_t>(),
-                P->tabs.port_off.as<int32_t>(), P->d_item_tile.as<int32_t>(),
-                P->d_item_m0.as<int32_t>(), nitems, P->d_twin.as<int32_t>(), P->d_g.as<double>(),
-                P->d_run.as<uint8_t>(), P->d_bc.as<float>(), P->d_bstate.as<float>(), npt, R, P->W,
-                P->d_bctrl.as<BatchCtrl>(), P->d_bpart.as<double>(), P->d_btol2.as<double>(),
-                nullptr, 0);
-          else if (prec == VTM_PREC_BF16)
-            batch_sweep_mma_kernel<<<nitems, 128, 0, s>>>(
-                P->d_T16.as<__nv_bfloat16>(), P->tabs.T_off.as<int64_t>(), P->tabs.T_ld.as<int32_t>(),
-                P->tabs.port_off.as<int32_t>(), P->d_item_tile.as<int32_t>(),
-                P->d_item_m0.as<int32_t>(), nitems, P->d_twin.as<int32_t>(), P->d_g.as<double>(),
-                P->d_run.as<uint8_t>(), P->d_bc.as<float>(), P->d_bstate.as<float>(), npt, R, P->W,
-                P->d_bctrl.as<BatchCtrl>(), P->d_bpart.as<double>(), P->d_btol2.as<double>(),
-                nullptr, 0);
-          else if (prec == VTM_PREC_FP32)
-            batch_sweep_kernel<float, float, float><<<nitems, 256, 0, s>>>(
-                P->d_T32.as<float>(), P->tabs.T_off.as<int64_t>(), P->tabs.T_ld.as<int32_t>(),
-                P->tabs.port_off.as<int32_t>(), P->d_item_tile.as<int32_t>(),
-                P->d_item_m0.as<int32_t>(), nitems, P->d_twin.as<int32_t>(), P->d_g.as<double>(),
-                P->d_run.as<uint8_t>(), P->d_bc.as<float>(), P->d_bstate.as<float>(), npt, R, P->W,
-                P->d_bctrl.as<BatchCtrl>(), P->d_bpart.as<double>(), P->d_btol2.as<double>(),
-                nullptr, 0);
-          else
-            batch_sweep_kernel<double, double, double><<<nitems, 256, 0, s>>>(
-                P->d_T64.as<double>(), P->tabs.T_off.as<int64_t>(), P->tabs.T_ld.as<int32_t>(),
-                P->tabs.port_off.as<int32_t>(), P->d_item_tile.as<int32_t>(),
-                P->d_item_m0.as<int32_t>(), nitems, P->d_twin.as<int32_t>(), P->d_g.as<double>(),
-                P->d_run.as<uint8_t>(), P->d_bc.as<double>(), P->d_bstate.as<double>(), npt, R,
-                P->W, P->d_bctrl.as<BatchCtrl>(), P->d_bpart.as<double>(), P->d_btol2.as<double>(),
-                nullptr, 0);
+        if (gexec) {
+          VTM_CUDA_TRY(cudaGraphLaunch(gexec, s));
+        } else {
+          for (int i = 0; i < m; ++i) launch_batch(kv);
         }
         VTM_CUDA_TRY(cudaGetLastError());
         launched += m;
@@ -756,18 +1098,18 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
         batch_gather_kernel<float><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, V32, n, R);
         batch_inject_kernel<float, float><<<g2, 256, 0, s>>>(
             P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(), P->d_beta.as<double>(),
-            P->d_bstate.as<float>() + (size_t)slot * npt * 2 * R, V32, npt, R);
+            P->d_bstate.as<float>() + (size_t)slot * npt * 2 * R, V32, npt, R, n);
         VTM_TRY(batch_band_solve<float>(P, V32, R, P->d_Lc32.as<float>(), P->d_Uc32.as<float>()));
       } else {
         batch_gather_kernel<double><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, V, n, R);
         if (lowp)
           batch_inject_kernel<double, float><<<g2, 256, 0, s>>>(
               P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(), P->d_beta.as<double>(),
-              P->d_bstate.as<float>() + (size_t)slot * npt * 2 * R, V, npt, R);
+              P->d_bstate.as<float>() + (size_t)slot * npt * 2 * R, V, npt, R, n);
         else
           batch_inject_kernel<double, double><<<g2, 256, 0, s>>>(
               P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(), P->d_beta.as<double>(),
-              P->d_bstate.as<double>() + (size_t)slot * npt * 2 * R, V, npt, R);
+              P->d_bstate.as<double>() + (size_t)slot * npt * 2 * R, V, npt, R, n);
         VTM_TRY(batch_band_solve<double>(P, V, R, P->d_Lc.as<double>(), P->d_Uc.as<double>()));
       }
     } else {
@@ -783,9 +1125,9 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
     info->outer_steps = outer + 1;
     bool all_ok = true, bad = false;
     double worst = 0.0;
+    VTM_TRY(batch_norms(P, xacc, d_b, r, R, rr2, bb2));
     for (int c = 0; c < R; ++c) {
-      double rr, bb;
-      VTM_TRY(residual_pair(P, xacc + (size_t)c * n, d_b + (size_t)c * n, r + (size_t)c * n, &rr, &bb));
+      const double rr = rr2[c];
       rnorm[c] = std::sqrt(rr);
       rel[c] = bnorm[c] > 0 ? rnorm[c] / bnorm[c] : rnorm[c];
       worst = std::max(worst, rel[c]);

@@ -258,6 +258,44 @@ __global__ void convert_bf16_kernel(const double* __restrict__ a, __nv_bfloat16*
     b[i] = __float2bfloat16_rn((float)a[i]);
 }
 
+// Packed symmetric copy of the reflection matrices (symmetric plans, scalar
+// W: T_P is symmetric, Sec. VIII).  The two stored halves of T_P differ only
+// by the rounding of their column solves; their mean is packed.
+__device__ __forceinline__ void store_low(float* p, double v) { *p = (float)v; }
+__device__ __forceinline__ void store_low(__nv_bfloat16* p, double v) {
+  *p = __float2bfloat16_rn((float)v);  // same rounding as the full BF16 copy
+}
+
+template <class TT>
+__global__ void pack_sym_kernel(const double* __restrict__ T64, const TileDesc* __restrict__ tdesc,
+                                TT* __restrict__ Tp) {
+  const TileDesc d = tdesc[blockIdx.x];
+  const int nb = (d.p + kSymB - 1) / kSymB;
+  const int nel = nb * (nb + 1) / 2 * kSymB * kSymB;
+  const double* Tb = T64 + d.T_off;
+  for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+    int blk = e / (kSymB * kSymB);
+    const int w = e % (kSymB * kSymB);
+    int bi = 0;
+    while (blk >= nb - bi) {
+      blk -= nb - bi;
+      ++bi;
+    }
+    const int bj = bi + blk;
+    const int s = bi * kSymB + w / kSymB, q = bj * kSymB + w % kSymB;
+    double v = 0.0;
+    if (s < d.p && q < d.p) v = 0.5 * (Tb[(size_t)q * d.ld + s] + Tb[(size_t)s * d.ld + q]);
+    store_low(Tp + d.Tp_off + e, v);
+  }
+}
+
+// Packed copies are kept for symmetric VTM plans whose sub-circuits have at
+// most 256 ports (16 blocks a side), in the plan's low precision.
+static bool packed_eligible(const vtm_plan_s* P) {
+  return P->symmetric && !P->general && P->max_ports <= 16 * kSymB &&
+         !P->port_node.empty() && P->opts.precision != VTM_PREC_FP64;
+}
+
 vtm_status build_reflections(vtm_plan_s* P) {
   cudaStream_t s = P->stream;
   const int64_t npt = (int64_t)P->port_node.size();
@@ -294,6 +332,18 @@ vtm_status build_reflections(vtm_plan_s* P) {
   } else if (P->opts.precision == VTM_PREC_BF16) {
     VTM_TRY(dev_alloc(P->d_T16, ne * sizeof(__nv_bfloat16)));
     convert_bf16_kernel<<<1216, 256, 0, s>>>(P->d_T64.as<double>(), P->d_T16.as<__nv_bfloat16>(), ne);
+  }
+  if (packed_eligible(P)) {
+    const int64_t np = std::max<int64_t>(P->Tp_elems, 8);
+    if (P->opts.precision == VTM_PREC_FP32) {
+      VTM_TRY(dev_alloc(P->d_Tp32, np * sizeof(float)));
+      pack_sym_kernel<float><<<P->nparts, 256, 0, s>>>(P->d_T64.as<double>(),
+                                                       P->d_tdesc.as<TileDesc>(), P->d_Tp32.as<float>());
+    } else {
+      VTM_TRY(dev_alloc(P->d_Tp16, np * sizeof(__nv_bfloat16)));
+      pack_sym_kernel<__nv_bfloat16><<<P->nparts, 256, 0, s>>>(
+          P->d_T64.as<double>(), P->d_tdesc.as<TileDesc>(), P->d_Tp16.as<__nv_bfloat16>());
+    }
   }
   VTM_CUDA_TRY(cudaGetLastError());
   VTM_CUDA_TRY(cudaStreamSynchronize(s));

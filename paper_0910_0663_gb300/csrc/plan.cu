@@ -297,8 +297,10 @@ static vtm_status build_structure(vtm_plan_s* P, std::vector<CutPair>& pairs) {
   // reflection-matrix layout: T^T blocks with rows padded to 8 elements
   P->T_ld.assign(np, 0);
   P->T_off.assign(np, 0);
-  int64_t toff = 0;
+  P->Tp_off.assign(np, 0);
+  int64_t toff = 0, tpoff = 0;
   P->sum_p2 = 0;
+  P->sum_tri = 0;
   P->max_ports = 0;
   for (int32_t t = 0; t < np; ++t) {
     int32_t p = P->port_off[t + 1] - P->port_off[t];
@@ -307,9 +309,14 @@ static vtm_status build_structure(vtm_plan_s* P, std::vector<CutPair>& pairs) {
     P->T_off[t] = toff;
     toff += (int64_t)p * ld;
     P->sum_p2 += (int64_t)p * p;
+    P->sum_tri += (int64_t)p * (p + 1) / 2;
     P->max_ports = std::max(P->max_ports, p);
+    const int64_t nb = (p + kSymB - 1) / kSymB;
+    P->Tp_off[t] = tpoff;
+    tpoff += nb * (nb + 1) / 2 * kSymB * kSymB;
   }
   P->T_elems = toff;
+  P->Tp_elems = tpoff;
   return VTM_OK;
 }
 
@@ -601,13 +608,14 @@ std::vector<DevBuf*> vtm_plan_s::all_bufs() {
   return {&tabs.node_off, &tabs.bw, &tabs.band_off, &tabs.port_off, &tabs.T_off, &tabs.T_ld,
           &tabs.order, &d_rowptr, &d_colidx, &d_vals, &d_perm, &d_Lc, &d_Uc, &d_Lc32, &d_Uc32, &d_v32,
           &d_port_loc, &d_port_pos, &d_tdesc,
-          &d_twin, &d_g, &d_beta, &d_run, &d_T64, &d_T32, &d_T16, &d_c64, &d_c32, &d_state64,
+          &d_twin, &d_g, &d_beta, &d_run, &d_T64, &d_T32, &d_T16, &d_Tp32, &d_Tp16, &d_c64, &d_c32, &d_state64,
           &d_state32, &d_v, &d_v2, &d_xacc, &d_r, &d_bcol, &d_partials, &d_ctrl, &d_hist,
           &d_err, &d_red, &d_in_off, &d_out_off, &d_in_src, &d_in_kind, &d_in_twin,
           &d_in_own_out, &d_in_loc, &d_res_perm, &d_res_run, &d_out_loc, &d_in_coef,
           &d_in_sigma, &d_out_scale, &d_out_diag, &d_E_off, &d_E_ld, &d_E, &d_cg, &d_gin,
-          &d_gout, &d_in_tile, &d_item_tile, &d_item_m0, &d_bV, &d_bV32, &d_bstate, &d_bc, &d_bpart,
-          &d_btol2, &d_bctrl};
+          &d_gout, &d_in_tile, &d_item_tile, &d_item_m0, &d_item_order, &d_bV, &d_bV32, &d_bstate,
+          &d_bc, &d_bpart,
+          &d_btol2, &d_bctrl, &d_bres};
 }
 
 static void fill_default_opts(vtm_opts* o) {
@@ -623,6 +631,10 @@ extern "C" vtm_status vtm_set_opts(vtm_plan_t P, const vtm_opts* opts) {
   if (opts) o = *opts;
   if (o.precision < 0 || o.precision > 2 || o.history_len < 0 || (o.history_len > 0 && !o.history)) {
     set_detail("vtm_set_opts: bad precision or history");
+    return VTM_EINVAL;
+  }
+  if (o.sweep_kernel < 0 || o.sweep_kernel > 6) {
+    set_detail("vtm_set_opts: sweep_kernel must be 0..6");
     return VTM_EINVAL;
   }
   bool prec_changed = o.precision != P->opts.precision;
@@ -744,7 +756,7 @@ extern "C" vtm_status vtm_plan(int64_t n, const int64_t* rowptr, const int32_t* 
   for (int32_t i = 0; i < nparts; ++i) {
     const int32_t t = order[i];
     tdesc[i] = TileDesc{t, P->port_off[t], P->port_off[t + 1] - P->port_off[t], P->T_ld[t],
-                        P->T_off[t], 0};
+                        P->T_off[t], P->Tp_off[t]};
   }
   if ((st = upload(P->d_tdesc, tdesc, s)) != VTM_OK) return fail(st);
   if ((st = upload(P->d_port_loc, P->port_loc, s)) != VTM_OK) return fail(st);
@@ -840,10 +852,13 @@ extern "C" vtm_status vtm_plan_get_stats(vtm_plan_t P, vtm_plan_stats* s) {
   s->max_nodes = P->max_nodes;
   s->max_band = P->max_bw;
   s->symmetric = P->symmetric ? 1 : 0;
-  s->t_bytes = (int64_t)(P->d_T64.bytes + P->d_T32.bytes + P->d_T16.bytes + P->d_E.bytes);
+  s->t_bytes = (int64_t)(P->d_T64.bytes + P->d_T32.bytes + P->d_T16.bytes + P->d_E.bytes +
+                         P->d_Tp32.bytes + P->d_Tp16.bytes);
   s->factor_bytes = (int64_t)(P->d_Lc.bytes + P->d_Uc.bytes);
   s->sweep_kernel = P->tuned_kernel[P->opts.precision] ? P->tuned_kernel[P->opts.precision]
                                                         : P->opts.sweep_kernel;
+  s->sum_tri = P->sum_tri;
+  s->packed_bytes = (int64_t)(P->d_Tp32.bytes + P->d_Tp16.bytes);
   return VTM_OK;
 }
 

@@ -116,6 +116,39 @@ __device__ double block_sum_value(double v) {
   return tot;
 }
 
+// The last CTA of sweep k closes the sweep: it records the residual of sweep
+// k-1 (reduced by that CTA in a fixed order) and decides whether to go on.
+// flag 1: converged, 2: sweep limit, 3: diverged or not finite, 4: stalled
+// (rounding floor of a low-precision inner solve); a flag already set (a
+// bounded wait that timed out) is kept.
+__device__ void sweep_decide(SweepCtrl* ctrl, int k, double tot, double* hist, int hist_len) {
+  int flag = 0;
+  if (k > 1) {
+    const int ks = k - 1;
+    if (hist && ks <= hist_len) hist[ks - 1] = sqrt(tot / ctrl->bnorm2);
+    if (ks == 1) ctrl->first_res2 = tot;
+    ctrl->last_res2 = tot;
+    if (ks == 1 || tot < 0.81 * ctrl->best_res2) {
+      ctrl->best_res2 = tot;
+      ctrl->best_k = ks;
+    }
+    if (!isfinite(tot) || (ks > 1 && tot > 1e12 * ctrl->first_res2 && ctrl->first_res2 > 0)) {
+      flag = 3;
+    } else if (tot <= ctrl->tol2) {
+      flag = 1;
+      ctrl->conv_sweep = ks;
+    } else if (ctrl->stall > 0 && ks - ctrl->best_k >= ctrl->stall) {
+      flag = 4;
+      ctrl->conv_sweep = ks;
+    }
+  }
+  if (!flag && k >= ctrl->k_max) flag = 2;
+  ctrl->counter = 0u;
+  ctrl->k = k + 1;
+  __threadfence();
+  if (ctrl->flag == 0) ctrl->flag = flag;
+}
+
 // r = b - A x (global order, FP64), ||r||^2 and ||b||^2 reduced in a fixed
 // order; out[0] = ||r||^2, out[1] = ||b||^2.  counter must be 0 on entry and
 // is left 0.
@@ -256,33 +289,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(
   if (!s_last) return;
   __threadfence();
   const double tot = block_sum_fixed(partials, nparts);
-  if (threadIdx.x == 0) {
-    int flag = 0;
-    if (k > 1) {
-      const int ks = k - 1;
-      if (hist && ks <= hist_len) hist[ks - 1] = sqrt(tot / ctrl->bnorm2);
-      if (ks == 1) ctrl->first_res2 = tot;
-      ctrl->last_res2 = tot;
-      if (ks == 1 || tot < 0.81 * ctrl->best_res2) {
-        ctrl->best_res2 = tot;
-        ctrl->best_k = ks;
-      }
-      if (!isfinite(tot) || (ks > 1 && tot > 1e12 * ctrl->first_res2 && ctrl->first_res2 > 0)) {
-        flag = 3;
-      } else if (tot <= ctrl->tol2) {
-        flag = 1;
-        ctrl->conv_sweep = ks;
-      } else if (ctrl->stall > 0 && ks - ctrl->best_k >= ctrl->stall) {
-        flag = 4;  // rounding floor of a low-precision inner solve
-        ctrl->conv_sweep = ks;
-      }
-    }
-    if (!flag && k >= ctrl->k_max) flag = 2;
-    ctrl->counter = 0u;
-    ctrl->k = k + 1;
-    __threadfence();
-    ctrl->flag = flag;
-  }
+  if (threadIdx.x == 0) sweep_decide(ctrl, k, tot, hist, hist_len);
 }
 
 // ---------------------------------------------------------------------------
@@ -516,33 +523,7 @@ __global__ void __launch_bounds__(256) sweep_staged_kernel(
   if (!s_last) return;
   __threadfence();
   const double tot = block_sum_fixed(partials, nparts);
-  if (tid == 0) {
-    int flag = 0;
-    if (k > 1) {
-      const int ks = k - 1;
-      if (hist && ks <= hist_len) hist[ks - 1] = sqrt(tot / ctrl->bnorm2);
-      if (ks == 1) ctrl->first_res2 = tot;
-      ctrl->last_res2 = tot;
-      if (ks == 1 || tot < 0.81 * ctrl->best_res2) {
-        ctrl->best_res2 = tot;
-        ctrl->best_k = ks;
-      }
-      if (!isfinite(tot) || (ks > 1 && tot > 1e12 * ctrl->first_res2 && ctrl->first_res2 > 0)) {
-        flag = 3;
-      } else if (tot <= ctrl->tol2) {
-        flag = 1;
-        ctrl->conv_sweep = ks;
-      } else if (ctrl->stall > 0 && ks - ctrl->best_k >= ctrl->stall) {
-        flag = 4;
-        ctrl->conv_sweep = ks;
-      }
-    }
-    if (!flag && k >= ctrl->k_max) flag = 2;
-    ctrl->counter = 0u;
-    ctrl->k = k + 1;
-    __threadfence();
-    if (ctrl->flag == 0) ctrl->flag = flag;
-  }
+  if (threadIdx.x == 0) sweep_decide(ctrl, k, tot, hist, hist_len);
 }
 
 // ---------------------------------------------------------------------------
@@ -706,33 +687,201 @@ __global__ void __launch_bounds__(NT) sweep_vec_kernel(
   if (!s_last) return;
   __threadfence();
   const double tot = block_sum_fixed(partials, nparts);
+  if (threadIdx.x == 0) sweep_decide(ctrl, k, tot, hist, hist_len);
+}
+
+// ---------------------------------------------------------------------------
+// Packed symmetric sweep.  With scalar W and symmetric A, T_P is symmetric
+// (its spectrum is (W - lambda)/(W + lambda), Sec. VIII), so only the 16x16
+// blocks on and above the diagonal are stored: about half the bytes of the
+// full matrix, which is what an HBM-bound sweep pays for.  A warp takes one
+// block (bi, bj) at a time; lane l holds row r = l/2, columns 8(l%2)..+7 and
+//   * adds T_blk w(bj) into the partial of row block bi (two-lane shuffle);
+//   * for bi < bj adds T_blk^T w(bi) into the partial of row block bj: the
+//     16-row sums are a reduce-scatter over lane bits 4, 3, 2 followed by
+//     one exchange over bit 1 (8 shuffles, a fixed summation tree).
+// part[a][b] holds block b's contribution to row block a; the outputs sum
+// them in the fixed order b = 0..nb-1, so every sweep is bitwise repeatable.
+// ---------------------------------------------------------------------------
+
+template <class TT>
+struct SymLoad;
+template <> struct SymLoad<float> {
+  struct raw {
+    float4 a, b;
+  };
+  __device__ static raw load(const float* p) {
+    raw r;
+    r.a = __ldg(reinterpret_cast<const float4*>(p));
+    r.b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+    return r;
+  }
+  __device__ static void unpack(const raw& v, float (&o)[8]) {
+    o[0] = v.a.x; o[1] = v.a.y; o[2] = v.a.z; o[3] = v.a.w;
+    o[4] = v.b.x; o[5] = v.b.y; o[6] = v.b.z; o[7] = v.b.w;
+  }
+};
+template <> struct SymLoad<__nv_bfloat16> {
+  using raw = uint4;
+  __device__ static raw load(const __nv_bfloat16* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }
+  __device__ static void unpack(const raw& v, float (&o)[8]) {
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float2 f = __bfloat1622float2(h[i]);
+      o[2 * i] = f.x;
+      o[2 * i + 1] = f.y;
+    }
+  }
+};
+
+template <class TT, int NT, int KB>
+__global__ void __launch_bounds__(NT) sweep_sym_kernel(
+    const TT* __restrict__ Tp, const TileDesc* __restrict__ tdesc,
+    const int32_t* __restrict__ twin, const double* __restrict__ g,
+    const uint8_t* __restrict__ run, const float* __restrict__ c, float* __restrict__ state,
+    int64_t nports, double W, SweepCtrl* __restrict__ ctrl, double* __restrict__ partials,
+    double* __restrict__ hist, int hist_len, int nparts, int pp_max) {
+  using LD = SymLoad<TT>;
+  constexpr int NW = NT / 32;
+  constexpr int B = kSymB;
+  constexpr unsigned FULL = 0xffffffffu;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_k, s_flag;
+  __shared__ bool s_last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const TileDesc dsc = tdesc[blockIdx.x];
+  const int tile = dsc.tile, p0 = dsc.p0, p = dsc.p;
+  const int nb = (p + B - 1) / B;
+  const int nblk = nb * (nb + 1) / 2;
+  const int r = lane >> 1, h = lane & 1;
+  const TT* Tl = Tp + dsc.Tp_off + r * B + h * 8;
+  float* w_in = reinterpret_cast<float*>(smem_raw);
+  float* rs = w_in + pp_max;
+  float* part = rs + pp_max;
+  // the first blocks of T go out before anything else (they need no waves)
+  typename LD::raw buf[KB];
+#pragma unroll
+  for (int b = 0; b < KB; ++b) {
+    const int kk = warp + b * NW;
+    if (kk < nblk) buf[b] = LD::load(Tl + (size_t)kk * B * B);
+  }
   if (tid == 0) {
-    int flag = 0;
-    if (k > 1) {
-      const int ks = k - 1;
-      if (hist && ks <= hist_len) hist[ks - 1] = sqrt(tot / ctrl->bnorm2);
-      if (ks == 1) ctrl->first_res2 = tot;
-      ctrl->last_res2 = tot;
-      if (ks == 1 || tot < 0.81 * ctrl->best_res2) {
-        ctrl->best_res2 = tot;
-        ctrl->best_k = ks;
-      }
-      if (!isfinite(tot) || (ks > 1 && tot > 1e12 * ctrl->first_res2 && ctrl->first_res2 > 0)) {
-        flag = 3;
-      } else if (tot <= ctrl->tol2) {
-        flag = 1;
-        ctrl->conv_sweep = ks;
-      } else if (ctrl->stall > 0 && ks - ctrl->best_k >= ctrl->stall) {
-        flag = 4;
-        ctrl->conv_sweep = ks;
+    s_k = *((volatile int*)&ctrl->k);
+    s_flag = *((volatile int*)&ctrl->flag);
+  }
+  __syncthreads();
+  if (s_flag) return;
+  const int k = s_k;
+  const float* prev = state + (size_t)((k - 1) & 1) * nports * 2;
+  float* cur = state + (size_t)(k & 1) * nports * 2;
+  const float hW = (float)W, inv2W = (float)(0.5 / W);
+  for (int s = tid; s < nb * B; s += NT) {
+    float wi = 0.f, rc = 0.f;
+    if (k > 1 && s < p) {
+      const int gs = p0 + s;
+      const int tw = twin[gs];
+      const float wi_t = prev[2 * tw], wo_t = prev[2 * tw + 1];
+      const float wi_s = prev[2 * gs], wo_s = prev[2 * gs + 1];
+      wi = wo_t;
+      const float gg = (float)g[gs];
+      const float us = (wi_s + wo_s) * inv2W, ut = (wi_t + wo_t) * inv2W;
+      rc = 0.5f * ((hW - 2 * gg) * us + (hW + 2 * gg) * ut - wi_s - wi_t);
+    }
+    w_in[s] = wi;  // zero past p: the padding of the last block
+    rs[s] = rc;
+  }
+  __syncthreads();
+  float sq = 0.f;
+  if (k > 1) {
+    for (int s = tid; s < p; s += NT) {
+      const int nr = run[p0 + s];
+      if (nr) {
+        float rr = 0.f;
+        for (int q = 0; q < nr; ++q) rr += rs[s + q];
+        sq += rr * rr;
       }
     }
-    if (!flag && k >= ctrl->k_max) flag = 2;
-    ctrl->counter = 0u;
-    ctrl->k = k + 1;
-    __threadfence();
-    ctrl->flag = flag;
   }
+  const double tile_sq = block_sum_value((double)sq);
+  int bi = 0, off = warp;  // block warp + i NW is (bi, bi + off) once off < nb - bi
+  for (int base = 0; base < nblk; base += KB * NW) {
+#pragma unroll
+    for (int b = 0; b < KB; ++b) {
+      const int kk = warp + base + b * NW;
+      if (kk < nblk) {
+        while (off >= nb - bi) {
+          off -= nb - bi;
+          ++bi;
+        }
+        const int bj = bi + off;
+        float v[8];
+        LD::unpack(buf[b], v);
+        const int kn = kk + KB * NW;
+        if (kn < nblk) buf[b] = LD::load(Tl + (size_t)kn * B * B);
+        const float4 c0 = *reinterpret_cast<const float4*>(w_in + bj * B + h * 8);
+        const float4 c1 = *reinterpret_cast<const float4*>(w_in + bj * B + h * 8 + 4);
+        float a = v[0] * c0.x;
+        a = fmaf(v[1], c0.y, a);
+        a = fmaf(v[2], c0.z, a);
+        a = fmaf(v[3], c0.w, a);
+        a = fmaf(v[4], c1.x, a);
+        a = fmaf(v[5], c1.y, a);
+        a = fmaf(v[6], c1.z, a);
+        a = fmaf(v[7], c1.w, a);
+        a += __shfl_xor_sync(FULL, a, 1);
+        if (h == 0) part[(bi * nb + bj) * B + r] = a;
+        if (bi != bj) {
+          const float wr = w_in[bi * B + r];
+          float u[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) u[j] = v[j] * wr;
+          const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+          float t4[4], t2[2];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float send = b4 ? u[i] : u[i + 4];
+            const float keep = b4 ? u[i + 4] : u[i];
+            t4[i] = keep + __shfl_xor_sync(FULL, send, 16);
+          }
+#pragma unroll
+          for (int i = 0; i < 2; ++i) {
+            const float send = b3 ? t4[i] : t4[i + 2];
+            const float keep = b3 ? t4[i + 2] : t4[i];
+            t2[i] = keep + __shfl_xor_sync(FULL, send, 8);
+          }
+          float t1;
+          {
+            const float send = b2 ? t2[0] : t2[1];
+            const float keep = b2 ? t2[1] : t2[0];
+            t1 = keep + __shfl_xor_sync(FULL, send, 4);
+          }
+          t1 += __shfl_xor_sync(FULL, t1, 2);
+          const int jc = (b4 ? 4 : 0) + (b3 ? 2 : 0) + (b2 ? 1 : 0);
+          if (!(lane & 2)) part[(bj * nb + bi) * B + h * 8 + jc] = t1;
+        }
+        off += NW;
+      }
+    }
+  }
+  __syncthreads();
+  for (int s = tid; s < p; s += NT) {
+    const int a = s / B, rr = s % B;
+    float acc = c[p0 + s];
+    for (int b = 0; b < nb; ++b) acc += part[(a * nb + b) * B + rr];
+    cur[2 * (p0 + s)] = w_in[s];
+    cur[2 * (p0 + s) + 1] = acc;
+  }
+  if (tid == 0) {
+    partials[tile] = tile_sq;
+    __threadfence();
+    s_last = atomicAdd(&ctrl->counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const double tot = block_sum_fixed(partials, nparts);
+  if (tid == 0) sweep_decide(ctrl, k, tot, hist, hist_len);
 }
 
 // ---------------------------------------------------------------------------
@@ -863,6 +1012,13 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   // vector-load kernel: every thread owns one vector column (nv <= threads)
   const bool vecload = (choice == 3 && nv_max <= 256) || (choice == 4 && nv_max <= 128);
   const size_t vec_smem = 2 * (size_t)ld_max * wsz + 256 * (size_t)vec * wsz + 16;
+  // packed symmetric kernel (FP32/BF16 copies exist only for symmetric plans)
+  const bool sym_ok = prec == VTM_PREC_FP32   ? P->d_Tp32.p != nullptr
+                      : prec == VTM_PREC_BF16 ? P->d_Tp16.p != nullptr
+                                              : false;
+  const int pp_max = std::max(kSymB, (P->max_ports + kSymB - 1) / kSymB * kSymB);
+  const int nb_max = pp_max / kSymB;
+  const size_t sym_smem = (2 * (size_t)pp_max + (size_t)nb_max * nb_max * kSymB) * sizeof(float) + 16;
   if (staged) {
     if (prec == VTM_PREC_FP64)
       VTM_CUDA_TRY(cudaFuncSetAttribute(sweep_staged_kernel<double, double, 2, 4>,
@@ -894,8 +1050,25 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   // keep as much of the low-precision reflection matrices in L2 as the
   // persisting carve-out allows (restored after the sweeps)
   L2Window l2win(P, prec);
-  // one sweep launch with kernel `kc` (1 direct, 2 staged, 3 vector loads)
+  // one sweep launch with kernel `kc` (1 direct, 2 staged, 3/4 vector loads with
+  // 256/128 threads, 5/6 packed symmetric with 128/256 threads)
   auto launch_one = [&](int kc) {
+    if (kc == 5 || kc == 6) {
+      auto go = [&](auto* kern, int nt, const auto* Tp) {
+        kern<<<P->nparts, nt, sym_smem, s>>>(
+            Tp, P->d_tdesc.as<TileDesc>(), P->d_twin.as<int32_t>(), P->d_g.as<double>(),
+            P->d_run.as<uint8_t>(), P->d_c32.as<float>(), P->d_state32.as<float>(), npt_, P->W,
+            P->d_ctrl.as<SweepCtrl>(), P->d_partials.as<double>(), hist, hist_len, P->nparts, pp_max);
+      };
+      if (prec == VTM_PREC_FP32) {
+        if (kc == 5) go(sweep_sym_kernel<float, 128, 4>, 128, P->d_Tp32.as<float>());
+        else go(sweep_sym_kernel<float, 256, 4>, 256, P->d_Tp32.as<float>());
+      } else {
+        if (kc == 5) go(sweep_sym_kernel<__nv_bfloat16, 128, 4>, 128, P->d_Tp16.as<__nv_bfloat16>());
+        else go(sweep_sym_kernel<__nv_bfloat16, 256, 4>, 256, P->d_Tp16.as<__nv_bfloat16>());
+      }
+      return;
+    }
     if (kc == 3 || kc == 4) {
       auto launch_vec = [&](auto* kern, int nt, const auto* T, const auto* c, auto* state) {
         kern<<<P->nparts, nt, vec_smem, s>>>(
@@ -903,27 +1076,21 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
             P->d_run.as<uint8_t>(), c, state, npt_, P->W, P->d_ctrl.as<SweepCtrl>(),
             P->d_partials.as<double>(), hist, hist_len, P->nparts, ld_max);
       };
-      if (kc == 3) {
-        if (prec == VTM_PREC_FP64)
-          launch_vec(sweep_vec_kernel<double, double, 2, 256, 8>, 256, P->d_T64.as<double>(),
-                     P->d_c64.as<double>(), P->d_state64.as<double>());
-        else if (prec == VTM_PREC_FP32)
-          launch_vec(sweep_vec_kernel<float, float, 4, 256, 8>, 256, P->d_T32.as<float>(),
-                     P->d_c32.as<float>(), P->d_state32.as<float>());
-        else
-          launch_vec(sweep_vec_kernel<__nv_bfloat16, float, 8, 256, 8>, 256,
-                     P->d_T16.as<__nv_bfloat16>(), P->d_c32.as<float>(), P->d_state32.as<float>());
-      } else {
-        if (prec == VTM_PREC_FP64)
-          launch_vec(sweep_vec_kernel<double, double, 2, 128, 4>, 128, P->d_T64.as<double>(),
-                     P->d_c64.as<double>(), P->d_state64.as<double>());
-        else if (prec == VTM_PREC_FP32)
-          launch_vec(sweep_vec_kernel<float, float, 4, 128, 4>, 128, P->d_T32.as<float>(),
-                     P->d_c32.as<float>(), P->d_state32.as<float>());
-        else
-          launch_vec(sweep_vec_kernel<__nv_bfloat16, float, 8, 128, 4>, 128,
-                     P->d_T16.as<__nv_bfloat16>(), P->d_c32.as<float>(), P->d_state32.as<float>());
-      }
+#define VTM_VEC_LAUNCH(NT, KB)                                                                  \
+  do {                                                                                          \
+    if (prec == VTM_PREC_FP64)                                                                  \
+      launch_vec(sweep_vec_kernel<double, double, 2, NT, KB>, NT, P->d_T64.as<double>(),        \
+                 P->d_c64.as<double>(), P->d_state64.as<double>());                             \
+    else if (prec == VTM_PREC_FP32)                                                             \
+      launch_vec(sweep_vec_kernel<float, float, 4, NT, KB>, NT, P->d_T32.as<float>(),           \
+                 P->d_c32.as<float>(), P->d_state32.as<float>());                               \
+    else                                                                                        \
+      launch_vec(sweep_vec_kernel<__nv_bfloat16, float, 8, NT, KB>, NT,                         \
+                 P->d_T16.as<__nv_bfloat16>(), P->d_c32.as<float>(), P->d_state32.as<float>()); \
+  } while (0)
+      if (kc == 3) VTM_VEC_LAUNCH(256, 8);
+      else VTM_VEC_LAUNCH(128, 4);
+#undef VTM_VEC_LAUNCH
       return;
     }
     if (kc == 2) {
@@ -951,7 +1118,8 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   // Autotuner: on the first solve of this precision, time every kernel that
   // fits on this plan's tiles (a few sweeps each, from a zero state that is
   // reset afterwards) and keep the fastest.
-  int kern = vecload ? choice : (staged ? 2 : 1);
+  const bool symload = (choice == 5 || choice == 6) && sym_ok;
+  int kern = (vecload || symload) ? choice : (staged ? 2 : 1);
   if (P->opts.sweep_kernel == 0) {
     if (P->tuned_kernel[prec] == 0) {
       const bool can_st = nv_max <= 4 * 256 && st_smem <= 200 * 1024;
@@ -959,8 +1127,10 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
       const bool can_vec128 = nv_max <= 128;
       float best = 1e30f;
       int best_k = 1;
-      for (int cand = 1; cand <= 4; ++cand) {
-        if ((cand == 2 && !can_st) || (cand == 3 && !can_vec) || (cand == 4 && !can_vec128)) continue;
+      for (int cand = 1; cand <= 6; ++cand) {
+        if ((cand == 2 && !can_st) || (cand == 3 && !can_vec) || (cand == 4 && !can_vec128) ||
+            (cand >= 5 && !sym_ok))
+          continue;
         if (cand == 2)
           VTM_CUDA_TRY(cudaFuncSetAttribute(
               prec == VTM_PREC_FP64 ? (const void*)sweep_staged_kernel<double, double, 2, 4>

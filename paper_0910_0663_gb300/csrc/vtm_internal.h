@@ -61,8 +61,13 @@ struct __align__(16) TileDesc {
   int32_t p;    // ports
   int32_t ld;   // row length of the T^T block
   int64_t T_off;
-  int64_t pad;
+  int64_t Tp_off;  // packed symmetric form: first element of the tile's 16x16 blocks
 };
+
+// Packed symmetric reflection matrices: T_P padded to pp = 16 ceil(p/16),
+// cut into 16x16 blocks, of which the upper triangle (bi <= bj) is stored,
+// row-major over (bi, bj), each block row-major.
+constexpr int kSymB = 16;
 
 // Offsets and sizes describing one tile-contiguous operator family.
 struct TileTables {
@@ -134,6 +139,9 @@ struct vtm_plan_s {
   std::vector<int64_t> T_off;
   int64_t T_elems = 0;
   int64_t sum_p2 = 0;
+  std::vector<int64_t> Tp_off;  // packed symmetric form (see TileDesc)
+  int64_t Tp_elems = 0;
+  int64_t sum_tri = 0;          // sum over tiles of p (p + 1) / 2
 
   // device copies
   vtm::TileTables tabs;
@@ -143,6 +151,7 @@ struct vtm_plan_s {
   vtm::DevBuf d_Lc32, d_Uc32, d_v32;       // FP32 factor copies and work vector (inner solves)
   vtm::DevBuf d_port_loc, d_port_pos, d_twin, d_g, d_beta, d_run, d_tdesc;
   vtm::DevBuf d_T64, d_T32, d_T16;         // reflection matrices (T^T blocks)
+  vtm::DevBuf d_Tp32, d_Tp16;              // packed symmetric copies (symmetric plans)
   vtm::DevBuf d_c64, d_c32;                // constant term of the sweep
   vtm::DevBuf d_state64, d_state32;        // [2][nports] (w_in, w_out) pairs
   vtm::DevBuf d_v, d_v2;                   // permuted work vectors [n]
@@ -193,7 +202,12 @@ struct vtm_plan_s {
 
   // batched right-hand sides (batch.cu)
   std::vector<int32_t> item_tile, item_m0;
-  vtm::DevBuf d_item_tile, d_item_m0, d_bV, d_bV32, d_bstate, d_bc, d_bpart, d_btol2, d_bctrl;
+  vtm::DevBuf d_item_tile, d_item_m0, d_item_order, d_bV, d_bV32, d_bstate, d_bc, d_bpart, d_btol2,
+      d_bctrl, d_bres;
+  bool bres_init = false;
+  int batch_tuned[3] = {0, 0, 0};    // batched sweep variant + 1, per precision
+  int batch_tuned_R[3] = {0, 0, 0};  // right-hand sides it was tuned for
+  int batch_grid[16] = {0};          // grid per (precision, variant)
 
   // adjoint of an unsymmetric system
   vtm_plan_s* transposed = nullptr;

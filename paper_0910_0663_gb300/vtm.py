@@ -11,6 +11,7 @@ import numpy as np
 import torch
 
 from . import _vtm as C
+from ._vtm import VTMError  # noqa: F401  (raised on every failing status)
 
 
 def _dev(a, dtype, device):
@@ -31,14 +32,15 @@ class Plan:
     def __init__(self, indptr, indices, data, partition, nparts, Zc=1.0, precision="fp64",
                  device="cuda", stream=None, max_sweeps=0, check_every=0, inner_tol=0.0,
                  max_outer=0, sweep_kernel=0, method="vtm", batch=0, l2_persist=0, graphs=0,
-                 factor=True):
+                 batch_solve=0, factor=True):
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.n = int(len(indptr) - 1)
         self.nparts = int(nparts)
         self._opts = dict(precision=precision, max_sweeps=max_sweeps, check_every=check_every,
                           inner_tol=inner_tol, max_outer=max_outer, sweep_kernel=sweep_kernel,
-                          method=method, batch=batch, l2_persist=l2_persist, graphs=graphs)
+                          method=method, batch=batch, l2_persist=l2_persist, graphs=graphs,
+                          batch_solve=batch_solve)
         self._history = None
         rp = _dev(indptr, torch.int64, self.device)
         ci = _dev(indices, torch.int32, self.device)
@@ -57,9 +59,10 @@ class Plan:
         C.vtm_set_values(self.handle, _dev(data, torch.float64, self.device))
 
     def set_options(self, history_len=0, **kw):
-        self._opts.update(kw)
-        self._history = np.zeros(history_len, np.float64) if history_len else None
-        C.vtm_set_opts(self.handle, C.make_opts(**self._opts, history=self._history))
+        opts = {**self._opts, **kw}
+        history = np.zeros(history_len, np.float64) if history_len else None
+        C.vtm_set_opts(self.handle, C.make_opts(**opts, history=history))
+        self._opts, self._history = opts, history
 
     @property
     def history(self):

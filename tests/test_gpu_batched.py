@@ -90,3 +90,20 @@ def test_thermal_full_size_64_rhs_bf16(vtm):
                                                  tear.port_remote[tear.tile_ports[P]].tolist()))}
         perm = np.array([keys[k] for k in zip(node[sel].tolist(), remote[sel].tolist())])
         assert np.abs(T_lib - T_ref[np.ix_(perm, perm)]).max() < 1e-10
+
+
+def test_batched_graph_path_on_a_dedicated_stream(vtm):
+    # own stream: persistent batched sweeps replayed from a CUDA graph, the
+    # tensor-core / CUDA-core choice autotuned; a second solve repeats the first
+    w = _thermal_small(16, seed=4)
+    A = w.csr()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc, stream=s,
+                        precision="bf16")
+        b = torch.from_numpy(w.b).cuda()
+        x1, _ = plan.solve(b, tol=1e-10)
+        x2, _ = plan.solve(b, tol=1e-10)
+    torch.cuda.synchronize()
+    assert torch.equal(x1, x2)
+    assert O.residual_norms(A, x1.cpu().numpy(), w.b).max() <= 1e-10

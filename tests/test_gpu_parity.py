@@ -213,9 +213,10 @@ def test_set_values_then_refactor(vtm):
     assert np.abs(x.cpu().numpy() - x_star).max() <= 1e-8 * np.abs(x_star).max()
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 3])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4])
 def test_every_sweep_kernel_matches_oracle(vtm, kernel):
-    # direct-load, bulk-copy staged and vector-load kernels compute the same sweep
+    # direct-load, bulk-copy staged and vector-load (256 / 128 threads)
+    # kernels compute the same FP64 sweep
     w = wl.power_grid(128, 128, 32, 32, Zc=1.0, seed=12)
     A = w.csr()
     plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc, sweep_kernel=kernel)
@@ -225,6 +226,47 @@ def test_every_sweep_kernel_matches_oracle(vtm, kernel):
     if info["sweeps"] == ref.sweeps:
         xs = x.cpu().numpy().reshape(w.b.shape)
         assert np.abs(xs - ref.x).max() <= 1e-11 * np.abs(ref.x).max()
+
+
+@pytest.mark.parametrize("precision,kernel,shape", [("fp32", 5, (90, 18)), ("fp32", 6, (192, 48)),
+                                                    ("bf16", 5, (192, 48)), ("bf16", 6, (90, 18))])
+def test_packed_symmetric_sweeps_follow_the_oracle(vtm, precision, kernel, shape):
+    # T_P is symmetric (scalar W, symmetric A): the packed kernels read the
+    # 16x16 blocks on and above the diagonal only.  18x18 tiles have 72, 54 or
+    # 36 ports (a ragged last block); 48x48 tiles up to 192 ports (12 blocks).
+    # The first inner solve is the plain VTM iteration on b, so its residual
+    # history follows the oracle's up to the rounding of the stored T_P.
+    n, t = shape
+    w = wl.grid2d(n, n, t, t, seed=16)
+    A = w.csr()
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc,
+                    precision=precision, sweep_kernel=kernel)
+    plan.set_options(history_len=40)
+    x, info = plan.solve(torch.from_numpy(w.b[0]).cuda(), tol=1e-10)
+    st = plan.stats()
+    assert st["sweep_kernel"] == kernel and st["packed_bytes"] > 0
+    assert O.residual_norms(A, x.cpu().numpy()[None], w.b[:1]).max() <= 1e-10
+    ref = O.vtm_midpoint(A, w.partition, w.nparts, w.b[:1], W=1 / w.Zc, tol=0, max_sweeps=40)
+    h, href = plan.history, ref.history[:, 0]
+    # BF16 entries carry 2^-9 relative rounding, which shifts the slow modes:
+    # compare the first 15 sweeps only
+    rtol, floor, kmax = (1e-3, 1e-4, 40) if precision == "fp32" else (5e-2, 2e-2, 15)
+    k = min(kmax, int(np.count_nonzero((h > 0) & (href[: len(h)] > floor))))
+    assert k >= 5
+    assert np.allclose(h[:k], href[:k], rtol=rtol, atol=0)
+
+
+def test_bad_options_are_rejected_and_the_plan_keeps_its_own(vtm):
+    w = wl.power_grid(64, 64, 32, 32, Zc=1.0, seed=15)
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc)
+    with pytest.raises(vtm.VTMError):
+        plan.set_options(sweep_kernel=7)
+    with pytest.raises(vtm.VTMError):
+        plan.set_options(sweep_kernel=-1)
+    with pytest.raises(vtm.VTMError):
+        plan.set_options(precision=5)
+    x, info = plan.solve(torch.from_numpy(w.b[0]).cuda(), tol=1e-10)
+    assert O.residual_norms(w.csr(), x.cpu().numpy()[None], w.b[:1]).max() <= 1e-10
 
 
 def test_graph_path_on_a_dedicated_stream(vtm):
@@ -240,7 +282,7 @@ def test_graph_path_on_a_dedicated_stream(vtm):
         x1, info1 = plan.solve(b, tol=1e-10)
         x2, info2 = plan.solve(b, tol=1e-10)  # graph replay
     torch.cuda.synchronize()
-    assert plan.stats()["sweep_kernel"] in (1, 2, 3)
+    assert plan.stats()["sweep_kernel"] in (1, 2, 3, 4, 5, 6)
     assert torch.equal(x1, x2)
     rel = O.residual_norms(A, x1.cpu().numpy()[None], w.b)
     assert rel.max() <= 1e-10
