@@ -50,9 +50,26 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--l2-persist", type=int, default=0, choices=[0, 1],
                     help="0: reflection matrices persisting in L2 during low-precision sweeps, 1: off")
-    ap.add_argument("--sweep-kernel", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6],
-                    help="0: autotuned, 1: direct-load, 2: bulk-copy staged, 3/4: vector-load (256/128 threads)")
+    ap.add_argument("--admittance", default="alpha", choices=["alpha", "diag", "wob", "sca"],
+                    help="line admittance (Sec. VIII): alpha = 1/Zc on every line (default), diag = 2g, "
+                         "wob = alpha 2g, sca = partial input admittance over --radius branches")
+    ap.add_argument("--alpha", type=float, default=0.5, help="the weight of --admittance wob")
+    ap.add_argument("--radius", type=int, default=1, help="the neighbourhood of --admittance sca")
+    ap.add_argument("--sweep-kernel", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6, 7],
+                    help="0: autotuned, 1: direct-load, 2: bulk-copy staged, 3/4: vector-load (256/128 "
+                         "threads), 5/6: packed symmetric (128/64 threads), 7: packed symmetric, tile by "
+                         "one bulk copy")
     return ap.parse_args()
+
+
+def admittance_config(args):
+    if args.admittance == "alpha":
+        return {}
+    desc = {"diag": "W = diag(C) = 2g per line (Sec. VIII choice 2)",
+            "wob": f"W = {args.alpha} C = {args.alpha} * 2g per line (Sec. VIII choice 4)",
+            "sca": f"W = diagonal of the partial input admittance over {args.radius} branch(es), "
+                   "lower-numbered end (Sec. VIII choice 5)"}[args.admittance]
+    return {"admittance": desc}
 
 
 def workload_config(args):
@@ -216,7 +233,7 @@ def sweep_bytes(stats, prec, nrhs=1):
     s_t = {0: 8, 1: 4, 2: 2}[prec]
     s_w = 8 if prec == 0 else 4
     # the packed symmetric kernels need only the entries on and above the diagonal
-    entries = stats["sum_tri"] if stats.get("sweep_kernel") in (5, 6) and nrhs == 1 else stats["sum_p2"]
+    entries = stats["sum_tri"] if stats.get("sweep_kernel") in (5, 6, 7) and nrhs == 1 else stats["sum_p2"]
     return entries * s_t + stats["nports"] * (7 * s_w * nrhs + 13)
 
 
@@ -314,6 +331,8 @@ def run_mode(args, prec, w, dev, stream, b_dev, b_host, x_host, flush, world):
             plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc,
                             precision=prec_name, device=dev, stream=stream, factor=False,
                             sweep_kernel=args.sweep_kernel, l2_persist=args.l2_persist, method=method)
+            if args.admittance != "alpha" and method == "vtm":
+                plan.set_admittance(args.admittance, alpha=args.alpha, radius=args.radius, factor=False)
             t1 = time.perf_counter()
             plan.factor()
         torch.cuda.synchronize()
@@ -396,7 +415,8 @@ def emit(args, results, errors, best, w, world, rank):
         "warmup": args.warmup, "ms_per_step": R["t_step_ms"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "fp32": "f32+f64 refinement", "bf16": "bf16+f64 refinement"}[best.split("_")[-1]],
-        "data": "synthetic", "config": dict(workload_config(args), precision=best),
+        "data": "synthetic", "config": dict(workload_config(args), precision=best,
+                                            **admittance_config(args)),
         "roofline": {"bound": "hbm", "kernel": "sweep_kernel",
                      "achieved": R["achieved_gbs"], "peak": peak, "unit": "GB/s",
                      "frac": R["achieved_gbs"] / peak, "peak_source": peak_src,

@@ -78,9 +78,11 @@ typedef struct {
   int max_sweeps;    /* sweeps per vtm_solve call, all refinement steps together; default 200000 */
   int check_every;   /* sweeps launched between two host polls of the convergence flag; default 32 */
   double inner_tol;  /* relative tolerance of each inner solve in the refinement modes;
-                        0 -> 1e-5 (FP32) / 1e-2 (BF16).  An inner solve also ends when
-                        its residual has not dropped by 10% within 64 sweeps (its
-                        rounding floor); the FP64 refinement then continues. */
+                        0 -> sqrt(tol/2) within [2e-6, 1e-4] (FP32: two steps reach tol)
+                        / 1e-2 (BF16).  An inner solve that can finish the job aims at
+                        tol/2 instead.  An inner solve also ends when its residual has
+                        not dropped by 10% within 64 sweeps (its rounding floor); the
+                        FP64 refinement then continues. */
   int max_outer;     /* refinement steps in the FP32/BF16 modes; default 40 */
   int method;        /* VTM_METHOD_VTM (default) or VTM_METHOD_BJ; read by vtm_plan only */
   int batch;         /* several right-hand sides: 0 (default) one batched iteration over
@@ -96,11 +98,13 @@ typedef struct {
                         fastest; 1: direct-load kernel; 2: bulk-copy staged kernel;
                         3: 16-byte vector-load kernel, 256 threads per tile;
                         4: the same with 128 threads (p <= 128 VEC);
-                        5, 6: packed symmetric kernel, 128 / 256 threads per tile --
+                        5, 6: packed symmetric kernel, 128 / 64 threads per tile --
                         FP32/BF16 plans of a symmetric A whose sub-circuits have at
                         most 256 ports keep only the 16x16 blocks of T_P on and above
                         the diagonal (T_P is symmetric for scalar W, Sec. VIII), about
-                        half the bytes per sweep; elsewhere 5, 6 fall back to kernel 1 */
+                        half the bytes per sweep; 7: the same blocks, each tile brought
+                        into shared memory by one bulk copy; elsewhere 5-7 fall back
+                        to kernel 1 */
   int graphs;        /* 0 (default): replay batches of check_every sweep launches from a
                         CUDA graph when the plan has its own stream; 1: plain launches */
   double* history;   /* optional host array: relative (interface) residual after each
@@ -158,9 +162,42 @@ vtm_status vtm_plan(int64_t n, const int64_t* rowptr, const int32_t* colidx, con
  * must be factored again before the next solve. */
 vtm_status vtm_set_values(vtm_plan_t plan, const double* vals);
 
+/* Characteristic admittance of the virtual lines (Sec. VIII: the speed of
+ * convergence depends on W; the paper lists five choices).  Under midpoint
+ * tearing C_P = diag(2 g_s) is diagonal, so every choice is one value per
+ * line, shared by its two ports. */
+enum {
+  VTM_W_ALPHA = 0, /* W = alpha I (choice 1); the plan's default is alpha = 1/Zc */
+  VTM_W_DIAG = 1,  /* W = diag(C) = 2 g_e on line e (choice 2; also choice 3, W = C);
+                      the VTM iteration then equals block Jacobi sweep by sweep */
+  VTM_W_WOB = 2,   /* W = alpha C = alpha 2 g_e (choice 4, weighted overlapped block) */
+  VTM_W_SCA = 3,   /* diagonal of the partial input admittance C - E~ D~^-1 F~ with D~ the
+                      rows of the sub-circuit within `radius` branches of the port's node
+                      (choice 5, small elements dropped to the pattern of C); a line takes
+                      the value of its end in the lower-numbered sub-circuit */
+  VTM_W_LINE = 4   /* one value per port, given by the caller */
+};
+
+/* vtm_set_admittance -- choose the line admittances (see the enum above).
+ * alpha: used by VTM_W_ALPHA and VTM_W_WOB, > 0.  radius: VTM_W_SCA, 0..8
+ * (the dense partial solve of a port is limited to 512 nodes).  W: VTM_W_LINE
+ * only, nports values in the port order of vtm_get_ports (host or device),
+ * positive and equal at both ports of a line.  DIAG, WOB and SCA follow the
+ * values: vtm_set_values recomputes them.  With any choice other than
+ * VTM_W_ALPHA the library carries power waves w / sqrt(W_s), under which the
+ * condensed operator of a symmetric A stays symmetric.  The plan must be
+ * factored again.  VTM_EINVAL (choice unchanged) for an unknown kind or a bad
+ * alpha, radius or W; VTM_ESINGULAR if a partial sub-circuit matrix is
+ * singular. */
+vtm_status vtm_set_admittance(vtm_plan_t plan, int kind, double alpha, int radius, const double* W);
+
+/* vtm_get_admittance -- the line admittance of every port (nports doubles,
+ * port order of vtm_get_ports; host or device). */
+vtm_status vtm_get_admittance(vtm_plan_t plan, double* W);
+
 /* vtm_set_opts -- replace the options of a plan (precision, limits, history).
  * VTM_EINVAL for a precision outside 0..2, a negative history_len, a history
- * length without an array, or a sweep_kernel outside 0..6; the plan keeps its
+ * length without an array, or a sweep_kernel outside 0..7; the plan keeps its
  * previous options then. */
 vtm_status vtm_set_opts(vtm_plan_t plan, const vtm_opts* opts);
 

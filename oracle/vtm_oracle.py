@@ -18,6 +18,9 @@ Algorithm to Solve the Linear System of Circuit" (arXiv 0910.0663):
                          side; zero initial boundary values.
 * ``reflection_ops``     Sec. VIII: input admittance ``S = C - E D^-1 F`` and
                          voltage reflection matrix ``T = (W - S)(W + S)^-1``.
+* ``line_admittance_choice``  Sec. VIII choices of W (alpha I, diagonal,
+                         weighted overlapped block, Schur complement
+                         approximation) as one admittance per virtual line.
 * ``twin_split`` /
   ``vtm_twin``           Sec. V-VI with a vertex-separator interface (Example
                          1/2, the four-node example of Sec. IX, Eq. 15-21) and
@@ -189,6 +192,68 @@ def _line_admittance(tear: Tearing, W) -> np.ndarray:
     Wp = np.broadcast_to(np.asarray(W, dtype=np.float64), tear.port_g.shape).copy()
     assert np.allclose(Wp, Wp[tear.twin]), "both ends of a line need one admittance"
     return Wp
+
+
+def line_admittance_choice(tear: Tearing, kind: str, alpha: float = 1.0,
+                           radius: int = -1) -> np.ndarray:
+    """Per-port characteristic admittance from the choices of Sec. VIII,
+    for the midpoint tearing, where C_P = diag(2 g_s) is diagonal:
+
+    ``'alpha'``  W = alpha I (choice 1).
+    ``'diag'``   W = diag(C): 2 g_e on line e (choice 2; C is diagonal here,
+                 so choice 3, W = C, is the same).
+    ``'wob'``    W = alpha C: alpha 2 g_e (choice 4).
+    ``'sca'``    the partial input admittance S~ = C - E~ D~^-1 F~ (choice 5)
+                 with D~ = D_P restricted to the nodes of P within ``radius``
+                 branches of ell(s) (radius < 0: all of P, so S~ = S_P); its
+                 small elements are dropped down to the pattern of C, i.e.
+                 its diagonal 2 g_s - 4 g_s^2 [D~^-1]_(ell, ell) is kept.  The
+                 two ends of a line see different S~; the line takes the value
+                 of its end in the lower-numbered sub-circuit (S~_1 of Sec.
+                 VIII, "W = S~_1 or S~_2").
+    """
+    g = tear.port_g
+    if kind == "alpha":
+        return np.full(len(g), float(alpha))
+    if kind == "diag":
+        return 2.0 * g
+    if kind == "wob":
+        return float(alpha) * 2.0 * g
+    if kind != "sca":
+        raise ValueError(kind)
+    S = np.empty(len(g))
+    for P in range(tear.nparts):
+        nodes = tear.tile_nodes[P]
+        ports = tear.tile_ports[P]
+        if len(ports) == 0:
+            continue
+        loc = np.full(tear.n, -1, dtype=np.int64)
+        loc[nodes] = np.arange(len(nodes))
+        D = tear.A_in[nodes][:, nodes].tolil()
+        ell = loc[tear.port_node[ports]]
+        for q, s in enumerate(ports):
+            D[ell[q], ell[q]] += g[s]
+        D = D.tocsr()
+        for q, s in enumerate(ports):
+            sel = np.arange(len(nodes))
+            if radius >= 0:  # breadth-first: nodes within `radius` branches
+                seen = {int(ell[q])}
+                front = [int(ell[q])]
+                for _ in range(radius):
+                    nxt = []
+                    for v in front:
+                        for u in D.indices[D.indptr[v]:D.indptr[v + 1]]:
+                            if int(u) not in seen:
+                                seen.add(int(u))
+                                nxt.append(int(u))
+                    front = nxt
+                sel = np.array(sorted(seen))
+            Dt = D[sel][:, sel].toarray()
+            e = (sel == ell[q]).astype(np.float64)
+            z = np.linalg.solve(Dt, e)
+            S[s] = 2 * g[s] - 4 * g[s] ** 2 * float(z @ e)
+    low_end = tear.port_tile <= tear.port_tile[tear.twin]
+    return np.where(low_end, S, S[tear.twin])
 
 
 def local_system(A: sp.csr_matrix, tear: Tearing, P: int, Wp: np.ndarray) -> sp.csc_matrix:

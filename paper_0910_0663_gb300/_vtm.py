@@ -21,6 +21,7 @@ VTM_OK, VTM_EINVAL, VTM_ENOMEM, VTM_ESINGULAR, VTM_ENOCONV = 0, -1, -2, -3, -4
 VTM_EDIVERGED, VTM_ETIMEOUT, VTM_ECUDA, VTM_EINTERNAL, VTM_ENOTFACTORED = -5, -6, -7, -8, -9
 PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
 METHOD = {"vtm": 0, "bj": 1}
+ADMITTANCE = {"alpha": 0, "diag": 1, "wob": 2, "sca": 3, "line": 4}
 
 
 class vtm_opts(ctypes.Structure):
@@ -76,6 +77,8 @@ def _load():
                                     ctypes.POINTER(P)]),
         "vtm_set_values": (ctypes.c_int, [P, P]),
         "vtm_set_opts": (ctypes.c_int, [P, ctypes.POINTER(vtm_opts)]),
+        "vtm_set_admittance": (ctypes.c_int, [P, ctypes.c_int, dbl, ctypes.c_int, P]),
+        "vtm_get_admittance": (ctypes.c_int, [P, P]),
         "vtm_factor": (ctypes.c_int, [P]),
         "vtm_solve": (ctypes.c_int, [P, P, P, i64, dbl, ctypes.POINTER(vtm_info)]),
         "vtm_adjoint": (ctypes.c_int, [P, P, P, i64, dbl, ctypes.POINTER(vtm_info)]),
@@ -100,7 +103,8 @@ def _load():
 
 
 _lib = _load()
-EXPORTED = ("vtm_plan", "vtm_set_values", "vtm_set_opts", "vtm_factor", "vtm_solve",
+EXPORTED = ("vtm_plan", "vtm_set_values", "vtm_set_opts", "vtm_set_admittance",
+            "vtm_get_admittance", "vtm_factor", "vtm_solve",
             "vtm_adjoint", "vtm_plan_get_stats", "vtm_get_ports", "vtm_get_reflection",
             "vtm_residual_norm", "vtm_residual_norm_noalloc", "vtm_netmap_create",
             "vtm_netmap_values", "vtm_netmap_gradient", "vtm_netmap_destroy", "vtm_destroy",
@@ -164,6 +168,17 @@ def vtm_set_values(plan, vals):
 
 def vtm_set_opts(plan, opts):
     _check(_lib.vtm_set_opts(plan, ctypes.byref(opts)), "vtm_set_opts")
+
+
+def vtm_set_admittance(plan, kind, alpha=1.0, radius=2, W=None):
+    k = ADMITTANCE[kind] if isinstance(kind, str) else int(kind)
+    _check(_lib.vtm_set_admittance(plan, k, float(alpha), int(radius), _ptr(W)), "vtm_set_admittance")
+
+
+def vtm_get_admittance(plan):
+    W = np.empty(vtm_plan_get_stats(plan).nports, np.float64)
+    _check(_lib.vtm_get_admittance(plan, _ptr(W)), "vtm_get_admittance")
+    return W
 
 
 def vtm_factor(plan):

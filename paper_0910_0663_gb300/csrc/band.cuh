@@ -118,7 +118,9 @@ __device__ __forceinline__ void warp_band_solve_pf(FT* v, int n, int bw, const F
   warp_scale_pass(v, n, uc, B);
 }
 
-// K_P^-1 v in place (v in shared or global memory, one warp).
+// K_P^-1 v in place (v in shared or global memory, one warp).  Deeper
+// prefetch than 16 rows costs more registers than it gains: occupancy drops
+// below one warp per tile and SM slot.
 template <class FT>
 __device__ __forceinline__ void warp_band_solve_any(FT* v, int n, int bw, const FT* __restrict__ lc,
                                                     const FT* __restrict__ uc, int start) {

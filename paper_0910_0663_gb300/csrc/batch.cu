@@ -352,17 +352,17 @@ __global__ void batch_band_solve_win_kernel(const int32_t* __restrict__ node_off
   cp_async_wait<0>();
 }
 
-// c[s][r] = 2 W beta_s x0[pos(s)][r]
+// c[s][r] = (2 W beta_s / d_s) x0[pos(s)][r]
 template <class FT, class WT>
-__global__ void batch_const_kernel(const int32_t* __restrict__ port_pos, const double* __restrict__ beta,
-                                   const FT* __restrict__ x0, double W, WT* __restrict__ c,
-                                   int64_t nports, int R, int64_t n) {
+__global__ void batch_const_kernel(const int32_t* __restrict__ port_pos, const double* __restrict__ bout,
+                                   const FT* __restrict__ x0, WT* __restrict__ c, int64_t nports, int R,
+                                   int64_t n) {
   const int64_t total = nports * R;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s = i / R;
     const int r = (int)(i % R);
-    c[i] = (WT)(2.0 * W * beta[s] * (double)x0[(int64_t)r * n + port_pos[s]]);
+    c[i] = (WT)(bout[s] * (double)x0[(int64_t)r * n + port_pos[s]]);
   }
 }
 
@@ -401,13 +401,12 @@ __device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162flo
 // red[r] receives the column sums in a fixed order.  State layout:
 // [port][2][R] = (w_in, w_out).
 template <class WT, class RT>
-__device__ void batch_residual(const int32_t* __restrict__ twin, const double* __restrict__ g,
+__device__ void batch_residual(const int32_t* __restrict__ twin, const double2* __restrict__ kd,
                                const uint8_t* __restrict__ run, const WT* __restrict__ prev,
-                               int p0, int m0, int m1, int R, double W, RT (*rsq)[64],
-                               double* red) {
+                               int p0, int m0, int m1, int R, RT (*rsq)[64], double* red) {
   // arithmetic in RT: FP32 for the low-precision sweeps (GB300's FP64 pipe is
-  // narrow), FP64 for the FP64 sweep
-  const RT hW = (RT)W, inv2W = (RT)(0.5 / W);
+  // narrow), FP64 for the FP64 sweep; kd = (g/W, d) of the line, the term is
+  // d/2 [(S_s + S_t)/2 - (g/W)(S_s - S_t) - w_in(s) - w_in(t)], S = w_in + w_out
   for (int r = threadIdx.x; r < R; r += blockDim.x) red[r] = 0.0;
   // rows in slices of 32 node runs; the column sums add the slices in order
   for (int h0 = m0; h0 < m1; h0 += 32) {
@@ -426,9 +425,9 @@ __device__ void batch_residual(const int32_t* __restrict__ twin, const double* _
         const RT wo_s = (RT)prev[(size_t)ps * 2 * R + R + r];
         const RT wi_t = (RT)prev[(size_t)tw * 2 * R + r];
         const RT wo_t = (RT)prev[(size_t)tw * 2 * R + R + r];
-        const RT gg = (RT)g[ps];
-        const RT us = (wi_s + wo_s) * inv2W, ut = (wi_t + wo_t) * inv2W;
-        rsum += (RT)0.5 * ((hW - 2 * gg) * us + (hW + 2 * gg) * ut - wi_s - wi_t);
+        const double2 k2 = kd[ps];
+        const RT Ss = wi_s + wo_s, St = wi_t + wo_t;
+        rsum += (RT)0.5 * (RT)k2.y * ((RT)0.5 * (Ss + St) - (RT)k2.x * (Ss - St) - wi_s - wi_t);
       }
       rsq[sl][r] = rsum * rsum;
     }
@@ -499,8 +498,8 @@ __global__ void __launch_bounds__(256) batch_sweep_kernel(
     const TT* __restrict__ T, const int64_t* __restrict__ T_off, const int32_t* __restrict__ T_ld,
     const int32_t* __restrict__ port_off, const int32_t* __restrict__ item_tile,
     const int32_t* __restrict__ item_m0, const int32_t* __restrict__ item_order, int nitems, const int32_t* __restrict__ twin,
-    const double* __restrict__ g, const uint8_t* __restrict__ run, const WT* __restrict__ c,
-    WT* __restrict__ state, int64_t nports, int R, double W, BatchCtrl* __restrict__ ctrl,
+    const double2* __restrict__ kd, const uint8_t* __restrict__ run, const WT* __restrict__ c,
+    WT* __restrict__ state, int64_t nports, int R, BatchCtrl* __restrict__ ctrl,
     double* __restrict__ partials, const double* __restrict__ tol2, double* __restrict__ hist,
     int hist_len) {
   __shared__ AT Ts[kKC][kMB];
@@ -534,7 +533,7 @@ __global__ void __launch_bounds__(256) batch_sweep_kernel(
   const TT* Tb = T + T_off[tile];
   const WT* prev = state + (size_t)((k - 1) & 1) * nports * 2 * R;
   WT* cur = state + (size_t)(k & 1) * nports * 2 * R;
-  if (k > 1) batch_residual<WT, AT>(twin, g, run, prev, p0, m0, m1, R, W, rsq, red);
+  if (k > 1) batch_residual<WT, AT>(twin, kd, run, prev, p0, m0, m1, R, rsq, red);
   const int tx = tid % 16, ty = tid / 16;
   AT acc[4][4];
 #pragma unroll
@@ -633,9 +632,9 @@ __global__ void __launch_bounds__(128) batch_sweep_mma_kernel(
     const __nv_bfloat16* __restrict__ T, const int64_t* __restrict__ T_off,
     const int32_t* __restrict__ T_ld, const int32_t* __restrict__ port_off,
     const int32_t* __restrict__ item_tile, const int32_t* __restrict__ item_m0, const int32_t* __restrict__ item_order, int nitems,
-    const int32_t* __restrict__ twin, const double* __restrict__ g,
+    const int32_t* __restrict__ twin, const double2* __restrict__ kd,
     const uint8_t* __restrict__ run, const float* __restrict__ c, float* __restrict__ state,
-    int64_t nports, int R, double W, BatchCtrl* __restrict__ ctrl, double* __restrict__ partials,
+    int64_t nports, int R, BatchCtrl* __restrict__ ctrl, double* __restrict__ partials,
     const double* __restrict__ tol2, double* __restrict__ hist, int hist_len) {
   constexpr int KC = 32;  // inputs per chunk (two k16 steps)
   __shared__ __align__(16) __nv_bfloat16 As[2][KC][kAPad];  // T^T chunk: [t][s], double-buffered
@@ -714,7 +713,7 @@ __global__ void __launch_bounds__(128) batch_sweep_mma_kernel(
   };
   if (k > 1) {
     load_chunk(0);  // in flight during the residual of sweep k-1
-    batch_residual<float, float>(twin, g, run, prev, p0, m0, m1, R, W, rsq, red);
+    batch_residual<float, float>(twin, kd, run, prev, p0, m0, m1, R, rsq, red);
     int buf = 0;
     for (int t0 = 0; t0 < p; t0 += KC, buf ^= 1) {
       store_chunk(buf);
@@ -943,15 +942,15 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
     if (npt > 0) {
       if (f32_solves)
         batch_const_kernel<float, float><<<g2, 256, 0, s>>>(P->d_port_pos.as<int32_t>(),
-                                                           P->d_beta.as<double>(), V32, P->W,
+                                                           P->d_bout.as<double>(), V32,
                                                            P->d_bc.as<float>(), npt, R, n);
       else if (lowp)
         batch_const_kernel<double, float><<<g2, 256, 0, s>>>(P->d_port_pos.as<int32_t>(),
-                                                            P->d_beta.as<double>(), V, P->W,
+                                                            P->d_bout.as<double>(), V,
                                                             P->d_bc.as<float>(), npt, R, n);
       else
         batch_const_kernel<double, double><<<g2, 256, 0, s>>>(P->d_port_pos.as<int32_t>(),
-                                                             P->d_beta.as<double>(), V, P->W,
+                                                             P->d_bout.as<double>(), V,
                                                              P->d_bc.as<double>(), npt, R, n);
       P->launch_count++;
       std::vector<double> t2(64, 1.0);
@@ -990,8 +989,8 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
           kern<<<P->batch_grid[key], threads, 0, s>>>(
               T, P->tabs.T_off.as<int64_t>(), P->tabs.T_ld.as<int32_t>(), P->tabs.port_off.as<int32_t>(),
               P->d_item_tile.as<int32_t>(), P->d_item_m0.as<int32_t>(), P->d_item_order.as<int32_t>(),
-              nitems, P->d_twin.as<int32_t>(), P->d_g.as<double>(), P->d_run.as<uint8_t>(), cc, st, npt,
-              R, P->W, P->d_bctrl.as<BatchCtrl>(), P->d_bpart.as<double>(), P->d_btol2.as<double>(),
+              nitems, P->d_twin.as<int32_t>(), P->d_kd.as<double2>(), P->d_run.as<uint8_t>(), cc, st,
+              npt, R, P->d_bctrl.as<BatchCtrl>(), P->d_bpart.as<double>(), P->d_btol2.as<double>(),
               nullptr, 0);
         };
         if (prec == VTM_PREC_BF16 && (kv & 1))

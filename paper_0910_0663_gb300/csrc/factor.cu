@@ -12,10 +12,14 @@
 //
 // The reflection matrix of Sec. VIII, T_P = (W - S_P)(W + S_P)^-1, is built
 // column by column from banded solves: column q of T_P is
-//   T(s, q) = 2 W beta_s y_q(l(s)) + delta_sq (W - 2 g_s)/(W + 2 g_s),
-//   K_P y_q = beta_q e_l(q),  beta = 2 g/(2 g + W).
-// It is stored transposed (row q of the block = column q of T_P) with rows
-// padded to a multiple of 8 elements.
+//   T(s, q) = 2 W_s beta_s y_q(l(s)) + delta_sq (W_s - 2 g_s)/(W_s + 2 g_s),
+//   K_P y_q = beta_q e_l(q),  beta = 2 g/(2 g + W)
+// (W_s the admittance of the line of port s).  With waves carried as w / d
+// (d_s = 1 for one W on every line, sqrt(W_s) otherwise) the stored operator
+// is D^-1 T_P D: bout_s = 2 W_s beta_s / d_s and bin_q = beta_q d_q take the
+// place of 2 W beta and beta, and it is symmetric whenever A is.
+// It is stored transposed (row q of the block = column q of the operator)
+// with rows padded to a multiple of 8 elements.
 #include <algorithm>
 
 #include "band.cuh"
@@ -218,10 +222,11 @@ __global__ void build_reflection_kernel(const int32_t* __restrict__ node_off,
                                         const int32_t* __restrict__ port_off,
                                         const int32_t* __restrict__ port_tile,
                                         const int32_t* __restrict__ port_loc,
-                                        const double* __restrict__ g,
-                                        const double* __restrict__ beta,
+                                        const double* __restrict__ bin,
+                                        const double* __restrict__ bout,
+                                        const double* __restrict__ rho,
                                         const int64_t* __restrict__ T_off,
-                                        const int32_t* __restrict__ T_ld, double W,
+                                        const int32_t* __restrict__ T_ld,
                                         double* __restrict__ T) {
   extern __shared__ double y[];
   const int q = blockIdx.x;
@@ -233,14 +238,14 @@ __global__ void build_reflection_kernel(const int32_t* __restrict__ node_off,
   for (int i = lane; i < n; i += 32) y[i] = 0.0;
   __syncwarp();
   const int lq = port_loc[q];
-  if (lane == 0) y[lq] = beta[q];
+  if (lane == 0) y[lq] = bin[q];
   __syncwarp();
   warp_band_solve_any(y, n, bwv[t], Lc + band_off[t], Uc + band_off[t], lq);
   double* row = T + T_off[t] + (size_t)(q - p0) * T_ld[t];
   for (int s = lane; s < p; s += 32) {
     const int ps = p0 + s;
-    double v = 2.0 * W * beta[ps] * y[port_loc[ps]];
-    if (ps == q) v += (W - 2.0 * g[ps]) / (W + 2.0 * g[ps]);
+    double v = bout[ps] * y[port_loc[ps]];
+    if (ps == q) v += rho[ps];
     row[s] = v;
   }
 }
@@ -318,9 +323,9 @@ vtm_status build_reflections(vtm_plan_s* P) {
     build_reflection_kernel<<<(unsigned)npt, 32, smem, s>>>(
         P->tabs.node_off.as<int32_t>(), P->tabs.bw.as<int32_t>(), P->tabs.band_off.as<int64_t>(),
         P->d_Lc.as<double>(), P->d_Uc.as<double>(), P->tabs.port_off.as<int32_t>(),
-        d_pt.as<int32_t>(), P->d_port_loc.as<int32_t>(), P->d_g.as<double>(),
-        P->d_beta.as<double>(), P->tabs.T_off.as<int64_t>(), P->tabs.T_ld.as<int32_t>(), P->W,
-        P->d_T64.as<double>());
+        d_pt.as<int32_t>(), P->d_port_loc.as<int32_t>(), P->d_beta.as<double>(),
+        P->d_bout.as<double>(), P->d_rho.as<double>(), P->tabs.T_off.as<int64_t>(),
+        P->tabs.T_ld.as<int32_t>(), P->d_T64.as<double>());
     VTM_CUDA_TRY(cudaGetLastError());
     VTM_CUDA_TRY(cudaStreamSynchronize(s));
     dev_free(d_pt);
@@ -407,7 +412,10 @@ extern "C" vtm_status vtm_get_reflection(vtm_plan_t P, int32_t part, double* T, 
   if (pp > 0)
     VTM_CUDA_TRY(cudaMemcpy(blk.data(), P->d_T64.as<double>() + P->T_off[part],
                             blk.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  // back from the plan's wave scaling: T_P(s, q) = d_s [D^-1 T_P D](s, q) / d_q
+  const int32_t p0 = P->port_off[part];
   for (int32_t q = 0; q < pp; ++q)
-    for (int32_t s = 0; s < pp; ++s) T[(size_t)s * pp + q] = blk[(size_t)q * ld + s];
+    for (int32_t s = 0; s < pp; ++s)
+      T[(size_t)s * pp + q] = blk[(size_t)q * ld + s] * (P->port_d[p0 + s] / P->port_d[p0 + q]);
   return VTM_OK;
 }

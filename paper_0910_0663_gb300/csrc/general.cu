@@ -15,7 +15,7 @@
 // K_P = A_PP, x_P^k = A_PP^-1 (b_P - sum_Q A_PQ x_Q^(k-1)) (Sec. X).
 //
 // Residual of sweep k at row i: torn branch s (twin t):
-//   ((W - 2g) u_s + (W + 2g) u_t - w_in(s) - w_in(t)) / 2,
+//   ((W - 2g) u_s + (W + 2g) u_t - w_in(s) - w_in(t)) / 2  (waves carried as w / d),
 // lagged entry q: rho_q (z_q - x_j^k)   (z_q = x_j^(k-1) was used).
 #include <algorithm>
 #include <cmath>
@@ -122,9 +122,9 @@ __global__ void __launch_bounds__(256) general_sweep_kernel(
     const int32_t* __restrict__ in_off, const int32_t* __restrict__ out_off,
     const int32_t* __restrict__ in_src, const uint8_t* __restrict__ in_kind,
     const int32_t* __restrict__ in_twin, const int32_t* __restrict__ in_own_out,
-    const double* __restrict__ coef, const int32_t* __restrict__ res_perm,
+    const double* __restrict__ coef, const double* __restrict__ dsc, const int32_t* __restrict__ res_perm,
     const uint8_t* __restrict__ res_run, const double* __restrict__ c, double* __restrict__ gin,
-    double* __restrict__ gout, int64_t n_in, int64_t n_out, double W, SweepCtrl* __restrict__ ctrl,
+    double* __restrict__ gout, int64_t n_in, int64_t n_out, SweepCtrl* __restrict__ ctrl,
     double* __restrict__ partials, double* __restrict__ hist, int hist_len, int nparts) {
   extern __shared__ double sm[];
   __shared__ int s_k, s_flag;
@@ -145,7 +145,6 @@ __global__ void __launch_bounds__(256) general_sweep_kernel(
   const double* pout = gout + (size_t)((k - 1) & 1) * n_out;
   double* cin = gin + (size_t)(k & 1) * n_in;
   double* cout_ = gout + (size_t)(k & 1) * n_out;
-  const double inv2W = 0.5 / W;
   for (int q = threadIdx.x; q < ni; q += blockDim.x) {
     const int a = a0 + q;
     double vi = 0.0, r = 0.0;
@@ -155,9 +154,9 @@ __global__ void __launch_bounds__(256) general_sweep_kernel(
       if (in_kind[a] == 0) {
         const double wi_s = pin[a], wo_s = pout[in_own_out[a]];
         const double wi_t = pin[in_twin[a]], wo_t = src;
-        const double g = coef[a];
-        const double us = (wi_s + wo_s) * inv2W, ut = (wi_t + wo_t) * inv2W;
-        r = 0.5 * ((W - 2 * g) * us + (W + 2 * g) * ut - wi_s - wi_t);
+        // coef = g/W, dsc = d of the line (waves carried as w / d)
+        const double Ss = wi_s + wo_s, St = wi_t + wo_t;
+        r = 0.5 * dsc[a] * (0.5 * (Ss + St) - coef[a] * (Ss - St) - wi_s - wi_t);
       } else {
         r = coef[a] * (pin[a] - src);
       }
@@ -279,9 +278,10 @@ vtm_status general_sweeps(vtm_plan_s* P, double bnorm2, double target2, int budg
           P->d_E.as<double>(), P->d_E_off.as<int64_t>(), P->d_E_ld.as<int32_t>(),
           P->d_in_off.as<int32_t>(), P->d_out_off.as<int32_t>(), P->d_in_src.as<int32_t>(),
           P->d_in_kind.as<uint8_t>(), P->d_in_twin.as<int32_t>(), P->d_in_own_out.as<int32_t>(),
-          P->d_in_coef.as<double>(), P->d_res_perm.as<int32_t>(), P->d_res_run.as<uint8_t>(),
+          P->d_in_coef.as<double>(), P->d_in_d.as<double>(), P->d_res_perm.as<int32_t>(),
+          P->d_res_run.as<uint8_t>(),
           P->d_cg.as<double>(), P->d_gin.as<double>(), P->d_gout.as<double>(), P->n_in, P->n_out,
-          P->W, P->d_ctrl.as<SweepCtrl>(), P->d_partials.as<double>(), hist, hist_len, P->nparts);
+          P->d_ctrl.as<SweepCtrl>(), P->d_partials.as<double>(), hist, hist_len, P->nparts);
     VTM_CUDA_TRY(cudaGetLastError());
     launched += m;
     VTM_CUDA_TRY(cudaEventRecord(P->evs1, s));

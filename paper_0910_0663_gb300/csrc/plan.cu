@@ -354,13 +354,130 @@ static bool same_cut_structure(const vtm_plan_s* P) {
   return std::includes(l0.begin(), l0.end(), lags.begin(), lags.end());
 }
 
-// Values: branch conductances, beta, lagged couplings and the band of K_P.
+// Diagonal of the partial input admittance S~ = C - E~ D~^-1 F~ of every port
+// (Sec. VIII, choice 5): D~ is D_P = A_PP + sum_s g_s e_l e_l^T restricted to
+// the nodes of the sub-circuit within `radius` branches of the port's node;
+// S~_ss = 2 g_s - 4 g_s^2 [D~^-1]_(l,l), by a dense LU with partial pivoting.
+static vtm_status schur_diag_ports(vtm_plan_s* P, int radius, std::vector<double>& S) {
+  const size_t npt = P->port_node.size();
+  S.assign(npt, 0.0);
+  std::vector<double> gsum(P->n, 0.0);
+  for (size_t s = 0; s < npt; ++s) gsum[P->port_node[s]] += P->port_g[s];
+  std::vector<int32_t> mark(P->n, -1), sel;
+  std::vector<double> D, z;
+  for (size_t s = 0; s < npt; ++s) {
+    const int32_t l = P->port_node[s], t = P->h_part[l];
+    sel.assign(1, l);
+    mark[l] = (int32_t)s;
+    size_t lo = 0;
+    for (int r = 0; r < radius; ++r) {
+      const size_t hi = sel.size();
+      for (size_t q = lo; q < hi; ++q) {
+        const int32_t i = sel[q];
+        for (int64_t e = P->h_rowptr[i]; e < P->h_rowptr[i + 1]; ++e) {
+          const int32_t j = P->h_colidx[e];
+          if (P->h_part[j] == t && mark[j] != (int32_t)s) {
+            mark[j] = (int32_t)s;
+            sel.push_back(j);
+          }
+        }
+      }
+      lo = hi;
+    }
+    const int m = (int)sel.size();
+    if (m > 512) {
+      set_detail("vtm_set_admittance: the neighbourhood of a port exceeds 512 nodes; lower radius");
+      return VTM_EINVAL;
+    }
+    std::vector<int32_t> pos(m);
+    D.assign((size_t)m * m, 0.0);
+    for (int a = 0; a < m; ++a) {
+      const int32_t i = sel[a];
+      for (int64_t e = P->h_rowptr[i]; e < P->h_rowptr[i + 1]; ++e) {
+        const int32_t j = P->h_colidx[e];
+        if (P->h_part[j] != t || mark[j] != (int32_t)s) continue;
+        const int b = (int)(std::find(sel.begin(), sel.end(), j) - sel.begin());
+        D[(size_t)a * m + b] += P->h_vals[e];
+      }
+      D[(size_t)a * m + a] += gsum[i];
+    }
+    // solve D z = e_0 (the port's node is sel[0])
+    z.assign(m, 0.0);
+    z[0] = 1.0;
+    for (int c = 0; c < m; ++c) {
+      int piv = c;
+      for (int r = c + 1; r < m; ++r)
+        if (std::fabs(D[(size_t)r * m + c]) > std::fabs(D[(size_t)piv * m + c])) piv = r;
+      if (D[(size_t)piv * m + c] == 0.0) {
+        set_detail("vtm_set_admittance: singular partial sub-circuit matrix");
+        return VTM_ESINGULAR;
+      }
+      if (piv != c) {
+        for (int k = 0; k < m; ++k) std::swap(D[(size_t)c * m + k], D[(size_t)piv * m + k]);
+        std::swap(z[c], z[piv]);
+      }
+      for (int r = c + 1; r < m; ++r) {
+        const double f = D[(size_t)r * m + c] / D[(size_t)c * m + c];
+        if (f == 0.0) continue;
+        for (int k = c; k < m; ++k) D[(size_t)r * m + k] -= f * D[(size_t)c * m + k];
+        z[r] -= f * z[c];
+      }
+    }
+    for (int c = m - 1; c >= 0; --c) {
+      double acc = z[c];
+      for (int k = c + 1; k < m; ++k) acc -= D[(size_t)c * m + k] * z[k];
+      z[c] = acc / D[(size_t)c * m + c];
+    }
+    const double g = P->port_g[s];
+    S[s] = 2 * g - 4 * g * g * z[0];
+  }
+  return VTM_OK;
+}
+
+// Admittance of every line from the plan's choice (Sec. VIII); both ports of
+// a line get the same value.
+static vtm_status line_admittance(vtm_plan_s* P) {
+  const size_t npt = P->port_node.size();
+  P->port_W.assign(npt, P->W);
+  switch (P->w_kind) {
+    case VTM_W_ALPHA:
+      break;
+    case VTM_W_DIAG:
+      for (size_t s = 0; s < npt; ++s) P->port_W[s] = 2.0 * P->port_g[s];
+      break;
+    case VTM_W_WOB:
+      for (size_t s = 0; s < npt; ++s) P->port_W[s] = P->w_alpha * 2.0 * P->port_g[s];
+      break;
+    case VTM_W_SCA: {
+      std::vector<double> S;
+      VTM_TRY(schur_diag_ports(P, P->w_radius, S));
+      for (size_t s = 0; s < npt; ++s) {
+        const int32_t tw = P->port_twin[s];
+        const bool low = P->h_part[P->port_node[s]] <= P->h_part[P->port_node[tw]];
+        P->port_W[s] = low ? S[s] : S[tw];
+      }
+      break;
+    }
+    case VTM_W_LINE:
+      P->port_W = P->w_user;
+      break;
+    default:
+      return VTM_EINVAL;
+  }
+  for (size_t s = 0; s < npt; ++s)
+    if (!(P->port_W[s] > 0) || !std::isfinite(P->port_W[s])) {
+      set_detail("line admittance not positive at port " + std::to_string(s));
+      return VTM_EINVAL;
+    }
+  return VTM_OK;
+}
+
+// Values: branch conductances, line admittances, the per-port coefficients,
+// lagged couplings and the band of K_P.
 vtm_status assemble_local(vtm_plan_s* P) {
   const int32_t np = P->nparts;
-  const double W = P->W;
   const size_t npt = P->port_node.size();
   P->port_g.resize(npt);
-  std::vector<double> beta(npt);
   for (size_t s = 0; s < npt; ++s) {
     double g = -(val_at(P, P->port_pos_ij[s]) + val_at(P, P->port_pos_ji[s])) / 2.0;
     if (!(g > 0)) {
@@ -368,7 +485,30 @@ vtm_status assemble_local(vtm_plan_s* P) {
       return VTM_EINVAL;
     }
     P->port_g[s] = g;
+  }
+  if (P->w_dirty || P->port_W.size() != npt) {
+    VTM_TRY(line_admittance(P));
+    P->w_dirty = false;
+  }
+  // waves are carried as w / d_s with d_s = sqrt(W_s / W_ref): for one W on
+  // every line d = 1; otherwise d = sqrt(W_s) (power waves), which keeps the
+  // condensed operator symmetric for a symmetric A
+  const bool scalar_w = P->w_kind == VTM_W_ALPHA;
+  std::vector<double> beta(npt), bin(npt), bout(npt), rho(npt), kd(2 * npt);
+  std::vector<float> kd32(2 * npt);
+  P->port_d.assign(npt, 1.0);
+  for (size_t s = 0; s < npt; ++s) {
+    const double g = P->port_g[s], W = P->port_W[s];
+    const double d = scalar_w ? 1.0 : std::sqrt(W);
+    P->port_d[s] = d;
     beta[s] = 2 * g / (2 * g + W);
+    bin[s] = scalar_w ? beta[s] : beta[s] * d;
+    bout[s] = scalar_w ? 2.0 * W * beta[s] : 2.0 * W * beta[s] / d;
+    rho[s] = (W - 2.0 * g) / (W + 2.0 * g);
+    kd[2 * s] = g / W;
+    kd[2 * s + 1] = d;
+    kd32[2 * s] = (float)(g / W);
+    kd32[2 * s + 1] = (float)d;
   }
   P->lag_rho.resize(P->lag_i.size());
   for (size_t q = 0; q < P->lag_i.size(); ++q) {
@@ -401,7 +541,7 @@ vtm_status assemble_local(vtm_plan_s* P) {
       }
     }
     for (int32_t s = P->port_off[t]; s < P->port_off[t + 1]; ++s) {
-      double g = P->port_g[s];
+      const double g = P->port_g[s], W = P->port_W[s];
       lc[(int64_t)P->port_loc[s] * B] += g - 4 * g * g / (2 * g + W);
     }
   }
@@ -412,18 +552,23 @@ vtm_status assemble_local(vtm_plan_s* P) {
   } else {
     VTM_TRY(dev_alloc(P->d_Uc, std::max<size_t>(16, Lc.size() * sizeof(double))));
   }
-  VTM_TRY(upload(P->d_g, P->port_g, st));
-  VTM_TRY(upload(P->d_beta, beta, st));
+  VTM_TRY(upload(P->d_beta, bin, st));
+  VTM_TRY(upload(P->d_bout, bout, st));
+  VTM_TRY(upload(P->d_rho, rho, st));
+  VTM_TRY(upload(P->d_kd, kd, st));
+  VTM_TRY(upload(P->d_kd32, kd32, st));
   if (P->general) {
-    // per input: residual coefficient (g or rho) and right-hand-side weight
-    // (beta or -rho); per output: scale (2 W beta or 1) and the diagonal
-    // reflection term of a port
-    std::vector<double> coef(P->n_in), sigma(P->n_in), scale(P->n_out), diag(P->n_out, 0.0);
+    // per input: residual coefficients (g/W and d of a port, rho of a lagged
+    // entry) and right-hand-side weight (beta d or -rho); per output: scale
+    // (2 W beta / d or 1) and the diagonal reflection term of a port
+    std::vector<double> coef(P->n_in), dsc(P->n_in, 0.0), sigma(P->n_in), scale(P->n_out),
+        diag(P->n_out, 0.0);
     for (int64_t a = 0; a < P->n_in; ++a) {
       const int32_t it = P->in_item[a];
       if (P->in_kind[a] == 0) {
-        coef[a] = P->port_g[it];
-        sigma[a] = beta[it];
+        coef[a] = kd[2 * it];
+        dsc[a] = kd[2 * it + 1];
+        sigma[a] = bin[it];
       } else {
         coef[a] = P->lag_rho[it];
         sigma[a] = -P->lag_rho[it];
@@ -432,14 +577,14 @@ vtm_status assemble_local(vtm_plan_s* P) {
     for (int64_t o = 0; o < P->n_out; ++o) {
       const int32_t it = P->out_item[o];
       if (it >= 0) {
-        const double g = P->port_g[it];
-        scale[o] = 2.0 * W * beta[it];
-        diag[o] = (W - 2.0 * g) / (W + 2.0 * g);
+        scale[o] = bout[it];
+        diag[o] = rho[it];
       } else {
         scale[o] = 1.0;
       }
     }
     VTM_TRY(upload(P->d_in_coef, coef, st));
+    VTM_TRY(upload(P->d_in_d, dsc, st));
     VTM_TRY(upload(P->d_in_sigma, sigma, st));
     VTM_TRY(upload(P->d_out_scale, scale, st));
     VTM_TRY(upload(P->d_out_diag, diag, st));
@@ -608,10 +753,10 @@ std::vector<DevBuf*> vtm_plan_s::all_bufs() {
   return {&tabs.node_off, &tabs.bw, &tabs.band_off, &tabs.port_off, &tabs.T_off, &tabs.T_ld,
           &tabs.order, &d_rowptr, &d_colidx, &d_vals, &d_perm, &d_Lc, &d_Uc, &d_Lc32, &d_Uc32, &d_v32,
           &d_port_loc, &d_port_pos, &d_tdesc,
-          &d_twin, &d_g, &d_beta, &d_run, &d_T64, &d_T32, &d_T16, &d_Tp32, &d_Tp16, &d_c64, &d_c32, &d_state64,
+          &d_twin, &d_beta, &d_bout, &d_rho, &d_kd, &d_kd32, &d_run, &d_T64, &d_T32, &d_T16, &d_Tp32, &d_Tp16, &d_c64, &d_c32, &d_state64,
           &d_state32, &d_v, &d_v2, &d_xacc, &d_r, &d_bcol, &d_partials, &d_ctrl, &d_hist,
           &d_err, &d_red, &d_in_off, &d_out_off, &d_in_src, &d_in_kind, &d_in_twin,
-          &d_in_own_out, &d_in_loc, &d_res_perm, &d_res_run, &d_out_loc, &d_in_coef,
+          &d_in_own_out, &d_in_loc, &d_res_perm, &d_res_run, &d_out_loc, &d_in_coef, &d_in_d,
           &d_in_sigma, &d_out_scale, &d_out_diag, &d_E_off, &d_E_ld, &d_E, &d_cg, &d_gin,
           &d_gout, &d_in_tile, &d_item_tile, &d_item_m0, &d_item_order, &d_bV, &d_bV32, &d_bstate,
           &d_bc, &d_bpart,
@@ -625,6 +770,85 @@ static void fill_default_opts(vtm_opts* o) {
   if (o->precision < 0 || o->precision > 2) o->precision = 0;
 }
 
+extern "C" vtm_status vtm_set_admittance(vtm_plan_t P, int kind, double alpha, int radius,
+                                         const double* W) {
+  if (!P) return VTM_EINVAL;
+  const size_t npt = P->port_node.size();
+  std::vector<double> user;
+  switch (kind) {
+    case VTM_W_ALPHA:
+    case VTM_W_WOB:
+      if (!(alpha > 0) || !std::isfinite(alpha)) {
+        set_detail("vtm_set_admittance: alpha must be positive");
+        return VTM_EINVAL;
+      }
+      break;
+    case VTM_W_DIAG:
+      break;
+    case VTM_W_SCA:
+      if (radius < 0 || radius > 8) {
+        set_detail("vtm_set_admittance: radius must be 0..8");
+        return VTM_EINVAL;
+      }
+      break;
+    case VTM_W_LINE: {
+      if (!W && npt > 0) {
+        set_detail("vtm_set_admittance: VTM_W_LINE needs W[nports]");
+        return VTM_EINVAL;
+      }
+      VTM_TRY(fetch(user, W, npt));
+      for (size_t s = 0; s < npt; ++s)
+        if (!(user[s] > 0) || !std::isfinite(user[s]) || user[s] != user[P->port_twin[s]]) {
+          set_detail("vtm_set_admittance: W must be positive and equal at both ports of a line "
+                     "(port " + std::to_string(s) + ")");
+          return VTM_EINVAL;
+        }
+      break;
+    }
+    default:
+      set_detail("vtm_set_admittance: unknown kind");
+      return VTM_EINVAL;
+  }
+  const int o_kind = P->w_kind, o_radius = P->w_radius;
+  const double o_alpha = P->w_alpha, o_W = P->W;
+  std::vector<double> o_user = P->w_user;
+  P->w_kind = kind;
+  P->w_alpha = alpha;
+  P->w_radius = radius;
+  P->w_user = std::move(user);
+  if (kind == VTM_W_ALPHA) P->W = alpha;
+  P->w_dirty = true;
+  vtm_status st = assemble_local(P);
+  if (st != VTM_OK) {
+    P->w_kind = o_kind;
+    P->w_alpha = o_alpha;
+    P->w_radius = o_radius;
+    P->w_user = std::move(o_user);
+    P->W = o_W;
+    P->w_dirty = true;
+    assemble_local(P);
+    return st;
+  }
+  P->factored = false;
+  if (P->transposed) {
+    vtm_destroy(P->transposed);
+    P->transposed = nullptr;
+  }
+  return VTM_OK;
+}
+
+extern "C" vtm_status vtm_get_admittance(vtm_plan_t P, double* W) {
+  if (!P || !W) return VTM_EINVAL;
+  const size_t npt = P->port_node.size();
+  if (npt == 0) return VTM_OK;
+  if (is_device_ptr(W)) {
+    VTM_CUDA_TRY(cudaMemcpy(W, P->port_W.data(), npt * sizeof(double), cudaMemcpyHostToDevice));
+  } else {
+    std::copy(P->port_W.begin(), P->port_W.end(), W);
+  }
+  return VTM_OK;
+}
+
 extern "C" vtm_status vtm_set_opts(vtm_plan_t P, const vtm_opts* opts) {
   if (!P) return VTM_EINVAL;
   vtm_opts o{};
@@ -633,8 +857,8 @@ extern "C" vtm_status vtm_set_opts(vtm_plan_t P, const vtm_opts* opts) {
     set_detail("vtm_set_opts: bad precision or history");
     return VTM_EINVAL;
   }
-  if (o.sweep_kernel < 0 || o.sweep_kernel > 6) {
-    set_detail("vtm_set_opts: sweep_kernel must be 0..6");
+  if (o.sweep_kernel < 0 || o.sweep_kernel > 7) {
+    set_detail("vtm_set_opts: sweep_kernel must be 0..7");
     return VTM_EINVAL;
   }
   bool prec_changed = o.precision != P->opts.precision;
@@ -824,9 +1048,11 @@ extern "C" vtm_status vtm_set_values(vtm_plan_t P, const double* vals) {
     set_detail("vtm_set_values: the set of torn lines or lagged couplings changed");
     return VTM_EINVAL;
   }
+  P->w_dirty = true;
   st = assemble_local(P);
   if (st != VTM_OK) {
     P->h_vals = old;
+    P->w_dirty = true;
     assemble_local(P);
     return st;
   }

@@ -35,6 +35,26 @@ namespace vtm {
 // small kernels
 // ---------------------------------------------------------------------------
 
+// Residual term of a torn branch seen from port s (twin t), from the
+// (w_in, w_out) pairs of both ends in the plan's wave scaling w / d:
+//   ((W - 2g) u_s + (W + 2g) u_t - w_in(s) - w_in(t)) / 2,  u = d (w_in + w_out) / (2W)
+//   = d/2 [ (S_s + S_t)/2 - (g/W)(S_s - S_t) - w_in(s) - w_in(t) ],  S = w_in + w_out
+// with kd = (g/W, d) of the line.
+template <class AT, class KD>
+__device__ __forceinline__ AT port_residual(AT wi_s, AT wo_s, AT wi_t, AT wo_t, const KD& kd) {
+  const AT Ss = wi_s + wo_s, St = wi_t + wo_t;
+  return (AT)0.5 * (AT)kd.y * ((AT)0.5 * (Ss + St) - (AT)kd.x * (Ss - St) - wi_s - wi_t);
+}
+
+template <class AT>
+struct KdOf {
+  using type = float2;
+};
+template <>
+struct KdOf<double> {
+  using type = double2;
+};
+
 __global__ void gather_perm_kernel(const int32_t* __restrict__ perm, const double* __restrict__ src,
                                    double* __restrict__ dst, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -43,23 +63,23 @@ __global__ void gather_perm_kernel(const int32_t* __restrict__ perm, const doubl
 }
 
 // dst[perm[i]] (+)= src[i]
-__global__ void scatter_perm_kernel(const int32_t* __restrict__ perm, const double* __restrict__ src,
+template <class VT>
+__global__ void scatter_perm_kernel(const int32_t* __restrict__ perm, const VT* __restrict__ src,
                                     double* __restrict__ dst, int64_t n, int accumulate) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    if (accumulate) dst[perm[i]] += src[i];
-    else dst[perm[i]] = src[i];
+    if (accumulate) dst[perm[i]] += (double)src[i];
+    else dst[perm[i]] = (double)src[i];
   }
 }
 
-// c(s) = 2 W beta_s x0(l(s)) (permuted position pos(s))
+// c(s) = (2 W beta_s / d_s) x0(l(s)) (permuted position pos(s))
 template <class WT, class XT>
-__global__ void port_const_kernel(const int32_t* __restrict__ port_pos, const double* __restrict__ beta,
-                                  const XT* __restrict__ x0, double W, WT* __restrict__ c,
-                                  int64_t nports) {
+__global__ void port_const_kernel(const int32_t* __restrict__ port_pos, const double* __restrict__ bout,
+                                  const XT* __restrict__ x0, WT* __restrict__ c, int64_t nports) {
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nports;
        s += (int64_t)gridDim.x * blockDim.x)
-    c[s] = (WT)(2.0 * W * beta[s] * (double)x0[port_pos[s]]);
+    c[s] = (WT)(bout[s] * (double)x0[port_pos[s]]);
 }
 
 __global__ void gather_perm_f32_kernel(const int32_t* __restrict__ perm, const double* __restrict__ src,
@@ -71,25 +91,39 @@ __global__ void gather_perm_f32_kernel(const int32_t* __restrict__ perm, const d
 
 // v(l(s)) += sum over the node's ports of beta_s w_in(s); w_in of the chosen
 // sweep sits in state[slot][s].x
-template <class WT>
+template <class WT, class VT>
 __global__ void inject_kernel(const int32_t* __restrict__ port_pos, const uint8_t* __restrict__ run,
                               const double* __restrict__ beta, const WT* __restrict__ st,
-                              double* __restrict__ v, int64_t nports) {
+                              VT* __restrict__ v, int64_t nports) {
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nports;
        s += (int64_t)gridDim.x * blockDim.x) {
     int nr = run[s];
     if (!nr) continue;
     double acc = 0.0;
     for (int q = 0; q < nr; ++q) acc += beta[s + q] * (double)st[2 * (s + q)];
-    v[port_pos[s]] += acc;
+    v[port_pos[s]] = (VT)((double)v[port_pos[s]] + acc);
   }
 }
 
 // Fixed-order sum of `count` doubles by one block (result valid in thread 0).
+// Loads go out 16 at a time (the sum runs at the end of every sweep, on one
+// CTA, so its latency is on the critical path); each thread still adds its
+// elements in increasing index order.
 __device__ double block_sum_fixed(const double* __restrict__ a, int64_t count) {
   __shared__ double red[32];
+  constexpr int kMLP = 16;
   double acc = 0.0;
-  for (int64_t i = threadIdx.x; i < count; i += blockDim.x) acc += a[i];
+  const int64_t stride = blockDim.x;
+  for (int64_t base = threadIdx.x; base < count; base += kMLP * stride) {
+    double v[kMLP];
+#pragma unroll
+    for (int j = 0; j < kMLP; ++j) {
+      const int64_t i = base + j * stride;
+      v[j] = i < count ? __ldcg(a + i) : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < kMLP; ++j) acc += v[j];
+  }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   __syncthreads();
@@ -98,6 +132,21 @@ __device__ double block_sum_fixed(const double* __restrict__ a, int64_t count) {
   double tot = 0.0;
   if (threadIdx.x == 0)
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += red[i];
+  __syncthreads();
+  return tot;
+}
+
+// Fixed-order block sum of one float per thread (result valid in thread 0).
+__device__ float block_sum_value_f(float v) {
+  __shared__ float red3[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red3[w] = v;
+  __syncthreads();
+  float tot = 0.f;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += red3[i];
   __syncthreads();
   return tot;
 }
@@ -216,9 +265,9 @@ template <class TT, class WT>
 __global__ void __launch_bounds__(256) sweep_kernel(
     const TT* __restrict__ T, const int64_t* __restrict__ T_off, const int32_t* __restrict__ T_ld,
     const int32_t* __restrict__ port_off, const int32_t* __restrict__ order,
-    const int32_t* __restrict__ twin, const double* __restrict__ g,
+    const int32_t* __restrict__ twin, const typename KdOf<WT>::type* __restrict__ kd,
     const uint8_t* __restrict__ run, const WT* __restrict__ c, WT* __restrict__ state,
-    int64_t nports, double W, SweepCtrl* __restrict__ ctrl, double* __restrict__ partials,
+    int64_t nports, SweepCtrl* __restrict__ ctrl, double* __restrict__ partials,
     double* __restrict__ hist, int hist_len, int nparts) {
   using AT = WT;  // accumulation type: FP64 for FP64 waves, FP32 otherwise
   extern __shared__ unsigned char smem_raw[];
@@ -238,7 +287,6 @@ __global__ void __launch_bounds__(256) sweep_kernel(
   AT* rs = reinterpret_cast<AT*>(smem_raw + sizeof(WT) * ((p + 1) & ~1));
   const WT* prev = state + (size_t)((k - 1) & 1) * nports * 2;
   WT* cur = state + (size_t)(k & 1) * nports * 2;
-  const AT hW = (AT)W, inv2W = (AT)(0.5 / W);
   // gather the incident waves (delay 1) and the residual terms of sweep k-1
   for (int s = threadIdx.x; s < p; s += blockDim.x) {
     const int gs = p0 + s;
@@ -248,9 +296,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(
       const AT wi_t = (AT)prev[2 * tw], wo_t = (AT)prev[2 * tw + 1];
       const AT wi_s = (AT)prev[2 * gs], wo_s = (AT)prev[2 * gs + 1];
       wi = wo_t;
-      const AT gg = (AT)g[gs];
-      const AT us = (wi_s + wo_s) * inv2W, ut = (wi_t + wo_t) * inv2W;
-      rc = (AT)0.5 * ((hW - 2 * gg) * us + (hW + 2 * gg) * ut - wi_s - wi_t);
+      rc = port_residual<AT>(wi_s, wo_s, wi_t, wo_t, kd[gs]);
     }
     w_in[s] = (WT)wi;
     rs[s] = rc;
@@ -339,9 +385,9 @@ template <class TT, class WT, int VEC, int MAXV>
 __global__ void __launch_bounds__(256) sweep_staged_kernel(
     const TT* __restrict__ T, const int64_t* __restrict__ T_off, const int32_t* __restrict__ T_ld,
     const int32_t* __restrict__ port_off, const int32_t* __restrict__ order,
-    const int32_t* __restrict__ twin, const double* __restrict__ g,
+    const int32_t* __restrict__ twin, const typename KdOf<WT>::type* __restrict__ kd,
     const uint8_t* __restrict__ run, const WT* __restrict__ c, WT* __restrict__ state,
-    int64_t nports, double W, SweepCtrl* __restrict__ ctrl, double* __restrict__ partials,
+    int64_t nports, SweepCtrl* __restrict__ ctrl, double* __restrict__ partials,
     double* __restrict__ hist, int hist_len, int nparts, int ch, int ld_max) {
   using AT = WT;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -397,7 +443,6 @@ __global__ void __launch_bounds__(256) sweep_staged_kernel(
     for (int i = 0; i < kStages; ++i) issue_next();
   const WT* prev = state + (size_t)((k - 1) & 1) * nports * 2;
   WT* cur = state + (size_t)(k & 1) * nports * 2;
-  const AT hW = (AT)W, inv2W = (AT)(0.5 / W);
   uint32_t consumed = 0;
   for (int it = blockIdx.x; it < nparts; it += gridDim.x) {
     const int tile = order[it];
@@ -414,9 +459,7 @@ __global__ void __launch_bounds__(256) sweep_staged_kernel(
         const AT wi_t = (AT)prev[2 * tw], wo_t = (AT)prev[2 * tw + 1];
         const AT wi_s = (AT)prev[2 * gs], wo_s = (AT)prev[2 * gs + 1];
         wi = wo_t;
-        const AT gg = (AT)g[gs];
-        const AT us = (wi_s + wo_s) * inv2W, ut = (wi_t + wo_t) * inv2W;
-        rc = (AT)0.5 * ((hW - 2 * gg) * us + (hW + 2 * gg) * ut - wi_s - wi_t);
+        rc = port_residual<AT>(wi_s, wo_s, wi_t, wo_t, kd[gs]);
       }
       w_in[s] = (WT)wi;
       rs[s] = rc;
@@ -564,9 +607,9 @@ template <> struct VecLoadG<__nv_bfloat16, 8> {
 template <class TT, class WT, int VEC, int NT, int KB>
 __global__ void __launch_bounds__(NT) sweep_vec_kernel(
     const TT* __restrict__ T, const TileDesc* __restrict__ tdesc,
-    const int32_t* __restrict__ twin, const double* __restrict__ g,
+    const int32_t* __restrict__ twin, const typename KdOf<WT>::type* __restrict__ kd,
     const uint8_t* __restrict__ run, const WT* __restrict__ c, WT* __restrict__ state,
-    int64_t nports, double W, SweepCtrl* __restrict__ ctrl, double* __restrict__ partials,
+    int64_t nports, SweepCtrl* __restrict__ ctrl, double* __restrict__ partials,
     double* __restrict__ hist, int hist_len, int nparts, int ld_max) {
   using AT = WT;
   using LD = VecLoadG<TT, VEC>;
@@ -606,7 +649,6 @@ __global__ void __launch_bounds__(NT) sweep_vec_kernel(
   const int k = s_k;
   const WT* prev = state + (size_t)((k - 1) & 1) * nports * 2;
   WT* cur = state + (size_t)(k & 1) * nports * 2;
-  const AT hW = (AT)W, inv2W = (AT)(0.5 / W);
   for (int s = tid; s < p; s += blockDim.x) {
     const int gs = p0 + s;
     AT wi = 0, rc = 0;
@@ -615,9 +657,7 @@ __global__ void __launch_bounds__(NT) sweep_vec_kernel(
       const AT wi_t = (AT)prev[2 * tw], wo_t = (AT)prev[2 * tw + 1];
       const AT wi_s = (AT)prev[2 * gs], wo_s = (AT)prev[2 * gs + 1];
       wi = wo_t;
-      const AT gg = (AT)g[gs];
-      const AT us = (wi_s + wo_s) * inv2W, ut = (wi_t + wo_t) * inv2W;
-      rc = (AT)0.5 * ((hW - 2 * gg) * us + (hW + 2 * gg) * ut - wi_s - wi_t);
+      rc = port_residual<AT>(wi_s, wo_s, wi_t, wo_t, kd[gs]);
     }
     w_in[s] = (WT)wi;
     rs[s] = rc;
@@ -702,50 +742,243 @@ __global__ void __launch_bounds__(NT) sweep_vec_kernel(
 //     one exchange over bit 1 (8 shuffles, a fixed summation tree).
 // part[a][b] holds block b's contribution to row block a; the outputs sum
 // them in the fixed order b = 0..nb-1, so every sweep is bitwise repeatable.
+// Two ways to bring a tile's blocks in: 16-byte register loads a few blocks
+// ahead (sweep_sym_kernel), or one bulk copy of the whole packed tile into
+// shared memory issued before anything else (sweep_symb_kernel).
 // ---------------------------------------------------------------------------
 
 template <class TT>
 struct SymLoad;
+// FP32: lane l holds float4 number l (row l/4, columns 4(l%4)..+3) and
+// number l + 32 (row l/4 + 8, same columns): each load instruction of the
+// warp covers 512 contiguous bytes (no shared-memory bank conflicts).
 template <> struct SymLoad<float> {
   struct raw {
     float4 a, b;
   };
-  __device__ static raw load(const float* p) {
+  __device__ static raw load(const float* blk, int lane) {
     raw r;
-    r.a = __ldg(reinterpret_cast<const float4*>(p));
-    r.b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+    r.a = __ldg(reinterpret_cast<const float4*>(blk) + lane);
+    r.b = __ldg(reinterpret_cast<const float4*>(blk) + lane + 32);
     return r;
   }
-  __device__ static void unpack(const raw& v, float (&o)[8]) {
-    o[0] = v.a.x; o[1] = v.a.y; o[2] = v.a.z; o[3] = v.a.w;
-    o[4] = v.b.x; o[5] = v.b.y; o[6] = v.b.z; o[7] = v.b.w;
+  __device__ static raw load_shared(const float* blk, int lane) {
+    raw r;
+    r.a = reinterpret_cast<const float4*>(blk)[lane];
+    r.b = reinterpret_cast<const float4*>(blk)[lane + 32];
+    return r;
   }
 };
+// BF16: lane l holds the 16 bytes number l (row l/2, columns 8(l%2)..+7).
 template <> struct SymLoad<__nv_bfloat16> {
   using raw = uint4;
-  __device__ static raw load(const __nv_bfloat16* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }
-  __device__ static void unpack(const raw& v, float (&o)[8]) {
-    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+  __device__ static raw load(const __nv_bfloat16* blk, int lane) {
+    return __ldg(reinterpret_cast<const uint4*>(blk) + lane);
+  }
+  __device__ static raw load_shared(const __nv_bfloat16* blk, int lane) {
+    return reinterpret_cast<const uint4*>(blk)[lane];
+  }
+};
+
+// Per-port inputs that do not depend on the sweep index, loaded at kernel
+// start by thread tid for ports tid + j NT (p <= 256).
+template <int NT>
+struct SymPorts {
+  static constexpr int PPT = 16 * kSymB / NT;
+  int tw[PPT], rn[PPT];
+  float2 kq[PPT];
+  float cq[PPT];
+  __device__ void load(const int32_t* __restrict__ twin, const float2* __restrict__ kd,
+                       const uint8_t* __restrict__ run, const float* __restrict__ c, int p0, int p) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      float2 f = __bfloat1622float2(h[i]);
-      o[2 * i] = f.x;
-      o[2 * i + 1] = f.y;
+    for (int j = 0; j < PPT; ++j) {
+      const int s = threadIdx.x + j * NT;
+      tw[j] = rn[j] = 0;
+      kq[j] = make_float2(0.f, 0.f);
+      cq[j] = 0.f;
+      if (s < p) {
+        tw[j] = twin[p0 + s];
+        kq[j] = kd[p0 + s];
+        cq[j] = c[p0 + s];
+        rn[j] = run[p0 + s];
+      }
     }
   }
 };
 
+// Incident waves of the tile (zero past p, the padding of the last block)
+// and this thread's share of the squared node residuals of sweep k - 1.
+template <int NT>
+__device__ __forceinline__ float sym_gather(const SymPorts<NT>& pt, const float* __restrict__ prev,
+                                            float* w_in, float* rs, int p0, int p, int nb, int k) {
+#pragma unroll
+  for (int j = 0; j < SymPorts<NT>::PPT; ++j) {
+    const int s = threadIdx.x + j * NT;
+    if (s < nb * kSymB) {
+      float wi = 0.f, rc = 0.f;
+      if (k > 1 && s < p) {
+        const float2 wt = *reinterpret_cast<const float2*>(prev + 2 * (size_t)pt.tw[j]);
+        const float2 ws = *reinterpret_cast<const float2*>(prev + 2 * (size_t)(p0 + s));
+        wi = wt.y;
+        rc = port_residual<float>(ws.x, ws.y, wt.x, wt.y, pt.kq[j]);
+      }
+      w_in[s] = wi;
+      rs[s] = rc;
+    }
+  }
+  __syncthreads();
+  float sq = 0.f;
+  if (k > 1) {
+#pragma unroll
+    for (int j = 0; j < SymPorts<NT>::PPT; ++j) {
+      const int s = threadIdx.x + j * NT;
+      if (s < p && pt.rn[j]) {
+        float rr = 0.f;
+        for (int q = 0; q < pt.rn[j]; ++q) rr += rs[s + q];
+        sq += rr * rr;
+      }
+    }
+  }
+  return sq;
+}
+
+// One 16x16 block (bi, bj) of a warp: the row-block partial T_blk w(bj) and,
+// off the diagonal, the column-block partial T_blk^T w(bi) (see above).
+__device__ __forceinline__ void sym_block(const SymLoad<float>::raw& v, int bi, int bj, int nb,
+                                          int lane, const float* w_in, float* part) {
+  constexpr int B = kSymB;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int r1 = lane >> 2, cg = lane & 3;
+  const float4 wc = *reinterpret_cast<const float4*>(w_in + bj * B + cg * 4);
+  float a1 = v.a.x * wc.x;
+  a1 = fmaf(v.a.y, wc.y, a1);
+  a1 = fmaf(v.a.z, wc.z, a1);
+  a1 = fmaf(v.a.w, wc.w, a1);
+  float a2 = v.b.x * wc.x;
+  a2 = fmaf(v.b.y, wc.y, a2);
+  a2 = fmaf(v.b.z, wc.z, a2);
+  a2 = fmaf(v.b.w, wc.w, a2);
+  // rows r1 and r1 + 8: sums over the four lanes of a row (bits 0, 1)
+  const bool b0 = lane & 1;
+  float t = (b0 ? a2 : a1) + __shfl_xor_sync(FULL, b0 ? a1 : a2, 1);
+  t += __shfl_xor_sync(FULL, t, 2);
+  if (!(lane & 2)) part[(bi * nb + bj) * B + (b0 ? r1 + 8 : r1)] = t;
+  if (bi != bj) {
+    const float wr1 = w_in[bi * B + r1], wr2 = w_in[bi * B + r1 + 8];
+    const float u0 = fmaf(v.b.x, wr2, v.a.x * wr1);
+    const float u1 = fmaf(v.b.y, wr2, v.a.y * wr1);
+    const float u2 = fmaf(v.b.z, wr2, v.a.z * wr1);
+    const float u3 = fmaf(v.b.w, wr2, v.a.w * wr1);
+    // columns 4 cg..+3: sums over the eight lanes of a column group (bits 4, 3, 2)
+    const bool b4 = lane & 16, b3 = lane & 8;
+    float k0 = b4 ? u2 : u0, k1 = b4 ? u3 : u1;
+    k0 += __shfl_xor_sync(FULL, b4 ? u0 : u2, 16);
+    k1 += __shfl_xor_sync(FULL, b4 ? u1 : u3, 16);
+    float t1 = (b3 ? k1 : k0) + __shfl_xor_sync(FULL, b3 ? k0 : k1, 8);
+    t1 += __shfl_xor_sync(FULL, t1, 4);
+    if (!(lane & 4)) part[(bj * nb + bi) * B + cg * 4 + (b4 ? 2 : 0) + (b3 ? 1 : 0)] = t1;
+  }
+}
+
+__device__ __forceinline__ void sym_block(const SymLoad<__nv_bfloat16>::raw& raw, int bi, int bj,
+                                          int nb, int lane, const float* w_in, float* part) {
+  constexpr int B = kSymB;
+  constexpr unsigned FULL = 0xffffffffu;
+  float v[8];
+  {
+    const __nv_bfloat162* hv = reinterpret_cast<const __nv_bfloat162*>(&raw);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 f = __bfloat1622float2(hv[i]);
+      v[2 * i] = f.x;
+      v[2 * i + 1] = f.y;
+    }
+  }
+  const int r = lane >> 1, h = lane & 1;
+  const float4 c0 = *reinterpret_cast<const float4*>(w_in + bj * B + h * 8);
+  const float4 c1 = *reinterpret_cast<const float4*>(w_in + bj * B + h * 8 + 4);
+  float a = v[0] * c0.x;
+  a = fmaf(v[1], c0.y, a);
+  a = fmaf(v[2], c0.z, a);
+  a = fmaf(v[3], c0.w, a);
+  a = fmaf(v[4], c1.x, a);
+  a = fmaf(v[5], c1.y, a);
+  a = fmaf(v[6], c1.z, a);
+  a = fmaf(v[7], c1.w, a);
+  a += __shfl_xor_sync(FULL, a, 1);
+  if (h == 0) part[(bi * nb + bj) * B + r] = a;
+  if (bi != bj) {
+    const float wr = w_in[bi * B + r];
+    float u[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) u[j] = v[j] * wr;
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    float t4[4], t2[2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float send = b4 ? u[i] : u[i + 4];
+      const float keep = b4 ? u[i + 4] : u[i];
+      t4[i] = keep + __shfl_xor_sync(FULL, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const float send = b3 ? t4[i] : t4[i + 2];
+      const float keep = b3 ? t4[i + 2] : t4[i];
+      t2[i] = keep + __shfl_xor_sync(FULL, send, 8);
+    }
+    float t1;
+    {
+      const float send = b2 ? t2[0] : t2[1];
+      const float keep = b2 ? t2[1] : t2[0];
+      t1 = keep + __shfl_xor_sync(FULL, send, 4);
+    }
+    t1 += __shfl_xor_sync(FULL, t1, 2);
+    const int jc = (b4 ? 4 : 0) + (b3 ? 2 : 0) + (b2 ? 1 : 0);
+    if (!(lane & 2)) part[(bj * nb + bi) * B + h * 8 + jc] = t1;
+  }
+}
+
+// w_out = c + sum of the row block's partials in block order; then the
+// tile's residual partial and the last-CTA close of the sweep.
+template <int NT>
+__device__ __forceinline__ void sym_finish(const SymPorts<NT>& pt, const float* part, const float* w_in,
+                                           float* __restrict__ cur, int p0, int p, int nb, int tile,
+                                           double tile_sq, int k, SweepCtrl* __restrict__ ctrl,
+                                           double* __restrict__ partials, double* __restrict__ hist,
+                                           int hist_len, int nparts, bool* s_last) {
+  constexpr int B = kSymB;
+#pragma unroll
+  for (int j = 0; j < SymPorts<NT>::PPT; ++j) {
+    const int s = threadIdx.x + j * NT;
+    if (s < p) {
+      const int a = s / B, rr = s % B;
+      float acc = pt.cq[j];
+      for (int b = 0; b < nb; ++b) acc += part[(a * nb + b) * B + rr];
+      *reinterpret_cast<float2*>(cur + 2 * (size_t)(p0 + s)) = make_float2(w_in[s], acc);
+    }
+  }
+  if (threadIdx.x == 0) {
+    partials[tile] = tile_sq;
+    __threadfence();
+    *s_last = atomicAdd(&ctrl->counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!*s_last) return;
+  __threadfence();
+  const double tot = block_sum_fixed(partials, nparts);
+  if (threadIdx.x == 0) sweep_decide(ctrl, k, tot, hist, hist_len);
+}
+
 template <class TT, int NT, int KB>
-__global__ void __launch_bounds__(NT) sweep_sym_kernel(
+__global__ void __launch_bounds__(NT, 768 / NT) sweep_sym_kernel(
     const TT* __restrict__ Tp, const TileDesc* __restrict__ tdesc,
-    const int32_t* __restrict__ twin, const double* __restrict__ g,
+    const int32_t* __restrict__ twin, const float2* __restrict__ kd,
     const uint8_t* __restrict__ run, const float* __restrict__ c, float* __restrict__ state,
-    int64_t nports, double W, SweepCtrl* __restrict__ ctrl, double* __restrict__ partials,
-    double* __restrict__ hist, int hist_len, int nparts, int pp_max) {
+    int64_t nports, SweepCtrl* __restrict__ ctrl,
+    double* __restrict__ partials, double* __restrict__ hist, int hist_len, int nparts, int pp_max) {
   using LD = SymLoad<TT>;
   constexpr int NW = NT / 32;
   constexpr int B = kSymB;
-  constexpr unsigned FULL = 0xffffffffu;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_k, s_flag;
   __shared__ bool s_last;
@@ -754,8 +987,7 @@ __global__ void __launch_bounds__(NT) sweep_sym_kernel(
   const int tile = dsc.tile, p0 = dsc.p0, p = dsc.p;
   const int nb = (p + B - 1) / B;
   const int nblk = nb * (nb + 1) / 2;
-  const int r = lane >> 1, h = lane & 1;
-  const TT* Tl = Tp + dsc.Tp_off + r * B + h * 8;
+  const TT* Tl = Tp + dsc.Tp_off;
   float* w_in = reinterpret_cast<float*>(smem_raw);
   float* rs = w_in + pp_max;
   float* part = rs + pp_max;
@@ -764,8 +996,10 @@ __global__ void __launch_bounds__(NT) sweep_sym_kernel(
 #pragma unroll
   for (int b = 0; b < KB; ++b) {
     const int kk = warp + b * NW;
-    if (kk < nblk) buf[b] = LD::load(Tl + (size_t)kk * B * B);
+    if (kk < nblk) buf[b] = LD::load(Tl + (size_t)kk * B * B, lane);
   }
+  SymPorts<NT> pt;
+  pt.load(twin, kd, run, c, p0, p);
   if (tid == 0) {
     s_k = *((volatile int*)&ctrl->k);
     s_flag = *((volatile int*)&ctrl->flag);
@@ -775,35 +1009,8 @@ __global__ void __launch_bounds__(NT) sweep_sym_kernel(
   const int k = s_k;
   const float* prev = state + (size_t)((k - 1) & 1) * nports * 2;
   float* cur = state + (size_t)(k & 1) * nports * 2;
-  const float hW = (float)W, inv2W = (float)(0.5 / W);
-  for (int s = tid; s < nb * B; s += NT) {
-    float wi = 0.f, rc = 0.f;
-    if (k > 1 && s < p) {
-      const int gs = p0 + s;
-      const int tw = twin[gs];
-      const float wi_t = prev[2 * tw], wo_t = prev[2 * tw + 1];
-      const float wi_s = prev[2 * gs], wo_s = prev[2 * gs + 1];
-      wi = wo_t;
-      const float gg = (float)g[gs];
-      const float us = (wi_s + wo_s) * inv2W, ut = (wi_t + wo_t) * inv2W;
-      rc = 0.5f * ((hW - 2 * gg) * us + (hW + 2 * gg) * ut - wi_s - wi_t);
-    }
-    w_in[s] = wi;  // zero past p: the padding of the last block
-    rs[s] = rc;
-  }
-  __syncthreads();
-  float sq = 0.f;
-  if (k > 1) {
-    for (int s = tid; s < p; s += NT) {
-      const int nr = run[p0 + s];
-      if (nr) {
-        float rr = 0.f;
-        for (int q = 0; q < nr; ++q) rr += rs[s + q];
-        sq += rr * rr;
-      }
-    }
-  }
-  const double tile_sq = block_sum_value((double)sq);
+  const float sq = sym_gather<NT>(pt, prev, w_in, rs, p0, p, nb, k);
+  const double tile_sq = (double)block_sum_value_f(sq);
   int bi = 0, off = warp;  // block warp + i NW is (bi, bi + off) once off < nb - bi
   for (int base = 0; base < nblk; base += KB * NW) {
 #pragma unroll
@@ -814,74 +1021,90 @@ __global__ void __launch_bounds__(NT) sweep_sym_kernel(
           off -= nb - bi;
           ++bi;
         }
-        const int bj = bi + off;
-        float v[8];
-        LD::unpack(buf[b], v);
+        const typename LD::raw v = buf[b];
         const int kn = kk + KB * NW;
-        if (kn < nblk) buf[b] = LD::load(Tl + (size_t)kn * B * B);
-        const float4 c0 = *reinterpret_cast<const float4*>(w_in + bj * B + h * 8);
-        const float4 c1 = *reinterpret_cast<const float4*>(w_in + bj * B + h * 8 + 4);
-        float a = v[0] * c0.x;
-        a = fmaf(v[1], c0.y, a);
-        a = fmaf(v[2], c0.z, a);
-        a = fmaf(v[3], c0.w, a);
-        a = fmaf(v[4], c1.x, a);
-        a = fmaf(v[5], c1.y, a);
-        a = fmaf(v[6], c1.z, a);
-        a = fmaf(v[7], c1.w, a);
-        a += __shfl_xor_sync(FULL, a, 1);
-        if (h == 0) part[(bi * nb + bj) * B + r] = a;
-        if (bi != bj) {
-          const float wr = w_in[bi * B + r];
-          float u[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) u[j] = v[j] * wr;
-          const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
-          float t4[4], t2[2];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const float send = b4 ? u[i] : u[i + 4];
-            const float keep = b4 ? u[i + 4] : u[i];
-            t4[i] = keep + __shfl_xor_sync(FULL, send, 16);
-          }
-#pragma unroll
-          for (int i = 0; i < 2; ++i) {
-            const float send = b3 ? t4[i] : t4[i + 2];
-            const float keep = b3 ? t4[i + 2] : t4[i];
-            t2[i] = keep + __shfl_xor_sync(FULL, send, 8);
-          }
-          float t1;
-          {
-            const float send = b2 ? t2[0] : t2[1];
-            const float keep = b2 ? t2[1] : t2[0];
-            t1 = keep + __shfl_xor_sync(FULL, send, 4);
-          }
-          t1 += __shfl_xor_sync(FULL, t1, 2);
-          const int jc = (b4 ? 4 : 0) + (b3 ? 2 : 0) + (b2 ? 1 : 0);
-          if (!(lane & 2)) part[(bj * nb + bi) * B + h * 8 + jc] = t1;
-        }
+        if (kn < nblk) buf[b] = LD::load(Tl + (size_t)kn * B * B, lane);
+        sym_block(v, bi, bi + off, nb, lane, w_in, part);
         off += NW;
       }
     }
   }
   __syncthreads();
-  for (int s = tid; s < p; s += NT) {
-    const int a = s / B, rr = s % B;
-    float acc = c[p0 + s];
-    for (int b = 0; b < nb; ++b) acc += part[(a * nb + b) * B + rr];
-    cur[2 * (p0 + s)] = w_in[s];
-    cur[2 * (p0 + s) + 1] = acc;
-  }
+  sym_finish<NT>(pt, part, w_in, cur, p0, p, nb, tile, tile_sq, k, ctrl, partials, hist, hist_len,
+                 nparts, &s_last);
+}
+
+// The whole packed tile arrives by one bulk copy into shared memory, issued
+// first; the wave gather and the residual run while it is in flight.  The
+// wait is bounded: on timeout the CTA waits (bounded) for its copy, sets flag
+// 5 and leaves the sweep unfinished, which the host reports as VTM_ETIMEOUT.
+template <class TT, int NT>
+__global__ void __launch_bounds__(NT) sweep_symb_kernel(
+    const TT* __restrict__ Tp, const TileDesc* __restrict__ tdesc,
+    const int32_t* __restrict__ twin, const float2* __restrict__ kd,
+    const uint8_t* __restrict__ run, const float* __restrict__ c, float* __restrict__ state,
+    int64_t nports, SweepCtrl* __restrict__ ctrl,
+    double* __restrict__ partials, double* __restrict__ hist, int hist_len, int nparts, int pp_max,
+    int tbuf_elems) {
+  using LD = SymLoad<TT>;
+  constexpr int NW = NT / 32;
+  constexpr int B = kSymB;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ uint64_t bar;
+  __shared__ int s_k, s_flag, s_timeout;
+  __shared__ bool s_last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const TileDesc dsc = tdesc[blockIdx.x];
+  const int tile = dsc.tile, p0 = dsc.p0, p = dsc.p;
+  const int nb = (p + B - 1) / B;
+  const int nblk = nb * (nb + 1) / 2;
+  TT* tb = reinterpret_cast<TT*>(smem_raw);
+  float* w_in = reinterpret_cast<float*>(smem_raw + (size_t)tbuf_elems * sizeof(TT));
+  float* rs = w_in + pp_max;
+  float* part = rs + pp_max;
+  const uint32_t bytes = (uint32_t)nblk * B * B * sizeof(TT);
   if (tid == 0) {
-    partials[tile] = tile_sq;
-    __threadfence();
-    s_last = atomicAdd(&ctrl->counter, 1u) == gridDim.x - 1;
+    // launches past the end of the solve copy nothing
+    s_k = *((volatile int*)&ctrl->k);
+    s_flag = *((volatile int*)&ctrl->flag);
+    s_timeout = 0;
+    if (!s_flag && bytes) {
+      mbar_init(&bar, 1);
+      fence_mbar_init();
+      mbar_arrive_expect_tx(&bar, bytes);
+      bulk_copy_g2s(tb, Tp + dsc.Tp_off, bytes, &bar);
+    }
+  }
+  SymPorts<NT> pt;
+  pt.load(twin, kd, run, c, p0, p);
+  __syncthreads();
+  if (s_flag) return;
+  const int k = s_k;
+  const float* prev = state + (size_t)((k - 1) & 1) * nports * 2;
+  float* cur = state + (size_t)(k & 1) * nports * 2;
+  const float sq = sym_gather<NT>(pt, prev, w_in, rs, p0, p, nb, k);
+  const double tile_sq = (double)block_sum_value_f(sq);
+  if (tid == 0 && bytes && !mbar_wait_bounded(&bar, 0, kWaitPolls)) s_timeout = 1;
+  __syncthreads();
+  if (s_timeout) {
+    if (tid == 0) {
+      mbar_wait_bounded(&bar, 0, kWaitPolls);
+      atomicExch(&ctrl->flag, 5);
+    }
+    return;
+  }
+  int bi = 0, off = warp;
+  for (int kk = warp; kk < nblk; kk += NW) {
+    while (off >= nb - bi) {
+      off -= nb - bi;
+      ++bi;
+    }
+    sym_block(LD::load_shared(tb + (size_t)kk * B * B, lane), bi, bi + off, nb, lane, w_in, part);
+    off += NW;
   }
   __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  const double tot = block_sum_fixed(partials, nparts);
-  if (tid == 0) sweep_decide(ctrl, k, tot, hist, hist_len);
+  sym_finish<NT>(pt, part, w_in, cur, p0, p, nb, tile, tile_sq, k, ctrl, partials, hist, hist_len,
+                 nparts, &s_last);
 }
 
 // ---------------------------------------------------------------------------
@@ -900,14 +1123,21 @@ struct SweepLaunch {
   int prec;
 };
 
+// per-port residual coefficients (g/W, d) in the wave precision
+template <class WT>
+static const typename KdOf<WT>::type* kd_of(vtm_plan_s* P) {
+  if constexpr (std::is_same<WT, double>::value) return P->d_kd.as<double2>();
+  else return P->d_kd32.as<float2>();
+}
+
 template <class TT, class WT>
 static void launch_sweep(vtm_plan_s* P, const TT* T, const WT* c, WT* state, int threads,
                          size_t smem, double* hist, int hist_len) {
   sweep_kernel<TT, WT><<<P->nparts, threads, smem, P->stream>>>(
       T, P->tabs.T_off.as<int64_t>(), P->tabs.T_ld.as<int32_t>(), P->tabs.port_off.as<int32_t>(),
-      P->tabs.order.as<int32_t>(), P->d_twin.as<int32_t>(), P->d_g.as<double>(),
-      P->d_run.as<uint8_t>(), c, state, (int64_t)P->port_node.size(), P->W,
-      P->d_ctrl.as<SweepCtrl>(), P->d_partials.as<double>(), hist, hist_len, P->nparts);
+      P->tabs.order.as<int32_t>(), P->d_twin.as<int32_t>(), kd_of<WT>(P), P->d_run.as<uint8_t>(), c,
+      state, (int64_t)P->port_node.size(), P->d_ctrl.as<SweepCtrl>(), P->d_partials.as<double>(), hist,
+      hist_len, P->nparts);
 }
 
 // Scoped access-policy window on the plan's stream over the FP32/BF16
@@ -1019,6 +1249,11 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   const int pp_max = std::max(kSymB, (P->max_ports + kSymB - 1) / kSymB * kSymB);
   const int nb_max = pp_max / kSymB;
   const size_t sym_smem = (2 * (size_t)pp_max + (size_t)nb_max * nb_max * kSymB) * sizeof(float) + 16;
+  // bulk-copy variant: the largest packed tile plus the same work arrays
+  const int tbuf_elems = nb_max * (nb_max + 1) / 2 * kSymB * kSymB;
+  const size_t symb_smem = (size_t)tbuf_elems * (prec == VTM_PREC_FP32 ? 4 : 2) + sym_smem;
+  const bool symb_ok = sym_ok && symb_smem <= 160 * 1024;
+
   if (staged) {
     if (prec == VTM_PREC_FP64)
       VTM_CUDA_TRY(cudaFuncSetAttribute(sweep_staged_kernel<double, double, 2, 4>,
@@ -1043,38 +1278,51 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
     }
     kern<<<st_grid, st_threads, st_smem, s>>>(
         T, P->tabs.T_off.as<int64_t>(), P->tabs.T_ld.as<int32_t>(), P->tabs.port_off.as<int32_t>(),
-        P->tabs.order.as<int32_t>(), P->d_twin.as<int32_t>(), P->d_g.as<double>(),
-        P->d_run.as<uint8_t>(), c, state, npt_, P->W, P->d_ctrl.as<SweepCtrl>(),
-        P->d_partials.as<double>(), hist, hist_len, P->nparts, ch, ld_max);
+        P->tabs.order.as<int32_t>(), P->d_twin.as<int32_t>(),
+        kd_of<std::remove_pointer_t<decltype(state)>>(P), P->d_run.as<uint8_t>(), c, state, npt_,
+        P->d_ctrl.as<SweepCtrl>(), P->d_partials.as<double>(), hist, hist_len, P->nparts, ch, ld_max);
   };
   // keep as much of the low-precision reflection matrices in L2 as the
   // persisting carve-out allows (restored after the sweeps)
   L2Window l2win(P, prec);
   // one sweep launch with kernel `kc` (1 direct, 2 staged, 3/4 vector loads with
-  // 256/128 threads, 5/6 packed symmetric with 128/256 threads)
+  // 256/128 threads, 5/6 packed symmetric with 128/64 threads, 7 packed
+  // symmetric with the tile in shared memory by one bulk copy)
   auto launch_one = [&](int kc) {
+    if (kc == 7) {
+      auto go = [&](auto* kern, const auto* Tp) {
+        kern<<<P->nparts, 128, symb_smem, s>>>(
+            Tp, P->d_tdesc.as<TileDesc>(), P->d_twin.as<int32_t>(), P->d_kd32.as<float2>(),
+            P->d_run.as<uint8_t>(), P->d_c32.as<float>(), P->d_state32.as<float>(), npt_,
+            P->d_ctrl.as<SweepCtrl>(), P->d_partials.as<double>(), hist, hist_len, P->nparts, pp_max,
+            tbuf_elems);
+      };
+      if (prec == VTM_PREC_FP32) go(sweep_symb_kernel<float, 128>, P->d_Tp32.as<float>());
+      else go(sweep_symb_kernel<__nv_bfloat16, 128>, P->d_Tp16.as<__nv_bfloat16>());
+      return;
+    }
     if (kc == 5 || kc == 6) {
       auto go = [&](auto* kern, int nt, const auto* Tp) {
         kern<<<P->nparts, nt, sym_smem, s>>>(
-            Tp, P->d_tdesc.as<TileDesc>(), P->d_twin.as<int32_t>(), P->d_g.as<double>(),
-            P->d_run.as<uint8_t>(), P->d_c32.as<float>(), P->d_state32.as<float>(), npt_, P->W,
+            Tp, P->d_tdesc.as<TileDesc>(), P->d_twin.as<int32_t>(), P->d_kd32.as<float2>(),
+            P->d_run.as<uint8_t>(), P->d_c32.as<float>(), P->d_state32.as<float>(), npt_,
             P->d_ctrl.as<SweepCtrl>(), P->d_partials.as<double>(), hist, hist_len, P->nparts, pp_max);
       };
       if (prec == VTM_PREC_FP32) {
         if (kc == 5) go(sweep_sym_kernel<float, 128, 4>, 128, P->d_Tp32.as<float>());
-        else go(sweep_sym_kernel<float, 256, 4>, 256, P->d_Tp32.as<float>());
+        else go(sweep_sym_kernel<float, 64, 4>, 64, P->d_Tp32.as<float>());
       } else {
-        if (kc == 5) go(sweep_sym_kernel<__nv_bfloat16, 128, 4>, 128, P->d_Tp16.as<__nv_bfloat16>());
-        else go(sweep_sym_kernel<__nv_bfloat16, 256, 4>, 256, P->d_Tp16.as<__nv_bfloat16>());
+        if (kc == 5) go(sweep_sym_kernel<__nv_bfloat16, 128, 8>, 128, P->d_Tp16.as<__nv_bfloat16>());
+        else go(sweep_sym_kernel<__nv_bfloat16, 64, 8>, 64, P->d_Tp16.as<__nv_bfloat16>());
       }
       return;
     }
     if (kc == 3 || kc == 4) {
       auto launch_vec = [&](auto* kern, int nt, const auto* T, const auto* c, auto* state) {
         kern<<<P->nparts, nt, vec_smem, s>>>(
-            T, P->d_tdesc.as<TileDesc>(), P->d_twin.as<int32_t>(), P->d_g.as<double>(),
-            P->d_run.as<uint8_t>(), c, state, npt_, P->W, P->d_ctrl.as<SweepCtrl>(),
-            P->d_partials.as<double>(), hist, hist_len, P->nparts, ld_max);
+            T, P->d_tdesc.as<TileDesc>(), P->d_twin.as<int32_t>(),
+            kd_of<std::remove_pointer_t<decltype(state)>>(P), P->d_run.as<uint8_t>(), c, state, npt_,
+            P->d_ctrl.as<SweepCtrl>(), P->d_partials.as<double>(), hist, hist_len, P->nparts, ld_max);
       };
 #define VTM_VEC_LAUNCH(NT, KB)                                                                  \
   do {                                                                                          \
@@ -1118,7 +1366,14 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   // Autotuner: on the first solve of this precision, time every kernel that
   // fits on this plan's tiles (a few sweeps each, from a zero state that is
   // reset afterwards) and keep the fastest.
-  const bool symload = (choice == 5 || choice == 6) && sym_ok;
+  const bool symload = ((choice == 5 || choice == 6) && sym_ok) || (choice == 7 && symb_ok);
+  if (symb_ok) {
+    VTM_CUDA_TRY(cudaFuncSetAttribute(prec == VTM_PREC_FP32
+                                          ? (const void*)sweep_symb_kernel<float, 128>
+                                          : (const void*)sweep_symb_kernel<__nv_bfloat16, 128>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)symb_smem));
+  }
+
   int kern = (vecload || symload) ? choice : (staged ? 2 : 1);
   if (P->opts.sweep_kernel == 0) {
     if (P->tuned_kernel[prec] == 0) {
@@ -1127,9 +1382,9 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
       const bool can_vec128 = nv_max <= 128;
       float best = 1e30f;
       int best_k = 1;
-      for (int cand = 1; cand <= 6; ++cand) {
+      for (int cand = 1; cand <= 7; ++cand) {
         if ((cand == 2 && !can_st) || (cand == 3 && !can_vec) || (cand == 4 && !can_vec128) ||
-            (cand >= 5 && !sym_ok))
+            ((cand == 5 || cand == 6) && !sym_ok) || (cand == 7 && !symb_ok))
           continue;
         if (cand == 2)
           VTM_CUDA_TRY(cudaFuncSetAttribute(
@@ -1298,8 +1553,14 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
   }
   const double target = tol * bnorm;
   double rnorm = bnorm;
+  // default inner tolerance: FP32 splits the reduction evenly over two
+  // refinement steps (sqrt(tol / 2), within what FP32 sweeps attain); BF16
+  // sweeps gain about two digits per step
   double inner_tol = P->opts.inner_tol;
-  if (inner_tol <= 0) inner_tol = prec == VTM_PREC_FP32 ? 1e-5 : (prec == VTM_PREC_BF16 ? 1e-2 : 0.0);
+  if (inner_tol <= 0)
+    inner_tol = prec == VTM_PREC_FP32   ? std::min(1e-4, std::max(2e-6, std::sqrt(0.5 * tol)))
+                : prec == VTM_PREC_BF16 ? 1e-2
+                                        : 0.0;
   const int max_outer = (prec == VTM_PREC_FP64 || P->general) ? 4 : P->opts.max_outer;
   int sweeps_left = P->opts.max_sweeps;
   vtm_status result = VTM_ENOCONV;
@@ -1320,6 +1581,7 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
       launch_band_solve(P, v, 1, n, s);
     }
     int kc = 0, flag = 1;
+    bool recovered_f32 = false;
     if (P->general && P->n_in > 0) {
       // channel form (lagged couplings / block Jacobi), FP64 sweeps
       VTM_TRY(general_const(P, v));
@@ -1341,17 +1603,21 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
     } else if (!P->general && npt > 0) {
       if (prec == VTM_PREC_FP64)
         port_const_kernel<double, double><<<g2, 256, 0, s>>>(
-            P->d_port_pos.as<int32_t>(), P->d_beta.as<double>(), v, P->W, P->d_c64.as<double>(), npt);
+            P->d_port_pos.as<int32_t>(), P->d_bout.as<double>(), v, P->d_c64.as<double>(), npt);
       else if (x0_f32)
         port_const_kernel<float, float><<<g2, 256, 0, s>>>(P->d_port_pos.as<int32_t>(),
-                                                           P->d_beta.as<double>(), P->d_v32.as<float>(),
-                                                           P->W, P->d_c32.as<float>(), npt);
+                                                           P->d_bout.as<double>(), P->d_v32.as<float>(),
+                                                           P->d_c32.as<float>(), npt);
       else
         port_const_kernel<float, double><<<g2, 256, 0, s>>>(
-            P->d_port_pos.as<int32_t>(), P->d_beta.as<double>(), v, P->W, P->d_c32.as<float>(), npt);
+            P->d_port_pos.as<int32_t>(), P->d_bout.as<double>(), v, P->d_c32.as<float>(), npt);
       VTM_CUDA_TRY(cudaGetLastError());
       P->launch_count++;
-      double t_abs = prec == VTM_PREC_FP64 ? target : std::max(target, inner_tol * rnorm);
+      // a low-precision inner solve that can finish the job aims below the
+      // target (its recovery adds rounding); earlier ones stop at inner_tol
+      double t_abs = target;
+      if (prec != VTM_PREC_FP64)
+        t_abs = inner_tol * rnorm <= 4.0 * target ? 0.5 * target : std::max(target, inner_tol * rnorm);
       double* hist = (record_hist && outer == 0 && P->opts.history) ? P->d_hist.as<double>() : nullptr;
       const int hist_len = hist ? P->opts.history_len : 0;
       if (hist) VTM_CUDA_TRY(cudaMemsetAsync(hist, 0, hist_len * sizeof(double), s));
@@ -1367,24 +1633,40 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
       if (outer == 0 && flag == 1) info->first_sweep_converged = kc;
       info->sweeps += kc;
       sweeps_left -= kc;
-      // recovery of the sweep kc: x_P = K_P^-1 (rhs_P + B beta w_in)
-      gather_perm_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, v, n);
+      // recovery of the sweep kc: x_P = K_P^-1 (rhs_P + B beta w_in), in
+      // FP32 after a low-precision inner solve (the correction it yields
+      // needs ~1e-5 relative accuracy; the FP64 refinement does the rest)
       P->launch_count += 2;
       const int slot = kc & 1;
-      if (prec == VTM_PREC_FP64)
-        inject_kernel<double><<<g2, 256, 0, s>>>(P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(),
-                                                 P->d_beta.as<double>(),
-                                                 P->d_state64.as<double>() + (size_t)slot * npt * 2, v, npt);
-      else
-        inject_kernel<float><<<g2, 256, 0, s>>>(P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(),
-                                                P->d_beta.as<double>(),
-                                                P->d_state32.as<float>() + (size_t)slot * npt * 2, v, npt);
-      launch_band_solve(P, v, 1, n, s);
+      if (prec == VTM_PREC_FP64) {
+        gather_perm_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, v, n);
+        inject_kernel<double, double><<<g2, 256, 0, s>>>(
+            P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(), P->d_beta.as<double>(),
+            P->d_state64.as<double>() + (size_t)slot * npt * 2, v, npt);
+        launch_band_solve(P, v, 1, n, s);
+      } else if (x0_f32) {
+        gather_perm_f32_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, P->d_v32.as<float>(), n);
+        inject_kernel<float, float><<<g2, 256, 0, s>>>(
+            P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(), P->d_beta.as<double>(),
+            P->d_state32.as<float>() + (size_t)slot * npt * 2, P->d_v32.as<float>(), npt);
+        launch_band_solve32(P, P->d_v32.as<float>(), 1, n, s);
+      } else {
+        gather_perm_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, v, n);
+        inject_kernel<float, double><<<g2, 256, 0, s>>>(
+            P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(), P->d_beta.as<double>(),
+            P->d_state32.as<float>() + (size_t)slot * npt * 2, v, npt);
+        launch_band_solve(P, v, 1, n, s);
+      }
+      recovered_f32 = x0_f32;
     } else {
       info->sweeps += 1;  // one direct solve per sub-circuit
       if (outer == 0) info->first_sweep_converged = 1;
     }
-    scatter_perm_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), v, xacc, n, outer > 0 ? 1 : 0);
+    if (recovered_f32)
+      scatter_perm_kernel<float><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), P->d_v32.as<float>(), xacc, n,
+                                                    outer > 0 ? 1 : 0);
+    else
+      scatter_perm_kernel<double><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), v, xacc, n, outer > 0 ? 1 : 0);
     P->launch_count++;
     VTM_CUDA_TRY(cudaGetLastError());
     info->outer_steps = outer + 1;
@@ -1553,7 +1835,11 @@ extern "C" vtm_status vtm_adjoint(vtm_plan_t P, const double* g, double* lam, in
     vtm_plan_t T = nullptr;
     VTM_TRY(vtm_plan(n, rp.data(), ci.data(), va.data(), P->h_part.data(), P->nparts, P->Zc, &P->opts,
                      P->stream, &T));
-    vtm_status st = vtm_factor(T);
+    // the same lines (the tearing is symmetric in i, j) with the same admittances
+    vtm_status st = P->w_kind == VTM_W_ALPHA
+                        ? vtm_set_admittance(T, VTM_W_ALPHA, P->W, 0, nullptr)
+                        : vtm_set_admittance(T, VTM_W_LINE, 0.0, 0, P->port_W.data());
+    if (st == VTM_OK) st = vtm_factor(T);
     if (st != VTM_OK) {
       vtm_destroy(T);
       return st;

@@ -96,7 +96,18 @@ struct vtm_plan_s {
   int64_t nnz = 0;
   int32_t nparts = 0;
   double Zc = 1.0;
-  double W = 1.0;
+  double W = 1.0;  // admittance of every line while the choice is alpha I
+
+  // characteristic admittance of the virtual lines (Sec. VIII), see
+  // vtm_set_admittance; per port: W_s, the wave scaling d_s = sqrt(W_s/W_ref)
+  // (1 for a scalar W) under which T_P stays symmetric, and the coefficients
+  // the kernels use (beta d, 2 W beta / d, (W - 2g)/(W + 2g), (g/W, d))
+  int w_kind = 0;
+  double w_alpha = 0.0;
+  int w_radius = 2;
+  std::vector<double> w_user;
+  std::vector<double> port_W, port_d;
+  bool w_dirty = true;  // port_W to be recomputed from the current values
   vtm_opts opts{};
   cudaStream_t stream = nullptr;
   bool symmetric = true;
@@ -149,7 +160,8 @@ struct vtm_plan_s {
   vtm::DevBuf d_perm;                      // int32[n]
   vtm::DevBuf d_Lc, d_Uc;                  // band factors (doubles)
   vtm::DevBuf d_Lc32, d_Uc32, d_v32;       // FP32 factor copies and work vector (inner solves)
-  vtm::DevBuf d_port_loc, d_port_pos, d_twin, d_g, d_beta, d_run, d_tdesc;
+  vtm::DevBuf d_port_loc, d_port_pos, d_twin, d_beta, d_run, d_tdesc;  // d_beta: beta d
+  vtm::DevBuf d_bout, d_rho, d_kd, d_kd32;  // per port: 2 W beta / d, reflection, (g/W, d)
   vtm::DevBuf d_T64, d_T32, d_T16;         // reflection matrices (T^T blocks)
   vtm::DevBuf d_Tp32, d_Tp16;              // packed symmetric copies (symmetric plans)
   vtm::DevBuf d_c64, d_c32;                // constant term of the sweep
@@ -198,7 +210,7 @@ struct vtm_plan_s {
   int64_t n_in = 0, n_out = 0;
   vtm::DevBuf d_in_off, d_out_off, d_in_src, d_in_kind, d_in_twin, d_in_own_out, d_in_loc,
       d_res_perm, d_res_run, d_out_loc, d_in_coef, d_in_sigma, d_out_scale, d_out_diag, d_E_off,
-      d_E_ld, d_E, d_cg, d_gin, d_gout, d_in_tile;
+      d_E_ld, d_E, d_cg, d_gin, d_gout, d_in_tile, d_in_d;
 
   // batched right-hand sides (batch.cu)
   std::vector<int32_t> item_tile, item_m0;

@@ -58,6 +58,19 @@ class Plan:
     def set_values(self, data):
         C.vtm_set_values(self.handle, _dev(data, torch.float64, self.device))
 
+    def set_admittance(self, kind, alpha=1.0, radius=2, W=None, factor=True):
+        """Line admittances (Sec. VIII): "alpha" (alpha I), "diag" (2 g_e),
+        "wob" (alpha 2 g_e), "sca" (partial input admittance over `radius`
+        branches) or "line" (W per port, equal at both ends of a line)."""
+        if W is not None:
+            W = np.ascontiguousarray(np.asarray(W, dtype=np.float64))
+        C.vtm_set_admittance(self.handle, kind, alpha, radius, W)
+        if factor:
+            self.factor()
+
+    def admittance(self) -> np.ndarray:
+        return C.vtm_get_admittance(self.handle)
+
     def set_options(self, history_len=0, **kw):
         opts = {**self._opts, **kw}
         history = np.zeros(history_len, np.float64) if history_len else None

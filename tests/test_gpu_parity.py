@@ -229,7 +229,9 @@ def test_every_sweep_kernel_matches_oracle(vtm, kernel):
 
 
 @pytest.mark.parametrize("precision,kernel,shape", [("fp32", 5, (90, 18)), ("fp32", 6, (192, 48)),
-                                                    ("bf16", 5, (192, 48)), ("bf16", 6, (90, 18))])
+                                                    ("fp32", 7, (90, 18)), ("fp32", 7, (192, 48)),
+                                                    ("bf16", 5, (192, 48)), ("bf16", 6, (90, 18)),
+                                                    ("bf16", 7, (192, 48))])
 def test_packed_symmetric_sweeps_follow_the_oracle(vtm, precision, kernel, shape):
     # T_P is symmetric (scalar W, symmetric A): the packed kernels read the
     # 16x16 blocks on and above the diagonal only.  18x18 tiles have 72, 54 or
@@ -260,7 +262,7 @@ def test_bad_options_are_rejected_and_the_plan_keeps_its_own(vtm):
     w = wl.power_grid(64, 64, 32, 32, Zc=1.0, seed=15)
     plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc)
     with pytest.raises(vtm.VTMError):
-        plan.set_options(sweep_kernel=7)
+        plan.set_options(sweep_kernel=8)
     with pytest.raises(vtm.VTMError):
         plan.set_options(sweep_kernel=-1)
     with pytest.raises(vtm.VTMError):
@@ -282,7 +284,7 @@ def test_graph_path_on_a_dedicated_stream(vtm):
         x1, info1 = plan.solve(b, tol=1e-10)
         x2, info2 = plan.solve(b, tol=1e-10)  # graph replay
     torch.cuda.synchronize()
-    assert plan.stats()["sweep_kernel"] in (1, 2, 3, 4, 5, 6)
+    assert plan.stats()["sweep_kernel"] in (1, 2, 3, 4, 5, 6, 7)
     assert torch.equal(x1, x2)
     rel = O.residual_norms(A, x1.cpu().numpy()[None], w.b)
     assert rel.max() <= 1e-10

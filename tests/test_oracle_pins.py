@@ -527,3 +527,75 @@ def test_multi_rhs_columns_are_independent():
         assert np.abs(one.x[0] - res.x[r]).max() <= 1e-13 * np.abs(res.x[r]).max()
     x_star = O.direct_solve(A, w.b)
     assert np.abs(res.x - x_star).max() <= 1e-9 * np.abs(x_star).max()
+
+
+# ---------------------------------------------------------------------------
+# Per-line characteristic admittance (Sec. VIII choices of W)
+# ---------------------------------------------------------------------------
+
+def test_diagonal_admittance_is_block_jacobi_sweep_by_sweep():
+    # W = diag(C) = 2 g on every line: a twin's port row is 4g u - 2g x = w_in,
+    # so the wave sent back is 2g x of its node and the node across the line
+    # sees the current g (x_j - x_i^(k-1)): exactly the lagged coupling of
+    # block Jacobi (Sec. X), iterate by iterate (the paper's VTM_Diag ~ BJ)
+    w = wl.grid2d(24, 24, 8, 6, seed=5)
+    A = w.csr()
+    tear = O.tear_midpoint(A, w.partition, w.nparts)
+    Wd = O.line_admittance_choice(tear, "diag")
+    assert np.allclose(Wd, 2 * tear.port_g)
+    res, its = O.vtm_midpoint(A, w.partition, w.nparts, w.b, W=Wd, tol=0, max_sweeps=25,
+                              keep_iterates=True)
+    x_bj, k_bj, _, h_bj = O.block_jacobi(A, w.partition, w.nparts, w.b, tol=0, max_sweeps=25)
+    assert k_bj == res.sweeps == 25
+    assert np.allclose(res.history, h_bj, rtol=1e-10, atol=0)
+    assert np.abs(its[-1] - x_bj).max() <= 1e-12 * np.abs(x_bj).max()
+
+
+def test_schur_approximation_limits():
+    # radius 0: D~ is the 1x1 block of the port's node, D_ll = a_ll + sum of
+    # the g of its torn branches -> S~ = 2g - 4g^2 / D_ll (closed form);
+    # growing the neighbourhood can only lower S~ (principal submatrices of an
+    # M-matrix have smaller inverse diagonals) down to diag(S_P) of the dense
+    # input admittance C - E D^-1 F (reflection_ops), all positive
+    w = wl.grid2d(24, 24, 8, 6, seed=6)
+    A = w.csr()
+    tear = O.tear_midpoint(A, w.partition, w.nparts)
+    g = tear.port_g
+    low = tear.port_tile <= tear.port_tile[tear.twin]
+    s_at = {}
+    for s in range(len(g)):
+        s_at.setdefault(int(tear.port_node[s]), []).append(s)
+    Dll = np.array([A[tear.port_node[s], tear.port_node[s]] + g[s_at[int(tear.port_node[s])]].sum()
+                    for s in range(len(g))])
+    S0 = 2 * g - 4 * g ** 2 / Dll
+    W0 = O.line_admittance_choice(tear, "sca", radius=0)
+    assert np.allclose(W0[low], S0[low], rtol=1e-13)
+    assert np.allclose(W0, W0[tear.twin])
+    diagS = np.empty(len(g))
+    for P in range(w.nparts):
+        S, _ = O.reflection_ops(A, tear, P, 1.0)
+        diagS[tear.tile_ports[P]] = np.diag(S)
+    Wfull = O.line_admittance_choice(tear, "sca", radius=-1)
+    assert np.allclose(Wfull[low], diagS[low], rtol=1e-11)
+    prev = W0
+    for r in (1, 2, 4):
+        Wr = O.line_admittance_choice(tear, "sca", radius=r)
+        assert np.all(Wr <= prev * (1 + 1e-12))
+        assert np.all(Wr >= Wfull * (1 - 1e-12))
+        prev = Wr
+    assert np.all(Wfull > 0)
+
+
+@pytest.mark.parametrize("kind,alpha,radius", [("diag", 1.0, -1), ("wob", 0.3, -1), ("sca", 1.0, 2),
+                                               ("sca", 1.0, -1), ("alpha", 2.5, -1)])
+def test_per_line_admittance_keeps_the_fixed_point(kind, alpha, radius):
+    # Lemma 2 / the fixed-point argument holds for any W > 0 per line
+    w = wl.c1_small_grid()
+    A = w.csr()
+    tear = O.tear_midpoint(A, w.partition, w.nparts)
+    Wl = O.line_admittance_choice(tear, kind, alpha=alpha, radius=radius)
+    assert np.all(Wl > 0) and np.allclose(Wl, Wl[tear.twin])
+    res = O.vtm_midpoint(A, w.partition, w.nparts, w.b, W=Wl, tol=1e-12, max_sweeps=20000)
+    assert res.converged
+    x_star = O.direct_solve(A, w.b)
+    assert np.abs(res.x - x_star).max() <= 1e-8 * np.abs(x_star).max()
