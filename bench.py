@@ -229,12 +229,15 @@ def sweep_bytes(stats, prec, nrhs=1):
     """Algorithmic bytes of one sweep launch: the reflection matrices once,
     and per port and right-hand side the twin's (w_in, w_out), its own
     (w_in, w_out) of the previous sweep, c, the new (w_in, w_out); per port
-    g (8 B), twin index (4 B) and node-run byte (1 B)."""
+    the residual coefficients (g/W, d) (2 x 8 B in FP64, 2 x 4 B otherwise;
+    the batched sweep reads them in FP64), twin index (4 B) and node-run byte
+    (1 B)."""
     s_t = {0: 8, 1: 4, 2: 2}[prec]
     s_w = 8 if prec == 0 else 4
+    s_kd = 16 if (prec == 0 or nrhs > 1) else 8
     # the packed symmetric kernels need only the entries on and above the diagonal
     entries = stats["sum_tri"] if stats.get("sweep_kernel") in (5, 6, 7) and nrhs == 1 else stats["sum_p2"]
-    return entries * s_t + stats["nports"] * (7 * s_w * nrhs + 13)
+    return entries * s_t + stats["nports"] * (7 * s_w * nrhs + 5 + s_kd)
 
 
 def plan_rowptr(w, dev):

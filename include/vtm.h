@@ -78,8 +78,8 @@ typedef struct {
   int max_sweeps;    /* sweeps per vtm_solve call, all refinement steps together; default 200000 */
   int check_every;   /* sweeps launched between two host polls of the convergence flag; default 32 */
   double inner_tol;  /* relative tolerance of each inner solve in the refinement modes;
-                        0 -> sqrt(tol/2) within [2e-6, 1e-4] (FP32: two steps reach tol)
-                        / 1e-2 (BF16).  An inner solve that can finish the job aims at
+                        0 -> 1e-5 (FP32) / 1e-2 (BF16).  An inner solve that can finish
+                        the job (inner_tol x its right-hand side <= 4 tol ||b||) aims at
                         tol/2 instead.  An inner solve also ends when its residual has
                         not dropped by 10% within 64 sweeps (its rounding floor); the
                         FP64 refinement then continues. */
@@ -242,7 +242,21 @@ vtm_status vtm_get_ports(vtm_plan_t plan, int32_t* node, int32_t* remote, int32_
  * doubles); *p receives p_P.  Requires vtm_factor. */
 vtm_status vtm_get_reflection(vtm_plan_t plan, int32_t part, double* T, int64_t cap, int32_t* p);
 
-/* vtm_residual_norm -- rel[r] = ||b_r - A x_r||_2 / ||b_r||_2 for each of
+/* vtm_march -- backward-Euler transient of an RC network with the plan's
+ * matrix A = G + C/h: for k = 1..nsteps
+ *   A x_k = p_k + (C/h) x_{k-1},
+ * each step solved to tol like vtm_solve, starting from x_{k-1} (warm start:
+ * the refinement's first inner problem is A d = b_k - A x_{k-1}).
+ * cdiag[n]: C/h per node (the part of A's diagonal carried by the state).
+ * p: n x nsteps injections (column k-1 = step k).  x0[n]: initial state, or
+ * NULL for zero.  X: n x nsteps output (column k-1 = x_k).  Arrays host or
+ * device.  info: sweeps and outer_steps summed over the steps, relres the
+ * largest, t_solve_ms the whole march.  Errors as vtm_solve; a failing step
+ * ends the march (vtm_last_error_detail names it). */
+vtm_status vtm_march(vtm_plan_t plan, const double* cdiag, const double* p, const double* x0,
+                     double* X, int64_t nsteps, double tol, vtm_info* info);
+
+/* vtm_residual_norm -- rel[r] = ||b_r - A x_r||_2 / ||b_r||_2 for each of/* vtm_residual_norm -- rel[r] = ||b_r - A x_r||_2 / ||b_r||_2 for each of
  * nrhs columns, in FP64 on the plan's stream (A = the plan's current values).
  * x, b: n x nrhs column-major (host or device); rel: host array[nrhs]. */
 vtm_status vtm_residual_norm(vtm_plan_t plan, const double* x, const double* b, int64_t nrhs,

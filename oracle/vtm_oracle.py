@@ -26,6 +26,8 @@ Algorithm to Solve the Linear System of Circuit" (arXiv 0910.0663):
                          1/2, the four-node example of Sec. IX, Eq. 15-21) and
                          a full characteristic-admittance matrix ``W``.
 * ``direct_solve``       the reference answer ``x = A^-1 b`` (Eq. 1).
+* ``backward_euler_march``  a transient of x_k = A^-1 (p_k + C/h x_(k-1)) by
+                         direct solves (the time march of an RC network).
 * ``block_jacobi``       the block Jacobi comparison method (Sec. X).
 * ``stationary_*``       Jacobi / Gauss-Seidel / SOR / SSOR iteration matrices
                          (Sec. IX comparison).
@@ -392,6 +394,21 @@ def port_excitation(A: sp.csr_matrix, tear: Tearing, P: int, b: np.ndarray) -> n
     E = np.zeros((len(ports), len(nodes)))
     E[np.arange(len(ports)), ell] = -2 * g
     return -(E @ np.linalg.solve(D, np.atleast_2d(b)[:, nodes].T)).T
+
+
+def backward_euler_march(A: sp.csr_matrix, cdiag: np.ndarray, p: np.ndarray,
+                         x0: Optional[np.ndarray] = None) -> np.ndarray:
+    """Backward-Euler transient of an RC network: A = G + C/h, and for
+    k = 1..nsteps  A x_k = p_k + (C/h) x_{k-1}  (cdiag = C/h per node), each
+    step by a direct solve (Eq. 1).  ``p``: (nsteps, n); returns (nsteps, n)."""
+    A = A.tocsr()
+    p = np.atleast_2d(np.asarray(p, dtype=np.float64))
+    x = np.zeros(A.shape[0]) if x0 is None else np.asarray(x0, dtype=np.float64)
+    out = np.empty_like(p)
+    for k in range(p.shape[0]):
+        x = direct_solve(A, (p[k] + cdiag * x)[None])[0]
+        out[k] = x
+    return out
 
 
 # ---------------------------------------------------------------------------

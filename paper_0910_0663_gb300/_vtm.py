@@ -82,6 +82,7 @@ def _load():
         "vtm_factor": (ctypes.c_int, [P]),
         "vtm_solve": (ctypes.c_int, [P, P, P, i64, dbl, ctypes.POINTER(vtm_info)]),
         "vtm_adjoint": (ctypes.c_int, [P, P, P, i64, dbl, ctypes.POINTER(vtm_info)]),
+        "vtm_march": (ctypes.c_int, [P, P, P, P, P, i64, dbl, ctypes.POINTER(vtm_info)]),
         "vtm_plan_get_stats": (ctypes.c_int, [P, ctypes.POINTER(vtm_plan_stats)]),
         "vtm_get_ports": (ctypes.c_int, [P, P, P, P, P]),
         "vtm_get_reflection": (ctypes.c_int, [P, i32, P, i64, ctypes.POINTER(i32)]),
@@ -104,7 +105,7 @@ def _load():
 
 _lib = _load()
 EXPORTED = ("vtm_plan", "vtm_set_values", "vtm_set_opts", "vtm_set_admittance",
-            "vtm_get_admittance", "vtm_factor", "vtm_solve",
+            "vtm_get_admittance", "vtm_factor", "vtm_solve", "vtm_march",
             "vtm_adjoint", "vtm_plan_get_stats", "vtm_get_ports", "vtm_get_reflection",
             "vtm_residual_norm", "vtm_residual_norm_noalloc", "vtm_netmap_create",
             "vtm_netmap_values", "vtm_netmap_gradient", "vtm_netmap_destroy", "vtm_destroy",
@@ -198,6 +199,15 @@ def vtm_adjoint(plan, g, lam, nrhs, tol, check=True):
     st = _lib.vtm_adjoint(plan, _ptr(g), _ptr(lam), int(nrhs), float(tol), ctypes.byref(info))
     if check:
         _check(st, "vtm_adjoint")
+    return st, info
+
+
+def vtm_march(plan, cdiag, p, x0, X, nsteps, tol, check=True):
+    info = vtm_info()
+    st = _lib.vtm_march(plan, _ptr(cdiag), _ptr(p), _ptr(x0), _ptr(X), int(nsteps), float(tol),
+                        ctypes.byref(info))
+    if check:
+        _check(st, "vtm_march")
     return st, info
 
 

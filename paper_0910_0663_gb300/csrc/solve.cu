@@ -1524,8 +1524,10 @@ vtm_status residual_pair(vtm_plan_s* P, const double* x, const double* b, double
 }
 
 // Solve one column: d_b (global order) -> d_x (global order).
+// One right-hand side.  d_x0 (device, may be NULL): warm start -- the
+// refinement starts from x = d_x0 (its first inner problem is A d = b - A x0).
 static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, double tol,
-                            vtm_info* info, bool record_hist) {
+                            vtm_info* info, bool record_hist, const double* d_x0 = nullptr) {
   cudaStream_t s = P->stream;
   const int64_t n = P->n;
   const int64_t npt = (int64_t)P->port_node.size();
@@ -1539,8 +1541,12 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
     VTM_TRY(dev_alloc(P->d_state32, 4 * std::max<int64_t>(npt, 1) * sizeof(float)));
   }
   double rr0, bb;
-  // ||b||^2 (x = 0 gives r = b)
-  VTM_CUDA_TRY(cudaMemsetAsync(xacc, 0, n * sizeof(double), s));
+  // ||b||^2 and r = b - A x (x = 0 gives r = b)
+  const bool warm = d_x0 != nullptr;
+  if (warm)
+    VTM_CUDA_TRY(cudaMemcpyAsync(xacc, d_x0, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  else
+    VTM_CUDA_TRY(cudaMemsetAsync(xacc, 0, n * sizeof(double), s));
   VTM_TRY(norms(P, xacc, d_b, r, &rr0, &bb));
   const double bnorm = std::sqrt(bb);
   info->sweeps = 0;
@@ -1552,21 +1558,24 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
     return VTM_OK;
   }
   const double target = tol * bnorm;
-  double rnorm = bnorm;
-  // default inner tolerance: FP32 splits the reduction evenly over two
-  // refinement steps (sqrt(tol / 2), within what FP32 sweeps attain); BF16
-  // sweeps gain about two digits per step
+  double rnorm = warm ? std::sqrt(rr0) : bnorm;
+  if (warm && rnorm <= target) {  // the start already meets the tolerance
+    info->relres = rnorm / bnorm;
+    VTM_CUDA_TRY(cudaMemcpyAsync(d_x, xacc, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    VTM_CUDA_TRY(cudaStreamSynchronize(s));
+    return VTM_OK;
+  }
+  // Default inner tolerance: FP32 sweeps gain five digits per refinement step
+  // (two steps reach 1e-10), BF16 sweeps about two.
   double inner_tol = P->opts.inner_tol;
-  if (inner_tol <= 0)
-    inner_tol = prec == VTM_PREC_FP32   ? std::min(1e-4, std::max(2e-6, std::sqrt(0.5 * tol)))
-                : prec == VTM_PREC_BF16 ? 1e-2
-                                        : 0.0;
+  if (inner_tol <= 0) inner_tol = prec == VTM_PREC_FP32 ? 1e-5 : (prec == VTM_PREC_BF16 ? 1e-2 : 0.0);
   const int max_outer = (prec == VTM_PREC_FP64 || P->general) ? 4 : P->opts.max_outer;
   int sweeps_left = P->opts.max_sweeps;
   vtm_status result = VTM_ENOCONV;
   for (int outer = 0; outer < max_outer; ++outer) {
-    // inner problem A d = r (r = b at the first step)
-    const double* rhs = outer == 0 ? d_b : r;
+    // inner problem A d = r (r = b at the first step of a cold start)
+    const double* rhs = (outer == 0 && !warm) ? d_b : r;
+    const int accumulate = (outer > 0 || warm) ? 1 : 0;
     // x0 = K_P^-1 rhs_P: FP64, or FP32 for a low-precision inner solve (it
     // only feeds c, whose error the next refinement step removes)
     const bool x0_f32 = prec != VTM_PREC_FP64 && !P->general && npt > 0 && P->d_Lc32.p;
@@ -1581,7 +1590,6 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
       launch_band_solve(P, v, 1, n, s);
     }
     int kc = 0, flag = 1;
-    bool recovered_f32 = false;
     if (P->general && P->n_in > 0) {
       // channel form (lagged couplings / block Jacobi), FP64 sweeps
       VTM_TRY(general_const(P, v));
@@ -1614,7 +1622,8 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
       VTM_CUDA_TRY(cudaGetLastError());
       P->launch_count++;
       // a low-precision inner solve that can finish the job aims below the
-      // target (its recovery adds rounding); earlier ones stop at inner_tol
+      // target (the rounding of its waves and of c is on top); earlier ones
+      // stop at inner_tol
       double t_abs = target;
       if (prec != VTM_PREC_FP64)
         t_abs = inner_tol * rnorm <= 4.0 * target ? 0.5 * target : std::max(target, inner_tol * rnorm);
@@ -1634,39 +1643,25 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
       info->sweeps += kc;
       sweeps_left -= kc;
       // recovery of the sweep kc: x_P = K_P^-1 (rhs_P + B beta w_in), in
-      // FP32 after a low-precision inner solve (the correction it yields
-      // needs ~1e-5 relative accuracy; the FP64 refinement does the rest)
+      // FP64 (an FP32 recovery leaves ~1e-7 cond(K_P) relative error in the
+      // correction: on the power grid it cost a third refinement step)
       P->launch_count += 2;
       const int slot = kc & 1;
-      if (prec == VTM_PREC_FP64) {
-        gather_perm_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, v, n);
+      gather_perm_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, v, n);
+      if (prec == VTM_PREC_FP64)
         inject_kernel<double, double><<<g2, 256, 0, s>>>(
             P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(), P->d_beta.as<double>(),
             P->d_state64.as<double>() + (size_t)slot * npt * 2, v, npt);
-        launch_band_solve(P, v, 1, n, s);
-      } else if (x0_f32) {
-        gather_perm_f32_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, P->d_v32.as<float>(), n);
-        inject_kernel<float, float><<<g2, 256, 0, s>>>(
-            P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(), P->d_beta.as<double>(),
-            P->d_state32.as<float>() + (size_t)slot * npt * 2, P->d_v32.as<float>(), npt);
-        launch_band_solve32(P, P->d_v32.as<float>(), 1, n, s);
-      } else {
-        gather_perm_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, v, n);
+      else
         inject_kernel<float, double><<<g2, 256, 0, s>>>(
             P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(), P->d_beta.as<double>(),
             P->d_state32.as<float>() + (size_t)slot * npt * 2, v, npt);
-        launch_band_solve(P, v, 1, n, s);
-      }
-      recovered_f32 = x0_f32;
+      launch_band_solve(P, v, 1, n, s);
     } else {
       info->sweeps += 1;  // one direct solve per sub-circuit
       if (outer == 0) info->first_sweep_converged = 1;
     }
-    if (recovered_f32)
-      scatter_perm_kernel<float><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), P->d_v32.as<float>(), xacc, n,
-                                                    outer > 0 ? 1 : 0);
-    else
-      scatter_perm_kernel<double><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), v, xacc, n, outer > 0 ? 1 : 0);
+    scatter_perm_kernel<double><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), v, xacc, n, accumulate);
     P->launch_count++;
     VTM_CUDA_TRY(cudaGetLastError());
     info->outer_steps = outer + 1;
@@ -1810,6 +1805,65 @@ static vtm_status solve_entry(vtm_plan_s* P, const double* b, double* x, int64_t
 extern "C" vtm_status vtm_solve(vtm_plan_t P, const double* b, double* x, int64_t nrhs, double tol,
                                 vtm_info* info) {
   return solve_entry(P, b, x, nrhs, tol, info);
+}
+
+// b_k = p_k + cdiag .* x_{k-1}  (x_{k-1} = NULL: zero initial state)
+__global__ void march_rhs_kernel(const double* __restrict__ p, const double* __restrict__ cdiag,
+                                 const double* __restrict__ xprev, double* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = xprev ? p[i] + cdiag[i] * xprev[i] : p[i];
+}
+
+extern "C" vtm_status vtm_march(vtm_plan_t P, const double* cdiag, const double* p, const double* x0,
+                                double* X, int64_t nsteps, double tol, vtm_info* info) {
+  if (!P || !cdiag || !p || !X || nsteps <= 0 || !(tol > 0)) return VTM_EINVAL;
+  if (!P->factored) return VTM_ENOTFACTORED;
+  cudaSetDevice(P->device);
+  vtm_info local{};
+  if (!info) info = &local;
+  *info = vtm_info{};
+  const int64_t n = P->n;
+  Staged Sp, Sc, S0;
+  VTM_TRY(stage(P, p, X, n * nsteps, Sp));
+  VTM_TRY(stage(P, cdiag, nullptr, n, Sc));
+  if (x0) VTM_TRY(stage(P, x0, nullptr, n, S0));
+  DevBuf bk;
+  VTM_TRY(dev_alloc(bk, (size_t)n * sizeof(double)));
+  P->launch_count = 0;
+  P->sweep_launch_count = 0;
+  P->sweep_ms = 0.0;
+  VTM_CUDA_TRY(cudaEventRecord(P->ev0, P->stream));
+  vtm_status st = VTM_OK;
+  for (int64_t k = 0; k < nsteps; ++k) {
+    const double* xprev = k == 0 ? (x0 ? S0.in_dev : nullptr) : Sp.out_dev + (k - 1) * n;
+    march_rhs_kernel<<<grid_for(n), 256, 0, P->stream>>>(Sp.in_dev + k * n, Sc.in_dev, xprev,
+                                                          bk.as<double>(), n);
+    P->launch_count++;
+    vtm_info one{};
+    // each step starts from the previous state (warm start)
+    st = solve_one(P, bk.as<double>(), Sp.out_dev + k * n, tol, &one, k == 0, xprev);
+    info->sweeps += one.sweeps;
+    info->outer_steps += one.outer_steps;
+    info->relres = std::max(info->relres, one.relres);
+    if (k == 0) info->first_sweep_converged = one.first_sweep_converged;
+    if (st != VTM_OK) {
+      set_detail("vtm_march: step " + std::to_string(k) + ": " + vtm_strerror(st));
+      break;
+    }
+  }
+  VTM_CUDA_TRY(cudaEventRecord(P->ev1, P->stream));
+  if (Sp.out_host)
+    VTM_CUDA_TRY(cudaMemcpyAsync(X, Sp.out_dev, n * nsteps * sizeof(double), cudaMemcpyDeviceToHost,
+                                 P->stream));
+  VTM_CUDA_TRY(cudaStreamSynchronize(P->stream));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, P->ev0, P->ev1);
+  info->t_solve_ms = ms;
+  info->kernel_launches = P->launch_count;
+  info->sweep_launches = P->sweep_launch_count;
+  info->t_sweeps_ms = P->sweep_ms;
+  return st;
 }
 
 extern "C" vtm_status vtm_adjoint(vtm_plan_t P, const double* g, double* lam, int64_t nrhs,

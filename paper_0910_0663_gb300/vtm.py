@@ -114,6 +114,18 @@ class Plan:
         x, info, _ = self._run(C.vtm_adjoint, g, tol, check)
         return x, info
 
+    def march(self, cdiag, p, x0=None, tol=1e-10, check=True):
+        """Backward-Euler transient: A x_k = p_k + cdiag * x_{k-1}, k = 1..nsteps,
+        each step warm-started from x_{k-1}.  p: (nsteps, n); returns X
+        (nsteps, n) and the summed info."""
+        dev = self.device
+        cd = _dev(cdiag, torch.float64, dev)
+        pp = _dev(p, torch.float64, dev).reshape(-1, self.n).contiguous()
+        x0d = None if x0 is None else _dev(x0, torch.float64, dev)
+        X = torch.empty_like(pp)
+        st, info = C.vtm_march(self.handle, cd, pp, x0d, X, pp.shape[0], tol, check=check)
+        return X, info.as_dict()
+
     def residual(self, x, b):
         x = x.reshape(-1, self.n).to(torch.float64).contiguous()
         b = b.reshape(-1, self.n).to(torch.float64).contiguous()

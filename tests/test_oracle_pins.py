@@ -599,3 +599,38 @@ def test_per_line_admittance_keeps_the_fixed_point(kind, alpha, radius):
     assert res.converged
     x_star = O.direct_solve(A, w.b)
     assert np.abs(res.x - x_star).max() <= 1e-8 * np.abs(x_star).max()
+
+
+# ---------------------------------------------------------------------------
+# Backward-Euler march (the transient an RC workload's G + C/h comes from)
+# ---------------------------------------------------------------------------
+
+def test_march_single_rc_node_closed_form():
+    # one node, conductance g to ground, capacitance term c = C/h, injection I:
+    # x_k = (I + c x_(k-1)) / (g + c)  =>  x_k = I/g + (x0 - I/g) (c/(g+c))^k
+    g, c, I, x0 = 0.7, 3.0, 2.0, -1.5
+    A = sp.csr_matrix(np.array([[g + c]]))
+    X = O.backward_euler_march(A, np.array([c]), np.full((12, 1), I), np.array([x0]))
+    k = np.arange(1, 13)
+    ref = I / g + (x0 - I / g) * (c / (g + c)) ** k
+    assert np.allclose(X[:, 0], ref, rtol=1e-13, atol=0)
+
+
+def test_march_settles_to_the_dc_solution_and_is_linear():
+    # constant injections: x_k -> G^-1 p (G = A - diag(c)); the march is linear
+    # in (p, x0)
+    w = wl.grid2d(6, 6, 3, 3, seed=41)
+    G = w.csr()
+    G = G + sp.diags(np.full(w.n, 0.5))          # a stronger ground: fast settling
+    c = np.random.default_rng(1).uniform(0.1, 0.3, w.n)
+    A = (G + sp.diags(c)).tocsr()
+    p = np.tile(w.b[0], (400, 1))
+    X = O.backward_euler_march(A, c, p)
+    x_dc = np.linalg.solve(G.toarray(), w.b[0])
+    assert np.abs(X[-1] - x_dc).max() <= 1e-12 * np.abs(x_dc).max()
+    rng = np.random.default_rng(2)
+    p1, p2 = rng.uniform(-1, 1, (5, w.n)), rng.uniform(-1, 1, (5, w.n))
+    a1, a2 = rng.uniform(-1, 1, w.n), rng.uniform(-1, 1, w.n)
+    lhs = O.backward_euler_march(A, c, p1 + p2, a1 + a2)
+    rhs = O.backward_euler_march(A, c, p1, a1) + O.backward_euler_march(A, c, p2, a2)
+    assert np.allclose(lhs, rhs, rtol=1e-12, atol=1e-13)
