@@ -55,10 +55,10 @@ def parse():
                          "wob = alpha 2g, sca = partial input admittance over --radius branches")
     ap.add_argument("--alpha", type=float, default=0.5, help="the weight of --admittance wob")
     ap.add_argument("--radius", type=int, default=1, help="the neighbourhood of --admittance sca")
-    ap.add_argument("--sweep-kernel", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6, 7],
+    ap.add_argument("--sweep-kernel", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6, 7, 8],
                     help="0: autotuned, 1: direct-load, 2: bulk-copy staged, 3/4: vector-load (256/128 "
                          "threads), 5/6: packed symmetric (128/64 threads), 7: packed symmetric, tile by "
-                         "one bulk copy")
+                         "one bulk copy, 8: packed symmetric dataflow sweeps (one launch per inner solve)")
     return ap.parse_args()
 
 
@@ -236,7 +236,7 @@ def sweep_bytes(stats, prec, nrhs=1):
     s_w = 8 if prec == 0 else 4
     s_kd = 16 if (prec == 0 or nrhs > 1) else 8
     # the packed symmetric kernels need only the entries on and above the diagonal
-    entries = stats["sum_tri"] if stats.get("sweep_kernel") in (5, 6, 7) and nrhs == 1 else stats["sum_p2"]
+    entries = stats["sum_tri"] if stats.get("sweep_kernel") in (5, 6, 7, 8) and nrhs == 1 else stats["sum_p2"]
     return entries * s_t + stats["nports"] * (7 * s_w * nrhs + 5 + s_kd)
 
 

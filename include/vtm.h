@@ -103,8 +103,11 @@ typedef struct {
                         most 256 ports keep only the 16x16 blocks of T_P on and above
                         the diagonal (T_P is symmetric for scalar W, Sec. VIII), about
                         half the bytes per sweep; 7: the same blocks, each tile brought
-                        into shared memory by one bulk copy; elsewhere 5-7 fall back
-                        to kernel 1 */
+                        into shared memory by one bulk copy; 8: the same blocks in one
+                        cooperative launch per inner solve, each tile starting sweep k
+                        once the tiles across its lines have finished sweep k - 1 (no
+                        kernel boundary per sweep; same iterates as 5); elsewhere 5-8
+                        fall back to kernel 1 */
   int graphs;        /* 0 (default): replay batches of check_every sweep launches from a
                         CUDA graph when the plan has its own stream; 1: plain launches */
   double* history;   /* optional host array: relative (interface) residual after each
@@ -197,7 +200,7 @@ vtm_status vtm_get_admittance(vtm_plan_t plan, double* W);
 
 /* vtm_set_opts -- replace the options of a plan (precision, limits, history).
  * VTM_EINVAL for a precision outside 0..2, a negative history_len, a history
- * length without an array, or a sweep_kernel outside 0..7; the plan keeps its
+ * length without an array, or a sweep_kernel outside 0..8; the plan keeps its
  * previous options then. */
 vtm_status vtm_set_opts(vtm_plan_t plan, const vtm_opts* opts);
 

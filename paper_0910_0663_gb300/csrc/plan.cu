@@ -753,7 +753,7 @@ std::vector<DevBuf*> vtm_plan_s::all_bufs() {
   return {&tabs.node_off, &tabs.bw, &tabs.band_off, &tabs.port_off, &tabs.T_off, &tabs.T_ld,
           &tabs.order, &d_rowptr, &d_colidx, &d_vals, &d_perm, &d_Lc, &d_Uc, &d_Lc32, &d_Uc32, &d_v32,
           &d_port_loc, &d_port_pos, &d_tdesc,
-          &d_twin, &d_beta, &d_bout, &d_rho, &d_kd, &d_kd32, &d_run, &d_T64, &d_T32, &d_T16, &d_Tp32, &d_Tp16, &d_c64, &d_c32, &d_state64,
+          &d_twin, &d_beta, &d_bout, &d_rho, &d_kd, &d_kd32, &d_run, &d_T64, &d_T32, &d_T16, &d_Tp32, &d_Tp16, &d_nbr_off, &d_nbr, &d_done, &d_flow, &d_part4, &d_fstate32, &d_c64, &d_c32, &d_state64,
           &d_state32, &d_v, &d_v2, &d_xacc, &d_r, &d_bcol, &d_partials, &d_ctrl, &d_hist,
           &d_err, &d_red, &d_in_off, &d_out_off, &d_in_src, &d_in_kind, &d_in_twin,
           &d_in_own_out, &d_in_loc, &d_res_perm, &d_res_run, &d_out_loc, &d_in_coef, &d_in_d,
@@ -857,8 +857,8 @@ extern "C" vtm_status vtm_set_opts(vtm_plan_t P, const vtm_opts* opts) {
     set_detail("vtm_set_opts: bad precision or history");
     return VTM_EINVAL;
   }
-  if (o.sweep_kernel < 0 || o.sweep_kernel > 7) {
-    set_detail("vtm_set_opts: sweep_kernel must be 0..7");
+  if (o.sweep_kernel < 0 || o.sweep_kernel > 8) {
+    set_detail("vtm_set_opts: sweep_kernel must be 0..8");
     return VTM_EINVAL;
   }
   bool prec_changed = o.precision != P->opts.precision;
@@ -983,6 +983,23 @@ extern "C" vtm_status vtm_plan(int64_t n, const int64_t* rowptr, const int32_t* 
                         P->T_off[t], P->Tp_off[t]};
   }
   if ((st = upload(P->d_tdesc, tdesc, s)) != VTM_OK) return fail(st);
+  {
+    // tiles across the lines of each tile (for the dataflow sweeps)
+    std::vector<int32_t> off(nparts + 1, 0), nb;
+    std::vector<int32_t> seen(nparts, -1);
+    for (int32_t t = 0; t < nparts; ++t) {
+      for (int32_t q = P->port_off[t]; q < P->port_off[t + 1]; ++q) {
+        const int32_t u = P->h_part[P->port_node[P->port_twin[q]]];
+        if (u != t && seen[u] != t) {
+          seen[u] = t;
+          nb.push_back(u);
+        }
+      }
+      off[t + 1] = (int32_t)nb.size();
+    }
+    if ((st = upload(P->d_nbr_off, off, s)) != VTM_OK) return fail(st);
+    if ((st = upload(P->d_nbr, nb, s)) != VTM_OK) return fail(st);
+  }
   if ((st = upload(P->d_port_loc, P->port_loc, s)) != VTM_OK) return fail(st);
   std::vector<int32_t> port_pos(P->port_node.size());
   for (size_t q = 0; q < port_pos.size(); ++q) port_pos[q] = P->iperm[P->port_node[q]];

@@ -1108,6 +1108,154 @@ __global__ void __launch_bounds__(NT) sweep_symb_kernel(
 }
 
 // ---------------------------------------------------------------------------
+// Dataflow sweeps: one cooperative launch runs every sweep of an inner solve.
+// Sweep k of tile P needs only the sweep-(k-1) waves of the tiles across its
+// lines (the one-sweep delay of Eq. 11), so instead of a kernel boundary per
+// sweep each tile waits for its neighbours' done counters.  The iterates are
+// those of the launch-per-sweep kernels (same arithmetic, packed blocks).
+//   * waves live in three slots (sweep k writes slot k mod 3): a tile may run
+//     one sweep ahead of a neighbour, and the slot of the converged iterate
+//     must survive the sweep after it;
+//   * the last tile to finish sweep k reduces the residual partials of sweep
+//     k (slot k mod 4, fixed order) and publishes the decision (gk = k); no
+//     tile starts sweep k + 2 before that, so a stop decided at sweep k never
+//     meets a tile that has overwritten what the host recovers from;
+//   * every wait is bounded; a wait that runs out sets flag 5 (VTM_ETIMEOUT)
+//     and any wait returns as soon as a flag is set.
+// All CTAs are co-resident (cooperative launch), so the waits always end.
+// ---------------------------------------------------------------------------
+
+constexpr uint32_t kFlowPolls = 1u << 22;  // a few seconds at most
+
+// Warp 0 waits (bounded) until the published decision has reached sweep
+// k - 2 and every tile across the lines of `tile` has finished sweep k - 1:
+// its lanes read the counters at once (lane 31 the decision, lanes 0..30 a
+// chunk of neighbours).  false if a flag is raised (or the wait ran out, and
+// then flag 5 is set).  Called by all 32 lanes of warp 0.
+__device__ __forceinline__ bool flow_wait_ready(const int* gk, const int* done,
+                                                const int32_t* __restrict__ nbr, int e0, int e1, int k,
+                                                SweepCtrl* ctrl) {
+  const int lane = threadIdx.x & 31;
+  for (int base = e0; base < e1 || base == e0; base += 31) {
+    const int e = base + lane;
+    const int* p = lane == 31 ? gk : (e < e1 ? done + nbr[e] : nullptr);
+    const int need = lane == 31 ? k - 2 : k - 1;
+    uint32_t i = 0;
+    for (;; ++i) {
+      const bool ok = !p || *((volatile const int*)p) >= need;
+      if (__all_sync(0xffffffffu, ok)) break;
+      if (i >= kFlowPolls) {
+        if (lane == 0) atomicCAS(&ctrl->flag, 0, 5);
+        return false;
+      }
+      if ((i & 15u) == 15u) {
+        if (*((volatile int*)&ctrl->flag)) return false;
+        __nanosleep(32);
+      }
+    }
+  }
+  return true;
+}
+
+template <class TT, int NT, int KB>
+__global__ void __launch_bounds__(NT, 768 / NT) sweep_flow_kernel(
+    const TT* __restrict__ Tp, const TileDesc* __restrict__ tdesc,
+    const int32_t* __restrict__ twin, const float2* __restrict__ kd,
+    const uint8_t* __restrict__ run, const float* __restrict__ c, float* __restrict__ state3,
+    int64_t nports, const int32_t* __restrict__ nbr_off, const int32_t* __restrict__ nbr,
+    int* __restrict__ done, unsigned* __restrict__ count, int* __restrict__ gk,
+    SweepCtrl* __restrict__ ctrl, double* __restrict__ part4, double* __restrict__ hist,
+    int hist_len, int nparts, int pp_max, int k0) {
+  using LD = SymLoad<TT>;
+  constexpr int NW = NT / 32;
+  constexpr int B = kSymB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_stop;
+  __shared__ bool s_last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float* w_in = reinterpret_cast<float*>(smem_raw);
+  float* rs = w_in + pp_max;
+  float* part = rs + pp_max;
+  for (int k = k0;; ++k) {
+    for (int slot = blockIdx.x; slot < nparts; slot += gridDim.x) {
+      const TileDesc dsc = tdesc[slot];
+      const int tile = dsc.tile, p0 = dsc.p0, p = dsc.p;
+      const int nb = (p + B - 1) / B;
+      const int nblk = nb * (nb + 1) / 2;
+      const TT* Tl = Tp + dsc.Tp_off;
+      // what does not depend on the waves goes out before the waits
+      typename LD::raw buf[KB];
+#pragma unroll
+      for (int b = 0; b < KB; ++b) {
+        const int kk = warp + b * NW;
+        if (kk < nblk) buf[b] = LD::load(Tl + (size_t)kk * B * B, lane);
+      }
+      SymPorts<NT> pt;
+      pt.load(twin, kd, run, c, p0, p);
+      if (warp == 0) {
+        bool ok = flow_wait_ready(gk, done, nbr, nbr_off[tile], nbr_off[tile + 1], k, ctrl);
+        __threadfence();  // every lane that saw a counter orders its later reads
+        if (tid == 0) s_stop = (ok && !*((volatile int*)&ctrl->flag)) ? 0 : 1;
+      }
+      __syncthreads();
+      if (s_stop) return;
+      const float* prev = state3 + (size_t)((k - 1) % 3) * nports * 2;
+      float* cur = state3 + (size_t)(k % 3) * nports * 2;
+      const float sq = sym_gather<NT>(pt, prev, w_in, rs, p0, p, nb, k);
+      const double tile_sq = (double)block_sum_value_f(sq);
+      int bi = 0, off = warp;
+      for (int base = 0; base < nblk; base += KB * NW) {
+#pragma unroll
+        for (int b = 0; b < KB; ++b) {
+          const int kk = warp + base + b * NW;
+          if (kk < nblk) {
+            while (off >= nb - bi) {
+              off -= nb - bi;
+              ++bi;
+            }
+            const typename LD::raw v = buf[b];
+            const int kn = kk + KB * NW;
+            if (kn < nblk) buf[b] = LD::load(Tl + (size_t)kn * B * B, lane);
+            sym_block(v, bi, bi + off, nb, lane, w_in, part);
+            off += NW;
+          }
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < SymPorts<NT>::PPT; ++j) {
+        const int s = tid + j * NT;
+        if (s < p) {
+          const int a = s / B, rr = s % B;
+          float acc = pt.cq[j];
+          for (int b = 0; b < nb; ++b) acc += part[(a * nb + b) * B + rr];
+          *reinterpret_cast<float2*>(cur + 2 * (size_t)(p0 + s)) = make_float2(w_in[s], acc);
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        part4[(size_t)(k & 3) * nparts + tile] = tile_sq;
+        __threadfence();
+        atomicExch(done + tile, k);
+        s_last = atomicAdd(count + (k & 3), 1u) == (unsigned)nparts - 1;
+      }
+      __syncthreads();
+      if (s_last) {
+        __threadfence();
+        const double tot = block_sum_fixed(part4 + (size_t)(k & 3) * nparts, nparts);
+        if (tid == 0) {
+          sweep_decide(ctrl, k, tot, hist, hist_len);
+          count[(k + 2) & 3] = 0u;
+          __threadfence();
+          atomicExch(gk, k);
+        }
+        __syncthreads();
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
 
@@ -1287,7 +1435,8 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   L2Window l2win(P, prec);
   // one sweep launch with kernel `kc` (1 direct, 2 staged, 3/4 vector loads with
   // 256/128 threads, 5/6 packed symmetric with 128/64 threads, 7 packed
-  // symmetric with the tile in shared memory by one bulk copy)
+  // symmetric with the tile in shared memory by one bulk copy; 8, the dataflow
+  // sweeps, is launched once per inner solve by launch_flow)
   auto launch_one = [&](int kc) {
     if (kc == 7) {
       auto go = [&](auto* kern, const auto* Tp) {
@@ -1366,7 +1515,56 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   // Autotuner: on the first solve of this precision, time every kernel that
   // fits on this plan's tiles (a few sweeps each, from a zero state that is
   // reset afterwards) and keep the fastest.
-  const bool symload = ((choice == 5 || choice == 6) && sym_ok) || (choice == 7 && symb_ok);
+  // dataflow sweeps: packed symmetric blocks, one cooperative launch per inner
+  // solve, all CTAs co-resident
+  int flow_grid = 0;
+  if (sym_ok) {
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, P->device);
+    const void* kfn = prec == VTM_PREC_FP32 ? (const void*)sweep_flow_kernel<float, 128, 4>
+                                            : (const void*)sweep_flow_kernel<__nv_bfloat16, 128, 8>;
+    int per_sm = 0;
+    if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 128, sym_smem) == cudaSuccess &&
+        per_sm > 0)
+      flow_grid = std::min(P->nparts, per_sm * sms);
+    cudaGetLastError();
+  }
+  const bool flow_ok = flow_grid > 0;
+  if (flow_ok) {
+    VTM_TRY(dev_alloc(P->d_done, (size_t)P->nparts * sizeof(int)));
+    VTM_TRY(dev_alloc(P->d_flow, 64));
+    VTM_TRY(dev_alloc(P->d_part4, 4 * (size_t)P->nparts * sizeof(double)));
+    VTM_TRY(dev_alloc(P->d_fstate32, 6 * (size_t)std::max<int64_t>(npt, 1) * sizeof(float)));
+  }
+  // one cooperative launch runs sweeps 1.. until a flag (k_max in ctrl)
+  auto launch_flow = [&]() -> cudaError_t {
+    cudaMemsetAsync(P->d_done.p, 0, (size_t)P->nparts * sizeof(int), s);
+    cudaMemsetAsync(P->d_flow.p, 0, 64, s);
+    const void* Tp = prec == VTM_PREC_FP32 ? P->d_Tp32.p : P->d_Tp16.p;
+    const TileDesc* td = P->d_tdesc.as<TileDesc>();
+    const int32_t* tw = P->d_twin.as<int32_t>();
+    const float2* kdp = P->d_kd32.as<float2>();
+    const uint8_t* rn = P->d_run.as<uint8_t>();
+    const float* cp = P->d_c32.as<float>();
+    float* st3 = P->d_fstate32.as<float>();
+    const int32_t* no = P->d_nbr_off.as<int32_t>();
+    const int32_t* nbp = P->d_nbr.as<int32_t>();
+    int* dn = P->d_done.as<int>();
+    unsigned* cnt = reinterpret_cast<unsigned*>(P->d_flow.p);
+    int* gkp = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(P->d_flow.p) + 32);
+    SweepCtrl* ct = P->d_ctrl.as<SweepCtrl>();
+    double* p4 = P->d_part4.as<double>();
+    int np = P->nparts, ppm = pp_max, hl = hist_len, k0 = 1;
+    int64_t npv = npt_;
+    double* hp = hist;
+    void* args[] = {&Tp, &td, &tw, &kdp, &rn, &cp, &st3, &npv, &no, &nbp, &dn, &cnt, &gkp, &ct, &p4, &hp,
+                    &hl, &np, &ppm, &k0};
+    const void* kfn = prec == VTM_PREC_FP32 ? (const void*)sweep_flow_kernel<float, 128, 4>
+                                            : (const void*)sweep_flow_kernel<__nv_bfloat16, 128, 8>;
+    return cudaLaunchCooperativeKernel(kfn, flow_grid, 128, args, sym_smem, s);
+  };
+  const bool symload = ((choice == 5 || choice == 6) && sym_ok) || (choice == 7 && symb_ok) ||
+                       (choice == 8 && flow_ok);
   if (symb_ok) {
     VTM_CUDA_TRY(cudaFuncSetAttribute(prec == VTM_PREC_FP32
                                           ? (const void*)sweep_symb_kernel<float, 128>
@@ -1382,10 +1580,35 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
       const bool can_vec128 = nv_max <= 128;
       float best = 1e30f;
       int best_k = 1;
-      for (int cand = 1; cand <= 7; ++cand) {
+      for (int cand = 1; cand <= 8; ++cand) {
         if ((cand == 2 && !can_st) || (cand == 3 && !can_vec) || (cand == 4 && !can_vec128) ||
-            ((cand == 5 || cand == 6) && !sym_ok) || (cand == 7 && !symb_ok))
+            ((cand == 5 || cand == 6) && !sym_ok) || (cand == 7 && !symb_ok) || (cand == 8 && !flow_ok))
           continue;
+        if (cand == 8) {  // one launch of 8 sweeps, per-sweep time compared with the others' 6
+          SweepCtrl t = h;
+          t.k_max = 8;
+          t.tol2 = -1.0;
+          t.stall = 0;
+          *P->h_ctrl = t;
+          VTM_CUDA_TRY(cudaMemcpyAsync(P->d_ctrl.p, P->h_ctrl, sizeof(SweepCtrl), cudaMemcpyHostToDevice, s));
+          VTM_CUDA_TRY(cudaEventRecord(P->evs0, s));
+          VTM_CUDA_TRY(launch_flow());
+          VTM_CUDA_TRY(cudaEventRecord(P->evs1, s));
+          VTM_CUDA_TRY(cudaEventSynchronize(P->evs1));
+          float ms = 0.f;
+          VTM_CUDA_TRY(cudaEventElapsedTime(&ms, P->evs0, P->evs1));
+          P->launch_count += 1;
+          VTM_CUDA_TRY(cudaMemcpy(P->h_ctrl, P->d_ctrl.p, sizeof(SweepCtrl), cudaMemcpyDeviceToHost));
+          if (P->h_ctrl->flag == 5) {
+            set_detail("vtm_solve: a bounded wait of the dataflow sweeps ran out");
+            return VTM_ETIMEOUT;
+          }
+          if (ms * 6.0f / 8.0f < best) {
+            best = ms * 6.0f / 8.0f;
+            best_k = cand;
+          }
+          continue;
+        }
         if (cand == 2)
           VTM_CUDA_TRY(cudaFuncSetAttribute(
               prec == VTM_PREC_FP64 ? (const void*)sweep_staged_kernel<double, double, 2, 4>
@@ -1437,6 +1660,27 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, st_threads, st_smem);
     st_grid = std::max(1, std::min(P->nparts, std::max(per_sm, 1) * sms));
+  }
+  if (kern == 8) {
+    VTM_CUDA_TRY(cudaEventRecord(P->evs0, s));
+    VTM_CUDA_TRY(launch_flow());
+    VTM_CUDA_TRY(cudaEventRecord(P->evs1, s));
+    VTM_CUDA_TRY(cudaMemcpyAsync(P->h_ctrl, P->d_ctrl.p, sizeof(SweepCtrl), cudaMemcpyDeviceToHost, s));
+    VTM_CUDA_TRY(cudaStreamSynchronize(s));
+    float bms = 0.f;
+    VTM_CUDA_TRY(cudaEventElapsedTime(&bms, P->evs0, P->evs1));
+    P->sweep_ms += bms;
+    const SweepCtrl& r = *P->h_ctrl;
+    P->sweep_launch_count += std::max(r.k - 1, 1);  // sweeps run by the one launch
+    P->launch_count += 1;
+    if (r.flag == 5) {
+      set_detail("vtm_solve: a bounded wait of the dataflow sweeps ran out");
+      return VTM_ETIMEOUT;
+    }
+    *flag_out = r.flag;
+    *sweep_out = (r.flag == 1 || r.flag == 4) ? r.conv_sweep : std::min(r.k - 1, budget);
+    P->wave_slot = P->d_fstate32.as<float>() + (size_t)(*sweep_out % 3) * npt * 2;
+    return VTM_OK;
   }
   // Batches of check_every launches, captured once into a CUDA graph when the
   // plan has its own stream (launches past convergence or the sweep limit
@@ -1494,6 +1738,9 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   *flag_out = r.flag;
   if (r.flag == 1 || r.flag == 4) *sweep_out = r.conv_sweep;
   else *sweep_out = std::min(r.k - 1, budget);
+  P->wave_slot = prec == VTM_PREC_FP64
+                     ? (const void*)(P->d_state64.as<double>() + (size_t)(*sweep_out & 1) * npt * 2)
+                     : (const void*)(P->d_state32.as<float>() + (size_t)(*sweep_out & 1) * npt * 2);
   return VTM_OK;
 }
 
@@ -1590,6 +1837,7 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
       launch_band_solve(P, v, 1, n, s);
     }
     int kc = 0, flag = 1;
+    bool recovered_f32 = false;
     if (P->general && P->n_in > 0) {
       // channel form (lagged couplings / block Jacobi), FP64 sweeps
       VTM_TRY(general_const(P, v));
@@ -1642,26 +1890,39 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
       if (outer == 0 && flag == 1) info->first_sweep_converged = kc;
       info->sweeps += kc;
       sweeps_left -= kc;
-      // recovery of the sweep kc: x_P = K_P^-1 (rhs_P + B beta w_in), in
-      // FP64 (an FP32 recovery leaves ~1e-7 cond(K_P) relative error in the
-      // correction: on the power grid it cost a third refinement step)
+      // recovery of the sweep kc: x_P = K_P^-1 (rhs_P + B beta w_in).  An
+      // FP32 recovery leaves ~1e-7 cond(K_P) relative error in the correction
+      // (6e-5 on the power grid): below what a BF16 step gains (1e-2), so BF16
+      // steps recover in FP32; FP32 steps gain five digits and recover in FP64.
       P->launch_count += 2;
-      const int slot = kc & 1;
-      gather_perm_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, v, n);
-      if (prec == VTM_PREC_FP64)
-        inject_kernel<double, double><<<g2, 256, 0, s>>>(
-            P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(), P->d_beta.as<double>(),
-            P->d_state64.as<double>() + (size_t)slot * npt * 2, v, npt);
-      else
-        inject_kernel<float, double><<<g2, 256, 0, s>>>(
-            P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(), P->d_beta.as<double>(),
-            P->d_state32.as<float>() + (size_t)slot * npt * 2, v, npt);
-      launch_band_solve(P, v, 1, n, s);
+      const float* slot32 = static_cast<const float*>(P->wave_slot);
+      recovered_f32 = prec == VTM_PREC_BF16 && x0_f32;
+      if (recovered_f32) {
+        gather_perm_f32_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, P->d_v32.as<float>(), n);
+        inject_kernel<float, float><<<g2, 256, 0, s>>>(P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(),
+                                                      P->d_beta.as<double>(), slot32,
+                                                      P->d_v32.as<float>(), npt);
+        launch_band_solve32(P, P->d_v32.as<float>(), 1, n, s);
+      } else {
+        gather_perm_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, v, n);
+        if (prec == VTM_PREC_FP64)
+          inject_kernel<double, double><<<g2, 256, 0, s>>>(
+              P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(), P->d_beta.as<double>(),
+              static_cast<const double*>(P->wave_slot), v, npt);
+        else
+          inject_kernel<float, double><<<g2, 256, 0, s>>>(P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(),
+                                                         P->d_beta.as<double>(), slot32, v, npt);
+        launch_band_solve(P, v, 1, n, s);
+      }
     } else {
       info->sweeps += 1;  // one direct solve per sub-circuit
       if (outer == 0) info->first_sweep_converged = 1;
     }
-    scatter_perm_kernel<double><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), v, xacc, n, accumulate);
+    if (recovered_f32)
+      scatter_perm_kernel<float><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), P->d_v32.as<float>(), xacc, n,
+                                                    accumulate);
+    else
+      scatter_perm_kernel<double><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), v, xacc, n, accumulate);
     P->launch_count++;
     VTM_CUDA_TRY(cudaGetLastError());
     info->outer_steps = outer + 1;

@@ -164,6 +164,11 @@ struct vtm_plan_s {
   vtm::DevBuf d_bout, d_rho, d_kd, d_kd32;  // per port: 2 W beta / d, reflection, (g/W, d)
   vtm::DevBuf d_T64, d_T32, d_T16;         // reflection matrices (T^T blocks)
   vtm::DevBuf d_Tp32, d_Tp16;              // packed symmetric copies (symmetric plans)
+  // dataflow sweeps: tiles across the lines of each tile (CSR), per-tile done
+  // counters, per-sweep tile counts and the published decision, residual
+  // partials of four sweeps, waves in three slots
+  vtm::DevBuf d_nbr_off, d_nbr, d_done, d_flow, d_part4, d_fstate32;
+  const void* wave_slot = nullptr;  // (w_in, w_out) pairs of the sweep the last inner solve ended on
   vtm::DevBuf d_c64, d_c32;                // constant term of the sweep
   vtm::DevBuf d_state64, d_state32;        // [2][nports] (w_in, w_out) pairs
   vtm::DevBuf d_v, d_v2;                   // permuted work vectors [n]

@@ -231,7 +231,8 @@ def test_every_sweep_kernel_matches_oracle(vtm, kernel):
 @pytest.mark.parametrize("precision,kernel,shape", [("fp32", 5, (90, 18)), ("fp32", 6, (192, 48)),
                                                     ("fp32", 7, (90, 18)), ("fp32", 7, (192, 48)),
                                                     ("bf16", 5, (192, 48)), ("bf16", 6, (90, 18)),
-                                                    ("bf16", 7, (192, 48))])
+                                                    ("bf16", 7, (192, 48)), ("fp32", 8, (90, 18)),
+                                                    ("fp32", 8, (192, 48)), ("bf16", 8, (90, 18))])
 def test_packed_symmetric_sweeps_follow_the_oracle(vtm, precision, kernel, shape):
     # T_P is symmetric (scalar W, symmetric A): the packed kernels read the
     # 16x16 blocks on and above the diagonal only.  18x18 tiles have 72, 54 or
@@ -258,11 +259,30 @@ def test_packed_symmetric_sweeps_follow_the_oracle(vtm, precision, kernel, shape
     assert np.allclose(h[:k], href[:k], rtol=rtol, atol=0)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_dataflow_sweeps_repeat_the_launch_per_sweep_kernel_bitwise(vtm, precision):
+    # one cooperative launch with per-tile neighbour waits computes the same
+    # iterates as one launch per sweep (same block arithmetic, same fixed-order
+    # reductions, same decisions)
+    w = wl.power_grid(256, 256, 32, 32, Zc=1.0, seed=17)
+    out = []
+    for kernel in (5, 8):
+        plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc,
+                        precision=precision, sweep_kernel=kernel)
+        plan.set_options(history_len=64)
+        x, info = plan.solve(torch.from_numpy(w.b[0]).cuda(), tol=1e-10)
+        assert plan.stats()["sweep_kernel"] == kernel
+        out.append((x, info["sweeps"], info["outer_steps"], plan.history))
+    assert out[0][1:3] == out[1][1:3]
+    assert np.array_equal(out[0][3], out[1][3])
+    assert torch.equal(out[0][0], out[1][0])
+
+
 def test_bad_options_are_rejected_and_the_plan_keeps_its_own(vtm):
     w = wl.power_grid(64, 64, 32, 32, Zc=1.0, seed=15)
     plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc)
     with pytest.raises(vtm.VTMError):
-        plan.set_options(sweep_kernel=8)
+        plan.set_options(sweep_kernel=9)
     with pytest.raises(vtm.VTMError):
         plan.set_options(sweep_kernel=-1)
     with pytest.raises(vtm.VTMError):
@@ -284,7 +304,7 @@ def test_graph_path_on_a_dedicated_stream(vtm):
         x1, info1 = plan.solve(b, tol=1e-10)
         x2, info2 = plan.solve(b, tol=1e-10)  # graph replay
     torch.cuda.synchronize()
-    assert plan.stats()["sweep_kernel"] in (1, 2, 3, 4, 5, 6, 7)
+    assert plan.stats()["sweep_kernel"] in (1, 2, 3, 4, 5, 6, 7, 8)
     assert torch.equal(x1, x2)
     rel = O.residual_norms(A, x1.cpu().numpy()[None], w.b)
     assert rel.max() <= 1e-10
