@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--admittance", default="alpha", choices=["alpha", "diag", "wob", "sca"],
                     help="line admittance (Sec. VIII): alpha = 1/Zc on every line (default), diag = 2g, "
                          "wob = alpha 2g, sca = partial input admittance over --radius branches")
+    ap.add_argument("--method", default="vtm", choices=["vtm", "async"],
+                    help="vtm: synchronous sweeps; async: asynchronous VTM (tiles read the latest "
+                         "waves of their neighbours, FP32/BF16 symmetric plans)")
     ap.add_argument("--alpha", type=float, default=0.5, help="the weight of --admittance wob")
     ap.add_argument("--radius", type=int, default=1, help="the neighbourhood of --admittance sca")
     ap.add_argument("--sweep-kernel", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6, 7, 8],
@@ -63,13 +66,15 @@ def parse():
 
 
 def admittance_config(args):
+    extra = {"method": "asynchronous VTM (one cooperative launch, latest neighbour waves)"} \
+        if args.method == "async" else {}
     if args.admittance == "alpha":
-        return {}
+        return extra
     desc = {"diag": "W = diag(C) = 2g per line (Sec. VIII choice 2)",
             "wob": f"W = {args.alpha} C = {args.alpha} * 2g per line (Sec. VIII choice 4)",
             "sca": f"W = diagonal of the partial input admittance over {args.radius} branch(es), "
                    "lower-numbered end (Sec. VIII choice 5)"}[args.admittance]
-    return {"admittance": desc}
+    return dict(extra, admittance=desc)
 
 
 def workload_config(args):
@@ -299,6 +304,8 @@ def gpu_arm(args):
         precs = ["fp64", "bj_fp64"]
     elif args.precision == "auto":
         precs = ["fp64", "fp32", "bf16"] if args.workload != "grad" else ["fp64", "fp32"]
+        if args.method == "async":
+            precs = ["fp32", "bf16"]  # asynchronous sweeps run in FP32/BF16 only
     else:
         precs = [args.precision]
     results = {}
@@ -324,7 +331,7 @@ def run_mode(args, prec, w, dev, stream, b_dev, b_host, x_host, flush, world):
     import torch
     import torch.distributed as dist
     from paper_0910_0663_gb300 import vtm
-    method = "bj" if prec.startswith("bj_") else "vtm"
+    method = "bj" if prec.startswith("bj_") else args.method
     prec_name = prec.split("_")[-1]
     nrhs = 1 if b_dev.dim() == 1 else b_dev.shape[0]
     grad = args.workload == "grad"
@@ -334,7 +341,7 @@ def run_mode(args, prec, w, dev, stream, b_dev, b_host, x_host, flush, world):
             plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc,
                             precision=prec_name, device=dev, stream=stream, factor=False,
                             sweep_kernel=args.sweep_kernel, l2_persist=args.l2_persist, method=method)
-            if args.admittance != "alpha" and method == "vtm":
+            if args.admittance != "alpha" and method != "bj":
                 plan.set_admittance(args.admittance, alpha=args.alpha, radius=args.radius, factor=False)
             t1 = time.perf_counter()
             plan.factor()

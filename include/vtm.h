@@ -69,8 +69,14 @@ enum {
 /* Iteration run by a plan. */
 enum {
   VTM_METHOD_VTM = 0, /* virtual transmission lines on the torn branches (Sec. VI) */
-  VTM_METHOD_BJ = 1   /* block Jacobi over the same sub-circuits (the comparison method of
+  VTM_METHOD_BJ = 1,  /* block Jacobi over the same sub-circuits (the comparison method of
                          Sec. X): every cut entry is applied with one sweep of delay */
+  VTM_METHOD_ASYNC = 2 /* asynchronous VTM (Sec. XI: lines with different, varying delays):
+                         one cooperative launch in which every tile reads the waves its
+                         neighbours last wrote, without waiting for them (kept within two
+                         sweeps of each other).  Same fixed point, timing-dependent
+                         iterates.  Needs FP32/BF16 sweeps of a symmetric plan with at most
+                         256 ports per sub-circuit (VTM_EINVAL at vtm_solve otherwise) */
 };
 
 typedef struct {
@@ -84,7 +90,8 @@ typedef struct {
                         not dropped by 10% within 64 sweeps (its rounding floor); the
                         FP64 refinement then continues. */
   int max_outer;     /* refinement steps in the FP32/BF16 modes; default 40 */
-  int method;        /* VTM_METHOD_VTM (default) or VTM_METHOD_BJ; read by vtm_plan only */
+  int method;        /* VTM_METHOD_VTM (default), VTM_METHOD_BJ (chosen at vtm_plan only) or
+                        VTM_METHOD_ASYNC (switchable with VTM by vtm_set_opts) */
   int batch;         /* several right-hand sides: 0 (default) one batched iteration over
                         up to 64 columns at a time; 1: one column after the other */
   int batch_solve;   /* batched FP32 band solves: 0 (default) row window in shared memory;

@@ -16,6 +16,8 @@ Algorithm to Solve the Linear System of Circuit" (arXiv 0910.0663):
                          own system with ``C + W`` on the twin rows and the
                          delayed waves ``W u_twin - i_twin`` on the right-hand
                          side; zero initial boundary values.
+* ``vtm_midpoint_delayed``  VTM with stochastic line delays (Sec. XI, the
+                         asynchronous/chaotic form).
 * ``reflection_ops``     Sec. VIII: input admittance ``S = C - E D^-1 F`` and
                          voltage reflection matrix ``T = (W - S)(W + S)^-1``.
 * ``line_admittance_choice``  Sec. VIII choices of W (alpha I, diagonal,
@@ -354,6 +356,65 @@ def vtm_midpoint(A: sp.csr_matrix, partition: np.ndarray, nparts: int, b: np.nda
     if keep_iterates:
         return res, iterates
     return res
+
+
+def vtm_midpoint_delayed(A: sp.csr_matrix, partition: np.ndarray, nparts: int, b: np.ndarray,
+                         W=1.0, tol: float = 1e-10, max_sweeps: int = 100000, max_delay: int = 2,
+                         seed: int = 0, tear: Optional[Tearing] = None):
+    """VTM with stochastic line delays (Sec. XI: "if the delays of virtual
+    transmission lines are different and stochastic, VTM would turn to be a
+    fully asynchronous and chaotic numerical algorithm").
+
+    As ``vtm_midpoint``, except that at sweep k the wave arriving at port s
+    left its twin d sweeps earlier, d drawn uniformly from 1..max_delay for
+    every (port, sweep) by ``numpy.random.default_rng(seed)``:
+        w_in(s)^k = W u_twin^(k-d) - i_twin^(k-d)   (zero before sweep 1).
+    max_delay = 1 is ``vtm_midpoint``.  Returns a ``VTMResult``."""
+    A = A.tocsr()
+    b = np.atleast_2d(np.asarray(b, dtype=np.float64))
+    nrhs, n = b.shape
+    if tear is None:
+        tear = tear_midpoint(A, partition, nparts)
+    Wp = _line_admittance(tear, W)
+    nports = len(tear.port_g)
+    rng = np.random.default_rng(seed)
+    lus = [spla.splu(local_system(A, tear, P, Wp)) for P in range(nparts)]
+    # sent[j] = outgoing wave W u - i of every port after sweep k - j
+    sent = [np.zeros((nrhs, nports)) for _ in range(max_delay)]
+    x = np.zeros((nrhs, n))
+    u = np.zeros((nrhs, nports))
+    cur = np.zeros((nrhs, nports))
+    w_in = np.zeros((nrhs, nports))
+    history = []
+    lag = sp.csr_matrix((tear.lag_rho, (tear.lag_i, tear.lag_j)), shape=(n, n))
+    converged = False
+    k = 0
+    while k < max_sweeps:
+        k += 1
+        d = rng.integers(1, max_delay + 1, size=nports)
+        w_in = np.empty((nrhs, nports))
+        for s_ in range(nports):
+            w_in[:, s_] = sent[d[s_] - 1][:, tear.twin[s_]]
+        rhs_nodes = b - (lag @ x.T).T
+        u_new = np.empty_like(u)
+        x_new = np.empty_like(x)
+        for P in range(nparts):
+            ports = tear.tile_ports[P]
+            nodes = tear.tile_nodes[P]
+            rhs = np.concatenate([w_in[:, ports].T, rhs_nodes[:, nodes].T], axis=0)
+            sol = lus[P].solve(np.ascontiguousarray(rhs))
+            u_new[:, ports] = sol[:len(ports)].T
+            x_new[:, nodes] = sol[len(ports):].T
+        cur = -Wp * u_new + w_in
+        u = u_new
+        x = x_new
+        sent = [Wp * u - cur] + sent[:-1]
+        rel = residual_norms(A, x, b)
+        history.append(rel)
+        if np.all(rel <= tol):
+            converged = True
+            break
+    return VTMResult(x, k, converged, np.array(history), u, cur, w_in)
 
 
 def reflection_ops(A: sp.csr_matrix, tear: Tearing, P: int, W=1.0):

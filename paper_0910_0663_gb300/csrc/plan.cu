@@ -861,6 +861,10 @@ extern "C" vtm_status vtm_set_opts(vtm_plan_t P, const vtm_opts* opts) {
     set_detail("vtm_set_opts: sweep_kernel must be 0..8");
     return VTM_EINVAL;
   }
+  if (o.method < 0 || o.method > 2 || ((o.method == VTM_METHOD_BJ) != (P->method == VTM_METHOD_BJ))) {
+    set_detail("vtm_set_opts: method must be 0..2, and block Jacobi is chosen by vtm_plan");
+    return VTM_EINVAL;
+  }
   bool prec_changed = o.precision != P->opts.precision;
   fill_default_opts(&o);
   P->opts = o;
@@ -945,11 +949,12 @@ extern "C" vtm_status vtm_plan(int64_t n, const int64_t* rowptr, const int32_t* 
     }
   vtm_opts o{};
   if (opts) o = *opts;
-  if (o.method != VTM_METHOD_VTM && o.method != VTM_METHOD_BJ) {
+  if (o.method != VTM_METHOD_VTM && o.method != VTM_METHOD_BJ && o.method != VTM_METHOD_ASYNC) {
     set_detail("vtm_plan: unknown method");
     return fail(VTM_EINVAL);
   }
-  P->method = o.method;
+  // asynchronous VTM tears like VTM; only its sweeps differ
+  P->method = o.method == VTM_METHOD_BJ ? VTM_METHOD_BJ : VTM_METHOD_VTM;
   std::vector<CutPair> pairs;
   if ((st = build_structure(P, pairs)) != VTM_OK) return fail(st);
   P->general = !P->lag_i.empty() || P->method == VTM_METHOD_BJ;

@@ -1157,7 +1157,12 @@ __device__ __forceinline__ bool flow_wait_ready(const int* gk, const int* done,
   return true;
 }
 
-template <class TT, int NT, int KB>
+// ASYNC: asynchronous VTM (Sec. XI: lines with different, varying delays).
+// No neighbour waits and one wave slot: a tile reads whatever waves its
+// neighbours last wrote (delay 0, 1 or 2 sweeps; the decision lag still keeps
+// every tile within two sweeps of the slowest).  The fixed point is the same;
+// the iterates depend on timing.
+template <class TT, int NT, int KB, bool ASYNC>
 __global__ void __launch_bounds__(NT, 768 / NT) sweep_flow_kernel(
     const TT* __restrict__ Tp, const TileDesc* __restrict__ tdesc,
     const int32_t* __restrict__ twin, const float2* __restrict__ kd,
@@ -1193,14 +1198,15 @@ __global__ void __launch_bounds__(NT, 768 / NT) sweep_flow_kernel(
       SymPorts<NT> pt;
       pt.load(twin, kd, run, c, p0, p);
       if (warp == 0) {
-        bool ok = flow_wait_ready(gk, done, nbr, nbr_off[tile], nbr_off[tile + 1], k, ctrl);
+        bool ok = ASYNC ? flow_wait_ready(gk, done, nbr, 0, 0, k, ctrl)
+                        : flow_wait_ready(gk, done, nbr, nbr_off[tile], nbr_off[tile + 1], k, ctrl);
         __threadfence();  // every lane that saw a counter orders its later reads
         if (tid == 0) s_stop = (ok && !*((volatile int*)&ctrl->flag)) ? 0 : 1;
       }
       __syncthreads();
       if (s_stop) return;
-      const float* prev = state3 + (size_t)((k - 1) % 3) * nports * 2;
-      float* cur = state3 + (size_t)(k % 3) * nports * 2;
+      const float* prev = state3 + (ASYNC ? 0 : (size_t)((k - 1) % 3) * nports * 2);
+      float* cur = state3 + (ASYNC ? 0 : (size_t)(k % 3) * nports * 2);
       const float sq = sym_gather<NT>(pt, prev, w_in, rs, p0, p, nb, k);
       const double tile_sq = (double)block_sum_value_f(sq);
       int bi = 0, off = warp;
@@ -1521,8 +1527,8 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   if (sym_ok) {
     int coop = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, P->device);
-    const void* kfn = prec == VTM_PREC_FP32 ? (const void*)sweep_flow_kernel<float, 128, 4>
-                                            : (const void*)sweep_flow_kernel<__nv_bfloat16, 128, 8>;
+    const void* kfn = prec == VTM_PREC_FP32 ? (const void*)sweep_flow_kernel<float, 128, 4, false>
+                                            : (const void*)sweep_flow_kernel<__nv_bfloat16, 128, 8, false>;
     int per_sm = 0;
     if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 128, sym_smem) == cudaSuccess &&
         per_sm > 0)
@@ -1559,12 +1565,22 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
     double* hp = hist;
     void* args[] = {&Tp, &td, &tw, &kdp, &rn, &cp, &st3, &npv, &no, &nbp, &dn, &cnt, &gkp, &ct, &p4, &hp,
                     &hl, &np, &ppm, &k0};
-    const void* kfn = prec == VTM_PREC_FP32 ? (const void*)sweep_flow_kernel<float, 128, 4>
-                                            : (const void*)sweep_flow_kernel<__nv_bfloat16, 128, 8>;
+    const bool async = P->opts.method == VTM_METHOD_ASYNC;
+    const void* kfn =
+        prec == VTM_PREC_FP32
+            ? (async ? (const void*)sweep_flow_kernel<float, 128, 4, true>
+                     : (const void*)sweep_flow_kernel<float, 128, 4, false>)
+            : (async ? (const void*)sweep_flow_kernel<__nv_bfloat16, 128, 8, true>
+                     : (const void*)sweep_flow_kernel<__nv_bfloat16, 128, 8, false>);
     return cudaLaunchCooperativeKernel(kfn, flow_grid, 128, args, sym_smem, s);
   };
   const bool symload = ((choice == 5 || choice == 6) && sym_ok) || (choice == 7 && symb_ok) ||
                        (choice == 8 && flow_ok);
+  if (P->opts.method == VTM_METHOD_ASYNC && !flow_ok) {
+    set_detail("vtm_solve: asynchronous VTM runs on the packed symmetric dataflow kernel: it needs "
+               "FP32/BF16 sweeps of a symmetric plan with at most 256 ports per sub-circuit");
+    return VTM_EINVAL;
+  }
   if (symb_ok) {
     VTM_CUDA_TRY(cudaFuncSetAttribute(prec == VTM_PREC_FP32
                                           ? (const void*)sweep_symb_kernel<float, 128>
@@ -1573,7 +1589,8 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   }
 
   int kern = (vecload || symload) ? choice : (staged ? 2 : 1);
-  if (P->opts.sweep_kernel == 0) {
+  if (P->opts.method == VTM_METHOD_ASYNC) kern = 8;  // its own iteration: not autotuned
+  else if (P->opts.sweep_kernel == 0) {
     if (P->tuned_kernel[prec] == 0) {
       const bool can_st = nv_max <= 4 * 256 && st_smem <= 200 * 1024;
       const bool can_vec = nv_max <= 256;
@@ -1679,7 +1696,8 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
     }
     *flag_out = r.flag;
     *sweep_out = (r.flag == 1 || r.flag == 4) ? r.conv_sweep : std::min(r.k - 1, budget);
-    P->wave_slot = P->d_fstate32.as<float>() + (size_t)(*sweep_out % 3) * npt * 2;
+    P->wave_slot = P->d_fstate32.as<float>() +
+                   (P->opts.method == VTM_METHOD_ASYNC ? 0 : (size_t)(*sweep_out % 3) * npt * 2);
     return VTM_OK;
   }
   // Batches of check_every launches, captured once into a CUDA graph when the
@@ -1953,7 +1971,8 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
 vtm_status solve_columns(vtm_plan_s* P, const double* d_b, double* d_x, int64_t nrhs, double tol,
                          vtm_info* info) {
   // several right-hand sides: one batched iteration (up to 64 per pass)
-  const bool batch = P->opts.batch != 1 && nrhs >= 2 && !P->general && !P->port_node.empty();
+  const bool batch = P->opts.batch != 1 && nrhs >= 2 && !P->general && !P->port_node.empty() &&
+                     P->opts.method != VTM_METHOD_ASYNC;  // asynchronous VTM: column by column
   if (batch) {
     vtm_status worst = VTM_OK;
     vtm_info agg{};

@@ -634,3 +634,32 @@ def test_march_settles_to_the_dc_solution_and_is_linear():
     lhs = O.backward_euler_march(A, c, p1 + p2, a1 + a2)
     rhs = O.backward_euler_march(A, c, p1, a1) + O.backward_euler_march(A, c, p2, a2)
     assert np.allclose(lhs, rhs, rtol=1e-12, atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# Stochastic line delays (the asynchronous form of Sec. XI)
+# ---------------------------------------------------------------------------
+
+def test_unit_delays_are_the_synchronous_iteration():
+    w = wl.grid2d(24, 24, 8, 6, seed=61)
+    A = w.csr()
+    r1 = O.vtm_midpoint(A, w.partition, w.nparts, w.b, W=1.0, tol=0, max_sweeps=40)
+    r2 = O.vtm_midpoint_delayed(A, w.partition, w.nparts, w.b, W=1.0, tol=0, max_sweeps=40,
+                                max_delay=1)
+    assert np.allclose(r1.history, r2.history, rtol=1e-12, atol=0)
+    assert np.abs(r1.x - r2.x).max() <= 1e-13 * np.abs(r1.x).max()
+
+
+@pytest.mark.parametrize("max_delay,seed", [(2, 0), (3, 1), (4, 2)])
+def test_stochastic_delays_keep_the_fixed_point(max_delay, seed):
+    # whatever the delays, a converged state satisfies the twin-row and node
+    # equations of Eq. 11 with equal waves both ways, i.e. A x = b
+    w = wl.power_grid(64, 64, 16, 16, Zc=1.0, seed=62)
+    A = w.csr()
+    r = O.vtm_midpoint_delayed(A, w.partition, w.nparts, w.b, W=1.0, tol=1e-11, max_sweeps=20000,
+                               max_delay=max_delay, seed=seed)
+    assert r.converged
+    x_star = O.direct_solve(A, w.b)
+    assert np.abs(r.x - x_star).max() <= 1e-8 * np.abs(x_star).max()
+    sync = O.vtm_midpoint(A, w.partition, w.nparts, w.b, W=1.0, tol=1e-11)
+    assert r.sweeps >= sync.sweeps  # delays slow the exchange down
