@@ -541,18 +541,41 @@ __global__ void __launch_bounds__(256) batch_sweep_kernel(
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0;
   if (k > 1) {
-    for (int t0 = 0; t0 < p; t0 += kKC) {
-      for (int i = tid; i < kKC * kMB; i += blockDim.x) {
+    // chunk loads are staged in registers one chunk ahead (256 threads x 4
+    // elements of T and of W_in), so their latency hides behind the FMAs
+    constexpr int PT = kKC * kMB / 256, PW = kKC * 64 / 256;
+    static_assert(PT * 256 == kKC * kMB && PW * 256 == kKC * 64, "chunk shape");
+    AT tv[PT], wv[PW];
+    auto fetch = [&](int t0) {
+#pragma unroll
+      for (int e = 0; e < PT; ++e) {
+        const int i = tid + e * 256;
         const int kk = i / kMB, mm = i % kMB;
         const int t = t0 + kk, s = m0 + mm;
-        Ts[kk][mm] = (t < p && s < m1) ? to_acc(Tb[(size_t)t * ld + s]) : AT(0);
+        tv[e] = (t < p && s < m1) ? to_acc(Tb[(size_t)t * ld + s]) : AT(0);
       }
-      for (int i = tid; i < kKC * 64; i += blockDim.x) {
+#pragma unroll
+      for (int e = 0; e < PW; ++e) {
+        const int i = tid + e * 256;
         const int kk = i / 64, r = i % 64;
         const int t = t0 + kk;
-        Ws[kk][r] = (t < p && r < R) ? (AT)prev[(size_t)twin[p0 + t] * 2 * R + R + r] : AT(0);
+        wv[e] = (t < p && r < R) ? (AT)prev[(size_t)twin[p0 + t] * 2 * R + R + r] : AT(0);
+      }
+    };
+    fetch(0);
+    for (int t0 = 0; t0 < p; t0 += kKC) {
+#pragma unroll
+      for (int e = 0; e < PT; ++e) {
+        const int i = tid + e * 256;
+        Ts[i / kMB][i % kMB] = tv[e];
+      }
+#pragma unroll
+      for (int e = 0; e < PW; ++e) {
+        const int i = tid + e * 256;
+        Ws[i / 64][i % 64] = wv[e];
       }
       __syncthreads();
+      if (t0 + kKC < p) fetch(t0 + kKC);
 #pragma unroll
       for (int kk = 0; kk < kKC; ++kk) {
         AT a[4], b[4];
