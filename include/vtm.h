@@ -105,7 +105,8 @@ typedef struct {
                         fastest; 1: direct-load kernel; 2: bulk-copy staged kernel;
                         3: 16-byte vector-load kernel, 256 threads per tile;
                         4: the same with 128 threads (p <= 128 VEC);
-                        5, 6: packed symmetric kernel, 128 / 64 threads per tile --
+                        5, 6: packed symmetric kernel, 128 threads per tile, up to 85 / 64
+                        registers (6 / 8 CTAs per SM) --
                         FP32/BF16 plans of a symmetric A whose sub-circuits have at
                         most 256 ports keep only the 16x16 blocks of T_P on and above
                         the diagonal (T_P is symmetric for scalar W, Sec. VIII), about

@@ -969,8 +969,8 @@ __device__ __forceinline__ void sym_finish(const SymPorts<NT>& pt, const float* 
   if (threadIdx.x == 0) sweep_decide(ctrl, k, tot, hist, hist_len);
 }
 
-template <class TT, int NT, int KB>
-__global__ void __launch_bounds__(NT, 768 / NT) sweep_sym_kernel(
+template <class TT, int NT, int KB, int MINB>
+__global__ void __launch_bounds__(NT, MINB) sweep_sym_kernel(
     const TT* __restrict__ Tp, const TileDesc* __restrict__ tdesc,
     const int32_t* __restrict__ twin, const float2* __restrict__ kd,
     const uint8_t* __restrict__ run, const float* __restrict__ c, float* __restrict__ state,
@@ -1010,7 +1010,6 @@ __global__ void __launch_bounds__(NT, 768 / NT) sweep_sym_kernel(
   const float* prev = state + (size_t)((k - 1) & 1) * nports * 2;
   float* cur = state + (size_t)(k & 1) * nports * 2;
   const float sq = sym_gather<NT>(pt, prev, w_in, rs, p0, p, nb, k);
-  const double tile_sq = (double)block_sum_value_f(sq);
   int bi = 0, off = warp;  // block warp + i NW is (bi, bi + off) once off < nb - bi
   for (int base = 0; base < nblk; base += KB * NW) {
 #pragma unroll
@@ -1029,7 +1028,9 @@ __global__ void __launch_bounds__(NT, 768 / NT) sweep_sym_kernel(
       }
     }
   }
-  __syncthreads();
+  // the residual of sweep k - 1 is reduced after the blocks (its barriers
+  // would otherwise hold every warp back before its first block)
+  const double tile_sq = (double)block_sum_value_f(sq);
   sym_finish<NT>(pt, part, w_in, cur, p0, p, nb, tile, tile_sq, k, ctrl, partials, hist, hist_len,
                  nparts, &s_last);
 }
@@ -1440,7 +1441,7 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   // persisting carve-out allows (restored after the sweeps)
   L2Window l2win(P, prec);
   // one sweep launch with kernel `kc` (1 direct, 2 staged, 3/4 vector loads with
-  // 256/128 threads, 5/6 packed symmetric with 128/64 threads, 7 packed
+  // 256/128 threads, 5/6 packed symmetric (128 threads, 85/64 registers), 7 packed
   // symmetric with the tile in shared memory by one bulk copy; 8, the dataflow
   // sweeps, is launched once per inner solve by launch_flow)
   auto launch_one = [&](int kc) {
@@ -1463,12 +1464,13 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
             P->d_run.as<uint8_t>(), P->d_c32.as<float>(), P->d_state32.as<float>(), npt_,
             P->d_ctrl.as<SweepCtrl>(), P->d_partials.as<double>(), hist, hist_len, P->nparts, pp_max);
       };
+      // 5: up to 85 registers (6 CTAs per SM); 6: 64 registers (8 CTAs per SM)
       if (prec == VTM_PREC_FP32) {
-        if (kc == 5) go(sweep_sym_kernel<float, 128, 4>, 128, P->d_Tp32.as<float>());
-        else go(sweep_sym_kernel<float, 64, 4>, 64, P->d_Tp32.as<float>());
+        if (kc == 5) go(sweep_sym_kernel<float, 128, 4, 6>, 128, P->d_Tp32.as<float>());
+        else go(sweep_sym_kernel<float, 128, 4, 8>, 128, P->d_Tp32.as<float>());
       } else {
-        if (kc == 5) go(sweep_sym_kernel<__nv_bfloat16, 128, 8>, 128, P->d_Tp16.as<__nv_bfloat16>());
-        else go(sweep_sym_kernel<__nv_bfloat16, 64, 8>, 64, P->d_Tp16.as<__nv_bfloat16>());
+        if (kc == 5) go(sweep_sym_kernel<__nv_bfloat16, 128, 8, 6>, 128, P->d_Tp16.as<__nv_bfloat16>());
+        else go(sweep_sym_kernel<__nv_bfloat16, 128, 8, 8>, 128, P->d_Tp16.as<__nv_bfloat16>());
       }
       return;
     }
