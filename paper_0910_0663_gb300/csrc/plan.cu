@@ -1103,8 +1103,9 @@ extern "C" vtm_status vtm_plan_get_stats(vtm_plan_t P, vtm_plan_stats* s) {
   s->t_bytes = (int64_t)(P->d_T64.bytes + P->d_T32.bytes + P->d_T16.bytes + P->d_E.bytes +
                          P->d_Tp32.bytes + P->d_Tp16.bytes);
   s->factor_bytes = (int64_t)(P->d_Lc.bytes + P->d_Uc.bytes);
-  s->sweep_kernel = P->tuned_kernel[P->opts.precision] ? P->tuned_kernel[P->opts.precision]
-                                                        : P->opts.sweep_kernel;
+  s->sweep_kernel = P->opts.method == VTM_METHOD_ASYNC   ? 8
+                    : P->tuned_kernel[P->opts.precision] ? P->tuned_kernel[P->opts.precision]
+                                                         : P->opts.sweep_kernel;
   s->sum_tri = P->sum_tri;
   s->packed_bytes = (int64_t)(P->d_Tp32.bytes + P->d_Tp16.bytes);
   return VTM_OK;
