@@ -255,18 +255,22 @@ def plan_colidx(w, dev):
     return torch.from_numpy(w.indices).to(dev)
 
 
-def traffic_record(prec):
-    """ncu DRAM bytes per sweep launch, if captured for the current kernel."""
+def traffic_record(prec, stats, workload):
+    """ncu DRAM bytes per sweep launch (profiles/sweep_traffic.json), if they
+    were captured for this precision, this sweep kernel and the unchanged
+    kernel source (the file records the sha256 of solve.cu); else None."""
     path = os.path.join(ROOT, "profiles", "sweep_traffic.json")
-    if not os.path.exists(path):
+    if not os.path.exists(path) or workload != "power_grid":
         return None
     with open(path) as fh:
         rec = json.load(fh)
     src = open(os.path.join(ROOT, "paper_0910_0663_gb300", "csrc", "solve.cu"), "rb").read()
     if rec.get("solve_cu_sha256") != hashlib.sha256(src).hexdigest():
         return None
-    v = rec.get("bytes_per_launch", {}).get({0: "fp64", 1: "fp32", 2: "bf16"}[prec])
-    return v
+    entry = rec.get("per_launch", {}).get({0: "fp64", 1: "fp32", 2: "bf16"}[prec])
+    if not entry or stats.get("sweep_kernel") not in entry.get("sweep_kernels", []):
+        return None
+    return entry.get("bytes")
 
 
 def gpu_arm(args):
@@ -433,7 +437,8 @@ def emit(args, results, errors, best, w, world, rank):
         "roofline": {"bound": "hbm", "kernel": "sweep_kernel",
                      "achieved": R["achieved_gbs"], "peak": peak, "unit": "GB/s",
                      "frac": R["achieved_gbs"] / peak, "peak_source": peak_src,
-                     "traffic": traffic_record(prec_id),
+                     "traffic": traffic_record(prec_id, R["stats"], args.workload)
+                     if args.grid == 2048 else None,
                      "algorithmic_bytes_per_launch": R["bytes_sweep"],
                      "avg_launch_ms": R["t_sweep_ms"]},
         "e2e": {"value": R["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": w.n * 8 * R["nrhs"],
