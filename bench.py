@@ -255,6 +255,17 @@ def plan_colidx(w, dev):
     return torch.from_numpy(w.indices).to(dev)
 
 
+def sweep_kernel_name(kernel, nrhs):
+    if nrhs > 1:
+        return "batch_sweep_kernel / batch_sweep_mma_kernel (batched right-hand sides)"
+    return {1: "sweep_kernel (direct loads)", 2: "sweep_staged_kernel (bulk-copy ring)",
+            3: "sweep_vec_kernel (256 threads)", 4: "sweep_vec_kernel (128 threads)",
+            5: "sweep_sym_kernel (packed symmetric, 128 threads)",
+            6: "sweep_sym_kernel (packed symmetric, 64 registers)",
+            7: "sweep_symb_kernel (packed symmetric, one bulk copy per tile)",
+            8: "sweep_flow_kernel (dataflow, one cooperative launch)"}.get(kernel, str(kernel))
+
+
 def traffic_record(prec, stats, workload):
     """ncu DRAM bytes per sweep launch (profiles/sweep_traffic.json), if they
     were captured for this precision, this sweep kernel and the unchanged
@@ -434,7 +445,7 @@ def emit(args, results, errors, best, w, world, rank):
         "dtype": {"fp64": "f64", "fp32": "f32+f64 refinement", "bf16": "bf16+f64 refinement"}[best.split("_")[-1]],
         "data": "synthetic", "config": dict(workload_config(args), precision=best,
                                             **admittance_config(args)),
-        "roofline": {"bound": "hbm", "kernel": "sweep_kernel",
+        "roofline": {"bound": "hbm", "kernel": sweep_kernel_name(R["stats"].get("sweep_kernel"), R["nrhs"]),
                      "achieved": R["achieved_gbs"], "peak": peak, "unit": "GB/s",
                      "frac": R["achieved_gbs"] / peak, "peak_source": peak_src,
                      "traffic": traffic_record(prec_id, R["stats"], args.workload)
