@@ -266,17 +266,26 @@ def sweep_kernel_name(kernel, nrhs):
             8: "sweep_flow_kernel (dataflow, one cooperative launch)"}.get(kernel, str(kernel))
 
 
+def sweep_kernel_source_hash():
+    """sha256 of the device code of the packed sweep kernels in solve.cu (the
+    text from their section header to the host driver's)."""
+    src = open(os.path.join(ROOT, "paper_0910_0663_gb300", "csrc", "solve.cu")).read()
+    i = src.find("// Packed symmetric sweep.")
+    j = src.find("// host driver", i)
+    return hashlib.sha256(src[i:j].encode()).hexdigest() if 0 <= i < j else None
+
+
 def traffic_record(prec, stats, workload):
     """ncu DRAM bytes per sweep launch (profiles/sweep_traffic.json), if they
     were captured for this precision, this sweep kernel and the unchanged
-    kernel source (the file records the sha256 of solve.cu); else None."""
+    kernel source (the file records the hash of the packed kernels' source);
+    else None."""
     path = os.path.join(ROOT, "profiles", "sweep_traffic.json")
     if not os.path.exists(path) or workload != "power_grid":
         return None
     with open(path) as fh:
         rec = json.load(fh)
-    src = open(os.path.join(ROOT, "paper_0910_0663_gb300", "csrc", "solve.cu"), "rb").read()
-    if rec.get("solve_cu_sha256") != hashlib.sha256(src).hexdigest():
+    if rec.get("kernel_source_sha256") != sweep_kernel_source_hash():
         return None
     entry = rec.get("per_launch", {}).get({0: "fp64", 1: "fp32", 2: "bf16"}[prec])
     if not entry or stats.get("sweep_kernel") not in entry.get("sweep_kernels", []):

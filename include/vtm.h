@@ -84,7 +84,7 @@ typedef struct {
   int max_sweeps;    /* sweeps per vtm_solve call, all refinement steps together; default 200000 */
   int check_every;   /* sweeps launched between two host polls of the convergence flag; default 32 */
   double inner_tol;  /* relative tolerance of each inner solve in the refinement modes;
-                        0 -> 1e-5 (FP32) / 1e-2 (BF16).  An inner solve that can finish
+                        0 -> 1e-5 (FP32) / 3e-3 (BF16).  An inner solve that can finish
                         the job (inner_tol x its right-hand side <= 4 tol ||b||) aims at
                         tol/2 instead.  An inner solve also ends when its residual has
                         not dropped by 10% within 64 sweeps (its rounding floor); the

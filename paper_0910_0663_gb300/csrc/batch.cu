@@ -945,7 +945,7 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
   info->relres = 0.0;
   info->first_sweep_converged = 0;
   double inner_tol = P->opts.inner_tol;
-  if (inner_tol <= 0) inner_tol = prec == VTM_PREC_FP32 ? 1e-5 : (prec == VTM_PREC_BF16 ? 1e-2 : 0.0);
+  if (inner_tol <= 0) inner_tol = prec == VTM_PREC_FP32 ? 1e-5 : (prec == VTM_PREC_BF16 ? 3e-3 : 0.0);
   const int max_outer = prec == VTM_PREC_FP64 ? 4 : P->opts.max_outer;
   int sweeps_left = P->opts.max_sweeps;
   vtm_status result = VTM_ENOCONV;

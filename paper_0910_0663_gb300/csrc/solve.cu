@@ -1833,9 +1833,10 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
     return VTM_OK;
   }
   // Default inner tolerance: FP32 sweeps gain five digits per refinement step
-  // (two steps reach 1e-10), BF16 sweeps about two.
+  // (two steps reach 1e-10), BF16 sweeps two and a half (measured: 3e-3 takes
+  // one step less than 1e-2 on the power grid and the thermal grid).
   double inner_tol = P->opts.inner_tol;
-  if (inner_tol <= 0) inner_tol = prec == VTM_PREC_FP32 ? 1e-5 : (prec == VTM_PREC_BF16 ? 1e-2 : 0.0);
+  if (inner_tol <= 0) inner_tol = prec == VTM_PREC_FP32 ? 1e-5 : (prec == VTM_PREC_BF16 ? 3e-3 : 0.0);
   const int max_outer = (prec == VTM_PREC_FP64 || P->general) ? 4 : P->opts.max_outer;
   int sweeps_left = P->opts.max_sweeps;
   vtm_status result = VTM_ENOCONV;
