@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="vtm", choices=["vtm", "reference"])
-    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "fp32", "bf16"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "fp32", "bf16", "fp16"])
     ap.add_argument("--workload", default="power_grid", choices=["power_grid", "thermal", "vccs", "grad"],
                     help="power_grid: the headline 2048^2 grid; thermal: 128x128x32 RC grid, 400 boxes, "
                          "64 RHS; vccs: 1024^2 grid with controlled sources, VTM and block Jacobi; "
@@ -55,7 +55,7 @@ def parse():
                          "wob = alpha 2g, sca = partial input admittance over --radius branches")
     ap.add_argument("--method", default="vtm", choices=["vtm", "async"],
                     help="vtm: synchronous sweeps; async: asynchronous VTM (tiles read the latest "
-                         "waves of their neighbours, FP32/BF16 symmetric plans)")
+                         "waves of their neighbours, FP32/BF16/FP16 symmetric plans)")
     ap.add_argument("--alpha", type=float, default=0.5, help="the weight of --admittance wob")
     ap.add_argument("--radius", type=int, default=1, help="the neighbourhood of --admittance sca")
     ap.add_argument("--sweep-kernel", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6, 7, 8],
@@ -237,7 +237,7 @@ def sweep_bytes(stats, prec, nrhs=1):
     the residual coefficients (g/W, d) (2 x 8 B in FP64, 2 x 4 B otherwise;
     the batched sweep reads them in FP64), twin index (4 B) and node-run byte
     (1 B)."""
-    s_t = {0: 8, 1: 4, 2: 2}[prec]
+    s_t = {0: 8, 1: 4, 2: 2, 3: 2}[prec]
     s_w = 8 if prec == 0 else 4
     s_kd = 16 if (prec == 0 or nrhs > 1) else 8
     # the packed symmetric kernels need only the entries on and above the diagonal
@@ -287,7 +287,7 @@ def traffic_record(prec, stats, workload):
         rec = json.load(fh)
     if rec.get("kernel_source_sha256") != sweep_kernel_source_hash():
         return None
-    entry = rec.get("per_launch", {}).get({0: "fp64", 1: "fp32", 2: "bf16"}[prec])
+    entry = rec.get("per_launch", {}).get({0: "fp64", 1: "fp32", 2: "bf16", 3: "fp16"}[prec])
     if not entry or stats.get("sweep_kernel") not in entry.get("sweep_kernels", []):
         return None
     return entry.get("bytes")
@@ -327,9 +327,9 @@ def gpu_arm(args):
     if args.workload == "vccs":
         precs = ["fp64", "bj_fp64"]
     elif args.precision == "auto":
-        precs = ["fp64", "fp32", "bf16"] if args.workload != "grad" else ["fp64", "fp32"]
+        precs = ["fp64", "fp32", "bf16", "fp16"] if args.workload != "grad" else ["fp64", "fp32"]
         if args.method == "async":
-            precs = ["fp32", "bf16"]  # asynchronous sweeps run in FP32/BF16 only
+            precs = ["fp32", "bf16", "fp16"]  # asynchronous sweeps run in FP32/16-bit only
     else:
         precs = [args.precision]
     results = {}
@@ -426,7 +426,7 @@ def run_mode(args, prec, w, dev, stream, b_dev, b_host, x_host, flush, world):
             e2e.append(h1 - h0)
         st = plan.stats()
         inf = infos[-1]
-        bytes_sweep = sweep_bytes(st, {"fp64": 0, "fp32": 1, "bf16": 2}[prec_name], nrhs)
+        bytes_sweep = sweep_bytes(st, {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3}[prec_name], nrhs)
         # the CUDA events bracket each batch of sweep launches on the plan's
         # stream; launches past convergence in the last batch return at once
         # and stay inside the time: per sweep = batch time / sweeps run
@@ -446,12 +446,13 @@ def run_mode(args, prec, w, dev, stream, b_dev, b_host, x_host, flush, world):
 def emit(args, results, errors, best, w, world, rank):
     R = results[best]
     peak, peak_src = measured_peaks()
-    prec_id = {"fp64": 0, "fp32": 1, "bf16": 2}[best.split("_")[-1]]
+    prec_id = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3}[best.split("_")[-1]]
     line = {
         "metric": METRIC, "value": R["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": R["t_step_ms"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64", "fp32": "f32+f64 refinement", "bf16": "bf16+f64 refinement"}[best.split("_")[-1]],
+        "dtype": {"fp64": "f64", "fp32": "f32+f64 refinement", "bf16": "bf16+f64 refinement",
+                  "fp16": "f16+f64 refinement"}[best.split("_")[-1]],
         "data": "synthetic", "config": dict(workload_config(args), precision=best,
                                             **admittance_config(args)),
         "roofline": {"bound": "hbm", "kernel": sweep_kernel_name(R["stats"].get("sweep_kernel"), R["nrhs"]),

@@ -63,7 +63,10 @@ typedef enum {
 enum {
   VTM_PREC_FP64 = 0, /* plain FP64 VTM */
   VTM_PREC_FP32 = 1, /* FP32 T_P and waves, FP32 accumulate, inside FP64 iterative refinement */
-  VTM_PREC_BF16 = 2  /* BF16 T_P, FP32 waves and accumulate, inside FP64 iterative refinement */
+  VTM_PREC_BF16 = 2, /* BF16 T_P, FP32 waves and accumulate, inside FP64 iterative refinement */
+  VTM_PREC_FP16 = 3  /* FP16 T_P, FP32 waves and accumulate, inside FP64 iterative refinement:
+                        the bytes of BF16 with a 10-bit mantissa; T_P of a symmetric plan has
+                        its spectrum in (-1, 1] (Sec. VIII), so no entry leaves FP16's range */
 };
 
 /* Iteration run by a plan. */
@@ -75,7 +78,7 @@ enum {
                          one cooperative launch in which every tile reads the waves its
                          neighbours last wrote, without waiting for them (kept within two
                          sweeps of each other).  Same fixed point, timing-dependent
-                         iterates.  Needs FP32/BF16 sweeps of a symmetric plan with at most
+                         iterates.  Needs FP32/BF16/FP16 sweeps of a symmetric plan with at most
                          256 ports per sub-circuit (VTM_EINVAL at vtm_solve otherwise) */
 };
 
@@ -84,19 +87,19 @@ typedef struct {
   int max_sweeps;    /* sweeps per vtm_solve call, all refinement steps together; default 200000 */
   int check_every;   /* sweeps launched between two host polls of the convergence flag; default 32 */
   double inner_tol;  /* relative tolerance of each inner solve in the refinement modes;
-                        0 -> 1e-5 (FP32) / 3e-3 (BF16).  An inner solve that can finish
+                        0 -> 1e-5 (FP32) / 1e-3 (FP16) / 3e-3 (BF16).  An inner solve that can finish
                         the job (inner_tol x its right-hand side <= 4 tol ||b||) aims at
                         tol/2 instead.  An inner solve also ends when its residual has
                         not dropped by 10% within 64 sweeps (its rounding floor); the
                         FP64 refinement then continues. */
-  int max_outer;     /* refinement steps in the FP32/BF16 modes; default 40 */
+  int max_outer;     /* refinement steps in the FP32/BF16/FP16 modes; default 40 */
   int method;        /* VTM_METHOD_VTM (default), VTM_METHOD_BJ (chosen at vtm_plan only) or
                         VTM_METHOD_ASYNC (switchable with VTM by vtm_set_opts) */
   int batch;         /* several right-hand sides: 0 (default) one batched iteration over
                         up to 64 columns at a time; 1: one column after the other */
   int batch_solve;   /* batched FP32 band solves: 0 (default) row window in shared memory;
                         1: whole column block in shared memory */
-  int l2_persist;    /* 0 (default): during FP32/BF16 sweeps, mark the reflection matrices
+  int l2_persist;    /* 0 (default): during FP32/16-bit sweeps, mark the reflection matrices
                         persisting in L2 (access-policy window on the plan's stream; the
                         context's persisting carve-out is set and restored around the
                         sweeps); 1: off.  Needs a non-default stream. */
@@ -107,7 +110,7 @@ typedef struct {
                         4: the same with 128 threads (p <= 128 VEC);
                         5, 6: packed symmetric kernel, 128 threads per tile, up to 85 / 64
                         registers (6 / 8 CTAs per SM) --
-                        FP32/BF16 plans of a symmetric A whose sub-circuits have at
+                        FP32/BF16/FP16 plans of a symmetric A whose sub-circuits have at
                         most 256 ports keep only the 16x16 blocks of T_P on and above
                         the diagonal (T_P is symmetric for scalar W, Sec. VIII), about
                         half the bytes per sweep; 7: the same blocks, each tile brought
@@ -207,7 +210,7 @@ vtm_status vtm_set_admittance(vtm_plan_t plan, int kind, double alpha, int radiu
 vtm_status vtm_get_admittance(vtm_plan_t plan, double* W);
 
 /* vtm_set_opts -- replace the options of a plan (precision, limits, history).
- * VTM_EINVAL for a precision outside 0..2, a negative history_len, a history
+ * VTM_EINVAL for a precision outside 0..3, a negative history_len, a history
  * length without an array, or a sweep_kernel outside 0..8; the plan keeps its
  * previous options then. */
 vtm_status vtm_set_opts(vtm_plan_t plan, const vtm_opts* opts);

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libvtm.so")
 
 VTM_OK, VTM_EINVAL, VTM_ENOMEM, VTM_ESINGULAR, VTM_ENOCONV = 0, -1, -2, -3, -4
 VTM_EDIVERGED, VTM_ETIMEOUT, VTM_ECUDA, VTM_EINTERNAL, VTM_ENOTFACTORED = -5, -6, -7, -8, -9
-PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
+PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3}
 METHOD = {"vtm": 0, "bj": 1, "async": 2}
 ADMITTANCE = {"alpha": 0, "diag": 1, "wob": 2, "sca": 3, "line": 4}
 

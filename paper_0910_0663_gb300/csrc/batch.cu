@@ -394,6 +394,7 @@ constexpr int kKC = 16;  // inputs per chunk
 __device__ __forceinline__ float to_acc(float v) { return v; }
 __device__ __forceinline__ double to_acc(double v) { return v; }
 __device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_acc(__half v) { return __half2float(v); }
 
 // Residual terms of the previous sweep for the node runs that start in
 // [m0, m1) of the tile starting at port p0 (a run may reach past m1), per
@@ -945,7 +946,7 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
   info->relres = 0.0;
   info->first_sweep_converged = 0;
   double inner_tol = P->opts.inner_tol;
-  if (inner_tol <= 0) inner_tol = prec == VTM_PREC_FP32 ? 1e-5 : (prec == VTM_PREC_BF16 ? 3e-3 : 0.0);
+  if (inner_tol <= 0) inner_tol = default_inner_tol(prec);
   const int max_outer = prec == VTM_PREC_FP64 ? 4 : P->opts.max_outer;
   int sweeps_left = P->opts.max_sweeps;
   vtm_status result = VTM_ENOCONV;
@@ -1022,6 +1023,9 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
         else if (prec == VTM_PREC_BF16)
           go(batch_sweep_kernel<__nv_bfloat16, float, float>, 256, P->d_T16.as<__nv_bfloat16>(),
              P->d_bc.as<float>(), P->d_bstate.as<float>());
+        else if (prec == VTM_PREC_FP16)
+          go(batch_sweep_kernel<__half, float, float>, 256, P->d_T16.as<__half>(), P->d_bc.as<float>(),
+             P->d_bstate.as<float>());
         else if (prec == VTM_PREC_FP32)
           go(batch_sweep_kernel<float, float, float>, 256, P->d_T32.as<float>(), P->d_bc.as<float>(),
              P->d_bstate.as<float>());
@@ -1030,7 +1034,9 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
              P->d_bstate.as<double>());
       };
       // autotune the variant once per plan and precision (tensor cores: BF16
-      // with R % 8 == 0)
+      // with R % 8 == 0; the MMA rounds the waves to the operand type, which
+      // for FP16 could overflow on unscaled right-hand sides, so FP16 plans
+      // keep the CUDA-core sweep)
       int kv = 0;
       {
         if (P->batch_tuned[prec] == 0 || P->batch_tuned_R[prec] != R) {

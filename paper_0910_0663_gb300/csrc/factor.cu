@@ -358,20 +358,22 @@ __global__ void convert_f32_kernel(const double* __restrict__ a, float* __restri
     b[i] = (float)a[i];
 }
 
-__global__ void convert_bf16_kernel(const double* __restrict__ a, __nv_bfloat16* __restrict__ b,
-                                    int64_t n) {
+__device__ __forceinline__ void store_low(float* p, double v) { *p = (float)v; }
+__device__ __forceinline__ void store_low(__nv_bfloat16* p, double v) { *p = __float2bfloat16_rn((float)v); }
+__device__ __forceinline__ void store_low(__half* p, double v) { *p = __float2half_rn((float)v); }
+
+// the full (unpacked) 16-bit copy of the reflection matrices
+template <class H>
+__global__ void convert_16_kernel(const double* __restrict__ a, H* __restrict__ b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = __float2bfloat16_rn((float)a[i]);
+    store_low(b + i, a[i]);
 }
 
 // Packed symmetric copy of the reflection matrices (symmetric plans, scalar
 // W: T_P is symmetric, Sec. VIII).  The two stored halves of T_P differ only
 // by the rounding of their column solves; their mean is packed.
-__device__ __forceinline__ void store_low(float* p, double v) { *p = (float)v; }
-__device__ __forceinline__ void store_low(__nv_bfloat16* p, double v) {
-  *p = __float2bfloat16_rn((float)v);  // same rounding as the full BF16 copy
-}
+// (store_low above: the same rounding as the full 16-bit copies)
 
 template <class TT>
 __global__ void pack_sym_kernel(const double* __restrict__ T64, const TileDesc* __restrict__ tdesc,
@@ -438,7 +440,10 @@ vtm_status build_reflections(vtm_plan_s* P) {
     convert_f32_kernel<<<1216, 256, 0, s>>>(P->d_T64.as<double>(), P->d_T32.as<float>(), ne);
   } else if (P->opts.precision == VTM_PREC_BF16) {
     VTM_TRY(dev_alloc(P->d_T16, ne * sizeof(__nv_bfloat16)));
-    convert_bf16_kernel<<<1216, 256, 0, s>>>(P->d_T64.as<double>(), P->d_T16.as<__nv_bfloat16>(), ne);
+    convert_16_kernel<<<1216, 256, 0, s>>>(P->d_T64.as<double>(), P->d_T16.as<__nv_bfloat16>(), ne);
+  } else if (P->opts.precision == VTM_PREC_FP16) {
+    VTM_TRY(dev_alloc(P->d_T16, ne * sizeof(__half)));
+    convert_16_kernel<<<1216, 256, 0, s>>>(P->d_T64.as<double>(), P->d_T16.as<__half>(), ne);
   }
   if (packed_eligible(P)) {
     const int64_t np = std::max<int64_t>(P->Tp_elems, 8);
@@ -446,10 +451,14 @@ vtm_status build_reflections(vtm_plan_s* P) {
       VTM_TRY(dev_alloc(P->d_Tp32, np * sizeof(float)));
       pack_sym_kernel<float><<<P->nparts, 256, 0, s>>>(P->d_T64.as<double>(),
                                                        P->d_tdesc.as<TileDesc>(), P->d_Tp32.as<float>());
-    } else {
+    } else if (P->opts.precision == VTM_PREC_BF16) {
       VTM_TRY(dev_alloc(P->d_Tp16, np * sizeof(__nv_bfloat16)));
       pack_sym_kernel<__nv_bfloat16><<<P->nparts, 256, 0, s>>>(
           P->d_T64.as<double>(), P->d_tdesc.as<TileDesc>(), P->d_Tp16.as<__nv_bfloat16>());
+    } else {
+      VTM_TRY(dev_alloc(P->d_Tp16, np * sizeof(__half)));
+      pack_sym_kernel<__half><<<P->nparts, 256, 0, s>>>(P->d_T64.as<double>(), P->d_tdesc.as<TileDesc>(),
+                                                        P->d_Tp16.as<__half>());
     }
   }
   VTM_CUDA_TRY(cudaGetLastError());

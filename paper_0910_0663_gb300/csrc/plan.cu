@@ -767,7 +767,7 @@ static void fill_default_opts(vtm_opts* o) {
   if (o->max_sweeps <= 0) o->max_sweeps = 200000;
   if (o->check_every <= 0) o->check_every = 32;
   if (o->max_outer <= 0) o->max_outer = 40;
-  if (o->precision < 0 || o->precision > 2) o->precision = 0;
+  if (o->precision < 0 || o->precision > 3) o->precision = 0;
 }
 
 extern "C" vtm_status vtm_set_admittance(vtm_plan_t P, int kind, double alpha, int radius,
@@ -853,7 +853,7 @@ extern "C" vtm_status vtm_set_opts(vtm_plan_t P, const vtm_opts* opts) {
   if (!P) return VTM_EINVAL;
   vtm_opts o{};
   if (opts) o = *opts;
-  if (o.precision < 0 || o.precision > 2 || o.history_len < 0 || (o.history_len > 0 && !o.history)) {
+  if (o.precision < 0 || o.precision > 3 || o.history_len < 0 || (o.history_len > 0 && !o.history)) {
     set_detail("vtm_set_opts: bad precision or history");
     return VTM_EINVAL;
   }

@@ -260,6 +260,7 @@ int launch_residual(const int64_t* rowptr, const int32_t* col, const double* val
 __device__ __forceinline__ float load_t(const float* p) { return __ldg(p); }
 __device__ __forceinline__ double load_t(const double* p) { return __ldg(p); }
 __device__ __forceinline__ float load_t(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ float load_t(const __half* p) { return __half2float(*p); }
 
 template <class TT, class WT>
 __global__ void __launch_bounds__(256) sweep_kernel(
@@ -368,13 +369,13 @@ template <> struct VecLoad<float, 4> {
     o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
   }
 };
-template <> struct VecLoad<__nv_bfloat16, 8> {
-  __device__ static void load(const __nv_bfloat16* p, float (&o)[8]) {
+template <class H> struct VecLoad<H, 8> {  // 16-bit storage (BF16, FP16)
+  __device__ static void load(const H* p, float (&o)[8]) {
     uint4 v = *reinterpret_cast<const uint4*>(p);
-    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      float2 f = __bfloat1622float2(h[i]);
+      const float2 f = Pair16<H>::f2(w[i]);
       o[2 * i] = f.x;
       o[2 * i + 1] = f.y;
     }
@@ -590,14 +591,14 @@ template <> struct VecLoadG<float, 4> {
   __device__ static raw load(const float* p) { return __ldcs(reinterpret_cast<const float4*>(p)); }
   __device__ static void unpack(const raw& v, float (&o)[4]) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
 };
-template <> struct VecLoadG<__nv_bfloat16, 8> {
+template <class H> struct VecLoadG<H, 8> {  // 16-bit storage (BF16, FP16)
   using raw = uint4;
-  __device__ static raw load(const __nv_bfloat16* p) { return __ldcs(reinterpret_cast<const uint4*>(p)); }
+  __device__ static raw load(const H* p) { return __ldcs(reinterpret_cast<const uint4*>(p)); }
   __device__ static void unpack(const raw& v, float (&o)[8]) {
-    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      float2 f = __bfloat1622float2(h[i]);
+      const float2 f = Pair16<H>::f2(w[i]);
       o[2 * i] = f.x;
       o[2 * i + 1] = f.y;
     }
@@ -747,8 +748,18 @@ __global__ void __launch_bounds__(NT) sweep_vec_kernel(
 // shared memory issued before anything else (sweep_symb_kernel).
 // ---------------------------------------------------------------------------
 
+// 16-bit storage (BF16, FP16): lane l holds the 16 bytes number l (row l/2,
+// columns 8(l%2)..+7).
 template <class TT>
-struct SymLoad;
+struct SymLoad {
+  using raw = uint4;
+  __device__ static raw load(const TT* blk, int lane) {
+    return __ldg(reinterpret_cast<const uint4*>(blk) + lane);
+  }
+  __device__ static raw load_shared(const TT* blk, int lane) {
+    return reinterpret_cast<const uint4*>(blk)[lane];
+  }
+};
 // FP32: lane l holds float4 number l (row l/4, columns 4(l%4)..+3) and
 // number l + 32 (row l/4 + 8, same columns): each load instruction of the
 // warp covers 512 contiguous bytes (no shared-memory bank conflicts).
@@ -767,16 +778,6 @@ template <> struct SymLoad<float> {
     r.a = reinterpret_cast<const float4*>(blk)[lane];
     r.b = reinterpret_cast<const float4*>(blk)[lane + 32];
     return r;
-  }
-};
-// BF16: lane l holds the 16 bytes number l (row l/2, columns 8(l%2)..+7).
-template <> struct SymLoad<__nv_bfloat16> {
-  using raw = uint4;
-  __device__ static raw load(const __nv_bfloat16* blk, int lane) {
-    return __ldg(reinterpret_cast<const uint4*>(blk) + lane);
-  }
-  __device__ static raw load_shared(const __nv_bfloat16* blk, int lane) {
-    return reinterpret_cast<const uint4*>(blk)[lane];
   }
 };
 
@@ -880,16 +881,17 @@ __device__ __forceinline__ void sym_block(const SymLoad<float>::raw& v, int bi, 
   }
 }
 
-__device__ __forceinline__ void sym_block(const SymLoad<__nv_bfloat16>::raw& raw, int bi, int bj,
-                                          int nb, int lane, const float* w_in, float* part) {
+template <class H>
+__device__ __forceinline__ void sym_block16(const uint4& raw, int bi, int bj, int nb, int lane,
+                                            const float* w_in, float* part) {
   constexpr int B = kSymB;
   constexpr unsigned FULL = 0xffffffffu;
   float v[8];
   {
-    const __nv_bfloat162* hv = reinterpret_cast<const __nv_bfloat162*>(&raw);
+    const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const float2 f = __bfloat1622float2(hv[i]);
+      const float2 f = Pair16<H>::f2(w[i]);
       v[2 * i] = f.x;
       v[2 * i + 1] = f.y;
     }
@@ -936,6 +938,13 @@ __device__ __forceinline__ void sym_block(const SymLoad<__nv_bfloat16>::raw& raw
     const int jc = (b4 ? 4 : 0) + (b3 ? 2 : 0) + (b2 ? 1 : 0);
     if (!(lane & 2)) part[(bj * nb + bi) * B + h * 8 + jc] = t1;
   }
+}
+
+template <class TT>
+__device__ __forceinline__ void sym_apply(const typename SymLoad<TT>::raw& v, int bi, int bj, int nb,
+                                          int lane, const float* w_in, float* part) {
+  if constexpr (std::is_same<TT, float>::value) sym_block(v, bi, bj, nb, lane, w_in, part);
+  else sym_block16<TT>(v, bi, bj, nb, lane, w_in, part);
 }
 
 // w_out = c + sum of the row block's partials in block order; then the
@@ -1023,7 +1032,7 @@ __global__ void __launch_bounds__(NT, MINB) sweep_sym_kernel(
         const typename LD::raw v = buf[b];
         const int kn = kk + KB * NW;
         if (kn < nblk) buf[b] = LD::load(Tl + (size_t)kn * B * B, lane);
-        sym_block(v, bi, bi + off, nb, lane, w_in, part);
+        sym_apply<TT>(v, bi, bi + off, nb, lane, w_in, part);
         off += NW;
       }
     }
@@ -1100,7 +1109,7 @@ __global__ void __launch_bounds__(NT) sweep_symb_kernel(
       off -= nb - bi;
       ++bi;
     }
-    sym_block(LD::load_shared(tb + (size_t)kk * B * B, lane), bi, bi + off, nb, lane, w_in, part);
+    sym_apply<TT>(LD::load_shared(tb + (size_t)kk * B * B, lane), bi, bi + off, nb, lane, w_in, part);
     off += NW;
   }
   __syncthreads();
@@ -1223,7 +1232,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) sweep_flow_kernel(
             const typename LD::raw v = buf[b];
             const int kn = kk + KB * NW;
             if (kn < nblk) buf[b] = LD::load(Tl + (size_t)kn * B * B, lane);
-            sym_block(v, bi, bi + off, nb, lane, w_in, part);
+            sym_apply<TT>(v, bi, bi + off, nb, lane, w_in, part);
             off += NW;
           }
         }
@@ -1295,7 +1304,7 @@ static void launch_sweep(vtm_plan_s* P, const TT* T, const WT* c, WT* state, int
       hist_len, P->nparts);
 }
 
-// Scoped access-policy window on the plan's stream over the FP32/BF16
+// Scoped access-policy window on the plan's stream over the FP32/16-bit
 // reflection matrices: a persisting L2 carve-out of up to the device's
 // maximum is requested for this context and released (with the stream
 // attribute and the previous limit) when the sweeps end.
@@ -1389,7 +1398,7 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
                          256 * (size_t)vec * wsz + 128;
   const int nv_max = (P->max_ports + vec - 1) / vec;
   // auto: the FP64 sweep is bound by GB300's FP64 pipe, where the direct-load
-  // kernel does best; FP32/BF16 stream their matrices through the bulk-copy ring
+  // kernel does best; FP32/BF16/FP16 stream their matrices through the bulk-copy ring
   const int choice = P->opts.sweep_kernel
                          ? P->opts.sweep_kernel
                          : (prec == VTM_PREC_FP64 ? 1 : (nv_max <= 256 ? 3 : 2));
@@ -1397,10 +1406,23 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   // vector-load kernel: every thread owns one vector column (nv <= threads)
   const bool vecload = (choice == 3 && nv_max <= 256) || (choice == 4 && nv_max <= 128);
   const size_t vec_smem = 2 * (size_t)ld_max * wsz + 256 * (size_t)vec * wsz + 16;
-  // packed symmetric kernel (FP32/BF16 copies exist only for symmetric plans)
-  const bool sym_ok = prec == VTM_PREC_FP32   ? P->d_Tp32.p != nullptr
-                      : prec == VTM_PREC_BF16 ? P->d_Tp16.p != nullptr
+  // packed symmetric kernel (FP32/16-bit copies exist only for symmetric plans)
+  const bool sym_ok = prec == VTM_PREC_FP32 ? P->d_Tp32.p != nullptr
+                      : prec != VTM_PREC_FP64 ? P->d_Tp16.p != nullptr
                                               : false;
+  // the 16-bit storage type of a BF16 or FP16 plan, as a tag for the launches
+  auto with16 = [&](auto fn) {
+    if (prec == VTM_PREC_FP16) fn(__half{});
+    else fn(__nv_bfloat16{});
+  };
+  auto pick16 = [&](const void* bf16_kernel, const void* fp16_kernel) {
+    return prec == VTM_PREC_FP16 ? fp16_kernel : bf16_kernel;
+  };
+  const void* staged_kfn =
+      prec == VTM_PREC_FP64   ? (const void*)sweep_staged_kernel<double, double, 2, 4>
+      : prec == VTM_PREC_FP32 ? (const void*)sweep_staged_kernel<float, float, 4, 4>
+                              : pick16((const void*)sweep_staged_kernel<__nv_bfloat16, float, 8, 4>,
+                                       (const void*)sweep_staged_kernel<__half, float, 8, 4>);
   const int pp_max = std::max(kSymB, (P->max_ports + kSymB - 1) / kSymB * kSymB);
   const int nb_max = pp_max / kSymB;
   const size_t sym_smem = (2 * (size_t)pp_max + (size_t)nb_max * nb_max * kSymB) * sizeof(float) + 16;
@@ -1409,17 +1431,8 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   const size_t symb_smem = (size_t)tbuf_elems * (prec == VTM_PREC_FP32 ? 4 : 2) + sym_smem;
   const bool symb_ok = sym_ok && symb_smem <= 160 * 1024;
 
-  if (staged) {
-    if (prec == VTM_PREC_FP64)
-      VTM_CUDA_TRY(cudaFuncSetAttribute(sweep_staged_kernel<double, double, 2, 4>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st_smem));
-    else if (prec == VTM_PREC_FP32)
-      VTM_CUDA_TRY(cudaFuncSetAttribute(sweep_staged_kernel<float, float, 4, 4>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st_smem));
-    else
-      VTM_CUDA_TRY(cudaFuncSetAttribute(sweep_staged_kernel<__nv_bfloat16, float, 8, 4>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st_smem));
-  }
+  if (staged)
+    VTM_CUDA_TRY(cudaFuncSetAttribute(staged_kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st_smem));
   const int st_threads = 256;
   const int64_t npt_ = npt;
   int sms = 152;
@@ -1454,7 +1467,10 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
             tbuf_elems);
       };
       if (prec == VTM_PREC_FP32) go(sweep_symb_kernel<float, 128>, P->d_Tp32.as<float>());
-      else go(sweep_symb_kernel<__nv_bfloat16, 128>, P->d_Tp16.as<__nv_bfloat16>());
+      else with16([&](auto h) {
+        using H = decltype(h);
+        go(sweep_symb_kernel<H, 128>, P->d_Tp16.as<H>());
+      });
       return;
     }
     if (kc == 5 || kc == 6) {
@@ -1469,8 +1485,11 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
         if (kc == 5) go(sweep_sym_kernel<float, 128, 4, 6>, 128, P->d_Tp32.as<float>());
         else go(sweep_sym_kernel<float, 128, 4, 8>, 128, P->d_Tp32.as<float>());
       } else {
-        if (kc == 5) go(sweep_sym_kernel<__nv_bfloat16, 128, 8, 6>, 128, P->d_Tp16.as<__nv_bfloat16>());
-        else go(sweep_sym_kernel<__nv_bfloat16, 128, 8, 8>, 128, P->d_Tp16.as<__nv_bfloat16>());
+        with16([&](auto h) {
+          using H = decltype(h);
+          if (kc == 5) go(sweep_sym_kernel<H, 128, 8, 6>, 128, P->d_Tp16.as<H>());
+          else go(sweep_sym_kernel<H, 128, 8, 8>, 128, P->d_Tp16.as<H>());
+        });
       }
       return;
     }
@@ -1490,8 +1509,11 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
       launch_vec(sweep_vec_kernel<float, float, 4, NT, KB>, NT, P->d_T32.as<float>(),           \
                  P->d_c32.as<float>(), P->d_state32.as<float>());                               \
     else                                                                                        \
-      launch_vec(sweep_vec_kernel<__nv_bfloat16, float, 8, NT, KB>, NT,                         \
-                 P->d_T16.as<__nv_bfloat16>(), P->d_c32.as<float>(), P->d_state32.as<float>()); \
+      with16([&](auto h) {                                                                      \
+        using H = decltype(h);                                                                  \
+        launch_vec(sweep_vec_kernel<H, float, 8, NT, KB>, NT, P->d_T16.as<H>(),                 \
+                   P->d_c32.as<float>(), P->d_state32.as<float>());                             \
+      });                                                                                       \
   } while (0)
       if (kc == 3) VTM_VEC_LAUNCH(256, 8);
       else VTM_VEC_LAUNCH(128, 4);
@@ -1506,8 +1528,11 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
         launch_staged(sweep_staged_kernel<float, float, 4, 4>, P->d_T32.as<float>(),
                       P->d_c32.as<float>(), P->d_state32.as<float>());
       else
-        launch_staged(sweep_staged_kernel<__nv_bfloat16, float, 8, 4>, P->d_T16.as<__nv_bfloat16>(),
-                      P->d_c32.as<float>(), P->d_state32.as<float>());
+        with16([&](auto h) {
+          using H = decltype(h);
+          launch_staged(sweep_staged_kernel<H, float, 8, 4>, P->d_T16.as<H>(), P->d_c32.as<float>(),
+                        P->d_state32.as<float>());
+        });
       return;
     }
     if (prec == VTM_PREC_FP64)
@@ -1517,8 +1542,11 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
       launch_sweep<float, float>(P, P->d_T32.as<float>(), P->d_c32.as<float>(),
                                  P->d_state32.as<float>(), threads, smem, hist, hist_len);
     else
-      launch_sweep<__nv_bfloat16, float>(P, P->d_T16.as<__nv_bfloat16>(), P->d_c32.as<float>(),
-                                         P->d_state32.as<float>(), threads, smem, hist, hist_len);
+      with16([&](auto h) {
+        using H = decltype(h);
+        launch_sweep<H, float>(P, P->d_T16.as<H>(), P->d_c32.as<float>(), P->d_state32.as<float>(), threads,
+                               smem, hist, hist_len);
+      });
   };
   // Autotuner: on the first solve of this precision, time every kernel that
   // fits on this plan's tiles (a few sweeps each, from a zero state that is
@@ -1529,8 +1557,10 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   if (sym_ok) {
     int coop = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, P->device);
-    const void* kfn = prec == VTM_PREC_FP32 ? (const void*)sweep_flow_kernel<float, 128, 4, false>
-                                            : (const void*)sweep_flow_kernel<__nv_bfloat16, 128, 8, false>;
+    const void* kfn = prec == VTM_PREC_FP32
+                          ? (const void*)sweep_flow_kernel<float, 128, 4, false>
+                          : pick16((const void*)sweep_flow_kernel<__nv_bfloat16, 128, 8, false>,
+                                   (const void*)sweep_flow_kernel<__half, 128, 8, false>);
     int per_sm = 0;
     if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 128, sym_smem) == cudaSuccess &&
         per_sm > 0)
@@ -1572,21 +1602,24 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
         prec == VTM_PREC_FP32
             ? (async ? (const void*)sweep_flow_kernel<float, 128, 4, true>
                      : (const void*)sweep_flow_kernel<float, 128, 4, false>)
-            : (async ? (const void*)sweep_flow_kernel<__nv_bfloat16, 128, 8, true>
-                     : (const void*)sweep_flow_kernel<__nv_bfloat16, 128, 8, false>);
+            : (async ? pick16((const void*)sweep_flow_kernel<__nv_bfloat16, 128, 8, true>,
+                              (const void*)sweep_flow_kernel<__half, 128, 8, true>)
+                     : pick16((const void*)sweep_flow_kernel<__nv_bfloat16, 128, 8, false>,
+                              (const void*)sweep_flow_kernel<__half, 128, 8, false>));
     return cudaLaunchCooperativeKernel(kfn, flow_grid, 128, args, sym_smem, s);
   };
   const bool symload = ((choice == 5 || choice == 6) && sym_ok) || (choice == 7 && symb_ok) ||
                        (choice == 8 && flow_ok);
   if (P->opts.method == VTM_METHOD_ASYNC && !flow_ok) {
     set_detail("vtm_solve: asynchronous VTM runs on the packed symmetric dataflow kernel: it needs "
-               "FP32/BF16 sweeps of a symmetric plan with at most 256 ports per sub-circuit");
+               "FP32/BF16/FP16 sweeps of a symmetric plan with at most 256 ports per sub-circuit");
     return VTM_EINVAL;
   }
   if (symb_ok) {
     VTM_CUDA_TRY(cudaFuncSetAttribute(prec == VTM_PREC_FP32
                                           ? (const void*)sweep_symb_kernel<float, 128>
-                                          : (const void*)sweep_symb_kernel<__nv_bfloat16, 128>,
+                                          : pick16((const void*)sweep_symb_kernel<__nv_bfloat16, 128>,
+                                                   (const void*)sweep_symb_kernel<__half, 128>),
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)symb_smem));
   }
 
@@ -1629,11 +1662,8 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
           continue;
         }
         if (cand == 2)
-          VTM_CUDA_TRY(cudaFuncSetAttribute(
-              prec == VTM_PREC_FP64 ? (const void*)sweep_staged_kernel<double, double, 2, 4>
-              : prec == VTM_PREC_FP32 ? (const void*)sweep_staged_kernel<float, float, 4, 4>
-                                      : (const void*)sweep_staged_kernel<__nv_bfloat16, float, 8, 4>,
-              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st_smem));
+          VTM_CUDA_TRY(
+              cudaFuncSetAttribute(staged_kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st_smem));
         SweepCtrl t = h;
         t.k_max = 1 << 30;
         t.tol2 = -1.0;  // never converges while timing
@@ -1666,18 +1696,11 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
     }
     kern = P->tuned_kernel[prec];
     if (kern == 2)
-      VTM_CUDA_TRY(cudaFuncSetAttribute(
-          prec == VTM_PREC_FP64 ? (const void*)sweep_staged_kernel<double, double, 2, 4>
-          : prec == VTM_PREC_FP32 ? (const void*)sweep_staged_kernel<float, float, 4, 4>
-                                  : (const void*)sweep_staged_kernel<__nv_bfloat16, float, 8, 4>,
-          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st_smem));
+      VTM_CUDA_TRY(cudaFuncSetAttribute(staged_kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st_smem));
   }
   if (kern == 2 && !st_grid) {  // occupancy query before any capture
-    const void* kfn = prec == VTM_PREC_FP64 ? (const void*)sweep_staged_kernel<double, double, 2, 4>
-                      : prec == VTM_PREC_FP32 ? (const void*)sweep_staged_kernel<float, float, 4, 4>
-                                              : (const void*)sweep_staged_kernel<__nv_bfloat16, float, 8, 4>;
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, st_threads, st_smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, staged_kfn, st_threads, st_smem);
     st_grid = std::max(1, std::min(P->nparts, std::max(per_sm, 1) * sms));
   }
   if (kern == 8) {
@@ -1836,7 +1859,7 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
   // (two steps reach 1e-10), BF16 sweeps two and a half (measured: 3e-3 takes
   // one step less than 1e-2 on the power grid and the thermal grid).
   double inner_tol = P->opts.inner_tol;
-  if (inner_tol <= 0) inner_tol = prec == VTM_PREC_FP32 ? 1e-5 : (prec == VTM_PREC_BF16 ? 3e-3 : 0.0);
+  if (inner_tol <= 0) inner_tol = default_inner_tol(prec);
   const int max_outer = (prec == VTM_PREC_FP64 || P->general) ? 4 : P->opts.max_outer;
   int sweeps_left = P->opts.max_sweeps;
   vtm_status result = VTM_ENOCONV;
@@ -1917,7 +1940,7 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
       // steps recover in FP32; FP32 steps gain five digits and recover in FP64.
       P->launch_count += 2;
       const float* slot32 = static_cast<const float*>(P->wave_slot);
-      recovered_f32 = prec == VTM_PREC_BF16 && x0_f32;
+      recovered_f32 = (prec == VTM_PREC_BF16 || prec == VTM_PREC_FP16) && x0_f32;
       if (recovered_f32) {
         gather_perm_f32_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, P->d_v32.as<float>(), n);
         inject_kernel<float, float><<<g2, 256, 0, s>>>(P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(),

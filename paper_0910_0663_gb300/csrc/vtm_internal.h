@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include <string>
@@ -63,6 +64,35 @@ struct __align__(16) TileDesc {
   int64_t T_off;
   int64_t Tp_off;  // packed symmetric form: first element of the tile's 16x16 blocks
 };
+
+// Two 16-bit storage types of the reflection matrices (BF16, FP16): a packed
+// pair of them as two floats.
+template <class H>
+struct Pair16;
+template <>
+struct Pair16<__nv_bfloat16> {
+  __device__ static float2 f2(uint32_t w) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+  }
+  __device__ static float f(__nv_bfloat16 v) { return __bfloat162float(v); }
+};
+template <>
+struct Pair16<__half> {
+  __device__ static float2 f2(uint32_t w) { return __half22float2(*reinterpret_cast<const __half2*>(&w)); }
+  __device__ static float f(__half v) { return __half2float(v); }
+};
+
+// Relative residual at which an inner low-precision solve hands back to the
+// FP64 refinement: a few units of the storage type's rounding of T_P (FP32
+// 2^-24, FP16 2^-11, BF16 2^-8 relative), where its sweeps stop gaining.
+inline double default_inner_tol(int precision) {
+  switch (precision) {
+    case VTM_PREC_FP32: return 1e-5;
+    case VTM_PREC_FP16: return 1e-3;
+    case VTM_PREC_BF16: return 3e-3;
+    default: return 0.0;
+  }
+}
 
 // Packed symmetric reflection matrices: T_P padded to pp = 16 ceil(p/16),
 // cut into 16x16 blocks, of which the upper triangle (bi <= bj) is stored,
@@ -182,10 +212,10 @@ struct vtm_plan_s {
   vtm::SweepCtrl* h_ctrl = nullptr;        // pinned mirror
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evs0 = nullptr, evs1 = nullptr;
   // sweep-kernel autotuning and graphs, per precision
-  int tuned_kernel[3] = {0, 0, 0};
-  float tuned_ms[3] = {0.f, 0.f, 0.f};
-  vtm::SweepGraph sweep_graph[3];
-  vtm::SweepGraph batch_graph[3];
+  int tuned_kernel[4] = {0, 0, 0, 0};
+  float tuned_ms[4] = {0.f, 0.f, 0.f, 0.f};
+  vtm::SweepGraph sweep_graph[4];
+  vtm::SweepGraph batch_graph[4];
   // per-call accounting (reset by each solve)
   int launch_count = 0;
   int sweep_launch_count = 0;
@@ -222,8 +252,8 @@ struct vtm_plan_s {
   vtm::DevBuf d_item_tile, d_item_m0, d_item_order, d_bV, d_bV32, d_bstate, d_bc, d_bpart, d_btol2,
       d_bctrl, d_bres;
   bool bres_init = false;
-  int batch_tuned[3] = {0, 0, 0};    // batched sweep variant + 1, per precision
-  int batch_tuned_R[3] = {0, 0, 0};  // right-hand sides it was tuned for
+  int batch_tuned[4] = {0, 0, 0, 0};  // batched sweep variant + 1, per precision
+  int batch_tuned_R[4] = {0, 0, 0, 0};  // right-hand sides it was tuned for
   int batch_grid[16] = {0};          // grid per (precision, variant)
 
   // adjoint of an unsymmetric system

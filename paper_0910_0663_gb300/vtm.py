@@ -26,7 +26,7 @@ class Plan:
     indptr/indices/data: CSR of A (int64 / int32 / float64); partition: node
     -> sub-circuit (int32); Zc: characteristic impedance of the virtual lines
     (W = 1/Zc).  ``precision`` selects the arithmetic of the sweeps:
-    "fp64", or "fp32"/"bf16" inside FP64 iterative refinement.
+    "fp64", or "fp32"/"bf16"/"fp16" inside FP64 iterative refinement.
     """
 
     def __init__(self, indptr, indices, data, partition, nparts, Zc=1.0, precision="fp64",

@@ -27,7 +27,8 @@ def vtm():
     return V
 
 
-@pytest.mark.parametrize("precision,shape", [("fp32", (256, 32)), ("fp32", (192, 48)), ("bf16", (256, 32))])
+@pytest.mark.parametrize("precision,shape", [("fp32", (256, 32)), ("fp32", (192, 48)), ("bf16", (256, 32)),
+                                                 ("fp16", (256, 32))])
 def test_async_vtm_reaches_the_direct_solution(vtm, precision, shape):
     n, t = shape
     w = wl.power_grid(n, n, t, t, Zc=1.0, seed=71)

@@ -57,7 +57,7 @@ def test_batched_equals_column_by_column_at_equal_sweeps(vtm):
         assert torch.allclose(xr, xb[r], rtol=1e-12, atol=1e-14 * float(xb[r].abs().max()))
 
 
-@pytest.mark.parametrize("precision,nrhs", [("bf16", 16), ("fp32", 5), ("bf16", 6)])
+@pytest.mark.parametrize("precision,nrhs", [("bf16", 16), ("fp32", 5), ("bf16", 6), ("fp16", 16)])
 def test_batched_low_precision_reaches_tolerance(vtm, precision, nrhs):
     w = _thermal_small(nrhs, seed=3)
     A = w.csr()

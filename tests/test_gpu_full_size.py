@@ -31,7 +31,7 @@ def power_grid():
     return w, w.csr()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
 def test_power_grid_2048_as_benchmarked(vtm, power_grid, precision):
     w, A = power_grid
     s = torch.cuda.Stream()

@@ -135,7 +135,7 @@ def test_fixed_point_is_direct_solution(vtm):
     assert np.abs(x.cpu().numpy() - x_star).max() <= 1e-9 * np.abs(x_star).max()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
 def test_mixed_precision_reaches_fp64_tolerance(vtm, precision):
     w = wl.power_grid(256, 256, 32, 32, Zc=1.0, seed=4)
     plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc, precision=precision)
@@ -232,7 +232,9 @@ def test_every_sweep_kernel_matches_oracle(vtm, kernel):
                                                     ("fp32", 7, (90, 18)), ("fp32", 7, (192, 48)),
                                                     ("bf16", 5, (192, 48)), ("bf16", 6, (90, 18)),
                                                     ("bf16", 7, (192, 48)), ("fp32", 8, (90, 18)),
-                                                    ("fp32", 8, (192, 48)), ("bf16", 8, (90, 18))])
+                                                    ("fp32", 8, (192, 48)), ("bf16", 8, (90, 18)),
+                                                    ("fp16", 5, (192, 48)), ("fp16", 6, (90, 18)),
+                                                    ("fp16", 7, (90, 18)), ("fp16", 8, (192, 48))])
 def test_packed_symmetric_sweeps_follow_the_oracle(vtm, precision, kernel, shape):
     # T_P is symmetric (scalar W, symmetric A): the packed kernels read the
     # 16x16 blocks on and above the diagonal only.  18x18 tiles have 72, 54 or
@@ -252,14 +254,14 @@ def test_packed_symmetric_sweeps_follow_the_oracle(vtm, precision, kernel, shape
     ref = O.vtm_midpoint(A, w.partition, w.nparts, w.b[:1], W=1 / w.Zc, tol=0, max_sweeps=40)
     h, href = plan.history, ref.history[:, 0]
     # BF16 entries carry 2^-9 relative rounding, which shifts the slow modes:
-    # compare the first 15 sweeps only
-    rtol, floor, kmax = (1e-3, 1e-4, 40) if precision == "fp32" else (5e-2, 2e-2, 15)
+    # compare the first 15 sweeps only; FP16 (2^-11) follows longer
+    rtol, floor, kmax = {"fp32": (1e-3, 1e-4, 40), "fp16": (2e-2, 5e-3, 20), "bf16": (5e-2, 2e-2, 15)}[precision]
     k = min(kmax, int(np.count_nonzero((h > 0) & (href[: len(h)] > floor))))
     assert k >= 5
     assert np.allclose(h[:k], href[:k], rtol=rtol, atol=0)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
 def test_dataflow_sweeps_repeat_the_launch_per_sweep_kernel_bitwise(vtm, precision):
     # one cooperative launch with per-tile neighbour waits computes the same
     # iterates as one launch per sweep (same block arithmetic, same fixed-order
@@ -285,8 +287,9 @@ def test_bad_options_are_rejected_and_the_plan_keeps_its_own(vtm):
         plan.set_options(sweep_kernel=9)
     with pytest.raises(vtm.VTMError):
         plan.set_options(sweep_kernel=-1)
-    with pytest.raises(vtm.VTMError):
-        plan.set_options(precision=5)
+    for bad in (4, 5, -1):
+        with pytest.raises(vtm.VTMError):
+            plan.set_options(precision=bad)
     x, info = plan.solve(torch.from_numpy(w.b[0]).cuda(), tol=1e-10)
     assert O.residual_norms(w.csr(), x.cpu().numpy()[None], w.b[:1]).max() <= 1e-10
 
