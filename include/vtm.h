@@ -117,10 +117,17 @@ typedef struct {
                         into shared memory by one bulk copy; 8: the same blocks in one
                         cooperative launch per inner solve, each tile starting sweep k
                         once the tiles across its lines have finished sweep k - 1 (no
-                        kernel boundary per sweep; same iterates as 5); elsewhere 5-8
-                        fall back to kernel 1 */
+                        kernel boundary per sweep; same iterates as 5); 9: the same
+                        blocks with one warp per tile (8 tiles per CTA, no CTA barrier
+                        inside a tile, every tile of a few-thousand-tile plan resident
+                        at once; same iterates as 5); elsewhere 5-9 fall back to
+                        kernel 1 */
   int graphs;        /* 0 (default): replay batches of check_every sweep launches from a
                         CUDA graph when the plan has its own stream; 1: plain launches */
+  int pdl;           /* 0 (default): the packed sweeps (kernels 5-7) are launched as
+                        programmatic dependents of the sweep before them, so each tile
+                        loads its reflection blocks and port data while the previous
+                        sweep finishes, and reads the waves only once it has; 1: off */
   double* history;   /* optional host array: relative (interface) residual after each
                         sweep k=1..history_len of the first column; NULL = not recorded */
   int history_len;
@@ -211,7 +218,7 @@ vtm_status vtm_get_admittance(vtm_plan_t plan, double* W);
 
 /* vtm_set_opts -- replace the options of a plan (precision, limits, history).
  * VTM_EINVAL for a precision outside 0..3, a negative history_len, a history
- * length without an array, or a sweep_kernel outside 0..8; the plan keeps its
+ * length without an array, or a sweep_kernel outside 0..9; the plan keeps its
  * previous options then. */
 vtm_status vtm_set_opts(vtm_plan_t plan, const vtm_opts* opts);
 

@@ -30,6 +30,7 @@ class vtm_opts(ctypes.Structure):
                 ("max_outer", ctypes.c_int), ("method", ctypes.c_int), ("batch", ctypes.c_int),
                 ("batch_solve", ctypes.c_int),
                 ("l2_persist", ctypes.c_int), ("sweep_kernel", ctypes.c_int), ("graphs", ctypes.c_int),
+                ("pdl", ctypes.c_int),
                 ("history", ctypes.POINTER(ctypes.c_double)),
                 ("history_len", ctypes.c_int)]
 
@@ -134,7 +135,7 @@ def _check(status, where):
 
 def make_opts(precision="fp64", max_sweeps=0, check_every=0, inner_tol=0.0, max_outer=0,
               history=None, sweep_kernel=0, method="vtm", batch=0, l2_persist=0, graphs=0,
-              batch_solve=0):
+              batch_solve=0, pdl=0):
     o = vtm_opts()
     o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
     o.max_sweeps = max_sweeps
@@ -146,6 +147,7 @@ def make_opts(precision="fp64", max_sweeps=0, check_every=0, inner_tol=0.0, max_
     o.batch = int(batch)
     o.l2_persist = int(l2_persist)
     o.graphs = int(graphs)
+    o.pdl = int(pdl)
     o.batch_solve = int(batch_solve)
     if history is not None:
         assert history.dtype == np.float64 and history.flags["C_CONTIGUOUS"]

@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <cmath>
 #include <type_traits>
+#include <utility>
 
 #include "ptx.h"
 #include "vtm_internal.h"
@@ -108,13 +109,16 @@ __global__ void inject_kernel(const int32_t* __restrict__ port_pos, const uint8_
 // Fixed-order sum of `count` doubles by one block (result valid in thread 0).
 // Loads go out 16 at a time (the sum runs at the end of every sweep, on one
 // CTA, so its latency is on the critical path); each thread still adds its
-// elements in increasing index order.
+// elements in increasing index order.  With NT > 0 the first NT threads do
+// the sum (the order of an NT-thread block); all threads reach the barriers.
+template <int NT = 0>
 __device__ double block_sum_fixed(const double* __restrict__ a, int64_t count) {
   __shared__ double red[32];
   constexpr int kMLP = 16;
   double acc = 0.0;
-  const int64_t stride = blockDim.x;
-  for (int64_t base = threadIdx.x; base < count; base += kMLP * stride) {
+  const int nt = NT > 0 ? NT : (int)blockDim.x;
+  const int64_t stride = nt;
+  for (int64_t base = threadIdx.x; (int)threadIdx.x < nt && base < count; base += kMLP * stride) {
     double v[kMLP];
 #pragma unroll
     for (int j = 0; j < kMLP; ++j) {
@@ -131,7 +135,7 @@ __device__ double block_sum_fixed(const double* __restrict__ a, int64_t count) {
   __syncthreads();
   double tot = 0.0;
   if (threadIdx.x == 0)
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += red[i];
+    for (int i = 0; i < (nt >> 5); ++i) tot += red[i];
   __syncthreads();
   return tot;
 }
@@ -782,30 +786,53 @@ template <> struct SymLoad<float> {
 };
 
 // Per-port inputs that do not depend on the sweep index, loaded at kernel
-// start by thread tid for ports tid + j NT (p <= 256).
+// start by thread tid for ports tid + j NT (p <= 256): the plan's own tables
+// (twin, residual coefficients, node runs), fixed since vtm_factor, and c of
+// the current inner solve.
 template <int NT>
 struct SymPorts {
   static constexpr int PPT = 16 * kSymB / NT;
   int tw[PPT], rn[PPT];
   float2 kq[PPT];
   float cq[PPT];
-  __device__ void load(const int32_t* __restrict__ twin, const float2* __restrict__ kd,
-                       const uint8_t* __restrict__ run, const float* __restrict__ c, int p0, int p) {
+  __device__ void load_tables(const int32_t* __restrict__ twin, const float2* __restrict__ kd,
+                              const uint8_t* __restrict__ run, int p0, int p) {
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
       const int s = threadIdx.x + j * NT;
       tw[j] = rn[j] = 0;
       kq[j] = make_float2(0.f, 0.f);
-      cq[j] = 0.f;
       if (s < p) {
         tw[j] = twin[p0 + s];
         kq[j] = kd[p0 + s];
-        cq[j] = c[p0 + s];
         rn[j] = run[p0 + s];
       }
     }
   }
+  __device__ void load_c(const float* __restrict__ c, int p0, int p) {
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+      const int s = threadIdx.x + j * NT;
+      cq[j] = s < p ? c[p0 + s] : 0.f;
+    }
+  }
+  __device__ void load(const int32_t* __restrict__ twin, const float2* __restrict__ kd,
+                       const uint8_t* __restrict__ run, const float* __restrict__ c, int p0, int p) {
+    load_tables(twin, kd, run, p0, p);
+    load_c(c, p0, p);
+  }
 };
+
+// Programmatic dependent launch (sm_90+): a sweep launched with the
+// programmatic-serialization attribute may start while the sweep before it
+// finishes.  Before pdl_wait it reads only what no kernel of the solve
+// writes (the reflection blocks, the plan's tables); pdl_wait returns once
+// the previous grid has completed and its writes are visible.  Without the
+// attribute both are no-ops.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // Incident waves of the tile (zero past p, the padding of the last block)
 // and this thread's share of the squared node residuals of sweep k - 1.
@@ -843,10 +870,26 @@ __device__ __forceinline__ float sym_gather(const SymPorts<NT>& pt, const float*
   return sq;
 }
 
+// Where a block's partial goes: sink(a, b, i, v) receives element i of block
+// b's contribution to row block a.  PartSink stores it for a later fixed-order
+// sum over b (several warps per tile); AccSink adds it at once to output a B
+// + i (one warp per tile, blocks in row-major order, so each output still
+// sums c, then b = 0, 1, ..., nb - 1: the same order as PartSink's sum).
+struct PartSink {
+  float* part;
+  int nb;
+  __device__ void operator()(int a, int b, int i, float v) const { part[(a * nb + b) * kSymB + i] = v; }
+};
+struct AccSink {
+  float* acc;
+  __device__ void operator()(int a, int, int i, float v) const { acc[a * kSymB + i] += v; }
+};
+
 // One 16x16 block (bi, bj) of a warp: the row-block partial T_blk w(bj) and,
 // off the diagonal, the column-block partial T_blk^T w(bi) (see above).
-__device__ __forceinline__ void sym_block(const SymLoad<float>::raw& v, int bi, int bj, int nb,
-                                          int lane, const float* w_in, float* part) {
+template <class Sink>
+__device__ __forceinline__ void sym_block(const SymLoad<float>::raw& v, int bi, int bj, int lane,
+                                          const float* w_in, const Sink& sink) {
   constexpr int B = kSymB;
   constexpr unsigned FULL = 0xffffffffu;
   const int r1 = lane >> 2, cg = lane & 3;
@@ -863,7 +906,7 @@ __device__ __forceinline__ void sym_block(const SymLoad<float>::raw& v, int bi, 
   const bool b0 = lane & 1;
   float t = (b0 ? a2 : a1) + __shfl_xor_sync(FULL, b0 ? a1 : a2, 1);
   t += __shfl_xor_sync(FULL, t, 2);
-  if (!(lane & 2)) part[(bi * nb + bj) * B + (b0 ? r1 + 8 : r1)] = t;
+  if (!(lane & 2)) sink(bi, bj, b0 ? r1 + 8 : r1, t);
   if (bi != bj) {
     const float wr1 = w_in[bi * B + r1], wr2 = w_in[bi * B + r1 + 8];
     const float u0 = fmaf(v.b.x, wr2, v.a.x * wr1);
@@ -877,13 +920,13 @@ __device__ __forceinline__ void sym_block(const SymLoad<float>::raw& v, int bi, 
     k1 += __shfl_xor_sync(FULL, b4 ? u1 : u3, 16);
     float t1 = (b3 ? k1 : k0) + __shfl_xor_sync(FULL, b3 ? k0 : k1, 8);
     t1 += __shfl_xor_sync(FULL, t1, 4);
-    if (!(lane & 4)) part[(bj * nb + bi) * B + cg * 4 + (b4 ? 2 : 0) + (b3 ? 1 : 0)] = t1;
+    if (!(lane & 4)) sink(bj, bi, cg * 4 + (b4 ? 2 : 0) + (b3 ? 1 : 0), t1);
   }
 }
 
-template <class H>
-__device__ __forceinline__ void sym_block16(const uint4& raw, int bi, int bj, int nb, int lane,
-                                            const float* w_in, float* part) {
+template <class H, class Sink>
+__device__ __forceinline__ void sym_block16(const uint4& raw, int bi, int bj, int lane, const float* w_in,
+                                            const Sink& sink) {
   constexpr int B = kSymB;
   constexpr unsigned FULL = 0xffffffffu;
   float v[8];
@@ -908,7 +951,7 @@ __device__ __forceinline__ void sym_block16(const uint4& raw, int bi, int bj, in
   a = fmaf(v[6], c1.z, a);
   a = fmaf(v[7], c1.w, a);
   a += __shfl_xor_sync(FULL, a, 1);
-  if (h == 0) part[(bi * nb + bj) * B + r] = a;
+  if (h == 0) sink(bi, bj, r, a);
   if (bi != bj) {
     const float wr = w_in[bi * B + r];
     float u[8];
@@ -936,15 +979,15 @@ __device__ __forceinline__ void sym_block16(const uint4& raw, int bi, int bj, in
     }
     t1 += __shfl_xor_sync(FULL, t1, 2);
     const int jc = (b4 ? 4 : 0) + (b3 ? 2 : 0) + (b2 ? 1 : 0);
-    if (!(lane & 2)) part[(bj * nb + bi) * B + h * 8 + jc] = t1;
+    if (!(lane & 2)) sink(bj, bi, h * 8 + jc, t1);
   }
 }
 
-template <class TT>
-__device__ __forceinline__ void sym_apply(const typename SymLoad<TT>::raw& v, int bi, int bj, int nb,
-                                          int lane, const float* w_in, float* part) {
-  if constexpr (std::is_same<TT, float>::value) sym_block(v, bi, bj, nb, lane, w_in, part);
-  else sym_block16<TT>(v, bi, bj, nb, lane, w_in, part);
+template <class TT, class Sink = PartSink>
+__device__ __forceinline__ void sym_apply(const typename SymLoad<TT>::raw& v, int bi, int bj, int lane,
+                                          const float* w_in, const Sink& sink) {
+  if constexpr (std::is_same<TT, float>::value) sym_block(v, bi, bj, lane, w_in, sink);
+  else sym_block16<TT>(v, bi, bj, lane, w_in, sink);
 }
 
 // w_out = c + sum of the row block's partials in block order; then the
@@ -1008,7 +1051,10 @@ __global__ void __launch_bounds__(NT, MINB) sweep_sym_kernel(
     if (kk < nblk) buf[b] = LD::load(Tl + (size_t)kk * B * B, lane);
   }
   SymPorts<NT> pt;
-  pt.load(twin, kd, run, c, p0, p);
+  pt.load_tables(twin, kd, run, p0, p);
+  pdl_launch_dependents();
+  pdl_wait();  // the previous sweep's waves, decision and counters
+  pt.load_c(c, p0, p);
   if (tid == 0) {
     s_k = *((volatile int*)&ctrl->k);
     s_flag = *((volatile int*)&ctrl->flag);
@@ -1032,7 +1078,7 @@ __global__ void __launch_bounds__(NT, MINB) sweep_sym_kernel(
         const typename LD::raw v = buf[b];
         const int kn = kk + KB * NW;
         if (kn < nblk) buf[b] = LD::load(Tl + (size_t)kn * B * B, lane);
-        sym_apply<TT>(v, bi, bi + off, nb, lane, w_in, part);
+        sym_apply<TT>(v, bi, bi + off, lane, w_in, PartSink{part, nb});
         off += NW;
       }
     }
@@ -1048,6 +1094,10 @@ __global__ void __launch_bounds__(NT, MINB) sweep_sym_kernel(
 // first; the wave gather and the residual run while it is in flight.  The
 // wait is bounded: on timeout the CTA waits (bounded) for its copy, sets flag
 // 5 and leaves the sweep unfinished, which the host reports as VTM_ETIMEOUT.
+// The copy is skipped when the flag already reads set; read before pdl_wait
+// the flag may still be clear for the one launch after the stop (set flags
+// stay set within a batch), and that launch then waits for its copy and
+// returns.
 template <class TT, int NT>
 __global__ void __launch_bounds__(NT) sweep_symb_kernel(
     const TT* __restrict__ Tp, const TileDesc* __restrict__ tdesc,
@@ -1075,7 +1125,6 @@ __global__ void __launch_bounds__(NT) sweep_symb_kernel(
   const uint32_t bytes = (uint32_t)nblk * B * B * sizeof(TT);
   if (tid == 0) {
     // launches past the end of the solve copy nothing
-    s_k = *((volatile int*)&ctrl->k);
     s_flag = *((volatile int*)&ctrl->flag);
     s_timeout = 0;
     if (!s_flag && bytes) {
@@ -1086,9 +1135,21 @@ __global__ void __launch_bounds__(NT) sweep_symb_kernel(
     }
   }
   SymPorts<NT> pt;
-  pt.load(twin, kd, run, c, p0, p);
+  pt.load_tables(twin, kd, run, p0, p);
+  pdl_launch_dependents();
   __syncthreads();
-  if (s_flag) return;
+  if (s_flag) return;  // no copy was issued
+  pdl_wait();  // the previous sweep's waves, decision and counters
+  pt.load_c(c, p0, p);
+  if (tid == 0) {
+    s_k = *((volatile int*)&ctrl->k);
+    s_flag = *((volatile int*)&ctrl->flag);
+  }
+  __syncthreads();
+  if (s_flag) {
+    if (tid == 0 && bytes) mbar_wait_bounded(&bar, 0, kWaitPolls);  // the copy lands before the CTA ends
+    return;
+  }
   const int k = s_k;
   const float* prev = state + (size_t)((k - 1) & 1) * nports * 2;
   float* cur = state + (size_t)(k & 1) * nports * 2;
@@ -1109,12 +1170,165 @@ __global__ void __launch_bounds__(NT) sweep_symb_kernel(
       off -= nb - bi;
       ++bi;
     }
-    sym_apply<TT>(LD::load_shared(tb + (size_t)kk * B * B, lane), bi, bi + off, nb, lane, w_in, part);
+    sym_apply<TT>(LD::load_shared(tb + (size_t)kk * B * B, lane), bi, bi + off, lane, w_in,
+                  PartSink{part, nb});
     off += NW;
   }
   __syncthreads();
   sym_finish<NT>(pt, part, w_in, cur, p0, p, nb, tile, tile_sq, k, ctrl, partials, hist, hist_len,
                  nparts, &s_last);
+}
+
+// blocks in flight per warp of sweep_wsym_kernel (registers: 4 per block for
+// 16-bit entries, 8 for FP32)
+constexpr int kWsymKB16 = 6;
+constexpr int kWsymKB32 = 3;
+
+// One warp per tile: the warp takes all of its tile's packed blocks in
+// row-major order and adds each partial straight into the tile's outputs
+// (AccSink), with the next KB blocks of the tile in flight in its registers.
+// There is no CTA barrier inside a tile and a CTA holds 8 tiles, so every tile
+// of a few-thousand-tile plan is resident at once (27 warps per SM for 4096
+// tiles on 152 SMs): a sweep streams the blocks without waves of CTAs, each
+// tile's chain of dependent loads overlapped by all the others.
+// The arithmetic and its order are those of the 128-thread kernels (5, 7):
+// the same block partials; outputs summed from c in block order; each
+// tile's squared residual reduced as four 32-thread groups (virtual thread
+// lane + 32 v owns ports lane + 32 v + 128 j) and the tiles' partials summed
+// in the order of a 128-thread block -- so its iterates are bitwise theirs.
+// PPL ports per lane: 4 (tiles of at most 128 ports) or 8 (256).
+template <class TT, int KB, int PPL>
+__global__ void __launch_bounds__(256, PPL == 4 ? 4 : 3) sweep_wsym_kernel(
+    const TT* __restrict__ Tp, const TileDesc* __restrict__ tdesc,
+    const int32_t* __restrict__ twin, const float2* __restrict__ kd,
+    const uint8_t* __restrict__ run, const float* __restrict__ c, float* __restrict__ state,
+    int64_t nports, SweepCtrl* __restrict__ ctrl,
+    double* __restrict__ partials, double* __restrict__ hist, int hist_len, int nparts, int pp_max) {
+  using LD = SymLoad<TT>;
+  constexpr int B = kSymB;
+  static_assert(PPL == 4 || PPL == 8, "ports per lane");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_k, s_flag;
+  __shared__ bool s_last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = blockIdx.x * 8 + warp;
+  const bool valid = g < nparts;
+  TileDesc dsc{};
+  if (valid) dsc = tdesc[g];
+  const int p0 = dsc.p0, p = valid ? dsc.p : 0;
+  const int nb = (p + B - 1) / B;
+  const int nblk = nb * (nb + 1) / 2;
+  const TT* Tl = Tp + dsc.Tp_off;
+  float* w_in = reinterpret_cast<float*>(smem_raw) + (size_t)warp * 3 * pp_max;
+  float* rs = w_in + pp_max;
+  float* acc = rs + pp_max;
+  // the first blocks and the plan's port tables go out before the wait
+  typename LD::raw buf[KB];
+#pragma unroll
+  for (int b = 0; b < KB; ++b)
+    if (b < nblk) buf[b] = LD::load(Tl + (size_t)b * B * B, lane);
+  int tw[PPL];
+  uint32_t rn4[PPL / 4];  // node-run lengths, one byte per port
+#pragma unroll
+  for (int m = 0; m < PPL; ++m) {
+    const int s = lane + 32 * m;
+    tw[m] = s < p ? twin[p0 + s] : 0;
+  }
+#pragma unroll
+  for (int j = 0; j < PPL / 4; ++j) {
+    uint32_t r = 0;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int s = lane + 32 * (v + 4 * j);
+      if (s < p) r |= (uint32_t)run[p0 + s] << (8 * v);
+    }
+    rn4[j] = r;
+  }
+  pdl_launch_dependents();
+  pdl_wait();  // the previous sweep's waves, decision and counters
+  if (tid == 0) {
+    s_k = *((volatile int*)&ctrl->k);
+    s_flag = *((volatile int*)&ctrl->flag);
+  }
+  __syncthreads();
+  if (s_flag) return;
+  const int k = s_k;
+  const float* prev = state + (size_t)((k - 1) & 1) * nports * 2;
+  float* cur = state + (size_t)(k & 1) * nports * 2;
+  // incident waves and residual terms of sweep k - 1; the outputs start at c
+#pragma unroll
+  for (int m = 0; m < PPL; ++m) {
+    const int s = lane + 32 * m;
+    if (s < nb * B) {
+      float wi = 0.f, rc = 0.f, c0 = 0.f;
+      if (s < p) {
+        c0 = c[p0 + s];
+        if (k > 1) {
+          const float2 wt = *reinterpret_cast<const float2*>(prev + 2 * (size_t)tw[m]);
+          const float2 ws = *reinterpret_cast<const float2*>(prev + 2 * (size_t)(p0 + s));
+          wi = wt.y;
+          rc = port_residual<float>(ws.x, ws.y, wt.x, wt.y, kd[p0 + s]);
+        }
+      }
+      w_in[s] = wi;
+      rs[s] = rc;
+      acc[s] = c0;
+    }
+  }
+  __syncwarp();
+  float tile_sq = 0.f;  // lane 0: the four groups in order
+  if (k > 1) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      float sq = 0.f;
+#pragma unroll
+      for (int j = 0; j < PPL / 4; ++j) {
+        const int s = lane + 32 * (v + 4 * j);
+        const int nr = (rn4[j] >> (8 * v)) & 0xff;
+        if (s < p && nr) {
+          float rr = 0.f;
+          for (int q = 0; q < nr; ++q) rr += rs[s + q];
+          sq += rr * rr;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
+      tile_sq += sq;
+    }
+  }
+  const AccSink sink{acc};
+  int bi = 0, bj = 0;
+  for (int base = 0; base < nblk; base += KB) {
+#pragma unroll
+    for (int b = 0; b < KB; ++b) {
+      const int kk = base + b;
+      if (kk < nblk) {
+        const typename LD::raw v = buf[b];
+        if (kk + KB < nblk) buf[b] = LD::load(Tl + (size_t)(kk + KB) * B * B, lane);
+        sym_apply<TT>(v, bi, bj, lane, w_in, sink);
+        __syncwarp();  // the next block may add to the same outputs from other lanes
+        if (++bj == nb) bj = ++bi;
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < PPL; ++m) {
+    const int s = lane + 32 * m;
+    if (s < p) *reinterpret_cast<float2*>(cur + 2 * (size_t)(p0 + s)) = make_float2(w_in[s], acc[s]);
+  }
+  if (valid && lane == 0) {
+    partials[dsc.tile] = (double)tile_sq;
+    __threadfence();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    s_last = atomicAdd(&ctrl->counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const double tot = block_sum_fixed<128>(partials, nparts);
+  if (tid == 0) sweep_decide(ctrl, k, tot, hist, hist_len);
 }
 
 // ---------------------------------------------------------------------------
@@ -1232,7 +1446,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) sweep_flow_kernel(
             const typename LD::raw v = buf[b];
             const int kn = kk + KB * NW;
             if (kn < nblk) buf[b] = LD::load(Tl + (size_t)kn * B * B, lane);
-            sym_apply<TT>(v, bi, bi + off, nb, lane, w_in, part);
+            sym_apply<TT>(v, bi, bi + off, lane, w_in, PartSink{part, nb});
             off += NW;
           }
         }
@@ -1292,6 +1506,25 @@ template <class WT>
 static const typename KdOf<WT>::type* kd_of(vtm_plan_s* P) {
   if constexpr (std::is_same<WT, double>::value) return P->d_kd.as<double2>();
   else return P->d_kd32.as<float2>();
+}
+
+// One launch of a packed sweep (kernels 5-7), as a programmatic dependent of
+// the kernel before it on the stream unless the plan turned that off
+// (vtm_opts.pdl = 1).  Launch errors surface through cudaGetLastError.
+template <class... KArgs, class... Args>
+static void launch_packed(const vtm_plan_s* P, void (*kern)(KArgs...), int grid, int threads, size_t smem,
+                          cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = P->opts.pdl == 1 ? 0 : 1;
+  cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
 template <class TT, class WT>
@@ -1430,6 +1663,8 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   const int tbuf_elems = nb_max * (nb_max + 1) / 2 * kSymB * kSymB;
   const size_t symb_smem = (size_t)tbuf_elems * (prec == VTM_PREC_FP32 ? 4 : 2) + sym_smem;
   const bool symb_ok = sym_ok && symb_smem <= 160 * 1024;
+  // one warp per tile: per warp w_in, residual terms and outputs of the tile
+  const size_t wsym_smem = 8 * 3 * (size_t)pp_max * sizeof(float);
 
   if (staged)
     VTM_CUDA_TRY(cudaFuncSetAttribute(staged_kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st_smem));
@@ -1460,11 +1695,10 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   auto launch_one = [&](int kc) {
     if (kc == 7) {
       auto go = [&](auto* kern, const auto* Tp) {
-        kern<<<P->nparts, 128, symb_smem, s>>>(
-            Tp, P->d_tdesc.as<TileDesc>(), P->d_twin.as<int32_t>(), P->d_kd32.as<float2>(),
-            P->d_run.as<uint8_t>(), P->d_c32.as<float>(), P->d_state32.as<float>(), npt_,
-            P->d_ctrl.as<SweepCtrl>(), P->d_partials.as<double>(), hist, hist_len, P->nparts, pp_max,
-            tbuf_elems);
+        launch_packed(P, kern, P->nparts, 128, symb_smem, s, Tp, P->d_tdesc.as<TileDesc>(),
+                      P->d_twin.as<int32_t>(), P->d_kd32.as<float2>(), P->d_run.as<uint8_t>(),
+                      P->d_c32.as<float>(), P->d_state32.as<float>(), npt_, P->d_ctrl.as<SweepCtrl>(),
+                      P->d_partials.as<double>(), hist, hist_len, P->nparts, pp_max, tbuf_elems);
       };
       if (prec == VTM_PREC_FP32) go(sweep_symb_kernel<float, 128>, P->d_Tp32.as<float>());
       else with16([&](auto h) {
@@ -1473,12 +1707,32 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
       });
       return;
     }
+    if (kc == 9) {
+      auto go = [&](auto* kern, const auto* Tp) {
+        launch_packed(P, kern, (P->nparts + 7) / 8, 256, wsym_smem, s, Tp, P->d_tdesc.as<TileDesc>(),
+                      P->d_twin.as<int32_t>(), P->d_kd32.as<float2>(), P->d_run.as<uint8_t>(),
+                      P->d_c32.as<float>(), P->d_state32.as<float>(), npt_, P->d_ctrl.as<SweepCtrl>(),
+                      P->d_partials.as<double>(), hist, hist_len, P->nparts, pp_max);
+      };
+      const bool wide = pp_max > 128;
+      if (prec == VTM_PREC_FP32) {
+        if (wide) go(sweep_wsym_kernel<float, kWsymKB32, 8>, P->d_Tp32.as<float>());
+        else go(sweep_wsym_kernel<float, kWsymKB32, 4>, P->d_Tp32.as<float>());
+      } else {
+        with16([&](auto h) {
+          using H = decltype(h);
+          if (wide) go(sweep_wsym_kernel<H, kWsymKB16, 8>, P->d_Tp16.as<H>());
+          else go(sweep_wsym_kernel<H, kWsymKB16, 4>, P->d_Tp16.as<H>());
+        });
+      }
+      return;
+    }
     if (kc == 5 || kc == 6) {
       auto go = [&](auto* kern, int nt, const auto* Tp) {
-        kern<<<P->nparts, nt, sym_smem, s>>>(
-            Tp, P->d_tdesc.as<TileDesc>(), P->d_twin.as<int32_t>(), P->d_kd32.as<float2>(),
-            P->d_run.as<uint8_t>(), P->d_c32.as<float>(), P->d_state32.as<float>(), npt_,
-            P->d_ctrl.as<SweepCtrl>(), P->d_partials.as<double>(), hist, hist_len, P->nparts, pp_max);
+        launch_packed(P, kern, P->nparts, nt, sym_smem, s, Tp, P->d_tdesc.as<TileDesc>(),
+                      P->d_twin.as<int32_t>(), P->d_kd32.as<float2>(), P->d_run.as<uint8_t>(),
+                      P->d_c32.as<float>(), P->d_state32.as<float>(), npt_, P->d_ctrl.as<SweepCtrl>(),
+                      P->d_partials.as<double>(), hist, hist_len, P->nparts, pp_max);
       };
       // 5: up to 85 registers (6 CTAs per SM); 6: 64 registers (8 CTAs per SM)
       if (prec == VTM_PREC_FP32) {
@@ -1608,7 +1862,7 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
                               (const void*)sweep_flow_kernel<__half, 128, 8, false>));
     return cudaLaunchCooperativeKernel(kfn, flow_grid, 128, args, sym_smem, s);
   };
-  const bool symload = ((choice == 5 || choice == 6) && sym_ok) || (choice == 7 && symb_ok) ||
+  const bool symload = ((choice == 5 || choice == 6 || choice == 9) && sym_ok) || (choice == 7 && symb_ok) ||
                        (choice == 8 && flow_ok);
   if (P->opts.method == VTM_METHOD_ASYNC && !flow_ok) {
     set_detail("vtm_solve: asynchronous VTM runs on the packed symmetric dataflow kernel: it needs "
@@ -1632,9 +1886,10 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
       const bool can_vec128 = nv_max <= 128;
       float best = 1e30f;
       int best_k = 1;
-      for (int cand = 1; cand <= 8; ++cand) {
+      for (int cand = 1; cand <= 9; ++cand) {
         if ((cand == 2 && !can_st) || (cand == 3 && !can_vec) || (cand == 4 && !can_vec128) ||
-            ((cand == 5 || cand == 6) && !sym_ok) || (cand == 7 && !symb_ok) || (cand == 8 && !flow_ok))
+            ((cand == 5 || cand == 6 || cand == 9) && !sym_ok) || (cand == 7 && !symb_ok) ||
+            (cand == 8 && !flow_ok))
           continue;
         if (cand == 8) {  // one launch of 8 sweeps, per-sweep time compared with the others' 6
           SweepCtrl t = h;
@@ -1732,8 +1987,8 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   cudaGraphExec_t gexec = nullptr;
   if (P->stream && P->opts.graphs != 1) {
     SweepGraph& G = P->sweep_graph[prec];
-    const uint64_t key = ((uint64_t)kern << 56) ^ ((uint64_t)batch << 32) ^ (uint64_t)(uintptr_t)hist ^
-                         ((uint64_t)hist_len << 16);
+    const uint64_t key = ((uint64_t)kern << 56) ^ ((uint64_t)(P->opts.pdl == 1) << 52) ^
+                         ((uint64_t)batch << 32) ^ (uint64_t)(uintptr_t)hist ^ ((uint64_t)hist_len << 16);
     if (!G.exec || G.key != key) {
       if (G.exec) cudaGraphExecDestroy(G.exec);
       G.exec = nullptr;

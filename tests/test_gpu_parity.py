@@ -234,7 +234,9 @@ def test_every_sweep_kernel_matches_oracle(vtm, kernel):
                                                     ("bf16", 7, (192, 48)), ("fp32", 8, (90, 18)),
                                                     ("fp32", 8, (192, 48)), ("bf16", 8, (90, 18)),
                                                     ("fp16", 5, (192, 48)), ("fp16", 6, (90, 18)),
-                                                    ("fp16", 7, (90, 18)), ("fp16", 8, (192, 48))])
+                                                    ("fp16", 7, (90, 18)), ("fp16", 8, (192, 48)),
+                                                    ("fp32", 9, (90, 18)), ("fp32", 9, (192, 48)),
+                                                    ("bf16", 9, (90, 18)), ("fp16", 9, (192, 48))])
 def test_packed_symmetric_sweeps_follow_the_oracle(vtm, precision, kernel, shape):
     # T_P is symmetric (scalar W, symmetric A): the packed kernels read the
     # 16x16 blocks on and above the diagonal only.  18x18 tiles have 72, 54 or
@@ -262,29 +264,59 @@ def test_packed_symmetric_sweeps_follow_the_oracle(vtm, precision, kernel, shape
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
-def test_dataflow_sweeps_repeat_the_launch_per_sweep_kernel_bitwise(vtm, precision):
-    # one cooperative launch with per-tile neighbour waits computes the same
-    # iterates as one launch per sweep (same block arithmetic, same fixed-order
-    # reductions, same decisions)
+def test_dataflow_and_warp_per_tile_sweeps_repeat_kernel_5_bitwise(vtm, precision):
+    # one cooperative launch with per-tile neighbour waits (8), and one warp per
+    # tile adding its partials in block order (9), compute the same iterates as
+    # four warps per tile (5): same block arithmetic, same fixed-order
+    # reductions, same decisions
     w = wl.power_grid(256, 256, 32, 32, Zc=1.0, seed=17)
     out = []
-    for kernel in (5, 8):
+    for kernel in (5, 8, 9):
         plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc,
                         precision=precision, sweep_kernel=kernel)
         plan.set_options(history_len=64)
         x, info = plan.solve(torch.from_numpy(w.b[0]).cuda(), tol=1e-10)
         assert plan.stats()["sweep_kernel"] == kernel
         out.append((x, info["sweeps"], info["outer_steps"], plan.history))
-    assert out[0][1:3] == out[1][1:3]
-    assert np.array_equal(out[0][3], out[1][3])
-    assert torch.equal(out[0][0], out[1][0])
+    for o in out[1:]:
+        assert out[0][1:3] == o[1:3]
+        assert np.array_equal(out[0][3], o[3])
+        assert torch.equal(out[0][0], o[0])
+
+
+@pytest.mark.parametrize("precision,kernel", [("fp32", 5), ("fp32", 6), ("fp16", 7), ("bf16", 7), ("fp16", 9)])
+def test_overlapped_sweep_launches_compute_the_same_iterates(vtm, precision, kernel):
+    # packed sweeps launched as programmatic dependents of the sweep before
+    # them (the default) against plain launches: same iterates, same stop,
+    # in CUDA graphs (own stream) and in plain launches
+    w = wl.power_grid(192, 192, 32, 32, Zc=1.0, seed=18)
+    b = torch.from_numpy(w.b[0]).cuda()
+    s = torch.cuda.Stream()
+    out = []
+    for pdl, graphs in ((0, 0), (1, 0), (0, 1)):
+        with torch.cuda.stream(s):
+            plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc, precision=precision,
+                            sweep_kernel=kernel, pdl=pdl, graphs=graphs, stream=s)
+            plan.set_options(history_len=64)
+            x, info = plan.solve(b, tol=1e-10)
+            x2, info2 = plan.solve(b, tol=1e-10)
+        torch.cuda.synchronize()
+        assert plan.stats()["sweep_kernel"] == kernel
+        assert torch.equal(x, x2) and info["sweeps"] == info2["sweeps"]
+        out.append((x, info["sweeps"], info["outer_steps"], plan.history))
+        plan.close()
+    for o in out[1:]:
+        assert o[1:3] == out[0][1:3]
+        assert np.array_equal(o[3], out[0][3])
+        assert torch.equal(o[0], out[0][0])
+    assert O.residual_norms(w.csr(), out[0][0].cpu().numpy()[None], w.b[:1]).max() <= 1e-10
 
 
 def test_bad_options_are_rejected_and_the_plan_keeps_its_own(vtm):
     w = wl.power_grid(64, 64, 32, 32, Zc=1.0, seed=15)
     plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc)
     with pytest.raises(vtm.VTMError):
-        plan.set_options(sweep_kernel=9)
+        plan.set_options(sweep_kernel=10)
     with pytest.raises(vtm.VTMError):
         plan.set_options(sweep_kernel=-1)
     for bad in (4, 5, -1):
