@@ -391,7 +391,15 @@ __global__ void pack_sym_kernel(const double* __restrict__ T64, const TileDesc* 
       ++bi;
     }
     const int bj = bi + blk;
-    const int s = bi * kSymB + w / kSymB, q = bj * kSymB + w % kSymB;
+    // FP32 blocks are row-major; a 16-bit block keeps, at the 16 bytes of
+    // lane l, row l/4 columns 4(l%4)..+3 then row l/4 + 8 (the sweep's order)
+    int r = w / kSymB, q4 = w % kSymB;
+    if (sizeof(TT) == 2) {
+      const int l = w >> 3, e8 = w & 7;
+      r = (l >> 2) + ((e8 >> 2) << 3);
+      q4 = ((l & 3) << 2) + (e8 & 3);
+    }
+    const int s = bi * kSymB + r, q = bj * kSymB + q4;
     double v = 0.0;
     if (s < d.p && q < d.p) v = 0.5 * (Tb[(size_t)q * d.ld + s] + Tb[(size_t)s * d.ld + q]);
     store_low(Tp + d.Tp_off + e, v);

@@ -740,20 +740,24 @@ __global__ void __launch_bounds__(NT) sweep_vec_kernel(
 // (its spectrum is (W - lambda)/(W + lambda), Sec. VIII), so only the 16x16
 // blocks on and above the diagonal are stored: about half the bytes of the
 // full matrix, which is what an HBM-bound sweep pays for.  A warp takes one
-// block (bi, bj) at a time; lane l holds row r = l/2, columns 8(l%2)..+7 and
-//   * adds T_blk w(bj) into the partial of row block bi (two-lane shuffle);
+// block (bi, bj) at a time; lane l holds rows l/4 and l/4 + 8, columns
+// 4(l%4)..+3, and
+//   * adds T_blk w(bj) into the partial of row block bi: a reduce-scatter of
+//     its two rows over lane bit 0, then a sum over bit 1;
 //   * for bi < bj adds T_blk^T w(bi) into the partial of row block bj: the
-//     16-row sums are a reduce-scatter over lane bits 4, 3, 2 followed by
-//     one exchange over bit 1 (8 shuffles, a fixed summation tree).
+//     16-row sums of its four columns are a reduce-scatter over lane bits 4
+//     and 3, then a sum over bit 2 (6 shuffles in all, a fixed summation tree).
 // part[a][b] holds block b's contribution to row block a; the outputs sum
 // them in the fixed order b = 0..nb-1, so every sweep is bitwise repeatable.
-// Two ways to bring a tile's blocks in: 16-byte register loads a few blocks
-// ahead (sweep_sym_kernel), or one bulk copy of the whole packed tile into
-// shared memory issued before anything else (sweep_symb_kernel).
+// Ways to bring a tile's blocks in: 16-byte register loads a few blocks ahead
+// (sweep_sym_kernel), one bulk copy of the whole packed tile into shared
+// memory issued before anything else (sweep_symb_kernel), a per-warp ring of
+// asynchronous copies (sweep_wsym_kernel).
 // ---------------------------------------------------------------------------
 
-// 16-bit storage (BF16, FP16): lane l holds the 16 bytes number l (row l/2,
-// columns 8(l%2)..+7).
+// 16-bit storage (BF16, FP16): lane l holds the 16 bytes number l: row l/4,
+// columns 4(l%4)..+3, then row l/4 + 8, the same columns (the packing orders
+// each 16-bit block that way, so the FP32 block code serves both).
 template <class TT>
 struct SymLoad {
   using raw = uint4;
@@ -893,15 +897,13 @@ __device__ __forceinline__ void sym_block(const SymLoad<float>::raw& v, int bi, 
   constexpr int B = kSymB;
   constexpr unsigned FULL = 0xffffffffu;
   const int r1 = lane >> 2, cg = lane & 3;
+  // paired FP32 arithmetic (two lanes of a 64-bit register per instruction):
+  // each row's four products as two pairs, then the pair's halves added
   const float4 wc = *reinterpret_cast<const float4*>(w_in + bj * B + cg * 4);
-  float a1 = v.a.x * wc.x;
-  a1 = fmaf(v.a.y, wc.y, a1);
-  a1 = fmaf(v.a.z, wc.z, a1);
-  a1 = fmaf(v.a.w, wc.w, a1);
-  float a2 = v.b.x * wc.x;
-  a2 = fmaf(v.b.y, wc.y, a2);
-  a2 = fmaf(v.b.z, wc.z, a2);
-  a2 = fmaf(v.b.w, wc.w, a2);
+  const float2 wc01 = make_float2(wc.x, wc.y), wc23 = make_float2(wc.z, wc.w);
+  const float2 pa = __ffma2_rn(make_float2(v.a.z, v.a.w), wc23, __fmul2_rn(make_float2(v.a.x, v.a.y), wc01));
+  const float2 pb = __ffma2_rn(make_float2(v.b.z, v.b.w), wc23, __fmul2_rn(make_float2(v.b.x, v.b.y), wc01));
+  const float a1 = pa.x + pa.y, a2 = pb.x + pb.y;
   // rows r1 and r1 + 8: sums over the four lanes of a row (bits 0, 1)
   const bool b0 = lane & 1;
   float t = (b0 ? a2 : a1) + __shfl_xor_sync(FULL, b0 ? a1 : a2, 1);
@@ -909,10 +911,10 @@ __device__ __forceinline__ void sym_block(const SymLoad<float>::raw& v, int bi, 
   if (!(lane & 2)) sink(bi, bj, b0 ? r1 + 8 : r1, t);
   if (bi != bj) {
     const float wr1 = w_in[bi * B + r1], wr2 = w_in[bi * B + r1 + 8];
-    const float u0 = fmaf(v.b.x, wr2, v.a.x * wr1);
-    const float u1 = fmaf(v.b.y, wr2, v.a.y * wr1);
-    const float u2 = fmaf(v.b.z, wr2, v.a.z * wr1);
-    const float u3 = fmaf(v.b.w, wr2, v.a.w * wr1);
+    const float2 w1 = make_float2(wr1, wr1), w2 = make_float2(wr2, wr2);
+    const float2 u01 = __ffma2_rn(make_float2(v.b.x, v.b.y), w2, __fmul2_rn(make_float2(v.a.x, v.a.y), w1));
+    const float2 u23 = __ffma2_rn(make_float2(v.b.z, v.b.w), w2, __fmul2_rn(make_float2(v.a.z, v.a.w), w1));
+    const float u0 = u01.x, u1 = u01.y, u2 = u23.x, u3 = u23.y;
     // columns 4 cg..+3: sums over the eight lanes of a column group (bits 4, 3, 2)
     const bool b4 = lane & 16, b3 = lane & 8;
     float k0 = b4 ? u2 : u0, k1 = b4 ? u3 : u1;
@@ -927,60 +929,12 @@ __device__ __forceinline__ void sym_block(const SymLoad<float>::raw& v, int bi, 
 template <class H, class Sink>
 __device__ __forceinline__ void sym_block16(const uint4& raw, int bi, int bj, int lane, const float* w_in,
                                             const Sink& sink) {
-  constexpr int B = kSymB;
-  constexpr unsigned FULL = 0xffffffffu;
-  float v[8];
-  {
-    const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const float2 f = Pair16<H>::f2(w[i]);
-      v[2 * i] = f.x;
-      v[2 * i + 1] = f.y;
-    }
-  }
-  const int r = lane >> 1, h = lane & 1;
-  const float4 c0 = *reinterpret_cast<const float4*>(w_in + bj * B + h * 8);
-  const float4 c1 = *reinterpret_cast<const float4*>(w_in + bj * B + h * 8 + 4);
-  float a = v[0] * c0.x;
-  a = fmaf(v[1], c0.y, a);
-  a = fmaf(v[2], c0.z, a);
-  a = fmaf(v[3], c0.w, a);
-  a = fmaf(v[4], c1.x, a);
-  a = fmaf(v[5], c1.y, a);
-  a = fmaf(v[6], c1.z, a);
-  a = fmaf(v[7], c1.w, a);
-  a += __shfl_xor_sync(FULL, a, 1);
-  if (h == 0) sink(bi, bj, r, a);
-  if (bi != bj) {
-    const float wr = w_in[bi * B + r];
-    float u[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) u[j] = v[j] * wr;
-    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
-    float t4[4], t2[2];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const float send = b4 ? u[i] : u[i + 4];
-      const float keep = b4 ? u[i + 4] : u[i];
-      t4[i] = keep + __shfl_xor_sync(FULL, send, 16);
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const float send = b3 ? t4[i] : t4[i + 2];
-      const float keep = b3 ? t4[i + 2] : t4[i];
-      t2[i] = keep + __shfl_xor_sync(FULL, send, 8);
-    }
-    float t1;
-    {
-      const float send = b2 ? t2[0] : t2[1];
-      const float keep = b2 ? t2[1] : t2[0];
-      t1 = keep + __shfl_xor_sync(FULL, send, 4);
-    }
-    t1 += __shfl_xor_sync(FULL, t1, 2);
-    const int jc = (b4 ? 4 : 0) + (b3 ? 2 : 0) + (b2 ? 1 : 0);
-    if (!(lane & 2)) sink(bj, bi, h * 8 + jc, t1);
-  }
+  const float2 e0 = Pair16<H>::f2(raw.x), e1 = Pair16<H>::f2(raw.y);
+  const float2 e2 = Pair16<H>::f2(raw.z), e3 = Pair16<H>::f2(raw.w);
+  SymLoad<float>::raw v;
+  v.a = make_float4(e0.x, e0.y, e1.x, e1.y);
+  v.b = make_float4(e2.x, e2.y, e3.x, e3.y);
+  sym_block(v, bi, bj, lane, w_in, sink);
 }
 
 template <class TT, class Sink = PartSink>
@@ -1179,14 +1133,36 @@ __global__ void __launch_bounds__(NT) sweep_symb_kernel(
                  nparts, &s_last);
 }
 
-// blocks in flight per warp of sweep_wsym_kernel (registers: 4 per block for
-// 16-bit entries, 8 for FP32)
-constexpr int kWsymKB16 = 6;
-constexpr int kWsymKB32 = 3;
+// ring slots per warp of sweep_wsym_kernel (one block each: 512 B for 16-bit
+// entries, 1 KB for FP32; one slot fewer is in flight)
+constexpr int kWsymKB16 = 8;
+constexpr int kWsymKB32 = 5;
+
+// 16-byte asynchronous copy global -> shared (L2 only), its groups and waits
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+// lane's share of one packed block: the bytes it later reads itself (SymLoad)
+template <class TT>
+__device__ __forceinline__ void copy_block_async(TT* dst, const TT* src, int lane) {
+  if constexpr (std::is_same<TT, float>::value) {
+    cp_async16(reinterpret_cast<float4*>(dst) + lane, reinterpret_cast<const float4*>(src) + lane);
+    cp_async16(reinterpret_cast<float4*>(dst) + lane + 32, reinterpret_cast<const float4*>(src) + lane + 32);
+  } else {
+    cp_async16(reinterpret_cast<uint4*>(dst) + lane, reinterpret_cast<const uint4*>(src) + lane);
+  }
+}
 
 // One warp per tile: the warp takes all of its tile's packed blocks in
 // row-major order and adds each partial straight into the tile's outputs
-// (AccSink), with the next KB blocks of the tile in flight in its registers.
+// (AccSink), with the next KB - 1 blocks of the tile in flight into a ring of
+// KB shared-memory slots (each lane copies, and later reads, its own bytes of
+// a block, so no warp barrier guards the ring).
 // There is no CTA barrier inside a tile and a CTA holds 8 tiles, so every tile
 // of a few-thousand-tile plan is resident at once (27 warps per SM for 4096
 // tiles on 152 SMs): a sweep streams the blocks without waves of CTAs, each
@@ -1219,14 +1195,22 @@ __global__ void __launch_bounds__(256, PPL == 4 ? 4 : 3) sweep_wsym_kernel(
   const int nb = (p + B - 1) / B;
   const int nblk = nb * (nb + 1) / 2;
   const TT* Tl = Tp + dsc.Tp_off;
-  float* w_in = reinterpret_cast<float*>(smem_raw) + (size_t)warp * 3 * pp_max;
+  TT* ring = reinterpret_cast<TT*>(smem_raw + (size_t)warp * (KB * B * B * sizeof(TT) + 12 * (size_t)pp_max));
+  float* w_in = reinterpret_cast<float*>(ring + KB * B * B);
   float* rs = w_in + pp_max;
   float* acc = rs + pp_max;
+  // launches past the end of the solve copy nothing (a set flag stays set
+  // within a batch; read before pdl_wait a clear one may be stale, and the
+  // check after it drains this launch's copies); one read for the whole CTA
+  if (tid == 0) s_flag = *((volatile int*)&ctrl->flag);
+  __syncthreads();
+  if (s_flag) return;
   // the first blocks and the plan's port tables go out before the wait
-  typename LD::raw buf[KB];
 #pragma unroll
-  for (int b = 0; b < KB; ++b)
-    if (b < nblk) buf[b] = LD::load(Tl + (size_t)b * B * B, lane);
+  for (int b = 0; b < KB - 1; ++b) {
+    if (b < nblk) copy_block_async(ring + b * B * B, Tl + (size_t)b * B * B, lane);
+    cp_async_commit_group();
+  }
   int tw[PPL];
   uint32_t rn4[PPL / 4];  // node-run lengths, one byte per port
 #pragma unroll
@@ -1251,7 +1235,10 @@ __global__ void __launch_bounds__(256, PPL == 4 ? 4 : 3) sweep_wsym_kernel(
     s_flag = *((volatile int*)&ctrl->flag);
   }
   __syncthreads();
-  if (s_flag) return;
+  if (s_flag) {
+    cp_async_wait_group<0>();  // no copy into shared memory outlives the CTA
+    return;
+  }
   const int k = s_k;
   const float* prev = state + (size_t)((k - 1) & 1) * nports * 2;
   float* cur = state + (size_t)(k & 1) * nports * 2;
@@ -1297,19 +1284,17 @@ __global__ void __launch_bounds__(256, PPL == 4 ? 4 : 3) sweep_wsym_kernel(
   }
   const AccSink sink{acc};
   int bi = 0, bj = 0;
-  for (int base = 0; base < nblk; base += KB) {
-#pragma unroll
-    for (int b = 0; b < KB; ++b) {
-      const int kk = base + b;
-      if (kk < nblk) {
-        const typename LD::raw v = buf[b];
-        if (kk + KB < nblk) buf[b] = LD::load(Tl + (size_t)(kk + KB) * B * B, lane);
-        sym_apply<TT>(v, bi, bj, lane, w_in, sink);
-        __syncwarp();  // the next block may add to the same outputs from other lanes
-        if (++bj == nb) bj = ++bi;
-      }
-    }
+  for (int kk = 0; kk < nblk; ++kk) {
+    // block kk + KB - 1 goes into the slot that block kk - 1 left
+    const int kn = kk + KB - 1;
+    if (kn < nblk) copy_block_async(ring + (kn % KB) * B * B, Tl + (size_t)kn * B * B, lane);
+    cp_async_commit_group();
+    cp_async_wait_group<KB - 1>();  // this lane's bytes of block kk have landed
+    sym_apply<TT>(LD::load_shared(ring + (kk % KB) * B * B, lane), bi, bj, lane, w_in, sink);
+    __syncwarp();  // the next block may add to the same outputs from other lanes
+    if (++bj == nb) bj = ++bi;
   }
+  cp_async_wait_group<0>();
 #pragma unroll
   for (int m = 0; m < PPL; ++m) {
     const int s = lane + 32 * m;
@@ -1663,8 +1648,23 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   const int tbuf_elems = nb_max * (nb_max + 1) / 2 * kSymB * kSymB;
   const size_t symb_smem = (size_t)tbuf_elems * (prec == VTM_PREC_FP32 ? 4 : 2) + sym_smem;
   const bool symb_ok = sym_ok && symb_smem <= 160 * 1024;
-  // one warp per tile: per warp w_in, residual terms and outputs of the tile
-  const size_t wsym_smem = 8 * 3 * (size_t)pp_max * sizeof(float);
+  // one warp per tile: per warp a ring of blocks, w_in, residual terms and
+  // outputs of the tile; the variant for this precision and tile size
+  const size_t wsym_smem =
+      8 * ((size_t)(prec == VTM_PREC_FP32 ? kWsymKB32 * 4 : kWsymKB16 * 2) * kSymB * kSymB + 12 * (size_t)pp_max);
+  auto with_wsym = [&](auto fn) {
+    const bool wide = pp_max > 128;
+    if (prec == VTM_PREC_FP32) {
+      if (wide) fn(sweep_wsym_kernel<float, kWsymKB32, 8>, P->d_Tp32.as<float>());
+      else fn(sweep_wsym_kernel<float, kWsymKB32, 4>, P->d_Tp32.as<float>());
+    } else {
+      with16([&](auto h) {
+        using H = decltype(h);
+        if (wide) fn(sweep_wsym_kernel<H, kWsymKB16, 8>, P->d_Tp16.as<H>());
+        else fn(sweep_wsym_kernel<H, kWsymKB16, 4>, P->d_Tp16.as<H>());
+      });
+    }
+  };
 
   if (staged)
     VTM_CUDA_TRY(cudaFuncSetAttribute(staged_kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st_smem));
@@ -1708,23 +1708,12 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
       return;
     }
     if (kc == 9) {
-      auto go = [&](auto* kern, const auto* Tp) {
+      with_wsym([&](auto* kern, const auto* Tp) {
         launch_packed(P, kern, (P->nparts + 7) / 8, 256, wsym_smem, s, Tp, P->d_tdesc.as<TileDesc>(),
                       P->d_twin.as<int32_t>(), P->d_kd32.as<float2>(), P->d_run.as<uint8_t>(),
                       P->d_c32.as<float>(), P->d_state32.as<float>(), npt_, P->d_ctrl.as<SweepCtrl>(),
                       P->d_partials.as<double>(), hist, hist_len, P->nparts, pp_max);
-      };
-      const bool wide = pp_max > 128;
-      if (prec == VTM_PREC_FP32) {
-        if (wide) go(sweep_wsym_kernel<float, kWsymKB32, 8>, P->d_Tp32.as<float>());
-        else go(sweep_wsym_kernel<float, kWsymKB32, 4>, P->d_Tp32.as<float>());
-      } else {
-        with16([&](auto h) {
-          using H = decltype(h);
-          if (wide) go(sweep_wsym_kernel<H, kWsymKB16, 8>, P->d_Tp16.as<H>());
-          else go(sweep_wsym_kernel<H, kWsymKB16, 4>, P->d_Tp16.as<H>());
-        });
-      }
+      });
       return;
     }
     if (kc == 5 || kc == 6) {
@@ -1868,6 +1857,13 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
     set_detail("vtm_solve: asynchronous VTM runs on the packed symmetric dataflow kernel: it needs "
                "FP32/BF16/FP16 sweeps of a symmetric plan with at most 256 ports per sub-circuit");
     return VTM_EINVAL;
+  }
+  if (sym_ok) {
+    cudaError_t e = cudaSuccess;
+    with_wsym([&](auto* kern, const auto*) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsym_smem);
+    });
+    VTM_CUDA_TRY(e);
   }
   if (symb_ok) {
     VTM_CUDA_TRY(cudaFuncSetAttribute(prec == VTM_PREC_FP32
