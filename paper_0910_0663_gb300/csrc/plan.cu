@@ -857,8 +857,8 @@ extern "C" vtm_status vtm_set_opts(vtm_plan_t P, const vtm_opts* opts) {
     set_detail("vtm_set_opts: bad precision or history");
     return VTM_EINVAL;
   }
-  if (o.sweep_kernel < 0 || o.sweep_kernel > 9) {
-    set_detail("vtm_set_opts: sweep_kernel must be 0..9");
+  if (o.sweep_kernel < 0 || o.sweep_kernel > 10) {
+    set_detail("vtm_set_opts: sweep_kernel must be 0..10");
     return VTM_EINVAL;
   }
   if (o.method < 0 || o.method > 2 || ((o.method == VTM_METHOD_BJ) != (P->method == VTM_METHOD_BJ))) {
@@ -1019,7 +1019,8 @@ extern "C" vtm_status vtm_plan(int64_t n, const int64_t* rowptr, const int32_t* 
   if ((st = dev_alloc(P->d_xacc, (size_t)n * sizeof(double))) != VTM_OK) return fail(st);
   if ((st = dev_alloc(P->d_r, (size_t)n * sizeof(double))) != VTM_OK) return fail(st);
   if ((st = dev_alloc(P->d_bcol, (size_t)n * sizeof(double))) != VTM_OK) return fail(st);
-  if ((st = dev_alloc(P->d_partials, sizeof(double) * std::max<size_t>(nparts, 4096))) != VTM_OK)
+  // two sweeps' worth (the one-warp-per-tile sweeps reduce one while writing the next)
+  if ((st = dev_alloc(P->d_partials, 2 * sizeof(double) * std::max<size_t>(nparts, 4096))) != VTM_OK)
     return fail(st);
   if ((st = dev_alloc(P->d_ctrl, sizeof(SweepCtrl))) != VTM_OK) return fail(st);
   if ((st = dev_alloc(P->d_err, 64)) != VTM_OK) return fail(st);
@@ -1103,7 +1104,7 @@ extern "C" vtm_status vtm_plan_get_stats(vtm_plan_t P, vtm_plan_stats* s) {
   s->t_bytes = (int64_t)(P->d_T64.bytes + P->d_T32.bytes + P->d_T16.bytes + P->d_E.bytes +
                          P->d_Tp32.bytes + P->d_Tp16.bytes);
   s->factor_bytes = (int64_t)(P->d_Lc.bytes + P->d_Uc.bytes);
-  s->sweep_kernel = P->opts.method == VTM_METHOD_ASYNC   ? 8
+  s->sweep_kernel = P->opts.method == VTM_METHOD_ASYNC   ? P->dataflow_kernel
                     : P->tuned_kernel[P->opts.precision] ? P->tuned_kernel[P->opts.precision]
                                                          : P->opts.sweep_kernel;
   s->sum_tri = P->sum_tri;

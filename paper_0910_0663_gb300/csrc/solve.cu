@@ -849,8 +849,9 @@ __device__ __forceinline__ float sym_gather(const SymPorts<NT>& pt, const float*
     if (s < nb * kSymB) {
       float wi = 0.f, rc = 0.f;
       if (k > 1 && s < p) {
-        const float2 wt = *reinterpret_cast<const float2*>(prev + 2 * (size_t)pt.tw[j]);
-        const float2 ws = *reinterpret_cast<const float2*>(prev + 2 * (size_t)(p0 + s));
+        // L2 reads: in the dataflow kernels other SMs wrote these during this launch
+        const float2 wt = __ldcg(reinterpret_cast<const float2*>(prev + 2 * (size_t)pt.tw[j]));
+        const float2 ws = __ldcg(reinterpret_cast<const float2*>(prev + 2 * (size_t)(p0 + s)));
         wi = wt.y;
         rc = port_residual<float>(ws.x, ws.y, wt.x, wt.y, pt.kq[j]);
       }
@@ -1137,6 +1138,10 @@ __global__ void __launch_bounds__(NT) sweep_symb_kernel(
 // entries, 1 KB for FP32; one slot fewer is in flight)
 constexpr int kWsymKB16 = 8;
 constexpr int kWsymKB32 = 5;
+// the dataflow form keeps a tile's state in registers for a whole inner solve:
+// 4 warps per CTA and 7 CTAs per SM (up to 72 registers) hold 28 tiles per SM
+constexpr int kWflowWarps = 4;
+constexpr int kWflowCtasPerSm = 7;
 
 // 16-byte asynchronous copy global -> shared (L2 only), its groups and waits
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -1158,81 +1163,121 @@ __device__ __forceinline__ void copy_block_async(TT* dst, const TT* src, int lan
   }
 }
 
+// Fixed-order sum of `count` doubles by the 128 threads t = 0..127 of a
+// named barrier group (bar id 1): the order of block_sum_fixed<128>, for four
+// warps that run beside others.  Valid in t = 0.
+__device__ double group128_sum_fixed(const double* __restrict__ a, int64_t count, int t, double* red) {
+  constexpr int kMLP = 16;
+  double acc = 0.0;
+  for (int64_t base = t; base < count; base += kMLP * 128) {
+    double v[kMLP];
+#pragma unroll
+    for (int j = 0; j < kMLP; ++j) {
+      const int64_t i = base + j * 128;
+      v[j] = i < count ? __ldcg(a + i) : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < kMLP; ++j) acc += v[j];
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((t & 31) == 0) red[t >> 5] = acc;
+  asm volatile("bar.sync 1, 128;" ::: "memory");
+  double tot = 0.0;
+  if (t == 0)
+    for (int i = 0; i < 4; ++i) tot += red[i];
+  return tot;
+}
+
 // One warp per tile: the warp takes all of its tile's packed blocks in
 // row-major order and adds each partial straight into the tile's outputs
 // (AccSink), with the next KB - 1 blocks of the tile in flight into a ring of
 // KB shared-memory slots (each lane copies, and later reads, its own bytes of
 // a block, so no warp barrier guards the ring).
-// There is no CTA barrier inside a tile and a CTA holds 8 tiles, so every tile
-// of a few-thousand-tile plan is resident at once (27 warps per SM for 4096
-// tiles on 152 SMs): a sweep streams the blocks without waves of CTAs, each
-// tile's chain of dependent loads overlapped by all the others.
+// There is no CTA barrier inside a tile; a CTA holds up to 32 tiles, dealt
+// round the CTAs (tile warp x gridDim + CTA), so every tile of a
+// few-thousand-tile plan is resident at once (one CTA of 27 tile warps per
+// SM for 4096 tiles on 152 SMs) and each SM carries the same mix of tile
+// sizes: a sweep streams the blocks without waves of CTAs, each tile's chain
+// of dependent loads overlapped by all the others.
+// The launch decides nothing about its own sweep: the four service warps
+// after the tile warps of CTA 0 sum the residual partials of the previous
+// sweep and take its decision while the tiles run, so no last-CTA tail sits
+// on the critical path of a sweep.  The stop therefore lands one launch
+// later, and the waves live in three slots (sweep k writes slot k mod 3),
+// so the iterate a decision names survives the sweep after it.  Each launch
+// takes its sweep number from a ticket (CTAs of launches past a stop leave
+// before taking one).
 // The arithmetic and its order are those of the 128-thread kernels (5, 7):
 // the same block partials; outputs summed from c in block order; each
 // tile's squared residual reduced as four 32-thread groups (virtual thread
 // lane + 32 v owns ports lane + 32 v + 128 j) and the tiles' partials summed
-// in the order of a 128-thread block -- so its iterates are bitwise theirs.
+// in the order of a 128-thread block -- so its iterates, residual history
+// and decisions are bitwise theirs.
 // PPL ports per lane: 4 (tiles of at most 128 ports) or 8 (256).
 template <class TT, int KB, int PPL>
-__global__ void __launch_bounds__(256, PPL == 4 ? 4 : 3) sweep_wsym_kernel(
+__global__ void __launch_bounds__(1024, 1) sweep_wsym_kernel(
     const TT* __restrict__ Tp, const TileDesc* __restrict__ tdesc,
     const int32_t* __restrict__ twin, const float2* __restrict__ kd,
-    const uint8_t* __restrict__ run, const float* __restrict__ c, float* __restrict__ state,
+    const uint8_t* __restrict__ run, const float* __restrict__ c, float* __restrict__ state3,
     int64_t nports, SweepCtrl* __restrict__ ctrl,
-    double* __restrict__ partials, double* __restrict__ hist, int hist_len, int nparts, int pp_max) {
+    double* __restrict__ partials2, double* __restrict__ hist, int hist_len, int nparts, int pp_max) {
   using LD = SymLoad<TT>;
   constexpr int B = kSymB;
   static_assert(PPL == 4 || PPL == 8, "ports per lane");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_k, s_flag;
-  __shared__ bool s_last;
+  __shared__ double s_red[4];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int g = blockIdx.x * 8 + warp;
-  const bool valid = g < nparts;
+  const int nw = (int)(blockDim.x >> 5) - 4;  // tile warps; the last four serve
+  // launches past the end of the solve copy nothing (a set flag stays set
+  // within a batch; read before pdl_wait a clear one may be stale)
+  if (tid == 0) s_flag = *((volatile int*)&ctrl->flag);
+  __syncthreads();
+  if (s_flag) return;
+  const bool tile_warp = warp < nw;
+  const int g = warp * gridDim.x + blockIdx.x;  // tiles dealt round the CTAs
+  const bool valid = tile_warp && g < nparts;
   TileDesc dsc{};
   if (valid) dsc = tdesc[g];
   const int p0 = dsc.p0, p = valid ? dsc.p : 0;
   const int nb = (p + B - 1) / B;
   const int nblk = nb * (nb + 1) / 2;
   const TT* Tl = Tp + dsc.Tp_off;
-  TT* ring = reinterpret_cast<TT*>(smem_raw + (size_t)warp * (KB * B * B * sizeof(TT) + 12 * (size_t)pp_max));
+  TT* ring = reinterpret_cast<TT*>(smem_raw +
+                                   (size_t)(tile_warp ? warp : 0) * (KB * B * B * sizeof(TT) + 12 * (size_t)pp_max));
   float* w_in = reinterpret_cast<float*>(ring + KB * B * B);
   float* rs = w_in + pp_max;
   float* acc = rs + pp_max;
-  // launches past the end of the solve copy nothing (a set flag stays set
-  // within a batch; read before pdl_wait a clear one may be stale, and the
-  // check after it drains this launch's copies); one read for the whole CTA
-  if (tid == 0) s_flag = *((volatile int*)&ctrl->flag);
-  __syncthreads();
-  if (s_flag) return;
-  // the first blocks and the plan's port tables go out before the wait
-#pragma unroll
-  for (int b = 0; b < KB - 1; ++b) {
-    if (b < nblk) copy_block_async(ring + b * B * B, Tl + (size_t)b * B * B, lane);
-    cp_async_commit_group();
-  }
+  // the ring's first blocks and the plan's port tables go out before the wait
   int tw[PPL];
   uint32_t rn4[PPL / 4];  // node-run lengths, one byte per port
+  if (tile_warp) {
 #pragma unroll
-  for (int m = 0; m < PPL; ++m) {
-    const int s = lane + 32 * m;
-    tw[m] = s < p ? twin[p0 + s] : 0;
-  }
-#pragma unroll
-  for (int j = 0; j < PPL / 4; ++j) {
-    uint32_t r = 0;
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int s = lane + 32 * (v + 4 * j);
-      if (s < p) r |= (uint32_t)run[p0 + s] << (8 * v);
+    for (int b = 0; b < KB - 1; ++b) {
+      if (b < nblk) copy_block_async(ring + b * B * B, Tl + (size_t)b * B * B, lane);
+      cp_async_commit_group();
     }
-    rn4[j] = r;
+#pragma unroll
+    for (int m = 0; m < PPL; ++m) {
+      const int s = lane + 32 * m;
+      tw[m] = s < p ? twin[p0 + s] : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < PPL / 4; ++j) {
+      uint32_t r = 0;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int s = lane + 32 * (v + 4 * j);
+        if (s < p) r |= (uint32_t)run[p0 + s] << (8 * v);
+      }
+      rn4[j] = r;
+    }
   }
   pdl_launch_dependents();
-  pdl_wait();  // the previous sweep's waves, decision and counters
+  pdl_wait();  // the previous sweep's waves, partials and decision
   if (tid == 0) {
-    s_k = *((volatile int*)&ctrl->k);
     s_flag = *((volatile int*)&ctrl->flag);
+    if (!s_flag) s_k = (int)(atomicAdd(&ctrl->ticket, 1u) / gridDim.x) + 1;
   }
   __syncthreads();
   if (s_flag) {
@@ -1240,8 +1285,15 @@ __global__ void __launch_bounds__(256, PPL == 4 ? 4 : 3) sweep_wsym_kernel(
     return;
   }
   const int k = s_k;
-  const float* prev = state + (size_t)((k - 1) & 1) * nports * 2;
-  float* cur = state + (size_t)(k & 1) * nports * 2;
+  if (!tile_warp) {  // service warps: CTA 0 decides on the previous sweep
+    if (blockIdx.x != 0 || k < 2) return;
+    const int t = tid - nw * 32;
+    const double tot = group128_sum_fixed(partials2 + (size_t)((k - 1) & 1) * nparts, nparts, t, s_red);
+    if (t == 0) sweep_decide(ctrl, k - 1, tot, hist, hist_len);
+    return;
+  }
+  const float* prev = state3 + (size_t)((k - 1) % 3) * nports * 2;
+  float* cur = state3 + (size_t)(k % 3) * nports * 2;
   // incident waves and residual terms of sweep k - 1; the outputs start at c
 #pragma unroll
   for (int m = 0; m < PPL; ++m) {
@@ -1300,20 +1352,7 @@ __global__ void __launch_bounds__(256, PPL == 4 ? 4 : 3) sweep_wsym_kernel(
     const int s = lane + 32 * m;
     if (s < p) *reinterpret_cast<float2*>(cur + 2 * (size_t)(p0 + s)) = make_float2(w_in[s], acc[s]);
   }
-  if (valid && lane == 0) {
-    partials[dsc.tile] = (double)tile_sq;
-    __threadfence();
-  }
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    s_last = atomicAdd(&ctrl->counter, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  const double tot = block_sum_fixed<128>(partials, nparts);
-  if (tid == 0) sweep_decide(ctrl, k, tot, hist, hist_len);
+  if (valid && lane == 0) partials2[(size_t)(k & 1) * nparts + dsc.tile] = (double)tile_sq;
 }
 
 // ---------------------------------------------------------------------------
@@ -1357,10 +1396,9 @@ __device__ __forceinline__ bool flow_wait_ready(const int* gk, const int* done,
         if (lane == 0) atomicCAS(&ctrl->flag, 0, 5);
         return false;
       }
-      if ((i & 15u) == 15u) {
-        if (*((volatile int*)&ctrl->flag)) return false;
-        __nanosleep(32);
-      }
+      if ((i & 15u) == 15u && *((volatile int*)&ctrl->flag)) return false;
+      // back off: a spinning warp takes issue slots from the warps that work
+      if (i >= 2) __nanosleep(i < 16 ? 64 : 256);
     }
   }
   return true;
@@ -1447,6 +1485,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) sweep_flow_kernel(
           *reinterpret_cast<float2*>(cur + 2 * (size_t)(p0 + s)) = make_float2(w_in[s], acc);
         }
       }
+      __threadfence();  // this thread's waves are visible device-wide before the done counter moves
       __syncthreads();
       if (tid == 0) {
         part4[(size_t)(k & 3) * nparts + tile] = tile_sq;
@@ -1465,6 +1504,174 @@ __global__ void __launch_bounds__(NT, 768 / NT) sweep_flow_kernel(
           atomicExch(gk, k);
         }
         __syncthreads();
+      }
+    }
+  }
+}
+
+// Dataflow sweeps with one warp per tile (every tile resident: one warp each,
+// kWflowWarps per CTA, a cooperative launch per inner solve).  Each warp runs
+// the sweeps of its own tile: it waits (flow_wait_ready) until the tiles
+// across its lines have finished sweep k - 1 and the published decision has
+// reached sweep k - 2, then gathers, streams its blocks and publishes its done
+// counter.  The tile's blocks are the same for every sweep, so its cp.async
+// ring runs on across sweep boundaries: the blocks of sweep k + 1 are in
+// flight while the warp publishes sweep k and waits for its neighbours.
+// Waves live in three slots, as for sweep_flow_kernel.  The residual of sweep
+// k - 1 (computed in sweep k) is reduced in two fixed-order levels off the
+// critical path: the last tile of each group of G tiles sums the group's
+// partials, the last group sums the group sums and publishes the decision.
+// Block arithmetic and order are those of kernel 9 (the iterates match it
+// bitwise; the residual sums differ by their order only).
+template <class TT, int KB, bool ASYNC>
+__global__ void __launch_bounds__(32 * kWflowWarps, kWflowCtasPerSm) sweep_wflow_kernel(
+    const TT* __restrict__ Tp, const TileDesc* __restrict__ tdesc,
+    const int32_t* __restrict__ twin, const float2* __restrict__ kd,
+    const uint8_t* __restrict__ run, const float* __restrict__ c, float* __restrict__ state3,
+    int64_t nports, const int32_t* __restrict__ nbr_off, const int32_t* __restrict__ nbr,
+    int* __restrict__ done, unsigned* __restrict__ count, int* __restrict__ gk,
+    unsigned* __restrict__ gcount, double* __restrict__ gsum, int G,
+    SweepCtrl* __restrict__ ctrl, double* __restrict__ part4, double* __restrict__ hist,
+    int hist_len, int nparts, int pp_max, int k0) {
+  using LD = SymLoad<TT>;
+  constexpr int B = kSymB;
+  constexpr int PPL = 4;
+  constexpr unsigned FULL = 0xffffffffu;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = blockIdx.x * kWflowWarps + warp;
+  if (g >= nparts) return;  // no CTA barrier below: idle warps just leave
+  const TileDesc dsc = tdesc[g];
+  const int tile = dsc.tile, p0 = dsc.p0, p = dsc.p;
+  const int nb = (p + B - 1) / B;
+  const int nblk = nb * (nb + 1) / 2;
+  const TT* Tl = Tp + dsc.Tp_off;
+  TT* ring = reinterpret_cast<TT*>(smem_raw + (size_t)warp * (KB * B * B * sizeof(TT) + 12 * (size_t)pp_max));
+  float* w_in = reinterpret_cast<float*>(ring + KB * B * B);
+  float* rs = w_in + pp_max;
+  float* acc = rs + pp_max;
+  const int ngroups = (nparts + G - 1) / G;
+  const int grp = g / G;
+  const unsigned gsize = (unsigned)min(G, nparts - grp * G);
+  const int e0 = ASYNC ? 0 : nbr_off[tile], e1 = ASYNC ? 0 : nbr_off[tile + 1];
+  int tw[PPL];
+  uint32_t rn4 = 0;
+#pragma unroll
+  for (int m = 0; m < PPL; ++m) {
+    const int s = lane + 32 * m;
+    tw[m] = s < p ? twin[p0 + s] : 0;
+    if (s < p) rn4 |= (uint32_t)run[p0 + s] << (8 * m);
+  }
+  // the block stream of the tile repeats every sweep: block number q of the
+  // stream is block q mod nblk of the tile, in ring slot q mod KB; qn and bn
+  // are the stream number and tile block of the next copy to issue
+  int q = 0, qn = 0, bn = 0;
+  auto issue = [&]() {
+    if (nblk) copy_block_async(ring + (qn % KB) * B * B, Tl + (size_t)bn * B * B, lane);
+    cp_async_commit_group();
+    ++qn;
+    if (++bn == nblk) bn = 0;
+  };
+#pragma unroll
+  for (int b = 0; b < KB - 1; ++b) issue();
+  for (int k = k0;; ++k) {
+    const bool ok = flow_wait_ready(gk, done, nbr, e0, e1, k, ctrl);
+    __threadfence();  // every lane that saw a counter orders its later reads
+    int stop = 0;
+    if (lane == 0) stop = (ok && !*((volatile int*)&ctrl->flag)) ? 0 : 1;
+    if (__shfl_sync(FULL, stop, 0)) {
+      cp_async_wait_group<0>();  // no copy into shared memory outlives the warp
+      return;
+    }
+    const float* prev = state3 + (ASYNC ? 0 : (size_t)((k - 1) % 3) * nports * 2);
+    float* cur = state3 + (ASYNC ? 0 : (size_t)(k % 3) * nports * 2);
+#pragma unroll
+    for (int m = 0; m < PPL; ++m) {
+      const int s = lane + 32 * m;
+      if (s < nb * B) {
+        float wi = 0.f, rc = 0.f, c0 = 0.f;
+        if (s < p) {
+          c0 = c[p0 + s];
+          if (k > 1) {
+            const float2 wt = __ldcg(reinterpret_cast<const float2*>(prev + 2 * (size_t)tw[m]));
+            const float2 ws = __ldcg(reinterpret_cast<const float2*>(prev + 2 * (size_t)(p0 + s)));
+            wi = wt.y;
+            rc = port_residual<float>(ws.x, ws.y, wt.x, wt.y, kd[p0 + s]);
+          }
+        }
+        w_in[s] = wi;
+        rs[s] = rc;
+        acc[s] = c0;
+      }
+    }
+    __syncwarp();
+    float tile_sq = 0.f;
+    if (k > 1) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        float sq = 0.f;
+        const int s = lane + 32 * v;
+        const int nr = (rn4 >> (8 * v)) & 0xff;
+        if (s < p && nr) {
+          float rr = 0.f;
+          for (int qq = 0; qq < nr; ++qq) rr += rs[s + qq];
+          sq += rr * rr;
+        }
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(FULL, sq, o);
+        tile_sq += sq;
+      }
+    }
+    const AccSink sink{acc};
+    int bi = 0, bj = 0;
+    for (int kk = 0; kk < nblk; ++kk, ++q) {
+      issue();  // stream number q + KB - 1
+      cp_async_wait_group<KB - 1>();  // this lane's bytes of block kk have landed
+      sym_apply<TT>(LD::load_shared(ring + (q % KB) * B * B, lane), bi, bj, lane, w_in, sink);
+      __syncwarp();  // the next block may add to the same outputs from other lanes
+      if (++bj == nb) bj = ++bi;
+    }
+#pragma unroll
+    for (int m = 0; m < PPL; ++m) {
+      const int s = lane + 32 * m;
+      if (s < p) *reinterpret_cast<float2*>(cur + 2 * (size_t)(p0 + s)) = make_float2(w_in[s], acc[s]);
+    }
+    // publish: partial, done counter, then the two-level residual sum (every
+    // lane's waves are visible device-wide before the done counter moves)
+    __threadfence();
+    __syncwarp();
+    int last = 0;
+    if (lane == 0) {
+      part4[(size_t)(k & 3) * nparts + g] = (double)tile_sq;
+      __threadfence();
+      atomicExch(done + tile, k);
+      last = atomicAdd(gcount + (k & 3) * 32 + grp, 1u) == gsize - 1;
+    }
+    if (__shfl_sync(FULL, last, 0)) {
+      __threadfence();
+      const double* pg = part4 + (size_t)(k & 3) * nparts + (size_t)grp * G;
+      double s = 0.0;
+      for (int i = lane; i < (int)gsize; i += 32) s += __ldcg(pg + i);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(FULL, s, o);
+      int top = 0;
+      if (lane == 0) {
+        gsum[(k & 3) * 32 + grp] = s;
+        __threadfence();
+        top = atomicAdd(count + (k & 3), 1u) == (unsigned)ngroups - 1;
+      }
+      if (__shfl_sync(FULL, top, 0)) {
+        __threadfence();
+        double t = lane < ngroups ? __ldcg(gsum + (k & 3) * 32 + lane) : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(FULL, t, o);
+        // counters of sweep k + 2 start from zero before anyone may finish it
+        gcount[((k + 2) & 3) * 32 + lane] = 0u;
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) {
+          count[(k + 2) & 3] = 0u;
+          sweep_decide(ctrl, k, t, hist, hist_len);
+          __threadfence();
+          atomicExch(gk, k);
+        }
       }
     }
   }
@@ -1523,7 +1730,7 @@ static void launch_sweep(vtm_plan_s* P, const TT* T, const WT* c, WT* state, int
 }
 
 // Scoped access-policy window on the plan's stream over the FP32/16-bit
-// reflection matrices: a persisting L2 carve-out of up to the device's
+// reflection matrices (their packed copy where the plan has one): a persisting L2 carve-out of up to the device's
 // maximum is requested for this context and released (with the stream
 // attribute and the previous limit) when the sweeps end.
 struct L2Window {
@@ -1532,8 +1739,11 @@ struct L2Window {
   bool active = false;
   L2Window(vtm_plan_s* P, int prec) {
     if (prec == VTM_PREC_FP64 || P->opts.l2_persist == 1 || !P->stream) return;
-    const void* base = prec == VTM_PREC_FP32 ? P->d_T32.p : P->d_T16.p;
-    const size_t bytes = prec == VTM_PREC_FP32 ? P->d_T32.bytes : P->d_T16.bytes;
+    // the packed copy when there is one (the packed kernels read only that)
+    const DevBuf& full = prec == VTM_PREC_FP32 ? P->d_T32 : P->d_T16;
+    const DevBuf& packed = prec == VTM_PREC_FP32 ? P->d_Tp32 : P->d_Tp16;
+    const void* base = packed.p ? packed.p : full.p;
+    const size_t bytes = packed.p ? packed.bytes : full.bytes;
     int maxp = 0, maxw = 0;
     if (cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, P->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, P->device) != cudaSuccess ||
@@ -1648,10 +1858,21 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   const int tbuf_elems = nb_max * (nb_max + 1) / 2 * kSymB * kSymB;
   const size_t symb_smem = (size_t)tbuf_elems * (prec == VTM_PREC_FP32 ? 4 : 2) + sym_smem;
   const bool symb_ok = sym_ok && symb_smem <= 160 * 1024;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
   // one warp per tile: per warp a ring of blocks, w_in, residual terms and
-  // outputs of the tile; the variant for this precision and tile size
-  const size_t wsym_smem =
-      8 * ((size_t)(prec == VTM_PREC_FP32 ? kWsymKB32 * 4 : kWsymKB16 * 2) * kSymB * kSymB + 12 * (size_t)pp_max);
+  // outputs of the tile.  One CTA per SM holds ceil(nparts / SMs) tile warps
+  // (at most 28, and what shared memory holds) and four service warps, so
+  // every SM carries the same number of tiles; the variant for this
+  // precision and tile size
+  const size_t wsym_per_warp =
+      (size_t)(prec == VTM_PREC_FP32 ? kWsymKB32 * 4 : kWsymKB16 * 2) * kSymB * kSymB + 12 * (size_t)pp_max;
+  int wsym_warps = std::min(28, std::max(1, (P->nparts + sms - 1) / sms));
+  wsym_warps = std::max(1, std::min(wsym_warps, (int)(220 * 1024 / wsym_per_warp)));
+  const int wsym_grid = (P->nparts + wsym_warps - 1) / wsym_warps;
+  const int wsym_threads = 32 * (wsym_warps + 4);
+  const size_t wsym_smem = wsym_warps * wsym_per_warp;
+  const size_t wflow_smem = kWflowWarps * wsym_per_warp;
   auto with_wsym = [&](auto fn) {
     const bool wide = pp_max > 128;
     if (prec == VTM_PREC_FP32) {
@@ -1670,8 +1891,6 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
     VTM_CUDA_TRY(cudaFuncSetAttribute(staged_kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st_smem));
   const int st_threads = 256;
   const int64_t npt_ = npt;
-  int sms = 152;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
   int st_grid = 0;
   auto launch_staged = [&](auto* kern, const auto* T, const auto* c, auto* state) {
     if (!st_grid) {
@@ -1709,9 +1928,9 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
     }
     if (kc == 9) {
       with_wsym([&](auto* kern, const auto* Tp) {
-        launch_packed(P, kern, (P->nparts + 7) / 8, 256, wsym_smem, s, Tp, P->d_tdesc.as<TileDesc>(),
+        launch_packed(P, kern, wsym_grid, wsym_threads, wsym_smem, s, Tp, P->d_tdesc.as<TileDesc>(),
                       P->d_twin.as<int32_t>(), P->d_kd32.as<float2>(), P->d_run.as<uint8_t>(),
-                      P->d_c32.as<float>(), P->d_state32.as<float>(), npt_, P->d_ctrl.as<SweepCtrl>(),
+                      P->d_c32.as<float>(), P->d_fstate32.as<float>(), npt_, P->d_ctrl.as<SweepCtrl>(),
                       P->d_partials.as<double>(), hist, hist_len, P->nparts, pp_max);
       });
       return;
@@ -1811,16 +2030,50 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
     cudaGetLastError();
   }
   const bool flow_ok = flow_grid > 0;
-  if (flow_ok) {
-    VTM_TRY(dev_alloc(P->d_done, (size_t)P->nparts * sizeof(int)));
-    VTM_TRY(dev_alloc(P->d_flow, 64));
-    VTM_TRY(dev_alloc(P->d_part4, 4 * (size_t)P->nparts * sizeof(double)));
-    VTM_TRY(dev_alloc(P->d_fstate32, 6 * (size_t)std::max<int64_t>(npt, 1) * sizeof(float)));
+  // dataflow sweeps with one warp per tile: every tile resident at once
+  const bool async = P->opts.method == VTM_METHOD_ASYNC;
+  const void* wflow_kfn = nullptr;
+  if (pp_max <= 128) {
+    if (prec == VTM_PREC_FP32)
+      wflow_kfn = async ? (const void*)sweep_wflow_kernel<float, kWsymKB32, true>
+                        : (const void*)sweep_wflow_kernel<float, kWsymKB32, false>;
+    else if (prec == VTM_PREC_BF16)
+      wflow_kfn = async ? (const void*)sweep_wflow_kernel<__nv_bfloat16, kWsymKB16, true>
+                        : (const void*)sweep_wflow_kernel<__nv_bfloat16, kWsymKB16, false>;
+    else if (prec == VTM_PREC_FP16)
+      wflow_kfn = async ? (const void*)sweep_wflow_kernel<__half, kWsymKB16, true>
+                        : (const void*)sweep_wflow_kernel<__half, kWsymKB16, false>;
   }
+  int wflow_grid = 0;
+  if (sym_ok && wflow_kfn) {
+    int coop = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, P->device);
+    const int need = (P->nparts + kWflowWarps - 1) / kWflowWarps;
+    if (coop &&
+        cudaFuncSetAttribute(wflow_kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wflow_smem) ==
+            cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wflow_kfn, 32 * kWflowWarps, wflow_smem) ==
+            cudaSuccess &&
+        per_sm * sms >= need)
+      wflow_grid = need;
+    cudaGetLastError();
+  }
+  const bool wflow_ok = wflow_grid > 0;
+  // counters of the dataflow kernels: 4 sweep counters, the published
+  // decision (byte 32), 4 x 32 group counters (byte 64), 4 x 32 group sums
+  // (byte 576)
+  constexpr size_t kFlowBytes = 2048;
+  if (flow_ok || wflow_ok) {
+    VTM_TRY(dev_alloc(P->d_done, (size_t)P->nparts * sizeof(int)));
+    VTM_TRY(dev_alloc(P->d_flow, kFlowBytes));
+    VTM_TRY(dev_alloc(P->d_part4, 4 * (size_t)P->nparts * sizeof(double)));
+  }
+  // three wave slots: the dataflow kernels and the one-warp-per-tile sweeps
+  if (sym_ok) VTM_TRY(dev_alloc(P->d_fstate32, 6 * (size_t)std::max<int64_t>(npt, 1) * sizeof(float)));
   // one cooperative launch runs sweeps 1.. until a flag (k_max in ctrl)
   auto launch_flow = [&]() -> cudaError_t {
     cudaMemsetAsync(P->d_done.p, 0, (size_t)P->nparts * sizeof(int), s);
-    cudaMemsetAsync(P->d_flow.p, 0, 64, s);
+    cudaMemsetAsync(P->d_flow.p, 0, kFlowBytes, s);
     const void* Tp = prec == VTM_PREC_FP32 ? P->d_Tp32.p : P->d_Tp16.p;
     const TileDesc* td = P->d_tdesc.as<TileDesc>();
     const int32_t* tw = P->d_twin.as<int32_t>();
@@ -1851,9 +2104,39 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
                               (const void*)sweep_flow_kernel<__half, 128, 8, false>));
     return cudaLaunchCooperativeKernel(kfn, flow_grid, 128, args, sym_smem, s);
   };
+  // the same with one warp per tile (kernel 10): one cooperative launch per
+  // inner solve; the residual's group size G keeps at most 32 groups
+  auto launch_wflow = [&]() -> cudaError_t {
+    cudaMemsetAsync(P->d_done.p, 0, (size_t)P->nparts * sizeof(int), s);
+    cudaMemsetAsync(P->d_flow.p, 0, kFlowBytes, s);
+    const void* Tp = prec == VTM_PREC_FP32 ? P->d_Tp32.p : P->d_Tp16.p;
+    const TileDesc* td = P->d_tdesc.as<TileDesc>();
+    const int32_t* tw = P->d_twin.as<int32_t>();
+    const float2* kdp = P->d_kd32.as<float2>();
+    const uint8_t* rn = P->d_run.as<uint8_t>();
+    const float* cp = P->d_c32.as<float>();
+    float* st3 = P->d_fstate32.as<float>();
+    const int32_t* no = P->d_nbr_off.as<int32_t>();
+    const int32_t* nbp = P->d_nbr.as<int32_t>();
+    int* dn = P->d_done.as<int>();
+    unsigned char* fb = reinterpret_cast<unsigned char*>(P->d_flow.p);
+    unsigned* cnt = reinterpret_cast<unsigned*>(fb);
+    int* gkp = reinterpret_cast<int*>(fb + 32);
+    unsigned* gcnt = reinterpret_cast<unsigned*>(fb + 64);
+    double* gs = reinterpret_cast<double*>(fb + 576);
+    int G = std::max(1, (P->nparts + 31) / 32);
+    SweepCtrl* ct = P->d_ctrl.as<SweepCtrl>();
+    double* p4 = P->d_part4.as<double>();
+    int np = P->nparts, ppm = pp_max, hl = hist_len, k0 = 1;
+    int64_t npv = npt_;
+    double* hp = hist;
+    void* args[] = {&Tp, &td, &tw, &kdp, &rn, &cp, &st3, &npv, &no, &nbp, &dn, &cnt, &gkp, &gcnt, &gs, &G,
+                    &ct, &p4, &hp, &hl, &np, &ppm, &k0};
+    return cudaLaunchCooperativeKernel(wflow_kfn, wflow_grid, 32 * kWflowWarps, args, wflow_smem, s);
+  };
   const bool symload = ((choice == 5 || choice == 6 || choice == 9) && sym_ok) || (choice == 7 && symb_ok) ||
-                       (choice == 8 && flow_ok);
-  if (P->opts.method == VTM_METHOD_ASYNC && !flow_ok) {
+                       (choice == 8 && flow_ok) || (choice == 10 && wflow_ok);
+  if (P->opts.method == VTM_METHOD_ASYNC && !flow_ok && !wflow_ok) {
     set_detail("vtm_solve: asynchronous VTM runs on the packed symmetric dataflow kernel: it needs "
                "FP32/BF16/FP16 sweeps of a symmetric plan with at most 256 ports per sub-circuit");
     return VTM_EINVAL;
@@ -1874,7 +2157,7 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   }
 
   int kern = (vecload || symload) ? choice : (staged ? 2 : 1);
-  if (P->opts.method == VTM_METHOD_ASYNC) kern = 8;  // its own iteration: not autotuned
+  if (P->opts.method == VTM_METHOD_ASYNC) kern = wflow_ok ? 10 : 8;  // its own iteration: not autotuned
   else if (P->opts.sweep_kernel == 0) {
     if (P->tuned_kernel[prec] == 0) {
       const bool can_st = nv_max <= 4 * 256 && st_smem <= 200 * 1024;
@@ -1882,12 +2165,12 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
       const bool can_vec128 = nv_max <= 128;
       float best = 1e30f;
       int best_k = 1;
-      for (int cand = 1; cand <= 9; ++cand) {
+      for (int cand = 1; cand <= 10; ++cand) {
         if ((cand == 2 && !can_st) || (cand == 3 && !can_vec) || (cand == 4 && !can_vec128) ||
             ((cand == 5 || cand == 6 || cand == 9) && !sym_ok) || (cand == 7 && !symb_ok) ||
-            (cand == 8 && !flow_ok))
+            (cand == 8 && !flow_ok) || (cand == 10 && !wflow_ok))
           continue;
-        if (cand == 8) {  // one launch of 8 sweeps, per-sweep time compared with the others' 6
+        if (cand == 8 || cand == 10) {  // one launch of 8 sweeps, per-sweep time against the others' 6
           SweepCtrl t = h;
           t.k_max = 8;
           t.tol2 = -1.0;
@@ -1895,7 +2178,7 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
           *P->h_ctrl = t;
           VTM_CUDA_TRY(cudaMemcpyAsync(P->d_ctrl.p, P->h_ctrl, sizeof(SweepCtrl), cudaMemcpyHostToDevice, s));
           VTM_CUDA_TRY(cudaEventRecord(P->evs0, s));
-          VTM_CUDA_TRY(launch_flow());
+          VTM_CUDA_TRY(cand == 10 ? launch_wflow() : launch_flow());
           VTM_CUDA_TRY(cudaEventRecord(P->evs1, s));
           VTM_CUDA_TRY(cudaEventSynchronize(P->evs1));
           float ms = 0.f;
@@ -1954,9 +2237,10 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, staged_kfn, st_threads, st_smem);
     st_grid = std::max(1, std::min(P->nparts, std::max(per_sm, 1) * sms));
   }
-  if (kern == 8) {
+  P->dataflow_kernel = kern;
+  if (kern == 8 || kern == 10) {
     VTM_CUDA_TRY(cudaEventRecord(P->evs0, s));
-    VTM_CUDA_TRY(launch_flow());
+    VTM_CUDA_TRY(kern == 10 ? launch_wflow() : launch_flow());
     VTM_CUDA_TRY(cudaEventRecord(P->evs1, s));
     VTM_CUDA_TRY(cudaMemcpyAsync(P->h_ctrl, P->d_ctrl.p, sizeof(SweepCtrl), cudaMemcpyDeviceToHost, s));
     VTM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -2032,9 +2316,12 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   *flag_out = r.flag;
   if (r.flag == 1 || r.flag == 4) *sweep_out = r.conv_sweep;
   else *sweep_out = std::min(r.k - 1, budget);
-  P->wave_slot = prec == VTM_PREC_FP64
-                     ? (const void*)(P->d_state64.as<double>() + (size_t)(*sweep_out & 1) * npt * 2)
-                     : (const void*)(P->d_state32.as<float>() + (size_t)(*sweep_out & 1) * npt * 2);
+  if (prec == VTM_PREC_FP64)
+    P->wave_slot = P->d_state64.as<double>() + (size_t)(*sweep_out & 1) * npt * 2;
+  else if (kern == 9)  // three slots
+    P->wave_slot = P->d_fstate32.as<float>() + (size_t)(*sweep_out % 3) * npt * 2;
+  else
+    P->wave_slot = P->d_state32.as<float>() + (size_t)(*sweep_out & 1) * npt * 2;
   return VTM_OK;
 }
 

@@ -236,7 +236,8 @@ def test_every_sweep_kernel_matches_oracle(vtm, kernel):
                                                     ("fp16", 5, (192, 48)), ("fp16", 6, (90, 18)),
                                                     ("fp16", 7, (90, 18)), ("fp16", 8, (192, 48)),
                                                     ("fp32", 9, (90, 18)), ("fp32", 9, (192, 48)),
-                                                    ("bf16", 9, (90, 18)), ("fp16", 9, (192, 48))])
+                                                    ("bf16", 9, (90, 18)), ("fp16", 9, (192, 48)),
+                                                    ("fp32", 10, (90, 18)), ("fp16", 10, (192, 32))])
 def test_packed_symmetric_sweeps_follow_the_oracle(vtm, precision, kernel, shape):
     # T_P is symmetric (scalar W, symmetric A): the packed kernels read the
     # 16x16 blocks on and above the diagonal only.  18x18 tiles have 72, 54 or
@@ -265,23 +266,27 @@ def test_packed_symmetric_sweeps_follow_the_oracle(vtm, precision, kernel, shape
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
 def test_dataflow_and_warp_per_tile_sweeps_repeat_kernel_5_bitwise(vtm, precision):
-    # one cooperative launch with per-tile neighbour waits (8), and one warp per
-    # tile adding its partials in block order (9), compute the same iterates as
-    # four warps per tile (5): same block arithmetic, same fixed-order
-    # reductions, same decisions
+    # one cooperative launch with per-tile neighbour waits (8), one warp per
+    # tile adding its partials in block order (9), and its dataflow form (10)
+    # compute the same iterates as four warps per tile (5): same block
+    # arithmetic, same fixed-order sums of the outputs; 8 and 9 also reduce the
+    # residual in kernel 5's order, 10 in two fixed-order levels of its own
     w = wl.power_grid(256, 256, 32, 32, Zc=1.0, seed=17)
     out = []
-    for kernel in (5, 8, 9):
+    for kernel in (5, 8, 9, 10):
         plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc,
                         precision=precision, sweep_kernel=kernel)
         plan.set_options(history_len=64)
         x, info = plan.solve(torch.from_numpy(w.b[0]).cuda(), tol=1e-10)
         assert plan.stats()["sweep_kernel"] == kernel
-        out.append((x, info["sweeps"], info["outer_steps"], plan.history))
-    for o in out[1:]:
-        assert out[0][1:3] == o[1:3]
-        assert np.array_equal(out[0][3], o[3])
-        assert torch.equal(out[0][0], o[0])
+        out.append((kernel, x, info["sweeps"], info["outer_steps"], plan.history))
+    for kernel, x, sweeps, steps, hist in out[1:]:
+        assert (sweeps, steps) == out[0][2:4]
+        if kernel == 10:
+            assert np.allclose(hist, out[0][4], rtol=1e-12, atol=0)
+        else:
+            assert np.array_equal(hist, out[0][4])
+        assert torch.equal(x, out[0][1])
 
 
 @pytest.mark.parametrize("precision,kernel", [("fp32", 5), ("fp32", 6), ("fp16", 7), ("bf16", 7), ("fp16", 9)])
@@ -316,7 +321,7 @@ def test_bad_options_are_rejected_and_the_plan_keeps_its_own(vtm):
     w = wl.power_grid(64, 64, 32, 32, Zc=1.0, seed=15)
     plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc)
     with pytest.raises(vtm.VTMError):
-        plan.set_options(sweep_kernel=10)
+        plan.set_options(sweep_kernel=11)
     with pytest.raises(vtm.VTMError):
         plan.set_options(sweep_kernel=-1)
     for bad in (4, 5, -1):
