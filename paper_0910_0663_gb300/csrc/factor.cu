@@ -273,10 +273,130 @@ __global__ void __launch_bounds__(32) band_solve_stream_kernel(
   for (int i = lane; i < n; i += 32) vg[i] = x[i];
 }
 
+// Band solves of bandwidth <= 32 in 32-row blocks held in registers: lane l
+// keeps row J + l of the current block and row J + 32 + l of the next one.
+// Step q of a block broadcasts u = v(J + q) from lane q (a shuffle, the only
+// serial link of the row chain) and every lane applies one multiplier of
+// column J + q: lanes l > q to their own row (offset l - q), lanes l <= q to
+// the next block's row (offset 32 + l - q, still within the band).  Each
+// lane therefore reads exactly one multiplier per column, loaded kPfD
+// columns ahead into a rotating register buffer.  The updates of every row
+// arrive in increasing column order, as in warp_band_solve_pf, so the
+// results are those of the column sweep.  The backward pass runs the same
+// steps in reversed row order over Uc; y lives in shared memory between the
+// passes.
+constexpr int kPfD = 16;  // columns of multipliers in flight per lane
+
+// Read-only loads and broadcasts as ordered (volatile) instructions: the
+// prefetch distance is then what the code says (kPfD loads in flight), not
+// the whole unrolled block hoisted into registers.
+__device__ __forceinline__ float ld_nc_if(const float* p, bool ok) {
+  float v = 0.f;
+  asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %2, 0;\n @q ld.global.nc.f32 %0, [%1];\n}"
+               : "+f"(v) : "l"(p), "r"((int)ok));
+  return v;
+}
+__device__ __forceinline__ double ld_nc_if(const double* p, bool ok) {
+  double v = 0.0;
+  asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %2, 0;\n @q ld.global.nc.f64 %0, [%1];\n}"
+               : "+d"(v) : "l"(p), "r"((int)ok));
+  return v;
+}
+__device__ __forceinline__ float shfl_idx_ordered(float x, int src) {
+  float r;
+  asm volatile("shfl.sync.idx.b32 %0, %1, %2, 0x1f, 0xffffffff;" : "=f"(r) : "f"(x), "r"(src));
+  return r;
+}
+__device__ __forceinline__ double shfl_idx_ordered(double x, int src) {
+  int lo = __double2loint(x), hi = __double2hiint(x);
+  asm volatile("shfl.sync.idx.b32 %0, %0, %1, 0x1f, 0xffffffff;" : "+r"(lo) : "r"(src));
+  asm volatile("shfl.sync.idx.b32 %0, %0, %1, 0x1f, 0xffffffff;" : "+r"(hi) : "r"(src));
+  return __hiloint2double(hi, lo);
+}
+
+template <class FT, bool FWD>
+__device__ __forceinline__ void band_pass_reg(const FT* __restrict__ colbase, int n, int bw, int B,
+                                              const FT* __restrict__ vin, FT* ysm, FT* __restrict__ vout,
+                                              int lane) {
+  // pass coordinate j: row j (forward) or n - 1 - j (backward)
+  auto src = [&](int j) -> FT { return j < n ? (FWD ? vin[j] : ysm[n - 1 - j]) : FT(0); };
+  auto diag = [&](int j) -> FT { return j < n ? __ldg(colbase + (ptrdiff_t)(FWD ? j : n - 1 - j) * B) : FT(0); };
+  // this lane's multiplier of pass column j = jb + q: offset a = l - q (own
+  // row) or 32 + l - q (the next block's row), that is ((l - q - 1) mod 32) +
+  // 1; it exists while a <= min(bw, n - 1 - j).  `ln` and `cs` are opaque
+  // per-block copies of the lane and the column stride, so that what depends
+  // only on (lane, q) is recomputed each block instead of being held in
+  // registers for all 32 steps.
+  auto load_col = [&](int jb, int q, int ln, int cs) -> FT {
+    const int j = jb + q;
+    const int a = ((ln - q - 1) & 31) + 1;
+    const FT* c = colbase + (ptrdiff_t)(FWD ? j : n - 1 - j) * cs;
+    return ld_nc_if(c + a, j < n && a <= min(bw, n - 1 - j));
+  };
+  FT buf[kPfD];
+#pragma unroll
+  for (int d = 0; d < kPfD; ++d) buf[d] = load_col(0, d, lane, B);
+  FT dg = diag(lane);
+  FT xc = src(lane), xn = src(32 + lane);
+  for (int J = 0; J < n; J += 32) {
+    int ln = lane, cs = B;
+    asm volatile("" : "+r"(ln), "+r"(cs));
+    const FT dg_next = diag(J + 32 + lane);
+    const FT x_after = src(J + 64 + lane);
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      const FT mq = buf[q % kPfD];
+      buf[q % kPfD] = load_col(J, q + kPfD, ln, cs);  // column J + q + kPfD
+      if (J + q < n) {
+        const FT u = shfl_idx_ordered(xc, q);
+        if (lane > q) xc -= mq * u;
+        else xn -= mq * u;
+      }
+    }
+    if (J + lane < n) {
+      const FT y = xc * dg;
+      if (FWD) ysm[J + lane] = y;
+      else vout[n - 1 - (J + lane)] = y;
+    }
+    xc = xn;
+    xn = x_after;
+    dg = dg_next;
+  }
+}
+
+template <class FT>
+__global__ void __launch_bounds__(32, 28) band_solve_reg_kernel(
+    const int32_t* __restrict__ node_off, const int32_t* __restrict__ bwv,
+    const int64_t* __restrict__ band_off, const FT* __restrict__ Lc, const FT* __restrict__ Uc,
+    FT* __restrict__ v, int64_t stride, int nparts) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  FT* ysm = reinterpret_cast<FT*>(smem_raw);
+  const int t = blockIdx.x % nparts;
+  const int colr = blockIdx.x / nparts;
+  const int off = node_off[t];
+  const int n = node_off[t + 1] - off;
+  const int bw = bwv[t];
+  const int lane = threadIdx.x;
+  FT* vg = v + (size_t)colr * stride + off;
+  band_pass_reg<FT, true>(Lc + band_off[t], n, bw, bw + 1, vg, ysm, vg, lane);
+  __syncwarp();
+  band_pass_reg<FT, false>(Uc + band_off[t], n, bw, bw + 1, vg, ysm, vg, lane);
+}
+
 template <class FT>
 static void launch_band_solve_t(vtm_plan_s* P, FT* v, const FT* Lc, const FT* Uc, int ncols,
                                 int64_t stride, cudaStream_t s) {
   P->launch_count++;
+  if (sizeof(FT) == 4 && P->max_bw <= 32) {
+    const size_t smem = (size_t)std::max(P->max_nodes, 1) * sizeof(FT);
+    if (smem <= 200 * 1024) {
+      cudaFuncSetAttribute(band_solve_reg_kernel<FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      band_solve_reg_kernel<FT><<<P->nparts * ncols, 32, smem, s>>>(
+          P->tabs.node_off.as<int32_t>(), P->tabs.bw.as<int32_t>(), P->tabs.band_off.as<int64_t>(), Lc, Uc, v,
+          stride, P->nparts);
+      return;
+    }
+  }
   // FP32 only: an FP64 solve is bound by GB300's FP64 pipe, where the
   // register-prefetch kernel (more resident warps) does better
   if (sizeof(FT) == 4 && P->max_bw <= 64) {
