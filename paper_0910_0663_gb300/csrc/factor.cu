@@ -302,6 +302,16 @@ __device__ __forceinline__ double ld_nc_if(const double* p, bool ok) {
                : "+d"(v) : "l"(p), "r"((int)ok));
   return v;
 }
+__device__ __forceinline__ float ld_nc(const float* p) {
+  float v;
+  asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double ld_nc(const double* p) {
+  double v;
+  asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
 __device__ __forceinline__ float shfl_idx_ordered(float x, int src) {
   float r;
   asm volatile("shfl.sync.idx.b32 %0, %1, %2, 0x1f, 0xffffffff;" : "=f"(r) : "f"(x), "r"(src));
@@ -343,14 +353,36 @@ __device__ __forceinline__ void band_pass_reg(const FT* __restrict__ colbase, in
     asm volatile("" : "+r"(ln), "+r"(cs));
     const FT dg_next = diag(J + 32 + lane);
     const FT x_after = src(J + 64 + lane);
+    if (bw == 32 && J + 96 <= n) {
+      // interior block of a full band: every multiplier loaded here exists.
+      // Element of the multiplier of column jj for this lane, from colbase:
+      // (jj or n - 1 - jj) 33 + a with a = ((l - jj - 1) mod 32) + 1; from
+      // one column to the next a drops by one, wrapping from 1 to 32, so the
+      // element moves by 32 or 64 (forward) or -34 or -2 (backward)
+      const int jj0 = J + kPfD;
+      int a = ((ln - jj0 - 1) & 31) + 1;
+      int e = (FWD ? jj0 : n - 1 - jj0) * 33 + a;
 #pragma unroll
-    for (int q = 0; q < 32; ++q) {
-      const FT mq = buf[q % kPfD];
-      buf[q % kPfD] = load_col(J, q + kPfD, ln, cs);  // column J + q + kPfD
-      if (J + q < n) {
+      for (int q = 0; q < 32; ++q) {
+        const FT mq = buf[q % kPfD];
+        buf[q % kPfD] = ld_nc(colbase + e);  // column J + q + kPfD
+        const bool wrap = a == 1;
+        e += FWD ? (wrap ? 64 : 32) : (wrap ? -2 : -34);
+        a = wrap ? 32 : a - 1;
         const FT u = shfl_idx_ordered(xc, q);
         if (lane > q) xc -= mq * u;
         else xn -= mq * u;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const FT mq = buf[q % kPfD];
+        buf[q % kPfD] = load_col(J, q + kPfD, ln, cs);  // column J + q + kPfD
+        if (J + q < n) {
+          const FT u = shfl_idx_ordered(xc, q);
+          if (lane > q) xc -= mq * u;
+          else xn -= mq * u;
+        }
       }
     }
     if (J + lane < n) {
