@@ -279,8 +279,8 @@ __global__ void __launch_bounds__(32) band_solve_stream_kernel(
 // serial link of the row chain) and every lane applies one multiplier of
 // column J + q: lanes l > q to their own row (offset l - q), lanes l <= q to
 // the next block's row (offset 32 + l - q, still within the band).  Each
-// lane therefore reads exactly one multiplier per column, loaded kPfD
-// columns ahead into a rotating register buffer.  The updates of every row
+// lane therefore reads exactly one multiplier per column, loaded kPfD (FP32)
+// or kPfD / 2 (FP64) columns ahead into a rotating register buffer.  The updates of every row
 // arrive in increasing column order, as in warp_band_solve_pf, so the
 // results are those of the column sweep.  The backward pass runs the same
 // steps in reversed row order over Uc; y lives in shared memory between the
@@ -343,9 +343,10 @@ __device__ __forceinline__ void band_pass_reg(const FT* __restrict__ colbase, in
     const FT* c = colbase + (ptrdiff_t)(FWD ? j : n - 1 - j) * cs;
     return ld_nc_if(c + a, j < n && a <= min(bw, n - 1 - j));
   };
-  FT buf[kPfD];
+  constexpr int PD = sizeof(FT) == 4 ? kPfD : kPfD / 2;  // FP64: half the depth (registers)
+  FT buf[PD];
 #pragma unroll
-  for (int d = 0; d < kPfD; ++d) buf[d] = load_col(0, d, lane, B);
+  for (int d = 0; d < PD; ++d) buf[d] = load_col(0, d, lane, B);
   FT dg = diag(lane);
   FT xc = src(lane), xn = src(32 + lane);
   for (int J = 0; J < n; J += 32) {
@@ -359,13 +360,13 @@ __device__ __forceinline__ void band_pass_reg(const FT* __restrict__ colbase, in
       // (jj or n - 1 - jj) 33 + a with a = ((l - jj - 1) mod 32) + 1; from
       // one column to the next a drops by one, wrapping from 1 to 32, so the
       // element moves by 32 or 64 (forward) or -34 or -2 (backward)
-      const int jj0 = J + kPfD;
+      const int jj0 = J + PD;
       int a = ((ln - jj0 - 1) & 31) + 1;
       int e = (FWD ? jj0 : n - 1 - jj0) * 33 + a;
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
-        const FT mq = buf[q % kPfD];
-        buf[q % kPfD] = ld_nc(colbase + e);  // column J + q + kPfD
+        const FT mq = buf[q % PD];
+        buf[q % PD] = ld_nc(colbase + e);  // column J + q + PD
         const bool wrap = a == 1;
         e += FWD ? (wrap ? 64 : 32) : (wrap ? -2 : -34);
         a = wrap ? 32 : a - 1;
@@ -376,8 +377,8 @@ __device__ __forceinline__ void band_pass_reg(const FT* __restrict__ colbase, in
     } else {
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
-        const FT mq = buf[q % kPfD];
-        buf[q % kPfD] = load_col(J, q + kPfD, ln, cs);  // column J + q + kPfD
+        const FT mq = buf[q % PD];
+        buf[q % PD] = load_col(J, q + PD, ln, cs);  // column J + q + PD
         if (J + q < n) {
           const FT u = shfl_idx_ordered(xc, q);
           if (lane > q) xc -= mq * u;
@@ -419,6 +420,8 @@ template <class FT>
 static void launch_band_solve_t(vtm_plan_s* P, FT* v, const FT* Lc, const FT* Uc, int ncols,
                                 int64_t stride, cudaStream_t s) {
   P->launch_count++;
+  // FP32 only: the FP64 solve is bound by GB300's FP64 pipe either way (the
+  // register-blocked form measured no faster for the 2048^2 power grid)
   if (sizeof(FT) == 4 && P->max_bw <= 32) {
     const size_t smem = (size_t)std::max(P->max_nodes, 1) * sizeof(FT);
     if (smem <= 200 * 1024) {
