@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--zc", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--l2-persist", type=int, default=0, choices=[0, 1],
-                    help="0: reflection matrices persisting in L2 during low-precision sweeps, 1: off")
+                    help="1: reflection matrices persisting in L2 during low-precision sweeps, 0: off")
     ap.add_argument("--admittance", default="alpha", choices=["alpha", "diag", "wob", "sca"],
                     help="line admittance (Sec. VIII): alpha = 1/Zc on every line (default), diag = 2g, "
                          "wob = alpha 2g, sca = partial input admittance over --radius branches")

@@ -99,10 +99,12 @@ typedef struct {
                         up to 64 columns at a time; 1: one column after the other */
   int batch_solve;   /* batched FP32 band solves: 0 (default) row window in shared memory;
                         1: whole column block in shared memory */
-  int l2_persist;    /* 0 (default): during FP32/16-bit sweeps, mark the reflection matrices
-                        persisting in L2 (access-policy window on the plan's stream; the
-                        context's persisting carve-out is set and restored around the
-                        sweeps); 1: off.  Needs a non-default stream. */
+  int l2_persist;    /* 1: during FP32/16-bit sweeps, mark the reflection matrices persisting
+                        in L2 (access-policy window on the plan's stream; the context's
+                        persisting carve-out is set and restored around each inner solve;
+                        needs a non-default stream); 0 (default): off -- on the 2048^2
+                        power grid the window saved nothing and its set-up and reset cost
+                        2-3% of a solve */
   int sweep_kernel;  /* 0 (default): autotuned -- the first solve of each precision times
                         every sweep kernel that fits the plan's sub-circuits and keeps the
                         fastest; 1: direct-load kernel; 2: bulk-copy staged kernel;

@@ -1738,7 +1738,7 @@ struct L2Window {
   size_t old_limit = 0;
   bool active = false;
   L2Window(vtm_plan_s* P, int prec) {
-    if (prec == VTM_PREC_FP64 || P->opts.l2_persist == 1 || !P->stream) return;
+    if (prec == VTM_PREC_FP64 || P->opts.l2_persist != 1 || !P->stream) return;
     // the packed copy when there is one (the packed kernels read only that)
     const DevBuf& full = prec == VTM_PREC_FP32 ? P->d_T32 : P->d_T16;
     const DevBuf& packed = prec == VTM_PREC_FP32 ? P->d_Tp32 : P->d_Tp16;
