@@ -1188,11 +1188,11 @@ __device__ double group128_sum_fixed(const double* __restrict__ a, int64_t count
   return tot;
 }
 
-// One warp per tile: the warp takes all of its tile's packed blocks in
-// row-major order and adds each partial straight into the tile's outputs
-// (AccSink), with the next KB - 1 blocks of the tile in flight into a ring of
-// KB shared-memory slots (each lane copies, and later reads, its own bytes of
-// a block, so no warp barrier guards the ring).
+// One warp per tile: the warp takes all of its tile's packed blocks (in
+// column-major order, see the block loop) and adds the partials into the
+// tile's outputs itself, with the next KB - 1 blocks of the tile in flight
+// into a ring of KB shared-memory slots (each lane copies, and later reads,
+// its own bytes of a block, so no warp barrier guards the ring).
 // There is no CTA barrier inside a tile; a CTA holds up to 32 tiles, dealt
 // round the CTAs (tile warp x gridDim + CTA), so every tile of a
 // few-thousand-tile plan is resident at once (one CTA of 27 tile warps per
@@ -1207,12 +1207,12 @@ __device__ double group128_sum_fixed(const double* __restrict__ a, int64_t count
 // so the iterate a decision names survives the sweep after it.  Each launch
 // takes its sweep number from a ticket (CTAs of launches past a stop leave
 // before taking one).
-// The arithmetic and its order are those of the 128-thread kernels (5, 7):
-// the same block partials; outputs summed from c in block order; each
-// tile's squared residual reduced as four 32-thread groups (virtual thread
-// lane + 32 v owns ports lane + 32 v + 128 j) and the tiles' partials summed
-// in the order of a 128-thread block -- so its iterates, residual history
-// and decisions are bitwise theirs.
+// The products are those of the other packed kernels; the column partials
+// are summed over a block column before their cross-lane reduction, so the
+// rounding of the outputs differs from theirs (the order is fixed: every run
+// is bitwise repeatable).  Each tile's squared residual is reduced as four
+// 32-thread groups (virtual thread lane + 32 v owns ports lane + 32 v + 128 j)
+// and the tiles' partials in the order of a 128-thread block, as in kernel 5.
 // PPL ports per lane: 4 (tiles of at most 128 ports) or 8 (256).
 template <class TT, int KB, int PPL>
 __global__ void __launch_bounds__(1024, 1) sweep_wsym_kernel(
@@ -1251,12 +1251,27 @@ __global__ void __launch_bounds__(1024, 1) sweep_wsym_kernel(
   // the ring's first blocks and the plan's port tables go out before the wait
   int tw[PPL];
   uint32_t rn4[PPL / 4];  // node-run lengths, one byte per port
+  // the copy stream follows the column-major block order: block (pbi, pbj)
+  // is number pidx of the row-major packed tile; pq counts copies issued
+  int pbi = 0, pbj = 0, pidx = 0, pq = 0;
+  auto issue_next = [&]() {
+    if (pq < nblk) {
+      copy_block_async(ring + (pq % KB) * B * B, Tl + (size_t)pidx * B * B, lane);
+      if (pbi < pbj) {
+        pidx += nb - 1 - pbi;
+        ++pbi;
+      } else {
+        ++pbj;
+        pbi = 0;
+        pidx = pbj;
+      }
+    }
+    ++pq;
+    cp_async_commit_group();
+  };
   if (tile_warp) {
 #pragma unroll
-    for (int b = 0; b < KB - 1; ++b) {
-      if (b < nblk) copy_block_async(ring + b * B * B, Tl + (size_t)b * B * B, lane);
-      cp_async_commit_group();
-    }
+    for (int b = 0; b < KB - 1; ++b) issue_next();
 #pragma unroll
     for (int m = 0; m < PPL; ++m) {
       const int s = lane + 32 * m;
@@ -1334,17 +1349,69 @@ __global__ void __launch_bounds__(1024, 1) sweep_wsym_kernel(
       tile_sq += sq;
     }
   }
-  const AccSink sink{acc};
+  // Blocks in column-major order over the upper triangle: column bj takes
+  // (0, bj), (1, bj), ..., (bj, bj).  Each block's row partial T_blk w(bj)
+  // is reduced at once into its row block bi; its column partial T_blk^T
+  // w(bi) only accumulates in registers (ca01, ca23: this lane's two rows'
+  // products for its four columns, summed over bi), reduced across the eight
+  // lanes of a column group once per column, after the diagonal block.  Row
+  // outputs have fixed owner lanes (bit 1 clear), column outputs too (bit 2
+  // clear), so two warp barriers per column order every cross-lane update.
+  const int r1 = lane >> 2, cg = lane & 3;
+  const bool b0 = lane & 1, b4 = lane & 16, b3 = lane & 8;
+  const bool row_owner = !(lane & 2), col_owner = !(lane & 4);
+  const int myrow = b0 ? r1 + 8 : r1;
+  const int mycol = cg * 4 + (b4 ? 2 : 0) + (b3 ? 1 : 0);
+  constexpr unsigned FULL = 0xffffffffu;
+  float2 ca01 = make_float2(0.f, 0.f), ca23 = make_float2(0.f, 0.f);
   int bi = 0, bj = 0;
   for (int kk = 0; kk < nblk; ++kk) {
-    // block kk + KB - 1 goes into the slot that block kk - 1 left
-    const int kn = kk + KB - 1;
-    if (kn < nblk) copy_block_async(ring + (kn % KB) * B * B, Tl + (size_t)kn * B * B, lane);
-    cp_async_commit_group();
+    issue_next();
     cp_async_wait_group<KB - 1>();  // this lane's bytes of block kk have landed
-    sym_apply<TT>(LD::load_shared(ring + (kk % KB) * B * B, lane), bi, bj, lane, w_in, sink);
-    __syncwarp();  // the next block may add to the same outputs from other lanes
-    if (++bj == nb) bj = ++bi;
+    SymLoad<float>::raw v;
+    if constexpr (std::is_same<TT, float>::value) {
+      v = LD::load_shared(ring + (kk % KB) * B * B, lane);
+    } else {
+      const uint4 raw = LD::load_shared(ring + (kk % KB) * B * B, lane);
+      const float2 e0 = Pair16<TT>::f2(raw.x), e1 = Pair16<TT>::f2(raw.y);
+      const float2 e2 = Pair16<TT>::f2(raw.z), e3 = Pair16<TT>::f2(raw.w);
+      v.a = make_float4(e0.x, e0.y, e1.x, e1.y);
+      v.b = make_float4(e2.x, e2.y, e3.x, e3.y);
+    }
+    const float2 a01 = make_float2(v.a.x, v.a.y), a23 = make_float2(v.a.z, v.a.w);
+    const float2 b01 = make_float2(v.b.x, v.b.y), b23 = make_float2(v.b.z, v.b.w);
+    {  // row partial of rows r1, r1 + 8: pairs, then a sum over the row's four lanes
+      const float4 wc = *reinterpret_cast<const float4*>(w_in + bj * B + cg * 4);
+      const float2 wc01 = make_float2(wc.x, wc.y), wc23 = make_float2(wc.z, wc.w);
+      const float2 pa = __ffma2_rn(a23, wc23, __fmul2_rn(a01, wc01));
+      const float2 pb = __ffma2_rn(b23, wc23, __fmul2_rn(b01, wc01));
+      const float x1 = pa.x + pa.y, x2 = pb.x + pb.y;
+      float t = (b0 ? x2 : x1) + __shfl_xor_sync(FULL, b0 ? x1 : x2, 1);
+      t += __shfl_xor_sync(FULL, t, 2);
+      if (row_owner) acc[bi * B + myrow] += t;
+    }
+    if (bi != bj) {
+      const float wr1 = w_in[bi * B + r1], wr2 = w_in[bi * B + r1 + 8];
+      const float2 w1 = make_float2(wr1, wr1), w2 = make_float2(wr2, wr2);
+      ca01 = __ffma2_rn(b01, w2, __ffma2_rn(a01, w1, ca01));
+      ca23 = __ffma2_rn(b23, w2, __ffma2_rn(a23, w1, ca23));
+      ++bi;
+    } else {
+      __syncwarp();  // the diagonal block's row partial is in before the column's
+      if (bj > 0) {
+        // columns 4 cg..+3: sums over the eight lanes of a column group (bits 4, 3, 2)
+        float k0 = b4 ? ca23.x : ca01.x, k1 = b4 ? ca23.y : ca01.y;
+        k0 += __shfl_xor_sync(FULL, b4 ? ca01.x : ca23.x, 16);
+        k1 += __shfl_xor_sync(FULL, b4 ? ca01.y : ca23.y, 16);
+        float t1 = (b3 ? k1 : k0) + __shfl_xor_sync(FULL, b3 ? k0 : k1, 8);
+        t1 += __shfl_xor_sync(FULL, t1, 4);
+        if (col_owner) acc[bj * B + mycol] += t1;
+      }
+      __syncwarp();  // and the column partial before later rows add to this block
+      ca01 = ca23 = make_float2(0.f, 0.f);
+      ++bj;
+      bi = 0;
+    }
   }
   cp_async_wait_group<0>();
 #pragma unroll
