@@ -76,8 +76,9 @@ enum {
                          Sec. X): every cut entry is applied with one sweep of delay */
   VTM_METHOD_ASYNC = 2 /* asynchronous VTM (Sec. XI: lines with different, varying delays):
                          one cooperative launch in which every tile reads the waves its
-                         neighbours last wrote, without waiting for them (kept within two
-                         sweeps of each other).  Same fixed point, timing-dependent
+                         neighbours last wrote, without waiting for them (kept within eight
+                         sweeps of the last residual decision; two on the older dataflow
+                         kernel used where one warp per tile does not fit).  Same fixed point, timing-dependent
                          iterates.  Needs FP32/BF16/FP16 sweeps of a symmetric plan with at most
                          256 ports per sub-circuit (VTM_EINVAL at vtm_solve otherwise) */
 };

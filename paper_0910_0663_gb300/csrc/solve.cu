@@ -1449,12 +1449,12 @@ constexpr uint32_t kFlowPolls = 1u << 22;  // a few seconds at most
 // then flag 5 is set).  Called by all 32 lanes of warp 0.
 __device__ __forceinline__ bool flow_wait_ready(const int* gk, const int* done,
                                                 const int32_t* __restrict__ nbr, int e0, int e1, int k,
-                                                SweepCtrl* ctrl) {
+                                                SweepCtrl* ctrl, int lag = 2) {
   const int lane = threadIdx.x & 31;
   for (int base = e0; base < e1 || base == e0; base += 31) {
     const int e = base + lane;
     const int* p = lane == 31 ? gk : (e < e1 ? done + nbr[e] : nullptr);
-    const int need = lane == 31 ? k - 2 : k - 1;
+    const int need = lane == 31 ? k - lag : k - 1;
     uint32_t i = 0;
     for (;; ++i) {
       const bool ok = !p || *((volatile const int*)p) >= need;
@@ -1588,8 +1588,9 @@ __global__ void __launch_bounds__(NT, 768 / NT) sweep_flow_kernel(
 // k - 1 (computed in sweep k) is reduced in two fixed-order levels off the
 // critical path: the last tile of each group of G tiles sums the group's
 // partials, the last group sums the group sums and publishes the decision.
-// Block arithmetic and order are those of kernel 9 (the iterates match it
-// bitwise; the residual sums differ by their order only).
+// Block arithmetic and order are those of kernel 9, blocks column by column
+// (the iterates match it bitwise; the residual sums differ by their order
+// only).  Asynchronous VTM runs it with a decision lag of 8 (kLag).
 template <class TT, int KB, bool ASYNC>
 __global__ void __launch_bounds__(32 * kWflowWarps, kWflowCtasPerSm) sweep_wflow_kernel(
     const TT* __restrict__ Tp, const TileDesc* __restrict__ tdesc,
@@ -1603,6 +1604,12 @@ __global__ void __launch_bounds__(32 * kWflowWarps, kWflowCtasPerSm) sweep_wflow
   using LD = SymLoad<TT>;
   constexpr int B = kSymB;
   constexpr int PPL = 4;
+  // decision lag: a tile starts sweep k once the decision of sweep k - kLag is
+  // out.  Synchronous sweeps keep their three wave slots safe with 2; the
+  // asynchronous iteration has one slot and runs ahead by up to 8.  Counters
+  // and partials of the sweeps in flight live in kSlots ring entries.
+  constexpr int kLag = ASYNC ? 8 : 2;
+  constexpr int kSlots = 16;
   constexpr unsigned FULL = 0xffffffffu;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1629,20 +1636,36 @@ __global__ void __launch_bounds__(32 * kWflowWarps, kWflowCtasPerSm) sweep_wflow
     tw[m] = s < p ? twin[p0 + s] : 0;
     if (s < p) rn4 |= (uint32_t)run[p0 + s] << (8 * m);
   }
-  // the block stream of the tile repeats every sweep: block number q of the
-  // stream is block q mod nblk of the tile, in ring slot q mod KB; qn and bn
-  // are the stream number and tile block of the next copy to issue
-  int q = 0, qn = 0, bn = 0;
+  // the block stream of the tile repeats every sweep, in the column-major
+  // order of sweep_wsym_kernel: copy number qn goes to ring slot qn mod KB and
+  // is block (pbi, pbj), number pidx of the row-major packed tile
+  int q = 0, qn = 0, pbi = 0, pbj = 0, pidx = 0;
   auto issue = [&]() {
-    if (nblk) copy_block_async(ring + (qn % KB) * B * B, Tl + (size_t)bn * B * B, lane);
+    if (nblk) {
+      copy_block_async(ring + (qn % KB) * B * B, Tl + (size_t)pidx * B * B, lane);
+      if (pbi < pbj) {
+        pidx += nb - 1 - pbi;
+        ++pbi;
+      } else if (pbj + 1 < nb) {
+        ++pbj;
+        pbi = 0;
+        pidx = pbj;
+      } else {
+        pbi = pbj = pidx = 0;  // the next sweep's first block
+      }
+    }
     cp_async_commit_group();
     ++qn;
-    if (++bn == nblk) bn = 0;
   };
 #pragma unroll
   for (int b = 0; b < KB - 1; ++b) issue();
+  const int r1 = lane >> 2, cg = lane & 3;
+  const bool b0 = lane & 1, b4 = lane & 16, b3 = lane & 8;
+  const bool row_owner = !(lane & 2), col_owner = !(lane & 4);
+  const int myrow = b0 ? r1 + 8 : r1;
+  const int mycol = cg * 4 + (b4 ? 2 : 0) + (b3 ? 1 : 0);
   for (int k = k0;; ++k) {
-    const bool ok = flow_wait_ready(gk, done, nbr, e0, e1, k, ctrl);
+    const bool ok = flow_wait_ready(gk, done, nbr, e0, e1, k, ctrl, kLag);
     __threadfence();  // every lane that saw a counter orders its later reads
     int stop = 0;
     if (lane == 0) stop = (ok && !*((volatile int*)&ctrl->flag)) ? 0 : 1;
@@ -1688,14 +1711,55 @@ __global__ void __launch_bounds__(32 * kWflowWarps, kWflowCtasPerSm) sweep_wflow
         tile_sq += sq;
       }
     }
-    const AccSink sink{acc};
+    // blocks column by column, as in sweep_wsym_kernel (the same arithmetic)
+    float2 ca01 = make_float2(0.f, 0.f), ca23 = make_float2(0.f, 0.f);
     int bi = 0, bj = 0;
     for (int kk = 0; kk < nblk; ++kk, ++q) {
       issue();  // stream number q + KB - 1
       cp_async_wait_group<KB - 1>();  // this lane's bytes of block kk have landed
-      sym_apply<TT>(LD::load_shared(ring + (q % KB) * B * B, lane), bi, bj, lane, w_in, sink);
-      __syncwarp();  // the next block may add to the same outputs from other lanes
-      if (++bj == nb) bj = ++bi;
+      SymLoad<float>::raw v;
+      if constexpr (std::is_same<TT, float>::value) {
+        v = LD::load_shared(ring + (q % KB) * B * B, lane);
+      } else {
+        const uint4 raw = LD::load_shared(ring + (q % KB) * B * B, lane);
+        const float2 e0_ = Pair16<TT>::f2(raw.x), e1_ = Pair16<TT>::f2(raw.y);
+        const float2 e2_ = Pair16<TT>::f2(raw.z), e3_ = Pair16<TT>::f2(raw.w);
+        v.a = make_float4(e0_.x, e0_.y, e1_.x, e1_.y);
+        v.b = make_float4(e2_.x, e2_.y, e3_.x, e3_.y);
+      }
+      const float2 a01 = make_float2(v.a.x, v.a.y), a23 = make_float2(v.a.z, v.a.w);
+      const float2 b01 = make_float2(v.b.x, v.b.y), b23 = make_float2(v.b.z, v.b.w);
+      {
+        const float4 wc = *reinterpret_cast<const float4*>(w_in + bj * B + cg * 4);
+        const float2 wc01 = make_float2(wc.x, wc.y), wc23 = make_float2(wc.z, wc.w);
+        const float2 pa = __ffma2_rn(a23, wc23, __fmul2_rn(a01, wc01));
+        const float2 pb = __ffma2_rn(b23, wc23, __fmul2_rn(b01, wc01));
+        const float x1 = pa.x + pa.y, x2 = pb.x + pb.y;
+        float t = (b0 ? x2 : x1) + __shfl_xor_sync(FULL, b0 ? x1 : x2, 1);
+        t += __shfl_xor_sync(FULL, t, 2);
+        if (row_owner) acc[bi * B + myrow] += t;
+      }
+      if (bi != bj) {
+        const float wr1 = w_in[bi * B + r1], wr2 = w_in[bi * B + r1 + 8];
+        const float2 w1 = make_float2(wr1, wr1), w2 = make_float2(wr2, wr2);
+        ca01 = __ffma2_rn(b01, w2, __ffma2_rn(a01, w1, ca01));
+        ca23 = __ffma2_rn(b23, w2, __ffma2_rn(a23, w1, ca23));
+        ++bi;
+      } else {
+        __syncwarp();
+        if (bj > 0) {
+          float k0 = b4 ? ca23.x : ca01.x, k1 = b4 ? ca23.y : ca01.y;
+          k0 += __shfl_xor_sync(FULL, b4 ? ca01.x : ca23.x, 16);
+          k1 += __shfl_xor_sync(FULL, b4 ? ca01.y : ca23.y, 16);
+          float t1 = (b3 ? k1 : k0) + __shfl_xor_sync(FULL, b3 ? k0 : k1, 8);
+          t1 += __shfl_xor_sync(FULL, t1, 4);
+          if (col_owner) acc[bj * B + mycol] += t1;
+        }
+        __syncwarp();
+        ca01 = ca23 = make_float2(0.f, 0.f);
+        ++bj;
+        bi = 0;
+      }
     }
 #pragma unroll
     for (int m = 0; m < PPL; ++m) {
@@ -1708,33 +1772,33 @@ __global__ void __launch_bounds__(32 * kWflowWarps, kWflowCtasPerSm) sweep_wflow
     __syncwarp();
     int last = 0;
     if (lane == 0) {
-      part4[(size_t)(k & 3) * nparts + g] = (double)tile_sq;
+      part4[(size_t)(k & (kSlots - 1)) * nparts + g] = (double)tile_sq;
       __threadfence();
       atomicExch(done + tile, k);
-      last = atomicAdd(gcount + (k & 3) * 32 + grp, 1u) == gsize - 1;
+      last = atomicAdd(gcount + (k & (kSlots - 1)) * 32 + grp, 1u) == gsize - 1;
     }
     if (__shfl_sync(FULL, last, 0)) {
       __threadfence();
-      const double* pg = part4 + (size_t)(k & 3) * nparts + (size_t)grp * G;
+      const double* pg = part4 + (size_t)(k & (kSlots - 1)) * nparts + (size_t)grp * G;
       double s = 0.0;
       for (int i = lane; i < (int)gsize; i += 32) s += __ldcg(pg + i);
       for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(FULL, s, o);
       int top = 0;
       if (lane == 0) {
-        gsum[(k & 3) * 32 + grp] = s;
+        gsum[(k & (kSlots - 1)) * 32 + grp] = s;
         __threadfence();
-        top = atomicAdd(count + (k & 3), 1u) == (unsigned)ngroups - 1;
+        top = atomicAdd(count + (k & (kSlots - 1)), 1u) == (unsigned)ngroups - 1;
       }
       if (__shfl_sync(FULL, top, 0)) {
         __threadfence();
-        double t = lane < ngroups ? __ldcg(gsum + (k & 3) * 32 + lane) : 0.0;
+        double t = lane < ngroups ? __ldcg(gsum + (k & (kSlots - 1)) * 32 + lane) : 0.0;
         for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(FULL, t, o);
         // counters of sweep k + 2 start from zero before anyone may finish it
-        gcount[((k + 2) & 3) * 32 + lane] = 0u;
+        gcount[((k + kLag) & (kSlots - 1)) * 32 + lane] = 0u;
         __threadfence();
         __syncwarp();
         if (lane == 0) {
-          count[(k + 2) & 3] = 0u;
+          count[(k + kLag) & (kSlots - 1)] = 0u;
           sweep_decide(ctrl, k, t, hist, hist_len);
           __threadfence();
           atomicExch(gk, k);
@@ -2126,14 +2190,15 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
     cudaGetLastError();
   }
   const bool wflow_ok = wflow_grid > 0;
-  // counters of the dataflow kernels: 4 sweep counters, the published
-  // decision (byte 32), 4 x 32 group counters (byte 64), 4 x 32 group sums
-  // (byte 576)
-  constexpr size_t kFlowBytes = 2048;
+  // counters of the dataflow kernels.  Kernel 8: 4 sweep counters, the
+  // published decision at byte 32.  Kernel 10: 16 sweep counters, the
+  // decision at byte 64, 16 x 32 group counters at byte 128, 16 x 32 group
+  // sums at byte 2176; 16 x nparts tile partials.
+  constexpr size_t kFlowBytes = 8192;
   if (flow_ok || wflow_ok) {
     VTM_TRY(dev_alloc(P->d_done, (size_t)P->nparts * sizeof(int)));
     VTM_TRY(dev_alloc(P->d_flow, kFlowBytes));
-    VTM_TRY(dev_alloc(P->d_part4, 4 * (size_t)P->nparts * sizeof(double)));
+    VTM_TRY(dev_alloc(P->d_part4, 16 * (size_t)P->nparts * sizeof(double)));
   }
   // three wave slots: the dataflow kernels and the one-warp-per-tile sweeps
   if (sym_ok) VTM_TRY(dev_alloc(P->d_fstate32, 6 * (size_t)std::max<int64_t>(npt, 1) * sizeof(float)));
@@ -2188,9 +2253,9 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
     int* dn = P->d_done.as<int>();
     unsigned char* fb = reinterpret_cast<unsigned char*>(P->d_flow.p);
     unsigned* cnt = reinterpret_cast<unsigned*>(fb);
-    int* gkp = reinterpret_cast<int*>(fb + 32);
-    unsigned* gcnt = reinterpret_cast<unsigned*>(fb + 64);
-    double* gs = reinterpret_cast<double*>(fb + 576);
+    int* gkp = reinterpret_cast<int*>(fb + 64);
+    unsigned* gcnt = reinterpret_cast<unsigned*>(fb + 128);
+    double* gs = reinterpret_cast<double*>(fb + 2176);
     int G = std::max(1, (P->nparts + 31) / 32);
     SweepCtrl* ct = P->d_ctrl.as<SweepCtrl>();
     double* p4 = P->d_part4.as<double>();

@@ -265,15 +265,20 @@ def test_packed_symmetric_sweeps_follow_the_oracle(vtm, precision, kernel, shape
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
-def test_dataflow_sweeps_repeat_kernel_5_bitwise(vtm, precision):
-    # one cooperative launch with per-tile neighbour waits (8), and the same
-    # with one warp per tile adding its partials in block order (10), compute
-    # the same iterates as four warps per tile (5): same block arithmetic,
-    # same fixed-order sums of the outputs; 8 also reduces the residual in
-    # kernel 5's order, 10 in two fixed-order levels of its own
+def test_dataflow_sweeps_repeat_the_launch_per_sweep_kernels_bitwise(vtm, precision):
+    # one cooperative launch with per-tile neighbour waits computes the same
+    # iterates as one launch per sweep: kernel 8 those of kernel 5 (four warps
+    # per tile, same block arithmetic and residual order), kernel 10 those of
+    # kernel 9 (one warp per tile, blocks column by column; its residual is
+    # summed in two fixed-order levels of its own)
     w = wl.power_grid(256, 256, 32, 32, Zc=1.0, seed=17)
+    for pair in ((5, 8), (9, 10)):
+        _assert_same_iterates(vtm, w, precision, pair)
+
+
+def _assert_same_iterates(vtm, w, precision, kernels):
     out = []
-    for kernel in (5, 8, 10):
+    for kernel in kernels:
         plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc,
                         precision=precision, sweep_kernel=kernel)
         plan.set_options(history_len=64)
