@@ -269,11 +269,12 @@ def sweep_kernel_name(kernel, nrhs):
 
 
 def sweep_kernel_source_hash():
-    """sha256 of the device code of the packed sweep kernels in solve.cu (the
-    text from their section header to the host driver's)."""
+    """sha256 of the device code of the launch-per-sweep packed kernels in
+    solve.cu and their shared block code (the text from their section header to
+    the dataflow kernels' section)."""
     src = open(os.path.join(ROOT, "paper_0910_0663_gb300", "csrc", "solve.cu")).read()
     i = src.find("// Packed symmetric sweep.")
-    j = src.find("// host driver", i)
+    j = src.find("// Dataflow sweeps: one cooperative launch", i)
     return hashlib.sha256(src[i:j].encode()).hexdigest() if 0 <= i < j else None
 
 
