@@ -236,6 +236,9 @@ vtm_status vtm_factor(vtm_plan_t plan);
 /* vtm_solve -- solve A x = b by VTM sweeps (Sec. VI, Eq. 11/14) with zero
  * initial waves, until ||b - A x||_2 <= tol ||b||_2 for every column.
  * b, x: n x nrhs column-major, host or device; x is output only.  tol > 0.
+ * Host arrays are copied through device buffers the plan keeps between calls
+ * (grown when a call needs more; freed by vtm_destroy), pinned host memory at
+ * the link's rate.
  * The convergence test after every sweep uses the residual of the torn
  * branches (the interior rows of each sub-circuit are solved exactly); the
  * returned info->relres comes from an FP64 SpMV of the returned x.

@@ -760,7 +760,8 @@ std::vector<DevBuf*> vtm_plan_s::all_bufs() {
           &d_in_sigma, &d_out_scale, &d_out_diag, &d_E_off, &d_E_ld, &d_E, &d_cg, &d_gin,
           &d_gout, &d_in_tile, &d_item_tile, &d_item_m0, &d_item_order, &d_bV, &d_bV32, &d_bstate,
           &d_bc, &d_bpart,
-          &d_btol2, &d_bctrl, &d_bres};
+          &d_btol2, &d_bctrl, &d_bres, &d_stage_in[0], &d_stage_in[1], &d_stage_in[2],
+          &d_stage_out[0], &d_stage_out[1], &d_stage_out[2]};
 }
 
 static void fill_default_opts(vtm_opts* o) {

@@ -2717,33 +2717,32 @@ vtm_status residual_norms(vtm_plan_s* P, const double* d_x, const double* d_b, i
 using namespace vtm;
 
 // Host/device staging of the caller's vectors.
+// A host array seen by the device: host input arrays are copied into, and
+// host outputs computed in, device buffers the plan keeps (slot 0..2; grown
+// when a call needs more), so repeated calls with host buffers allocate
+// nothing (an allocation and its release would synchronise the device).
 struct Staged {
-  vtm_plan_s* P = nullptr;
   const double* in_dev = nullptr;
   double* out_dev = nullptr;
-  DevBuf tmp_in, tmp_out;
   bool out_host = false;
-  ~Staged() {
-    dev_free(tmp_in);
-    dev_free(tmp_out);
-  }
 };
 
-static vtm_status stage(vtm_plan_s* P, const double* in, double* out, int64_t count, Staged& S) {
-  S.P = P;
+static vtm_status stage(vtm_plan_s* P, const double* in, double* out, int64_t count, Staged& S, int slot = 0) {
   if (is_device_ptr(in)) {
     S.in_dev = in;
   } else {
-    VTM_TRY(dev_alloc(S.tmp_in, count * sizeof(double)));
-    VTM_CUDA_TRY(cudaMemcpyAsync(S.tmp_in.p, in, count * sizeof(double), cudaMemcpyHostToDevice, P->stream));
-    S.in_dev = S.tmp_in.as<double>();
+    DevBuf& t = P->d_stage_in[slot];
+    VTM_TRY(dev_alloc(t, count * sizeof(double)));
+    VTM_CUDA_TRY(cudaMemcpyAsync(t.p, in, count * sizeof(double), cudaMemcpyHostToDevice, P->stream));
+    S.in_dev = t.as<double>();
   }
   if (out) {
     if (is_device_ptr(out)) {
       S.out_dev = out;
     } else {
-      VTM_TRY(dev_alloc(S.tmp_out, count * sizeof(double)));
-      S.out_dev = S.tmp_out.as<double>();
+      DevBuf& t = P->d_stage_out[slot];
+      VTM_TRY(dev_alloc(t, count * sizeof(double)));
+      S.out_dev = t.as<double>();
       S.out_host = true;
     }
   }
@@ -2801,9 +2800,9 @@ extern "C" vtm_status vtm_march(vtm_plan_t P, const double* cdiag, const double*
   *info = vtm_info{};
   const int64_t n = P->n;
   Staged Sp, Sc, S0;
-  VTM_TRY(stage(P, p, X, n * nsteps, Sp));
-  VTM_TRY(stage(P, cdiag, nullptr, n, Sc));
-  if (x0) VTM_TRY(stage(P, x0, nullptr, n, S0));
+  VTM_TRY(stage(P, p, X, n * nsteps, Sp, 0));
+  VTM_TRY(stage(P, cdiag, nullptr, n, Sc, 1));
+  if (x0) VTM_TRY(stage(P, x0, nullptr, n, S0, 2));
   DevBuf bk;
   VTM_TRY(dev_alloc(bk, (size_t)n * sizeof(double)));
   P->launch_count = 0;
@@ -2886,11 +2885,9 @@ extern "C" vtm_status vtm_residual_norm(vtm_plan_t P, const double* x, const dou
   cudaSetDevice(P->device);
   const int64_t count = P->n * nrhs;
   Staged Sx, Sb;
-  VTM_TRY(stage(P, x, nullptr, count, Sx));
-  VTM_TRY(stage(P, b, nullptr, count, Sb));
+  VTM_TRY(stage(P, x, nullptr, count, Sx, 0));
+  VTM_TRY(stage(P, b, nullptr, count, Sb, 1));
   vtm_status st = residual_norms(P, Sx.in_dev, Sb.in_dev, nrhs, rel);
   VTM_CUDA_TRY(cudaStreamSynchronize(P->stream));
-  dev_free(Sx.tmp_in);
-  dev_free(Sb.tmp_in);
   return st;
 }

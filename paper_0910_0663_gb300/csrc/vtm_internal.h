@@ -208,6 +208,7 @@ struct vtm_plan_s {
   vtm::DevBuf d_hist;                      // double[history capacity]
   vtm::DevBuf d_err;                       // int error word of factor kernels
   vtm::DevBuf d_red;                       // double[2] + unsigned counter for reductions
+  vtm::DevBuf d_stage_in[3], d_stage_out[3];  // device copies of host arrays, kept between calls
   int hist_cap = 0;
   vtm::SweepCtrl* h_ctrl = nullptr;        // pinned mirror
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evs0 = nullptr, evs1 = nullptr;
