@@ -322,6 +322,28 @@ def test_warp_per_tile_sweep_against_kernel_5(vtm, precision):
     assert k >= 5 and np.allclose(h9[:k], h5[:k], rtol=rtol, atol=0)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_warp_per_tile_sweep_with_more_tiles_than_resident_warps(vtm, precision):
+    # 16384 tiles of 8x8 (32 ports): 28 tile warps per CTA, 586 CTAs, several
+    # waves of CTAs per sweep; every CTA still takes its sweep number from the
+    # ticket before the next launch may start
+    w = wl.power_grid(1024, 1024, 8, 8, Zc=1.0, seed=19)
+    A = w.csr()
+    b = torch.from_numpy(w.b[0]).cuda()
+    xs = {}
+    for kernel in (5, 9):
+        plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc,
+                        precision=precision, sweep_kernel=kernel)
+        x, info = plan.solve(b, tol=1e-10)
+        x2, info2 = plan.solve(b, tol=1e-10)
+        assert plan.stats()["sweep_kernel"] == kernel and plan.stats()["nparts"] == 16384
+        assert torch.equal(x, x2) and info["sweeps"] == info2["sweeps"]
+        assert O.residual_norms(A, x.cpu().numpy()[None], w.b[:1]).max() <= 1e-10
+        xs[kernel] = (x.cpu().numpy(), info["sweeps"])
+    assert abs(xs[9][1] - xs[5][1]) <= max(4, xs[5][1] // 20)
+    assert np.abs(xs[9][0] - xs[5][0]).max() <= 1e-6 * np.abs(xs[5][0]).max()
+
+
 @pytest.mark.parametrize("precision,kernel", [("fp32", 5), ("fp32", 6), ("fp16", 7), ("bf16", 7), ("fp16", 9)])
 def test_overlapped_sweep_launches_compute_the_same_iterates(vtm, precision, kernel):
     # packed sweeps launched as programmatic dependents of the sweep before
