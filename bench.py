@@ -37,7 +37,7 @@ SAMPLE_N = 512  # oracle sample: 512x512 instance of the same recipe
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="vtm", choices=["vtm", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "fp32", "bf16", "fp16"])
@@ -119,6 +119,12 @@ class ClockSampler:
             self.thread.start()
         except OSError:
             self.proc = None
+            return self
+        # the timed region starts once the sampler has produced its first row
+        t0 = time.perf_counter()
+        while not self.lines and self.proc.poll() is None and time.perf_counter() - t0 < 5.0:
+            time.sleep(0.01)
+        self.lines.clear()
         return self
 
     def _read(self):
@@ -402,18 +408,19 @@ def run_mode(args, prec, w, dev, stream, b_dev, b_host, x_host, flush, world):
         times, infos = [], []
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
-        sampler = ClockSampler(dev.index)
-        with sampler:
-            for _ in range(args.steps):
-                flush.fill_(1.0)
-                torch.cuda.synchronize()
-                with torch.cuda.stream(stream):
-                    ev0.record(stream)
-                    x, info = step()
-                    ev1.record(stream)
-                torch.cuda.synchronize()
-                times.append(ev0.elapsed_time(ev1))
-                infos.append(info)
+        # clocks are sampled over both timed regions (device-resident and
+        # host-buffer calls); the host-buffer warm-up sits between them
+        sampler = ClockSampler(dev.index).__enter__()
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            with torch.cuda.stream(stream):
+                ev0.record(stream)
+                x, info = step()
+                ev1.record(stream)
+            torch.cuda.synchronize()
+            times.append(ev0.elapsed_time(ev1))
+            infos.append(info)
         t_step = float(np.mean(times))
         value, t_step = job_value(w.n * nrhs, t_step, world, dev)
         # end to end through the C ABI with host buffers (copies inside)
@@ -433,6 +440,7 @@ def run_mode(args, prec, w, dev, stream, b_dev, b_host, x_host, flush, world):
                 C.vtm_solve(plan.handle, b_host, x_host, nrhs, TOL)
             h1 = time.perf_counter()
             e2e.append(h1 - h0)
+        sampler.__exit__(None, None, None)
         st = plan.stats()
         inf = infos[-1]
         bytes_sweep = sweep_bytes(st, {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3}[prec_name], nrhs)
