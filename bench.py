@@ -58,10 +58,12 @@ def parse():
                          "waves of their neighbours, FP32/BF16/FP16 symmetric plans)")
     ap.add_argument("--alpha", type=float, default=0.5, help="the weight of --admittance wob")
     ap.add_argument("--radius", type=int, default=1, help="the neighbourhood of --admittance sca")
-    ap.add_argument("--sweep-kernel", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10],
+    ap.add_argument("--sweep-kernel", type=int, default=0, choices=list(range(12)),
                     help="0: autotuned, 1: direct-load, 2: bulk-copy staged, 3/4: vector-load (256/128 "
                          "threads), 5/6: packed symmetric (128/64 threads), 7: packed symmetric, tile by "
-                         "one bulk copy, 8: packed symmetric dataflow sweeps (one launch per inner solve)")
+                         "one bulk copy, 8: packed symmetric dataflow sweeps (one launch per inner solve), "
+                         "9: packed symmetric, one warp per tile, 10: kernel 9's dataflow form, 11: kernel 9 "
+                         "with the block products as warp MMAs (BF16/FP16)")
     return ap.parse_args()
 
 
@@ -247,7 +249,7 @@ def sweep_bytes(stats, prec, nrhs=1):
     s_w = 8 if prec == 0 else 4
     s_kd = 16 if (prec == 0 or nrhs > 1) else 8
     # the packed symmetric kernels need only the entries on and above the diagonal
-    entries = stats["sum_tri"] if stats.get("sweep_kernel") in (5, 6, 7, 8, 9, 10) and nrhs == 1 else stats["sum_p2"]
+    entries = stats["sum_tri"] if stats.get("sweep_kernel") in (5, 6, 7, 8, 9, 10, 11) and nrhs == 1 else stats["sum_p2"]
     return entries * s_t + stats["nports"] * (7 * s_w * nrhs + 5 + s_kd)
 
 
@@ -271,7 +273,9 @@ def sweep_kernel_name(kernel, nrhs):
             7: "sweep_symb_kernel (packed symmetric, one bulk copy per tile)",
             8: "sweep_flow_kernel (dataflow, one cooperative launch)",
             9: "sweep_wsym_kernel (packed symmetric, one warp per tile)",
-            10: "sweep_wflow_kernel (dataflow, one warp per tile, one cooperative launch)"}.get(kernel, str(kernel))
+            10: "sweep_wflow_kernel (dataflow, one warp per tile, one cooperative launch)",
+            11: "sweep_wmma_kernel (packed symmetric, one warp per tile, block products as warp MMAs)"}.get(
+                kernel, str(kernel))
 
 
 def sweep_kernel_source_hash():

@@ -121,9 +121,15 @@ typedef struct {
                         cooperative launch per inner solve, each tile starting sweep k
                         once the tiles across its lines have finished sweep k - 1 (no
                         kernel boundary per sweep; same iterates as 5); 9: the same
-                        blocks with one warp per tile (8 tiles per CTA, no CTA barrier
-                        inside a tile, every tile of a few-thousand-tile plan resident
-                        at once; same iterates as 5); elsewhere 5-9 fall back to
+                        blocks with one warp per tile (one CTA per SM holding
+                        ceil(sub-circuits / SMs) tile warps, blocks column by column;
+                        the same iteration as 5 up to rounding); 10: kernel 9's tiles
+                        in one cooperative launch per inner solve (same iterates as
+                        9); 11: kernel 9 with each block's products on the tensor
+                        cores (warp MMAs, FP32 accumulate; the incident waves enter
+                        as 16-bit hi + lo pairs scaled per tile by a power of two),
+                        BF16/FP16 plans with at most 128 ports per sub-circuit;
+                        where a packed kernel does not fit, 5-11 fall back to
                         kernel 1 */
   int graphs;        /* 0 (default): replay batches of check_every sweep launches from a
                         CUDA graph when the plan has its own stream; 1: plain launches */
@@ -221,7 +227,7 @@ vtm_status vtm_get_admittance(vtm_plan_t plan, double* W);
 
 /* vtm_set_opts -- replace the options of a plan (precision, limits, history).
  * VTM_EINVAL for a precision outside 0..3, a negative history_len, a history
- * length without an array, or a sweep_kernel outside 0..9; the plan keeps its
+ * length without an array, or a sweep_kernel outside 0..11; the plan keeps its
  * previous options then. */
 vtm_status vtm_set_opts(vtm_plan_t plan, const vtm_opts* opts);
 

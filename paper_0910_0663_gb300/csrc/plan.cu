@@ -858,8 +858,8 @@ extern "C" vtm_status vtm_set_opts(vtm_plan_t P, const vtm_opts* opts) {
     set_detail("vtm_set_opts: bad precision or history");
     return VTM_EINVAL;
   }
-  if (o.sweep_kernel < 0 || o.sweep_kernel > 10) {
-    set_detail("vtm_set_opts: sweep_kernel must be 0..10");
+  if (o.sweep_kernel < 0 || o.sweep_kernel > 11) {
+    set_detail("vtm_set_opts: sweep_kernel must be 0..11");
     return VTM_EINVAL;
   }
   if (o.method < 0 || o.method > 2 || ((o.method == VTM_METHOD_BJ) != (P->method == VTM_METHOD_BJ))) {

@@ -1423,6 +1423,281 @@ __global__ void __launch_bounds__(1024, 1) sweep_wsym_kernel(
 }
 
 // ---------------------------------------------------------------------------
+// Packed symmetric sweep with the block products on the tensor cores (kernel
+// 11; 16-bit blocks, tiles of at most 128 ports).  Kernel 9's organisation
+// (one warp per tile, one CTA per SM with four service warps, three wave
+// slots, the decision on sweep k - 1 taken by CTA 0's service warps), with
+// each 16x16 block applied by warp MMAs (mma.sync m16n8k16, FP32 accumulate):
+// the row part T_blk w(bj) and the column part T_blk^T w(bi) of block (bi, bj)
+// are one MMA each.  Their B operand carries the tile's incident waves, scaled
+// by a power of two sc (largest |sc w| in [2^13, 2^14)), as two 16-bit numbers
+// hi = rn(sc w) in column 0 and lo = rn(sc w - hi) in column 1 (zero
+// elsewhere): column 0 + column 1 of the product is T_blk (sc w) with the
+// waves kept to 22 (FP16) or 16 (BF16) bits, against the 11 / 8 bits of T_P's
+// own storage.  Lane l, g = l / 4, t = l % 4:
+//   * stored block (the 16-bit layout of the other packed kernels): words
+//     x = T[g][4t, 4t+1], y = T[g][4t+2, 4t+3], z = T[g+8][4t, 4t+1],
+//     w = T[g+8][4t+2, 4t+3];
+//   * row part: A = {x, z, y, w}, so MMA index k = 2t+e stands for block
+//     column 4t+e and k = 8+2t+e for 4t+2+e; B (lanes 0-3 hi, 4-7 lo) holds
+//     (w[4t], w[4t+1]) and (w[4t+2], w[4t+3]); output row r is block row r;
+//   * column part: A = the 8x8 transposes (movmatrix) of x, y, z, w, so k is
+//     the block row and MMA row m stands for block column kx(m) = 4(m/2) +
+//     m%2 (m < 8) or ky(m-8) = 4((m-8)/2) + 2 + m%2 (m >= 8); B holds
+//     (w[2t], w[2t+1]) and (w[8+2t], w[9+2t]).
+// The output of both sits in lanes 4q: rows q and q + 8, (hi, lo) pairs.
+// Blocks run column by column as in kernel 9: the column part of every block
+// of column bj, and the diagonal block (symmetric, so through the same
+// transposed form), accumulate in one MMA accumulator, stored once per
+// column; each row part is added at once to its row block's (hi, lo) pair in
+// shared memory by the lanes that own those rows.
+// ---------------------------------------------------------------------------
+
+template <class TT>
+struct Mma16;
+template <>
+struct Mma16<__half> {
+  __device__ static void mma(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                             uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+  }
+  // (hi, lo) of a pair of scaled waves, as two packed 16-bit pairs
+  __device__ static uint2 split(float v0, float v1) {
+    const __half2 h = __floats2half2_rn(v0, v1);
+    const float2 f = __half22float2(h);
+    const __half2 l = __floats2half2_rn(v0 - f.x, v1 - f.y);
+    return make_uint2(*reinterpret_cast<const uint32_t*>(&h), *reinterpret_cast<const uint32_t*>(&l));
+  }
+};
+template <>
+struct Mma16<__nv_bfloat16> {
+  __device__ static void mma(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                             uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+  }
+  __device__ static uint2 split(float v0, float v1) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+    const float2 f = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - f.x, v1 - f.y);
+    return make_uint2(*reinterpret_cast<const uint32_t*>(&h), *reinterpret_cast<const uint32_t*>(&l));
+  }
+};
+// transpose of an 8x8 16-bit matrix held one row-pair word per lane
+__device__ __forceinline__ uint32_t movm_trans(uint32_t a) {
+  uint32_t d;
+  asm volatile("movmatrix.sync.aligned.m8n8.trans.b16 %0, %1;" : "=r"(d) : "r"(a));
+  return d;
+}
+
+// f(integral_constant<int, I>) for I = 0 .. N - 1, unrolled at compile time
+template <int N, int I = 0, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>{});
+    static_for<N, I + 1>(f);
+  }
+}
+
+constexpr int kWmmaNB = 8;  // block rows of the largest tile (128 ports)
+
+template <class TT, int KB>
+__global__ void __launch_bounds__(1024, 1) sweep_wmma_kernel(
+    const TT* __restrict__ Tp, const TileDesc* __restrict__ tdesc,
+    const int32_t* __restrict__ twin, const float2* __restrict__ kd,
+    const uint8_t* __restrict__ run, const float* __restrict__ c, float* __restrict__ state3,
+    int64_t nports, SweepCtrl* __restrict__ ctrl,
+    double* __restrict__ partials2, double* __restrict__ hist, int hist_len, int nparts, int pp_max) {
+  using M = Mma16<TT>;
+  constexpr int B = kSymB;
+  constexpr int PPL = 4;
+  constexpr unsigned FULL = 0xffffffffu;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_k, s_flag;
+  __shared__ double s_red[4];
+  __shared__ uint2 s_zero[kWmmaNB * 8];  // the B operand rows of lanes 8-31
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nw = (int)(blockDim.x >> 5) - 4;  // tile warps; the last four serve
+  if (tid == 0) s_flag = *((volatile int*)&ctrl->flag);
+  if (tid < kWmmaNB * 8) s_zero[tid] = make_uint2(0u, 0u);
+  __syncthreads();
+  if (s_flag) return;
+  const bool tile_warp = warp < nw;
+  const int g = warp * gridDim.x + blockIdx.x;  // tiles dealt round the CTAs
+  const bool valid = tile_warp && g < nparts;
+  TileDesc dsc{};
+  if (valid) dsc = tdesc[g];
+  const int p0 = dsc.p0, p = valid ? dsc.p : 0;
+  const int nb = (p + B - 1) / B;
+  const TT* Tl = Tp + dsc.Tp_off;
+  // per warp: the ring, w_in, residual terms, c, the (hi, lo) row sums and
+  // the column parts' B operands (lanes 0-7, one row of eight per block row)
+  unsigned char* wbase =
+      smem_raw + (size_t)(tile_warp ? warp : 0) * (KB * B * B * sizeof(TT) + 20 * (size_t)pp_max + 64 * kWmmaNB);
+  TT* ring = reinterpret_cast<TT*>(wbase);
+  float* w_in = reinterpret_cast<float*>(ring + KB * B * B);
+  float* rs = w_in + pp_max;
+  float* cs = rs + pp_max;
+  float2* acc2 = reinterpret_cast<float2*>(cs + pp_max);
+  uint2* bcs = reinterpret_cast<uint2*>(acc2 + pp_max);
+  // copy number q (column-major block order: column bj holds blocks (0, bj) ..
+  // (bj, bj)) of the row-major packed tile, while it exists (bj < nb)
+  auto issue = [&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    constexpr int bj = q < 1 ? 0 : q < 3 ? 1 : q < 6 ? 2 : q < 10 ? 3 : q < 15 ? 4 : q < 21 ? 5 : q < 28 ? 6 : q < 36 ? 7 : 8;
+    constexpr int bi = q - bj * (bj + 1) / 2;
+    if (bj < nb) {
+      const int pidx = bi * nb - bi * (bi - 1) / 2 + bj - bi;
+      copy_block_async(ring + (q % KB) * B * B, Tl + (size_t)pidx * B * B, lane);
+    }
+    cp_async_commit_group();
+  };
+  int tw[PPL];
+  uint32_t rn4 = 0;  // node-run lengths, one byte per port
+  if (tile_warp) {
+    static_for<KB - 1>([&](auto qc) { issue(qc); });
+#pragma unroll
+    for (int m = 0; m < PPL; ++m) {
+      const int s = lane + 32 * m;
+      tw[m] = s < p ? twin[p0 + s] : 0;
+      if (s < p) rn4 |= (uint32_t)run[p0 + s] << (8 * m);
+    }
+  }
+  pdl_launch_dependents();
+  pdl_wait();  // the previous sweep's waves, partials and decision
+  if (tid == 0) {
+    s_flag = *((volatile int*)&ctrl->flag);
+    if (!s_flag) s_k = (int)(atomicAdd(&ctrl->ticket, 1u) / gridDim.x) + 1;
+  }
+  __syncthreads();
+  if (s_flag) {
+    cp_async_wait_group<0>();  // no copy into shared memory outlives the CTA
+    return;
+  }
+  const int k = s_k;
+  if (!tile_warp) {  // service warps: CTA 0 decides on the previous sweep
+    if (blockIdx.x != 0 || k < 2) return;
+    const int t = tid - nw * 32;
+    const double tot = group128_sum_fixed(partials2 + (size_t)((k - 1) & 1) * nparts, nparts, t, s_red);
+    if (t == 0) sweep_decide(ctrl, k - 1, tot, hist, hist_len);
+    return;
+  }
+  const float* prev = state3 + (size_t)((k - 1) % 3) * nports * 2;
+  float* cur = state3 + (size_t)(k % 3) * nports * 2;
+  // incident waves and residual terms of sweep k - 1, c, and the waves' scale
+  float amax = 0.f;
+#pragma unroll
+  for (int m = 0; m < PPL; ++m) {
+    const int s = lane + 32 * m;
+    if (s < nb * B) {
+      float wi = 0.f, rc = 0.f, c0 = 0.f;
+      if (s < p) {
+        c0 = c[p0 + s];
+        if (k > 1) {
+          const float2 wt = *reinterpret_cast<const float2*>(prev + 2 * (size_t)tw[m]);
+          const float2 ws = *reinterpret_cast<const float2*>(prev + 2 * (size_t)(p0 + s));
+          wi = wt.y;
+          rc = port_residual<float>(ws.x, ws.y, wt.x, wt.y, kd[p0 + s]);
+        }
+      }
+      w_in[s] = wi;
+      rs[s] = rc;
+      cs[s] = c0;
+      amax = fmaxf(amax, fabsf(wi));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(FULL, amax, o));
+  // sc = 2^(13 - E) for |w| max = 1.f x 2^E (biased exponent clamped so that
+  // sc and 1 / sc are both normal: their product is exactly one)
+  const int se = min(max(267 - (int)((__float_as_uint(amax) >> 23) & 0xff), 1), 253);
+  const float sc = __uint_as_float((uint32_t)se << 23), isc = __uint_as_float((uint32_t)(254 - se) << 23);
+  __syncwarp();
+  float tile_sq = 0.f;  // lane 0: the four groups in order
+  if (k > 1) {
+#pragma unroll
+    for (int m = 0; m < PPL; ++m) {
+      float sq = 0.f;
+      const int s = lane + 32 * m;
+      const int nr = (rn4 >> (8 * m)) & 0xff;
+      if (s < p && nr) {
+        float rr = 0.f;
+        for (int q = 0; q < nr; ++q) rr += rs[s + q];
+        sq = rr * rr;
+      }
+      for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(FULL, sq, o);
+      tile_sq += sq;
+    }
+  }
+  // B operands of the column parts, one per block row: lanes 0-3 hi, 4-7 lo;
+  // each of those lanes reads back only its own, the others read zeros
+  const int gq = lane >> 2, t4 = lane & 3;
+  const bool lo = gq == 1, bl = gq < 2;
+  if (bl) {
+    for (int r = 0; r < nb; ++r) {
+      const float2 u = *reinterpret_cast<const float2*>(w_in + r * B + 2 * t4);
+      const float2 v = *reinterpret_cast<const float2*>(w_in + r * B + 8 + 2 * t4);
+      const uint2 su = M::split(u.x * sc, u.y * sc), sv = M::split(v.x * sc, v.y * sc);
+      bcs[r * 8 + lane] = lo ? make_uint2(su.y, sv.y) : make_uint2(su.x, sv.x);
+    }
+  }
+  const uint2* bsrc = bl ? bcs + lane : s_zero;
+  const bool owner = t4 == 0;  // lanes 4q: rows q and q + 8 of each output
+  const int kxq = 4 * (gq >> 1) + (gq & 1), kyq = kxq + 2;
+  static_for<kWmmaNB>([&](auto jc) {
+    constexpr int bj = decltype(jc)::value;
+    if (bj < nb) {
+      // B operand of the row parts: w(bj) in the row part's column order
+      const float4 wv = *reinterpret_cast<const float4*>(w_in + bj * B + 4 * t4);
+      const uint2 s01 = M::split(wv.x * sc, wv.y * sc), s23 = M::split(wv.z * sc, wv.w * sc);
+      const uint32_t br0 = bl ? (lo ? s01.y : s01.x) : 0u, br1 = bl ? (lo ? s23.y : s23.x) : 0u;
+      float dc[4] = {0.f, 0.f, 0.f, 0.f};
+      static_for<bj + 1>([&](auto ic) {
+        constexpr int bi = decltype(ic)::value;
+        constexpr int kk = bj * (bj + 1) / 2 + bi;
+        issue(std::integral_constant<int, kk + KB - 1>{});
+        cp_async_wait_group<KB - 1>();  // this lane's bytes of block kk have landed
+        const uint4 raw = reinterpret_cast<const uint4*>(ring + (kk % KB) * B * B)[lane];
+        if constexpr (bi < bj) {
+          float2 r0 = acc2[bi * B + gq], r1 = acc2[bi * B + gq + 8];
+          float d[4] = {r0.x, r0.y, r1.x, r1.y};
+          M::mma(d, raw.x, raw.z, raw.y, raw.w, br0, br1);
+          if (owner) {
+            acc2[bi * B + gq] = make_float2(d[0], d[1]);
+            acc2[bi * B + gq + 8] = make_float2(d[2], d[3]);
+          }
+        }
+        const uint2 bc = bsrc[bi * 8];
+        M::mma(dc, movm_trans(raw.x), movm_trans(raw.y), movm_trans(raw.z), movm_trans(raw.w), bc.x, bc.y);
+      });
+      // the column's sums: row block bj has taken no row part yet
+      if (owner) {
+        acc2[bj * B + kxq] = make_float2(dc[0], dc[1]);
+        acc2[bj * B + kyq] = make_float2(dc[2], dc[3]);
+      }
+      __syncwarp();  // before later row parts read these from other lanes
+    }
+  });
+  cp_async_wait_group<0>();
+#pragma unroll
+  for (int m = 0; m < PPL; ++m) {
+    const int s = lane + 32 * m;
+    if (s < p) {
+      const float2 a = acc2[s];
+      *reinterpret_cast<float2*>(cur + 2 * (size_t)(p0 + s)) = make_float2(w_in[s], cs[s] + (a.x + a.y) * isc);
+    }
+  }
+  if (valid && lane == 0) partials2[(size_t)(k & 1) * nparts + dsc.tile] = (double)tile_sq;
+}
+
+// ---------------------------------------------------------------------------
 // Dataflow sweeps: one cooperative launch runs every sweep of an inner solve.
 // Sweep k of tile P needs only the sweep-(k-1) waves of the tiles across its
 // lines (the one-sweep delay of Eq. 11), so instead of a kernel boundary per
@@ -2004,6 +2279,15 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   const int wsym_threads = 32 * (wsym_warps + 4);
   const size_t wsym_smem = wsym_warps * wsym_per_warp;
   const size_t wflow_smem = kWflowWarps * wsym_per_warp;
+  // kernel 11 (tensor-core block products): 16-bit blocks, at most 128 ports
+  // per tile; per warp the ring, w_in, residual terms, c and (hi, lo) sums
+  const bool wmma_ok = sym_ok && prec != VTM_PREC_FP32 && pp_max <= kWmmaNB * kSymB;
+  const size_t wmma_per_warp = (size_t)kWsymKB16 * 2 * kSymB * kSymB + 20 * (size_t)pp_max + 64 * kWmmaNB;
+  int wmma_warps = std::min(28, std::max(1, (P->nparts + sms - 1) / sms));
+  wmma_warps = std::max(1, std::min(wmma_warps, (int)(220 * 1024 / wmma_per_warp)));
+  const int wmma_grid = (P->nparts + wmma_warps - 1) / wmma_warps;
+  const int wmma_threads = 32 * (wmma_warps + 4);
+  const size_t wmma_smem = wmma_warps * wmma_per_warp;
   auto with_wsym = [&](auto fn) {
     const bool wide = pp_max > 128;
     if (prec == VTM_PREC_FP32) {
@@ -2040,8 +2324,9 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   L2Window l2win(P, prec);
   // one sweep launch with kernel `kc` (1 direct, 2 staged, 3/4 vector loads with
   // 256/128 threads, 5/6 packed symmetric (128 threads, 85/64 registers), 7 packed
-  // symmetric with the tile in shared memory by one bulk copy; 8, the dataflow
-  // sweeps, is launched once per inner solve by launch_flow)
+  // symmetric with the tile in shared memory by one bulk copy; 9 one warp per
+  // tile, 11 the same with the block products as warp MMAs; 8 and 10, the
+  // dataflow sweeps, are launched once per inner solve)
   auto launch_one = [&](int kc) {
     if (kc == 7) {
       auto go = [&](auto* kern, const auto* Tp) {
@@ -2054,6 +2339,17 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
       else with16([&](auto h) {
         using H = decltype(h);
         go(sweep_symb_kernel<H, 128>, P->d_Tp16.as<H>());
+      });
+      return;
+    }
+    if (kc == 11) {
+      with16([&](auto h) {
+        using H = decltype(h);
+        launch_packed(P, sweep_wmma_kernel<H, kWsymKB16>, wmma_grid, wmma_threads, wmma_smem, s,
+                      P->d_Tp16.as<H>(), P->d_tdesc.as<TileDesc>(), P->d_twin.as<int32_t>(),
+                      P->d_kd32.as<float2>(), P->d_run.as<uint8_t>(), P->d_c32.as<float>(),
+                      P->d_fstate32.as<float>(), npt_, P->d_ctrl.as<SweepCtrl>(), P->d_partials.as<double>(),
+                      hist, hist_len, P->nparts, pp_max);
       });
       return;
     }
@@ -2267,7 +2563,7 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
     return cudaLaunchCooperativeKernel(wflow_kfn, wflow_grid, 32 * kWflowWarps, args, wflow_smem, s);
   };
   const bool symload = ((choice == 5 || choice == 6 || choice == 9) && sym_ok) || (choice == 7 && symb_ok) ||
-                       (choice == 8 && flow_ok) || (choice == 10 && wflow_ok);
+                       (choice == 8 && flow_ok) || (choice == 10 && wflow_ok) || (choice == 11 && wmma_ok);
   if (P->opts.method == VTM_METHOD_ASYNC && !flow_ok && !wflow_ok) {
     set_detail("vtm_solve: asynchronous VTM runs on the packed symmetric dataflow kernel: it needs "
                "FP32/BF16/FP16 sweeps of a symmetric plan with at most 256 ports per sub-circuit");
@@ -2279,6 +2575,11 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
       e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsym_smem);
     });
     VTM_CUDA_TRY(e);
+  }
+  if (wmma_ok) {
+    VTM_CUDA_TRY(cudaFuncSetAttribute(pick16((const void*)sweep_wmma_kernel<__nv_bfloat16, kWsymKB16>,
+                                             (const void*)sweep_wmma_kernel<__half, kWsymKB16>),
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wmma_smem));
   }
   if (symb_ok) {
     VTM_CUDA_TRY(cudaFuncSetAttribute(prec == VTM_PREC_FP32
@@ -2297,10 +2598,10 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
       const bool can_vec128 = nv_max <= 128;
       float best = 1e30f;
       int best_k = 1;
-      for (int cand = 1; cand <= 10; ++cand) {
+      for (int cand = 1; cand <= 11; ++cand) {
         if ((cand == 2 && !can_st) || (cand == 3 && !can_vec) || (cand == 4 && !can_vec128) ||
             ((cand == 5 || cand == 6 || cand == 9) && !sym_ok) || (cand == 7 && !symb_ok) ||
-            (cand == 8 && !flow_ok) || (cand == 10 && !wflow_ok))
+            (cand == 8 && !flow_ok) || (cand == 10 && !wflow_ok) || (cand == 11 && !wmma_ok))
           continue;
         if (cand == 8 || cand == 10) {  // one launch of 8 sweeps, per-sweep time against the others' 6
           SweepCtrl t = h;
@@ -2450,7 +2751,7 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   else *sweep_out = std::min(r.k - 1, budget);
   if (prec == VTM_PREC_FP64)
     P->wave_slot = P->d_state64.as<double>() + (size_t)(*sweep_out & 1) * npt * 2;
-  else if (kern == 9)  // three slots
+  else if (kern == 9 || kern == 11)  // three slots
     P->wave_slot = P->d_fstate32.as<float>() + (size_t)(*sweep_out % 3) * npt * 2;
   else
     P->wave_slot = P->d_state32.as<float>() + (size_t)(*sweep_out & 1) * npt * 2;

@@ -44,7 +44,7 @@ def test_power_grid_2048_as_benchmarked(vtm, power_grid, precision):
     st = plan.stats()
     assert st["nparts"] == 4096 and st["nports"] == 516096
     assert st["sum_p2"] == 65282048 and st["sum_tri"] == 32899072
-    assert st["sweep_kernel"] in (5, 6, 7, 8, 9, 10) and st["packed_bytes"] > 0
+    assert st["sweep_kernel"] in (5, 6, 7, 8, 9, 10, 11) and st["packed_bytes"] > 0
     assert O.residual_norms(A, x.cpu().numpy()[None], w.b[:1]).max() <= TOL_CHECK
     assert torch.equal(x, x2) and info["sweeps"] == info2["sweeps"]
     plan.close()

@@ -237,7 +237,9 @@ def test_every_sweep_kernel_matches_oracle(vtm, kernel):
                                                     ("fp16", 7, (90, 18)), ("fp16", 8, (192, 48)),
                                                     ("fp32", 9, (90, 18)), ("fp32", 9, (192, 48)),
                                                     ("bf16", 9, (90, 18)), ("fp16", 9, (192, 48)),
-                                                    ("fp32", 10, (90, 18)), ("fp16", 10, (192, 32))])
+                                                    ("fp32", 10, (90, 18)), ("fp16", 10, (192, 32)),
+                                                    ("fp16", 11, (90, 18)), ("bf16", 11, (90, 18)),
+                                                    ("fp16", 11, (192, 32)), ("bf16", 11, (256, 32))])
 def test_packed_symmetric_sweeps_follow_the_oracle(vtm, precision, kernel, shape):
     # T_P is symmetric (scalar W, symmetric A): the packed kernels read the
     # 16x16 blocks on and above the diagonal only.  18x18 tiles have 72, 54 or
@@ -322,6 +324,69 @@ def test_warp_per_tile_sweep_against_kernel_5(vtm, precision):
     assert k >= 5 and np.allclose(h9[:k], h5[:k], rtol=rtol, atol=0)
 
 
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_tensor_core_block_products_against_kernel_9(vtm, precision):
+    # kernel 11 applies each block by warp MMAs with the waves as scaled
+    # 16-bit (hi, lo) pairs: the same iteration as kernel 9 up to rounding
+    # well inside the stored precision of T_P, bitwise repeatable, the same
+    # FP64-verified result; 32x32 tiles (126 ports, eight block rows) and
+    # 24x24 tiles (94 ports, a ragged last block)
+    for shape in ((256, 32), (192, 24)):
+        n, t = shape
+        w = wl.power_grid(n, n, t, t, Zc=1.0, seed=21)
+        A = w.csr()
+        b = torch.from_numpy(w.b[0]).cuda()
+        res = {}
+        for kernel in (9, 11):
+            plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc,
+                            precision=precision, sweep_kernel=kernel)
+            plan.set_options(history_len=40)
+            x, info = plan.solve(b, tol=1e-10)
+            x2, info2 = plan.solve(b, tol=1e-10)
+            assert plan.stats()["sweep_kernel"] == kernel
+            assert torch.equal(x, x2) and info["sweeps"] == info2["sweeps"]
+            assert O.residual_norms(A, x.cpu().numpy()[None], w.b[:1]).max() <= 1e-10
+            res[kernel] = (x.cpu().numpy(), info, plan.history)
+        x9, i9, h9 = res[9]
+        x11, i11, h11 = res[11]
+        assert abs(i11["sweeps"] - i9["sweeps"]) <= max(4, i9["sweeps"] // 20)
+        assert np.abs(x11 - x9).max() <= 1e-6 * np.abs(x9).max()
+        # the waves' rounding (2^-22 / 2^-16 of the tile's largest) is far below
+        # T_P's (2^-11 / 2^-8): the residual histories agree closely
+        rtol = {"fp16": 2e-3, "bf16": 5e-3}[precision]
+        k = int(np.count_nonzero((h9 > 0) & (h11 > 0))) // 2
+        assert k >= 5 and np.allclose(h11[:k], h9[:k], rtol=rtol, atol=0)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_tensor_core_sweep_is_invariant_to_power_of_two_scaling(vtm, precision):
+    # the per-tile scale of the waves is a power of two, so solving for 2^e b
+    # repeats the iteration for b exactly: with 2^24 the waves are far above
+    # FP16's largest number, with 2^-12 their low halves would be subnormal
+    # (the FP32 residual squares stay normal at both ends)
+    w = wl.power_grid(128, 128, 32, 32, Zc=1.0, seed=22)
+    b = torch.from_numpy(w.b[0]).cuda()
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc,
+                    precision=precision, sweep_kernel=11)
+    x, info = plan.solve(b, tol=1e-10)
+    for e in (-12, 24):
+        xe, ie = plan.solve(b * 2.0 ** e, tol=1e-10)
+        assert ie["sweeps"] == info["sweeps"] and ie["outer_steps"] == info["outer_steps"]
+        assert torch.equal(xe, x * 2.0 ** e)
+
+
+def test_tensor_core_sweep_falls_back_where_it_does_not_fit(vtm):
+    # FP32 blocks, or sub-circuits of more than 128 ports: the request for
+    # kernel 11 runs the direct-load kernel, and the solve is the same
+    for precision, shape in (("fp32", (128, 32)), ("fp16", (192, 48))):
+        n, t = shape
+        w = wl.power_grid(n, n, t, t, Zc=1.0, seed=23)
+        plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc,
+                        precision=precision, sweep_kernel=11)
+        x, _ = plan.solve(torch.from_numpy(w.b[0]).cuda(), tol=1e-10)
+        assert O.residual_norms(w.csr(), x.cpu().numpy()[None], w.b[:1]).max() <= 1e-10
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])
 def test_warp_per_tile_sweep_with_more_tiles_than_resident_warps(vtm, precision):
     # 16384 tiles of 8x8 (32 ports): 28 tile warps per CTA, 586 CTAs, several
@@ -331,7 +396,7 @@ def test_warp_per_tile_sweep_with_more_tiles_than_resident_warps(vtm, precision)
     A = w.csr()
     b = torch.from_numpy(w.b[0]).cuda()
     xs = {}
-    for kernel in (5, 9):
+    for kernel in ((5, 9) if precision == "fp32" else (5, 9, 11)):
         plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc,
                         precision=precision, sweep_kernel=kernel)
         x, info = plan.solve(b, tol=1e-10)
@@ -340,11 +405,13 @@ def test_warp_per_tile_sweep_with_more_tiles_than_resident_warps(vtm, precision)
         assert torch.equal(x, x2) and info["sweeps"] == info2["sweeps"]
         assert O.residual_norms(A, x.cpu().numpy()[None], w.b[:1]).max() <= 1e-10
         xs[kernel] = (x.cpu().numpy(), info["sweeps"])
-    assert abs(xs[9][1] - xs[5][1]) <= max(4, xs[5][1] // 20)
-    assert np.abs(xs[9][0] - xs[5][0]).max() <= 1e-6 * np.abs(xs[5][0]).max()
+    for kernel in xs:
+        assert abs(xs[kernel][1] - xs[5][1]) <= max(4, xs[5][1] // 20)
+        assert np.abs(xs[kernel][0] - xs[5][0]).max() <= 1e-6 * np.abs(xs[5][0]).max()
 
 
-@pytest.mark.parametrize("precision,kernel", [("fp32", 5), ("fp32", 6), ("fp16", 7), ("bf16", 7), ("fp16", 9)])
+@pytest.mark.parametrize("precision,kernel", [("fp32", 5), ("fp32", 6), ("fp16", 7), ("bf16", 7), ("fp16", 9),
+                                              ("fp16", 11), ("bf16", 11)])
 def test_overlapped_sweep_launches_compute_the_same_iterates(vtm, precision, kernel):
     # packed sweeps launched as programmatic dependents of the sweep before
     # them (the default) against plain launches: same iterates, same stop,
@@ -376,7 +443,7 @@ def test_bad_options_are_rejected_and_the_plan_keeps_its_own(vtm):
     w = wl.power_grid(64, 64, 32, 32, Zc=1.0, seed=15)
     plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc)
     with pytest.raises(vtm.VTMError):
-        plan.set_options(sweep_kernel=11)
+        plan.set_options(sweep_kernel=12)
     with pytest.raises(vtm.VTMError):
         plan.set_options(sweep_kernel=-1)
     for bad in (4, 5, -1):
