@@ -107,7 +107,8 @@ def test_reflection_matrices_with_line_admittance(vtm):
         assert np.abs(T_lib - T_ref[np.ix_(pm, pm)]).max() < 1e-11
 
 
-@pytest.mark.parametrize("precision,kernel", [("fp32", 5), ("fp32", 7), ("bf16", 6), ("fp16", 7)])
+@pytest.mark.parametrize("precision,kernel", [("fp32", 5), ("fp32", 7), ("bf16", 6), ("fp16", 7), ("fp16", 11),
+                                              ("bf16", 11)])
 def test_packed_kernels_with_line_admittance(vtm, precision, kernel):
     # power waves keep the stored operator symmetric: the packed kernels run
     # and the first inner solve follows the oracle's residual history
