@@ -1598,25 +1598,38 @@ __global__ void __launch_bounds__(1024, 1) sweep_wmma_kernel(
   }
   const float* prev = state3 + (size_t)((k - 1) % 3) * nports * 2;
   float* cur = state3 + (size_t)(k % 3) * nports * 2;
-  // incident waves and residual terms of sweep k - 1, c, and the waves' scale
+  // incident waves and residual terms of sweep k - 1, c, and the waves'
+  // scale.  Every port's loads go out before any shared-memory store, so the
+  // lane waits for one round trip, not one per port.
+  float c0v[PPL];
+  float2 wtv[PPL], wsv[PPL], kqv[PPL];
+#pragma unroll
+  for (int m = 0; m < PPL; ++m) {
+    const int s = lane + 32 * m;
+    c0v[m] = 0.f;
+    wtv[m] = wsv[m] = kqv[m] = make_float2(0.f, 0.f);
+    if (s < p) {
+      c0v[m] = c[p0 + s];
+      if (k > 1) {
+        wtv[m] = *reinterpret_cast<const float2*>(prev + 2 * (size_t)tw[m]);
+        wsv[m] = *reinterpret_cast<const float2*>(prev + 2 * (size_t)(p0 + s));
+        kqv[m] = kd[p0 + s];
+      }
+    }
+  }
   float amax = 0.f;
 #pragma unroll
   for (int m = 0; m < PPL; ++m) {
     const int s = lane + 32 * m;
     if (s < nb * B) {
-      float wi = 0.f, rc = 0.f, c0 = 0.f;
-      if (s < p) {
-        c0 = c[p0 + s];
-        if (k > 1) {
-          const float2 wt = *reinterpret_cast<const float2*>(prev + 2 * (size_t)tw[m]);
-          const float2 ws = *reinterpret_cast<const float2*>(prev + 2 * (size_t)(p0 + s));
-          wi = wt.y;
-          rc = port_residual<float>(ws.x, ws.y, wt.x, wt.y, kd[p0 + s]);
-        }
+      float wi = 0.f, rc = 0.f;
+      if (s < p && k > 1) {
+        wi = wtv[m].y;
+        rc = port_residual<float>(wsv[m].x, wsv[m].y, wtv[m].x, wtv[m].y, kqv[m]);
       }
       w_in[s] = wi;
       rs[s] = rc;
-      cs[s] = c0;
+      cs[s] = c0v[m];
       amax = fmaxf(amax, fabsf(wi));
     }
   }
