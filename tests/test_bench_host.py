@@ -1,0 +1,86 @@
+"""Host logic of bench.py (CPU): the algorithmic byte model of one sweep launch
+(the numerator of the roofline fraction), the rule that an ncu traffic record
+counts only for the kernel source and the sweep kernel it was captured from,
+and the reference arm's JSON line (the oracle on the host cores).
+"""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+# the 2048 x 2048 power grid in 32 x 32 tiles (plan statistics)
+GRID2048 = {"nports": 516096, "sum_p2": 65282048, "sum_tri": 32899072}
+
+
+@pytest.mark.parametrize("prec,kernel,expected", [
+    # packed symmetric kernels read the blocks on and above the diagonal:
+    # 2 B x 32,899,072 + 516,096 ports x (7 x 4 B of waves and c + 5 B of
+    # twin index and run byte + 8 B of residual coefficients)
+    (3, 11, 2 * 32899072 + 516096 * 41),
+    (2, 11, 2 * 32899072 + 516096 * 41),
+    (3, 9, 2 * 32899072 + 516096 * 41),
+    (1, 9, 4 * 32899072 + 516096 * 41),
+    # full-matrix kernels read every entry; FP64 waves and coefficients
+    (1, 1, 4 * 65282048 + 516096 * 41),
+    (0, 1, 8 * 65282048 + 516096 * (7 * 8 + 5 + 16)),
+])
+def test_sweep_bytes_follow_the_byte_model(prec, kernel, expected):
+    assert bench.sweep_bytes(dict(GRID2048, sweep_kernel=kernel), prec) == expected
+
+
+def test_fp16_sweep_bytes_of_the_bench_line():
+    # 65.8 MB of stored entries + 21.2 MB of port data (the figure the bench
+    # line reports as algorithmic_bytes_per_launch)
+    assert bench.sweep_bytes(dict(GRID2048, sweep_kernel=11), 3) == 86958080
+
+
+def test_traffic_record_needs_its_own_source_and_kernel(monkeypatch):
+    with open(os.path.join(ROOT, "profiles", "sweep_traffic.json")) as fh:
+        rec = json.load(fh)
+    monkeypatch.setattr(bench, "sweep_kernel_source_hash", lambda: rec["kernel_source_sha256"])
+    for name, prec in (("fp32", 1), ("bf16", 2), ("fp16", 3)):
+        entry = rec["per_launch"][name]
+        for k in entry["sweep_kernels"]:
+            assert bench.traffic_record(prec, {"sweep_kernel": k}, "power_grid") == entry["bytes"]
+        others = [k for k in range(1, 12) if k not in entry["sweep_kernels"]]
+        assert all(bench.traffic_record(prec, {"sweep_kernel": k}, "power_grid") is None for k in others)
+        k0 = entry["sweep_kernels"][0]
+        assert bench.traffic_record(prec, {"sweep_kernel": k0}, "thermal") is None
+    # a changed kernel source voids the record
+    monkeypatch.setattr(bench, "sweep_kernel_source_hash", lambda: "0" * 64)
+    assert bench.traffic_record(3, {"sweep_kernel": rec["per_launch"]["fp16"]["sweep_kernels"][0]},
+                                "power_grid") is None
+
+
+def test_recorded_traffic_is_near_the_algorithmic_bytes():
+    # the ncu DRAM bytes of a cold sweep launch read every stored byte once:
+    # within 10% of the byte model (padding of the 16x16 blocks adds, cached
+    # port data subtracts)
+    with open(os.path.join(ROOT, "profiles", "sweep_traffic.json")) as fh:
+        rec = json.load(fh)
+    for name, prec in (("fp32", 1), ("bf16", 2), ("fp16", 3)):
+        entry = rec["per_launch"][name]
+        model = bench.sweep_bytes(dict(GRID2048, sweep_kernel=entry["sweep_kernels"][0]), prec)
+        assert abs(entry["bytes"] / model - 1) < 0.1, (name, entry["bytes"], model)
+
+
+def test_reference_arm_prints_the_contract_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], capture_output=True, text=True, cwd=ROOT, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == bench.UNIT and line["metric"] == bench.METRIC
+    assert line["higher_is_better"] is True and line["value"] > 0
+    assert abs(line["value"] - bench.SAMPLE_N ** 2 / (line["ms_per_step"] * 1e-3)) <= 1e-6 * line["value"]
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"] and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["config"]["workload"].startswith("power grid 2048x2048")
