@@ -58,6 +58,11 @@ def parse():
                          "waves of their neighbours, FP32/BF16/FP16 symmetric plans)")
     ap.add_argument("--alpha", type=float, default=0.5, help="the weight of --admittance wob")
     ap.add_argument("--radius", type=int, default=1, help="the neighbourhood of --admittance sca")
+    ap.add_argument("--configs", default="all", choices=["all", "none"],
+                    help="all: with the default power-grid line, also time the other configurations "
+                         "(Zc = 0.25 / 4, thermal 64 RHS, VCCS grid VTM / block Jacobi / admittances, "
+                         "gradient step) and report them under 'configs'")
+    ap.add_argument("--config-steps", type=int, default=3, help="timed steps of each extra configuration")
     ap.add_argument("--sweep-kernel", type=int, default=0, choices=list(range(12)),
                     help="0: autotuned, 1: direct-load, 2: bulk-copy staged, 3/4: vector-load (256/128 "
                          "threads), 5/6: packed symmetric (128/64 threads), 7: packed symmetric, tile by "
@@ -166,36 +171,65 @@ class ClockSampler:
 # the oracle on the host (CPU baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(args):
+def oracle_sample(args, workers=None):
     """Run the oracle, as it stands, on the SAMPLE_N x SAMPLE_N instance of
-    the same recipe (same tile size, distributions, Zc and tolerance)."""
+    the same recipe (same tile size, distributions, Zc and tolerance), from
+    scratch (tearing, factorisations, sweeps).  workers = None: the plain
+    single-process oracle; else its iteration spread over that many host
+    processes (the same sub-circuit solves, the same iterates).  Returns
+    (unknowns/s, seconds, sweeps)."""
     from oracle import vtm_oracle as O
+    from oracle.vtm_oracle_mp import vtm_midpoint_mp
     from paper_0910_0663_gb300 import workloads as wl
     w = wl.power_grid(SAMPLE_N, SAMPLE_N, 32, 32, Zc=args.zc, seed=0)
     A = w.csr()
     t0 = time.perf_counter()
-    res = O.vtm_midpoint(A, w.partition, w.nparts, w.b, W=1.0 / w.Zc, tol=TOL)
+    if workers is None:
+        res = O.vtm_midpoint(A, w.partition, w.nparts, w.b, W=1.0 / w.Zc, tol=TOL)
+    else:
+        res = vtm_midpoint_mp(A, w.partition, w.nparts, w.b, W=1.0 / w.Zc, tol=TOL, workers=workers)
     dt = time.perf_counter() - t0
     assert res.converged
     return w.n / dt, dt, res.sweeps
 
 
-def sample_text(sweeps=None):
-    s = (f"oracle VTM (numpy/scipy, FP64, literal Eq. 11 twin-row solves) on the {SAMPLE_N}x{SAMPLE_N} "
-         f"instance of the same power-grid recipe (32x32 tiles, same Zc), solved to 1e-10 from scratch "
-         f"(tearing, local factorisations and sweeps)")
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def sample_text(sweeps=None, workers=None):
+    how = ("the plain single-process oracle" if workers is None else
+           f"the oracle's iteration over {workers} host processes (each owns a share of the "
+           f"sub-circuits; same solves, same iterates)")
+    s = (f"oracle VTM (numpy/scipy, FP64, literal Eq. 11 twin-row solves), {how}, on the "
+         f"{SAMPLE_N}x{SAMPLE_N} instance of the same power-grid recipe (32x32 tiles, same Zc), solved to "
+         f"1e-10 from scratch (tearing, local factorisations and sweeps)")
     if sweeps is not None:
         s += f"; {sweeps} sweeps"
     return s
+
+
+def sample_config(args):
+    return {"workload": f"power grid {SAMPLE_N}x{SAMPLE_N} (the oracle's bounded sample of the "
+                        f"{args.grid}x{args.grid} power-grid recipe: {SAMPLE_N * SAMPLE_N} unknowns, "
+                        f"{(SAMPLE_N // 32) ** 2} tiles of 32x32), Zc={args.zc} ohm, 1 RHS",
+            "sample_of": workload_config(args)["workload"], "n": SAMPLE_N * SAMPLE_N, "nrhs": 1,
+            "tol": TOL, "seed": 0}
 
 
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    from oracle.vtm_oracle_mp import cpu_model
+    cores = host_cores()
     vals = []
+    sweeps = None
     for i in range(args.warmup + args.steps):
-        v, dt, sweeps = oracle_sample(args)
+        v, dt, sweeps = oracle_sample(args, workers=cores)
         if i >= args.warmup:
             vals.append(dt)
     t = float(np.mean(vals))
@@ -203,9 +237,9 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(args),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample_text(sweeps)},
+            "data": "synthetic", "config": sample_config(args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "cpu_model": cpu_model(),
+                             "kind": "oracle", "sample": sample_text(sweeps, cores)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -239,18 +273,25 @@ def measured_peaks():
 
 
 def sweep_bytes(stats, prec, nrhs=1):
-    """Algorithmic bytes of one sweep launch: the reflection matrices once,
-    and per port and right-hand side the twin's (w_in, w_out), its own
-    (w_in, w_out) of the previous sweep, c, the new (w_in, w_out); per port
-    the residual coefficients (g/W, d) (2 x 8 B in FP64, 2 x 4 B otherwise;
-    the batched sweep reads them in FP64), twin index (4 B) and node-run byte
-    (1 B)."""
+    """(algorithmic, overhead) bytes of one sweep launch.
+
+    Algorithmic: the stored reflection matrices once (the entries on and
+    above the diagonal for the packed symmetric kernels, every entry
+    otherwise) and, per port and right-hand side, five wave words: the
+    incident wave gathered from the twin, c, the outgoing wave, and the two
+    words of the residual term that comes from the twin.  Overhead (kept
+    apart): per port the two further wave words the kernels read for their own
+    residual term, the residual coefficients (g/W, d) (2 x 8 B in FP64 and in
+    the batched sweep, 2 x 4 B otherwise), the twin index (4 B) and the
+    node-run byte (1 B)."""
     s_t = {0: 8, 1: 4, 2: 2, 3: 2}[prec]
     s_w = 8 if prec == 0 else 4
     s_kd = 16 if (prec == 0 or nrhs > 1) else 8
     # the packed symmetric kernels need only the entries on and above the diagonal
     entries = stats["sum_tri"] if stats.get("sweep_kernel") in (5, 6, 7, 8, 9, 10, 11) and nrhs == 1 else stats["sum_p2"]
-    return entries * s_t + stats["nports"] * (7 * s_w * nrhs + 5 + s_kd)
+    algorithmic = entries * s_t + stats["nports"] * 5 * s_w * nrhs
+    overhead = stats["nports"] * (2 * s_w * nrhs + 5 + s_kd)
+    return algorithmic, overhead
 
 
 def plan_rowptr(w, dev):
@@ -320,7 +361,7 @@ def gpu_arm(args):
 
     from paper_0910_0663_gb300 import build
     build.build()
-    from paper_0910_0663_gb300 import vtm, workloads as wl
+    from paper_0910_0663_gb300 import workloads as wl
 
     if args.workload == "thermal":
         w = wl.c3_thermal(nrhs=64)
@@ -331,10 +372,6 @@ def gpu_arm(args):
     else:
         w = wl.c2_power_grid(Zc=args.zc, ny=args.grid, nx=args.grid)
     stream = torch.cuda.Stream(dev)
-    bsrc = w.b if args.workload == "thermal" else w.b[0]
-    b_dev = torch.from_numpy(bsrc).to(dev)
-    b_host = torch.from_numpy(bsrc).pin_memory()
-    x_host = torch.empty_like(b_host).pin_memory()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     if args.workload == "vccs":
@@ -345,69 +382,79 @@ def gpu_arm(args):
             precs = ["fp32", "bf16", "fp16"]  # asynchronous sweeps run in FP32/16-bit only
     else:
         precs = [args.precision]
+    adm = None if args.admittance == "alpha" else (args.admittance, args.alpha, args.radius)
     results = {}
-    plans = {}
     errors = {}
     for prec in precs:
         try:
-            results[prec], plans[prec] = run_mode(args, prec, w, dev, stream, b_dev, b_host, x_host,
-                                                  flush, world)
+            results[prec] = run_mode(prec, w, dev, stream, flush, world, args.steps, args.warmup,
+                                     method="bj" if prec.startswith("bj_") else args.method, adm=adm,
+                                     grad=args.workload == "grad", sweep_kernel=args.sweep_kernel,
+                                     l2_persist=args.l2_persist, e2e=True)
         except Exception as exc:  # a failing mode is reported, the others still run
             errors[prec] = repr(exc)
     if not results:
         raise RuntimeError(f"every mode failed: {errors}")
     best = max(results, key=lambda p: results[p]["value"])
-    emit(args, results, errors, best, w, world, rank)
-    for p in plans.values():
-        p.close()
+    configs = None
+    if (args.configs == "all" and args.workload == "power_grid" and args.grid == 2048 and args.method == "vtm"
+            and adm is None and args.precision == "auto" and args.sweep_kernel == 0):
+        configs = run_configs(args, w, dev, stream, flush, world)
+    emit(args, results, errors, best, w, world, rank, configs)
     if world > 1:
         dist.destroy_process_group()
 
 
-def run_mode(args, prec, w, dev, stream, b_dev, b_host, x_host, flush, world):
+def run_mode(prec, w, dev, stream, flush, world, steps, warmup, method="vtm", adm=None, grad=False,
+             sweep_kernel=0, l2_persist=0, e2e=True, Zc=None):
+    """Plan, factor and time one mode on workload w: `steps` solves after
+    `warmup` untimed ones, L2 flushed before each; with e2e also the same
+    solves through the C ABI with pinned host buffers.  The plan is closed
+    before returning."""
     import torch
-    import torch.distributed as dist
     from paper_0910_0663_gb300 import vtm
-    method = "bj" if prec.startswith("bj_") else args.method
+    from paper_0910_0663_gb300 import _vtm as C
     prec_name = prec.split("_")[-1]
-    nrhs = 1 if b_dev.dim() == 1 else b_dev.shape[0]
-    grad = args.workload == "grad"
-    if True:
-        t0 = time.perf_counter()
-        with torch.cuda.stream(stream):
-            plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc,
-                            precision=prec_name, device=dev, stream=stream, factor=False,
-                            sweep_kernel=args.sweep_kernel, l2_persist=args.l2_persist, method=method)
-            if args.admittance != "alpha" and method != "bj":
-                plan.set_admittance(args.admittance, alpha=args.alpha, radius=args.radius, factor=False)
-            t1 = time.perf_counter()
-            plan.factor()
-        torch.cuda.synchronize()
-        if grad:
-            netmap = vtm.C.vtm_netmap_create(w.n, plan_rowptr(w, dev), plan_colidx(w, dev),
-                                             len(w.edges), torch.from_numpy(w.edges[:, 0]).to(dev),
-                                             torch.from_numpy(w.edges[:, 1]).to(dev), stream.cuda_stream)
-            ei = torch.from_numpy(w.edges[:, 0]).to(dev)
-            gg = torch.empty(len(w.edges), dtype=torch.float64, device=dev)
-            gr = torch.empty(w.n, dtype=torch.float64, device=dev)
+    bsrc = w.b if w.b.shape[0] > 1 else w.b[0]
+    nrhs = 1 if bsrc.ndim == 1 else bsrc.shape[0]
+    b_dev = torch.from_numpy(bsrc).to(dev)
+    Zc = w.Zc if Zc is None else Zc
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=Zc,
+                        precision=prec_name, device=dev, stream=stream, factor=False,
+                        sweep_kernel=sweep_kernel, l2_persist=l2_persist, method=method)
+        if adm is not None and method != "bj":
+            plan.set_admittance(adm[0], alpha=adm[1], radius=adm[2], factor=False)
+        t1 = time.perf_counter()
+        plan.factor()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    netmap = None
+    if grad:
+        netmap = C.vtm_netmap_create(w.n, plan_rowptr(w, dev), plan_colidx(w, dev),
+                                     len(w.edges), torch.from_numpy(w.edges[:, 0]).to(dev),
+                                     torch.from_numpy(w.edges[:, 1]).to(dev), stream.cuda_stream)
+        gg = torch.empty(len(w.edges), dtype=torch.float64, device=dev)
+        gr = torch.empty(w.n, dtype=torch.float64, device=dev)
 
-        def step():
-            x, info = plan.solve(b_dev, tol=TOL)
-            if grad:
-                lam, info2 = plan.adjoint(2.0 * x, tol=TOL)
-                vtm.C.vtm_netmap_gradient(netmap, lam, x, 1, gg, gr)
-                info = dict(info)
-                for key in ("sweeps", "kernel_launches", "sweep_launches", "t_sweeps_ms"):
-                    info[key] = info[key] + info2[key]
-                info["relres"] = max(info["relres"], info2["relres"])
-            return x, info
-        t2 = time.perf_counter()
-        # warm-up
-        for _ in range(args.warmup):
+    def step():
+        x, info = plan.solve(b_dev, tol=TOL)
+        if grad:
+            lam, info2 = plan.adjoint(2.0 * x, tol=TOL)
+            C.vtm_netmap_gradient(netmap, lam, x, 1, gg, gr)
+            info = dict(info)
+            for key in ("sweeps", "kernel_launches", "sweep_launches", "t_sweeps_ms"):
+                info[key] = info[key] + info2[key]
+            info["relres"] = max(info["relres"], info2["relres"])
+        return x, info
+    try:
+        for _ in range(warmup):
             with torch.cuda.stream(stream):
                 x, info = step()
         torch.cuda.synchronize()
         if world > 1:
+            import torch.distributed as dist
             dist.barrier()
         times, infos = [], []
         ev0 = torch.cuda.Event(enable_timing=True)
@@ -415,7 +462,7 @@ def run_mode(args, prec, w, dev, stream, b_dev, b_host, x_host, flush, world):
         # clocks are sampled over both timed regions (device-resident and
         # host-buffer calls); the host-buffer warm-up sits between them
         sampler = ClockSampler(dev.index).__enter__()
-        for _ in range(args.steps):
+        for _ in range(steps):
             flush.fill_(1.0)
             torch.cuda.synchronize()
             with torch.cuda.stream(stream):
@@ -427,44 +474,93 @@ def run_mode(args, prec, w, dev, stream, b_dev, b_host, x_host, flush, world):
             infos.append(info)
         t_step = float(np.mean(times))
         value, t_step = job_value(w.n * nrhs, t_step, world, dev)
-        # end to end through the C ABI with host buffers (copies inside)
-        from paper_0910_0663_gb300 import _vtm as C
-        e2e = []
-        # warm-up through host buffers too (the plan's staging buffers are
-        # allocated by the first such call), then the timed calls
-        for _ in range(max(1, args.warmup)):
-            with torch.cuda.stream(stream):
-                C.vtm_solve(plan.handle, b_host, x_host, nrhs, TOL)
-        torch.cuda.synchronize()
-        for _ in range(max(1, args.steps)):
-            flush.fill_(1.0)
+        e2e_value = None
+        if e2e:
+            # end to end through the C ABI with host buffers (copies inside);
+            # warm-up through host buffers too (the plan's staging buffers are
+            # allocated by the first such call), then the timed calls
+            b_host = torch.from_numpy(bsrc).pin_memory()
+            x_host = torch.empty_like(b_host).pin_memory()
+            e2e_t = []
+            for _ in range(max(1, warmup)):
+                with torch.cuda.stream(stream):
+                    C.vtm_solve(plan.handle, b_host, x_host, nrhs, TOL)
             torch.cuda.synchronize()
-            h0 = time.perf_counter()
-            with torch.cuda.stream(stream):
-                C.vtm_solve(plan.handle, b_host, x_host, nrhs, TOL)
-            h1 = time.perf_counter()
-            e2e.append(h1 - h0)
+            for _ in range(max(1, steps)):
+                flush.fill_(1.0)
+                torch.cuda.synchronize()
+                h0 = time.perf_counter()
+                with torch.cuda.stream(stream):
+                    C.vtm_solve(plan.handle, b_host, x_host, nrhs, TOL)
+                h1 = time.perf_counter()
+                e2e_t.append(h1 - h0)
+            e2e_value = w.n * nrhs * world / float(np.mean(e2e_t))
         sampler.__exit__(None, None, None)
         st = plan.stats()
-        inf = infos[-1]
-        bytes_sweep = sweep_bytes(st, {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3}[prec_name], nrhs)
-        # the CUDA events bracket each batch of sweep launches on the plan's
-        # stream; launches past convergence in the last batch return at once
-        # and stay inside the time: per sweep = batch time / sweeps run
-        sweeps_eff = max(1, inf["sweeps"])
-        t_sweep_launch = inf["t_sweeps_ms"] / sweeps_eff
-        achieved = bytes_sweep * sweeps_eff / (inf["t_sweeps_ms"] * 1e-3) / 1e9
-        if grad:
-            vtm.C.vtm_netmap_destroy(netmap)
-        return dict(t_step_ms=t_step, t_plan_s=t1 - t0, t_factor_s=t2 - t1,
-                             value=value, nrhs=nrhs,
-                             e2e_value=w.n * nrhs * world / float(np.mean(e2e)), info=inf, stats=st,
-                             bytes_sweep=bytes_sweep, achieved_gbs=achieved,
-                             t_sweep_ms=t_sweep_launch, clocks=sampler.summary(),
-                             relres=max(i["relres"] for i in infos)), plan
+    finally:
+        if netmap is not None:
+            C.vtm_netmap_destroy(netmap)
+        plan.close()
+    inf = infos[-1]
+    alg, ovh = sweep_bytes(st, {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3}[prec_name], nrhs)
+    # the CUDA events bracket each batch of sweep launches on the plan's
+    # stream; launches past convergence in the last batch return at once
+    # and stay inside the time: per sweep = batch time / sweeps run
+    sweeps_eff = max(1, inf["sweeps"])
+    t_sweep_launch = inf["t_sweeps_ms"] / sweeps_eff
+    achieved = alg * sweeps_eff / (inf["t_sweeps_ms"] * 1e-3) / 1e9
+    return dict(t_step_ms=t_step, t_plan_s=t1 - t0, t_factor_s=t2 - t1, value=value, nrhs=nrhs,
+                e2e_value=e2e_value, info=inf, stats=st, bytes_sweep=alg, overhead_bytes=ovh,
+                achieved_gbs=achieved, t_sweep_ms=t_sweep_launch, clocks=sampler.summary(),
+                relres=max(i["relres"] for i in infos))
 
 
-def emit(args, results, errors, best, w, world, rank):
+def run_configs(args, w2, dev, stream, flush, world):
+    """The other configurations of the method's benchmark set, each timed
+    like the headline (fewer steps): the power grid at Zc = 0.25 and 4 ohm,
+    the RC thermal grid with 64 right-hand sides, the unsymmetric grid with
+    controlled sources (VTM, block Jacobi, VTM with Sec. VIII admittances) and
+    the gradient step on the 1024x1024 grid."""
+    from paper_0910_0663_gb300 import workloads as wl
+    steps, warmup = args.config_steps, max(1, min(args.warmup, 2))
+    peak, _ = measured_peaks()
+    out = {}
+
+    def entry(name, w, prec, **kw):
+        try:
+            r = run_mode(prec, w, dev, stream, flush, world, steps, warmup, e2e=False, **kw)
+        except Exception as exc:
+            out[name] = {"error": repr(exc)}
+            return
+        out[name] = {"mode": prec, "sweeps": r["info"]["sweeps"], "outer_steps": r["info"]["outer_steps"],
+                     "ms_per_step": r["t_step_ms"], "value": r["value"], "unit": UNIT,
+                     "relres": r["relres"], "n": w.n, "nrhs": r["nrhs"],
+                     "sweep_kernel": r["stats"].get("sweep_kernel"),
+                     "batch_kernel": r["stats"].get("batch_kernel"),
+                     "sweep_ms_per_launch": r["t_sweep_ms"],
+                     "sweep_hbm_frac": r["achieved_gbs"] / peak,
+                     "t_plan_s": r["t_plan_s"], "t_factor_s": r["t_factor_s"], "clocks": r["clocks"]}
+
+    for zc in (0.25, 4.0):
+        for prec in ("fp16", "fp64"):
+            entry(f"power_grid_2048_zc{zc:g}_{prec}", w2, prec, Zc=zc)
+    w3 = wl.c3_thermal(nrhs=64)
+    for prec in ("fp32", "bf16", "fp64"):
+        entry(f"thermal_128x128x32_64rhs_{prec}", w3, prec)
+    entry("thermal_128x128x32_64rhs_fp32_sca1", w3, "fp32", adm=("sca", 1.0, 1))
+    del w3
+    w4 = wl.c4_vccs()
+    entry("vccs_1024_vtm_fp64", w4, "fp64")
+    entry("vccs_1024_bj_fp64", w4, "bj_fp64", method="bj")
+    entry("vccs_1024_vtm_sca1_fp64", w4, "fp64", adm=("sca", 1.0, 1))
+    entry("vccs_1024_vtm_wob0.5_fp64", w4, "fp64", adm=("wob", 0.5, 1))
+    del w4
+    w5 = wl.c5_grad_grid()
+    entry("grad_1024_forward_adjoint_gradient_fp32", w5, "fp32", grad=True)
+    return out
+
+
+def emit(args, results, errors, best, w, world, rank, configs=None):
     R = results[best]
     peak, peak_src = measured_peaks()
     prec_id = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3}[best.split("_")[-1]]
@@ -482,6 +578,7 @@ def emit(args, results, errors, best, w, world, rank):
                      "traffic": traffic_record(prec_id, R["stats"], args.workload)
                      if args.grid == 2048 else None,
                      "algorithmic_bytes_per_launch": R["bytes_sweep"],
+                     "overhead_bytes_per_launch": R["overhead_bytes"],
                      "avg_launch_ms": R["t_sweep_ms"]},
         "e2e": {"value": R["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": w.n * 8 * R["nrhs"],
                 "d2h_bytes_per_step": w.n * 8 * R["nrhs"]},
@@ -489,10 +586,12 @@ def emit(args, results, errors, best, w, world, rank):
         "clocks": R["clocks"],
         "sweeps": R["info"]["sweeps"], "outer_steps": R["info"]["outer_steps"],
         "relres": R["relres"],
-        "setup": {"t_plan_s": R["t_plan_s"], "t_factor_s": R["t_factor_s"]},
+        "setup": {"t_plan_s": R["t_plan_s"], "t_factor_s": R["t_factor_s"],
+                  "t_plan_factor_solve_s": R["t_plan_s"] + R["t_factor_s"] + R["t_step_ms"] * 1e-3},
         "modes": {p: {"value": r["value"], "ms_per_step": r["t_step_ms"], "sweeps": r["info"]["sweeps"],
                       "outer_steps": r["info"]["outer_steps"], "relres": r["relres"],
-                      "sweep_gbs": r["achieved_gbs"], "t_factor_s": r["t_factor_s"],
+                      "sweep_gbs": r["achieved_gbs"], "sweep_hbm_frac": r["achieved_gbs"] / peak,
+                      "t_plan_s": r["t_plan_s"], "t_factor_s": r["t_factor_s"],
                       "sweep_ms_per_launch": r["t_sweep_ms"], "sweep_kernel": r["stats"].get("sweep_kernel"),
                       "gpu_launches": r["info"]["kernel_launches"]}
                   for p, r in results.items()},
@@ -501,10 +600,16 @@ def emit(args, results, errors, best, w, world, rank):
         line["mode_errors"] = errors
     if "fp64" in results:
         line["vs_plain_fp64"] = R["value"] / results["fp64"]["value"]
+    if configs is not None:
+        line["configs"] = configs
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "power_grid":
-        v, dt, sweeps = oracle_sample(args)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": sample_text(sweeps), "seconds": dt}
+        from oracle.vtm_oracle_mp import cpu_model
+        cores = host_cores()
+        v, dt, sweeps = oracle_sample(args, workers=cores)
+        v1, dt1, _ = oracle_sample(args)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "cpu_model": cpu_model(),
+                                "kind": "oracle", "sample": sample_text(sweeps, cores), "seconds": dt,
+                                "single_process": {"value": v1, "seconds": dt1, "cores": 1}}
     if rank == 0:
         print(json.dumps(line))
 

@@ -93,7 +93,11 @@ typedef struct {
                         tol/2 instead.  An inner solve also ends when its residual has
                         not dropped by 10% within 64 sweeps (its rounding floor); the
                         FP64 refinement then continues. */
-  int max_outer;     /* refinement steps in the FP32/BF16/FP16 modes; default 40 */
+  int max_outer;     /* refinement steps in the FP32/BF16/FP16 modes; default 40.  Every
+                        step must cut ||b - A x|| by 10x (FP32 sweeps) or 2x (BF16/FP16),
+                        or by 10% once ||r|| is within that factor of the target; a step
+                        that gains less ends the solve with VTM_ENOCONV (refinement
+                        stalled; x = the iterate so far) */
   int method;        /* VTM_METHOD_VTM (default), VTM_METHOD_BJ (chosen at vtm_plan only) or
                         VTM_METHOD_ASYNC (switchable with VTM by vtm_set_opts) */
   int batch;         /* several right-hand sides: 0 (default) one batched iteration over
@@ -140,6 +144,23 @@ typedef struct {
   double* history;   /* optional host array: relative (interface) residual after each
                         sweep k=1..history_len of the first column; NULL = not recorded */
   int history_len;
+  int batch_kernel;  /* batched sweep of several right-hand sides: 0 (default) autotuned
+                        at the first batched solve of each precision; 1: CUDA cores,
+                        persistent grid over the work list; 2: BF16 tensor cores
+                        (warp MMAs, FP32 accumulate), persistent; 3, 4: the same with
+                        one work item per CTA.  A tensor-core request in another
+                        precision, or with a column count that is not a multiple of 8,
+                        runs the CUDA-core variant of the same grid */
+  int wait_polls;    /* polls a bounded device-side wait of the dataflow sweeps
+                        (kernels 8 and 10) makes before it gives up with VTM_ETIMEOUT;
+                        0: default 4194304 (a few seconds).  The bulk-copy waits of
+                        kernels 2 and 7 keep their own limit: a CTA never leaves while a
+                        copy into its shared memory is in flight */
+  int flow_lag;      /* 0 (default): a dataflow tile starts sweep k once the residual
+                        decision of sweep k - 2 is out.  -1: every tile waits for the
+                        decision of its own sweep, which cannot come -- a host-made hang
+                        that the bounded waits end with VTM_ETIMEOUT (a test of that
+                        path; the plan stays usable) */
 } vtm_opts;
 
 typedef struct {
@@ -171,6 +192,8 @@ typedef struct {
   int64_t sum_tri;       /* sum over sub-circuits of p_P (p_P + 1) / 2: the entries of the
                             symmetric reflection matrices on and above the diagonal */
   int64_t packed_bytes;  /* bytes of the packed symmetric copies (0 if none) */
+  int32_t batch_kernel;  /* batched sweep variant of the last batched solve (see
+                            vtm_opts.batch_kernel; 0: none yet) */
 } vtm_plan_stats;
 
 /* vtm_plan -- wire tearing (Sec. V) and the port table.
@@ -275,6 +298,19 @@ vtm_status vtm_get_ports(vtm_plan_t plan, int32_t* node, int32_t* remote, int32_
  * doubles); *p receives p_P.  Requires vtm_factor. */
 vtm_status vtm_get_reflection(vtm_plan_t plan, int32_t part, double* T, int64_t cap, int32_t* p);
 
+/* vtm_get_reflection_stored -- T_P of sub-circuit `part` as the sweeps of the
+ * plan's precision read it, converted to FP64: for FP32/BF16/FP16 plans the
+ * packed 16x16 blocks on and above the diagonal (symmetric plans with at most
+ * 256 ports per sub-circuit; each stored entry is the rounded mean of T_P(s,q)
+ * and T_P(q,s), Sec. VIII symmetry) or else the full low-precision copy; for
+ * FP64 plans the FP64 matrix.  Layout, port order and wave scaling as
+ * vtm_get_reflection (p_P x p_P row-major in host array T of capacity `cap`),
+ * so that T - vtm_get_reflection(T) is the storage rounding the sweeps see.
+ * *stored receives the element size in bytes (8, 4 or 2) and *packed 1 if the
+ * packed blocks were read.  Requires vtm_factor. */
+vtm_status vtm_get_reflection_stored(vtm_plan_t plan, int32_t part, double* T, int64_t cap,
+                                     int32_t* p, int32_t* stored, int32_t* packed);
+
 /* vtm_march -- backward-Euler transient of an RC network with the plan's
  * matrix A = G + C/h: for k = 1..nsteps
  *   A x_k = p_k + (C/h) x_{k-1},
@@ -289,7 +325,7 @@ vtm_status vtm_get_reflection(vtm_plan_t plan, int32_t part, double* T, int64_t 
 vtm_status vtm_march(vtm_plan_t plan, const double* cdiag, const double* p, const double* x0,
                      double* X, int64_t nsteps, double tol, vtm_info* info);
 
-/* vtm_residual_norm -- rel[r] = ||b_r - A x_r||_2 / ||b_r||_2 for each of/* vtm_residual_norm -- rel[r] = ||b_r - A x_r||_2 / ||b_r||_2 for each of
+/* vtm_residual_norm -- rel[r] = ||b_r - A x_r||_2 / ||b_r||_2 for each of
  * nrhs columns, in FP64 on the plan's stream (A = the plan's current values).
  * x, b: n x nrhs column-major (host or device); rel: host array[nrhs]. */
 vtm_status vtm_residual_norm(vtm_plan_t plan, const double* x, const double* b, int64_t nrhs,
@@ -331,8 +367,8 @@ void vtm_netmap_destroy(vtm_netmap_t map);
  * cudaMalloc, code that only holds buffers lent to it).  The paper has no
  * counterpart; this is a service of the library.
  * Needs no plan and allocates nothing: rowptr[n+1], colidx[nnz], vals[nnz],
- * x and b (n x nrhs column-major) must all be device memory; rel is a host
- * array[nrhs].  Work runs on `stream` (a cudaStream_t or NULL) and the call
+ * x and b (n x nrhs column-major) must all be device memory of the current
+ * device (or managed memory); rel is a host array[nrhs].  Work runs on `stream` (a cudaStream_t or NULL) and the call
  * returns after it finished.  Scratch is a fixed 20,736-byte __device__ array
  * in the library, present on every GPU that loads it until the process
  * exits; hence nrhs <= 64 (VTM_EINVAL beyond).  The first call on a device
@@ -340,7 +376,8 @@ void vtm_netmap_destroy(vtm_netmap_t map);
  * call before any stream capture.  All calls on a device share the array,
  * so calls that overlap on the GPU (other streams or threads) race; the
  * array keeps the last call's sums and the call clears what must start at
- * zero.  Errors: VTM_EINVAL (sizes, NULL, host pointers), VTM_ECUDA. */
+ * zero.  Errors: VTM_EINVAL (sizes, NULL, host pointers, memory of another
+ * device; nothing is launched then), VTM_ECUDA. */
 vtm_status vtm_residual_norm_noalloc(int64_t n, const int64_t* rowptr, const int32_t* colidx,
                                      const double* vals, const double* x, const double* b,
                                      int64_t nrhs, double* rel, void* stream);

@@ -32,7 +32,8 @@ class vtm_opts(ctypes.Structure):
                 ("l2_persist", ctypes.c_int), ("sweep_kernel", ctypes.c_int), ("graphs", ctypes.c_int),
                 ("pdl", ctypes.c_int),
                 ("history", ctypes.POINTER(ctypes.c_double)),
-                ("history_len", ctypes.c_int)]
+                ("history_len", ctypes.c_int), ("batch_kernel", ctypes.c_int),
+                ("wait_polls", ctypes.c_int), ("flow_lag", ctypes.c_int)]
 
 
 class vtm_info(ctypes.Structure):
@@ -52,7 +53,7 @@ class vtm_plan_stats(ctypes.Structure):
                 ("max_band", ctypes.c_int32), ("symmetric", ctypes.c_int32),
                 ("t_bytes", ctypes.c_int64), ("factor_bytes", ctypes.c_int64),
                 ("sweep_kernel", ctypes.c_int32), ("sum_tri", ctypes.c_int64),
-                ("packed_bytes", ctypes.c_int64)]
+                ("packed_bytes", ctypes.c_int64), ("batch_kernel", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -87,6 +88,8 @@ def _load():
         "vtm_plan_get_stats": (ctypes.c_int, [P, ctypes.POINTER(vtm_plan_stats)]),
         "vtm_get_ports": (ctypes.c_int, [P, P, P, P, P]),
         "vtm_get_reflection": (ctypes.c_int, [P, i32, P, i64, ctypes.POINTER(i32)]),
+        "vtm_get_reflection_stored": (ctypes.c_int, [P, i32, P, i64, ctypes.POINTER(i32),
+                                                     ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "vtm_residual_norm": (ctypes.c_int, [P, P, P, i64, P]),
         "vtm_residual_norm_noalloc": (ctypes.c_int, [i64, P, P, P, P, P, i64, P, P]),
         "vtm_netmap_create": (ctypes.c_int, [i64, P, P, i64, P, P, P, ctypes.POINTER(P)]),
@@ -108,6 +111,7 @@ _lib = _load()
 EXPORTED = ("vtm_plan", "vtm_set_values", "vtm_set_opts", "vtm_set_admittance",
             "vtm_get_admittance", "vtm_factor", "vtm_solve", "vtm_march",
             "vtm_adjoint", "vtm_plan_get_stats", "vtm_get_ports", "vtm_get_reflection",
+            "vtm_get_reflection_stored",
             "vtm_residual_norm", "vtm_residual_norm_noalloc", "vtm_netmap_create",
             "vtm_netmap_values", "vtm_netmap_gradient", "vtm_netmap_destroy", "vtm_destroy",
             "vtm_strerror", "vtm_last_error_detail")
@@ -135,8 +139,11 @@ def _check(status, where):
 
 def make_opts(precision="fp64", max_sweeps=0, check_every=0, inner_tol=0.0, max_outer=0,
               history=None, sweep_kernel=0, method="vtm", batch=0, l2_persist=0, graphs=0,
-              batch_solve=0, pdl=0):
+              batch_solve=0, pdl=0, batch_kernel=0, wait_polls=0, flow_lag=0):
     o = vtm_opts()
+    o.batch_kernel = int(batch_kernel)
+    o.wait_polls = int(wait_polls)
+    o.flow_lag = int(flow_lag)
     o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
     o.max_sweeps = max_sweeps
     o.check_every = check_every
@@ -233,6 +240,17 @@ def vtm_get_reflection(plan, part):
     _check(_lib.vtm_get_reflection(plan, int(part), _ptr(T), T.size, ctypes.byref(p)),
            "vtm_get_reflection")
     return T
+
+
+def vtm_get_reflection_stored(plan, part):
+    """(T, element bytes, packed) -- T_P as the plan's sweeps read it, in FP64."""
+    p, es, pk = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.vtm_get_reflection_stored(plan, int(part), None, 0, ctypes.byref(p), ctypes.byref(es),
+                                          ctypes.byref(pk)), "vtm_get_reflection_stored")
+    T = np.empty((p.value, p.value), np.float64)
+    _check(_lib.vtm_get_reflection_stored(plan, int(part), _ptr(T), T.size, ctypes.byref(p), ctypes.byref(es),
+                                          ctypes.byref(pk)), "vtm_get_reflection_stored")
+    return T, es.value, bool(pk.value)
 
 
 def vtm_residual_norm(plan, x, b, nrhs):

@@ -882,7 +882,7 @@ static vtm_status batch_norms(vtm_plan_s* P, const double* x, const double* b, d
 }
 
 vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, double tol,
-                         vtm_info* info) {
+                         vtm_info* info, bool record_hist) {
   cudaStream_t s = P->stream;
   const int64_t n = P->n;
   const int64_t npt = (int64_t)P->port_node.size();
@@ -950,6 +950,7 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
   const int max_outer = prec == VTM_PREC_FP64 ? 4 : P->opts.max_outer;
   int sweeps_left = P->opts.max_sweeps;
   vtm_status result = VTM_ENOCONV;
+  bool stalled = false;
   const int g1 = grid_n(n * R), g2 = grid_n(npt * R);
   for (int outer = 0; outer < max_outer; ++outer) {
     const double* rhs = outer == 0 ? d_b : r;
@@ -984,6 +985,13 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
         t2[c] = std::max(t_abs * t_abs, 1e-300);
       }
       VTM_CUDA_TRY(cudaMemcpyAsync(P->d_btol2.p, t2.data(), 64 * sizeof(double), cudaMemcpyHostToDevice, s));
+      // residual history of column 0 in the first inner solve (the kernels
+      // record its squared interface residual; relative to ||rhs_0|| below)
+      double* bhist = (record_hist && outer == 0 && P->opts.history && P->opts.history_len > 0)
+                          ? P->d_hist.as<double>()
+                          : nullptr;
+      const int bhist_len = bhist ? P->opts.history_len : 0;
+      if (bhist) VTM_CUDA_TRY(cudaMemsetAsync(bhist, 0, bhist_len * sizeof(double), s));
       BatchCtrl h{};
       h.k = 1;
       h.k_max = sweeps_left;
@@ -1015,7 +1023,7 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
               P->d_item_tile.as<int32_t>(), P->d_item_m0.as<int32_t>(), P->d_item_order.as<int32_t>(),
               nitems, P->d_twin.as<int32_t>(), P->d_kd.as<double2>(), P->d_run.as<uint8_t>(), cc, st,
               npt, R, P->d_bctrl.as<BatchCtrl>(), P->d_bpart.as<double>(), P->d_btol2.as<double>(),
-              nullptr, 0);
+              bhist, bhist_len);
         };
         if (prec == VTM_PREC_BF16 && (kv & 1))
           go(batch_sweep_mma_kernel, 128, P->d_T16.as<__nv_bfloat16>(), P->d_bc.as<float>(),
@@ -1038,7 +1046,12 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
       // for FP16 could overflow on unscaled right-hand sides, so FP16 plans
       // keep the CUDA-core sweep)
       int kv = 0;
-      {
+      if (P->opts.batch_kernel > 0) {
+        // the caller's choice: bit 0 tensor cores (BF16 with R % 8 == 0 only),
+        // bit 1 one work item per CTA
+        kv = P->opts.batch_kernel - 1;
+        if ((kv & 1) && !(prec == VTM_PREC_BF16 && R % 8 == 0)) kv &= ~1;
+      } else {
         if (P->batch_tuned[prec] == 0 || P->batch_tuned_R[prec] != R) {
           float best = 1e30f;
           for (int cand = 0; cand <= 3; ++cand) {
@@ -1064,9 +1077,11 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
           P->batch_tuned_R[prec] = R;
           VTM_CUDA_TRY(cudaMemcpyAsync(P->d_bctrl.p, &h, sizeof(h), cudaMemcpyHostToDevice, s));
           VTM_CUDA_TRY(cudaMemsetAsync(P->d_bstate.p, 0, 4 * (size_t)npt * R * wsz, s));
+          if (bhist) VTM_CUDA_TRY(cudaMemsetAsync(bhist, 0, bhist_len * sizeof(double), s));
         }
         kv = P->batch_tuned[prec] - 1;
       }
+      P->batch_used = kv + 1;
       // batches of check_every launches replayed from a CUDA graph when the
       // plan has its own stream
       const int nb = P->opts.check_every;
@@ -1075,7 +1090,8 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
       if (P->stream && P->opts.graphs != 1) {
         SweepGraph& G = P->batch_graph[prec];
         const uint64_t key = ((uint64_t)kv << 56) ^ ((uint64_t)nb << 32) ^ ((uint64_t)R << 8) ^
-                             (uint64_t)(uintptr_t)P->d_bstate.p;
+                             (uint64_t)(uintptr_t)P->d_bstate.p ^ ((uint64_t)(uintptr_t)bhist << 3) ^
+                             ((uint64_t)bhist_len << 40);
         if (!G.exec || G.key != key) {
           if (G.exec) cudaGraphExecDestroy(G.exec);
           G.exec = nullptr;
@@ -1117,6 +1133,13 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
       }
       flag = hc.flag;
       kc = (flag == 1 || flag == 4) ? hc.conv_sweep : std::min(hc.k - 1, sweeps_left);
+      if (bhist) {
+        std::vector<double> hh(bhist_len);
+        VTM_CUDA_TRY(cudaMemcpyAsync(hh.data(), bhist, bhist_len * sizeof(double), cudaMemcpyDeviceToHost, s));
+        VTM_CUDA_TRY(cudaStreamSynchronize(s));
+        for (int i = 0; i < bhist_len; ++i)
+          P->opts.history[i] = rnorm[0] > 0 ? std::sqrt(hh[i]) / rnorm[0] : 0.0;
+      }
       if (outer == 0 && flag == 1) info->first_sweep_converged = kc;
       info->sweeps += kc;
       sweeps_left -= kc;
@@ -1151,12 +1174,16 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
     P->launch_count++;
     VTM_CUDA_TRY(cudaGetLastError());
     info->outer_steps = outer + 1;
-    bool all_ok = true, bad = false;
+    bool all_ok = true, bad = false, stall = false;
     double worst = 0.0;
     VTM_TRY(batch_norms(P, xacc, d_b, r, R, rr2, bb2));
     for (int c = 0; c < R; ++c) {
       const double rr = rr2[c];
+      const double rprev = rnorm[c];
       rnorm[c] = std::sqrt(rr);
+      // a column that has not met the tolerance must still gain (safeguard)
+      if (rnorm[c] > tol * bnorm[c] && refinement_stalled(prec, rprev, rnorm[c], tol * bnorm[c]))
+        stall = true;
       rel[c] = bnorm[c] > 0 ? rnorm[c] / bnorm[c] : rnorm[c];
       worst = std::max(worst, rel[c]);
       if (!std::isfinite(rr)) bad = true;
@@ -1175,10 +1202,18 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
       result = VTM_ENOCONV;
       break;
     }
+    if (stall) {
+      result = VTM_ENOCONV;
+      stalled = true;
+      break;
+    }
   }
   VTM_CUDA_TRY(cudaMemcpyAsync(d_x, xacc, (size_t)n * R * sizeof(double), cudaMemcpyDeviceToDevice, s));
   VTM_CUDA_TRY(cudaStreamSynchronize(s));
-  if (result == VTM_ENOCONV) set_detail("vtm_solve (batched): tolerance not met");
+  if (result == VTM_ENOCONV)
+    set_detail(stalled ? std::string("vtm_solve (batched): refinement stalled (a step cut ||r|| by less than ") +
+                             std::to_string((int)refinement_min_gain(prec)) + "x)"
+                       : std::string("vtm_solve (batched): tolerance not met"));
   if (result == VTM_EDIVERGED) set_detail("vtm_solve (batched): the iteration diverged");
   return result;
 }

@@ -21,6 +21,8 @@
 // It is stored transposed (row q of the block = column q of the operator)
 // with rows padded to a multiple of 8 elements.
 #include <algorithm>
+#include <cmath>
+#include <cstring>
 
 #include "band.cuh"
 #include "vtm_internal.h"
@@ -691,5 +693,87 @@ extern "C" vtm_status vtm_get_reflection(vtm_plan_t P, int32_t part, double* T, 
   for (int32_t q = 0; q < pp; ++q)
     for (int32_t s = 0; s < pp; ++s)
       T[(size_t)s * pp + q] = blk[(size_t)q * ld + s] * (P->port_d[p0 + s] / P->port_d[p0 + q]);
+  return VTM_OK;
+}
+
+// Host decoding of one stored element of the low-precision copies.
+static double stored_value(const void* base, int64_t i, int esize, int precision) {
+  if (esize == 8) return static_cast<const double*>(base)[i];
+  if (esize == 4) return static_cast<const float*>(base)[i];
+  const uint16_t h = static_cast<const uint16_t*>(base)[i];
+  if (precision == VTM_PREC_BF16) {
+    const uint32_t u = (uint32_t)h << 16;  // BF16 is the upper half of an FP32
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+  }
+  // FP16 (IEEE binary16): sign, 5-bit exponent (bias 15), 10-bit fraction
+  const int sgn = h >> 15, ex = (h >> 10) & 31, fr = h & 1023;
+  double v;
+  if (ex == 0) v = std::ldexp((double)fr, -24);                 // subnormal
+  else if (ex == 31) v = fr ? NAN : INFINITY;
+  else v = std::ldexp(1.0 + fr / 1024.0, ex - 15);
+  return sgn ? -v : v;
+}
+
+extern "C" vtm_status vtm_get_reflection_stored(vtm_plan_t P, int32_t part, double* T, int64_t cap,
+                                                int32_t* p, int32_t* stored, int32_t* packed) {
+  if (!P || part < 0 || part >= P->nparts) return VTM_EINVAL;
+  if (!P->factored) return VTM_ENOTFACTORED;
+  if (P->general) {
+    set_detail("vtm_get_reflection_stored: this plan carries lagged couplings");
+    return VTM_EINVAL;
+  }
+  cudaSetDevice(P->device);
+  const int prec = P->opts.precision;
+  const int32_t pp = P->port_off[part + 1] - P->port_off[part];
+  const bool is_packed = (P->d_Tp32.p || P->d_Tp16.p) && prec != VTM_PREC_FP64;
+  const int esize = prec == VTM_PREC_FP64 ? 8 : prec == VTM_PREC_FP32 ? 4 : 2;
+  if (p) *p = pp;
+  if (stored) *stored = esize;
+  if (packed) *packed = is_packed ? 1 : 0;
+  if (!T) return VTM_OK;
+  if (cap < (int64_t)pp * pp) return VTM_EINVAL;
+  if (pp == 0) return VTM_OK;
+  const int32_t p0 = P->port_off[part];
+  auto unscale = [&](int32_t s, int32_t q) { return P->port_d[p0 + s] / P->port_d[p0 + q]; };
+  if (is_packed) {
+    // blocks (bi <= bj) row-major over (bi, bj); an FP32 block is row-major, a
+    // 16-bit block keeps at the 16 bytes of lane l its row l/4, columns
+    // 4(l%4)..+3, then row l/4 + 8 (the layout pack_sym_kernel writes)
+    const int nb = (pp + kSymB - 1) / kSymB;
+    const int64_t nel = (int64_t)nb * (nb + 1) / 2 * kSymB * kSymB;
+    std::vector<unsigned char> raw((size_t)nel * esize);
+    const unsigned char* src = static_cast<const unsigned char*>(esize == 4 ? P->d_Tp32.p : P->d_Tp16.p);
+    VTM_CUDA_TRY(cudaMemcpy(raw.data(), src + (size_t)P->Tp_off[part] * esize, raw.size(),
+                            cudaMemcpyDeviceToHost));
+    int64_t e = 0;
+    for (int bi = 0; bi < nb; ++bi)
+      for (int bj = bi; bj < nb; ++bj)
+        for (int w = 0; w < kSymB * kSymB; ++w, ++e) {
+          int r = w / kSymB, q4 = w % kSymB;
+          if (esize == 2) {
+            const int l = w >> 3, e8 = w & 7;
+            r = (l >> 2) + ((e8 >> 2) << 3);
+            q4 = ((l & 3) << 2) + (e8 & 3);
+          }
+          const int s = bi * kSymB + r, q = bj * kSymB + q4;
+          if (s >= pp || q >= pp) continue;
+          const double v = stored_value(raw.data(), e, esize, prec);
+          T[(size_t)s * pp + q] = v * unscale(s, q);
+          T[(size_t)q * pp + s] = v * unscale(q, s);
+        }
+    return VTM_OK;
+  }
+  // full copy: per tile a p x ld block of T_P^T (row q = column q of T_P)
+  const int32_t ld = P->T_ld[part];
+  std::vector<unsigned char> raw((size_t)pp * ld * esize);
+  const unsigned char* src = static_cast<const unsigned char*>(
+      esize == 8 ? P->d_T64.p : esize == 4 ? P->d_T32.p : P->d_T16.p);
+  VTM_CUDA_TRY(cudaMemcpy(raw.data(), src + (size_t)P->T_off[part] * esize, raw.size(),
+                          cudaMemcpyDeviceToHost));
+  for (int32_t q = 0; q < pp; ++q)
+    for (int32_t s = 0; s < pp; ++s)
+      T[(size_t)s * pp + q] = stored_value(raw.data(), (int64_t)q * ld + s, esize, prec) * unscale(s, q);
   return VTM_OK;
 }

@@ -49,6 +49,19 @@ vtm_status scratch_on_current_device(double** out) {
   return VTM_OK;
 }
 
+// True if p is device memory of device `dev`, or managed memory (which any
+// device may touch).  Memory of another device would be read over the
+// interconnect at best and fault without peer access at worst.
+bool on_device(const void* p, int dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
 }  // namespace
 
 extern "C" vtm_status vtm_residual_norm_noalloc(int64_t n, const int64_t* rowptr,
@@ -64,9 +77,12 @@ extern "C" vtm_status vtm_residual_norm_noalloc(int64_t n, const int64_t* rowptr
                     " (size of the static scratch)");
     return VTM_EINVAL;
   }
-  if (!vtm::is_device_ptr(rowptr) || !vtm::is_device_ptr(colidx) || !vtm::is_device_ptr(vals) ||
-      !vtm::is_device_ptr(x) || !vtm::is_device_ptr(b)) {
-    vtm::set_detail("vtm_residual_norm_noalloc: matrix and vectors must be device memory");
+  int dev = 0;
+  VTM_CUDA_TRY(cudaGetDevice(&dev));
+  if (!on_device(rowptr, dev) || !on_device(colidx, dev) || !on_device(vals, dev) || !on_device(x, dev) ||
+      !on_device(b, dev)) {
+    vtm::set_detail("vtm_residual_norm_noalloc: matrix and vectors must be device memory of the "
+                    "current device (" + std::to_string(dev) + ")");
     return VTM_EINVAL;
   }
   double* scratch = nullptr;

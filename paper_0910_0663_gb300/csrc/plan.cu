@@ -769,6 +769,7 @@ static void fill_default_opts(vtm_opts* o) {
   if (o->check_every <= 0) o->check_every = 32;
   if (o->max_outer <= 0) o->max_outer = 40;
   if (o->precision < 0 || o->precision > 3) o->precision = 0;
+  if (o->wait_polls <= 0) o->wait_polls = 1 << 22;
 }
 
 extern "C" vtm_status vtm_set_admittance(vtm_plan_t P, int kind, double alpha, int radius,
@@ -864,6 +865,10 @@ extern "C" vtm_status vtm_set_opts(vtm_plan_t P, const vtm_opts* opts) {
   }
   if (o.method < 0 || o.method > 2 || ((o.method == VTM_METHOD_BJ) != (P->method == VTM_METHOD_BJ))) {
     set_detail("vtm_set_opts: method must be 0..2, and block Jacobi is chosen by vtm_plan");
+    return VTM_EINVAL;
+  }
+  if (o.batch_kernel < 0 || o.batch_kernel > 4 || o.wait_polls < 0 || (o.flow_lag != 0 && o.flow_lag != -1)) {
+    set_detail("vtm_set_opts: batch_kernel must be 0..4, wait_polls >= 0, flow_lag 0 or -1");
     return VTM_EINVAL;
   }
   bool prec_changed = o.precision != P->opts.precision;
@@ -1110,6 +1115,7 @@ extern "C" vtm_status vtm_plan_get_stats(vtm_plan_t P, vtm_plan_stats* s) {
                                                          : P->opts.sweep_kernel;
   s->sum_tri = P->sum_tri;
   s->packed_bytes = (int64_t)(P->d_Tp32.bytes + P->d_Tp16.bytes);
+  s->batch_kernel = P->batch_used;
   return VTM_OK;
 }
 

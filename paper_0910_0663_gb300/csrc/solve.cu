@@ -1741,7 +1741,10 @@ __global__ void __launch_bounds__(1024, 1) sweep_wmma_kernel(
 // All CTAs are co-resident (cooperative launch), so the waits always end.
 // ---------------------------------------------------------------------------
 
-constexpr uint32_t kFlowPolls = 1u << 22;  // a few seconds at most
+// A wait gives up after `max_polls` polls (vtm_opts.wait_polls; default 2^22,
+// a few seconds).  lag_sel < 0 (vtm_opts.flow_lag = -1) makes every tile
+// wait for the decision of its own sweep, which needs that very sweep: a
+// host-made hang that the bounded waits must end (VTM_ETIMEOUT).
 
 // Warp 0 waits (bounded) until the published decision has reached sweep
 // k - 2 and every tile across the lines of `tile` has finished sweep k - 1:
@@ -1750,7 +1753,7 @@ constexpr uint32_t kFlowPolls = 1u << 22;  // a few seconds at most
 // then flag 5 is set).  Called by all 32 lanes of warp 0.
 __device__ __forceinline__ bool flow_wait_ready(const int* gk, const int* done,
                                                 const int32_t* __restrict__ nbr, int e0, int e1, int k,
-                                                SweepCtrl* ctrl, int lag = 2) {
+                                                SweepCtrl* ctrl, uint32_t max_polls, int lag = 2) {
   const int lane = threadIdx.x & 31;
   for (int base = e0; base < e1 || base == e0; base += 31) {
     const int e = base + lane;
@@ -1760,7 +1763,7 @@ __device__ __forceinline__ bool flow_wait_ready(const int* gk, const int* done,
     for (;; ++i) {
       const bool ok = !p || *((volatile const int*)p) >= need;
       if (__all_sync(0xffffffffu, ok)) break;
-      if (i >= kFlowPolls) {
+      if (i >= max_polls) {
         if (lane == 0) atomicCAS(&ctrl->flag, 0, 5);
         return false;
       }
@@ -1785,7 +1788,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) sweep_flow_kernel(
     int64_t nports, const int32_t* __restrict__ nbr_off, const int32_t* __restrict__ nbr,
     int* __restrict__ done, unsigned* __restrict__ count, int* __restrict__ gk,
     SweepCtrl* __restrict__ ctrl, double* __restrict__ part4, double* __restrict__ hist,
-    int hist_len, int nparts, int pp_max, int k0) {
+    int hist_len, int nparts, int pp_max, int k0, uint32_t max_polls, int lag_sel) {
   using LD = SymLoad<TT>;
   constexpr int NW = NT / 32;
   constexpr int B = kSymB;
@@ -1813,8 +1816,10 @@ __global__ void __launch_bounds__(NT, 768 / NT) sweep_flow_kernel(
       SymPorts<NT> pt;
       pt.load(twin, kd, run, c, p0, p);
       if (warp == 0) {
-        bool ok = ASYNC ? flow_wait_ready(gk, done, nbr, 0, 0, k, ctrl)
-                        : flow_wait_ready(gk, done, nbr, nbr_off[tile], nbr_off[tile + 1], k, ctrl);
+        const int wlag = lag_sel < 0 ? 0 : 2;
+        bool ok = ASYNC ? flow_wait_ready(gk, done, nbr, 0, 0, k, ctrl, max_polls, wlag)
+                        : flow_wait_ready(gk, done, nbr, nbr_off[tile], nbr_off[tile + 1], k, ctrl, max_polls,
+                                          wlag);
         __threadfence();  // every lane that saw a counter orders its later reads
         if (tid == 0) s_stop = (ok && !*((volatile int*)&ctrl->flag)) ? 0 : 1;
       }
@@ -1901,7 +1906,7 @@ __global__ void __launch_bounds__(32 * kWflowWarps, kWflowCtasPerSm) sweep_wflow
     int* __restrict__ done, unsigned* __restrict__ count, int* __restrict__ gk,
     unsigned* __restrict__ gcount, double* __restrict__ gsum, int G,
     SweepCtrl* __restrict__ ctrl, double* __restrict__ part4, double* __restrict__ hist,
-    int hist_len, int nparts, int pp_max, int k0) {
+    int hist_len, int nparts, int pp_max, int k0, uint32_t max_polls, int lag_sel) {
   using LD = SymLoad<TT>;
   constexpr int B = kSymB;
   constexpr int PPL = 4;
@@ -1966,7 +1971,7 @@ __global__ void __launch_bounds__(32 * kWflowWarps, kWflowCtasPerSm) sweep_wflow
   const int myrow = b0 ? r1 + 8 : r1;
   const int mycol = cg * 4 + (b4 ? 2 : 0) + (b3 ? 1 : 0);
   for (int k = k0;; ++k) {
-    const bool ok = flow_wait_ready(gk, done, nbr, e0, e1, k, ctrl, kLag);
+    const bool ok = flow_wait_ready(gk, done, nbr, e0, e1, k, ctrl, max_polls, lag_sel < 0 ? 0 : kLag);
     __threadfence();  // every lane that saw a counter orders its later reads
     int stop = 0;
     if (lane == 0) stop = (ok && !*((volatile int*)&ctrl->flag)) ? 0 : 1;
@@ -2545,8 +2550,10 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
     int np = P->nparts, ppm = pp_max, hl = hist_len, k0 = 1;
     int64_t npv = npt_;
     double* hp = hist;
+    uint32_t mp = (uint32_t)P->opts.wait_polls;
+    int ls = P->opts.flow_lag;
     void* args[] = {&Tp, &td, &tw, &kdp, &rn, &cp, &st3, &npv, &no, &nbp, &dn, &cnt, &gkp, &ct, &p4, &hp,
-                    &hl, &np, &ppm, &k0};
+                    &hl, &np, &ppm, &k0, &mp, &ls};
     const bool async = P->opts.method == VTM_METHOD_ASYNC;
     const void* kfn =
         prec == VTM_PREC_FP32
@@ -2584,8 +2591,10 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
     int np = P->nparts, ppm = pp_max, hl = hist_len, k0 = 1;
     int64_t npv = npt_;
     double* hp = hist;
+    uint32_t mp = (uint32_t)P->opts.wait_polls;
+    int ls = P->opts.flow_lag;
     void* args[] = {&Tp, &td, &tw, &kdp, &rn, &cp, &st3, &npv, &no, &nbp, &dn, &cnt, &gkp, &gcnt, &gs, &G,
-                    &ct, &p4, &hp, &hl, &np, &ppm, &k0};
+                    &ct, &p4, &hp, &hl, &np, &ppm, &k0, &mp, &ls};
     return cudaLaunchCooperativeKernel(wflow_kfn, wflow_grid, 32 * kWflowWarps, args, wflow_smem, s);
   };
   const bool symload = ((choice == 5 || choice == 6 || choice == 9) && sym_ok) || (choice == 7 && symb_ok) ||
@@ -2860,6 +2869,7 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
   const int max_outer = (prec == VTM_PREC_FP64 || P->general) ? 4 : P->opts.max_outer;
   int sweeps_left = P->opts.max_sweeps;
   vtm_status result = VTM_ENOCONV;
+  bool stalled = false;
   for (int outer = 0; outer < max_outer; ++outer) {
     // inner problem A d = r (r = b at the first step of a cold start)
     const double* rhs = (outer == 0 && !warm) ? d_b : r;
@@ -2969,6 +2979,7 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
     info->outer_steps = outer + 1;
     double rr;
     VTM_TRY(norms(P, xacc, d_b, r, &rr, &bb));
+    const double rprev = rnorm;
     rnorm = std::sqrt(rr);
     info->relres = rnorm / bnorm;
     if (flag == 3 || !std::isfinite(rnorm)) {
@@ -2983,10 +2994,18 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
       result = VTM_ENOCONV;
       break;
     }
+    if (!P->general && refinement_stalled(prec, rprev, rnorm, target)) {
+      result = VTM_ENOCONV;
+      stalled = true;
+      break;
+    }
   }
   VTM_CUDA_TRY(cudaMemcpyAsync(d_x, xacc, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   VTM_CUDA_TRY(cudaStreamSynchronize(s));
-  if (result == VTM_ENOCONV) set_detail("vtm_solve: tolerance not met");
+  if (result == VTM_ENOCONV)
+    set_detail(stalled ? "vtm_solve: refinement stalled (step " + std::to_string(info->outer_steps) +
+                             " cut ||r|| by less than " + std::to_string((int)refinement_min_gain(prec)) + "x)"
+                       : std::string("vtm_solve: tolerance not met"));
   if (result == VTM_EDIVERGED) set_detail("vtm_solve: the iteration diverged");
   return result;
 }
@@ -3002,7 +3021,7 @@ vtm_status solve_columns(vtm_plan_s* P, const double* d_b, double* d_x, int64_t 
     for (int64_t c0 = 0; c0 < nrhs; c0 += 64) {
       const int R = (int)std::min<int64_t>(64, nrhs - c0);
       vtm_info one{};
-      vtm_status st = solve_batched(P, d_b + c0 * P->n, d_x + c0 * P->n, R, tol, &one);
+      vtm_status st = solve_batched(P, d_b + c0 * P->n, d_x + c0 * P->n, R, tol, &one, c0 == 0);
       if (st != VTM_OK && st != VTM_ENOCONV && st != VTM_EDIVERGED) return st;
       if (st != VTM_OK && worst == VTM_OK) worst = st;
       agg.sweeps = std::max(agg.sweeps, one.sweeps);

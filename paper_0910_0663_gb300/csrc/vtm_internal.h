@@ -94,6 +94,24 @@ inline double default_inner_tol(int precision) {
   }
 }
 
+// Refinement safeguard.  Every FP64 refinement step around low-precision
+// sweeps must cut ||b - A x|| by a fixed factor: 10x with FP32 sweeps, 2x
+// with BF16/FP16 ones (whose T_P carries 2^-8 / 2^-11 relative rounding).
+// Once ||r|| is within that factor of the target, a step must still cut it
+// by 10%.  A step that gains less means the refinement has stalled (the
+// inner problem is too ill-conditioned for the storage precision, or the
+// inner tolerance is too loose) and the solve returns VTM_ENOCONV at once
+// instead of spending its remaining steps.
+inline double refinement_min_gain(int precision) {
+  return precision == VTM_PREC_FP32 ? 10.0 : 2.0;
+}
+inline bool refinement_stalled(int precision, double r_prev, double r_now, double target) {
+  if (precision == VTM_PREC_FP64) return false;
+  const double gain = refinement_min_gain(precision);
+  const double need = r_prev > gain * target ? r_prev / gain : 0.9 * r_prev;
+  return !(r_now <= need);
+}
+
 // Packed symmetric reflection matrices: T_P padded to pp = 16 ceil(p/16),
 // cut into 16x16 blocks, of which the upper triangle (bi <= bj) is stored,
 // row-major over (bi, bj), each block row-major.
@@ -256,6 +274,7 @@ struct vtm_plan_s {
   bool bres_init = false;
   int batch_tuned[4] = {0, 0, 0, 0};  // batched sweep variant + 1, per precision
   int batch_tuned_R[4] = {0, 0, 0, 0};  // right-hand sides it was tuned for
+  int batch_used = 0;                   // batched sweep variant + 1 of the last batched solve
   int batch_grid[16] = {0};          // grid per (precision, variant)
 
   // adjoint of an unsymmetric system
@@ -300,7 +319,7 @@ vtm_status residual_norms(vtm_plan_s* P, const double* d_x, const double* d_b, i
 vtm_status residual_pair(vtm_plan_s* P, const double* x, const double* b, double* r, double* rr,
                          double* bb);
 vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, double tol,
-                         vtm_info* info);
+                         vtm_info* info, bool record_hist = false);
 int launch_residual(const int64_t* rowptr, const int32_t* col, const double* val, const double* x,
                     const double* b, int64_t n, double* partials, unsigned* counter, double* out,
                     int max_grid, cudaStream_t s);

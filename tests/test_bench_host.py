@@ -19,26 +19,35 @@ import bench  # noqa: E402
 GRID2048 = {"nports": 516096, "sum_p2": 65282048, "sum_tri": 32899072}
 
 
-@pytest.mark.parametrize("prec,kernel,expected", [
+@pytest.mark.parametrize("prec,kernel,alg,ovh", [
     # packed symmetric kernels read the blocks on and above the diagonal:
-    # 2 B x 32,899,072 + 516,096 ports x (7 x 4 B of waves and c + 5 B of
-    # twin index and run byte + 8 B of residual coefficients)
-    (3, 11, 2 * 32899072 + 516096 * 41),
-    (2, 11, 2 * 32899072 + 516096 * 41),
-    (3, 9, 2 * 32899072 + 516096 * 41),
-    (1, 9, 4 * 32899072 + 516096 * 41),
+    # algorithmic 2 B x 32,899,072 + 516,096 ports x 5 wave words of 4 B (the
+    # twin's outgoing wave, c, the new outgoing wave, the twin's pair for the
+    # residual); overhead per port: the port's own pair (8 B), twin index and
+    # run byte (5 B), residual coefficients (8 B)
+    (3, 11, 2 * 32899072 + 516096 * 20, 516096 * 21),
+    (2, 11, 2 * 32899072 + 516096 * 20, 516096 * 21),
+    (3, 9, 2 * 32899072 + 516096 * 20, 516096 * 21),
+    (1, 9, 4 * 32899072 + 516096 * 20, 516096 * 21),
     # full-matrix kernels read every entry; FP64 waves and coefficients
-    (1, 1, 4 * 65282048 + 516096 * 41),
-    (0, 1, 8 * 65282048 + 516096 * (7 * 8 + 5 + 16)),
+    (1, 1, 4 * 65282048 + 516096 * 20, 516096 * 21),
+    (0, 1, 8 * 65282048 + 516096 * 40, 516096 * (16 + 5 + 16)),
 ])
-def test_sweep_bytes_follow_the_byte_model(prec, kernel, expected):
-    assert bench.sweep_bytes(dict(GRID2048, sweep_kernel=kernel), prec) == expected
+def test_sweep_bytes_follow_the_byte_model(prec, kernel, alg, ovh):
+    assert bench.sweep_bytes(dict(GRID2048, sweep_kernel=kernel), prec) == (alg, ovh)
 
 
 def test_fp16_sweep_bytes_of_the_bench_line():
-    # 65.8 MB of stored entries + 21.2 MB of port data (the figure the bench
-    # line reports as algorithmic_bytes_per_launch)
-    assert bench.sweep_bytes(dict(GRID2048, sweep_kernel=11), 3) == 86958080
+    # 65.8 MB of stored entries + 10.3 MB of wave words: 76.12 MB per sweep
+    # (algorithmic_bytes_per_launch); 10.8 MB of port metadata apart
+    assert bench.sweep_bytes(dict(GRID2048, sweep_kernel=11), 3) == (76120064, 10838016)
+
+
+def test_batched_sweep_bytes_count_every_column():
+    # the batched sweep reads every entry once for all R columns
+    alg, ovh = bench.sweep_bytes(dict(GRID2048, sweep_kernel=11), 2, nrhs=64)
+    assert alg == 2 * 65282048 + 516096 * 5 * 4 * 64
+    assert ovh == 516096 * (2 * 4 * 64 + 5 + 16)
 
 
 def test_traffic_record_needs_its_own_source_and_kernel(monkeypatch):
@@ -67,7 +76,8 @@ def test_recorded_traffic_is_near_the_algorithmic_bytes():
         rec = json.load(fh)
     for name, prec in (("fp32", 1), ("bf16", 2), ("fp16", 3)):
         entry = rec["per_launch"][name]
-        model = bench.sweep_bytes(dict(GRID2048, sweep_kernel=entry["sweep_kernels"][0]), prec)
+        alg, ovh = bench.sweep_bytes(dict(GRID2048, sweep_kernel=entry["sweep_kernels"][0]), prec)
+        model = alg + ovh
         assert abs(entry["bytes"] / model - 1) < 0.1, (name, entry["bytes"], model)
 
 
@@ -80,7 +90,11 @@ def test_reference_arm_prints_the_contract_line():
     assert line["higher_is_better"] is True and line["value"] > 0
     assert abs(line["value"] - bench.SAMPLE_N ** 2 / (line["ms_per_step"] * 1e-3)) <= 1e-6 * line["value"]
     cb = line["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"] and cb["sample"]
+    assert cb["kind"] == "oracle" and cb["cores"] == bench.host_cores() and cb["value"] == line["value"]
+    assert cb["sample"] and cb["cpu_model"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
-    assert line["config"]["workload"].startswith("power grid 2048x2048")
+    # the workload named is the sample the arm times, and which workload it samples
+    assert line["config"]["workload"].startswith("power grid 512x512")
+    assert line["config"]["sample_of"].startswith("power grid 2048x2048")
+    assert line["config"]["n"] == bench.SAMPLE_N ** 2

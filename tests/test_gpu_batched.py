@@ -107,3 +107,32 @@ def test_batched_graph_path_on_a_dedicated_stream(vtm):
     torch.cuda.synchronize()
     assert torch.equal(x1, x2)
     assert O.residual_norms(A, x1.cpu().numpy(), w.b).max() <= 1e-10
+
+
+@pytest.mark.parametrize("precision,batch_kernel", [("fp64", 1), ("fp64", 3), ("bf16", 1), ("bf16", 2),
+                                                    ("bf16", 3), ("bf16", 4)])
+def test_every_batched_variant_against_the_oracle(vtm, precision, batch_kernel):
+    # each variant forced (CUDA cores or BF16 tensor-core warp MMAs; persistent
+    # grid or one work item per CTA): the result is FP64-verified and the
+    # first inner solve of column 0 follows the oracle's VTM iteration on b --
+    # sweep by sweep to 1e-9 in FP64; within the storage rounding of T_P (and,
+    # on the tensor cores, of the waves as BF16 operands) in BF16
+    w = _thermal_small(16, seed=5)
+    A = w.csr()
+    # BF16: an inner tolerance of 1e-4 keeps the first inner solve going past
+    # the default 3e-3, so that several sweeps lie above BF16's rounding floor
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc, precision=precision,
+                    batch_kernel=batch_kernel, inner_tol=1e-4 if precision == "bf16" else 0.0)
+    plan.set_options(history_len=30)
+    x, info = plan.solve(torch.from_numpy(w.b).cuda(), tol=1e-10)
+    assert plan.stats()["batch_kernel"] == batch_kernel
+    assert O.residual_norms(A, x.cpu().numpy(), w.b).max() <= 1e-10
+    ref = O.vtm_midpoint(A, w.partition, w.nparts, w.b[:1], W=1 / w.Zc, tol=0, max_sweeps=30)
+    h, href = plan.history, ref.history[:, 0]
+    if precision == "fp64":
+        k = min(30, info["sweeps"])
+        assert np.allclose(h[:k], href[:k], rtol=1e-9, atol=1e-13)
+    else:
+        k = min(12, int(np.count_nonzero((h > 0) & (href[: len(h)] > 1e-3))))
+        assert k >= 3
+        assert np.allclose(h[:k], href[:k], rtol=5e-2, atol=0)

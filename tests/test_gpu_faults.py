@@ -90,3 +90,52 @@ def test_iterates_after_k_sweeps_match_the_oracle(vtm, k):
                             keep_iterates=True)
     ref = its[k - 1][0]
     assert np.abs(x.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_stalled_refinement_is_reported(vtm, precision):
+    # an inner tolerance of 0.9 lets every inner solve stop after a sweep or
+    # two, so a refinement step gains less than the 10x (FP32) / 2x (BF16) a
+    # step must gain: VTM_ENOCONV long before the 40-step limit, with the
+    # iterate so far; the same plan with default options then solves
+    from paper_0910_0663_gb300 import _vtm as C
+    w = wl.power_grid(128, 128, 32, 32, Zc=1.0, seed=83)
+    A = w.csr()
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc, precision=precision,
+                    inner_tol=0.9)
+    b = torch.from_numpy(w.b[0]).cuda()
+    x = torch.empty_like(b)
+    st, info = C.vtm_solve(plan.handle, b, x, 1, 1e-10, check=False)
+    assert st == C.VTM_ENOCONV
+    assert "stalled" in C.vtm_last_error_detail()
+    assert 1 <= info.outer_steps < 40 and info.relres > 1e-10
+    rel = O.residual_norms(A, x.cpu().numpy()[None], w.b[:1])[0]
+    assert rel == pytest.approx(info.relres, rel=1e-6)
+    plan.set_options(inner_tol=0.0)
+    x2, info2 = plan.solve(b, tol=1e-10)
+    assert O.residual_norms(A, x2.cpu().numpy()[None], w.b[:1]).max() <= 1e-10
+
+
+@pytest.mark.parametrize("kernel", [8, 10])
+def test_bounded_dataflow_wait_times_out_and_the_plan_recovers(vtm, kernel):
+    # flow_lag = -1: every tile waits for the residual decision of its own
+    # sweep, which needs that very sweep -- a wait on a flag that nothing
+    # sets.  With a short poll limit (4096 polls, about a millisecond) the
+    # wait gives up, the launch ends and the solve returns VTM_ETIMEOUT; the
+    # same plan with the default options then solves.  The bulk-copy waits
+    # of kernels 2 and 7 are not shortened (no CTA leaves with a copy into
+    # its shared memory in flight).
+    from paper_0910_0663_gb300 import _vtm as C
+    w = wl.power_grid(128, 128, 32, 32, Zc=1.0, seed=84)
+    A = w.csr()
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc, precision="fp16",
+                    sweep_kernel=kernel, wait_polls=4096, flow_lag=-1)
+    b = torch.from_numpy(w.b[0]).cuda()
+    x = torch.empty_like(b)
+    st, _ = C.vtm_solve(plan.handle, b, x, 1, 1e-10, check=False)
+    assert st == C.VTM_ETIMEOUT
+    assert "bounded wait" in C.vtm_last_error_detail()
+    plan.set_options(wait_polls=0, flow_lag=0)
+    x2, info = plan.solve(b, tol=1e-10)
+    assert plan.stats()["sweep_kernel"] == kernel
+    assert O.residual_norms(A, x2.cpu().numpy()[None], w.b[:1]).max() <= 1e-10

@@ -663,3 +663,133 @@ def test_stochastic_delays_keep_the_fixed_point(max_delay, seed):
     assert np.abs(r.x - x_star).max() <= 1e-8 * np.abs(x_star).max()
     sync = O.vtm_midpoint(A, w.partition, w.nparts, w.b, W=1.0, tol=1e-11)
     assert r.sweeps >= sync.sweeps  # delays slow the exchange down
+
+
+# ---------------------------------------------------------------------------
+# Weighted overlapped block admittance (Sec. VIII choice 4) by its dynamics
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("g0,g", [(0.5, 2.0), (3.0, 0.25)])
+def test_weighted_overlapped_block_admittance_on_two_nodes(g0, g):
+    # W = alpha C with C = 2g (the twin's share of the torn branch).  The error
+    # contracts by |(W - S)/(W + S)| per sweep with S = 2g g0/(2g + g0) the
+    # input admittance of each side (hand-solved), and the weight that makes
+    # alpha 2g = S matches the line: exact by sweep 2.  A weight on g instead of
+    # 2g, or a dropped alpha, breaks both.
+    A, part = _two_node(g0, g0, g)
+    tear = O.tear_midpoint(A, part, 2)
+    S = 2 * g * g0 / (2 * g + g0)
+    b = np.array([[0.7, -0.2]])
+    x_star = np.linalg.solve(A.toarray(), b[0])
+    alpha_match = S / (2 * g)
+    Wm = O.line_admittance_choice(tear, "wob", alpha=alpha_match)
+    _, its = O.vtm_midpoint(A, part, 2, b, W=Wm, tol=0, max_sweeps=3, keep_iterates=True)
+    assert np.abs(its[0][0] - x_star).max() > 1e-3
+    assert np.abs(its[1][0] - x_star).max() < 1e-14
+    for alpha in (0.3, 1.7):
+        Wa = O.line_admittance_choice(tear, "wob", alpha=alpha)
+        _, its = O.vtm_midpoint(A, part, 2, b, W=Wa, tol=0, max_sweeps=10, keep_iterates=True)
+        errs = [np.abs(x[0] - x_star).max() for x in its]
+        rate = abs((alpha * 2 * g - S) / (alpha * 2 * g + S))
+        for k in range(2, 8):
+            if errs[k - 1] < 1e-12:
+                break
+            assert errs[k] / errs[k - 1] == pytest.approx(rate, rel=1e-7)
+
+
+def test_weighted_overlapped_block_with_unit_weight_is_block_jacobi():
+    # alpha = 1 gives W = C, the overlapped-block choice: the same iteration as
+    # block Jacobi over the same sub-circuits, sweep by sweep
+    w = wl.grid2d(16, 16, 8, 8, seed=7)
+    A = w.csr()
+    tear = O.tear_midpoint(A, w.partition, w.nparts)
+    W1 = O.line_admittance_choice(tear, "wob", alpha=1.0)
+    res = O.vtm_midpoint(A, w.partition, w.nparts, w.b, W=W1, tol=0, max_sweeps=15)
+    _, _, _, h_bj = O.block_jacobi(A, w.partition, w.nparts, w.b, tol=0, max_sweeps=15)
+    assert np.allclose(res.history, h_bj, rtol=1e-10, atol=0)
+
+
+# ---------------------------------------------------------------------------
+# Classical iteration matrices (Sec. IX comparison) against plain sweeps and
+# Young's theorem
+# ---------------------------------------------------------------------------
+
+def _gs_sweep(A, x, omega, order):
+    # one relaxation sweep of A x = 0, node by node in `order`, written out
+    x = x.copy()
+    for i in order:
+        s = sum(A[i, j] * x[j] for j in range(len(x)) if j != i)
+        x[i] = (1 - omega) * x[i] + omega * (-s / A[i, i])
+    return x
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_stationary_matrices_equal_elementwise_sweeps(seed):
+    # G x equals one sweep of the update each method performs on A x = 0:
+    # Gauss-Seidel (forward, omega = 1), SOR (forward), SSOR (forward then
+    # backward); a wrong splitting or a transposed triangle fails at once
+    rng = np.random.default_rng(seed)
+    m = 6
+    A = rng.uniform(-1, 1, (m, m))
+    A[np.arange(m), np.arange(m)] = np.abs(A).sum(axis=1) + rng.uniform(0.5, 1.5, m)
+    x = rng.uniform(-1, 1, m)
+    fwd, bwd = list(range(m)), list(range(m - 1, -1, -1))
+    G = O.stationary_iteration_matrix(A, "gs")
+    assert np.allclose(G @ x, _gs_sweep(A, x, 1.0, fwd), rtol=1e-13, atol=1e-14)
+    for om in (0.7, 1.3):
+        G = O.stationary_iteration_matrix(A, "sor", omega=om)
+        assert np.allclose(G @ x, _gs_sweep(A, x, om, fwd), rtol=1e-13, atol=1e-14)
+        G = O.stationary_iteration_matrix(A, "ssor", omega=om)
+        assert np.allclose(G @ x, _gs_sweep(A, _gs_sweep(A, x, om, fwd), om, bwd), rtol=1e-13, atol=1e-14)
+    Gj = O.stationary_iteration_matrix(A, "jacobi")
+    xj = np.array([-sum(A[i, j] * x[j] for j in range(m) if j != i) / A[i, i] for i in range(m)])
+    assert np.allclose(Gj @ x, xj, rtol=1e-13, atol=1e-14)
+
+
+def test_stationary_radii_follow_youngs_theorem():
+    # The 1-D Laplacian tridiag(-1, 2, -1) of order m is consistently ordered:
+    # rho_J = cos(pi/(m+1)), rho_GS = rho_J^2, and SOR at
+    # omega_opt = 2/(1 + sqrt(1 - rho_J^2)) has rho = omega_opt - 1 (as has
+    # every omega above it); SSOR at omega = 1 is symmetric Gauss-Seidel, whose
+    # matrix is I - M^-1 A with M = (D - L) D^-1 (D - U)
+    m = 12
+    A = 2 * np.eye(m) - np.eye(m, k=1) - np.eye(m, k=-1)
+    rj = np.cos(np.pi / (m + 1))
+    assert O.spectral_radius(O.stationary_iteration_matrix(A, "jacobi")) == pytest.approx(rj, rel=1e-12)
+    assert O.spectral_radius(O.stationary_iteration_matrix(A, "gs")) == pytest.approx(rj ** 2, rel=1e-10)
+    w_opt = 2 / (1 + np.sqrt(1 - rj ** 2))
+    # at omega_opt the SOR matrix has one defective eigenvalue: eigvals carry
+    # ~sqrt(eps) of rounding there
+    assert O.spectral_radius(O.stationary_iteration_matrix(A, "sor", omega=w_opt)) == \
+        pytest.approx(w_opt - 1, rel=1e-6)
+    for om in (1.8, 1.9):
+        assert O.spectral_radius(O.stationary_iteration_matrix(A, "sor", omega=om)) == \
+            pytest.approx(om - 1, rel=1e-6)
+    D = np.diag(np.diag(A))
+    Lm, Um = -np.tril(A, -1), -np.triu(A, 1)
+    M = (D - Lm) @ np.linalg.solve(D, D - Um)
+    G_sgs = np.eye(m) - np.linalg.solve(M, A)
+    assert np.allclose(O.stationary_iteration_matrix(A, "ssor", omega=1.0), G_sgs, rtol=1e-12, atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# The multi-process form of the oracle iteration (the timed CPU baseline)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", ["grid", "lagged"])
+def test_multiprocess_oracle_repeats_the_oracle_bitwise(case):
+    # the same sub-circuit solves, spread over worker processes that exchange
+    # the waves through shared memory with one sweep of delay: the same
+    # history and iterate, bit for bit
+    from oracle.vtm_oracle_mp import vtm_midpoint_mp
+    if case == "grid":
+        w = wl.grid2d(24, 24, 8, 6, Zc=0.5, seed=21, nrhs=2)
+    else:
+        w = wl.vccs_grid(24, 24, 8, 8, seed=3)
+    A = w.csr()
+    ref = O.vtm_midpoint(A, w.partition, w.nparts, w.b, W=1 / w.Zc, tol=1e-10, max_sweeps=3000)
+    got = vtm_midpoint_mp(A, w.partition, w.nparts, w.b, W=1 / w.Zc, tol=1e-10, max_sweeps=3000, workers=3)
+    assert got.sweeps == ref.sweeps and got.converged == ref.converged
+    assert np.array_equal(got.history, ref.history)
+    assert np.array_equal(got.x, ref.x)
+    assert np.array_equal(got.w_in, ref.w_in)

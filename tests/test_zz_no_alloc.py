@@ -65,3 +65,41 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(mods):
     with pytest.raises(C.VTMError) as e:  # host vectors are refused, not staged
         C.vtm_residual_norm_noalloc(w.n, rp, ci, va, x.cpu(), x.cpu(), 1)
     assert e.value.status == C.VTM_EINVAL
+
+
+def test_noalloc_at_its_limits_matches_plan_residual(mods):
+    # more nodes than 1216 blocks x 256 threads (the grid is capped and every
+    # partial slot is used) and 64 columns (the last pair of sums)
+    C, vtm = mods
+    w = wl.grid2d(600, 600, 60, 60, seed=32, ground=0.01)
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=1.0, factor=False)
+    g = torch.Generator().manual_seed(5)
+    x = torch.rand((64, w.n), generator=g, dtype=torch.float64).cuda()
+    b = torch.rand((64, w.n), generator=g, dtype=torch.float64).cuda()
+    ref = plan.residual(x, b)
+    rp = torch.from_numpy(w.indptr).cuda()
+    ci = torch.from_numpy(w.indices).cuda()
+    va = torch.from_numpy(w.data).cuda()
+    stream = torch.cuda.current_stream().cuda_stream
+    assert w.n > 1216 * 256
+    for _ in range(2):
+        got = C.vtm_residual_norm_noalloc(w.n, rp, ci, va, x, b, 64, stream)
+        np.testing.assert_allclose(got, ref, rtol=1e-12, atol=0)
+    plan.close()
+
+
+def test_noalloc_refuses_memory_of_another_device(mods):
+    # tensors on cuda:1 while cuda:0 is current: refused before any launch
+    C, _ = mods
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs two visible GPUs")
+    w = wl.grid2d(8, 8, 4, 4, seed=1)
+    d1 = torch.device("cuda", 1)
+    rp = torch.from_numpy(w.indptr).to(d1)
+    ci = torch.from_numpy(w.indices).to(d1)
+    va = torch.from_numpy(w.data).to(d1)
+    x = torch.zeros(w.n, dtype=torch.float64, device=d1)
+    with torch.cuda.device(0):
+        with pytest.raises(C.VTMError) as e:
+            C.vtm_residual_norm_noalloc(w.n, rp, ci, va, x, x, 1)
+    assert e.value.status == C.VTM_EINVAL
