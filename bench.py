@@ -63,12 +63,13 @@ def parse():
                          "(Zc = 0.25 / 4, thermal 64 RHS, VCCS grid VTM / block Jacobi / admittances, "
                          "gradient step) and report them under 'configs'")
     ap.add_argument("--config-steps", type=int, default=3, help="timed steps of each extra configuration")
-    ap.add_argument("--sweep-kernel", type=int, default=0, choices=list(range(12)),
+    ap.add_argument("--sweep-kernel", type=int, default=0, choices=list(range(13)),
                     help="0: autotuned, 1: direct-load, 2: bulk-copy staged, 3/4: vector-load (256/128 "
                          "threads), 5/6: packed symmetric (128/64 threads), 7: packed symmetric, tile by "
                          "one bulk copy, 8: packed symmetric dataflow sweeps (one launch per inner solve), "
                          "9: packed symmetric, one warp per tile, 10: kernel 9's dataflow form, 11: kernel 9 "
-                         "with the block products as warp MMAs (BF16/FP16)")
+                         "with the block products as warp MMAs (BF16/FP16), 12: kernel 9's organisation in "
+                         "double-float arithmetic on packed hi/lo FP32 pairs (FP64 plans)")
     return ap.parse_args()
 
 
@@ -288,7 +289,7 @@ def sweep_bytes(stats, prec, nrhs=1):
     s_w = 8 if prec == 0 else 4
     s_kd = 16 if (prec == 0 or nrhs > 1) else 8
     # the packed symmetric kernels need only the entries on and above the diagonal
-    entries = stats["sum_tri"] if stats.get("sweep_kernel") in (5, 6, 7, 8, 9, 10, 11) and nrhs == 1 else stats["sum_p2"]
+    entries = stats["sum_tri"] if stats.get("sweep_kernel") in (5, 6, 7, 8, 9, 10, 11, 12) and nrhs == 1 else stats["sum_p2"]
     algorithmic = entries * s_t + stats["nports"] * 5 * s_w * nrhs
     overhead = stats["nports"] * (2 * s_w * nrhs + 5 + s_kd)
     return algorithmic, overhead
@@ -315,7 +316,9 @@ def sweep_kernel_name(kernel, nrhs):
             8: "sweep_flow_kernel (dataflow, one cooperative launch)",
             9: "sweep_wsym_kernel (packed symmetric, one warp per tile)",
             10: "sweep_wflow_kernel (dataflow, one warp per tile, one cooperative launch)",
-            11: "sweep_wmma_kernel (packed symmetric, one warp per tile, block products as warp MMAs)"}.get(
+            11: "sweep_wmma_kernel (packed symmetric, one warp per tile, block products as warp MMAs)",
+            12: "sweep_wdf_kernel (packed symmetric FP64 bytes as hi/lo FP32 pairs, double-float arithmetic, "
+                "one warp per tile)"}.get(
                 kernel, str(kernel))
 
 

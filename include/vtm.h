@@ -133,8 +133,13 @@ typedef struct {
                         cores (warp MMAs, FP32 accumulate; the incident waves enter
                         as 16-bit hi + lo pairs scaled per tile by a power of two),
                         BF16/FP16 plans with at most 128 ports per sub-circuit;
-                        where a packed kernel does not fit, 5-11 fall back to
-                        kernel 1 */
+                        12: FP64 plans of a symmetric A with at most 128 ports per
+                        sub-circuit: kernel 9's organisation on the packed blocks kept
+                        as hi + lo FP32 pairs (FP64 bytes, about 48 bits), waves and c
+                        as such pairs, every product and sum in double-float
+                        arithmetic on the FP32 pipes (GB300 runs FP64 arithmetic at a
+                        small fraction of its FP32 rate); where a packed kernel does
+                        not fit, 5-12 fall back to kernel 1 */
   int graphs;        /* 0 (default): replay batches of check_every sweep launches from a
                         CUDA graph when the plan has its own stream; 1: plain launches */
   int pdl;           /* 0 (default): the packed sweeps (kernels 5-7) are launched as
@@ -250,8 +255,9 @@ vtm_status vtm_get_admittance(vtm_plan_t plan, double* W);
 
 /* vtm_set_opts -- replace the options of a plan (precision, limits, history).
  * VTM_EINVAL for a precision outside 0..3, a negative history_len, a history
- * length without an array, or a sweep_kernel outside 0..11; the plan keeps its
- * previous options then. */
+ * length without an array, a sweep_kernel outside 0..12, a batch_kernel
+ * outside 0..4, a negative wait_polls or a flow_lag other than 0 and -1; the
+ * plan keeps its previous options then. */
 vtm_status vtm_set_opts(vtm_plan_t plan, const vtm_opts* opts);
 
 /* vtm_factor -- per sub-circuit factorisation of the condensed local matrix

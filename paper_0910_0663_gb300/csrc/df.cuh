@@ -1,0 +1,106 @@
+// Double-float arithmetic: a value is an unevaluated sum h + l of two FP32
+// numbers with |l| <= ulp(h)/2, about 48 significant bits.  GB300 runs FP64
+// at a small fraction of its FP32 rate, so the FP64-accurate sweep keeps
+// FP64 bytes in HBM and does its arithmetic here, on the FP32 pipes, with
+// error-free transformations:
+//   * TwoSum (Knuth, TAOCP vol. 2, 4.2.2): s + e = a + b exactly;
+//   * FastTwoSum (Dekker 1971): the same when |a| >= |b|;
+//   * TwoProd with an FMA (Ogita, Rump and Oishi, "Accurate sum and dot
+//     product", SIAM J. Sci. Comput. 26, 2005): p + e = a b exactly;
+//   * the double-word additions and products of Joldes, Muller and Popescu,
+//     "Tight and rigorous error bounds for basic building blocks of
+//     double-word arithmetic", ACM TOMS 44, 2017 (AccurateDWPlusDW,
+//     DWTimesFP3, DWTimesDW1);
+//   * dot products accumulated as in Dot2 (Ogita, Rump and Oishi): the high
+//     parts of the products summed with TwoSum, every error term in a second
+//     FP32 accumulator.
+// Every operation is rounded to nearest by the compiler's plain operators;
+// nothing here may be contracted or reassociated (the expressions rely on
+// the exact rounding of each step), hence the explicit __fadd_rn / __fmul_rn.
+#pragma once
+
+namespace vtm {
+
+struct df {
+  float h, l;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ df two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+
+// (a.h + a.l) + (b.h + b.l), relative error below 3 u^2 (u = 2^-24)
+__device__ __forceinline__ df df_add(df a, df b) {
+  const df s = two_sum(a.h, b.h);
+  const df t = two_sum(a.l, b.l);
+  const df v = fast_two_sum(s.h, __fadd_rn(s.l, t.h));
+  return fast_two_sum(v.h, __fadd_rn(t.l, v.l));
+}
+
+__device__ __forceinline__ df df_neg(df a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+
+// (a.h + a.l) y, relative error below 2 u^2
+__device__ __forceinline__ df df_mul_f(df a, float y) {
+  const df c = two_prod(a.h, y);
+  return fast_two_sum(c.h, __fmaf_rn(a.l, y, c.l));
+}
+
+// (a.h + a.l)(b.h + b.l), relative error below 7 u^2
+__device__ __forceinline__ df df_mul(df a, df b) {
+  const df c = two_prod(a.h, b.h);
+  const float tl = __fmaf_rn(a.l, b.h, __fmul_rn(a.h, b.l));
+  return fast_two_sum(c.h, __fadd_rn(c.l, tl));
+}
+
+// Dot2 accumulator: S collects the high parts of the terms exactly (TwoSum
+// errors moved to E), E everything else; the value is S + E.
+struct dacc {
+  float S, E;
+};
+
+// acc += (th + tl)(wh + wl): the product's high part p = rn(th wh) and its
+// exact error, plus the two cross terms (tl wl is below the precision kept)
+__device__ __forceinline__ void dacc_fma(dacc& a, float th, float tl, float wh, float wl) {
+  const float p = __fmul_rn(th, wh);
+  float e = __fmaf_rn(th, wh, -p);
+  e = __fmaf_rn(th, wl, e);
+  e = __fmaf_rn(tl, wh, e);
+  const df s = two_sum(a.S, p);
+  a.S = s.h;
+  a.E = __fadd_rn(a.E, __fadd_rn(s.l, e));
+}
+
+// the first term of a fresh accumulator
+__device__ __forceinline__ dacc dacc_first(float th, float tl, float wh, float wl) {
+  const float p = __fmul_rn(th, wh);
+  float e = __fmaf_rn(th, wh, -p);
+  e = __fmaf_rn(th, wl, e);
+  e = __fmaf_rn(tl, wh, e);
+  return {p, e};
+}
+
+// a + b of two accumulators
+__device__ __forceinline__ dacc dacc_add(dacc a, dacc b) {
+  const df s = two_sum(a.S, b.S);
+  return {s.h, __fadd_rn(__fadd_rn(a.E, b.E), s.l)};
+}
+
+// the accumulator's value as a normalised double-float (TwoSum: S may have
+// cancelled below E)
+__device__ __forceinline__ df dacc_value(dacc a) { return two_sum(a.S, a.E); }
+
+}  // namespace vtm

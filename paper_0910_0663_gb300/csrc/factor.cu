@@ -563,6 +563,43 @@ __global__ void pack_sym_kernel(const double* __restrict__ T64, const TileDesc* 
   }
 }
 
+// Packed double-float copy for the FP64-accurate sweep (kernel 12): the same
+// blocks as the FP32 packed copy, each entry v = (T(s,q) + T(q,s))/2 kept as
+// hi = rn32(v) in the block's first 256 floats and lo = rn32(v - hi) in its
+// next 256 (a block is 512 floats; a tile's blocks start at 2 Tp_off).
+__global__ void pack_sym_df_kernel(const double* __restrict__ T64, const TileDesc* __restrict__ tdesc,
+                                   float* __restrict__ Tp) {
+  const TileDesc d = tdesc[blockIdx.x];
+  const int nb = (d.p + kSymB - 1) / kSymB;
+  const int nel = nb * (nb + 1) / 2 * kSymB * kSymB;
+  const double* Tb = T64 + d.T_off;
+  float* out = Tp + 2 * d.Tp_off;
+  for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+    int blk = e / (kSymB * kSymB);
+    const int w = e % (kSymB * kSymB);
+    const int nblk_before = blk;
+    int bi = 0;
+    while (blk >= nb - bi) {
+      blk -= nb - bi;
+      ++bi;
+    }
+    const int bj = bi + blk;
+    const int s = bi * kSymB + w / kSymB, q = bj * kSymB + w % kSymB;
+    double v = 0.0;
+    if (s < d.p && q < d.p) v = 0.5 * (Tb[(size_t)q * d.ld + s] + Tb[(size_t)s * d.ld + q]);
+    const float h = (float)v;
+    out[(size_t)nblk_before * 2 * kSymB * kSymB + w] = h;
+    out[(size_t)nblk_before * 2 * kSymB * kSymB + kSymB * kSymB + w] = (float)(v - (double)h);
+  }
+}
+
+// the double-float copy serves FP64 plans of a symmetric A with at most 128
+// ports per sub-circuit (kernel 12)
+static bool packed_df_eligible(const vtm_plan_s* P) {
+  return P->symmetric && !P->general && P->max_ports <= 8 * kSymB && !P->port_node.empty() &&
+         P->opts.precision == VTM_PREC_FP64;
+}
+
 // Packed copies are kept for symmetric VTM plans whose sub-circuits have at
 // most 256 ports (16 blocks a side), in the plan's low precision.
 static bool packed_eligible(const vtm_plan_s* P) {
@@ -625,6 +662,14 @@ vtm_status build_reflections(vtm_plan_s* P) {
       pack_sym_kernel<__half><<<P->nparts, 256, 0, s>>>(P->d_T64.as<double>(), P->d_tdesc.as<TileDesc>(),
                                                         P->d_Tp16.as<__half>());
     }
+  }
+  if (packed_df_eligible(P)) {
+    const int64_t np = std::max<int64_t>(P->Tp_elems, 8);
+    VTM_TRY(dev_alloc(P->d_Tpdf, 2 * np * sizeof(float)));
+    pack_sym_df_kernel<<<P->nparts, 256, 0, s>>>(P->d_T64.as<double>(), P->d_tdesc.as<TileDesc>(),
+                                                 P->d_Tpdf.as<float>());
+  } else if (P->d_Tpdf.p) {
+    dev_free(P->d_Tpdf);  // the plan left FP64 (precision changed) or no longer qualifies
   }
   VTM_CUDA_TRY(cudaGetLastError());
   VTM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -727,7 +772,8 @@ extern "C" vtm_status vtm_get_reflection_stored(vtm_plan_t P, int32_t part, doub
   cudaSetDevice(P->device);
   const int prec = P->opts.precision;
   const int32_t pp = P->port_off[part + 1] - P->port_off[part];
-  const bool is_packed = (P->d_Tp32.p || P->d_Tp16.p) && prec != VTM_PREC_FP64;
+  const bool is_df = prec == VTM_PREC_FP64 && P->d_Tpdf.p;
+  const bool is_packed = ((P->d_Tp32.p || P->d_Tp16.p) && prec != VTM_PREC_FP64) || is_df;
   const int esize = prec == VTM_PREC_FP64 ? 8 : prec == VTM_PREC_FP32 ? 4 : 2;
   if (p) *p = pp;
   if (stored) *stored = esize;
@@ -744,9 +790,16 @@ extern "C" vtm_status vtm_get_reflection_stored(vtm_plan_t P, int32_t part, doub
     const int nb = (pp + kSymB - 1) / kSymB;
     const int64_t nel = (int64_t)nb * (nb + 1) / 2 * kSymB * kSymB;
     std::vector<unsigned char> raw((size_t)nel * esize);
-    const unsigned char* src = static_cast<const unsigned char*>(esize == 4 ? P->d_Tp32.p : P->d_Tp16.p);
+    const unsigned char* src = static_cast<const unsigned char*>(
+        is_df ? P->d_Tpdf.p : esize == 4 ? P->d_Tp32.p : P->d_Tp16.p);
     VTM_CUDA_TRY(cudaMemcpy(raw.data(), src + (size_t)P->Tp_off[part] * esize, raw.size(),
                             cudaMemcpyDeviceToHost));
+    // double-float blocks: 256 hi floats, then 256 lo floats
+    auto df_value = [&](int64_t e) {
+      const float* f = reinterpret_cast<const float*>(raw.data());
+      const int64_t blk = e / (kSymB * kSymB), w = e % (kSymB * kSymB);
+      return (double)f[blk * 2 * kSymB * kSymB + w] + (double)f[blk * 2 * kSymB * kSymB + kSymB * kSymB + w];
+    };
     int64_t e = 0;
     for (int bi = 0; bi < nb; ++bi)
       for (int bj = bi; bj < nb; ++bj)
@@ -759,7 +812,7 @@ extern "C" vtm_status vtm_get_reflection_stored(vtm_plan_t P, int32_t part, doub
           }
           const int s = bi * kSymB + r, q = bj * kSymB + q4;
           if (s >= pp || q >= pp) continue;
-          const double v = stored_value(raw.data(), e, esize, prec);
+          const double v = is_df ? df_value(e) : stored_value(raw.data(), e, esize, prec);
           T[(size_t)s * pp + q] = v * unscale(s, q);
           T[(size_t)q * pp + s] = v * unscale(q, s);
         }

@@ -496,6 +496,7 @@ vtm_status assemble_local(vtm_plan_s* P) {
   const bool scalar_w = P->w_kind == VTM_W_ALPHA;
   std::vector<double> beta(npt), bin(npt), bout(npt), rho(npt), kd(2 * npt);
   std::vector<float> kd32(2 * npt);
+  std::vector<float> kddf(4 * npt);  // (g/W, d) as double-float pairs (kernel 12)
   P->port_d.assign(npt, 1.0);
   for (size_t s = 0; s < npt; ++s) {
     const double g = P->port_g[s], W = P->port_W[s];
@@ -509,6 +510,10 @@ vtm_status assemble_local(vtm_plan_s* P) {
     kd[2 * s + 1] = d;
     kd32[2 * s] = (float)(g / W);
     kd32[2 * s + 1] = (float)d;
+    kddf[4 * s] = (float)(g / W);
+    kddf[4 * s + 1] = (float)(g / W - (double)kddf[4 * s]);
+    kddf[4 * s + 2] = (float)d;
+    kddf[4 * s + 3] = (float)(d - (double)kddf[4 * s + 2]);
   }
   P->lag_rho.resize(P->lag_i.size());
   for (size_t q = 0; q < P->lag_i.size(); ++q) {
@@ -557,6 +562,7 @@ vtm_status assemble_local(vtm_plan_s* P) {
   VTM_TRY(upload(P->d_rho, rho, st));
   VTM_TRY(upload(P->d_kd, kd, st));
   VTM_TRY(upload(P->d_kd32, kd32, st));
+  VTM_TRY(upload(P->d_kddf, kddf, st));
   if (P->general) {
     // per input: residual coefficients (g/W and d of a port, rho of a lagged
     // entry) and right-hand-side weight (beta d or -rho); per output: scale
@@ -753,7 +759,7 @@ std::vector<DevBuf*> vtm_plan_s::all_bufs() {
   return {&tabs.node_off, &tabs.bw, &tabs.band_off, &tabs.port_off, &tabs.T_off, &tabs.T_ld,
           &tabs.order, &d_rowptr, &d_colidx, &d_vals, &d_perm, &d_Lc, &d_Uc, &d_Lc32, &d_Uc32, &d_v32,
           &d_port_loc, &d_port_pos, &d_tdesc,
-          &d_twin, &d_beta, &d_bout, &d_rho, &d_kd, &d_kd32, &d_run, &d_T64, &d_T32, &d_T16, &d_Tp32, &d_Tp16, &d_nbr_off, &d_nbr, &d_done, &d_flow, &d_part4, &d_fstate32, &d_c64, &d_c32, &d_state64,
+          &d_twin, &d_beta, &d_bout, &d_rho, &d_kd, &d_kd32, &d_run, &d_T64, &d_T32, &d_T16, &d_Tp32, &d_Tp16, &d_Tpdf, &d_dfstate, &d_cdf, &d_kddf, &d_nbr_off, &d_nbr, &d_done, &d_flow, &d_part4, &d_fstate32, &d_c64, &d_c32, &d_state64,
           &d_state32, &d_v, &d_v2, &d_xacc, &d_r, &d_bcol, &d_partials, &d_ctrl, &d_hist,
           &d_err, &d_red, &d_in_off, &d_out_off, &d_in_src, &d_in_kind, &d_in_twin,
           &d_in_own_out, &d_in_loc, &d_res_perm, &d_res_run, &d_out_loc, &d_in_coef, &d_in_d,
@@ -859,8 +865,8 @@ extern "C" vtm_status vtm_set_opts(vtm_plan_t P, const vtm_opts* opts) {
     set_detail("vtm_set_opts: bad precision or history");
     return VTM_EINVAL;
   }
-  if (o.sweep_kernel < 0 || o.sweep_kernel > 11) {
-    set_detail("vtm_set_opts: sweep_kernel must be 0..11");
+  if (o.sweep_kernel < 0 || o.sweep_kernel > 12) {
+    set_detail("vtm_set_opts: sweep_kernel must be 0..12");
     return VTM_EINVAL;
   }
   if (o.method < 0 || o.method > 2 || ((o.method == VTM_METHOD_BJ) != (P->method == VTM_METHOD_BJ))) {
@@ -1108,13 +1114,13 @@ extern "C" vtm_status vtm_plan_get_stats(vtm_plan_t P, vtm_plan_stats* s) {
   s->max_band = P->max_bw;
   s->symmetric = P->symmetric ? 1 : 0;
   s->t_bytes = (int64_t)(P->d_T64.bytes + P->d_T32.bytes + P->d_T16.bytes + P->d_E.bytes +
-                         P->d_Tp32.bytes + P->d_Tp16.bytes);
+                         P->d_Tp32.bytes + P->d_Tp16.bytes + P->d_Tpdf.bytes);
   s->factor_bytes = (int64_t)(P->d_Lc.bytes + P->d_Uc.bytes);
   s->sweep_kernel = P->opts.method == VTM_METHOD_ASYNC   ? P->dataflow_kernel
                     : P->tuned_kernel[P->opts.precision] ? P->tuned_kernel[P->opts.precision]
                                                          : P->opts.sweep_kernel;
   s->sum_tri = P->sum_tri;
-  s->packed_bytes = (int64_t)(P->d_Tp32.bytes + P->d_Tp16.bytes);
+  s->packed_bytes = (int64_t)(P->d_Tp32.bytes + P->d_Tp16.bytes + P->d_Tpdf.bytes);
   s->batch_kernel = P->batch_used;
   return VTM_OK;
 }

@@ -27,6 +27,7 @@
 #include <type_traits>
 #include <utility>
 
+#include "df.cuh"
 #include "ptx.h"
 #include "vtm_internal.h"
 
@@ -1724,6 +1725,292 @@ __global__ void __launch_bounds__(1024, 1) sweep_wmma_kernel(
 }
 
 // ---------------------------------------------------------------------------
+// FP64-accurate packed sweep in double-float arithmetic (kernel 12; plain
+// FP64 plans of a symmetric A, tiles of at most 128 ports).  GB300 executes
+// FP64 at about 2 FMA per clock per SM, so the FP64 sweeps of the full T_P
+// (kernels 1-4) are bound by that pipe, not by HBM.  This kernel keeps FP64
+// bytes (each stored entry of T_P is the pair hi = rn32(T), lo = rn32(T -
+// hi), 8 bytes, about 48 significant bits; the waves and c are such pairs
+// too) and does all arithmetic on the FP32 pipes with error-free
+// transformations (df.cuh): the products of a block accumulate as in Dot2
+// (high parts through TwoSum, every error term in a second FP32 word), the
+// residual terms in double-word arithmetic.  Only the packed upper blocks are
+// stored (T_P is symmetric for scalar W, Sec. VIII), half the bytes of the
+// full FP64 matrix.
+// Organisation of kernel 9: one warp per tile (one CTA per SM, four service
+// warps of CTA 0 decide on the previous sweep, three wave slots, sweep
+// number from the ticket), blocks column by column with a per-warp ring of
+// KB asynchronously copied blocks.  A block is 2 KB: its hi block then its lo
+// block, each in the FP32 layout (lane l reads float4 l and l + 32: rows l/4
+// and l/4 + 8, columns 4(l%4)..+3).  State per port and slot: (w_in.h,
+// w_in.l, w_out.h, w_out.l).
+// ---------------------------------------------------------------------------
+
+constexpr int kWdfKB = 2;  // ring slots per warp (2 KB each)
+
+__host__ __device__ constexpr size_t wdf_warp_bytes(int pp_max, int kb) {
+  return (size_t)kb * 2 * kSymB * kSymB * sizeof(float) + 24 * (size_t)pp_max;
+}
+
+__device__ __forceinline__ df shfl_xor_df(df v, int m) {
+  return {__shfl_xor_sync(0xffffffffu, v.h, m), __shfl_xor_sync(0xffffffffu, v.l, m)};
+}
+__device__ __forceinline__ dacc shfl_xor_dacc(dacc v, int m) {
+  return {__shfl_xor_sync(0xffffffffu, v.S, m), __shfl_xor_sync(0xffffffffu, v.E, m)};
+}
+
+// Residual term of a torn branch (port_residual above) in double-word
+// arithmetic: the sum cancels to the residual, so every operation keeps
+// about 44 bits of its operands, the coefficients (g/W, d) included (kq =
+// (g/W hi, lo, d hi, lo)).
+__device__ __forceinline__ df port_residual_df(df wi_s, df wo_s, df wi_t, df wo_t, float4 kq) {
+  const df Ss = df_add(wi_s, wo_s), St = df_add(wi_t, wo_t);
+  df a = df_add(Ss, St);
+  a = {0.5f * a.h, 0.5f * a.l};
+  const df gd = df_mul(df_sub(Ss, St), df{kq.x, kq.y});
+  const df r = df_sub(df_sub(df_sub(a, gd), wi_s), wi_t);
+  const df hd = {0.5f * kq.z, 0.5f * kq.w};
+  return df_mul(r, hd);
+}
+
+template <int KB>
+__global__ void __launch_bounds__(1024, 1) sweep_wdf_kernel(
+    const float* __restrict__ Tp, const TileDesc* __restrict__ tdesc,
+    const int32_t* __restrict__ twin, const float4* __restrict__ kd,
+    const uint8_t* __restrict__ run, const float2* __restrict__ c, float4* __restrict__ state3,
+    int64_t nports, SweepCtrl* __restrict__ ctrl,
+    double* __restrict__ partials2, double* __restrict__ hist, int hist_len, int nparts, int pp_max) {
+  constexpr int B = kSymB;
+  constexpr int PPL = 4;
+  constexpr int BLK = 2 * B * B;  // floats of one stored block (hi, lo)
+  constexpr unsigned FULL = 0xffffffffu;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_k, s_flag;
+  __shared__ double s_red[4];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nw = (int)(blockDim.x >> 5) - 4;  // tile warps; the last four serve
+  if (tid == 0) s_flag = *((volatile int*)&ctrl->flag);
+  __syncthreads();
+  if (s_flag) return;
+  const bool tile_warp = warp < nw;
+  const int g = warp * gridDim.x + blockIdx.x;  // tiles dealt round the CTAs
+  const bool valid = tile_warp && g < nparts;
+  TileDesc dsc{};
+  if (valid) dsc = tdesc[g];
+  const int p0 = dsc.p0, p = valid ? dsc.p : 0;
+  const int nb = (p + B - 1) / B;
+  const int nblk = nb * (nb + 1) / 2;
+  const float* Tl = Tp + 2 * dsc.Tp_off;
+  float* ring = reinterpret_cast<float*>(smem_raw + (size_t)(tile_warp ? warp : 0) * wdf_warp_bytes(pp_max, KB));
+  df* w_in = reinterpret_cast<df*>(ring + KB * BLK);
+  df* rs = w_in + pp_max;
+  dacc* acc = reinterpret_cast<dacc*>(rs + pp_max);
+  int tw[PPL];
+  uint32_t rn4 = 0;
+  int pbi = 0, pbj = 0, pidx = 0, pq = 0;
+  auto issue_next = [&]() {
+    if (pq < nblk) {
+      float* dst = ring + (pq % KB) * BLK;
+      const float* src = Tl + (size_t)pidx * BLK;
+#pragma unroll
+      for (int h = 0; h < 4; ++h) cp_async16(dst + 4 * (lane + 32 * h), src + 4 * (lane + 32 * h));
+      if (pbi < pbj) {
+        pidx += nb - 1 - pbi;
+        ++pbi;
+      } else {
+        ++pbj;
+        pbi = 0;
+        pidx = pbj;
+      }
+    }
+    ++pq;
+    cp_async_commit_group();
+  };
+  if (tile_warp) {
+#pragma unroll
+    for (int b = 0; b < KB - 1; ++b) issue_next();
+#pragma unroll
+    for (int m = 0; m < PPL; ++m) {
+      const int s = lane + 32 * m;
+      tw[m] = s < p ? twin[p0 + s] : 0;
+      if (s < p) rn4 |= (uint32_t)run[p0 + s] << (8 * m);
+    }
+  }
+  pdl_launch_dependents();
+  pdl_wait();  // the previous sweep's waves, partials and decision
+  if (tid == 0) {
+    s_flag = *((volatile int*)&ctrl->flag);
+    if (!s_flag) s_k = (int)(atomicAdd(&ctrl->ticket, 1u) / gridDim.x) + 1;
+  }
+  __syncthreads();
+  if (s_flag) {
+    cp_async_wait_group<0>();  // no copy into shared memory outlives the CTA
+    return;
+  }
+  const int k = s_k;
+  if (!tile_warp) {  // service warps: CTA 0 decides on the previous sweep
+    if (blockIdx.x != 0 || k < 2) return;
+    const int t = tid - nw * 32;
+    const double tot = group128_sum_fixed(partials2 + (size_t)((k - 1) & 1) * nparts, nparts, t, s_red);
+    if (t == 0) sweep_decide(ctrl, k - 1, tot, hist, hist_len);
+    return;
+  }
+  const float4* prev = state3 + (size_t)((k - 1) % 3) * nports;
+  float4* cur = state3 + (size_t)(k % 3) * nports;
+  // incident waves and residual terms of sweep k - 1; the outputs start at c
+  {
+    float2 c0v[PPL];
+    float4 wtv[PPL], wsv[PPL], kqv[PPL];
+#pragma unroll
+    for (int m = 0; m < PPL; ++m) {
+      const int s = lane + 32 * m;
+      c0v[m] = make_float2(0.f, 0.f);
+      wtv[m] = wsv[m] = kqv[m] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (s < p) {
+        c0v[m] = c[p0 + s];
+        if (k > 1) {
+          wtv[m] = prev[tw[m]];
+          wsv[m] = prev[p0 + s];
+          kqv[m] = kd[p0 + s];
+        }
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < PPL; ++m) {
+      const int s = lane + 32 * m;
+      if (s < nb * B) {
+        df wi = {0.f, 0.f}, rc = {0.f, 0.f};
+        if (s < p && k > 1) {
+          wi = {wtv[m].z, wtv[m].w};  // the twin's outgoing wave
+          rc = port_residual_df({wsv[m].x, wsv[m].y}, {wsv[m].z, wsv[m].w}, {wtv[m].x, wtv[m].y}, wi, kqv[m]);
+        }
+        w_in[s] = wi;
+        rs[s] = rc;
+        acc[s] = {c0v[m].x, c0v[m].y};
+      }
+    }
+  }
+  __syncwarp();
+  df tile_sq = {0.f, 0.f};  // lane 0: the four groups in order
+  if (k > 1) {
+#pragma unroll
+    for (int m = 0; m < PPL; ++m) {
+      df sq = {0.f, 0.f};
+      const int s = lane + 32 * m;
+      const int nr = (rn4 >> (8 * m)) & 0xff;
+      if (s < p && nr) {
+        df rr = rs[s];
+        for (int q = 1; q < nr; ++q) rr = df_add(rr, rs[s + q]);
+        sq = df_mul(rr, rr);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const df t = {__shfl_down_sync(FULL, sq.h, o), __shfl_down_sync(FULL, sq.l, o)};
+        sq = df_add(sq, t);
+      }
+      tile_sq = df_add(tile_sq, sq);
+    }
+  }
+  // Blocks in column-major order over the upper triangle, as in kernel 9:
+  // each block's row partial is reduced at once into its row block; its
+  // column partial accumulates in registers over the block column (four
+  // columns x two rows per lane) and is reduced across the eight lanes of a
+  // column group after the diagonal block.
+  const int r1 = lane >> 2, cg = lane & 3;
+  const bool b0 = lane & 1, b4 = lane & 16, b3 = lane & 8;
+  const bool row_owner = !(lane & 2), col_owner = !(lane & 4);
+  const int myrow = b0 ? r1 + 8 : r1;
+  const int mycol = cg * 4 + (b4 ? 2 : 0) + (b3 ? 1 : 0);
+  dacc ca[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) ca[j] = {0.f, 0.f};
+  int bi = 0, bj = 0;
+  for (int kk = 0; kk < nblk; ++kk) {
+    issue_next();
+    cp_async_wait_group<KB - 1>();  // this lane's bytes of block kk have landed
+    const float* blk = ring + (kk % KB) * BLK;
+    const float4 ha = reinterpret_cast<const float4*>(blk)[lane];
+    const float4 hb = reinterpret_cast<const float4*>(blk)[lane + 32];
+    const float4 la = reinterpret_cast<const float4*>(blk + B * B)[lane];
+    const float4 lb = reinterpret_cast<const float4*>(blk + B * B)[lane + 32];
+    {  // row partials of rows r1 (a) and r1 + 8 (b) over this lane's four columns
+      const df* wc = w_in + bj * B + cg * 4;
+      const df w0 = wc[0], w1 = wc[1], w2 = wc[2], w3 = wc[3];
+      dacc x1 = dacc_first(ha.x, la.x, w0.h, w0.l);
+      dacc_fma(x1, ha.y, la.y, w1.h, w1.l);
+      dacc_fma(x1, ha.z, la.z, w2.h, w2.l);
+      dacc_fma(x1, ha.w, la.w, w3.h, w3.l);
+      dacc x2 = dacc_first(hb.x, lb.x, w0.h, w0.l);
+      dacc_fma(x2, hb.y, lb.y, w1.h, w1.l);
+      dacc_fma(x2, hb.z, lb.z, w2.h, w2.l);
+      dacc_fma(x2, hb.w, lb.w, w3.h, w3.l);
+      // the row's four lanes (bits 0, 1): reduce-scatter over bit 0, sum over bit 1
+      dacc t = dacc_add(b0 ? x2 : x1, shfl_xor_dacc(b0 ? x1 : x2, 1));
+      t = dacc_add(t, shfl_xor_dacc(t, 2));
+      if (row_owner) acc[bi * B + myrow] = dacc_add(acc[bi * B + myrow], t);
+    }
+    if (bi != bj) {
+      const df wr1 = w_in[bi * B + r1], wr2 = w_in[bi * B + r1 + 8];
+      dacc_fma(ca[0], ha.x, la.x, wr1.h, wr1.l);
+      dacc_fma(ca[0], hb.x, lb.x, wr2.h, wr2.l);
+      dacc_fma(ca[1], ha.y, la.y, wr1.h, wr1.l);
+      dacc_fma(ca[1], hb.y, lb.y, wr2.h, wr2.l);
+      dacc_fma(ca[2], ha.z, la.z, wr1.h, wr1.l);
+      dacc_fma(ca[2], hb.z, lb.z, wr2.h, wr2.l);
+      dacc_fma(ca[3], ha.w, la.w, wr1.h, wr1.l);
+      dacc_fma(ca[3], hb.w, lb.w, wr2.h, wr2.l);
+      ++bi;
+    } else {
+      __syncwarp();  // the diagonal block's row partial is in before the column's
+      if (bj > 0) {
+        // columns 4 cg..+3: sums over the eight lanes of a column group (bits 4, 3, 2)
+        dacc k0 = b4 ? ca[2] : ca[0], k1 = b4 ? ca[3] : ca[1];
+        k0 = dacc_add(k0, shfl_xor_dacc(b4 ? ca[0] : ca[2], 16));
+        k1 = dacc_add(k1, shfl_xor_dacc(b4 ? ca[1] : ca[3], 16));
+        dacc t1 = dacc_add(b3 ? k1 : k0, shfl_xor_dacc(b3 ? k0 : k1, 8));
+        t1 = dacc_add(t1, shfl_xor_dacc(t1, 4));
+        if (col_owner) acc[bj * B + mycol] = dacc_add(acc[bj * B + mycol], t1);
+      }
+      __syncwarp();  // and the column partial before later rows add to this block
+#pragma unroll
+      for (int j = 0; j < 4; ++j) ca[j] = {0.f, 0.f};
+      ++bj;
+      bi = 0;
+    }
+  }
+  cp_async_wait_group<0>();
+#pragma unroll
+  for (int m = 0; m < PPL; ++m) {
+    const int s = lane + 32 * m;
+    if (s < p) {
+      const df o = dacc_value(acc[s]);
+      cur[p0 + s] = make_float4(w_in[s].h, w_in[s].l, o.h, o.l);
+    }
+  }
+  if (valid && lane == 0) partials2[(size_t)(k & 1) * nparts + dsc.tile] = (double)tile_sq.h + (double)tile_sq.l;
+}
+
+// c as double-float pairs (once per inner solve of kernel 12)
+__global__ void split_df_kernel(const double* __restrict__ a, float2* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = a[i];
+    const float h = (float)v;
+    b[i] = make_float2(h, (float)(v - (double)h));
+  }
+}
+
+// the chosen double-float wave slot as FP64 (w_in, w_out) pairs for the
+// recovery
+__global__ void join_df_kernel(const float4* __restrict__ st, double* __restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 v = st[i];
+    out[2 * i] = (double)v.x + (double)v.y;
+    out[2 * i + 1] = (double)v.z + (double)v.w;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Dataflow sweeps: one cooperative launch runs every sweep of an inner solve.
 // Sweep k of tile P needs only the sweep-(k-1) waves of the tiles across its
 // lines (the one-sweep delay of Eq. 11), so instead of a kernel boundary per
@@ -2319,6 +2606,25 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   const int wmma_grid = (P->nparts + wmma_warps - 1) / wmma_warps;
   const int wmma_threads = 32 * (wmma_warps + 4);
   const size_t wmma_smem = wmma_warps * wmma_per_warp;
+  // kernel 12 (double-float FP64-accurate sweep): FP64 plans with the packed
+  // double-float copy, at most 128 ports per tile
+  const bool wdf_ok = prec == VTM_PREC_FP64 && P->d_Tpdf.p != nullptr && pp_max <= 8 * kSymB;
+  const size_t wdf_per_warp = wdf_warp_bytes(pp_max, kWdfKB);
+  int wdf_warps = std::min(28, std::max(1, (P->nparts + sms - 1) / sms));
+  wdf_warps = std::max(1, std::min(wdf_warps, (int)(220 * 1024 / wdf_per_warp)));
+  const int wdf_grid = (P->nparts + wdf_warps - 1) / wdf_warps;
+  const int wdf_threads = 32 * (wdf_warps + 4);
+  const size_t wdf_smem = wdf_warps * wdf_per_warp;
+  if (wdf_ok) {
+    VTM_TRY(dev_alloc(P->d_dfstate, 3 * (size_t)std::max<int64_t>(npt, 1) * sizeof(float4)));
+    VTM_TRY(dev_alloc(P->d_cdf, (size_t)std::max<int64_t>(npt, 1) * sizeof(float2)));
+    split_df_kernel<<<grid_for(std::max<int64_t>(npt, 1)), 256, 0, s>>>(P->d_c64.as<double>(),
+                                                                        P->d_cdf.as<float2>(), npt);
+    VTM_CUDA_TRY(cudaGetLastError());
+    P->launch_count++;
+    VTM_CUDA_TRY(cudaFuncSetAttribute(sweep_wdf_kernel<kWdfKB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)wdf_smem));
+  }
   auto with_wsym = [&](auto fn) {
     const bool wide = pp_max > 128;
     if (prec == VTM_PREC_FP32) {
@@ -2359,6 +2665,13 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   // tile, 11 the same with the block products as warp MMAs; 8 and 10, the
   // dataflow sweeps, are launched once per inner solve)
   auto launch_one = [&](int kc) {
+    if (kc == 12) {
+      launch_packed(P, sweep_wdf_kernel<kWdfKB>, wdf_grid, wdf_threads, wdf_smem, s, P->d_Tpdf.as<float>(),
+                    P->d_tdesc.as<TileDesc>(), P->d_twin.as<int32_t>(), P->d_kddf.as<float4>(),
+                    P->d_run.as<uint8_t>(), P->d_cdf.as<float2>(), P->d_dfstate.as<float4>(), npt_,
+                    P->d_ctrl.as<SweepCtrl>(), P->d_partials.as<double>(), hist, hist_len, P->nparts, pp_max);
+      return;
+    }
     if (kc == 7) {
       auto go = [&](auto* kern, const auto* Tp) {
         launch_packed(P, kern, P->nparts, 128, symb_smem, s, Tp, P->d_tdesc.as<TileDesc>(),
@@ -2598,7 +2911,8 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
     return cudaLaunchCooperativeKernel(wflow_kfn, wflow_grid, 32 * kWflowWarps, args, wflow_smem, s);
   };
   const bool symload = ((choice == 5 || choice == 6 || choice == 9) && sym_ok) || (choice == 7 && symb_ok) ||
-                       (choice == 8 && flow_ok) || (choice == 10 && wflow_ok) || (choice == 11 && wmma_ok);
+                       (choice == 8 && flow_ok) || (choice == 10 && wflow_ok) || (choice == 11 && wmma_ok) ||
+                       (choice == 12 && wdf_ok);
   if (P->opts.method == VTM_METHOD_ASYNC && !flow_ok && !wflow_ok) {
     set_detail("vtm_solve: asynchronous VTM runs on the packed symmetric dataflow kernel: it needs "
                "FP32/BF16/FP16 sweeps of a symmetric plan with at most 256 ports per sub-circuit");
@@ -2633,10 +2947,11 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
       const bool can_vec128 = nv_max <= 128;
       float best = 1e30f;
       int best_k = 1;
-      for (int cand = 1; cand <= 11; ++cand) {
+      for (int cand = 1; cand <= 12; ++cand) {
         if ((cand == 2 && !can_st) || (cand == 3 && !can_vec) || (cand == 4 && !can_vec128) ||
             ((cand == 5 || cand == 6 || cand == 9) && !sym_ok) || (cand == 7 && !symb_ok) ||
-            (cand == 8 && !flow_ok) || (cand == 10 && !wflow_ok) || (cand == 11 && !wmma_ok))
+            (cand == 8 && !flow_ok) || (cand == 10 && !wflow_ok) || (cand == 11 && !wmma_ok) ||
+            (cand == 12 && !wdf_ok))
           continue;
         if (cand == 8 || cand == 10) {  // one launch of 8 sweeps, per-sweep time against the others' 6
           SweepCtrl t = h;
@@ -2784,7 +3099,14 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   *flag_out = r.flag;
   if (r.flag == 1 || r.flag == 4) *sweep_out = r.conv_sweep;
   else *sweep_out = std::min(r.k - 1, budget);
-  if (prec == VTM_PREC_FP64)
+  if (kern == 12) {
+    // the chosen double-float slot as FP64 pairs for the recovery
+    join_df_kernel<<<grid_for(std::max<int64_t>(npt, 1)), 256, 0, s>>>(
+        P->d_dfstate.as<float4>() + (size_t)(*sweep_out % 3) * npt, P->d_state64.as<double>(), npt);
+    VTM_CUDA_TRY(cudaGetLastError());
+    P->launch_count++;
+    P->wave_slot = P->d_state64.as<double>();
+  } else if (prec == VTM_PREC_FP64)
     P->wave_slot = P->d_state64.as<double>() + (size_t)(*sweep_out & 1) * npt * 2;
   else if (kern == 9 || kern == 11)  // three slots
     P->wave_slot = P->d_fstate32.as<float>() + (size_t)(*sweep_out % 3) * npt * 2;

@@ -212,6 +212,9 @@ struct vtm_plan_s {
   vtm::DevBuf d_bout, d_rho, d_kd, d_kd32;  // per port: 2 W beta / d, reflection, (g/W, d)
   vtm::DevBuf d_T64, d_T32, d_T16;         // reflection matrices (T^T blocks)
   vtm::DevBuf d_Tp32, d_Tp16;              // packed symmetric copies (symmetric plans)
+  vtm::DevBuf d_Tpdf;                      // packed double-float copy (FP64 plans, kernel 12)
+  vtm::DevBuf d_dfstate, d_cdf;            // kernel 12: three double-float wave slots, c
+  vtm::DevBuf d_kddf;                      // (g/W, d) per port as double-float pairs (float4)
   // dataflow sweeps: tiles across the lines of each tile (CSR), per-tile done
   // counters, per-sweep tile counts and the published decision, residual
   // partials of four sweeps, waves in three slots

@@ -32,6 +32,8 @@ GRID2048 = {"nports": 516096, "sum_p2": 65282048, "sum_tri": 32899072}
     # full-matrix kernels read every entry; FP64 waves and coefficients
     (1, 1, 4 * 65282048 + 516096 * 20, 516096 * 21),
     (0, 1, 8 * 65282048 + 516096 * 40, 516096 * (16 + 5 + 16)),
+    # the double-float FP64 sweep reads the packed blocks as 8-byte hi/lo pairs
+    (0, 12, 8 * 32899072 + 516096 * 40, 516096 * (16 + 5 + 16)),
 ])
 def test_sweep_bytes_follow_the_byte_model(prec, kernel, alg, ovh):
     assert bench.sweep_bytes(dict(GRID2048, sweep_kernel=kernel), prec) == (alg, ovh)

@@ -213,10 +213,12 @@ def test_set_values_then_refactor(vtm):
     assert np.abs(x.cpu().numpy() - x_star).max() <= 1e-8 * np.abs(x_star).max()
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 3, 4])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 12])
 def test_every_sweep_kernel_matches_oracle(vtm, kernel):
     # direct-load, bulk-copy staged and vector-load (256 / 128 threads)
-    # kernels compute the same FP64 sweep
+    # kernels compute the same FP64 sweep; kernel 12 the same iteration in
+    # double-float arithmetic on the packed blocks (about 48 bits: the
+    # iterate at equal sweep count still agrees to 1e-11)
     w = wl.power_grid(128, 128, 32, 32, Zc=1.0, seed=12)
     A = w.csr()
     plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc, sweep_kernel=kernel)
@@ -443,9 +445,12 @@ def test_bad_options_are_rejected_and_the_plan_keeps_its_own(vtm):
     w = wl.power_grid(64, 64, 32, 32, Zc=1.0, seed=15)
     plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc)
     with pytest.raises(vtm.VTMError):
-        plan.set_options(sweep_kernel=12)
+        plan.set_options(sweep_kernel=13)
     with pytest.raises(vtm.VTMError):
         plan.set_options(sweep_kernel=-1)
+    for kw in ({"batch_kernel": 5}, {"wait_polls": -1}, {"flow_lag": 1}):
+        with pytest.raises(vtm.VTMError):
+            plan.set_options(**kw)
     for bad in (4, 5, -1):
         with pytest.raises(vtm.VTMError):
             plan.set_options(precision=bad)
@@ -470,3 +475,45 @@ def test_graph_path_on_a_dedicated_stream(vtm):
     assert torch.equal(x1, x2)
     rel = O.residual_norms(A, x1.cpu().numpy()[None], w.b)
     assert rel.max() <= 1e-10
+
+
+def test_double_float_sweep_history_and_stored_entries(vtm):
+    # kernel 12 keeps T_P as hi + lo FP32 pairs (48 bits) and computes in
+    # double-float arithmetic: its interface residual history equals the
+    # oracle's full b - A x^k to 1e-9 (as the FP64 kernels do), and every
+    # stored pair is the library's FP64 T_P to 2^-46 relative (and the
+    # oracle's within the 1e-11 the FP64 parity tests allow)
+    w = wl.grid2d(24, 24, 8, 6, Zc=0.5, seed=21)
+    A = w.csr()
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc, sweep_kernel=12)
+    plan.set_options(history_len=60)
+    x, info = plan.solve(torch.from_numpy(w.b).cuda(), tol=1e-10)
+    assert plan.stats()["sweep_kernel"] == 12
+    ref = O.vtm_midpoint(A, w.partition, w.nparts, w.b, W=1 / w.Zc, tol=0, max_sweeps=60)
+    k = min(60, info["sweeps"])
+    assert np.allclose(plan.history[:k], ref.history[:k, 0], rtol=1e-9, atol=1e-13)
+    assert O.residual_norms(A, x.cpu().numpy().reshape(w.b.shape), w.b).max() <= 1e-10
+    tear = O.tear_midpoint(A, w.partition, w.nparts)
+    for P in range(w.nparts):
+        Tq, esize, packed = plan.reflection_stored(P)
+        assert esize == 8 and packed
+        T64 = plan.reflection(P)
+        assert np.all(np.abs(Tq - 0.5 * (T64 + T64.T)) <= 2.0 ** -46 * np.abs(T64) + 1e-300)
+        _, T_ref = O.reflection_ops(A, tear, P, 1.0 / w.Zc)
+        perm = _match_ports(plan, tear, P)
+        assert np.abs(Tq - T_ref[np.ix_(perm, perm)]).max() < 1e-11
+
+
+@pytest.mark.parametrize("k", [1, 2, 10])
+def test_double_float_iterates_after_k_sweeps(vtm, k):
+    # x of sweep k of kernel 12 against the oracle's literal Eq. 11 iterate
+    w = wl.power_grid(128, 128, 32, 32, Zc=1.0, seed=24)
+    A = w.csr()
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc, sweep_kernel=12,
+                    max_sweeps=k)
+    x, info = plan.solve(torch.from_numpy(w.b[0]).cuda(), tol=1e-300, check=False)
+    assert info["sweeps"] == k and plan.stats()["sweep_kernel"] == 12
+    _, its = O.vtm_midpoint(A, w.partition, w.nparts, w.b[:1], W=1 / w.Zc, tol=0, max_sweeps=k,
+                            keep_iterates=True)
+    ref = its[k - 1][0]
+    assert np.abs(x.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
