@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--grid", type=int, default=2048)
     ap.add_argument("--zc", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-kernel", type=int, default=0, choices=list(range(6)),
+                    help="batched sweep (thermal workload): 0 autotuned, 1/3 CUDA cores, 2/4 warp MMAs, "
+                         "5 tcgen05")
     ap.add_argument("--l2-persist", type=int, default=0, choices=[0, 1],
                     help="1: reflection matrices persisting in L2 during low-precision sweeps, 0: off")
     ap.add_argument("--admittance", default="alpha", choices=["alpha", "diag", "wob", "sca"],
@@ -305,9 +308,12 @@ def plan_colidx(w, dev):
     return torch.from_numpy(w.indices).to(dev)
 
 
-def sweep_kernel_name(kernel, nrhs):
+def sweep_kernel_name(kernel, nrhs, batch_kernel=0):
     if nrhs > 1:
-        return "batch_sweep_kernel / batch_sweep_mma_kernel (batched right-hand sides)"
+        return {1: "batch_sweep_kernel (CUDA cores, persistent)", 2: "batch_sweep_mma_kernel (warp MMAs, persistent)",
+                3: "batch_sweep_kernel (CUDA cores, item per CTA)", 4: "batch_sweep_mma_kernel (warp MMAs, item per CTA)",
+                5: "batch_sweep_tc_kernel (tcgen05, TMEM accumulators, bulk-copy ring)"}.get(
+                    batch_kernel, "batched sweep")
     return {1: "sweep_kernel (direct loads)", 2: "sweep_staged_kernel (bulk-copy ring)",
             3: "sweep_vec_kernel (256 threads)", 4: "sweep_vec_kernel (128 threads)",
             5: "sweep_sym_kernel (packed symmetric, 128 threads)",
@@ -393,7 +399,7 @@ def gpu_arm(args):
             results[prec] = run_mode(prec, w, dev, stream, flush, world, args.steps, args.warmup,
                                      method="bj" if prec.startswith("bj_") else args.method, adm=adm,
                                      grad=args.workload == "grad", sweep_kernel=args.sweep_kernel,
-                                     l2_persist=args.l2_persist, e2e=True)
+                                     l2_persist=args.l2_persist, e2e=True, batch_kernel=args.batch_kernel)
         except Exception as exc:  # a failing mode is reported, the others still run
             errors[prec] = repr(exc)
     if not results:
@@ -409,7 +415,7 @@ def gpu_arm(args):
 
 
 def run_mode(prec, w, dev, stream, flush, world, steps, warmup, method="vtm", adm=None, grad=False,
-             sweep_kernel=0, l2_persist=0, e2e=True, Zc=None):
+             sweep_kernel=0, l2_persist=0, e2e=True, Zc=None, batch_kernel=0):
     """Plan, factor and time one mode on workload w: `steps` solves after
     `warmup` untimed ones, L2 flushed before each; with e2e also the same
     solves through the C ABI with pinned host buffers.  The plan is closed
@@ -426,7 +432,8 @@ def run_mode(prec, w, dev, stream, flush, world, steps, warmup, method="vtm", ad
     with torch.cuda.stream(stream):
         plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=Zc,
                         precision=prec_name, device=dev, stream=stream, factor=False,
-                        sweep_kernel=sweep_kernel, l2_persist=l2_persist, method=method)
+                        sweep_kernel=sweep_kernel, l2_persist=l2_persist, method=method,
+                        batch_kernel=batch_kernel)
         if adm is not None and method != "bj":
             plan.set_admittance(adm[0], alpha=adm[1], radius=adm[2], factor=False)
         t1 = time.perf_counter()
@@ -550,6 +557,8 @@ def run_configs(args, w2, dev, stream, flush, world):
     w3 = wl.c3_thermal(nrhs=64)
     for prec in ("fp32", "bf16", "fp64"):
         entry(f"thermal_128x128x32_64rhs_{prec}", w3, prec)
+    entry("thermal_128x128x32_64rhs_bf16_tcgen05", w3, "bf16", batch_kernel=5)
+    entry("thermal_128x128x32_64rhs_bf16_mma_sync", w3, "bf16", batch_kernel=2)
     entry("thermal_128x128x32_64rhs_fp32_sca1", w3, "fp32", adm=("sca", 1.0, 1))
     del w3
     w4 = wl.c4_vccs()
@@ -575,7 +584,8 @@ def emit(args, results, errors, best, w, world, rank, configs=None):
                   "fp16": "f16+f64 refinement"}[best.split("_")[-1]],
         "data": "synthetic", "config": dict(workload_config(args), precision=best,
                                             **admittance_config(args)),
-        "roofline": {"bound": "hbm", "kernel": sweep_kernel_name(R["stats"].get("sweep_kernel"), R["nrhs"]),
+        "roofline": {"bound": "hbm", "kernel": sweep_kernel_name(R["stats"].get("sweep_kernel"), R["nrhs"],
+                                                                 R["stats"].get("batch_kernel", 0)),
                      "achieved": R["achieved_gbs"], "peak": peak, "unit": "GB/s",
                      "frac": R["achieved_gbs"] / peak, "peak_source": peak_src,
                      "traffic": traffic_record(prec_id, R["stats"], args.workload)

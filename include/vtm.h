@@ -153,9 +153,12 @@ typedef struct {
                         at the first batched solve of each precision; 1: CUDA cores,
                         persistent grid over the work list; 2: BF16 tensor cores
                         (warp MMAs, FP32 accumulate), persistent; 3, 4: the same with
-                        one work item per CTA.  A tensor-core request in another
-                        precision, or with a column count that is not a multiple of 8,
-                        runs the CUDA-core variant of the same grid */
+                        one work item per CTA; 5: BF16 tcgen05 (128 x 64 tiles of
+                        T_P streamed by bulk copies into a shared-memory ring,
+                        incident waves gathered into the B operand, FP32
+                        accumulators in TMEM).  A tensor-core request in another
+                        precision, or (2, 4) with a column count that is not a
+                        multiple of 8, runs the CUDA-core variant */
   int wait_polls;    /* polls a bounded device-side wait of the dataflow sweeps
                         (kernels 8 and 10) makes before it gives up with VTM_ETIMEOUT;
                         0: default 4194304 (a few seconds).  The bulk-copy waits of
@@ -256,7 +259,7 @@ vtm_status vtm_get_admittance(vtm_plan_t plan, double* W);
 /* vtm_set_opts -- replace the options of a plan (precision, limits, history).
  * VTM_EINVAL for a precision outside 0..3, a negative history_len, a history
  * length without an array, a sweep_kernel outside 0..12, a batch_kernel
- * outside 0..4, a negative wait_polls or a flow_lag other than 0 and -1; the
+ * outside 0..5, a negative wait_polls or a flow_lag other than 0 and -1; the
  * plan keeps its previous options then. */
 vtm_status vtm_set_opts(vtm_plan_t plan, const vtm_opts* opts);
 

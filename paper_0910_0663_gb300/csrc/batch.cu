@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "ptx.h"
 #include "vtm_internal.h"
 
 namespace vtm {
@@ -798,6 +799,490 @@ __global__ void __launch_bounds__(128) batch_sweep_mma_kernel(
 }
 
 // ---------------------------------------------------------------------------
+// tcgen05 version (BF16 T and incident waves, FP32 accumulators in TMEM)
+// ---------------------------------------------------------------------------
+//
+// W_out(P) = T_P W_in(P) + C_P for up to 64 right-hand sides is a dense
+// contraction (Eq. 11 with many right-hand sides): M = the box's output ports,
+// K = its input ports, N = 64 columns.  A work item is a box and up to four
+// 128-row M tiles (512 outputs: 4 accumulators of 128 lanes x 64 FP32
+// columns, 256 TMEM columns); items run longest first from a work list over
+// persistent CTAs of 128 threads, two per SM.
+//   * A: T_P in 128 x 64 BF16 tiles prepared at factor time in the UMMA
+//     canonical K-major layout without swizzle (8 x 8 core matrices of 128
+//     bytes, the eight K groups of a row group adjacent: LBO = 128 B, SBO =
+//     1 KB), each item's tiles contiguous in consumption order (input chunk,
+//     then M tile), so one 16 KB bulk copy fills a stage of a 4-stage ring
+//     (mbarriers with transaction counts), issued three tiles ahead by thread
+//     0, which also issues the MMAs;
+//   * B: the incident waves of a 64-input chunk, gathered from the twins'
+//     outgoing waves of the previous sweep (FP32) by all threads, rounded to
+//     BF16 and written in the same canonical layout (double-buffered; a
+//     buffer is rewritten once the MMAs that read it have committed);
+//   * per chunk and M tile, four tcgen05.mma (M = 128, N = 64, K = 16) add
+//     into the tile's TMEM accumulator; tcgen05.commit frees the A stage and,
+//     after the chunk's last tile, the B buffer;
+//   * epilogue: each warp reads its 32 TMEM lanes (tcgen05.ld 32x32b), adds
+//     C and writes w_out; the residual terms of the previous sweep and the
+//     decision are those of the other batched kernels.
+// Every mbarrier wait is bounded (kTcPolls); a wait that runs out sets flag 5
+// (VTM_ETIMEOUT), and the CTA waits (bounded) for its copies and MMAs in
+// flight, frees its TMEM columns and leaves.
+constexpr int kTcM = 128;                            // rows per MMA tile
+constexpr int kTcK = 64;                             // inputs per chunk
+constexpr int kTcG = 4;                              // M tiles per work item
+constexpr int kTcS = 3;                              // A stages
+constexpr uint32_t kTcTileBytes = kTcM * kTcK * 2;   // 16 KB
+constexpr uint32_t kTcBBytes = 64 * kTcK * 2;        // 8 KB
+constexpr uint32_t kTcCols = 64 * kTcG;              // TMEM columns per CTA
+constexpr uint32_t kTcPolls = 1u << 24;
+constexpr int kTcThreads = 256;                      // 8 warps: two per TMEM lane quarter
+constexpr int kTcLd = 68;                            // FP32 staging row stride (conflict-free columns)
+constexpr size_t kTcSmem = kTcS * (size_t)kTcTileBytes + 2 * (size_t)kTcBBytes + 2 * (size_t)kTcK * kTcLd * 4 + 1024;
+
+// smem matrix descriptor: canonical K-major, no swizzle (LBO = 128 B between
+// the two K core matrices of a K = 16 step, SBO = 1 KB between 8-row groups)
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)(128 >> 4) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of the sm_100 family
+  return d;
+}
+// instruction descriptor: F32 accumulate, BF16 A and B, both K-major, N = 64, M = 128
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16_tc(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+// 16 FP32 columns of this warp's 32 lanes
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 2) batch_sweep_tc_kernel(
+    const __nv_bfloat16* __restrict__ Ttc, const int4* __restrict__ items, const int64_t* __restrict__ item_off,
+    const int32_t* __restrict__ item_order, int nitems, const int32_t* __restrict__ port_off,
+    const int32_t* __restrict__ twin, const double2* __restrict__ kd, const uint8_t* __restrict__ run,
+    const float* __restrict__ c, float* __restrict__ state, int64_t nports, int R,
+    BatchCtrl* __restrict__ ctrl, double* __restrict__ partials, const double* __restrict__ tol2,
+    double* __restrict__ hist, int hist_len) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  // 1 KB alignment of the stage buffers (canonical layouts need 16 B; the
+  // descriptors' base-offset field stays 0)
+  unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)tc_smem + 1023) & ~(uintptr_t)1023);
+  unsigned char* As = base;
+  unsigned char* Bs = As + kTcS * kTcTileBytes;
+  float* Sg = reinterpret_cast<float*>(Bs + 2 * kTcBBytes);  // 2 x 64 staging rows
+  const bool vecR = (R & 3) == 0;
+  __shared__ uint64_t full[kTcS], empty[kTcS], bfull[2], bdone[2];
+  __shared__ uint32_t s_tmem;
+  __shared__ double red[64];
+  __shared__ int s_k, s_flag, s_item, s_abort;
+  __shared__ bool s_last;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    s_k = *((volatile int*)&ctrl->k);
+    s_flag = *((volatile int*)&ctrl->flag);
+    s_abort = 0;
+    for (int i = 0; i < kTcS; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(&bdone[0], 1);
+    mbar_init(&bdone[1], 1);
+    mbar_init(&bfull[0], kTcThreads - 64);
+    mbar_init(&bfull[1], kTcThreads - 64);
+    fence_mbar_init();
+  }
+  if (tid < 64) red[tid] = 0.0;
+  __syncthreads();
+  if (s_flag) return;
+  const int k = s_k;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(kTcCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  // counters of this CTA over its items: A tiles issued (thread 0) and chunks
+  uint32_t q_issued = 0, q_base = 0, cg = 0;
+  auto abort_wait = [&]() {
+    atomicCAS(&ctrl->flag, 0, 5);
+    s_abort = 1;
+  };
+  // thread 0 (the producer): tile gq of this CTA's sequence into its stage
+  // (after the MMAs that read the stage's previous tile have committed)
+  auto issue_tile = [&](uint32_t gq, const __nv_bfloat16* src) -> bool {
+    const uint32_t st = gq % kTcS;
+    if (gq >= kTcS && !mbar_wait_bounded(&empty[st], ((gq / kTcS) - 1) & 1, kTcPolls)) return false;
+    mbar_arrive_expect_tx(&full[st], kTcTileBytes);
+    bulk_copy_g2s(As + st * kTcTileBytes, src, kTcTileBytes, &full[st]);
+    q_issued = gq + 1;
+    return true;
+  };
+  for (;;) {
+    if (tid == 0) s_item = (int)atomicAdd(&ctrl->work, 1u);
+    __syncthreads();
+    if (s_item >= nitems || s_abort) break;
+    const int item = item_order[s_item];
+    const int4 it = items[item];
+    const int tile = it.x, m0 = it.y, nmt = it.z, nkc = it.w;
+    const int p0 = port_off[tile];
+    const int p = port_off[tile + 1] - p0;
+    const int m1 = min(p, m0 + nmt * kTcM);
+    const __nv_bfloat16* Ab = Ttc + item_off[item];
+    const float* prev = state + (size_t)((k - 1) & 1) * nports * 2 * R;
+    float* cur = state + (size_t)(k & 1) * nports * 2 * R;
+    const int ntot = nmt * nkc;
+    if (k > 1) {
+      // Warp-specialised main loop: warp 0 (lane 0) streams the item's A
+      // tiles into the ring as stages free up; warp 1 (lane 0) issues the
+      // MMAs as tiles and B chunks become ready; warps 2-7 gather the B
+      // chunks.  No CTA barrier inside: mbarriers order everything (full /
+      // empty per A stage, bfull / bdone per B buffer), and every role runs
+      // its fixed number of steps, skipping its waits after an abort.
+      if (warp == 0) {
+        if (lane == 0)
+          for (int q = 0; q < ntot; ++q)
+            if (!s_abort && !issue_tile(q_base + q, Ab + (size_t)q * (kTcTileBytes / 2))) abort_wait();
+      } else if (warp == 1) {
+        if (lane == 0) {
+          for (int kc = 0; kc < nkc; ++kc) {
+            const uint32_t c2 = cg + kc, buf = c2 & 1;
+            if (!s_abort && !mbar_wait_bounded(&bfull[buf], (c2 >> 1) & 1, kTcPolls)) abort_wait();
+            tc_fence_after();
+            const uint32_t b0 = smem_u32(Bs + buf * kTcBBytes);
+            for (int mt = 0; mt < nmt; ++mt) {
+              const uint32_t gq = q_base + kc * nmt + mt, st = gq % kTcS;
+              if (s_abort || !mbar_wait_bounded(&full[st], (gq / kTcS) & 1, kTcPolls)) {
+                abort_wait();
+                break;
+              }
+              tc_fence_after();
+              const uint32_t a0 = smem_u32(As + st * kTcTileBytes);
+#pragma unroll
+              for (int ks = 0; ks < kTcK / 16; ++ks)
+                tc_mma(tmem + mt * 64, tc_desc(a0 + 256 * ks), tc_desc(b0 + 256 * ks), (kc > 0 || ks > 0) ? 1u : 0u);
+              tc_commit(&empty[st]);
+            }
+            tc_commit(&bdone[buf]);
+          }
+        }
+      } else {
+        // B builders: the 64 twin rows of chunk j (their outgoing waves, 64
+        // FP32 columns) are copied into FP32 staging rows (cp.async, one
+        // chunk ahead, double-buffered; plain loads when R is not a multiple
+        // of 4), then rounded to BF16 into the canonical B layout
+        const int bt = tid - 64;  // builder thread 0..191
+        constexpr int NB = kTcThreads - 64;
+        auto stage_rows = [&](int j) {
+          float* stg = Sg + (j & 1) * kTcK * kTcLd;
+          for (int e = bt; e < kTcK * 16; e += NB) {
+            const int r = e >> 4, seg = e & 15;
+            const int t = j * kTcK + r;
+            const int tw = t < p ? twin[p0 + t] : -1;
+            float* dst = stg + r * kTcLd + seg * 4;
+            if (tw >= 0 && vecR && seg * 4 < R) {
+              cp_async16_tc(dst, prev + (size_t)tw * 2 * R + R + seg * 4);
+            } else if (tw >= 0 && !vecR) {
+#pragma unroll
+              for (int q4 = 0; q4 < 4; ++q4) dst[q4] = seg * 4 + q4 < R ? prev[(size_t)tw * 2 * R + R + seg * 4 + q4] : 0.f;
+            } else {
+              *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+          }
+          asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        stage_rows(0);
+        for (int kc = 0; kc < nkc; ++kc) {
+          const uint32_t c2 = cg + kc, buf = c2 & 1;
+          unsigned char* Bb = Bs + buf * kTcBBytes;
+          asm volatile("cp.async.wait_group 0;" ::: "memory");  // this thread's rows of chunk kc
+          // every builder's rows of chunk kc have landed, and every builder
+          // has converted chunk kc - 1 (its staging rows may be refilled)
+          asm volatile("bar.sync 1, %0;" ::"r"(NB) : "memory");
+          if (kc + 1 < nkc) stage_rows(kc + 1);
+          // the MMAs of chunk c2 - 2 read this B buffer
+          if (c2 >= 2 && !s_abort && !mbar_wait_bounded(&bdone[buf], ((c2 - 2) >> 1) & 1, kTcPolls)) abort_wait();
+          const float* stg = Sg + (kc & 1) * kTcK * kTcLd;
+          // 64 columns x 8 input groups: eight inputs of one column per 16 bytes
+          for (int pi = bt; pi < 64 * 8; pi += NB) {
+            const int n = pi & 63, kg = pi >> 6;
+            uint32_t w[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const __nv_bfloat162 h = __floats2bfloat162_rn(stg[(kg * 8 + 2 * e) * kTcLd + n],
+                                                             stg[(kg * 8 + 2 * e + 1) * kTcLd + n]);
+              w[e] = *reinterpret_cast<const uint32_t*>(&h);
+            }
+            *reinterpret_cast<uint4*>(Bb + ((n >> 3) * 8 + kg) * 128 + (n & 7) * 16) =
+                make_uint4(w[0], w[1], w[2], w[3]);
+          }
+          fence_proxy_async_smem();  // the generic-proxy writes of B, before the MMAs read them
+          mbar_arrive(&bfull[buf]);
+        }
+      }
+      cg += nkc;
+      q_base += ntot;
+      // every MMA of the item has completed once its last chunk's commit has
+      if (!s_abort && !mbar_wait_bounded(&bdone[(cg - 1) & 1], ((cg - 1) >> 1) & 1, kTcPolls)) abort_wait();
+      tc_fence_after();
+    }
+    __syncthreads();
+    if (s_abort) break;
+    // Epilogue, one M tile at a time: the accumulators go through shared
+    // memory (the idle A ring: 128 rows of 64 floats, row stride 68) so that
+    // the global accesses run along the right-hand sides of a port (16
+    // threads x 4 columns per row, 8 rows per pass): w_out = T W_in + c, this
+    // sweep's w_in, and the residual terms of the previous sweep for the node
+    // runs that start in the item (each run's terms summed in port order, then
+    // squared), the same arithmetic as batch_residual.
+    float* tr = reinterpret_cast<float*>(As);
+    constexpr int kTrLd = 68;
+    constexpr int kRowSlots = kTcThreads / 16;
+    const int cq = tid & 15, rq = tid >> 4;  // column group, row slot
+    float sq[4] = {0.f, 0.f, 0.f, 0.f};
+    const bool vec = (R & 3) == 0;
+    const int quarter = warp & 3, half = warp >> 2;  // TMEM lanes 32 quarter.., columns 32 half..
+    for (int mt = 0; mt < nmt; ++mt) {
+      if (k > 1) {
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+          float v[16];
+          const int col = half * 32 + cc * 16;
+          tc_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + mt * 64 + col, v);
+          float* dst = tr + (32 * quarter + lane) * kTrLd + col;
+#pragma unroll
+          for (int i = 0; i < 16; i += 4) *reinterpret_cast<float4*>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+        }
+      }
+      // the tile's port tables (twin, node run, g/W, d/2) into the idle B buffers
+      int* mtw = reinterpret_cast<int*>(Bs);
+      int* mrn = mtw + kTcM;
+      float2* mkd = reinterpret_cast<float2*>(mrn + kTcM);
+      float* tm = Sg;  // residual term of every port of the tile (rows of 68)
+      if (tid < kTcM) {
+        const int s = m0 + mt * kTcM + tid;
+        int tw = 0, nr = 0;
+        float2 kk = make_float2(0.f, 0.f);
+        if (s < m1) {
+          const size_t ps = (size_t)(p0 + s);
+          tw = twin[ps];
+          nr = run[ps];
+          const double2 k2 = kd[ps];
+          kk = make_float2((float)k2.x, 0.5f * (float)k2.y);
+        }
+        mtw[tid] = tw;
+        mrn[tid] = nr;
+        mkd[tid] = kk;
+      }
+      __syncthreads();
+      auto load4 = [&](const float* src, int r0, float (&o)[4]) {
+        if (vec) {
+          const float4 f = *reinterpret_cast<const float4*>(src);
+          o[0] = f.x; o[1] = f.y; o[2] = f.z; o[3] = f.w;
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) o[j] = r0 + j < R ? src[j] : 0.f;
+        }
+      };
+      auto store4 = [&](float* dst, int r0, const float (&o)[4]) {
+        if (vec) {
+          *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (r0 + j < R) dst[j] = o[j];
+        }
+      };
+      // residual term of port pq (twin tq) for columns r0..+3: the arithmetic
+      // of batch_residual
+      auto term4 = [&](const float (&wis)[4], const float (&wos)[4], const float (&wit)[4],
+                       const float (&wot)[4], float2 kq, float (&t)[4]) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float Ss = wis[j] + wos[j], St = wit[j] + wot[j];
+          t[j] = kq.y * (0.5f * (Ss + St) - kq.x * (Ss - St) - wis[j] - wit[j]);
+        }
+      };
+      const int r0 = 4 * cq;
+      // outputs and every port's residual term: two rows of this thread at a
+      // time, all their loads issued together
+      constexpr int kRows = kTcM / kRowSlots;  // rows per thread and tile
+      for (int i0 = 0; i0 < kRows; i0 += 2) {
+        float cv[2][4], wt[2][4], wis[2][4], wos[2][4], wit[2][4];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int row = rq + kRowSlots * (i0 + u);
+          const int s = m0 + mt * kTcM + row;
+          const size_t ps = (size_t)(p0 + (s < m1 ? s : 0));
+#pragma unroll
+          for (int j = 0; j < 4; ++j) cv[u][j] = wt[u][j] = wis[u][j] = wos[u][j] = wit[u][j] = 0.f;
+          if (s < m1 && r0 < R) {
+            load4(c + ps * R + r0, r0, cv[u]);
+            if (k > 1) {
+              const size_t tw = (size_t)mtw[row];
+              load4(prev + tw * 2 * R + R + r0, r0, wt[u]);
+              load4(prev + ps * 2 * R + r0, r0, wis[u]);
+              load4(prev + ps * 2 * R + R + r0, r0, wos[u]);
+              load4(prev + tw * 2 * R + r0, r0, wit[u]);
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int row = rq + kRowSlots * (i0 + u);
+          const int s = m0 + mt * kTcM + row;
+          if (s < m1 && r0 < R) {
+            const size_t ps = (size_t)(p0 + s);
+            float o[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) o[j] = (k > 1 ? tr[row * kTrLd + r0 + j] : 0.f) + cv[u][j];
+            store4(cur + ps * 2 * R + r0, r0, wt[u]);
+            store4(cur + ps * 2 * R + R + r0, r0, o);
+            if (k > 1) {
+              float t[4];
+              term4(wis[u], wos[u], wit[u], wt[u], mkd[row], t);
+#pragma unroll
+              for (int j = 0; j < 4; ++j) tm[row * kTrLd + r0 + j] = t[j];
+            }
+          }
+        }
+      }
+      __syncthreads();
+      // the nodes whose runs of ports start in the tile: each run's terms
+      // summed in port order, then squared (ports past the tile's last row
+      // come from global memory)
+      if (k > 1 && r0 < R) {
+        for (int i = 0; i < kRows; ++i) {
+          const int row = rq + kRowSlots * i;
+          const int s = m0 + mt * kTcM + row;
+          if (s >= m1) break;
+          const int nr = mrn[row];
+          if (!nr) continue;
+          float rs[4] = {0.f, 0.f, 0.f, 0.f};
+          for (int qq = 0; qq < nr; ++qq) {
+            float t[4];
+            const int rowq = row + qq;
+            if (rowq < kTcM) {
+#pragma unroll
+              for (int j = 0; j < 4; ++j) t[j] = tm[rowq * kTrLd + r0 + j];
+            } else {
+              const size_t pq = (size_t)(p0 + s + qq);
+              const size_t tq = (size_t)twin[pq];
+              const double2 k2 = kd[pq];
+              float a1[4], a2[4], a3[4], a4[4];
+              load4(prev + pq * 2 * R + r0, r0, a1);
+              load4(prev + pq * 2 * R + R + r0, r0, a2);
+              load4(prev + tq * 2 * R + r0, r0, a3);
+              load4(prev + tq * 2 * R + R + r0, r0, a4);
+              term4(a1, a2, a3, a4, make_float2((float)k2.x, 0.5f * (float)k2.y), t);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) rs[j] += t[j];
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) sq[j] += rs[j] * rs[j];
+        }
+      }
+      __syncthreads();  // before the next tile's accumulators overwrite the staging rows
+    }
+    tc_fence_before();  // these TMEM reads precede the next item's MMAs
+    // the item's squared residual per column: the row slots in order (lanes
+    // l and l + 16 of a warp, then the warps)
+    double* red8 = reinterpret_cast<double*>(tr);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float o16 = __shfl_xor_sync(0xffffffffu, sq[j], 16);
+      if (lane < 16) red8[warp * 64 + 4 * cq + j] = (double)sq[j] + (double)o16;
+    }
+    __syncthreads();
+    for (int r = tid; r < R; r += blockDim.x) {
+      double t = 0.0;
+      if (k > 1)
+        for (int w8 = 0; w8 < kTcThreads / 32; ++w8) t += red8[w8 * 64 + r];
+      partials[(size_t)item * R + r] = t;
+    }
+    __syncthreads();
+  }  // work list
+  if (s_abort && warp == 0 && lane == 0) {
+    // copies in flight land before the CTA releases its shared memory (bounded)
+    for (uint32_t gq = (q_issued > kTcS ? q_issued - kTcS : 0); gq < q_issued; ++gq)
+      mbar_wait_bounded(&full[gq % kTcS], (gq / kTcS) & 1, kTcPolls);
+  }
+  if (s_abort && warp == 1 && lane == 0) {
+    // and the MMAs issued complete before it releases its TMEM (bounded)
+    tc_commit(&bdone[cg & 1]);
+    mbar_wait_bounded(&bdone[cg & 1], (cg >> 1) & 1, kTcPolls);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols) : "memory");
+  if (s_abort) return;
+  if (tid == 0) {
+    __threadfence();
+    s_last = atomicAdd(&ctrl->counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  batch_finish(ctrl, partials, nitems, R, tol2, hist, hist_len, k);
+}
+
+// T_P of every work item in the tcgen05 tile layout: tile q = kc * nmt + mt
+// of the item holds T_P(s, t) for s = m0 + 128 mt + m, t = 64 kc + kk at core
+// matrix (m / 8, kk / 8), row m % 8, element kk % 8 (BF16, zero outside p);
+// T_P(s, t) is element t ld + s of the tile's T^T block.
+__global__ void pack_tc_kernel(const double* __restrict__ T64, const int64_t* __restrict__ T_off,
+                               const int32_t* __restrict__ T_ld, const int32_t* __restrict__ port_off,
+                               const int4* __restrict__ items, const int64_t* __restrict__ item_off,
+                               __nv_bfloat16* __restrict__ out) {
+  const int4 it = items[blockIdx.x];
+  const int tile = it.x, m0 = it.y, nmt = it.z, nkc = it.w;
+  const int p = port_off[tile + 1] - port_off[tile];
+  const int ld = T_ld[tile];
+  const double* Tt = T64 + T_off[tile];
+  __nv_bfloat16* o = out + item_off[blockIdx.x];
+  const int64_t nel = (int64_t)nmt * nkc * kTcM * kTcK;
+  for (int64_t i = threadIdx.x; i < nel; i += blockDim.x) {
+    const int q = (int)(i / (kTcM * kTcK)), e = (int)(i % (kTcM * kTcK));
+    const int kc = q / nmt, mt = q % nmt;
+    const int core = e / 64, w = e % 64;
+    const int m = (core / 8) * 8 + w / 8, kk = (core % 8) * 8 + w % 8;
+    const int s = m0 + mt * kTcM + m, t = kc * kTcK + kk;
+    const double v = (s < p && t < p) ? Tt[(size_t)t * ld + s] : 0.0;
+    o[i] = __float2bfloat16_rn((float)v);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host driver for a batch of right-hand sides
 // ---------------------------------------------------------------------------
 
@@ -914,12 +1399,48 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
     VTM_TRY(upload(P->d_item_order, order, s));
   }
   const int nitems = (int)P->item_tile.size();
+  // tcgen05 work items and the tiled BF16 copy of T_P (BF16 plans; built at
+  // the first batched solve after each factorisation)
+  if (prec == VTM_PREC_BF16 && P->tc_nitems == 0) {
+    std::vector<int32_t> it4;
+    std::vector<int64_t> off;
+    std::vector<int64_t> cost;
+    int64_t o = 0;
+    for (int32_t t = 0; t < P->nparts; ++t) {
+      const int32_t pp = P->port_off[t + 1] - P->port_off[t];
+      if (pp == 0) continue;
+      const int nmt = (pp + kTcM - 1) / kTcM, nkc = (pp + kTcK - 1) / kTcK;
+      for (int g0 = 0; g0 < nmt; g0 += kTcG) {
+        const int ng = std::min(kTcG, nmt - g0);
+        it4.insert(it4.end(), {t, g0 * kTcM, ng, nkc});
+        off.push_back(o);
+        cost.push_back((int64_t)std::min(ng * kTcM, pp - g0 * kTcM) * pp);
+        o += (int64_t)ng * nkc * kTcM * kTcK;
+      }
+    }
+    const int nt = (int)off.size();
+    std::vector<int32_t> order(nt);
+    for (int i = 0; i < nt; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+    VTM_TRY(upload(P->d_tc_items, it4, s));
+    VTM_TRY(upload(P->d_tc_off, off, s));
+    VTM_TRY(upload(P->d_tc_order, order, s));
+    VTM_TRY(dev_alloc(P->d_Ttc, (size_t)std::max<int64_t>(o, 8) * sizeof(__nv_bfloat16)));
+    if (nt > 0)
+      pack_tc_kernel<<<nt, 256, 0, s>>>(P->d_T64.as<double>(), P->tabs.T_off.as<int64_t>(),
+                                        P->tabs.T_ld.as<int32_t>(), P->tabs.port_off.as<int32_t>(),
+                                        P->d_tc_items.as<int4>(), P->d_tc_off.as<int64_t>(),
+                                        P->d_Ttc.as<__nv_bfloat16>());
+    VTM_CUDA_TRY(cudaGetLastError());
+    P->launch_count++;
+    P->tc_nitems = nt;
+  }
   const bool lowp = prec != VTM_PREC_FP64;
   const size_t wsz = lowp ? sizeof(float) : sizeof(double);
   VTM_TRY(dev_alloc(P->d_bV, (size_t)n * R * sizeof(double)));
   VTM_TRY(dev_alloc(P->d_bstate, 4 * (size_t)std::max<int64_t>(npt, 1) * R * wsz));
   VTM_TRY(dev_alloc(P->d_bc, (size_t)std::max<int64_t>(npt, 1) * R * wsz));
-  VTM_TRY(dev_alloc(P->d_bpart, (size_t)std::max(nitems, 1) * R * sizeof(double)));
+  VTM_TRY(dev_alloc(P->d_bpart, (size_t)std::max(std::max(nitems, P->tc_nitems), 1) * R * sizeof(double)));
   VTM_TRY(dev_alloc(P->d_btol2, 64 * sizeof(double)));
   VTM_TRY(dev_alloc(P->d_bctrl, sizeof(BatchCtrl)));
   VTM_TRY(dev_alloc(P->d_xacc, (size_t)n * R * sizeof(double)));
@@ -1007,8 +1528,30 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
       // of a persistent grid (SMs x resident CTAs) over the work list
       // (dry = true: only size the grid, before any graph capture)
       auto launch_batch = [&](int kv, bool dry = false) {
+        if (kv == 4) {  // tcgen05 (BF16): persistent CTAs over the tcgen05 work list
+          const int key = prec * 8 + kv;
+          if (P->batch_grid[key] == 0) {
+            cudaFuncSetAttribute(batch_sweep_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+            cudaFuncSetAttribute(batch_sweep_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+            int sms = 152, smem_sm = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, P->device);
+            // two CTAs of 256 TMEM columns fill an SM's 512, where their shared
+            // memory fits (the occupancy query is not used: it reported one)
+            const int per_sm = smem_sm >= 2 * ((int)kTcSmem + 2048) ? 2 : 1;
+            P->batch_grid[key] = std::max(1, std::min(P->tc_nitems, per_sm * sms));
+          }
+          if (dry) return;
+          batch_sweep_tc_kernel<<<P->batch_grid[key], kTcThreads, kTcSmem, s>>>(
+              P->d_Ttc.as<__nv_bfloat16>(), P->d_tc_items.as<int4>(), P->d_tc_off.as<int64_t>(),
+              P->d_tc_order.as<int32_t>(), P->tc_nitems, P->tabs.port_off.as<int32_t>(), P->d_twin.as<int32_t>(),
+              P->d_kd.as<double2>(), P->d_run.as<uint8_t>(), P->d_bc.as<float>(), P->d_bstate.as<float>(), npt,
+              R, P->d_bctrl.as<BatchCtrl>(), P->d_bpart.as<double>(), P->d_btol2.as<double>(), bhist, bhist_len);
+          return;
+        }
         auto go = [&](auto* kern, int threads, const auto* T, const auto* cc, auto* st) {
-          const int key = prec * 4 + kv;
+          const int key = prec * 8 + kv;
           if (P->batch_grid[key] == 0) {
             int per_sm = 1;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
@@ -1048,14 +1591,16 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
       int kv = 0;
       if (P->opts.batch_kernel > 0) {
         // the caller's choice: bit 0 tensor cores (BF16 with R % 8 == 0 only),
-        // bit 1 one work item per CTA
+        // bit 1 one work item per CTA; 4: tcgen05 (BF16 plans, else CUDA cores)
         kv = P->opts.batch_kernel - 1;
-        if ((kv & 1) && !(prec == VTM_PREC_BF16 && R % 8 == 0)) kv &= ~1;
+        if (kv == 4 && prec != VTM_PREC_BF16) kv = 0;
+        if (kv != 4 && (kv & 1) && !(prec == VTM_PREC_BF16 && R % 8 == 0)) kv &= ~1;
       } else {
         if (P->batch_tuned[prec] == 0 || P->batch_tuned_R[prec] != R) {
           float best = 1e30f;
-          for (int cand = 0; cand <= 3; ++cand) {
-            if ((cand & 1) && !(prec == VTM_PREC_BF16 && R % 8 == 0)) continue;
+          for (int cand = 0; cand <= 4; ++cand) {
+            if (cand == 4 && prec != VTM_PREC_BF16) continue;
+            if (cand != 4 && (cand & 1) && !(prec == VTM_PREC_BF16 && R % 8 == 0)) continue;
             BatchCtrl tt = h;
             tt.k_max = 1 << 30;
             tt.stall = 0;
@@ -1132,6 +1677,10 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
         if (hc.flag || launched > sweeps_left) break;
       }
       flag = hc.flag;
+      if (flag == 5) {
+        set_detail("vtm_solve (batched): a bounded wait of the tcgen05 sweep ran out");
+        return VTM_ETIMEOUT;
+      }
       kc = (flag == 1 || flag == 4) ? hc.conv_sweep : std::min(hc.k - 1, sweeps_left);
       if (bhist) {
         std::vector<double> hh(bhist_len);

@@ -691,6 +691,9 @@ extern "C" vtm_status vtm_factor(vtm_plan_t P) {
     P->sweep_graph[i] = SweepGraph{};
     P->batch_graph[i] = SweepGraph{};
   }
+  // the tiled copy of the tcgen05 batched sweep follows the factors
+  dev_free(P->d_Ttc);
+  P->tc_nitems = 0;
   // the band arrays hold K_P before the factorisation: re-assemble if a
   // previous factorisation overwrote them
   static_assert(sizeof(double) == 8, "");

@@ -764,7 +764,7 @@ std::vector<DevBuf*> vtm_plan_s::all_bufs() {
           &d_err, &d_red, &d_in_off, &d_out_off, &d_in_src, &d_in_kind, &d_in_twin,
           &d_in_own_out, &d_in_loc, &d_res_perm, &d_res_run, &d_out_loc, &d_in_coef, &d_in_d,
           &d_in_sigma, &d_out_scale, &d_out_diag, &d_E_off, &d_E_ld, &d_E, &d_cg, &d_gin,
-          &d_gout, &d_in_tile, &d_item_tile, &d_item_m0, &d_item_order, &d_bV, &d_bV32, &d_bstate,
+          &d_gout, &d_in_tile, &d_item_tile, &d_item_m0, &d_item_order, &d_tc_items, &d_tc_off, &d_tc_order, &d_Ttc, &d_bV, &d_bV32, &d_bstate,
           &d_bc, &d_bpart,
           &d_btol2, &d_bctrl, &d_bres, &d_stage_in[0], &d_stage_in[1], &d_stage_in[2],
           &d_stage_out[0], &d_stage_out[1], &d_stage_out[2]};
@@ -873,8 +873,8 @@ extern "C" vtm_status vtm_set_opts(vtm_plan_t P, const vtm_opts* opts) {
     set_detail("vtm_set_opts: method must be 0..2, and block Jacobi is chosen by vtm_plan");
     return VTM_EINVAL;
   }
-  if (o.batch_kernel < 0 || o.batch_kernel > 4 || o.wait_polls < 0 || (o.flow_lag != 0 && o.flow_lag != -1)) {
-    set_detail("vtm_set_opts: batch_kernel must be 0..4, wait_polls >= 0, flow_lag 0 or -1");
+  if (o.batch_kernel < 0 || o.batch_kernel > 5 || o.wait_polls < 0 || (o.flow_lag != 0 && o.flow_lag != -1)) {
+    set_detail("vtm_set_opts: batch_kernel must be 0..5, wait_polls >= 0, flow_lag 0 or -1");
     return VTM_EINVAL;
   }
   bool prec_changed = o.precision != P->opts.precision;

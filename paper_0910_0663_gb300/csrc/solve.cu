@@ -1748,8 +1748,10 @@ __global__ void __launch_bounds__(1024, 1) sweep_wmma_kernel(
 
 constexpr int kWdfKB = 2;  // ring slots per warp (2 KB each)
 
+// per warp: the ring, then w_in and the output accumulators (the residual
+// terms live in the last ring slot, which no copy fills before the blocks)
 __host__ __device__ constexpr size_t wdf_warp_bytes(int pp_max, int kb) {
-  return (size_t)kb * 2 * kSymB * kSymB * sizeof(float) + 24 * (size_t)pp_max;
+  return (size_t)kb * 2 * kSymB * kSymB * sizeof(float) + 16 * (size_t)pp_max;
 }
 
 __device__ __forceinline__ df shfl_xor_df(df v, int m) {
@@ -1803,8 +1805,9 @@ __global__ void __launch_bounds__(1024, 1) sweep_wdf_kernel(
   const float* Tl = Tp + 2 * dsc.Tp_off;
   float* ring = reinterpret_cast<float*>(smem_raw + (size_t)(tile_warp ? warp : 0) * wdf_warp_bytes(pp_max, KB));
   df* w_in = reinterpret_cast<df*>(ring + KB * BLK);
-  df* rs = w_in + pp_max;
-  dacc* acc = reinterpret_cast<dacc*>(rs + pp_max);
+  dacc* acc = reinterpret_cast<dacc*>(w_in + pp_max);
+  // residual terms: in ring slot KB - 1, free until the block loop's first copy
+  df* rs = reinterpret_cast<df*>(ring + (KB - 1) * BLK);
   int tw[PPL];
   uint32_t rn4 = 0;
   int pbi = 0, pbj = 0, pidx = 0, pq = 0;

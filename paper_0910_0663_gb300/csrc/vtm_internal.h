@@ -278,7 +278,11 @@ struct vtm_plan_s {
   int batch_tuned[4] = {0, 0, 0, 0};  // batched sweep variant + 1, per precision
   int batch_tuned_R[4] = {0, 0, 0, 0};  // right-hand sides it was tuned for
   int batch_used = 0;                   // batched sweep variant + 1 of the last batched solve
-  int batch_grid[16] = {0};          // grid per (precision, variant)
+  int batch_grid[32] = {0};          // grid per (precision, variant)
+  // tcgen05 batched sweep: work items (tile, first row, M tiles, input
+  // chunks), their offsets into the tiled BF16 copy of T_P, longest first
+  int tc_nitems = 0;
+  vtm::DevBuf d_tc_items, d_tc_off, d_tc_order, d_Ttc;
 
   // adjoint of an unsymmetric system
   vtm_plan_s* transposed = nullptr;

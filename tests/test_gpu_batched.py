@@ -110,7 +110,7 @@ def test_batched_graph_path_on_a_dedicated_stream(vtm):
 
 
 @pytest.mark.parametrize("precision,batch_kernel", [("fp64", 1), ("fp64", 3), ("bf16", 1), ("bf16", 2),
-                                                    ("bf16", 3), ("bf16", 4)])
+                                                    ("bf16", 3), ("bf16", 4), ("bf16", 5)])
 def test_every_batched_variant_against_the_oracle(vtm, precision, batch_kernel):
     # each variant forced (CUDA cores or BF16 tensor-core warp MMAs; persistent
     # grid or one work item per CTA): the result is FP64-verified and the
@@ -136,3 +136,27 @@ def test_every_batched_variant_against_the_oracle(vtm, precision, batch_kernel):
         k = min(12, int(np.count_nonzero((h > 0) & (href[: len(h)] > 1e-3))))
         assert k >= 3
         assert np.allclose(h[:k], href[:k], rtol=5e-2, atol=0)
+
+
+@pytest.mark.parametrize("nrhs", [64, 5])
+def test_tcgen05_batched_sweep_on_the_full_thermal_grid(vtm, nrhs):
+    # the tcgen05 variant on the 128x128x32 grid in 400 boxes (ports per box
+    # 263-2459: up to 20 M tiles of 128 and 39 input chunks of 64, items of
+    # four M tiles), 64 columns and a ragged 5 (the B operand's other columns
+    # are zero): FP64-verified result, and its first inner solve follows the
+    # CUDA-core BF16 variant's residual history within the waves' BF16 rounding
+    w = wl.c3_thermal(nrhs=nrhs)
+    A = w.csr()
+    b = torch.from_numpy(w.b).cuda()
+    hist = {}
+    for bk in (5, 1):
+        plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc, precision="bf16",
+                        batch_kernel=bk)
+        plan.set_options(history_len=12)
+        x, info = plan.solve(b, tol=1e-10)
+        assert plan.stats()["batch_kernel"] == bk
+        assert O.residual_norms(A, x.cpu().numpy(), w.b).max() <= 1e-10
+        hist[bk] = plan.history
+        plan.close()
+    k = int(np.count_nonzero((hist[5] > 0) & (hist[1] > 0)))
+    assert k >= 3 and np.allclose(hist[5][:k], hist[1][:k], rtol=2e-2, atol=0)
