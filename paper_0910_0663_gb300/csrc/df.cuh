@@ -103,4 +103,43 @@ __device__ __forceinline__ dacc dacc_add(dacc a, dacc b) {
 // cancelled below E)
 __device__ __forceinline__ df dacc_value(dacc a) { return two_sum(a.S, a.E); }
 
+// Paired forms (two independent values in the two halves of a 64-bit
+// register, one FADD2 / FMUL2 / FFMA2 instruction for both): the same
+// roundings as dacc_first / dacc_fma, value by value, at half the
+// instructions.  A subtraction x - y is the exactly rounded fma(y, -1, x).
+struct dacc2 {
+  float2 S, E;
+};
+
+__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ dacc2 dacc2_first(float2 th, float2 tl, float2 wh, float2 wl) {
+  const float2 p = __fmul2_rn(th, wh);
+  float2 e = __ffma2_rn(th, wh, f2neg(p));
+  e = __ffma2_rn(th, wl, e);
+  e = __ffma2_rn(tl, wh, e);
+  return {p, e};
+}
+
+// a += (th + tl)(wh + wl); whn = -wh (the negated product's high part is
+// formed directly, so that p = -pn needs no extra instruction)
+__device__ __forceinline__ void dacc2_fma(dacc2& a, float2 th, float2 tl, float2 wh, float2 whn, float2 wl) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+  const float2 pn = __fmul2_rn(th, whn);           // -rn(th wh)
+  float2 e = __ffma2_rn(th, wh, pn);               // th wh - p, exact
+  e = __ffma2_rn(th, wl, e);
+  e = __ffma2_rn(tl, wh, e);
+  const float2 s = __ffma2_rn(pn, m1, a.S);        // S + p
+  const float2 bb = __ffma2_rn(a.S, m1, s);        // s - S
+  const float2 t1 = __ffma2_rn(bb, m1, s);         // s - bb
+  const float2 a1 = __ffma2_rn(t1, m1, a.S);       // S - t1
+  const float2 a2n = __fadd2_rn(pn, bb);           // -(p - bb)
+  const float2 err = __ffma2_rn(a2n, m1, a1);      // (S - t1) + (p - bb)
+  a.S = s;
+  a.E = __fadd2_rn(a.E, __fadd2_rn(err, e));
+}
+
+__device__ __forceinline__ dacc dacc2_lo(const dacc2& a) { return {a.S.x, a.E.x}; }
+__device__ __forceinline__ dacc dacc2_hi(const dacc2& a) { return {a.S.y, a.E.y}; }
+
 }  // namespace vtm

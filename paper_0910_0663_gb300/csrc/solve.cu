@@ -1923,9 +1923,8 @@ __global__ void __launch_bounds__(1024, 1) sweep_wdf_kernel(
   const bool row_owner = !(lane & 2), col_owner = !(lane & 4);
   const int myrow = b0 ? r1 + 8 : r1;
   const int mycol = cg * 4 + (b4 ? 2 : 0) + (b3 ? 1 : 0);
-  dacc ca[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) ca[j] = {0.f, 0.f};
+  // column partials of columns (0, 1) and (2, 3) of this lane's four, as pairs
+  dacc2 ca01 = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, ca23 = ca01;
   int bi = 0, bj = 0;
   for (int kk = 0; kk < nblk; ++kk) {
     issue_next();
@@ -1935,47 +1934,48 @@ __global__ void __launch_bounds__(1024, 1) sweep_wdf_kernel(
     const float4 hb = reinterpret_cast<const float4*>(blk)[lane + 32];
     const float4 la = reinterpret_cast<const float4*>(blk + B * B)[lane];
     const float4 lb = reinterpret_cast<const float4*>(blk + B * B)[lane + 32];
-    {  // row partials of rows r1 (a) and r1 + 8 (b) over this lane's four columns
+    {  // row partials of rows r1 (a) and r1 + 8 (b) over this lane's four columns,
+       // the two rows as the halves of one pair
       const df* wc = w_in + bj * B + cg * 4;
       const df w0 = wc[0], w1 = wc[1], w2 = wc[2], w3 = wc[3];
-      dacc x1 = dacc_first(ha.x, la.x, w0.h, w0.l);
-      dacc_fma(x1, ha.y, la.y, w1.h, w1.l);
-      dacc_fma(x1, ha.z, la.z, w2.h, w2.l);
-      dacc_fma(x1, ha.w, la.w, w3.h, w3.l);
-      dacc x2 = dacc_first(hb.x, lb.x, w0.h, w0.l);
-      dacc_fma(x2, hb.y, lb.y, w1.h, w1.l);
-      dacc_fma(x2, hb.z, lb.z, w2.h, w2.l);
-      dacc_fma(x2, hb.w, lb.w, w3.h, w3.l);
+      dacc2 x = dacc2_first(make_float2(ha.x, hb.x), make_float2(la.x, lb.x), make_float2(w0.h, w0.h),
+                            make_float2(w0.l, w0.l));
+      dacc2_fma(x, make_float2(ha.y, hb.y), make_float2(la.y, lb.y), make_float2(w1.h, w1.h),
+                make_float2(-w1.h, -w1.h), make_float2(w1.l, w1.l));
+      dacc2_fma(x, make_float2(ha.z, hb.z), make_float2(la.z, lb.z), make_float2(w2.h, w2.h),
+                make_float2(-w2.h, -w2.h), make_float2(w2.l, w2.l));
+      dacc2_fma(x, make_float2(ha.w, hb.w), make_float2(la.w, lb.w), make_float2(w3.h, w3.h),
+                make_float2(-w3.h, -w3.h), make_float2(w3.l, w3.l));
+      const dacc x1 = dacc2_lo(x), x2 = dacc2_hi(x);
       // the row's four lanes (bits 0, 1): reduce-scatter over bit 0, sum over bit 1
       dacc t = dacc_add(b0 ? x2 : x1, shfl_xor_dacc(b0 ? x1 : x2, 1));
       t = dacc_add(t, shfl_xor_dacc(t, 2));
       if (row_owner) acc[bi * B + myrow] = dacc_add(acc[bi * B + myrow], t);
     }
     if (bi != bj) {
+      // columns (0, 1) and (2, 3) as pairs, rows r1 and r1 + 8 one after the other
       const df wr1 = w_in[bi * B + r1], wr2 = w_in[bi * B + r1 + 8];
-      dacc_fma(ca[0], ha.x, la.x, wr1.h, wr1.l);
-      dacc_fma(ca[0], hb.x, lb.x, wr2.h, wr2.l);
-      dacc_fma(ca[1], ha.y, la.y, wr1.h, wr1.l);
-      dacc_fma(ca[1], hb.y, lb.y, wr2.h, wr2.l);
-      dacc_fma(ca[2], ha.z, la.z, wr1.h, wr1.l);
-      dacc_fma(ca[2], hb.z, lb.z, wr2.h, wr2.l);
-      dacc_fma(ca[3], ha.w, la.w, wr1.h, wr1.l);
-      dacc_fma(ca[3], hb.w, lb.w, wr2.h, wr2.l);
+      const float2 h1 = make_float2(wr1.h, wr1.h), n1 = make_float2(-wr1.h, -wr1.h), l1 = make_float2(wr1.l, wr1.l);
+      const float2 h2 = make_float2(wr2.h, wr2.h), n2 = make_float2(-wr2.h, -wr2.h), l2 = make_float2(wr2.l, wr2.l);
+      dacc2_fma(ca01, make_float2(ha.x, ha.y), make_float2(la.x, la.y), h1, n1, l1);
+      dacc2_fma(ca01, make_float2(hb.x, hb.y), make_float2(lb.x, lb.y), h2, n2, l2);
+      dacc2_fma(ca23, make_float2(ha.z, ha.w), make_float2(la.z, la.w), h1, n1, l1);
+      dacc2_fma(ca23, make_float2(hb.z, hb.w), make_float2(lb.z, lb.w), h2, n2, l2);
       ++bi;
     } else {
       __syncwarp();  // the diagonal block's row partial is in before the column's
       if (bj > 0) {
         // columns 4 cg..+3: sums over the eight lanes of a column group (bits 4, 3, 2)
-        dacc k0 = b4 ? ca[2] : ca[0], k1 = b4 ? ca[3] : ca[1];
-        k0 = dacc_add(k0, shfl_xor_dacc(b4 ? ca[0] : ca[2], 16));
-        k1 = dacc_add(k1, shfl_xor_dacc(b4 ? ca[1] : ca[3], 16));
+        const dacc c0 = dacc2_lo(ca01), c1 = dacc2_hi(ca01), c2 = dacc2_lo(ca23), c3 = dacc2_hi(ca23);
+        dacc k0 = b4 ? c2 : c0, k1 = b4 ? c3 : c1;
+        k0 = dacc_add(k0, shfl_xor_dacc(b4 ? c0 : c2, 16));
+        k1 = dacc_add(k1, shfl_xor_dacc(b4 ? c1 : c3, 16));
         dacc t1 = dacc_add(b3 ? k1 : k0, shfl_xor_dacc(b3 ? k0 : k1, 8));
         t1 = dacc_add(t1, shfl_xor_dacc(t1, 4));
         if (col_owner) acc[bj * B + mycol] = dacc_add(acc[bj * B + mycol], t1);
       }
       __syncwarp();  // and the column partial before later rows add to this block
-#pragma unroll
-      for (int j = 0; j < 4; ++j) ca[j] = {0.f, 0.f};
+      ca01 = ca23 = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
       ++bj;
       bi = 0;
     }
