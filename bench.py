@@ -329,12 +329,14 @@ def sweep_kernel_name(kernel, nrhs, batch_kernel=0):
 
 
 def sweep_kernel_source_hash():
-    """sha256 of the device code of the launch-per-sweep packed kernels in
+    """sha256 of the device code of the launch-per-sweep packed kernels 5-11 in
     solve.cu and their shared block code (the text from their section header to
-    the dataflow kernels' section)."""
+    the next section: the double-float kernel 12, or the dataflow kernels)."""
     src = open(os.path.join(ROOT, "paper_0910_0663_gb300", "csrc", "solve.cu")).read()
     i = src.find("// Packed symmetric sweep.")
-    j = src.find("// Dataflow sweeps: one cooperative launch", i)
+    j = src.find("// FP64-accurate packed sweep", i)
+    if j < 0:
+        j = src.find("// Dataflow sweeps: one cooperative launch", i)
     return hashlib.sha256(src[i:j].encode()).hexdigest() if 0 <= i < j else None
 
 

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <numeric>
 #include <queue>
+#include <thread>
 
 #include "vtm_internal.h"
 
@@ -127,6 +128,26 @@ static void tile_rcm(const vtm_plan_s* P, const std::vector<int32_t>& nodes, int
   for (size_t a = 0; a < m; ++a) out[a] = nodes[order[m - 1 - a]];
 }
 
+// f(i) for i in [0, count), spread over the host's cores (interleaved, so that
+// neighbouring items of uneven cost land on different threads).  f must only
+// write state that no other i touches.
+template <class F>
+static void parallel_items(int64_t count, F&& f) {
+  const unsigned hw = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  const int64_t nt = std::min<int64_t>(hw, std::max<int64_t>(1, count / 16));
+  if (nt <= 1) {
+    for (int64_t i = 0; i < count; ++i) f(i);
+    return;
+  }
+  std::vector<std::thread> pool;
+  pool.reserve(nt);
+  for (int64_t t = 0; t < nt; ++t)
+    pool.emplace_back([&, t]() {
+      for (int64_t i = t; i < count; i += nt) f(i);
+    });
+  for (auto& th : pool) th.join();
+}
+
 static int64_t csr_find(const vtm_plan_s* P, int32_t i, int32_t j) {
   const int32_t* b = P->h_colidx.data() + P->h_rowptr[i];
   const int32_t* e = P->h_colidx.data() + P->h_rowptr[i + 1];
@@ -164,10 +185,13 @@ static vtm_status build_structure(vtm_plan_s* P, std::vector<CutPair>& pairs) {
   P->perm.assign(n, 0);
   P->iperm.assign(n, 0);
   P->bw.assign(np, 0);
-  std::vector<int32_t> loc_of(n, 0), mark(n, 0), rcm;
-  P->max_nodes = 0;
-  P->max_bw = 0;
-  for (int32_t t = 0; t < np; ++t) {
+  // per tile: natural or reverse Cuthill-McKee order, whichever has the smaller
+  // half bandwidth; tiles in parallel (each touches only its own nodes'
+  // entries of loc_of, mark, perm and iperm)
+  std::vector<int32_t> loc_of(n, 0), mark(n, 0);
+  parallel_items(np, [&](int64_t tt) {
+    const int32_t t = (int32_t)tt;
+    std::vector<int32_t> rcm;
     auto& nd = tnodes[t];
     for (size_t a = 0; a < nd.size(); ++a) loc_of[nd[a]] = (int32_t)a;
     int bw_nat = tile_bandwidth(P, nd, loc_of, t);
@@ -188,8 +212,12 @@ static vtm_status build_structure(vtm_plan_s* P, std::vector<CutPair>& pairs) {
       P->iperm[node] = P->node_off[t] + (int32_t)a;
     }
     P->bw[t] = bw_best;
-    P->max_nodes = std::max<int32_t>(P->max_nodes, (int32_t)nd.size());
-    P->max_bw = std::max(P->max_bw, bw_best);
+  });
+  P->max_nodes = 0;
+  P->max_bw = 0;
+  for (int32_t t = 0; t < np; ++t) {
+    P->max_nodes = std::max<int32_t>(P->max_nodes, P->node_off[t + 1] - P->node_off[t]);
+    P->max_bw = std::max(P->max_bw, P->bw[t]);
   }
   P->band_off.assign(np, 0);
   int64_t off = 0;
@@ -947,18 +975,24 @@ extern "C" vtm_status vtm_plan(int64_t n, const int64_t* rowptr, const int32_t* 
       }
     }
   }
-  // symmetric values -> Cholesky, else LU without pivoting
-  P->symmetric = true;
-  for (int64_t i = 0; i < n && P->symmetric; ++i)
-    for (int64_t q = P->h_rowptr[i]; q < P->h_rowptr[i + 1]; ++q) {
-      int32_t j = P->h_colidx[q];
-      if (j <= i) continue;
-      int64_t t = csr_find(P, j, (int32_t)i);
-      if (t < 0 || P->h_vals[t] != P->h_vals[q]) {
-        P->symmetric = false;
-        break;
-      }
-    }
+  // symmetric values -> Cholesky, else LU without pivoting (row blocks in parallel)
+  {
+    const int64_t nblk = (n + 4095) / 4096;
+    std::vector<char> asym(nblk, 0);
+    parallel_items(nblk, [&](int64_t blk) {
+      for (int64_t i = blk * 4096; i < std::min<int64_t>(n, (blk + 1) * 4096) && !asym[blk]; ++i)
+        for (int64_t q = P->h_rowptr[i]; q < P->h_rowptr[i + 1]; ++q) {
+          int32_t j = P->h_colidx[q];
+          if (j <= i) continue;
+          int64_t t = csr_find(P, j, (int32_t)i);
+          if (t < 0 || P->h_vals[t] != P->h_vals[q]) {
+            asym[blk] = 1;
+            break;
+          }
+        }
+    });
+    P->symmetric = std::find(asym.begin(), asym.end(), (char)1) == asym.end();
+  }
   vtm_opts o{};
   if (opts) o = *opts;
   if (o.method != VTM_METHOD_VTM && o.method != VTM_METHOD_BJ && o.method != VTM_METHOD_ASYNC) {
