@@ -901,6 +901,10 @@ extern "C" vtm_status vtm_set_opts(vtm_plan_t P, const vtm_opts* opts) {
     set_detail("vtm_set_opts: method must be 0..2, and block Jacobi is chosen by vtm_plan");
     return VTM_EINVAL;
   }
+  if (o.batch_solve < 0 || o.batch_solve > 1) {
+    set_detail("vtm_set_opts: batch_solve must be 0 or 1");
+    return VTM_EINVAL;
+  }
   if (o.batch_kernel < 0 || o.batch_kernel > 5 || o.wait_polls < 0 || (o.flow_lag != 0 && o.flow_lag != -1)) {
     set_detail("vtm_set_opts: batch_kernel must be 0..5, wait_polls >= 0, flow_lag 0 or -1");
     return VTM_EINVAL;

@@ -517,3 +517,24 @@ def test_double_float_iterates_after_k_sweeps(vtm, k):
                             keep_iterates=True)
     ref = its[k - 1][0]
     assert np.abs(x.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+@pytest.mark.parametrize("scale", [1e-30, 1e30])
+def test_tensor_core_sweep_at_extreme_magnitudes(vtm, precision, scale):
+    # b scaled by 1e-30 and 1e30 (not powers of two): the per-tile scale of the
+    # waves (2^(13 - E)) keeps the 16-bit (hi, lo) pairs in range, and the
+    # FP64 refinement reaches the tolerance the oracle's residual confirms
+    w = wl.power_grid(32 * 4, 32 * 4, 32, 32, Zc=1.0, seed=25)
+    A = w.csr()
+    b = w.b[0] * scale
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc, precision=precision,
+                    sweep_kernel=11)
+    x, info = plan.solve(torch.from_numpy(b).cuda(), tol=1e-10)
+    assert plan.stats()["sweep_kernel"] == 11
+    xs = x.cpu().numpy()
+    assert np.all(np.isfinite(xs))
+    assert O.residual_norms(A, xs[None], b[None]).max() <= 1e-10
+    # the same iteration as the unscaled solve up to the waves' rounding
+    x1, info1 = plan.solve(torch.from_numpy(w.b[0]).cuda(), tol=1e-10)
+    assert abs(info["sweeps"] - info1["sweeps"]) <= max(4, info1["sweeps"] // 20)
