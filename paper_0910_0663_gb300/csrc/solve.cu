@@ -48,6 +48,23 @@ __device__ __forceinline__ AT port_residual(AT wi_s, AT wo_s, AT wi_t, AT wo_t, 
   return (AT)0.5 * (AT)kd.y * ((AT)0.5 * (Ss + St) - (AT)kd.x * (Ss - St) - wi_s - wi_t);
 }
 
+// Range of the squared residuals in FP32: each tile scales its node
+// residuals by 2^-e (e the exponent of the largest) before squaring and the
+// FP64 partial is scaled back by 2^2e, so that residuals from 1e-30 to 1e30
+// of the right-hand side neither underflow nor overflow.  Power-of-two
+// scalings are exact: in FP32's normal range the partial is the same bits as
+// the unscaled sum.
+__device__ __forceinline__ int pow2_exponent(float v) {  // v >= 0
+  const int eb = (int)((__float_as_uint(v) >> 23) & 0xff);
+  return min(max(eb - 127, -126), 126);
+}
+__device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }
+__device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+__device__ __forceinline__ float warp_max(float v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
 template <class AT>
 struct KdOf {
   using type = float2;
@@ -1331,8 +1348,25 @@ __global__ void __launch_bounds__(1024, 1) sweep_wsym_kernel(
     }
   }
   __syncwarp();
-  float tile_sq = 0.f;  // lane 0: the four groups in order
+  float tile_sq = 0.f;  // lane 0: the four groups in order, scaled by 2^-2 tile_e
+  int tile_e = 0;
   if (k > 1) {
+    float rrv[PPL];
+    float rmax = 0.f;
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+#pragma unroll
+      for (int j = 0; j < PPL / 4; ++j) {
+        const int s = lane + 32 * (v + 4 * j);
+        const int nr = (rn4[j] >> (8 * v)) & 0xff;
+        float rr = 0.f;
+        if (s < p && nr)
+          for (int q = 0; q < nr; ++q) rr += rs[s + q];
+        rrv[v * (PPL / 4) + j] = rr;
+        rmax = fmaxf(rmax, fabsf(rr));
+      }
+    tile_e = pow2_exponent(warp_max(rmax));
+    const float rsc = pow2f(-tile_e);
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       float sq = 0.f;
@@ -1341,8 +1375,7 @@ __global__ void __launch_bounds__(1024, 1) sweep_wsym_kernel(
         const int s = lane + 32 * (v + 4 * j);
         const int nr = (rn4[j] >> (8 * v)) & 0xff;
         if (s < p && nr) {
-          float rr = 0.f;
-          for (int q = 0; q < nr; ++q) rr += rs[s + q];
+          const float rr = rrv[v * (PPL / 4) + j] * rsc;
           sq += rr * rr;
         }
       }
@@ -1420,7 +1453,7 @@ __global__ void __launch_bounds__(1024, 1) sweep_wsym_kernel(
     const int s = lane + 32 * m;
     if (s < p) *reinterpret_cast<float2*>(cur + 2 * (size_t)(p0 + s)) = make_float2(w_in[s], acc[s]);
   }
-  if (valid && lane == 0) partials2[(size_t)(k & 1) * nparts + dsc.tile] = (double)tile_sq;
+  if (valid && lane == 0) partials2[(size_t)(k & 1) * nparts + dsc.tile] = (double)tile_sq * pow2d(2 * tile_e);
 }
 
 // ---------------------------------------------------------------------------
@@ -1641,16 +1674,30 @@ __global__ void __launch_bounds__(1024, 1) sweep_wmma_kernel(
   const int se = min(max(267 - (int)((__float_as_uint(amax) >> 23) & 0xff), 1), 253);
   const float sc = __uint_as_float((uint32_t)se << 23), isc = __uint_as_float((uint32_t)(254 - se) << 23);
   __syncwarp();
-  float tile_sq = 0.f;  // lane 0: the four groups in order
+  float tile_sq = 0.f;  // lane 0: the four groups in order, scaled by 2^-2 tile_e
+  int tile_e = 0;
   if (k > 1) {
+    float rrv[PPL];
+    float rmax = 0.f;
+#pragma unroll
+    for (int m = 0; m < PPL; ++m) {
+      const int s = lane + 32 * m;
+      const int nr = (rn4 >> (8 * m)) & 0xff;
+      float rr = 0.f;
+      if (s < p && nr)
+        for (int q = 0; q < nr; ++q) rr += rs[s + q];
+      rrv[m] = rr;
+      rmax = fmaxf(rmax, fabsf(rr));
+    }
+    tile_e = pow2_exponent(warp_max(rmax));
+    const float rsc = pow2f(-tile_e);
 #pragma unroll
     for (int m = 0; m < PPL; ++m) {
       float sq = 0.f;
       const int s = lane + 32 * m;
       const int nr = (rn4 >> (8 * m)) & 0xff;
       if (s < p && nr) {
-        float rr = 0.f;
-        for (int q = 0; q < nr; ++q) rr += rs[s + q];
+        const float rr = rrv[m] * rsc;
         sq = rr * rr;
       }
       for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(FULL, sq, o);
@@ -1721,7 +1768,7 @@ __global__ void __launch_bounds__(1024, 1) sweep_wmma_kernel(
       *reinterpret_cast<float2*>(cur + 2 * (size_t)(p0 + s)) = make_float2(w_in[s], cs[s] + (a.x + a.y) * isc);
     }
   }
-  if (valid && lane == 0) partials2[(size_t)(k & 1) * nparts + dsc.tile] = (double)tile_sq;
+  if (valid && lane == 0) partials2[(size_t)(k & 1) * nparts + dsc.tile] = (double)tile_sq * pow2d(2 * tile_e);
 }
 
 // ---------------------------------------------------------------------------
@@ -1894,16 +1941,32 @@ __global__ void __launch_bounds__(1024, 1) sweep_wdf_kernel(
     }
   }
   __syncwarp();
-  df tile_sq = {0.f, 0.f};  // lane 0: the four groups in order
+  df tile_sq = {0.f, 0.f};  // lane 0: the four groups in order, scaled by 2^-2 tile_e
+  int tile_e = 0;
   if (k > 1) {
+    df rrv[PPL];
+    float rmax = 0.f;
+#pragma unroll
+    for (int m = 0; m < PPL; ++m) {
+      const int s = lane + 32 * m;
+      const int nr = (rn4 >> (8 * m)) & 0xff;
+      df rr = {0.f, 0.f};
+      if (s < p && nr) {
+        rr = rs[s];
+        for (int q = 1; q < nr; ++q) rr = df_add(rr, rs[s + q]);
+      }
+      rrv[m] = rr;
+      rmax = fmaxf(rmax, fabsf(rr.h));
+    }
+    tile_e = pow2_exponent(warp_max(rmax));
+    const float rsc = pow2f(-tile_e);
 #pragma unroll
     for (int m = 0; m < PPL; ++m) {
       df sq = {0.f, 0.f};
       const int s = lane + 32 * m;
       const int nr = (rn4 >> (8 * m)) & 0xff;
       if (s < p && nr) {
-        df rr = rs[s];
-        for (int q = 1; q < nr; ++q) rr = df_add(rr, rs[s + q]);
+        const df rr = {rrv[m].h * rsc, rrv[m].l * rsc};
         sq = df_mul(rr, rr);
       }
       for (int o = 16; o > 0; o >>= 1) {
@@ -1989,7 +2052,8 @@ __global__ void __launch_bounds__(1024, 1) sweep_wdf_kernel(
       cur[p0 + s] = make_float4(w_in[s].h, w_in[s].l, o.h, o.l);
     }
   }
-  if (valid && lane == 0) partials2[(size_t)(k & 1) * nparts + dsc.tile] = (double)tile_sq.h + (double)tile_sq.l;
+  if (valid && lane == 0)
+    partials2[(size_t)(k & 1) * nparts + dsc.tile] = ((double)tile_sq.h + (double)tile_sq.l) * pow2d(2 * tile_e);
 }
 
 // c as double-float pairs (once per inner solve of kernel 12)

@@ -49,10 +49,13 @@ def _random_line_admittance(tear, seed):
 @pytest.mark.parametrize("kind,alpha,radius", [("diag", 1.0, 0), ("wob", 0.4, 0), ("sca", 1.0, 2),
                                                ("sca", 1.0, 0), ("line", 1.0, 0), ("alpha", 0.3, 0)])
 def test_admittance_choice_follows_the_oracle(vtm, kind, alpha, radius):
+    # FP64 arithmetic (kernel 1), so that even the very slow diagonal choice
+    # (W = 2g is block Jacobi: about 10,860 sweeps) stops at the oracle's sweep;
+    # the double-float kernel 12 is checked against the same run below
     w = wl.grid2d(24, 24, 8, 6, seed=31)
     A = w.csr()
     tear = O.tear_midpoint(A, w.partition, w.nparts)
-    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc, factor=False)
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc, factor=False, sweep_kernel=1)
     perm = _oracle_port_order(plan, tear)
     if kind == "line":
         W_ref = _random_line_admittance(tear, 7)
@@ -72,6 +75,15 @@ def test_admittance_choice_follows_the_oracle(vtm, kind, alpha, radius):
     if info["sweeps"] == ref.sweeps:
         assert np.abs(xs - ref.x).max() <= 1e-10 * np.abs(ref.x).max()
     assert O.residual_norms(A, xs, w.b).max() <= TOL_CHECK
+    # kernel 12 (2^-44 of rounding per sweep instead of 2^-53): the same
+    # history to 1e-8, the stop within 0.05% of the sweeps (a slowly
+    # converging residual crosses the tolerance a sweep or two apart)
+    plan.set_options(history_len=50, sweep_kernel=12)
+    x12, info12 = plan.solve(torch.from_numpy(w.b).cuda(), tol=1e-10)
+    assert plan.stats()["sweep_kernel"] == 12
+    assert abs(info12["sweeps"] - ref.sweeps) <= max(1, ref.sweeps // 2000)
+    assert np.allclose(plan.history[:k], ref.history[:k, 0], rtol=1e-8, atol=1e-13)
+    assert O.residual_norms(A, x12.cpu().numpy().reshape(w.b.shape), w.b).max() <= TOL_CHECK
 
 
 def test_diagonal_admittance_is_block_jacobi_on_the_gpu(vtm):
