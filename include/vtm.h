@@ -102,8 +102,14 @@ typedef struct {
                         VTM_METHOD_ASYNC (switchable with VTM by vtm_set_opts) */
   int batch;         /* several right-hand sides: 0 (default) one batched iteration over
                         up to 64 columns at a time; 1: one column after the other */
-  int batch_solve;   /* batched FP32 band solves: 0 (default) row window in shared memory;
-                        1: whole column block in shared memory */
+  int batch_solve;   /* batched FP32 band solves: 0 (default) blocked when every half
+                        bandwidth is at most 128, else row window; 1: whole column block
+                        in shared memory; 2: row window in shared memory; 3: blocked --
+                        rows in blocks of 64, each block one product with the inverted
+                        diagonal block of the factor and its coupling to the previous
+                        rows (matrices formed in FP64 at the first FP32 batched solve
+                        after each factorisation, stored in FP32; VTM_EINVAL for a half
+                        bandwidth above 128) */
   int l2_persist;    /* 1: during FP32/16-bit sweeps, mark the reflection matrices persisting
                         in L2 (access-policy window on the plan's stream; the context's
                         persisting carve-out is set and restored around each inner solve;

@@ -353,6 +353,223 @@ __global__ void batch_band_solve_win_kernel(const int32_t* __restrict__ node_off
   cp_async_wait<0>();
 }
 
+// ---------------------------------------------------------------------------
+// Blocked band solves: the rows of a tile in blocks of kBkNB, each block one
+// dense product
+// ---------------------------------------------------------------------------
+//
+// With L = L1 Dl^-1 (L1 unit lower, L1(j+a, j) = Lc[j][a]; Dl = diag(Lc[j][0]))
+// the forward solve L y = v restricted to the block of rows [s, s + NB) is
+//   y_blk = L_bb^-1 (v_blk - L[blk, win] y_win),   win = [s - W, s),
+// W >= bw (only the last bw rows before the block reach it).  With
+//   G_f = [ -L_bb^-1 L[blk, win] | L_bb^-1 ]            (NB x (W + NB))
+// the block is y_blk = G_f [y_win; v_blk]: one product over the W + NB
+// consecutive rows [s - W, s + NB).  Backward, with U = U1 Du^-1,
+//   x_blk = U_bb^-1 (y_blk - U[blk, win'] x_win'),   win' = [s + NB, s + NB + W),
+//   G_b = [ U_bb^-1 | -U_bb^-1 U[blk, win'] ]  over the rows [s, s + NB + W).
+// G_f and G_b are formed once per factorisation in FP64 (substitutions local
+// to each block on the band factors) and kept in FP32; a pass of the solve is
+// then a chain of ceil(n / NB) small GEMMs instead of n dependent row steps.
+
+constexpr int kBkNB = 64;                 // rows per block
+constexpr int kBkRG = 64;                 // right-hand sides per CTA
+constexpr int kBkS = 256;                 // ring rows; needs W + 2 NB <= kBkS
+constexpr int kBkLd = kBkRG + 4;          // floats per ring row
+constexpr int kBkStages = 4;              // G chunks (16 rows of G^T) in flight
+constexpr int kBkThreads = 256;
+constexpr int kBkMaxW = kBkS - 2 * kBkNB;  // widest window (bw <= 128)
+constexpr int kBkLdx = 257;               // doubles per row of the set-up array
+constexpr size_t kBkSmem = (size_t)(kBkS * kBkLd + kBkStages * 16 * kBkNB) * sizeof(float);
+constexpr size_t kBkInvSmem = (size_t)kBkNB * kBkLdx * sizeof(double);
+
+// One CTA per (block, pass).  Thread c takes column c of [-L[blk, win] | I]
+// (forward) or [I | -U[blk, win']] (backward) through the block's own
+// substitution with the pre-divided multipliers; the result times the
+// block's diagonal factor is G, stored k-major (G[kk][i], kk the column) in
+// FP32.  Backward blocks are stored in the order the solve visits them.
+__global__ void __launch_bounds__(kBkThreads) blk_inverse_kernel(
+    const int32_t* __restrict__ node_off, const int32_t* __restrict__ bwv,
+    const int64_t* __restrict__ band_off, const int32_t* __restrict__ Wv,
+    const int64_t* __restrict__ g_off, const int2* __restrict__ blk_list,
+    const double* __restrict__ Lc, const double* __restrict__ Uc, float* __restrict__ Gf,
+    float* __restrict__ Gb) {
+  extern __shared__ double X[];  // X[i * kBkLdx + c]
+  const int2 bk = blk_list[blockIdx.x];
+  const int t = bk.x, k = bk.y;
+  const bool fwd = blockIdx.y == 0;
+  const int n = node_off[t + 1] - node_off[t];
+  const int bw = bwv[t], B = bw + 1, W = Wv[t], K = W + kBkNB;
+  const int nblk = (n + kBkNB - 1) / kBkNB;
+  const int s = k * kBkNB;
+  const int rows = min(kBkNB, n - s);
+  const double* f = (fwd ? Lc : Uc) + band_off[t];
+  const int c = threadIdx.x;
+  if (c < K) {
+    for (int i = 0; i < kBkNB; ++i) {
+      double v = 0.0;
+      if (i < rows) {
+        if (fwd) {
+          if (c >= W) {
+            v = c - W == i ? 1.0 : 0.0;
+          } else {
+            const int w = s - W + c, a = s + i - w;  // -L(s + i, w)
+            if (w >= 0 && a <= bw) v = -f[(size_t)w * B + a] / f[(size_t)w * B];
+          }
+        } else {
+          if (c < kBkNB) {
+            v = c == i ? 1.0 : 0.0;
+          } else {
+            const int w = s + c, b = w - (s + i);  // -U(s + i, w)
+            if (w < n && b <= bw) v = -f[(size_t)w * B + b] / f[(size_t)w * B];
+          }
+        }
+      }
+      X[i * kBkLdx + c] = v;
+    }
+    if (fwd) {
+      for (int j = 0; j < rows; ++j) {
+        const double e = X[j * kBkLdx + c];
+        if (e == 0.0) continue;
+        const double* col = f + (size_t)(s + j) * B;
+        const int m = min(bw, rows - 1 - j);
+        for (int a = 1; a <= m; ++a) X[(j + a) * kBkLdx + c] -= col[a] * e;
+      }
+    } else {
+      for (int j = rows - 1; j >= 0; --j) {
+        const double e = X[j * kBkLdx + c];
+        if (e == 0.0) continue;
+        const double* col = f + (size_t)(s + j) * B;
+        const int m = min(bw, j);
+        for (int b = 1; b <= m; ++b) X[(j - b) * kBkLdx + c] -= col[b] * e;
+      }
+    }
+  }
+  __syncthreads();
+  const int slot = fwd ? k : nblk - 1 - k;
+  float* G = (fwd ? Gf : Gb) + g_off[t] + (size_t)slot * K * kBkNB;
+  for (int e = threadIdx.x; e < K * kBkNB; e += blockDim.x) {
+    const int kk = e / kBkNB, i = e % kBkNB;
+    G[e] = i < rows ? (float)(f[(size_t)(s + i) * B] * X[i * kBkLdx + kk]) : 0.f;
+  }
+}
+
+__device__ __forceinline__ void cp_async16_cg(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+// 4-byte copy, zero-filled when !ok (the source is then not read)
+__device__ __forceinline__ void cp_async4_zfill(void* smem, const void* gmem, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(smem)), "l"(gmem),
+               "r"(ok ? 4 : 0)
+               : "memory");
+}
+
+// One CTA per (tile, 64 right-hand sides): both passes.  Rows of the tile's
+// column block live in a ring of kBkS rows (row g in slot g mod kBkS; rows
+// outside [0, n) read as zero); the G^T of each block streams through
+// kBkStages chunks of 16 rows by cp.async, and the input rows of the next
+// block are fetched while the current one is multiplied.  Thread (ty, tx)
+// accumulates rows 4 ty .. 4 ty + 3, columns 4 tx .. 4 tx + 3 of the block.
+// Row-block moves between V and the ring map lane l of warp w, step m, to
+// row 8 (task & 7) + (l & 7), column 4 (task >> 3) + (l >> 3), task = w + 8 m
+// (conflict-free ring access; the same thread writes y in the forward pass
+// and reads it back in the backward pass).
+__global__ void __launch_bounds__(kBkThreads, 2) batch_band_solve_blk_kernel(
+    const int32_t* __restrict__ node_off, const int32_t* __restrict__ Wv,
+    const int64_t* __restrict__ g_off, const int32_t* __restrict__ order,
+    const float* __restrict__ Gf, const float* __restrict__ Gb, float* __restrict__ V, int R,
+    int64_t ntot) {
+  extern __shared__ __align__(16) float bsm[];
+  float* ring = bsm;
+  float* gst = bsm + kBkS * kBkLd;
+  const int ngroups = (R + kBkRG - 1) / kBkRG;
+  const int t = order[blockIdx.x / ngroups];
+  const int r0 = (blockIdx.x % ngroups) * kBkRG;
+  const int rg = min(kBkRG, R - r0);
+  const int base = node_off[t];
+  const int n = node_off[t + 1] - base;
+  const int W = Wv[t], KC = (W + kBkNB) / 16;
+  const int nblk = (n + kBkNB - 1) / kBkNB;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int lane = tid & 31, warp = tid >> 5;
+  float* Vt = V + (int64_t)r0 * ntot + base;
+  const int Q = nblk * KC;
+  for (int pass = 0; pass < 2; ++pass) {
+    const float* G = (pass == 0 ? Gf : Gb) + g_off[t];
+    for (int i = tid; i < kBkS * kBkLd; i += kBkThreads) ring[i] = 0.f;
+    __syncthreads();
+    auto blk_start = [&](int b) { return (pass == 0 ? b : nblk - 1 - b) * kBkNB; };
+    auto load_v = [&](int b) {
+      if (b >= nblk) return;
+      const int s = blk_start(b);
+#pragma unroll 4
+      for (int m = 0; m < 16; ++m) {
+        const int task = warp + 8 * m;
+        const int g = s + 8 * (task & 7) + (lane & 7);
+        const int c = 4 * (task >> 3) + (lane >> 3);
+        const bool ok = g < n && c < rg;
+        cp_async4_zfill(&ring[(g & (kBkS - 1)) * kBkLd + c], ok ? Vt + (int64_t)c * ntot + g : Vt, ok);
+      }
+    };
+    auto load_chunk = [&](int q) {
+      if (q < Q)
+        cp_async16_cg(&gst[(q % kBkStages) * 16 * kBkNB + tid * 4], G + (size_t)q * 16 * kBkNB + tid * 4);
+    };
+    load_v(0);
+#pragma unroll
+    for (int q = 0; q < kBkStages - 1; ++q) {
+      load_chunk(q);
+      cp_async_commit();
+    }
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int q = 0; q < Q; ++q) {
+      cp_async_wait<kBkStages - 2>();
+      __syncthreads();
+      const int b = q / KC, kc = q - b * KC;
+      if (kc == 0) load_v(b + 1);
+      load_chunk(q + kBkStages - 1);
+      cp_async_commit();
+      const int s = blk_start(b);
+      const int row0 = (pass == 0 ? s - W : s) + 16 * kc;
+      const float* gq = gst + (q % kBkStages) * 16 * kBkNB + 4 * ty;
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) {
+        const float4 a = *reinterpret_cast<const float4*>(gq + kk * kBkNB);
+        const float4 x =
+            *reinterpret_cast<const float4*>(&ring[((row0 + kk) & (kBkS - 1)) * kBkLd + 4 * tx]);
+        const float av[4] = {a.x, a.y, a.z, a.w}, xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], xv[j], acc[i][j]);
+      }
+      if (kc == KC - 1) {
+        __syncthreads();  // every read of the block's input rows is done
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          *reinterpret_cast<float4*>(&ring[((s + 4 * ty + i) & (kBkS - 1)) * kBkLd + 4 * tx]) =
+              make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int m = 0; m < 16; ++m) {
+          const int task = warp + 8 * m;
+          const int g = s + 8 * (task & 7) + (lane & 7);
+          const int c = 4 * (task >> 3) + (lane >> 3);
+          if (g < n && c < rg) Vt[(int64_t)c * ntot + g] = ring[(g & (kBkS - 1)) * kBkLd + c];
+        }
+      }
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+  }
+}
+
 // c[s][r] = (2 W beta_s / d_s) x0[pos(s)][r]
 template <class FT, class WT>
 __global__ void batch_const_kernel(const int32_t* __restrict__ port_pos, const double* __restrict__ bout,
@@ -1311,10 +1528,69 @@ static vtm_status batch_band_solve_win(vtm_plan_s* P, float* V, int R, const flo
   return VTM_OK;
 }
 
+// The blocked solve's tables and G_f / G_b, formed from the FP64 band
+// factors (once per factorisation).
+static vtm_status blk_prepare(vtm_plan_s* P) {
+  if (P->bk_ready) return VTM_OK;
+  cudaStream_t s = P->stream;
+  std::vector<int32_t> W(P->nparts), order(P->nparts);
+  std::vector<int64_t> goff(P->nparts), cost(P->nparts);
+  std::vector<int2> blks;
+  int64_t o = 0;
+  for (int32_t t = 0; t < P->nparts; ++t) {
+    const int n = P->node_off[t + 1] - P->node_off[t];
+    const int nblk = (n + kBkNB - 1) / kBkNB;
+    W[t] = (P->bw[t] + 15) / 16 * 16;
+    goff[t] = o;
+    cost[t] = (int64_t)nblk * (W[t] + kBkNB);
+    for (int k = 0; k < nblk; ++k) blks.push_back(make_int2(t, k));
+    o += (int64_t)nblk * (W[t] + kBkNB) * kBkNB;
+    order[t] = t;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+  VTM_TRY(upload(P->d_bk_W, W, s));
+  VTM_TRY(upload(P->d_bk_goff, goff, s));
+  VTM_TRY(upload(P->d_bk_order, order, s));
+  VTM_TRY(upload(P->d_bk_blk, blks, s));
+  VTM_TRY(dev_alloc(P->d_bk_Gf, (size_t)std::max<int64_t>(o, 16) * sizeof(float)));
+  VTM_TRY(dev_alloc(P->d_bk_Gb, (size_t)std::max<int64_t>(o, 16) * sizeof(float)));
+  if (!blks.empty()) {
+    VTM_CUDA_TRY(cudaFuncSetAttribute(blk_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kBkInvSmem));
+    blk_inverse_kernel<<<dim3((unsigned)blks.size(), 2), kBkThreads, kBkInvSmem, s>>>(
+        P->tabs.node_off.as<int32_t>(), P->tabs.bw.as<int32_t>(), P->tabs.band_off.as<int64_t>(),
+        P->d_bk_W.as<int32_t>(), P->d_bk_goff.as<int64_t>(), P->d_bk_blk.as<int2>(),
+        P->d_Lc.as<double>(), P->d_Uc.as<double>(), P->d_bk_Gf.as<float>(), P->d_bk_Gb.as<float>());
+    P->launch_count++;
+    VTM_CUDA_TRY(cudaGetLastError());
+  }
+  P->bk_ready = true;
+  return VTM_OK;
+}
+
+static vtm_status batch_band_solve_blk(vtm_plan_s* P, float* V, int R) {
+  if (P->max_bw > kBkMaxW) {
+    set_detail("batched solve: the blocked band solve takes half bandwidths up to 128");
+    return VTM_EINVAL;
+  }
+  VTM_TRY(blk_prepare(P));
+  const int ngroups = (R + kBkRG - 1) / kBkRG;
+  VTM_CUDA_TRY(cudaFuncSetAttribute(batch_band_solve_blk_kernel,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBkSmem));
+  batch_band_solve_blk_kernel<<<P->nparts * ngroups, kBkThreads, kBkSmem, P->stream>>>(
+      P->tabs.node_off.as<int32_t>(), P->d_bk_W.as<int32_t>(), P->d_bk_goff.as<int64_t>(),
+      P->d_bk_order.as<int32_t>(), P->d_bk_Gf.as<float>(), P->d_bk_Gb.as<float>(), V, R, P->n);
+  P->launch_count++;
+  VTM_CUDA_TRY(cudaGetLastError());
+  return VTM_OK;
+}
+
 template <class FT>
 static vtm_status batch_band_solve(vtm_plan_s* P, FT* V, int R, const FT* Lc, const FT* Uc) {
   if constexpr (sizeof(FT) == 4) {
-    if (P->opts.batch_solve != 1) return batch_band_solve_win(P, V, R, Lc, Uc);
+    const int mode = P->opts.batch_solve;
+    if (mode == 3 || (mode == 0 && P->max_bw <= kBkMaxW)) return batch_band_solve_blk(P, V, R);
+    if (mode != 1) return batch_band_solve_win(P, V, R, Lc, Uc);
   }
   constexpr int RG = 8;
   constexpr int D = 8;

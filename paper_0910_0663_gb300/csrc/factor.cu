@@ -694,6 +694,10 @@ extern "C" vtm_status vtm_factor(vtm_plan_t P) {
   // the tiled copy of the tcgen05 batched sweep follows the factors
   dev_free(P->d_Ttc);
   P->tc_nitems = 0;
+  // so do the blocked band-solve matrices
+  dev_free(P->d_bk_Gf);
+  dev_free(P->d_bk_Gb);
+  P->bk_ready = false;
   // the band arrays hold K_P before the factorisation: re-assemble if a
   // previous factorisation overwrote them
   static_assert(sizeof(double) == 8, "");

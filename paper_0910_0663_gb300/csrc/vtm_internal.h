@@ -283,6 +283,11 @@ struct vtm_plan_s {
   // chunks), their offsets into the tiled BF16 copy of T_P, longest first
   int tc_nitems = 0;
   vtm::DevBuf d_tc_items, d_tc_off, d_tc_order, d_Ttc;
+  // blocked batched band solves: per tile the window width W, the offset of
+  // its G blocks, tiles longest first, (tile, block) list, G_f and G_b
+  // (built at the first FP32 batched solve after each factorisation)
+  bool bk_ready = false;
+  vtm::DevBuf d_bk_W, d_bk_goff, d_bk_order, d_bk_blk, d_bk_Gf, d_bk_Gb;
 
   // adjoint of an unsymmetric system
   vtm_plan_s* transposed = nullptr;

@@ -160,3 +160,46 @@ def test_tcgen05_batched_sweep_on_the_full_thermal_grid(vtm, nrhs):
         plan.close()
     k = int(np.count_nonzero((hist[5] > 0) & (hist[1] > 0)))
     assert k >= 3 and np.allclose(hist[5][:k], hist[1][:k], rtol=2e-2, atol=0)
+
+
+@pytest.mark.parametrize("nrhs", [5, 64, 70])
+def test_batched_band_solve_variants_agree(vtm, nrhs):
+    # the FP32 band solves of the batched iteration -- whole column block in
+    # shared memory (1), row window (2), blocked with the diagonal blocks of
+    # the factors inverted ahead (3) -- are the same K_P^-1 up to FP32
+    # rounding: each result is FP64-verified and the first inner solves follow
+    # one another's residual history (70 columns: a call of 64 and one of 6)
+    w = _thermal_small(nrhs, seed=6)
+    A = w.csr()
+    b = torch.from_numpy(w.b).cuda()
+    hist = {}
+    for mode in (1, 2, 3):
+        plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc, precision="fp32",
+                        batch_solve=mode)
+        plan.set_options(history_len=20)
+        x, info = plan.solve(b, tol=1e-10)
+        assert O.residual_norms(A, x.cpu().numpy(), w.b).max() <= 1e-10
+        hist[mode] = plan.history
+        plan.close()
+    k = int(np.count_nonzero((hist[1] > 1e-5) & (hist[3] > 1e-5)))
+    assert k >= 5
+    for mode in (2, 3):
+        assert np.allclose(hist[mode][:k], hist[1][:k], rtol=1e-3, atol=0)
+
+
+def test_blocked_band_solve_needs_a_band_of_at_most_128(vtm):
+    # 280 x 280 plane in four 140 x 140 quadrants: half bandwidths above 128,
+    # so the blocked solve refuses (VTM_EINVAL) and the default takes the row
+    # window
+    w = wl.thermal3d(1, 280, 280, 4, nrhs=3, seed=7, min_box=1, max_box=280 * 280)
+    iy, ix = np.divmod(np.arange(w.n), 280)
+    part = ((iy >= 140).astype(np.int32) * 2 + (ix >= 140)).astype(np.int32)
+    b = torch.from_numpy(w.b).cuda()
+    plan = vtm.Plan(w.indptr, w.indices, w.data, part, 4, Zc=w.Zc, precision="fp32")
+    assert plan.stats()["max_band"] > 128
+    x, _ = plan.solve(b, tol=1e-10)
+    assert O.residual_norms(w.csr(), x.cpu().numpy(), w.b).max() <= 1e-10
+    plan.set_options(batch_solve=3)
+    with pytest.raises(vtm.VTMError, match="half bandwidths up to 128"):
+        plan.solve(b, tol=1e-10)
+    plan.close()
