@@ -56,50 +56,63 @@ __global__ void batch_gather_kernel(const int32_t* __restrict__ perm, const doub
   }
 }
 
+// dst[r][node] (+)= src[r][iperm[node]]: written along the caller's order,
+// read through the inverse permutation (one column at a time stays in L2)
 template <class FT>
-__global__ void batch_scatter_kernel(const int32_t* __restrict__ perm, const FT* __restrict__ src,
+__global__ void batch_scatter_kernel(const int32_t* __restrict__ iperm, const FT* __restrict__ src,
                                      double* __restrict__ dst, int64_t n, int R, int accumulate) {
   const int64_t total = n * R;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = i / n, pos = i % n;
-    double* d = dst + r * n + perm[pos];
-    if (accumulate) *d += (double)src[i];
-    else *d = (double)src[i];
+    const int64_t r = i / n, node = i % n;
+    const double v = (double)src[r * n + iperm[node]];
+    if (accumulate) dst[i] += v;
+    else dst[i] = v;
   }
 }
 
 // r = b - A x for R columns at once (column-major), with ||r_c||^2 and
-// ||b_c||^2 per column: block (bx, by) covers rows bx, bx + gx, ... of the
-// columns 8 by .. 8 by + 7; per-block partial sums, then the last block of
-// each column group adds them in a fixed order.  counters[by] start at 0 and
-// are left at 0; out[2 c] = ||r_c||^2, out[2 c + 1] = ||b_c||^2.
+// ||b_c||^2 per column.  Block b covers column group by = b % gy (columns
+// 8 by .. 8 by + 7) and rows bx, bx + gx, ... (units of 256 rows), bx = b /
+// gy: the groups of one row range run side by side, so each row of A comes
+// from DRAM once.  Per row, the products of one nonzero with the 8 columns
+// are independent loads.  Per-block partial sums, then the last block of
+// each group adds them in a fixed order.  counters[by] start at 0 and are
+// left at 0; out[2 c] = ||r_c||^2, out[2 c + 1] = ||b_c||^2.
 __global__ void __launch_bounds__(256) batch_residual_norms_kernel(
     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
     const double* __restrict__ val, const double* __restrict__ x, const double* __restrict__ b,
-    double* __restrict__ r, int64_t n, int R, double* __restrict__ partials,
+    double* __restrict__ r, int64_t n, int R, int gx, int gy, double* __restrict__ partials,
     unsigned* __restrict__ counters, double* __restrict__ out) {
   constexpr int CG = 8;
   __shared__ double red[2 * CG][8];
   __shared__ bool last;
-  const int c0 = blockIdx.y * CG;
+  const int by = blockIdx.x % gy, bx = blockIdx.x / gy;
+  const int c0 = by * CG;
   const int nc = min(CG, R - c0);
+  const double* xg = x + (int64_t)c0 * n;
+  const double* bg = b + (int64_t)c0 * n;
   double rr[CG], bb[CG];
 #pragma unroll
   for (int c = 0; c < CG; ++c) rr[c] = bb[c] = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = bx * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gx * blockDim.x) {
     const int64_t q0 = rowptr[i], q1 = rowptr[i + 1];
+    double acc[CG], bi[CG];
+#pragma unroll
+    for (int c = 0; c < CG; ++c) acc[c] = bi[c] = c < nc ? bg[(int64_t)c * n + i] : 0.0;
+    for (int64_t q = q0; q < q1; ++q) {
+      const int64_t j = col[q];
+      const double v = val[q];
+#pragma unroll
+      for (int c = 0; c < CG; ++c)
+        if (c < nc) acc[c] -= v * xg[(int64_t)c * n + j];
+    }
 #pragma unroll
     for (int c = 0; c < CG; ++c) {
       if (c < nc) {
-        const double* xc = x + (int64_t)(c0 + c) * n;
-        const double bi = b[(int64_t)(c0 + c) * n + i];
-        double acc = bi;
-        for (int64_t q = q0; q < q1; ++q) acc -= val[q] * xc[col[q]];
-        if (r) r[(int64_t)(c0 + c) * n + i] = acc;
-        rr[c] += acc * acc;
-        bb[c] += bi * bi;
+        if (r) r[(int64_t)(c0 + c) * n + i] = acc[c];
+        rr[c] += acc[c] * acc[c];
+        bb[c] += bi[c] * bi[c];
       }
     }
   }
@@ -117,7 +130,7 @@ __global__ void __launch_bounds__(256) batch_residual_norms_kernel(
     }
   }
   __syncthreads();
-  const size_t pb = ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 2 * CG;
+  const size_t pb = ((size_t)by * gx + bx) * 2 * CG;
   if (threadIdx.x < 2 * CG) {
     double t = 0.0;
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[threadIdx.x][k];
@@ -126,19 +139,18 @@ __global__ void __launch_bounds__(256) batch_residual_norms_kernel(
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    last = atomicAdd(&counters[blockIdx.y], 1u) == gridDim.x - 1;
+    last = atomicAdd(&counters[by], 1u) == (unsigned)gx - 1;
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
   if (threadIdx.x < 2 * CG) {
     double t = 0.0;
-    for (unsigned bx = 0; bx < gridDim.x; ++bx)
-      t += partials[((size_t)blockIdx.y * gridDim.x + bx) * 2 * CG + threadIdx.x];
+    for (int k = 0; k < gx; ++k) t += partials[((size_t)by * gx + k) * 2 * CG + threadIdx.x];
     const int c = threadIdx.x % CG;
     if (c < nc) out[2 * (c0 + c) + (threadIdx.x >= CG ? 1 : 0)] = t;
   }
-  if (threadIdx.x == 0) counters[blockIdx.y] = 0u;
+  if (threadIdx.x == 0) counters[by] = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -533,18 +545,24 @@ __global__ void __launch_bounds__(kBkThreads, 2) batch_band_solve_blk_kernel(
       load_chunk(q + kBkStages - 1);
       cp_async_commit();
       const int s = blk_start(b);
-      const int row0 = (pass == 0 ? s - W : s) + 16 * kc;
-      const float* gq = gst + (q % kBkStages) * 16 * kBkNB + 4 * ty;
+      const int row0 = (pass == 0 ? s - W : s) + 16 * kc;  // a multiple of 16: no wrap inside
+      // the inverted diagonal block is triangular: a warp (rows 8 warp .. 8 warp
+      // + 7) skips the chunks of it that are zero in all its rows
+      const int j0 = pass == 0 ? 16 * kc - W : 16 * kc;  // first diagonal-block column
+      const bool skip = pass == 0 ? (j0 >= 0 && j0 > 8 * warp + 7) : (j0 < kBkNB && j0 + 15 < 8 * warp);
+      if (!skip) {
+        const float* gq = gst + (q % kBkStages) * 16 * kBkNB + 4 * ty;
+        const float* xq = ring + (row0 & (kBkS - 1)) * kBkLd + 4 * tx;
 #pragma unroll
-      for (int kk = 0; kk < 16; ++kk) {
-        const float4 a = *reinterpret_cast<const float4*>(gq + kk * kBkNB);
-        const float4 x =
-            *reinterpret_cast<const float4*>(&ring[((row0 + kk) & (kBkS - 1)) * kBkLd + 4 * tx]);
-        const float av[4] = {a.x, a.y, a.z, a.w}, xv[4] = {x.x, x.y, x.z, x.w};
+        for (int kk = 0; kk < 16; ++kk) {
+          const float4 a = *reinterpret_cast<const float4*>(gq + kk * kBkNB);
+          const float4 x = *reinterpret_cast<const float4*>(xq + kk * kBkLd);
+          const float av[4] = {a.x, a.y, a.z, a.w}, xv[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+          for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], xv[j], acc[i][j]);
+            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], xv[j], acc[i][j]);
+        }
       }
       if (kc == KC - 1) {
         __syncthreads();  // every read of the block's input rows is done
@@ -570,35 +588,54 @@ __global__ void __launch_bounds__(kBkThreads, 2) batch_band_solve_blk_kernel(
   }
 }
 
+// Port-wise moves between [port][R] rows and the column-major [R][n] vectors
+// go through a shared-memory tile of 32 ports x R: the [port][R] side is read
+// or written along R, the vector side along the ports (whose nodes lie close
+// together in the band order).
+
 // c[s][r] = (2 W beta_s / d_s) x0[pos(s)][r]
 template <class FT, class WT>
-__global__ void batch_const_kernel(const int32_t* __restrict__ port_pos, const double* __restrict__ bout,
-                                   const FT* __restrict__ x0, WT* __restrict__ c, int64_t nports, int R,
-                                   int64_t n) {
-  const int64_t total = nports * R;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t s = i / R;
-    const int r = (int)(i % R);
-    c[i] = (WT)(bout[s] * (double)x0[(int64_t)r * n + port_pos[s]]);
+__global__ void __launch_bounds__(256) batch_const_kernel(const int32_t* __restrict__ port_pos,
+                                                          const double* __restrict__ bout,
+                                                          const FT* __restrict__ x0, WT* __restrict__ c,
+                                                          int64_t nports, int R, int64_t n) {
+  __shared__ WT tile[32][65];
+  const int64_t s0 = (int64_t)blockIdx.x * 32;
+  const int ns = (int)(nports - s0 < 32 ? nports - s0 : 32);
+  const int sl = threadIdx.x & 31;
+  if (sl < ns) {
+    const int64_t pos = port_pos[s0 + sl];
+    const double bo = bout[s0 + sl];
+    for (int r = threadIdx.x >> 5; r < R; r += 8) tile[sl][r] = (WT)(bo * (double)x0[(int64_t)r * n + pos]);
   }
+  __syncthreads();
+  for (int e = threadIdx.x; e < ns * R; e += blockDim.x) c[s0 * R + e] = tile[e / R][e % R];
 }
 
 // V[pos(node)][r] += sum over the node's ports of beta_s w_in[s][r]
 template <class FT, class WT>
-__global__ void batch_inject_kernel(const int32_t* __restrict__ port_pos, const uint8_t* __restrict__ run,
-                                    const double* __restrict__ beta, const WT* __restrict__ st,
-                                    FT* __restrict__ V, int64_t nports, int R, int64_t n) {
-  const int64_t total = nports * R;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t s = i / R;
-    const int r = (int)(i % R);
+__global__ void __launch_bounds__(256) batch_inject_kernel(const int32_t* __restrict__ port_pos,
+                                                           const uint8_t* __restrict__ run,
+                                                           const double* __restrict__ beta,
+                                                           const WT* __restrict__ st, FT* __restrict__ V,
+                                                           int64_t nports, int R, int64_t n) {
+  __shared__ double tile[32][65];
+  const int64_t s0 = (int64_t)blockIdx.x * 32;
+  const int ns = (int)(nports - s0 < 32 ? nports - s0 : 32);
+  for (int e = threadIdx.x; e < ns * R; e += blockDim.x) {
+    const int sl = e / R, r = e % R;
+    const int64_t s = s0 + sl;
     const int nr = run[s];
     if (!nr) continue;
     double acc = 0.0;
     for (int q = 0; q < nr; ++q) acc += beta[s + q] * (double)st[(s + q) * 2 * R + r];
-    V[(int64_t)r * n + port_pos[s]] += (FT)acc;
+    tile[sl][r] = acc;
+  }
+  __syncthreads();
+  const int sl = threadIdx.x & 31;
+  if (sl < ns && run[s0 + sl]) {
+    const int64_t pos = port_pos[s0 + sl];
+    for (int r = threadIdx.x >> 5; r < R; r += 8) V[(int64_t)r * n + pos] += (FT)tile[sl][r];
   }
 }
 
@@ -1625,9 +1662,9 @@ static vtm_status batch_norms(vtm_plan_s* P, const double* x, const double* b, d
     VTM_CUDA_TRY(cudaMemsetAsync(counters, 0, 64 * sizeof(double), P->stream));
     P->bres_init = true;
   }
-  batch_residual_norms_kernel<<<dim3(gx, gy), 256, 0, P->stream>>>(
+  batch_residual_norms_kernel<<<gx * gy, 256, 0, P->stream>>>(
       P->d_rowptr.as<int64_t>(), P->d_colidx.as<int32_t>(), P->d_vals.as<double>(), x, b, r, P->n, R,
-      partials, counters, out);
+      gx, gy, partials, counters, out);
   P->launch_count++;
   VTM_CUDA_TRY(cudaGetLastError());
   std::vector<double> h(2 * R);
@@ -1675,6 +1712,7 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
     VTM_TRY(upload(P->d_item_order, order, s));
   }
   const int nitems = (int)P->item_tile.size();
+  if (!P->d_iperm.p) VTM_TRY(upload(P->d_iperm, P->iperm, s));
   // tcgen05 work items and the tiled BF16 copy of T_P (BF16 plans; built at
   // the first batched solve after each factorisation)
   if (prec == VTM_PREC_BF16 && P->tc_nitems == 0) {
@@ -1748,7 +1786,8 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
   int sweeps_left = P->opts.max_sweeps;
   vtm_status result = VTM_ENOCONV;
   bool stalled = false;
-  const int g1 = grid_n(n * R), g2 = grid_n(npt * R);
+  // const / inject: one block per 32 ports
+  const int g1 = grid_n(n * R), g2 = (int)std::max<int64_t>(1, (npt + 31) / 32);
   for (int outer = 0; outer < max_outer; ++outer) {
     const double* rhs = outer == 0 ? d_b : r;
     if (f32_solves) {
@@ -1993,9 +2032,9 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
       if (outer == 0) info->first_sweep_converged = 1;
     }
     if (f32_solves && npt > 0)
-      batch_scatter_kernel<float><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), V32, xacc, n, R, outer > 0);
+      batch_scatter_kernel<float><<<g1, 256, 0, s>>>(P->d_iperm.as<int32_t>(), V32, xacc, n, R, outer > 0);
     else
-      batch_scatter_kernel<double><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), V, xacc, n, R, outer > 0);
+      batch_scatter_kernel<double><<<g1, 256, 0, s>>>(P->d_iperm.as<int32_t>(), V, xacc, n, R, outer > 0);
     P->launch_count++;
     VTM_CUDA_TRY(cudaGetLastError());
     info->outer_steps = outer + 1;

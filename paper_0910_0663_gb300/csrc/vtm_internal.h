@@ -206,6 +206,7 @@ struct vtm_plan_s {
   vtm::TileTables tabs;
   vtm::DevBuf d_rowptr, d_colidx, d_vals;  // A for the FP64 residual
   vtm::DevBuf d_perm;                      // int32[n]
+  vtm::DevBuf d_iperm;                     // int32[n] (batched solves)
   vtm::DevBuf d_Lc, d_Uc;                  // band factors (doubles)
   vtm::DevBuf d_Lc32, d_Uc32, d_v32;       // FP32 factor copies and work vector (inner solves)
   vtm::DevBuf d_port_loc, d_port_pos, d_twin, d_beta, d_run, d_tdesc;  // d_beta: beta d
