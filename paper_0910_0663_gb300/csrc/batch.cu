@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "df.cuh"
 #include "ptx.h"
 #include "vtm_internal.h"
 
@@ -151,6 +152,195 @@ __global__ void __launch_bounds__(256) batch_residual_norms_kernel(
     if (c < nc) out[2 * (c0 + c) + (threadIdx.x >= CG ? 1 : 0)] = t;
   }
   if (threadIdx.x == 0) counters[by] = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// double-float residuals of the low-precision batched solves
+// ---------------------------------------------------------------------------
+//
+// GB300's FP64 pipe is narrow: b - A x in FP64 for 64 columns costs about
+// seven FP64 FMAs per nonzero and column.  The low-precision refinement
+// only needs the residual to about 1e-14 of ||b|| (it is rounded to FP32 as
+// the next right-hand side, and its norm decides convergence at 1e-10), so
+// it runs in double-float arithmetic on the FP32 pipes instead: A's values
+// split once into (h, l) pairs, each column of b and of the iterate scaled by
+// 2^-f_c (f_c = the exponent of max |b_c|, an exact scale that keeps every
+// double-float within FP32's exponent range) and split by their bits.
+
+// emax[c] = max over the column of the biased exponent of b (emax zeroed)
+__global__ void batch_colexp_kernel(const double* __restrict__ b, int64_t n, int R, int* __restrict__ emax) {
+  const int c = blockIdx.y;
+  int m = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, (int)((__double_as_longlong(b[(int64_t)c * n + i]) >> 52) & 0x7ff));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&emax[c], m);
+}
+
+// dst = src 2^-f[column] as double-floats ([R][n]; f = nullptr: no scale)
+__global__ void batch_split_kernel(const double* __restrict__ src, const int* __restrict__ f,
+                                   float2* __restrict__ dst, int64_t n, int R) {
+  const int64_t total = n * R;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = df_from_double(src[i], f ? f[i / n] : 0);
+}
+
+// r' = b' - A x' per column (all three scaled by 2^-f_c; x' = nullptr: x = 0),
+// with ||r'_c||^2 and ||b'_c||^2: block b covers column group by = b % gy
+// (CG columns, in pairs on the paired FP32 instructions) and rows bx, bx +
+// gx, ... (units of 256), bx = b / gy.  The products are double-float (Dot2
+// accumulation, seeded with b'); the iterate's values are loaded one nonzero
+// ahead and the column indices two ahead.  Squares are summed in FP32 per
+// thread and per warp, then the warp partials in FP64, added in a fixed order
+// by the last block of each group.  counters[by] start at 0 and are left at
+// 0; out[2 c] = ||r'_c||^2, out[2 c + 1] = ||b'_c||^2.
+template <int CG, int MINB>
+__global__ void __launch_bounds__(256, MINB) batch_residual_df_kernel(
+    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+    const float2* __restrict__ vdf, const float2* __restrict__ xdf, const float2* __restrict__ bdf,
+    float2* __restrict__ rdf, int64_t n, int R, int gx, int gy, double* __restrict__ partials,
+    unsigned* __restrict__ counters, double* __restrict__ out) {
+  constexpr int NP = CG / 2;
+  __shared__ double red[2 * CG][8];
+  __shared__ bool last;
+  const int by = blockIdx.x % gy, bx = blockIdx.x / gy;
+  const int c0 = by * CG;
+  const int nc = min(CG, R - c0);
+  const float2* xg = xdf ? xdf + (int64_t)c0 * n : nullptr;
+  float rr[CG], bb[CG];
+#pragma unroll
+  for (int c = 0; c < CG; ++c) rr[c] = bb[c] = 0.f;
+  for (int64_t i = bx * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gx * blockDim.x) {
+    dacc2 acc[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const float2 b0 = 2 * p < nc ? bdf[(int64_t)(c0 + 2 * p) * n + i] : make_float2(0.f, 0.f);
+      const float2 b1 = 2 * p + 1 < nc ? bdf[(int64_t)(c0 + 2 * p + 1) * n + i] : make_float2(0.f, 0.f);
+      acc[p].S = make_float2(b0.x, b1.x);
+      acc[p].E = make_float2(b0.y, b1.y);
+      bb[2 * p] += b0.x * b0.x;
+      bb[2 * p + 1] += b1.x * b1.x;
+    }
+    if (xg) {
+      const int64_t q0 = rowptr[i], q1 = rowptr[i + 1];
+      auto ldx = [&](float2 (&xv)[CG], int64_t j) {
+#pragma unroll
+        for (int c = 0; c < CG; ++c) xv[c] = c < nc ? xg[(int64_t)c * n + j] : make_float2(0.f, 0.f);
+      };
+      float2 xv[CG], a = make_float2(0.f, 0.f), an = make_float2(0.f, 0.f);
+      int64_t jn = 0;
+      if (q0 < q1) {
+        a = vdf[q0];
+        ldx(xv, col[q0]);
+      }
+      if (q0 + 1 < q1) {
+        jn = col[q0 + 1];
+        an = vdf[q0 + 1];
+      }
+      for (int64_t q = q0; q < q1; ++q) {
+        float2 xn[CG];
+        const bool more = q + 1 < q1;
+        if (more) ldx(xn, jn);
+        int64_t jnn = 0;
+        float2 ann = make_float2(0.f, 0.f);
+        if (q + 2 < q1) {
+          jnn = col[q + 2];
+          ann = vdf[q + 2];
+        }
+        const float2 ah = make_float2(-a.x, -a.x), al = make_float2(-a.y, -a.y);
+#pragma unroll
+        for (int p = 0; p < NP; ++p)
+          dacc2_fma(acc[p], ah, al, make_float2(xv[2 * p].x, xv[2 * p + 1].x),
+                    make_float2(-xv[2 * p].x, -xv[2 * p + 1].x), make_float2(xv[2 * p].y, xv[2 * p + 1].y));
+        if (more) {
+#pragma unroll
+          for (int c = 0; c < CG; ++c) xv[c] = xn[c];
+          a = an;
+        }
+        jn = jnn;
+        an = ann;
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = 2 * p + h;
+        if (c < nc) {
+          const df v = dacc_value(h ? dacc2_hi(acc[p]) : dacc2_lo(acc[p]));
+          rdf[(int64_t)(c0 + c) * n + i] = make_float2(v.h, v.l);
+          rr[c] += v.h * v.h;
+        }
+      }
+    }
+  }
+  // warp sums in FP32 (GB300's FP64 pipe would make a 64-bit shuffle tree
+  // the slowest part of the kernel), FP64 from the warp partials on
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int c = 0; c < CG; ++c) {
+    float a = rr[c], e = bb[c];
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      e += __shfl_down_sync(0xffffffffu, e, o);
+    }
+    if (l == 0) {
+      red[c][w] = a;
+      red[CG + c][w] = e;
+    }
+  }
+  __syncthreads();
+  const size_t pb = ((size_t)by * gx + bx) * 2 * CG;
+  if (threadIdx.x < 2 * CG) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[threadIdx.x][k];
+    partials[pb + threadIdx.x] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&counters[by], 1u) == (unsigned)gx - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x < 2 * CG) {
+    double t = 0.0;
+    for (int k = 0; k < gx; ++k) t += partials[((size_t)by * gx + k) * 2 * CG + threadIdx.x];
+    const int c = threadIdx.x % CG;
+    if (c < nc) out[2 * (c0 + c) + (threadIdx.x >= CG ? 1 : 0)] = t;
+  }
+  if (threadIdx.x == 0) counters[by] = 0u;
+}
+
+// V'[r][pos] = r'[r][perm[pos]] rounded to FP32
+__global__ void batch_gather_df_kernel(const int32_t* __restrict__ perm, const float2* __restrict__ src,
+                                       float* __restrict__ dst, int64_t n, int R) {
+  const int64_t total = n * R;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / n, pos = i % n;
+    const float2 v = src[r * n + perm[pos]];
+    dst[i] = v.x + v.y;
+  }
+}
+
+// x[r][node] (+)= 2^f_r d[r][iperm[node]] (the correction of the scaled
+// system, exact in FP64), and x'[r][node] = x 2^-f_r as a double-float
+__global__ void batch_scatter_df_kernel(const int32_t* __restrict__ iperm, const float* __restrict__ d,
+                                        double* __restrict__ x, float2* __restrict__ xdf,
+                                        const int* __restrict__ f, int64_t n, int R, int accumulate) {
+  const int64_t total = n * R;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / n, node = i % n;
+    const int fr = f[r];
+    const double v = double_from_float(d[r * n + iperm[node]], fr);
+    const double xn = accumulate ? x[i] + v : v;
+    x[i] = xn;
+    xdf[i] = df_from_double(xn, fr);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1648,9 +1838,13 @@ static vtm_status batch_band_solve(vtm_plan_s* P, FT* V, int R, const FT* Lc, co
   return VTM_OK;
 }
 
-// ||b_c - A x_c||^2 and ||b_c||^2 for every column (r: residuals out, may be NULL)
+// ||b_c - A x_c||^2 and ||b_c||^2 for every column (r: residuals out, may be
+// NULL); with dfb / dfr set instead, the double-float form on the scaled
+// columns (dfx = NULL: x = 0), squares of the scaled values.
 static vtm_status batch_norms(vtm_plan_s* P, const double* x, const double* b, double* r, int R,
-                              std::vector<double>& rr, std::vector<double>& bb) {
+                              std::vector<double>& rr, std::vector<double>& bb,
+                              const float2* dfx = nullptr, const float2* dfb = nullptr,
+                              float2* dfr = nullptr) {
   const int gx = (int)std::max<int64_t>(1, std::min<int64_t>((P->n + 255) / 256, 152 * 2));
   const int gy = (R + 7) / 8;
   // fixed layout for up to 8 column groups: partials | out[128] | counters
@@ -1662,9 +1856,14 @@ static vtm_status batch_norms(vtm_plan_s* P, const double* x, const double* b, d
     VTM_CUDA_TRY(cudaMemsetAsync(counters, 0, 64 * sizeof(double), P->stream));
     P->bres_init = true;
   }
-  batch_residual_norms_kernel<<<gx * gy, 256, 0, P->stream>>>(
-      P->d_rowptr.as<int64_t>(), P->d_colidx.as<int32_t>(), P->d_vals.as<double>(), x, b, r, P->n, R,
-      gx, gy, partials, counters, out);
+  if (dfb)
+    batch_residual_df_kernel<8, 2><<<gx * gy, 256, 0, P->stream>>>(
+        P->d_rowptr.as<int64_t>(), P->d_colidx.as<int32_t>(), P->d_vals_df.as<float2>(), dfx, dfb, dfr,
+        P->n, R, gx, gy, partials, counters, out);
+  else
+    batch_residual_norms_kernel<<<gx * gy, 256, 0, P->stream>>>(
+        P->d_rowptr.as<int64_t>(), P->d_colidx.as<int32_t>(), P->d_vals.as<double>(), x, b, r, P->n, R,
+        gx, gy, partials, counters, out);
   P->launch_count++;
   VTM_CUDA_TRY(cudaGetLastError());
   std::vector<double> h(2 * R);
@@ -1758,24 +1957,76 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
   VTM_TRY(dev_alloc(P->d_btol2, 64 * sizeof(double)));
   VTM_TRY(dev_alloc(P->d_bctrl, sizeof(BatchCtrl)));
   VTM_TRY(dev_alloc(P->d_xacc, (size_t)n * R * sizeof(double)));
-  VTM_TRY(dev_alloc(P->d_r, (size_t)n * R * sizeof(double)));
   double* V = P->d_bV.as<double>();
   // low precision: both banded solves of each refinement step in FP32 (their
   // error is removed by the next step like the sweeps' rounding)
   const bool f32_solves = lowp && P->d_Lc32.p;
   if (f32_solves) VTM_TRY(dev_alloc(P->d_bV32, (size_t)n * R * sizeof(float)));
+  // ... and the residuals in double-float when A's nonzeros lie within
+  // 2^-100 .. 2^100 (the scaled products then stay inside FP32's range)
+  if (f32_solves && P->vals_df_state == 0) {
+    bool ok = true;
+    for (double v : P->h_vals) {
+      int e = 0;
+      if (!std::isfinite(v)) ok = false;
+      else if (v != 0.0) std::frexp(v, &e);
+      if (!ok || e < -100 || e > 100) {
+        ok = false;
+        break;
+      }
+    }
+    P->vals_df_state = ok ? 1 : 2;
+    if (ok) {
+      VTM_TRY(dev_alloc(P->d_vals_df, (size_t)std::max<int64_t>(P->nnz, 1) * sizeof(float2)));
+      batch_split_kernel<<<grid_n(P->nnz), 256, 0, s>>>(P->d_vals.as<double>(), nullptr,
+                                                         P->d_vals_df.as<float2>(), P->nnz, 1);
+      P->launch_count++;
+    }
+  }
+  const bool dfres = f32_solves && P->vals_df_state == 1;
+  if (dfres) {
+    VTM_TRY(dev_alloc(P->d_bdf, (size_t)n * R * sizeof(float2)));
+    VTM_TRY(dev_alloc(P->d_rdf, (size_t)n * R * sizeof(float2)));
+    VTM_TRY(dev_alloc(P->d_xdf, (size_t)n * R * sizeof(float2)));
+    VTM_TRY(dev_alloc(P->d_bexp, 2 * 64 * sizeof(int)));
+  } else {
+    VTM_TRY(dev_alloc(P->d_r, (size_t)n * R * sizeof(double)));
+  }
   float* V32 = P->d_bV32.as<float>();
   double* xacc = P->d_xacc.as<double>();
   double* r = P->d_r.as<double>();
-  // ||b_r||
-  std::vector<double> bnorm(R), rnorm(R), rel(R);
+  float2* bdf = P->d_bdf.as<float2>();
+  float2* rdf = P->d_rdf.as<float2>();
+  float2* xdf = P->d_xdf.as<float2>();
+  int* d_emax = P->d_bexp.as<int>();
+  int* d_f = d_emax + 64;
+  // ||b_r||; double-float residuals: column c scaled by sc[c] = 2^-fexp[c],
+  // max |b_c| sc[c] in [1, 2)
+  std::vector<double> bnorm(R), rnorm(R), rel(R), sc(R, 1.0);
+  std::vector<int> fexp(R, 0);
   VTM_CUDA_TRY(cudaMemsetAsync(xacc, 0, (size_t)n * R * sizeof(double), s));
   std::vector<double> rr2, bb2;
-  VTM_TRY(batch_norms(P, xacc, d_b, r, R, rr2, bb2));
-  for (int c = 0; c < R; ++c) {
-    bnorm[c] = std::sqrt(bb2[c]);
-    rnorm[c] = bnorm[c];
+  if (dfres) {
+    VTM_CUDA_TRY(cudaMemsetAsync(d_emax, 0, 64 * sizeof(int), s));
+    batch_colexp_kernel<<<dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 304)), R),
+                          256, 0, s>>>(d_b, n, R, d_emax);
+    std::vector<int> emax(R);
+    VTM_CUDA_TRY(cudaMemcpyAsync(emax.data(), d_emax, R * sizeof(int), cudaMemcpyDeviceToHost, s));
+    VTM_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int c = 0; c < R; ++c) {
+      fexp[c] = emax[c] > 0 && emax[c] < 0x7ff ? emax[c] - 1023 : 0;
+      sc[c] = std::ldexp(1.0, -fexp[c]);
+    }
+    VTM_CUDA_TRY(cudaMemcpyAsync(d_f, fexp.data(), R * sizeof(int), cudaMemcpyHostToDevice, s));
+    batch_split_kernel<<<grid_n(n * R), 256, 0, s>>>(d_b, d_f, bdf, n, R);
+    P->launch_count += 2;
+    VTM_TRY(batch_norms(P, nullptr, nullptr, nullptr, R, rr2, bb2, nullptr, bdf, rdf));
+    for (int c = 0; c < R; ++c) bnorm[c] = std::ldexp(std::sqrt(bb2[c]), fexp[c]);
+  } else {
+    VTM_TRY(batch_norms(P, xacc, d_b, r, R, rr2, bb2));
+    for (int c = 0; c < R; ++c) bnorm[c] = std::sqrt(bb2[c]);
   }
+  for (int c = 0; c < R; ++c) rnorm[c] = bnorm[c];
   info->sweeps = 0;
   info->outer_steps = 0;
   info->relres = 0.0;
@@ -1791,7 +2042,8 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
   for (int outer = 0; outer < max_outer; ++outer) {
     const double* rhs = outer == 0 ? d_b : r;
     if (f32_solves) {
-      batch_gather_kernel<float><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, V32, n, R);
+      if (dfres) batch_gather_df_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rdf, V32, n, R);
+      else batch_gather_kernel<float><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, V32, n, R);
       P->launch_count++;
       VTM_TRY(batch_band_solve<float>(P, V32, R, P->d_Lc32.as<float>(), P->d_Uc32.as<float>()));
     } else {
@@ -1817,7 +2069,7 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
       std::vector<double> t2(64, 1.0);
       for (int c = 0; c < R; ++c) {
         const double target = tol * bnorm[c];
-        const double t_abs = prec == VTM_PREC_FP64 ? target : std::max(target, inner_tol * rnorm[c]);
+        const double t_abs = (prec == VTM_PREC_FP64 ? target : std::max(target, inner_tol * rnorm[c])) * sc[c];
         t2[c] = std::max(t_abs * t_abs, 1e-300);
       }
       VTM_CUDA_TRY(cudaMemcpyAsync(P->d_btol2.p, t2.data(), 64 * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -2002,7 +2254,7 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
         VTM_CUDA_TRY(cudaMemcpyAsync(hh.data(), bhist, bhist_len * sizeof(double), cudaMemcpyDeviceToHost, s));
         VTM_CUDA_TRY(cudaStreamSynchronize(s));
         for (int i = 0; i < bhist_len; ++i)
-          P->opts.history[i] = rnorm[0] > 0 ? std::sqrt(hh[i]) / rnorm[0] : 0.0;
+          P->opts.history[i] = rnorm[0] > 0 ? std::sqrt(hh[i]) / (rnorm[0] * sc[0]) : 0.0;
       }
       if (outer == 0 && flag == 1) info->first_sweep_converged = kc;
       info->sweeps += kc;
@@ -2010,7 +2262,8 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
       const int slot = kc & 1;
       P->launch_count += 2;
       if (f32_solves) {
-        batch_gather_kernel<float><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, V32, n, R);
+        if (dfres) batch_gather_df_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rdf, V32, n, R);
+        else batch_gather_kernel<float><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, V32, n, R);
         batch_inject_kernel<float, float><<<g2, 256, 0, s>>>(
             P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(), P->d_beta.as<double>(),
             P->d_bstate.as<float>() + (size_t)slot * npt * 2 * R, V32, npt, R, n);
@@ -2031,7 +2284,9 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
       info->sweeps += 1;
       if (outer == 0) info->first_sweep_converged = 1;
     }
-    if (f32_solves && npt > 0)
+    if (dfres)
+      batch_scatter_df_kernel<<<g1, 256, 0, s>>>(P->d_iperm.as<int32_t>(), V32, xacc, xdf, d_f, n, R, outer > 0);
+    else if (f32_solves)
       batch_scatter_kernel<float><<<g1, 256, 0, s>>>(P->d_iperm.as<int32_t>(), V32, xacc, n, R, outer > 0);
     else
       batch_scatter_kernel<double><<<g1, 256, 0, s>>>(P->d_iperm.as<int32_t>(), V, xacc, n, R, outer > 0);
@@ -2040,11 +2295,12 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
     info->outer_steps = outer + 1;
     bool all_ok = true, bad = false, stall = false;
     double worst = 0.0;
-    VTM_TRY(batch_norms(P, xacc, d_b, r, R, rr2, bb2));
+    if (dfres) VTM_TRY(batch_norms(P, nullptr, nullptr, nullptr, R, rr2, bb2, xdf, bdf, rdf));
+    else VTM_TRY(batch_norms(P, xacc, d_b, r, R, rr2, bb2));
     for (int c = 0; c < R; ++c) {
       const double rr = rr2[c];
       const double rprev = rnorm[c];
-      rnorm[c] = std::sqrt(rr);
+      rnorm[c] = std::ldexp(std::sqrt(rr), fexp[c]);
       // a column that has not met the tolerance must still gain (safeguard)
       if (rnorm[c] > tol * bnorm[c] && refinement_stalled(prec, rprev, rnorm[c], tol * bnorm[c]))
         stall = true;

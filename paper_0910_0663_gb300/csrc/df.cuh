@@ -19,6 +19,8 @@
 // the exact rounding of each step), hence the explicit __fadd_rn / __fmul_rn.
 #pragma once
 
+#include <stdint.h>
+
 namespace vtm {
 
 struct df {
@@ -137,6 +139,43 @@ __device__ __forceinline__ void dacc2_fma(dacc2& a, float2 th, float2 tl, float2
   const float2 err = __ffma2_rn(a2n, m1, a1);      // (S - t1) + (p - bb)
   a.S = s;
   a.E = __fadd2_rn(a.E, __fadd2_rn(err, e));
+}
+
+// Conversions by the bits alone (integer instructions, no FP64 pipe), with
+// an exact power-of-two scale.
+//
+// v 2^-f as a double-float: h = v's leading 24 significant bits (truncated,
+// so |l| < ulp(h) rather than ulp(h)/2), l = the next 29 bits (rounded to
+// FP32, so h + l keeps about 48 of v's 53 bits).  |v 2^-f| below 2^-126 reads
+// as a signed zero, at or above 2^128 as an infinity; an infinity or NaN
+// stays one.
+__device__ __forceinline__ float2 df_from_double(double v, int f) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const int E = (int)((u >> 52) & 0x7ff);
+  const uint32_t sign = (uint32_t)(u >> 63) << 31;
+  const unsigned long long M = u & 0xfffffffffffffull;
+  if (E == 0x7ff) return make_float2(__uint_as_float(sign | 0x7f800000u | (M ? 0x400000u : 0u)), 0.f);
+  const int e = E - 1023 - f;
+  if (E == 0 || e < -126) return make_float2(__uint_as_float(sign), 0.f);
+  if (e > 127) return make_float2(__uint_as_float(sign | 0x7f800000u), 0.f);
+  const float h = __uint_as_float(sign | ((uint32_t)(e + 127) << 23) | (uint32_t)(M >> 29));
+  const float rm = __uint2float_rn((uint32_t)(M & 0x1fffffffu));  // l = rm 2^(e - 52)
+  float l = e >= -74 ? __fmul_rn(rm, __uint_as_float((uint32_t)(e - 52 + 127) << 23))
+                     : __fmul_rn(__fmul_rn(rm, __uint_as_float((uint32_t)(e + 12 + 127) << 23)),
+                                 __uint_as_float((uint32_t)(-64 + 127) << 23));
+  return make_float2(h, sign ? -l : l);
+}
+
+// x 2^f as a double (exact for a normal x whose scaled exponent fits a
+// double; anything else through the FP64 pipe)
+__device__ __forceinline__ double double_from_float(float x, int f) {
+  const uint32_t u = __float_as_uint(x);
+  const int E = (int)((u >> 23) & 0xff);
+  const int Ed = E - 127 + f + 1023;
+  if (E == 0 || E == 0xff || Ed <= 0 || Ed >= 0x7ff) return ldexp((double)x, f);
+  return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) |
+                                          ((unsigned long long)Ed << 52) |
+                                          ((unsigned long long)(u & 0x7fffffu) << 29)));
 }
 
 __device__ __forceinline__ dacc dacc2_lo(const dacc2& a) { return {a.S.x, a.E.x}; }

@@ -288,6 +288,11 @@ struct vtm_plan_s {
   // its G blocks, tiles longest first, (tile, block) list, G_f and G_b
   // (built at the first FP32 batched solve after each factorisation)
   bool bk_ready = false;
+  // double-float residuals of the low-precision batched solves: A's values as
+  // (h, l) pairs (state 0 not built, 1 built, 2 values out of range), the
+  // scaled b, residual and iterate, per-column exponents
+  int vals_df_state = 0;
+  vtm::DevBuf d_vals_df, d_bdf, d_rdf, d_xdf, d_bexp;
   vtm::DevBuf d_bk_W, d_bk_goff, d_bk_order, d_bk_blk, d_bk_Gf, d_bk_Gb;
 
   // adjoint of an unsymmetric system

@@ -203,3 +203,42 @@ def test_blocked_band_solve_needs_a_band_of_at_most_128(vtm):
     with pytest.raises(vtm.VTMError, match="half bandwidths up to 128"):
         plan.solve(b, tol=1e-10)
     plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_batched_columns_of_very_different_magnitudes(vtm, precision):
+    # the low-precision batched residuals are double-float on columns scaled
+    # by 2^-f (f from max |b_c|): columns of size 1e-30, 1 and 1e30 each reach
+    # the tolerance by the oracle's FP64 residual
+    w = _thermal_small(3, seed=8)
+    A = w.csr()
+    b = w.b * np.array([1e-30, 1.0, 1e30])[:, None]
+    plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc, precision=precision)
+    x, info = plan.solve(torch.from_numpy(b).cuda(), tol=1e-10)
+    rel = O.residual_norms(A, x.cpu().numpy(), b)
+    assert rel.max() <= 1e-10, rel
+    assert info["relres"] <= 1e-10
+
+
+def test_batched_low_precision_without_ports(vtm):
+    # one sub-circuit: no torn lines, the batched step is the FP32 band solve
+    # alone, refined in FP64
+    w = _thermal_small(3, seed=9)
+    A = w.csr()
+    part = np.zeros(w.n, np.int32)
+    plan = vtm.Plan(w.indptr, w.indices, w.data, part, 1, Zc=w.Zc, precision="fp32")
+    assert plan.stats()["nports"] == 0
+    x, info = plan.solve(torch.from_numpy(w.b).cuda(), tol=1e-10)
+    assert O.residual_norms(A, x.cpu().numpy(), w.b).max() <= 1e-10
+
+
+def test_batched_matrix_beyond_double_float_range(vtm):
+    # nonzeros near 2^101 (outside 2^-100 .. 2^100): the residuals stay FP64;
+    # the solve reaches the tolerance all the same
+    w = _thermal_small(4, seed=10)
+    scale = 2.0 ** 101
+    A = w.csr() * scale
+    plan = vtm.Plan(w.indptr, w.indices, w.data * scale, w.partition, w.nparts, Zc=w.Zc / scale,
+                    precision="fp32")
+    x, info = plan.solve(torch.from_numpy(w.b).cuda(), tol=1e-10)
+    assert O.residual_norms(A, x.cpu().numpy(), w.b).max() <= 1e-10
