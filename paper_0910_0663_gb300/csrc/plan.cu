@@ -1072,7 +1072,9 @@ extern "C" vtm_status vtm_plan(int64_t n, const int64_t* rowptr, const int32_t* 
   // two sweeps' worth (the one-warp-per-tile sweeps reduce one while writing the next)
   if ((st = dev_alloc(P->d_partials, 2 * sizeof(double) * std::max<size_t>(nparts, 4096))) != VTM_OK)
     return fail(st);
-  if ((st = dev_alloc(P->d_ctrl, sizeof(SweepCtrl))) != VTM_OK) return fail(st);
+  // the control block, then one sweep counter per CTA of the one-warp-per-tile
+  // kernels (their grids have at most one CTA per tile)
+  if ((st = dev_alloc(P->d_ctrl, sizeof(SweepCtrl) + 4 * ((size_t)P->nparts + 4))) != VTM_OK) return fail(st);
   if ((st = dev_alloc(P->d_err, 64)) != VTM_OK) return fail(st);
   if ((st = dev_alloc(P->d_red, 256)) != VTM_OK) return fail(st);
   if (cudaMemsetAsync(P->d_red.p, 0, 256, s) != cudaSuccess) return fail(VTM_ECUDA);  // counters start at 0

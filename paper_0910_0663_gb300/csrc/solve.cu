@@ -192,6 +192,19 @@ __device__ double block_sum_value(double v) {
 // flag 1: converged, 2: sweep limit, 3: diverged or not finite, 4: stalled
 // (rounding floor of a low-precision inner solve); a flag already set (a
 // bounded wait that timed out) is kept.
+// The sweep a CTA of the one-warp-per-tile kernels runs: one counter per CTA
+// index after the control block (reset with it), counting the launches this
+// CTA index has started.  Every launch has the same grid and each counter is
+// touched by one thread per launch, after the wait for the previous launch,
+// so it needs no atomic (a shared ticket made every CTA of a sweep queue on
+// one address).
+__device__ __forceinline__ unsigned take_sweep_number(SweepCtrl* ctrl) {
+  unsigned* tk = reinterpret_cast<unsigned*>(ctrl + 1) + blockIdx.x;
+  const unsigned t = *reinterpret_cast<volatile unsigned*>(tk) + 1u;
+  *tk = t;
+  return t;
+}
+
 __device__ void sweep_decide(SweepCtrl* ctrl, int k, double tot, double* hist, int hist_len) {
   int flag = 0;
   if (k > 1) {
@@ -1310,7 +1323,7 @@ __global__ void __launch_bounds__(1024, 1) sweep_wsym_kernel(
   pdl_wait();  // the previous sweep's waves, partials and decision
   if (tid == 0) {
     s_flag = *((volatile int*)&ctrl->flag);
-    if (!s_flag) s_k = (int)(atomicAdd(&ctrl->ticket, 1u) / gridDim.x) + 1;
+    if (!s_flag) s_k = (int)take_sweep_number(ctrl);
   }
   __syncthreads();
   if (s_flag) {
@@ -1618,7 +1631,7 @@ __global__ void __launch_bounds__(1024, 1) sweep_wmma_kernel(
   pdl_wait();  // the previous sweep's waves, partials and decision
   if (tid == 0) {
     s_flag = *((volatile int*)&ctrl->flag);
-    if (!s_flag) s_k = (int)(atomicAdd(&ctrl->ticket, 1u) / gridDim.x) + 1;
+    if (!s_flag) s_k = (int)take_sweep_number(ctrl);
   }
   __syncthreads();
   if (s_flag) return;
@@ -1890,7 +1903,7 @@ __global__ void __launch_bounds__(1024, 1) sweep_wdf_kernel(
   pdl_wait();  // the previous sweep's waves, partials and decision
   if (tid == 0) {
     s_flag = *((volatile int*)&ctrl->flag);
-    if (!s_flag) s_k = (int)(atomicAdd(&ctrl->ticket, 1u) / gridDim.x) + 1;
+    if (!s_flag) s_k = (int)take_sweep_number(ctrl);
   }
   __syncthreads();
   if (s_flag) {
@@ -2581,8 +2594,17 @@ struct L2Window {
 // Run sweeps from a zero state until the interface residual is below
 // target2 (absolute, squared) or the sweep budget is used.  Returns the
 // sweep whose waves are to be recovered and its flag.
+// *P->h_ctrl to the device, with the per-CTA sweep counters zeroed
+static vtm_status upload_ctrl(vtm_plan_s* P, cudaStream_t s) {
+  VTM_CUDA_TRY(cudaMemcpyAsync(P->d_ctrl.p, P->h_ctrl, sizeof(SweepCtrl), cudaMemcpyHostToDevice, s));
+  VTM_CUDA_TRY(cudaMemsetAsync(reinterpret_cast<SweepCtrl*>(P->d_ctrl.p) + 1, 0,
+                               P->d_ctrl.bytes - sizeof(SweepCtrl), s));
+  return VTM_OK;
+}
+
 static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int budget, int prec,
-                             double* hist, int hist_len, int stall, int* sweep_out, int* flag_out) {
+                             double* hist, int hist_len, int stall, int* sweep_out, int* flag_out,
+                             int hint = 0) {
   cudaStream_t s = P->stream;
   const int64_t npt = (int64_t)P->port_node.size();
   SweepCtrl h{};
@@ -2597,7 +2619,7 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   h.tol2 = target2;
   h.bnorm2 = bnorm2 > 0 ? bnorm2 : 1.0;
   *P->h_ctrl = h;
-  VTM_CUDA_TRY(cudaMemcpyAsync(P->d_ctrl.p, P->h_ctrl, sizeof(SweepCtrl), cudaMemcpyHostToDevice, s));
+  VTM_TRY(upload_ctrl(P, s));
   const int threads = P->max_ports <= 64 ? 64 : (P->max_ports <= 128 ? 128 : 256);
   size_t wsz = prec == VTM_PREC_FP64 ? sizeof(double) : sizeof(float);
   size_t smem = (size_t)((P->max_ports + 2) & ~1) * wsz * 2 + 16;
@@ -3026,7 +3048,7 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
           t.tol2 = -1.0;
           t.stall = 0;
           *P->h_ctrl = t;
-          VTM_CUDA_TRY(cudaMemcpyAsync(P->d_ctrl.p, P->h_ctrl, sizeof(SweepCtrl), cudaMemcpyHostToDevice, s));
+          VTM_TRY(upload_ctrl(P, s));
           VTM_CUDA_TRY(cudaEventRecord(P->evs0, s));
           VTM_CUDA_TRY(cand == 10 ? launch_wflow() : launch_flow());
           VTM_CUDA_TRY(cudaEventRecord(P->evs1, s));
@@ -3053,7 +3075,7 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
         t.tol2 = -1.0;  // never converges while timing
         t.stall = 0;
         *P->h_ctrl = t;
-        VTM_CUDA_TRY(cudaMemcpyAsync(P->d_ctrl.p, P->h_ctrl, sizeof(SweepCtrl), cudaMemcpyHostToDevice, s));
+        VTM_TRY(upload_ctrl(P, s));
         for (int i = 0; i < 2; ++i) launch_one(cand);
         VTM_CUDA_TRY(cudaEventRecord(P->evs0, s));
         for (int i = 0; i < 6; ++i) launch_one(cand);
@@ -3072,7 +3094,7 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
       P->tuned_ms[prec] = best / 6.0f;
       // back to the initial state of this inner solve
       *P->h_ctrl = h;
-      VTM_CUDA_TRY(cudaMemcpyAsync(P->d_ctrl.p, P->h_ctrl, sizeof(SweepCtrl), cudaMemcpyHostToDevice, s));
+      VTM_TRY(upload_ctrl(P, s));
       if (prec == VTM_PREC_FP64)
         VTM_CUDA_TRY(cudaMemsetAsync(P->d_state64.p, 0, 4 * npt * sizeof(double), s));
       else
@@ -3137,16 +3159,21 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
     }
     gexec = G.exec;
   }
+  // hint: the sweeps the same refinement step took last time.  That many
+  // launches (whole batches) go out before the first poll of the flag: a
+  // poll costs a host round trip with the GPU idle, a launch that finds the
+  // solve converged returns at once.
   int launched = 0;
+  int reps = gexec ? std::min(std::max(1, (hint + batch - 1) / batch), 64) : 1;
   while (true) {
     const int m = gexec ? batch : std::min(batch, budget + 1 - launched);
     VTM_CUDA_TRY(cudaEventRecord(P->evs0, s));
     if (gexec) {
-      VTM_CUDA_TRY(cudaGraphLaunch(gexec, s));
+      for (int i = 0; i < reps; ++i) VTM_CUDA_TRY(cudaGraphLaunch(gexec, s));
     } else {
       for (int i = 0; i < m; ++i) launch_one(kern);
     }
-    launched += m;
+    launched += m * reps;
     VTM_CUDA_TRY(cudaGetLastError());
     VTM_CUDA_TRY(cudaEventRecord(P->evs1, s));
     VTM_CUDA_TRY(cudaMemcpyAsync(P->h_ctrl, P->d_ctrl.p, sizeof(SweepCtrl), cudaMemcpyDeviceToHost, s));
@@ -3154,8 +3181,9 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
     float bms = 0.f;
     VTM_CUDA_TRY(cudaEventElapsedTime(&bms, P->evs0, P->evs1));
     P->sweep_ms += bms;
-    P->sweep_launch_count += m;
-    P->launch_count += m;
+    P->sweep_launch_count += m * reps;
+    P->launch_count += m * reps;
+    reps = 1;
     if (P->h_ctrl->flag || launched > budget) break;
   }
   const SweepCtrl& r = *P->h_ctrl;
@@ -3321,8 +3349,10 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
       if (sweeps_left <= 0) break;
       // low-precision inner solves stop at their rounding floor as well
       const int stall = prec == VTM_PREC_FP64 ? 0 : 64;
+      const int step = std::min(outer, 7);
       VTM_TRY(run_sweeps(P, rnorm * rnorm, t_abs * t_abs, sweeps_left, prec, hist, hist_len, stall,
-                         &kc, &flag));
+                         &kc, &flag, P->sweep_hint[prec][step]));
+      P->sweep_hint[prec][step] = kc;
       if (hist) {
         VTM_CUDA_TRY(cudaMemcpyAsync(P->opts.history, hist, hist_len * sizeof(double),
                                      cudaMemcpyDeviceToHost, s));

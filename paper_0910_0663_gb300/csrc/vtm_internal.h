@@ -47,7 +47,8 @@ struct SweepCtrl {
   int k_max;           // last sweep allowed
   int best_k;          // sweep with the smallest residual so far
   int stall;           // sweeps without a 10% improvement that end the run (0 = never)
-  unsigned ticket;     // CTAs that started a sweep (the one-warp-per-tile sweeps)
+  unsigned ticket;     // unused (kept for the layout; the one-warp-per-tile sweeps count
+                       // their sweeps per CTA after the block)
   double best_res2;    // smallest squared residual so far
   double tol2;         // (tol * ||b||)^2 for the residual test
   double bnorm2;       // ||b||^2 of the current right-hand side
@@ -238,6 +239,7 @@ struct vtm_plan_s {
   int tuned_kernel[4] = {0, 0, 0, 0};
   int dataflow_kernel = 8;  // kernel of the last sweeps run (8 or 10 for asynchronous VTM)
   float tuned_ms[4] = {0.f, 0.f, 0.f, 0.f};
+  int sweep_hint[4][8] = {};  // sweeps of refinement step i of the last solve, per precision
   vtm::SweepGraph sweep_graph[4];
   vtm::SweepGraph batch_graph[4];
   // per-call accounting (reset by each solve)
