@@ -175,6 +175,11 @@ typedef struct {
                         decision of its own sweep, which cannot come -- a host-made hang
                         that the bounded waits end with VTM_ETIMEOUT (a test of that
                         path; the plan stays usable) */
+  int band_solve;    /* single-column FP32 band solves of half bandwidth <= 32 (the
+                        right-hand-side preparation and recovery of low-precision
+                        solves): 0 (default) factor columns streamed by bulk copies
+                        through a shared-memory ring per tile; 1: the same arithmetic
+                        with register prefetch.  Both give the same bits */
 } vtm_opts;
 
 typedef struct {

@@ -33,7 +33,7 @@ class vtm_opts(ctypes.Structure):
                 ("pdl", ctypes.c_int),
                 ("history", ctypes.POINTER(ctypes.c_double)),
                 ("history_len", ctypes.c_int), ("batch_kernel", ctypes.c_int),
-                ("wait_polls", ctypes.c_int), ("flow_lag", ctypes.c_int)]
+                ("wait_polls", ctypes.c_int), ("flow_lag", ctypes.c_int), ("band_solve", ctypes.c_int)]
 
 
 class vtm_info(ctypes.Structure):
@@ -139,8 +139,9 @@ def _check(status, where):
 
 def make_opts(precision="fp64", max_sweeps=0, check_every=0, inner_tol=0.0, max_outer=0,
               history=None, sweep_kernel=0, method="vtm", batch=0, l2_persist=0, graphs=0,
-              batch_solve=0, pdl=0, batch_kernel=0, wait_polls=0, flow_lag=0):
+              batch_solve=0, pdl=0, batch_kernel=0, wait_polls=0, flow_lag=0, band_solve=0):
     o = vtm_opts()
+    o.band_solve = int(band_solve)
     o.batch_kernel = int(batch_kernel)
     o.wait_polls = int(wait_polls)
     o.flow_lag = int(flow_lag)

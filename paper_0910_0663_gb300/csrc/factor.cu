@@ -25,6 +25,7 @@
 #include <cstring>
 
 #include "band.cuh"
+#include "ptx.h"
 #include "vtm_internal.h"
 
 namespace vtm {
@@ -418,12 +419,165 @@ __global__ void __launch_bounds__(32, 28) band_solve_reg_kernel(
   band_pass_reg<FT, false>(Uc + band_off[t], n, bw, bw + 1, vg, ysm, vg, lane);
 }
 
+// The same register-blocked solve (FP32, half bandwidth <= 32) with the
+// multipliers streamed through shared memory: each warp (one tile and column)
+// keeps a ring of kRgS chunks of kRgC columns, filled by bulk copies that
+// complete on one mbarrier per chunk slot, so that two chunks (about 4 KB) are
+// on their way while the third is read -- twice the bytes in flight of the
+// register prefetch, without its registers.  The forward results go back into
+// v (global memory) instead of a shared-memory copy of the tile, which leaves
+// room for 32 warps per SM.  Each lane applies the same multiplier of each
+// column to the same row, in the same order, as band_pass_reg: the results are
+// the same bits.  A chunk's copy starts at the 16-byte boundary below its
+// first column (the FP32 factor arrays carry 64 bytes of tail padding for the
+// rounded-up end of the last chunk).  Waits are bounded: a copy that never
+// lands leaves the tile's column NaN (the refinement then reports a
+// divergence) after a second bounded wait for the copies in flight.
+constexpr int kRgC = 16;                  // columns per chunk
+constexpr int kRgS = 3;                   // chunks per warp
+constexpr int kRgStage = kRgC * 33 + 4;   // floats per chunk slot (532: a multiple of 4)
+constexpr int kRgWarps = 4;               // warps per CTA
+constexpr uint32_t kRgPolls = 1u << 24;   // mbarrier polls before giving up
+constexpr size_t kRgSmem = (size_t)kRgWarps * (kRgS * kRgStage * sizeof(float) + kRgS * sizeof(uint64_t));
+
+template <bool FWD>
+__device__ __forceinline__ bool band_pass_ring(const float* __restrict__ colbase, int n, int bw, int B,
+                                               float* v, float* ring, uint64_t* bars, uint32_t& par,
+                                               int lane) {
+  // pass coordinate j: row j (forward) or n - 1 - j (backward)
+  auto src = [&](int j) -> float { return j < n ? v[FWD ? j : n - 1 - j] : 0.f; };
+  auto diag = [&](int j) -> float {
+    return j < n ? __ldg(colbase + (ptrdiff_t)(FWD ? j : n - 1 - j) * B) : 0.f;
+  };
+  const int nch = (n + kRgC - 1) / kRgC;
+  // memory columns [mc0, mc1) of chunk c (pass columns [kRgC c, kRgC c + kRgC))
+  auto first_col = [&](int c) { return FWD ? c * kRgC : n - min(n, c * kRgC + kRgC); };
+  auto issue = [&](int c) {  // lane 0: chunk c into slot c mod kRgS
+    const int mc0 = first_col(c);
+    const int mc1 = FWD ? min(n, c * kRgC + kRgC) : n - c * kRgC;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(colbase + (size_t)mc0 * B);
+    const uintptr_t a0 = a & ~(uintptr_t)15;
+    const uint32_t bytes = (uint32_t)(((a - a0) + (size_t)(mc1 - mc0) * B * sizeof(float) + 15) & ~(size_t)15);
+    uint64_t* bar = &bars[c % kRgS];
+    mbar_arrive_expect_tx(bar, bytes);
+    bulk_copy_g2s(ring + (c % kRgS) * kRgStage, reinterpret_cast<const void*>(a0), bytes, bar);
+  };
+  if (lane == 0) {
+    fence_proxy_async_smem();  // the slots' earlier reads come before the copies
+    for (int c = 0; c < kRgS && c < nch; ++c) issue(c);
+  }
+  float dg = diag(lane);
+  float xc = src(lane), xn = src(32 + lane);
+  for (int J = 0; J < n; J += 32) {
+    const float dg_next = diag(J + 32 + lane);
+    const float x_after = src(J + 64 + lane);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = (J >> 4) + h;
+      if (c < nch) {
+        const int sl = c % kRgS;
+        if (!mbar_wait_bounded(&bars[sl], (par >> sl) & 1u, kRgPolls)) return false;
+        par ^= 1u << sl;
+        const float* st = ring + sl * kRgStage;
+        const int mc0 = first_col(c);
+        const int dl = (int)((reinterpret_cast<uintptr_t>(colbase + (size_t)mc0 * B) >> 2) & 3);
+        if (bw == 32 && J + 96 <= n) {
+          // interior block of a full band: every multiplier exists, and from
+          // one column to the next the lane's element moves by 32 or 64
+          // (forward) or -34 or -2 (backward) as its offset a wraps
+          const int q0 = kRgC * h;
+          int a = ((lane - q0 - 1) & 31) + 1;
+          int e = dl + ((FWD ? J + q0 : n - 1 - (J + q0)) - mc0) * 33 + a;
+#pragma unroll
+          for (int qq = 0; qq < kRgC; ++qq) {
+            const int q = q0 + qq;
+            const float mq = st[e];
+            const bool wrap = a == 1;
+            e += FWD ? (wrap ? 64 : 32) : (wrap ? -2 : -34);
+            a = wrap ? 32 : a - 1;
+            const float u = shfl_idx_ordered(xc, q);
+            if (lane > q) xc -= mq * u;
+            else xn -= mq * u;
+          }
+        } else {
+#pragma unroll
+          for (int qq = 0; qq < kRgC; ++qq) {
+            const int q = kRgC * h + qq, j = J + q;
+            const int a = ((lane - q - 1) & 31) + 1;
+            const int m = FWD ? j : n - 1 - j;
+            const float mq = (j < n && a <= min(bw, n - 1 - j)) ? st[dl + (m - mc0) * B + a] : 0.f;
+            if (j < n) {
+              const float u = shfl_idx_ordered(xc, q);
+              if (lane > q) xc -= mq * u;
+              else xn -= mq * u;
+            }
+          }
+        }
+        __syncwarp();  // every lane is done with the slot
+        if (lane == 0 && c + kRgS < nch) {
+          fence_proxy_async_smem();
+          issue(c + kRgS);
+        }
+      }
+    }
+    if (J + lane < n) v[FWD ? J + lane : n - 1 - (J + lane)] = xc * dg;
+    xc = xn;
+    xn = x_after;
+    dg = dg_next;
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(32 * kRgWarps, 7) band_solve_ring_kernel(
+    const int32_t* __restrict__ node_off, const int32_t* __restrict__ bwv,
+    const int64_t* __restrict__ band_off, const float* __restrict__ Lc, const float* __restrict__ Uc,
+    float* __restrict__ v, int64_t stride, int nparts, int nwork) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw) + warp * kRgS;
+  float* ring = reinterpret_cast<float*>(smem_raw + kRgWarps * kRgS * sizeof(uint64_t)) +
+                (size_t)warp * kRgS * kRgStage;
+  const int g = blockIdx.x * kRgWarps + warp;
+  if (g >= nwork) return;
+  const int t = g % nparts;
+  const int colr = g / nparts;
+  const int off = node_off[t];
+  const int n = node_off[t + 1] - off;
+  const int bw = bwv[t];
+  float* vg = v + (size_t)colr * stride + off;
+  if (lane == 0) {
+    for (int i = 0; i < kRgS; ++i) mbar_init(&bars[i], 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  uint32_t par = 0;
+  bool ok = band_pass_ring<true>(Lc + band_off[t], n, bw, bw + 1, vg, ring, bars, par, lane);
+  __syncwarp();  // y of every lane before the backward pass reads it
+  if (ok) ok = band_pass_ring<false>(Uc + band_off[t], n, bw, bw + 1, vg, ring, bars, par, lane);
+  if (!ok) {
+    // a copy did not land: wait (bounded) for the slots still in flight,
+    // then mark the column
+    for (int i = 0; i < kRgS; ++i) mbar_wait_bounded(&bars[i], (par >> i) & 1u, kRgPolls);
+    for (int i = lane; i < n; i += 32) vg[i] = __int_as_float(0x7fc00000);
+  }
+}
+
 template <class FT>
 static void launch_band_solve_t(vtm_plan_s* P, FT* v, const FT* Lc, const FT* Uc, int ncols,
                                 int64_t stride, cudaStream_t s) {
   P->launch_count++;
   // FP32 only: the FP64 solve is bound by GB300's FP64 pipe either way (the
   // register-blocked form measured no faster for the 2048^2 power grid)
+  if constexpr (sizeof(FT) == 4) {
+    if (P->max_bw <= 32 && P->opts.band_solve == 0) {
+      const int nwork = P->nparts * ncols;
+      cudaFuncSetAttribute(band_solve_ring_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRgSmem);
+      band_solve_ring_kernel<<<(nwork + kRgWarps - 1) / kRgWarps, 32 * kRgWarps, kRgSmem, s>>>(
+          P->tabs.node_off.as<int32_t>(), P->tabs.bw.as<int32_t>(), P->tabs.band_off.as<int64_t>(), Lc, Uc, v,
+          stride, P->nparts, nwork);
+      return;
+    }
+  }
   if (sizeof(FT) == 4 && P->max_bw <= 32) {
     const size_t smem = (size_t)std::max(P->max_nodes, 1) * sizeof(FT);
     if (smem <= 200 * 1024) {
@@ -707,8 +861,10 @@ extern "C" vtm_status vtm_factor(vtm_plan_t P) {
     // FP32 copy of the factors for the right-hand-side preparation of the
     // inner (low-precision) solves
     const int64_t ne = std::max<int64_t>(P->band_elems, 8);
-    VTM_TRY(dev_alloc(P->d_Lc32, ne * sizeof(float)));
-    VTM_TRY(dev_alloc(P->d_Uc32, ne * sizeof(float)));
+    // (+ 64 bytes: the bulk copies of the band solve round their last chunk up
+    // to a 16-byte multiple)
+    VTM_TRY(dev_alloc(P->d_Lc32, ne * sizeof(float) + 64));
+    VTM_TRY(dev_alloc(P->d_Uc32, ne * sizeof(float) + 64));
     convert_f32_kernel<<<1216, 256, 0, P->stream>>>(P->d_Lc.as<double>(), P->d_Lc32.as<float>(), ne);
     convert_f32_kernel<<<1216, 256, 0, P->stream>>>(P->d_Uc.as<double>(), P->d_Uc32.as<float>(), ne);
     VTM_CUDA_TRY(cudaGetLastError());

@@ -905,8 +905,9 @@ extern "C" vtm_status vtm_set_opts(vtm_plan_t P, const vtm_opts* opts) {
     set_detail("vtm_set_opts: batch_solve must be 0, 1, 2 or 3");
     return VTM_EINVAL;
   }
-  if (o.batch_kernel < 0 || o.batch_kernel > 5 || o.wait_polls < 0 || (o.flow_lag != 0 && o.flow_lag != -1)) {
-    set_detail("vtm_set_opts: batch_kernel must be 0..5, wait_polls >= 0, flow_lag 0 or -1");
+  if (o.batch_kernel < 0 || o.batch_kernel > 5 || o.wait_polls < 0 || (o.flow_lag != 0 && o.flow_lag != -1) ||
+      o.band_solve < 0 || o.band_solve > 1) {
+    set_detail("vtm_set_opts: batch_kernel must be 0..5, wait_polls >= 0, flow_lag 0 or -1, band_solve 0 or 1");
     return VTM_EINVAL;
   }
   bool prec_changed = o.precision != P->opts.precision;

@@ -32,7 +32,7 @@ class Plan:
     def __init__(self, indptr, indices, data, partition, nparts, Zc=1.0, precision="fp64",
                  device="cuda", stream=None, max_sweeps=0, check_every=0, inner_tol=0.0,
                  max_outer=0, sweep_kernel=0, method="vtm", batch=0, l2_persist=0, graphs=0,
-                 batch_solve=0, pdl=0, batch_kernel=0, wait_polls=0, flow_lag=0, factor=True):
+                 batch_solve=0, pdl=0, batch_kernel=0, wait_polls=0, flow_lag=0, band_solve=0, factor=True):
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.n = int(len(indptr) - 1)
@@ -41,7 +41,7 @@ class Plan:
                           inner_tol=inner_tol, max_outer=max_outer, sweep_kernel=sweep_kernel,
                           method=method, batch=batch, l2_persist=l2_persist, graphs=graphs,
                           batch_solve=batch_solve, pdl=pdl, batch_kernel=batch_kernel,
-                          wait_polls=wait_polls, flow_lag=flow_lag)
+                          wait_polls=wait_polls, flow_lag=flow_lag, band_solve=band_solve)
         self._history = None
         rp = _dev(indptr, torch.int64, self.device)
         ci = _dev(indices, torch.int32, self.device)

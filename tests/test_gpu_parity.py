@@ -538,3 +538,25 @@ def test_tensor_core_sweep_at_extreme_magnitudes(vtm, precision, scale):
     # the same iteration as the unscaled solve up to the waves' rounding
     x1, info1 = plan.solve(torch.from_numpy(w.b[0]).cuda(), tol=1e-10)
     assert abs(info["sweeps"] - info1["sweeps"]) <= max(4, info1["sweeps"] // 20)
+
+
+@pytest.mark.parametrize("precision", ["fp16", "fp32"])
+def test_band_solve_ring_and_register_forms_give_the_same_bits(vtm, precision):
+    # the FP32 band solves of the refinement (half bandwidth <= 32): factor
+    # columns through a bulk-copy ring (default) or register prefetch, the same
+    # arithmetic in the same order -- the same iterates and the same x, bit
+    # for bit; ragged edge tiles (200 x 232 nodes in 32 x 32 tiles)
+    w = wl.power_grid(200, 232, 32, 32, Zc=1.0, seed=6)
+    A = w.csr()
+    b = torch.from_numpy(w.b[0]).cuda()
+    out = {}
+    for bs in (0, 1):
+        plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=w.Zc, precision=precision,
+                        band_solve=bs)
+        assert plan.stats()["max_band"] <= 32
+        x, info = plan.solve(b, tol=1e-10)
+        out[bs] = (x.cpu(), info["sweeps"], info["outer_steps"])
+        plan.close()
+    assert torch.equal(out[0][0], out[1][0])
+    assert out[0][1:] == out[1][1:]
+    assert O.residual_norms(A, out[0][0].numpy()[None, :], w.b).max() <= 1e-10
