@@ -448,7 +448,8 @@ def test_bad_options_are_rejected_and_the_plan_keeps_its_own(vtm):
         plan.set_options(sweep_kernel=13)
     with pytest.raises(vtm.VTMError):
         plan.set_options(sweep_kernel=-1)
-    for kw in ({"batch_kernel": 6}, {"wait_polls": -1}, {"flow_lag": 1}, {"batch_solve": 4}):
+    for kw in ({"batch_kernel": 6}, {"wait_polls": -1}, {"flow_lag": 1}, {"batch_solve": 4},
+               {"band_solve": 2}):
         with pytest.raises(vtm.VTMError):
             plan.set_options(**kw)
     for bad in (4, 5, -1):
