@@ -44,8 +44,9 @@ struct BatchCtrl {
 // permutation between the caller's column-major n x R and [pos][R]
 // ---------------------------------------------------------------------------
 
-// Permuted vectors are column-major too, V[r * n + pos], so both sides of
-// the permutation are read and written along a column.
+// Permuted FP64 vectors are column-major too, V[r * n + pos], so both sides
+// of the permutation are read and written along a column (the FP32 vectors of
+// the low-precision path are row-major: see batch_gather_rm_kernel).
 template <class FT>
 __global__ void batch_gather_kernel(const int32_t* __restrict__ perm, const double* __restrict__ src,
                                     FT* __restrict__ dst, int64_t n, int R) {
@@ -177,62 +178,88 @@ __global__ void batch_colexp_kernel(const double* __restrict__ b, int64_t n, int
   if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&emax[c], m);
 }
 
-// dst = src 2^-f[column] as double-floats ([R][n]; f = nullptr: no scale)
-__global__ void batch_split_kernel(const double* __restrict__ src, const int* __restrict__ f,
-                                   float2* __restrict__ dst, int64_t n, int R) {
-  const int64_t total = n * R;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x)
-    dst[i] = df_from_double(src[i], f ? f[i / n] : 0);
+// dst[pos][r] = src[r][pos] 2^-f[r] as double-floats: the caller's
+// column-major b into the row-major [n][R] layout of the double-float
+// vectors, through a shared-memory tile of 32 rows x R
+__global__ void __launch_bounds__(256) batch_split_rm_kernel(const double* __restrict__ src,
+                                                             const int* __restrict__ f,
+                                                             float2* __restrict__ dst, int64_t n, int R) {
+  __shared__ float2 tile[32][65];
+  const int64_t n0 = (int64_t)blockIdx.x * 32;
+  const int nn = (int)(n - n0 < 32 ? n - n0 : 32);
+  const int nl = threadIdx.x & 31;
+  if (nl < nn)
+    for (int r = threadIdx.x >> 5; r < R; r += 8) tile[nl][r] = df_from_double(src[(int64_t)r * n + n0 + nl], f[r]);
+  __syncthreads();
+  for (int e = threadIdx.x; e < nn * R; e += blockDim.x) dst[n0 * R + e] = tile[e / R][e % R];
 }
 
-// r' = b' - A x' per column (all three scaled by 2^-f_c; x' = nullptr: x = 0),
-// with ||r'_c||^2 and ||b'_c||^2: block b covers column group by = b % gy
-// (CG columns, in pairs on the paired FP32 instructions) and rows bx, bx +
-// gx, ... (units of 256), bx = b / gy.  The products are double-float (Dot2
-// accumulation, seeded with b'); the iterate's values are loaded one nonzero
-// ahead and the column indices two ahead.  Squares are summed in FP32 per
-// thread and per warp, then the warp partials in FP64, added in a fixed order
-// by the last block of each group.  counters[by] start at 0 and are left at
-// 0; out[2 c] = ||r'_c||^2, out[2 c + 1] = ||b'_c||^2.
-template <int CG, int MINB>
-__global__ void __launch_bounds__(256, MINB) batch_residual_df_kernel(
+// dst = src as double-floats (A's values, no scale)
+__global__ void batch_split_kernel(const double* __restrict__ src, float2* __restrict__ dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = df_from_double(src[i], 0);
+}
+
+// r' = b' - A x' for up to 64 scaled columns (b', x', r' row-major, [n][R];
+// x' = nullptr: x = 0), with ||r'_c||^2 and ||b'_c||^2, in double-float
+// arithmetic (Dot2 accumulation seeded with b', paired FP32 instructions for
+// two columns at a time).  The lanes lie along the rows: lane l of a warp
+// takes row slot l / 8 (four rows per warp) and columns 8 (l % 8) .. + 7, so
+// one load instruction of the warp reads four whole 512-byte rows of x'
+// (64 columns) and the rows' nonzeros are shared by their eight lanes.  One
+// group of up to 64 columns; block bx covers rows 32 bx .. + 31, then every
+// 32 gx.  Squares: FP32 per thread and across the lanes of a column, FP64 from
+// the warp sums on, blocks added in a fixed order by the last block.
+// out[2 c] = ||r'_c||^2, out[2 c + 1] = ||b'_c||^2; counter 0 on entry, left 0.
+__global__ void __launch_bounds__(256, 2) batch_residual_rows_kernel(
     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
     const float2* __restrict__ vdf, const float2* __restrict__ xdf, const float2* __restrict__ bdf,
-    float2* __restrict__ rdf, int64_t n, int R, int gx, int gy, double* __restrict__ partials,
-    unsigned* __restrict__ counters, double* __restrict__ out) {
-  constexpr int NP = CG / 2;
-  __shared__ double red[2 * CG][8];
+    float2* __restrict__ rdf, int64_t n, int R, int gx, double* __restrict__ partials,
+    unsigned* __restrict__ counter, double* __restrict__ out) {
+  constexpr int CG = 8, NP = CG / 2;
+  __shared__ float red[128][8];
   __shared__ bool last;
-  const int by = blockIdx.x % gy, bx = blockIdx.x / gy;
-  const int c0 = by * CG;
-  const int nc = min(CG, R - c0);
-  const float2* xg = xdf ? xdf + (int64_t)c0 * n : nullptr;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int c0 = CG * (lane & 7);
+  const int nc = max(0, min(CG, R - c0));
+  const bool vec = nc == CG && (R & 1) == 0;
+  auto ld_row = [&](const float2* p, float2 (&o)[CG]) {
+    if (vec) {
+#pragma unroll
+      for (int c = 0; c < CG; c += 2) {
+        const float4 q = *reinterpret_cast<const float4*>(p + c);
+        o[c] = make_float2(q.x, q.y);
+        o[c + 1] = make_float2(q.z, q.w);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < CG; ++c) o[c] = c < nc ? p[c] : make_float2(0.f, 0.f);
+    }
+  };
   float rr[CG], bb[CG];
 #pragma unroll
   for (int c = 0; c < CG; ++c) rr[c] = bb[c] = 0.f;
-  for (int64_t i = bx * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gx * blockDim.x) {
+  for (int64_t i = (int64_t)blockIdx.x * 32 + warp * 4 + (lane >> 3); i < n; i += (int64_t)gx * 32) {
     dacc2 acc[NP];
+    {
+      float2 bv[CG];
+      ld_row(bdf + i * R + c0, bv);
 #pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      const float2 b0 = 2 * p < nc ? bdf[(int64_t)(c0 + 2 * p) * n + i] : make_float2(0.f, 0.f);
-      const float2 b1 = 2 * p + 1 < nc ? bdf[(int64_t)(c0 + 2 * p + 1) * n + i] : make_float2(0.f, 0.f);
-      acc[p].S = make_float2(b0.x, b1.x);
-      acc[p].E = make_float2(b0.y, b1.y);
-      bb[2 * p] += b0.x * b0.x;
-      bb[2 * p + 1] += b1.x * b1.x;
+      for (int p = 0; p < NP; ++p) {
+        acc[p].S = make_float2(bv[2 * p].x, bv[2 * p + 1].x);
+        acc[p].E = make_float2(bv[2 * p].y, bv[2 * p + 1].y);
+        bb[2 * p] += bv[2 * p].x * bv[2 * p].x;
+        bb[2 * p + 1] += bv[2 * p + 1].x * bv[2 * p + 1].x;
+      }
     }
-    if (xg) {
+    if (xdf && nc > 0) {
+      // the iterate's row one nonzero ahead, the column index two ahead
       const int64_t q0 = rowptr[i], q1 = rowptr[i + 1];
-      auto ldx = [&](float2 (&xv)[CG], int64_t j) {
-#pragma unroll
-        for (int c = 0; c < CG; ++c) xv[c] = c < nc ? xg[(int64_t)c * n + j] : make_float2(0.f, 0.f);
-      };
       float2 xv[CG], a = make_float2(0.f, 0.f), an = make_float2(0.f, 0.f);
       int64_t jn = 0;
       if (q0 < q1) {
         a = vdf[q0];
-        ldx(xv, col[q0]);
+        ld_row(xdf + (int64_t)col[q0] * R + c0, xv);
       }
       if (q0 + 1 < q1) {
         jn = col[q0 + 1];
@@ -241,7 +268,7 @@ __global__ void __launch_bounds__(256, MINB) batch_residual_df_kernel(
       for (int64_t q = q0; q < q1; ++q) {
         float2 xn[CG];
         const bool more = q + 1 < q1;
-        if (more) ldx(xn, jn);
+        if (more) ld_row(xdf + jn * R + c0, xn);
         int64_t jnn = 0;
         float2 ann = make_float2(0.f, 0.f);
         if (q + 2 < q1) {
@@ -262,84 +289,175 @@ __global__ void __launch_bounds__(256, MINB) batch_residual_df_kernel(
         an = ann;
       }
     }
+    float2 rv[CG];
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int c = 2 * p + h;
-        if (c < nc) {
-          const df v = dacc_value(h ? dacc2_hi(acc[p]) : dacc2_lo(acc[p]));
-          rdf[(int64_t)(c0 + c) * n + i] = make_float2(v.h, v.l);
-          rr[c] += v.h * v.h;
-        }
+        const df v = dacc_value(h ? dacc2_hi(acc[p]) : dacc2_lo(acc[p]));
+        rv[2 * p + h] = make_float2(v.h, v.l);
+        rr[2 * p + h] += v.h * v.h;
       }
     }
+    float2* rp = rdf + i * R + c0;
+    if (vec) {
+#pragma unroll
+      for (int c = 0; c < CG; c += 2)
+        *reinterpret_cast<float4*>(rp + c) = make_float4(rv[c].x, rv[c].y, rv[c + 1].x, rv[c + 1].y);
+    } else {
+#pragma unroll
+      for (int c = 0; c < CG; ++c)
+        if (c < nc) rp[c] = rv[c];
+    }
   }
-  // warp sums in FP32 (GB300's FP64 pipe would make a 64-bit shuffle tree
-  // the slowest part of the kernel), FP64 from the warp partials on
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  // per column: the four row slots of the warp (lanes l, l + 8, l + 16, l + 24)
 #pragma unroll
   for (int c = 0; c < CG; ++c) {
-    float a = rr[c], e = bb[c];
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_down_sync(0xffffffffu, a, o);
-      e += __shfl_down_sync(0xffffffffu, e, o);
-    }
-    if (l == 0) {
-      red[c][w] = a;
-      red[CG + c][w] = e;
+    rr[c] += __shfl_xor_sync(0xffffffffu, rr[c], 8);
+    rr[c] += __shfl_xor_sync(0xffffffffu, rr[c], 16);
+    bb[c] += __shfl_xor_sync(0xffffffffu, bb[c], 8);
+    bb[c] += __shfl_xor_sync(0xffffffffu, bb[c], 16);
+  }
+  if (lane < 8) {
+#pragma unroll
+    for (int c = 0; c < CG; ++c) {
+      red[c0 + c][warp] = rr[c];
+      red[64 + c0 + c][warp] = bb[c];
     }
   }
   __syncthreads();
-  const size_t pb = ((size_t)by * gx + bx) * 2 * CG;
-  if (threadIdx.x < 2 * CG) {
+  if (tid < 128) {
     double t = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[threadIdx.x][k];
-    partials[pb + threadIdx.x] = t;
+    for (int k = 0; k < 8; ++k) t += (double)red[tid][k];
+    partials[(size_t)blockIdx.x * 128 + tid] = t;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     __threadfence();
-    last = atomicAdd(&counters[by], 1u) == (unsigned)gx - 1;
+    last = atomicAdd(counter, 1u) == (unsigned)gx - 1;
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
-  if (threadIdx.x < 2 * CG) {
+  if (tid < 128) {
     double t = 0.0;
-    for (int k = 0; k < gx; ++k) t += partials[((size_t)by * gx + k) * 2 * CG + threadIdx.x];
-    const int c = threadIdx.x % CG;
-    if (c < nc) out[2 * (c0 + c) + (threadIdx.x >= CG ? 1 : 0)] = t;
+    for (int k = 0; k < gx; ++k) t += partials[(size_t)k * 128 + tid];
+    const int c = tid & 63;
+    if (c < R) out[2 * c + (tid >= 64 ? 1 : 0)] = t;
   }
-  if (threadIdx.x == 0) counters[by] = 0u;
+  if (tid == 0) *counter = 0u;
 }
 
-// V'[r][pos] = r'[r][perm[pos]] rounded to FP32
-__global__ void batch_gather_df_kernel(const int32_t* __restrict__ perm, const float2* __restrict__ src,
+// The FP32 work vectors of the low-precision batched solves are row-major,
+// V32[pos][R]: a port's right-hand sides are one contiguous row, so the
+// port-wise kernels (injection, port constants) and the band solves' row
+// blocks run along rows.  The caller's vectors (and the FP64 path's) stay
+// column-major; the two permuting copies transpose through a shared-memory
+// tile of 32 positions x R.
+__device__ __forceinline__ float to_f32(double v) { return (float)v; }
+__device__ __forceinline__ float to_f32(float2 v) { return v.x + v.y; }
+
+// dst[pos][r] = src[perm[pos]][r] rounded to FP32, both row-major (the
+// double-float residual h + l)
+__global__ void batch_gather_rr_kernel(const int32_t* __restrict__ perm, const float2* __restrict__ src,
                                        float* __restrict__ dst, int64_t n, int R) {
   const int64_t total = n * R;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = i / n, pos = i % n;
-    const float2 v = src[r * n + perm[pos]];
+    const int64_t pos = i / R;
+    const int r = (int)(i % R);
+    const float2 v = src[(int64_t)perm[pos] * R + r];
     dst[i] = v.x + v.y;
   }
 }
 
-// x[r][node] (+)= 2^f_r d[r][iperm[node]] (the correction of the scaled
-// system, exact in FP64), and x'[r][node] = x 2^-f_r as a double-float
-__global__ void batch_scatter_df_kernel(const int32_t* __restrict__ iperm, const float* __restrict__ d,
-                                        double* __restrict__ x, float2* __restrict__ xdf,
-                                        const int* __restrict__ f, int64_t n, int R, int accumulate) {
-  const int64_t total = n * R;
+// dst[pos][r] = src[r][perm[pos]] rounded to FP32 (src FP64, or a
+// double-float pair h + l)
+template <class ST>
+__global__ void __launch_bounds__(256) batch_gather_rm_kernel(const int32_t* __restrict__ perm,
+                                                              const ST* __restrict__ src,
+                                                              float* __restrict__ dst, int64_t n, int R) {
+  __shared__ float tile[32][65];
+  const int64_t p0 = (int64_t)blockIdx.x * 32;
+  const int np = (int)(n - p0 < 32 ? n - p0 : 32);
+  const int pl = threadIdx.x & 31;
+  if (pl < np) {
+    const int64_t node = perm[p0 + pl];
+    for (int r = threadIdx.x >> 5; r < R; r += 8) tile[pl][r] = to_f32(src[(int64_t)r * n + node]);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < np * R; e += blockDim.x) dst[p0 * R + e] = tile[e / R][e % R];
+}
+
+// x[r][node] (+)= d[iperm[node]][r] (DF: times 2^f_r, exact in FP64, and
+// x'[node][r] = x 2^-f_r as a double-float, row-major through a second tile)
+template <bool DF>
+__global__ void __launch_bounds__(256) batch_scatter_rm_kernel(const int32_t* __restrict__ iperm,
+                                                               const float* __restrict__ d,
+                                                               double* __restrict__ x, float2* __restrict__ xdf,
+                                                               const int* __restrict__ f, int64_t n, int R,
+                                                               int accumulate) {
+  __shared__ float tile[32][65];
+  __shared__ float2 tdf[DF ? 32 : 1][DF ? 65 : 1];
+  const int64_t n0 = (int64_t)blockIdx.x * 32;
+  const int nn = (int)(n - n0 < 32 ? n - n0 : 32);
+  for (int e = threadIdx.x; e < nn * R; e += blockDim.x) {
+    const int nl = e / R, r = e % R;
+    tile[nl][r] = d[(int64_t)iperm[n0 + nl] * R + r];
+  }
+  __syncthreads();
+  const int nl = threadIdx.x & 31;
+  if (nl < nn) {
+    for (int r = threadIdx.x >> 5; r < R; r += 8) {
+      const int64_t i = (int64_t)r * n + n0 + nl;
+      if (DF) {
+        const int fr = f[r];
+        const double v = double_from_float(tile[nl][r], fr);
+        const double xn = accumulate ? x[i] + v : v;
+        x[i] = xn;
+        tdf[nl][r] = df_from_double(xn, fr);
+      } else {
+        const double v = (double)tile[nl][r];
+        if (accumulate) x[i] += v;
+        else x[i] = v;
+      }
+    }
+  }
+  if (DF) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < nn * R; e += blockDim.x) xdf[n0 * R + e] = tdf[e / R][e % R];
+  }
+}
+
+// V32[pos(node)][r] += sum over the node's ports of beta_s w_in[s][r], in FP32
+// (beta in FP32: GB300's FP64 pipe would bound the kernel, and the rounding
+// is far below what the FP32 / 16-bit sweeps carry)
+__global__ void batch_inject_rm_kernel(const int32_t* __restrict__ port_pos, const uint8_t* __restrict__ run,
+                                       const float* __restrict__ beta, const float* __restrict__ st,
+                                       float* __restrict__ V, int64_t nports, int R) {
+  const int64_t total = nports * R;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = i / n, node = i % n;
-    const int fr = f[r];
-    const double v = double_from_float(d[r * n + iperm[node]], fr);
-    const double xn = accumulate ? x[i] + v : v;
-    x[i] = xn;
-    xdf[i] = df_from_double(xn, fr);
+    const int64_t s = i / R;
+    const int r = (int)(i % R);
+    const int nr = run[s];
+    if (!nr) continue;
+    float acc = 0.f;
+    for (int q = 0; q < nr; ++q) acc = fmaf(beta[s + q], st[(s + q) * 2 * R + r], acc);
+    V[(int64_t)port_pos[s] * R + r] += acc;
+  }
+}
+
+// c[s][r] = (2 W beta_s / d_s) x0[pos(s)][r], x0 row-major FP32, in FP32
+__global__ void batch_const_rm_kernel(const int32_t* __restrict__ port_pos, const float* __restrict__ bout,
+                                      const float* __restrict__ x0, float* __restrict__ c, int64_t nports,
+                                      int R) {
+  const int64_t total = nports * R;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = i / R;
+    const int r = (int)(i % R);
+    c[i] = bout[s] * x0[(int64_t)port_pos[s] * R + r];
   }
 }
 
@@ -358,7 +476,7 @@ __global__ void batch_band_solve_kernel(const int32_t* __restrict__ node_off,
                                         const int32_t* __restrict__ bwv,
                                         const int64_t* __restrict__ band_off,
                                         const FT* __restrict__ Lc, const FT* __restrict__ Uc,
-                                        FT* __restrict__ V, int R) {
+                                        FT* __restrict__ V, int R, int64_t rs, int64_t cs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ngroups = (R + RG - 1) / RG;
   const int t = blockIdx.x / ngroups;
@@ -374,10 +492,9 @@ __global__ void batch_band_solve_kernel(const int32_t* __restrict__ node_off,
   // column-major in shared memory, v[c * n + row]: at every step the threads
   // (band offsets) touch consecutive rows of a column, without bank conflicts
   FT* v = reinterpret_cast<FT*>(smem_raw);
-  const int64_t ntot = (int64_t)node_off[gridDim.x / ngroups];  // all nodes (column stride)
   for (int i = tid; i < n * RG; i += blockDim.x) {
     const int c = i / n, row = i % n;
-    v[i] = c < rg ? V[(int64_t)(r0 + c) * ntot + base + row] : FT(0);
+    v[i] = c < rg ? V[(int64_t)(base + row) * rs + (int64_t)(r0 + c) * cs] : FT(0);
   }
   __syncthreads();
   const int a = tid + 1;  // band offset of this thread
@@ -428,7 +545,7 @@ __global__ void batch_band_solve_kernel(const int32_t* __restrict__ node_off,
   }
   for (int i = tid; i < n * RG; i += blockDim.x) {
     const int c = i / n, row = i % n;
-    if (c < rg) V[(int64_t)(r0 + c) * ntot + base + row] = v[i] * uc[(size_t)row * B];
+    if (c < rg) V[(int64_t)(base + row) * rs + (int64_t)(r0 + c) * cs] = v[i] * uc[(size_t)row * B];
   }
 }
 
@@ -450,7 +567,7 @@ __global__ void batch_band_solve_win_kernel(const int32_t* __restrict__ node_off
                                             const int32_t* __restrict__ bwv,
                                             const int64_t* __restrict__ band_off,
                                             const float* __restrict__ Lc, const float* __restrict__ Uc,
-                                            float* __restrict__ V, int R) {
+                                            float* __restrict__ V, int R, int64_t rs, int64_t cs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ngroups = (R + RG - 1) / RG;
   const int t = blockIdx.x / ngroups;
@@ -463,18 +580,17 @@ __global__ void batch_band_solve_win_kernel(const int32_t* __restrict__ node_off
   const int WB = bw + 1 + PF;  // window rows
   const float* lc = Lc + band_off[t];
   const float* uc = Uc + band_off[t];
-  const int64_t ntot = (int64_t)node_off[gridDim.x / ngroups];
   const int tid = threadIdx.x;
   float* win = reinterpret_cast<float*>(smem_raw);  // win[c * WB + row % WB]
   const int a = tid + 1;
   const bool act = a <= bw;
   const bool loader = tid < RG;  // thread c moves column c in and out
   const int c = tid;
-  float* Vc = V + (int64_t)(r0 + min(c, RG - 1)) * ntot + base;
+  float* Vc = V + (int64_t)base * rs + (int64_t)(r0 + min(c, RG - 1)) * cs;  // row j at Vc[j rs]
   // ---- forward: rows [j, j + WB) in the window ----
   for (int i = tid; i < min(WB, n) * RG; i += blockDim.x) {
     const int cc = i / min(WB, n), row = i % min(WB, n);
-    win[cc * WB + row] = cc < rg ? V[(int64_t)(r0 + cc) * ntot + base + row] : 0.f;
+    win[cc * WB + row] = cc < rg ? V[(int64_t)(base + row) * rs + (int64_t)(r0 + cc) * cs] : 0.f;
   }
   float pf[D], dg[D];
 #pragma unroll
@@ -501,8 +617,8 @@ __global__ void batch_band_solve_win_kernel(const int32_t* __restrict__ node_off
           // row j is final: store y_j; bring row j + WB into its slot (first
           // used PF steps from now)
           const int slot = j % WB;
-          if (c < rg) Vc[j] = win[c * WB + slot] * dg[d];
-          if (j + WB < n && c < rg) cp_async4(&win[c * WB + slot], Vc + j + WB);
+          if (c < rg) Vc[(int64_t)j * rs] = win[c * WB + slot] * dg[d];
+          if (j + WB < n && c < rg) cp_async4(&win[c * WB + slot], Vc + (int64_t)(j + WB) * rs);
           cp_async_commit();
           dg[d] = jn < n ? lc[(size_t)jn * B] : 0.f;
           cp_async_wait<PF - 1>();
@@ -517,7 +633,7 @@ __global__ void batch_band_solve_win_kernel(const int32_t* __restrict__ node_off
   for (int i = tid; i < min(WB, n) * RG; i += blockDim.x) {
     const int cc = i / min(WB, n), k = i % min(WB, n);
     const int row = n - 1 - k;
-    win[cc * WB + row % WB] = cc < rg ? V[(int64_t)(r0 + cc) * ntot + base + row] : 0.f;
+    win[cc * WB + row % WB] = cc < rg ? V[(int64_t)(base + row) * rs + (int64_t)(r0 + cc) * cs] : 0.f;
   }
 #pragma unroll
   for (int d = 0; d < D; ++d) {
@@ -542,8 +658,8 @@ __global__ void batch_band_solve_win_kernel(const int32_t* __restrict__ node_off
         __syncthreads();
         if (loader) {
           const int slot = j % WB;
-          if (c < rg) Vc[j] = win[c * WB + slot] * dg[d];
-          if (j - WB >= 0 && c < rg) cp_async4(&win[c * WB + slot], Vc + j - WB);
+          if (c < rg) Vc[(int64_t)j * rs] = win[c * WB + slot] * dg[d];
+          if (j - WB >= 0 && c < rg) cp_async4(&win[c * WB + slot], Vc + (int64_t)(j - WB) * rs);
           cp_async_commit();
           dg[d] = jn >= 0 ? uc[(size_t)jn * B] : 0.f;
           cp_async_wait<PF - 1>();
@@ -658,6 +774,12 @@ __global__ void __launch_bounds__(kBkThreads) blk_inverse_kernel(
 __device__ __forceinline__ void cp_async16_cg(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
 }
+// 16-byte copy (both addresses 16-byte aligned), zero-filled when !ok
+__device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, bool ok) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(smem)), "l"(gmem),
+               "r"(ok ? 16 : 0)
+               : "memory");
+}
 // 4-byte copy, zero-filled when !ok (the source is then not read)
 __device__ __forceinline__ void cp_async4_zfill(void* smem, const void* gmem, bool ok) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(smem)), "l"(gmem),
@@ -671,15 +793,18 @@ __device__ __forceinline__ void cp_async4_zfill(void* smem, const void* gmem, bo
 // kBkStages chunks of 16 rows by cp.async, and the input rows of the next
 // block are fetched while the current one is multiplied.  Thread (ty, tx)
 // accumulates rows 4 ty .. 4 ty + 3, columns 4 tx .. 4 tx + 3 of the block.
-// Row-block moves between V and the ring map lane l of warp w, step m, to
-// row 8 (task & 7) + (l & 7), column 4 (task >> 3) + (l >> 3), task = w + 8 m
-// (conflict-free ring access; the same thread writes y in the forward pass
-// and reads it back in the backward pass).
+// V is addressed by strides (row-major FP32 work vectors: rs = R, cs = 1).
+// Row-block moves between V and the ring: with whole rows of 16-byte groups,
+// item e = tid + 256 m (m < 4) moves row e / 16, columns 4 (e % 16) .. + 3 as
+// one 16-byte copy; otherwise 4-byte copies map lane l of warp w, step m, to
+// row 8 (task & 7) + (l & 7), column 4 (task >> 3) + (l >> 3), task = w + 8 m.
+// Both are conflict-free on the ring, and in both the same thread writes y in
+// the forward pass and reads it back in the backward pass.
 __global__ void __launch_bounds__(kBkThreads, 2) batch_band_solve_blk_kernel(
     const int32_t* __restrict__ node_off, const int32_t* __restrict__ Wv,
     const int64_t* __restrict__ g_off, const int32_t* __restrict__ order,
     const float* __restrict__ Gf, const float* __restrict__ Gb, float* __restrict__ V, int R,
-    int64_t ntot) {
+    int64_t rs, int64_t cs) {
   extern __shared__ __align__(16) float bsm[];
   float* ring = bsm;
   float* gst = bsm + kBkS * kBkLd;
@@ -693,7 +818,9 @@ __global__ void __launch_bounds__(kBkThreads, 2) batch_band_solve_blk_kernel(
   const int nblk = (n + kBkNB - 1) / kBkNB;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int lane = tid & 31, warp = tid >> 5;
-  float* Vt = V + (int64_t)r0 * ntot + base;
+  float* Vt = V + (int64_t)base * rs + (int64_t)r0 * cs;  // (row g, column c) at Vt[g rs + c cs]
+  // row-major rows of whole 16-byte groups: 16-byte moves
+  const bool vec4 = cs == 1 && (rs & 3) == 0;
   const int Q = nblk * KC;
   for (int pass = 0; pass < 2; ++pass) {
     const float* G = (pass == 0 ? Gf : Gb) + g_off[t];
@@ -703,13 +830,25 @@ __global__ void __launch_bounds__(kBkThreads, 2) batch_band_solve_blk_kernel(
     auto load_v = [&](int b) {
       if (b >= nblk) return;
       const int s = blk_start(b);
+      if (vec4) {
+        // row-major with whole 16-byte groups: item e = tid + 256 m is row
+        // e / 16, columns 4 (e % 16) .. + 3 (a warp moves two 256-byte rows)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int e = tid + kBkThreads * m;
+          const int g = s + (e >> 4), c = 4 * (e & 15);
+          const bool ok = g < n && c < rg;
+          cp_async16_zfill(&ring[(g & (kBkS - 1)) * kBkLd + c], ok ? Vt + (int64_t)g * rs + c : Vt, ok);
+        }
+        return;
+      }
 #pragma unroll 4
       for (int m = 0; m < 16; ++m) {
         const int task = warp + 8 * m;
         const int g = s + 8 * (task & 7) + (lane & 7);
         const int c = 4 * (task >> 3) + (lane >> 3);
         const bool ok = g < n && c < rg;
-        cp_async4_zfill(&ring[(g & (kBkS - 1)) * kBkLd + c], ok ? Vt + (int64_t)c * ntot + g : Vt, ok);
+        cp_async4_zfill(&ring[(g & (kBkS - 1)) * kBkLd + c], ok ? Vt + (int64_t)g * rs + (int64_t)c * cs : Vt, ok);
       }
     };
     auto load_chunk = [&](int q) {
@@ -764,12 +903,23 @@ __global__ void __launch_bounds__(kBkThreads, 2) batch_band_solve_blk_kernel(
           for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
         }
         __syncthreads();
+        if (vec4) {
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            const int e = tid + kBkThreads * m;
+            const int g = s + (e >> 4), c = 4 * (e & 15);
+            if (g < n && c < rg)
+              *reinterpret_cast<float4*>(Vt + (int64_t)g * rs + c) =
+                  *reinterpret_cast<const float4*>(&ring[(g & (kBkS - 1)) * kBkLd + c]);
+          }
+        } else {
 #pragma unroll 4
-        for (int m = 0; m < 16; ++m) {
-          const int task = warp + 8 * m;
-          const int g = s + 8 * (task & 7) + (lane & 7);
-          const int c = 4 * (task >> 3) + (lane >> 3);
-          if (g < n && c < rg) Vt[(int64_t)c * ntot + g] = ring[(g & (kBkS - 1)) * kBkLd + c];
+          for (int m = 0; m < 16; ++m) {
+            const int task = warp + 8 * m;
+            const int g = s + 8 * (task & 7) + (lane & 7);
+            const int c = 4 * (task >> 3) + (lane >> 3);
+            if (g < n && c < rg) Vt[(int64_t)g * rs + (int64_t)c * cs] = ring[(g & (kBkS - 1)) * kBkLd + c];
+          }
         }
       }
     }
@@ -1749,7 +1899,7 @@ static vtm_status batch_band_solve_win(vtm_plan_s* P, float* V, int R, const flo
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   batch_band_solve_win_kernel<RG, D, PF><<<P->nparts * ngroups, threads, smem, P->stream>>>(
       P->tabs.node_off.as<int32_t>(), P->tabs.bw.as<int32_t>(), P->tabs.band_off.as<int64_t>(), Lc,
-      Uc, V, R);
+      Uc, V, R, (int64_t)R, (int64_t)1);
   P->launch_count++;
   VTM_CUDA_TRY(cudaGetLastError());
   return VTM_OK;
@@ -1806,7 +1956,8 @@ static vtm_status batch_band_solve_blk(vtm_plan_s* P, float* V, int R) {
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBkSmem));
   batch_band_solve_blk_kernel<<<P->nparts * ngroups, kBkThreads, kBkSmem, P->stream>>>(
       P->tabs.node_off.as<int32_t>(), P->d_bk_W.as<int32_t>(), P->d_bk_goff.as<int64_t>(),
-      P->d_bk_order.as<int32_t>(), P->d_bk_Gf.as<float>(), P->d_bk_Gb.as<float>(), V, R, P->n);
+      P->d_bk_order.as<int32_t>(), P->d_bk_Gf.as<float>(), P->d_bk_Gb.as<float>(), V, R, (int64_t)R,
+      (int64_t)1);
   P->launch_count++;
   VTM_CUDA_TRY(cudaGetLastError());
   return VTM_OK;
@@ -1830,9 +1981,11 @@ static vtm_status batch_band_solve(vtm_plan_s* P, FT* V, int R, const FT* Lc, co
   }
   VTM_CUDA_TRY(cudaFuncSetAttribute(batch_band_solve_kernel<FT, RG, D>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // FP32 work vectors are row-major ([position][column]), FP64 ones column-major
+  const int64_t rs = sizeof(FT) == 4 ? R : 1, cs = sizeof(FT) == 4 ? 1 : P->n;
   batch_band_solve_kernel<FT, RG, D><<<P->nparts * ngroups, threads, smem, P->stream>>>(
       P->tabs.node_off.as<int32_t>(), P->tabs.bw.as<int32_t>(), P->tabs.band_off.as<int64_t>(), Lc,
-      Uc, V, R);
+      Uc, V, R, rs, cs);
   P->launch_count++;
   VTM_CUDA_TRY(cudaGetLastError());
   return VTM_OK;
@@ -1856,11 +2009,22 @@ static vtm_status batch_norms(vtm_plan_s* P, const double* x, const double* b, d
     VTM_CUDA_TRY(cudaMemsetAsync(counters, 0, 64 * sizeof(double), P->stream));
     P->bres_init = true;
   }
-  if (dfb)
-    batch_residual_df_kernel<8, 2><<<gx * gy, 256, 0, P->stream>>>(
+  if (dfb) {
+    // one group of up to 64 columns, 32 rows per block and step
+    const int gr = (int)std::max<int64_t>(1, std::min<int64_t>((P->n + 31) / 32, 152 * 8));
+    VTM_TRY(dev_alloc(P->d_bres2, ((size_t)gr * 128 + 2 * 64 + 8) * sizeof(double)));
+    double* part2 = P->d_bres2.as<double>();
+    double* out2 = part2 + (size_t)gr * 128;
+    unsigned* cnt2 = reinterpret_cast<unsigned*>(out2 + 2 * 64);
+    if (!P->bres2_init) {
+      VTM_CUDA_TRY(cudaMemsetAsync(cnt2, 0, 8 * sizeof(double), P->stream));
+      P->bres2_init = true;
+    }
+    batch_residual_rows_kernel<<<gr, 256, 0, P->stream>>>(
         P->d_rowptr.as<int64_t>(), P->d_colidx.as<int32_t>(), P->d_vals_df.as<float2>(), dfx, dfb, dfr,
-        P->n, R, gx, gy, partials, counters, out);
-  else
+        P->n, R, gr, part2, cnt2, out2);
+    out = out2;
+  } else
     batch_residual_norms_kernel<<<gx * gy, 256, 0, P->stream>>>(
         P->d_rowptr.as<int64_t>(), P->d_colidx.as<int32_t>(), P->d_vals.as<double>(), x, b, r, P->n, R,
         gx, gy, partials, counters, out);
@@ -1978,8 +2142,8 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
     P->vals_df_state = ok ? 1 : 2;
     if (ok) {
       VTM_TRY(dev_alloc(P->d_vals_df, (size_t)std::max<int64_t>(P->nnz, 1) * sizeof(float2)));
-      batch_split_kernel<<<grid_n(P->nnz), 256, 0, s>>>(P->d_vals.as<double>(), nullptr,
-                                                         P->d_vals_df.as<float2>(), P->nnz, 1);
+      batch_split_kernel<<<grid_n(P->nnz), 256, 0, s>>>(P->d_vals.as<double>(), P->d_vals_df.as<float2>(),
+                                                         P->nnz);
       P->launch_count++;
     }
   }
@@ -2018,7 +2182,7 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
       sc[c] = std::ldexp(1.0, -fexp[c]);
     }
     VTM_CUDA_TRY(cudaMemcpyAsync(d_f, fexp.data(), R * sizeof(int), cudaMemcpyHostToDevice, s));
-    batch_split_kernel<<<grid_n(n * R), 256, 0, s>>>(d_b, d_f, bdf, n, R);
+    batch_split_rm_kernel<<<(unsigned)((n + 31) / 32), 256, 0, s>>>(d_b, d_f, bdf, n, R);
     P->launch_count += 2;
     VTM_TRY(batch_norms(P, nullptr, nullptr, nullptr, R, rr2, bb2, nullptr, bdf, rdf));
     for (int c = 0; c < R; ++c) bnorm[c] = std::ldexp(std::sqrt(bb2[c]), fexp[c]);
@@ -2037,13 +2201,16 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
   int sweeps_left = P->opts.max_sweeps;
   vtm_status result = VTM_ENOCONV;
   bool stalled = false;
-  // const / inject: one block per 32 ports
+  // const / inject on column-major FP64 vectors: one block per 32 ports;
+  // row-major FP32 vectors: transposing copies per 32 positions, port-wise
+  // kernels along the rows
   const int g1 = grid_n(n * R), g2 = (int)std::max<int64_t>(1, (npt + 31) / 32);
+  const int gt = (int)std::max<int64_t>(1, (n + 31) / 32), gp = grid_n(std::max<int64_t>(npt, 1) * R);
   for (int outer = 0; outer < max_outer; ++outer) {
     const double* rhs = outer == 0 ? d_b : r;
     if (f32_solves) {
-      if (dfres) batch_gather_df_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rdf, V32, n, R);
-      else batch_gather_kernel<float><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, V32, n, R);
+      if (dfres) batch_gather_rr_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rdf, V32, n, R);
+      else batch_gather_rm_kernel<double><<<gt, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, V32, n, R);
       P->launch_count++;
       VTM_TRY(batch_band_solve<float>(P, V32, R, P->d_Lc32.as<float>(), P->d_Uc32.as<float>()));
     } else {
@@ -2054,9 +2221,8 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
     int kc = 0, flag = 1;
     if (npt > 0) {
       if (f32_solves)
-        batch_const_kernel<float, float><<<g2, 256, 0, s>>>(P->d_port_pos.as<int32_t>(),
-                                                           P->d_bout.as<double>(), V32,
-                                                           P->d_bc.as<float>(), npt, R, n);
+        batch_const_rm_kernel<<<gp, 256, 0, s>>>(P->d_port_pos.as<int32_t>(), P->d_bout32.as<float>(), V32,
+                                                 P->d_bc.as<float>(), npt, R);
       else if (lowp)
         batch_const_kernel<double, float><<<g2, 256, 0, s>>>(P->d_port_pos.as<int32_t>(),
                                                             P->d_bout.as<double>(), V,
@@ -2262,11 +2428,11 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
       const int slot = kc & 1;
       P->launch_count += 2;
       if (f32_solves) {
-        if (dfres) batch_gather_df_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rdf, V32, n, R);
-        else batch_gather_kernel<float><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, V32, n, R);
-        batch_inject_kernel<float, float><<<g2, 256, 0, s>>>(
-            P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(), P->d_beta.as<double>(),
-            P->d_bstate.as<float>() + (size_t)slot * npt * 2 * R, V32, npt, R, n);
+        if (dfres) batch_gather_rr_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rdf, V32, n, R);
+        else batch_gather_rm_kernel<double><<<gt, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, V32, n, R);
+        batch_inject_rm_kernel<<<gp, 256, 0, s>>>(P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(),
+                                                  P->d_beta32.as<float>(),
+                                                  P->d_bstate.as<float>() + (size_t)slot * npt * 2 * R, V32, npt, R);
         VTM_TRY(batch_band_solve<float>(P, V32, R, P->d_Lc32.as<float>(), P->d_Uc32.as<float>()));
       } else {
         batch_gather_kernel<double><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, V, n, R);
@@ -2285,9 +2451,11 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
       if (outer == 0) info->first_sweep_converged = 1;
     }
     if (dfres)
-      batch_scatter_df_kernel<<<g1, 256, 0, s>>>(P->d_iperm.as<int32_t>(), V32, xacc, xdf, d_f, n, R, outer > 0);
+      batch_scatter_rm_kernel<true><<<gt, 256, 0, s>>>(P->d_iperm.as<int32_t>(), V32, xacc, xdf, d_f, n, R,
+                                                       outer > 0);
     else if (f32_solves)
-      batch_scatter_kernel<float><<<g1, 256, 0, s>>>(P->d_iperm.as<int32_t>(), V32, xacc, n, R, outer > 0);
+      batch_scatter_rm_kernel<false><<<gt, 256, 0, s>>>(P->d_iperm.as<int32_t>(), V32, xacc, nullptr, nullptr, n,
+                                                        R, outer > 0);
     else
       batch_scatter_kernel<double><<<g1, 256, 0, s>>>(P->d_iperm.as<int32_t>(), V, xacc, n, R, outer > 0);
     P->launch_count++;

@@ -587,6 +587,13 @@ vtm_status assemble_local(vtm_plan_s* P) {
   }
   VTM_TRY(upload(P->d_beta, bin, st));
   VTM_TRY(upload(P->d_bout, bout, st));
+  // FP32 copies for the port-wise kernels of the low-precision batched path
+  {
+    std::vector<float> b32(bin.begin(), bin.end()), o32(bout.begin(), bout.end());
+    VTM_TRY(upload(P->d_beta32, b32, st));
+    VTM_TRY(upload(P->d_bout32, o32, st));
+    VTM_CUDA_TRY(cudaStreamSynchronize(st));  // the host vectors are about to go
+  }
   VTM_TRY(upload(P->d_rho, rho, st));
   VTM_TRY(upload(P->d_kd, kd, st));
   VTM_TRY(upload(P->d_kd32, kd32, st));
@@ -787,12 +794,12 @@ std::vector<DevBuf*> vtm_plan_s::all_bufs() {
   return {&tabs.node_off, &tabs.bw, &tabs.band_off, &tabs.port_off, &tabs.T_off, &tabs.T_ld,
           &tabs.order, &d_rowptr, &d_colidx, &d_vals, &d_perm, &d_iperm, &d_Lc, &d_Uc, &d_Lc32, &d_Uc32, &d_v32,
           &d_port_loc, &d_port_pos, &d_tdesc,
-          &d_twin, &d_beta, &d_bout, &d_rho, &d_kd, &d_kd32, &d_run, &d_T64, &d_T32, &d_T16, &d_Tp32, &d_Tp16, &d_Tpdf, &d_dfstate, &d_cdf, &d_kddf, &d_nbr_off, &d_nbr, &d_done, &d_flow, &d_part4, &d_fstate32, &d_c64, &d_c32, &d_state64,
+          &d_twin, &d_beta, &d_bout, &d_beta32, &d_bout32, &d_rho, &d_kd, &d_kd32, &d_run, &d_T64, &d_T32, &d_T16, &d_Tp32, &d_Tp16, &d_Tpdf, &d_dfstate, &d_cdf, &d_kddf, &d_nbr_off, &d_nbr, &d_done, &d_flow, &d_part4, &d_fstate32, &d_c64, &d_c32, &d_state64,
           &d_state32, &d_v, &d_v2, &d_xacc, &d_r, &d_bcol, &d_partials, &d_ctrl, &d_hist,
           &d_err, &d_red, &d_in_off, &d_out_off, &d_in_src, &d_in_kind, &d_in_twin,
           &d_in_own_out, &d_in_loc, &d_res_perm, &d_res_run, &d_out_loc, &d_in_coef, &d_in_d,
           &d_in_sigma, &d_out_scale, &d_out_diag, &d_E_off, &d_E_ld, &d_E, &d_cg, &d_gin,
-          &d_gout, &d_in_tile, &d_item_tile, &d_item_m0, &d_item_order, &d_tc_items, &d_tc_off, &d_tc_order, &d_Ttc, &d_bk_W, &d_bk_goff, &d_bk_order, &d_bk_blk, &d_bk_Gf, &d_bk_Gb, &d_vals_df, &d_bdf, &d_rdf, &d_xdf, &d_bexp, &d_bV, &d_bV32, &d_bstate,
+          &d_gout, &d_in_tile, &d_item_tile, &d_item_m0, &d_item_order, &d_tc_items, &d_tc_off, &d_tc_order, &d_Ttc, &d_bk_W, &d_bk_goff, &d_bk_order, &d_bk_blk, &d_bk_Gf, &d_bk_Gb, &d_vals_df, &d_bdf, &d_rdf, &d_xdf, &d_bexp, &d_bres2, &d_bV, &d_bV32, &d_bstate,
           &d_bc, &d_bpart,
           &d_btol2, &d_bctrl, &d_bres, &d_stage_in[0], &d_stage_in[1], &d_stage_in[2],
           &d_stage_out[0], &d_stage_out[1], &d_stage_out[2]};

@@ -212,6 +212,7 @@ struct vtm_plan_s {
   vtm::DevBuf d_Lc32, d_Uc32, d_v32;       // FP32 factor copies and work vector (inner solves)
   vtm::DevBuf d_port_loc, d_port_pos, d_twin, d_beta, d_run, d_tdesc;  // d_beta: beta d
   vtm::DevBuf d_bout, d_rho, d_kd, d_kd32;  // per port: 2 W beta / d, reflection, (g/W, d)
+  vtm::DevBuf d_beta32, d_bout32;           // FP32 copies of beta d and 2 W beta / d
   vtm::DevBuf d_T64, d_T32, d_T16;         // reflection matrices (T^T blocks)
   vtm::DevBuf d_Tp32, d_Tp16;              // packed symmetric copies (symmetric plans)
   vtm::DevBuf d_Tpdf;                      // packed double-float copy (FP64 plans, kernel 12)
@@ -278,6 +279,8 @@ struct vtm_plan_s {
   vtm::DevBuf d_item_tile, d_item_m0, d_item_order, d_bV, d_bV32, d_bstate, d_bc, d_bpart, d_btol2,
       d_bctrl, d_bres;
   bool bres_init = false;
+  vtm::DevBuf d_bres2;  // the double-float residual's partials | out[128] | counter
+  bool bres2_init = false;
   int batch_tuned[4] = {0, 0, 0, 0};  // batched sweep variant + 1, per precision
   int batch_tuned_R[4] = {0, 0, 0, 0};  // right-hand sides it was tuned for
   int batch_used = 0;                   // batched sweep variant + 1 of the last batched solve
