@@ -203,24 +203,26 @@ __global__ void batch_split_kernel(const double* __restrict__ src, float2* __res
 // r' = b' - A x' for up to 64 scaled columns (b', x', r' row-major, [n][R];
 // x' = nullptr: x = 0), with ||r'_c||^2 and ||b'_c||^2, in double-float
 // arithmetic (Dot2 accumulation seeded with b', paired FP32 instructions for
-// two columns at a time).  The lanes lie along the rows: lane l of a warp
-// takes row slot l / 8 (four rows per warp) and columns 8 (l % 8) .. + 7, so
-// one load instruction of the warp reads four whole 512-byte rows of x'
-// (64 columns) and the rows' nonzeros are shared by their eight lanes.  One
-// group of up to 64 columns; block bx covers rows 32 bx .. + 31, then every
-// 32 gx.  Squares: FP32 per thread and across the lanes of a column, FP64 from
+// two columns at a time).  The lanes lie along the rows: with CG columns per
+// lane, LPR = 64 / CG lanes share a row (row slot l / LPR, columns CG (l %
+// LPR) .. + CG - 1), so one load instruction of the warp reads 32 / LPR whole
+// 512-byte rows of x' (64 columns) and a row's nonzeros serve its LPR lanes.
+// One group of up to 64 columns; block bx covers 8 (32 / LPR) rows per step.
+// CG = 4 (64 registers, four CTAs per SM) measured faster than CG = 8 (128
+// registers, two).  Squares: FP32 per thread and across the lanes of a column, FP64 from
 // the warp sums on, blocks added in a fixed order by the last block.
 // out[2 c] = ||r'_c||^2, out[2 c + 1] = ||b'_c||^2; counter 0 on entry, left 0.
-__global__ void __launch_bounds__(256, 2) batch_residual_rows_kernel(
+template <int CG, int MINB>
+__global__ void __launch_bounds__(256, MINB) batch_residual_rows_kernel(
     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
     const float2* __restrict__ vdf, const float2* __restrict__ xdf, const float2* __restrict__ bdf,
     float2* __restrict__ rdf, int64_t n, int R, int gx, double* __restrict__ partials,
     unsigned* __restrict__ counter, double* __restrict__ out) {
-  constexpr int CG = 8, NP = CG / 2;
+  constexpr int NP = CG / 2, LPR = 64 / CG, RPW = 32 / LPR;  // lanes per row, rows per warp
   __shared__ float red[128][8];
   __shared__ bool last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int c0 = CG * (lane & 7);
+  const int c0 = CG * (lane % LPR);
   const int nc = max(0, min(CG, R - c0));
   const bool vec = nc == CG && (R & 1) == 0;
   auto ld_row = [&](const float2* p, float2 (&o)[CG]) {
@@ -239,7 +241,8 @@ __global__ void __launch_bounds__(256, 2) batch_residual_rows_kernel(
   float rr[CG], bb[CG];
 #pragma unroll
   for (int c = 0; c < CG; ++c) rr[c] = bb[c] = 0.f;
-  for (int64_t i = (int64_t)blockIdx.x * 32 + warp * 4 + (lane >> 3); i < n; i += (int64_t)gx * 32) {
+  for (int64_t i = (int64_t)blockIdx.x * (8 * RPW) + warp * RPW + lane / LPR; i < n;
+       i += (int64_t)gx * (8 * RPW)) {
     dacc2 acc[NP];
     {
       float2 bv[CG];
@@ -310,15 +313,16 @@ __global__ void __launch_bounds__(256, 2) batch_residual_rows_kernel(
         if (c < nc) rp[c] = rv[c];
     }
   }
-  // per column: the four row slots of the warp (lanes l, l + 8, l + 16, l + 24)
+  // per column: the row slots of the warp (lanes l, l + LPR, ...)
 #pragma unroll
   for (int c = 0; c < CG; ++c) {
-    rr[c] += __shfl_xor_sync(0xffffffffu, rr[c], 8);
-    rr[c] += __shfl_xor_sync(0xffffffffu, rr[c], 16);
-    bb[c] += __shfl_xor_sync(0xffffffffu, bb[c], 8);
-    bb[c] += __shfl_xor_sync(0xffffffffu, bb[c], 16);
+#pragma unroll
+    for (int o = LPR; o < 32; o <<= 1) {
+      rr[c] += __shfl_xor_sync(0xffffffffu, rr[c], o);
+      bb[c] += __shfl_xor_sync(0xffffffffu, bb[c], o);
+    }
   }
-  if (lane < 8) {
+  if (lane < LPR) {
 #pragma unroll
     for (int c = 0; c < CG; ++c) {
       red[c0 + c][warp] = rr[c];
@@ -2010,8 +2014,8 @@ static vtm_status batch_norms(vtm_plan_s* P, const double* x, const double* b, d
     P->bres_init = true;
   }
   if (dfb) {
-    // one group of up to 64 columns, 32 rows per block and step
-    const int gr = (int)std::max<int64_t>(1, std::min<int64_t>((P->n + 31) / 32, 152 * 8));
+    // one group of up to 64 columns, 16 rows per block and step
+    const int gr = (int)std::max<int64_t>(1, std::min<int64_t>((P->n + 15) / 16, 152 * 8));
     VTM_TRY(dev_alloc(P->d_bres2, ((size_t)gr * 128 + 2 * 64 + 8) * sizeof(double)));
     double* part2 = P->d_bres2.as<double>();
     double* out2 = part2 + (size_t)gr * 128;
@@ -2020,7 +2024,7 @@ static vtm_status batch_norms(vtm_plan_s* P, const double* x, const double* b, d
       VTM_CUDA_TRY(cudaMemsetAsync(cnt2, 0, 8 * sizeof(double), P->stream));
       P->bres2_init = true;
     }
-    batch_residual_rows_kernel<<<gr, 256, 0, P->stream>>>(
+    batch_residual_rows_kernel<4, 4><<<gr, 256, 0, P->stream>>>(
         P->d_rowptr.as<int64_t>(), P->d_colidx.as<int32_t>(), P->d_vals_df.as<float2>(), dfx, dfb, dfr,
         P->n, R, gr, part2, cnt2, out2);
     out = out2;
