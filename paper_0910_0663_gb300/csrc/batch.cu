@@ -225,11 +225,14 @@ __global__ void __launch_bounds__(256, MINB) batch_residual_rows_kernel(
   const int c0 = CG * (lane % LPR);
   const int nc = max(0, min(CG, R - c0));
   const bool vec = nc == CG && (R & 1) == 0;
-  auto ld_row = [&](const float2* p, float2 (&o)[CG]) {
+  // STREAM: b', read once, marked evict-first (with the stores of r'), so
+  // that the rows of x' the neighbouring rows reuse stay in L2
+  auto ld_row = [&](const float2* p, float2 (&o)[CG], bool stream) {
     if (vec) {
 #pragma unroll
       for (int c = 0; c < CG; c += 2) {
-        const float4 q = *reinterpret_cast<const float4*>(p + c);
+        const float4 q = stream ? __ldcs(reinterpret_cast<const float4*>(p + c))
+                                : *reinterpret_cast<const float4*>(p + c);
         o[c] = make_float2(q.x, q.y);
         o[c + 1] = make_float2(q.z, q.w);
       }
@@ -246,7 +249,7 @@ __global__ void __launch_bounds__(256, MINB) batch_residual_rows_kernel(
     dacc2 acc[NP];
     {
       float2 bv[CG];
-      ld_row(bdf + i * R + c0, bv);
+      ld_row(bdf + i * R + c0, bv, true);
 #pragma unroll
       for (int p = 0; p < NP; ++p) {
         acc[p].S = make_float2(bv[2 * p].x, bv[2 * p + 1].x);
@@ -262,7 +265,7 @@ __global__ void __launch_bounds__(256, MINB) batch_residual_rows_kernel(
       int64_t jn = 0;
       if (q0 < q1) {
         a = vdf[q0];
-        ld_row(xdf + (int64_t)col[q0] * R + c0, xv);
+        ld_row(xdf + (int64_t)col[q0] * R + c0, xv, false);
       }
       if (q0 + 1 < q1) {
         jn = col[q0 + 1];
@@ -271,7 +274,7 @@ __global__ void __launch_bounds__(256, MINB) batch_residual_rows_kernel(
       for (int64_t q = q0; q < q1; ++q) {
         float2 xn[CG];
         const bool more = q + 1 < q1;
-        if (more) ld_row(xdf + jn * R + c0, xn);
+        if (more) ld_row(xdf + jn * R + c0, xn, false);
         int64_t jnn = 0;
         float2 ann = make_float2(0.f, 0.f);
         if (q + 2 < q1) {
@@ -306,7 +309,7 @@ __global__ void __launch_bounds__(256, MINB) batch_residual_rows_kernel(
     if (vec) {
 #pragma unroll
       for (int c = 0; c < CG; c += 2)
-        *reinterpret_cast<float4*>(rp + c) = make_float4(rv[c].x, rv[c].y, rv[c + 1].x, rv[c + 1].y);
+        __stcs(reinterpret_cast<float4*>(rp + c), make_float4(rv[c].x, rv[c].y, rv[c + 1].x, rv[c + 1].y));
     } else {
 #pragma unroll
       for (int c = 0; c < CG; ++c)
