@@ -2049,6 +2049,33 @@ static vtm_status batch_norms(vtm_plan_s* P, const double* x, const double* b, d
   return VTM_OK;
 }
 
+// A's values as double-float pairs, for the double-float residuals: built
+// once per set of values when every nonzero lies within 2^-100 .. 2^100 (the
+// scaled products then stay inside FP32's range); vals_df_state 1 = built,
+// 2 = out of range.
+vtm_status ensure_vals_df(vtm_plan_s* P) {
+  if (P->vals_df_state != 0) return VTM_OK;
+  bool ok = true;
+  for (double v : P->h_vals) {
+    int e = 0;
+    if (!std::isfinite(v)) ok = false;
+    else if (v != 0.0) std::frexp(v, &e);
+    if (!ok || e < -100 || e > 100) {
+      ok = false;
+      break;
+    }
+  }
+  P->vals_df_state = ok ? 1 : 2;
+  if (ok) {
+    VTM_TRY(dev_alloc(P->d_vals_df, (size_t)std::max<int64_t>(P->nnz, 1) * sizeof(float2)));
+    batch_split_kernel<<<grid_n(P->nnz), 256, 0, P->stream>>>(P->d_vals.as<double>(), P->d_vals_df.as<float2>(),
+                                                                P->nnz);
+    P->launch_count++;
+    VTM_CUDA_TRY(cudaGetLastError());
+  }
+  return VTM_OK;
+}
+
 vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, double tol,
                          vtm_info* info, bool record_hist) {
   cudaStream_t s = P->stream;
@@ -2133,27 +2160,8 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
   // error is removed by the next step like the sweeps' rounding)
   const bool f32_solves = lowp && P->d_Lc32.p;
   if (f32_solves) VTM_TRY(dev_alloc(P->d_bV32, (size_t)n * R * sizeof(float)));
-  // ... and the residuals in double-float when A's nonzeros lie within
-  // 2^-100 .. 2^100 (the scaled products then stay inside FP32's range)
-  if (f32_solves && P->vals_df_state == 0) {
-    bool ok = true;
-    for (double v : P->h_vals) {
-      int e = 0;
-      if (!std::isfinite(v)) ok = false;
-      else if (v != 0.0) std::frexp(v, &e);
-      if (!ok || e < -100 || e > 100) {
-        ok = false;
-        break;
-      }
-    }
-    P->vals_df_state = ok ? 1 : 2;
-    if (ok) {
-      VTM_TRY(dev_alloc(P->d_vals_df, (size_t)std::max<int64_t>(P->nnz, 1) * sizeof(float2)));
-      batch_split_kernel<<<grid_n(P->nnz), 256, 0, s>>>(P->d_vals.as<double>(), P->d_vals_df.as<float2>(),
-                                                         P->nnz);
-      P->launch_count++;
-    }
-  }
+  // ... and the residuals in double-float when A's nonzeros allow it
+  if (f32_solves) VTM_TRY(ensure_vals_df(P));
   const bool dfres = f32_solves && P->vals_df_state == 1;
   if (dfres) {
     VTM_TRY(dev_alloc(P->d_bdf, (size_t)n * R * sizeof(float2)));

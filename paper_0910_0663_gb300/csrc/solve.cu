@@ -187,11 +187,6 @@ __device__ double block_sum_value(double v) {
   return tot;
 }
 
-// The last CTA of sweep k closes the sweep: it records the residual of sweep
-// k-1 (reduced by that CTA in a fixed order) and decides whether to go on.
-// flag 1: converged, 2: sweep limit, 3: diverged or not finite, 4: stalled
-// (rounding floor of a low-precision inner solve); a flag already set (a
-// bounded wait that timed out) is kept.
 // The sweep a CTA of the one-warp-per-tile kernels runs: one counter per CTA
 // index after the control block (reset with it), counting the launches this
 // CTA index has started.  Every launch has the same grid and each counter is
@@ -205,6 +200,11 @@ __device__ __forceinline__ unsigned take_sweep_number(SweepCtrl* ctrl) {
   return t;
 }
 
+// The last CTA of sweep k closes the sweep: it records the residual of sweep
+// k-1 (reduced by that CTA in a fixed order) and decides whether to go on.
+// flag 1: converged, 2: sweep limit, 3: diverged or not finite, 4: stalled
+// (rounding floor of a low-precision inner solve); a flag already set (a
+// bounded wait that timed out) is kept.
 __device__ void sweep_decide(SweepCtrl* ctrl, int k, double tot, double* hist, int hist_len) {
   int flag = 0;
   if (k > 1) {

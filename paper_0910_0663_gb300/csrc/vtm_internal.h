@@ -343,6 +343,7 @@ vtm_status residual_pair(vtm_plan_s* P, const double* x, const double* b, double
                          double* bb);
 vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, double tol,
                          vtm_info* info, bool record_hist = false);
+vtm_status ensure_vals_df(vtm_plan_s* P);
 int launch_residual(const int64_t* rowptr, const int32_t* col, const double* val, const double* x,
                     const double* b, int64_t n, double* partials, unsigned* counter, double* out,
                     int max_grid, cudaStream_t s);
