@@ -117,7 +117,13 @@ __device__ double gblock_sum_array(const double* __restrict__ a, int count) {
   return gblock_sum(acc);
 }
 
-__global__ void __launch_bounds__(256) general_sweep_kernel(
+// One CTA per tile; the products run in KS groups of blockDim / KS threads:
+// group g takes the inputs a = g, g + KS, ... of each output, the KS partial
+// sums meet in shared memory and are added in group order (more loads in
+// flight per output than one thread walking every input: a tile's E_P streams
+// with only a few CTAs per SM).
+template <int KS>
+__global__ void __launch_bounds__(1024) general_sweep_kernel(
     const double* __restrict__ E, const int64_t* __restrict__ E_off, const int32_t* __restrict__ E_ld,
     const int32_t* __restrict__ in_off, const int32_t* __restrict__ out_off,
     const int32_t* __restrict__ in_src, const uint8_t* __restrict__ in_kind,
@@ -141,6 +147,7 @@ __global__ void __launch_bounds__(256) general_sweep_kernel(
   const int o0 = out_off[t], no = out_off[t + 1] - o0;
   double* vin = sm;       // [max_in]
   double* rc = sm + ni;   // [max_in]
+  double* part = rc + ni;  // [KS][blockDim / KS]
   const double* pin = gin + (size_t)((k - 1) & 1) * n_in;
   const double* pout = gout + (size_t)((k - 1) & 1) * n_out;
   double* cin = gin + (size_t)(k & 1) * n_in;
@@ -179,11 +186,22 @@ __global__ void __launch_bounds__(256) general_sweep_kernel(
   const double tile_sq = gblock_sum(sq);
   const double* Eb = E + E_off[t];
   const int ld = E_ld[t];
-  for (int q = threadIdx.x; q < no; q += blockDim.x) {
-    double acc = c[o0 + q];
+  const int to = (int)blockDim.x / KS, g = threadIdx.x / to, ql = threadIdx.x % to;
+  for (int q0 = 0; q0 < no; q0 += to) {
+    const int q = q0 + ql;
+    double acc = 0.0;
+    if (q < no) {
 #pragma unroll 4
-    for (int a = 0; a < ni; ++a) acc += __ldg(Eb + (size_t)a * ld + q) * vin[a];
-    cout_[o0 + q] = acc;
+      for (int a = g; a < ni; a += KS) acc += __ldg(Eb + (size_t)a * ld + q) * vin[a];
+    }
+    part[g * to + ql] = acc;
+    __syncthreads();
+    if (g == 0 && q < no) {
+      double tot = c[o0 + q];
+      for (int gg = 0; gg < KS; ++gg) tot += part[gg * to + ql];
+      cout_[o0 + q] = tot;
+    }
+    __syncthreads();
   }
   for (int q = threadIdx.x; q < ni; q += blockDim.x) cin[a0 + q] = vin[q];
   if (threadIdx.x == 0) {
@@ -264,17 +282,21 @@ vtm_status general_sweeps(vtm_plan_s* P, double bnorm2, double target2, int budg
   VTM_CUDA_TRY(cudaMemcpyAsync(P->d_ctrl.p, P->h_ctrl, sizeof(SweepCtrl), cudaMemcpyHostToDevice, s));
   VTM_CUDA_TRY(cudaMemsetAsync(P->d_gin.p, 0, 2 * std::max<int64_t>(P->n_in, 1) * sizeof(double), s));
   VTM_CUDA_TRY(cudaMemsetAsync(P->d_gout.p, 0, 2 * std::max<int64_t>(P->n_out, 1) * sizeof(double), s));
-  const int threads = P->max_out <= 64 ? 64 : (P->max_out <= 128 ? 128 : 256);
-  const size_t smem = 2 * (size_t)std::max(P->max_in, 1) * sizeof(double);
+  // four groups of up to 256 threads per tile (one output each; eight groups
+  // of 128 measured slower on the 1024^2 VCCS grid)
+  constexpr int KS = 4;
+  const int to = P->max_out <= 64 ? 64 : (P->max_out <= 128 ? 128 : 256);
+  const int threads = KS * to;
+  const size_t smem = (2 * (size_t)std::max(P->max_in, 1) + threads) * sizeof(double);
   if (smem > 48 * 1024)
-    VTM_CUDA_TRY(cudaFuncSetAttribute(general_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    VTM_CUDA_TRY(cudaFuncSetAttribute(general_sweep_kernel<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
   int launched = 0;
   while (true) {
     const int m = std::min(P->opts.check_every, budget + 1 - launched);
     VTM_CUDA_TRY(cudaEventRecord(P->evs0, s));
     for (int i = 0; i < m; ++i)
-      general_sweep_kernel<<<P->nparts, threads, smem, s>>>(
+      general_sweep_kernel<KS><<<P->nparts, threads, smem, s>>>(
           P->d_E.as<double>(), P->d_E_off.as<int64_t>(), P->d_E_ld.as<int32_t>(),
           P->d_in_off.as<int32_t>(), P->d_out_off.as<int32_t>(), P->d_in_src.as<int32_t>(),
           P->d_in_kind.as<uint8_t>(), P->d_in_twin.as<int32_t>(), P->d_in_own_out.as<int32_t>(),
