@@ -40,6 +40,22 @@ struct BatchCtrl {
   double first_ratio;
 };
 
+// sum of p[0], p[stride], ... p[(n-1) stride] (rows written by other CTAs of
+// this launch: read through L2) with four interleaved accumulators, so that
+// four loads are in flight per step; the order depends on n only
+__device__ __forceinline__ double ordered_sum_strided(const double* p, int n, int stride) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int k = 0;
+  for (; k + 4 <= n; k += 4) {
+    a0 += __ldcg(p + (size_t)k * stride);
+    a1 += __ldcg(p + (size_t)(k + 1) * stride);
+    a2 += __ldcg(p + (size_t)(k + 2) * stride);
+    a3 += __ldcg(p + (size_t)(k + 3) * stride);
+  }
+  for (; k < n; ++k) a0 += __ldcg(p + (size_t)k * stride);
+  return (a0 + a1) + (a2 + a3);
+}
+
 // ---------------------------------------------------------------------------
 // permutation between the caller's column-major n x R and [pos][R]
 // ---------------------------------------------------------------------------
@@ -147,8 +163,7 @@ __global__ void __launch_bounds__(256) batch_residual_norms_kernel(
   if (!last) return;
   __threadfence();
   if (threadIdx.x < 2 * CG) {
-    double t = 0.0;
-    for (int k = 0; k < gx; ++k) t += partials[((size_t)by * gx + k) * 2 * CG + threadIdx.x];
+    const double t = ordered_sum_strided(partials + (size_t)by * gx * 2 * CG + threadIdx.x, gx, 2 * CG);
     const int c = threadIdx.x % CG;
     if (c < nc) out[2 * (c0 + c) + (threadIdx.x >= CG ? 1 : 0)] = t;
   }
@@ -347,8 +362,7 @@ __global__ void __launch_bounds__(256, MINB) batch_residual_rows_kernel(
   if (!last) return;
   __threadfence();
   if (tid < 128) {
-    double t = 0.0;
-    for (int k = 0; k < gx; ++k) t += partials[(size_t)k * 128 + tid];
+    const double t = ordered_sum_strided(partials + tid, gx, 128);
     const int c = tid & 63;
     if (c < R) out[2 * c + (tid >= 64 ? 1 : 0)] = t;
   }
@@ -1067,24 +1081,14 @@ constexpr int kBGrp = 64;
 
 // out[r] = sum of rows[0..nrows)[r]: G slices of consecutive rows, each with
 // four interleaved accumulators, then the slices in order.  Called by every
-// thread of the CTA; scr holds at least 256 doubles (shared).  The rows were
-// written by other CTAs of this launch: read through L2.
+// thread of the CTA; scr holds at least 256 doubles (shared).
 __device__ void batch_ordered_sum(const double* rows, int nrows, int R, double* scr, double* out) {
   const int G = max(1, min((int)blockDim.x, 256) / R);
   const int t = threadIdx.x;
   if (t < G * R) {
     const int g = t / R, r = t % R;
     const int w0 = nrows * g / G, w1 = nrows * (g + 1) / G;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    int w = w0;
-    for (; w + 4 <= w1; w += 4) {
-      a0 += __ldcg(rows + (size_t)w * R + r);
-      a1 += __ldcg(rows + (size_t)(w + 1) * R + r);
-      a2 += __ldcg(rows + (size_t)(w + 2) * R + r);
-      a3 += __ldcg(rows + (size_t)(w + 3) * R + r);
-    }
-    for (; w < w1; ++w) a0 += __ldcg(rows + (size_t)w * R + r);
-    scr[g * R + r] = (a0 + a1) + (a2 + a3);
+    scr[g * R + r] = ordered_sum_strided(rows + (size_t)w0 * R + r, w1 - w0, R);
   }
   __syncthreads();
   for (int r = t; r < R; r += blockDim.x) {
@@ -2422,6 +2426,9 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
         else if (prec == VTM_PREC_BF16)
           go(batch_sweep_kernel<__nv_bfloat16, float, float>, 256, P->d_T16.as<__nv_bfloat16>(),
              P->d_bc.as<float>(), P->d_bstate.as<float>());
+        else if (prec == VTM_PREC_FP16 && getenv("VTM_BTM") && atoi(getenv("VTM_BTM")) == 8)
+          go(batch_sweep_kernel<__half, float, float, 8>, 128, P->d_T16.as<__half>(), P->d_bc.as<float>(),
+             P->d_bstate.as<float>());
         else if (prec == VTM_PREC_FP16)
           go(batch_sweep_kernel<__half, float, float>, 256, P->d_T16.as<__half>(), P->d_bc.as<float>(),
              P->d_bstate.as<float>());
@@ -2476,31 +2483,46 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
       }
       P->batch_used = kv + 1;
       // batches of check_every launches replayed from a CUDA graph when the
-      // plan has its own stream
+      // plan has its own stream, and quarter batches for the tail up to the
+      // sweeps this refinement step took in the previous solve (the launches
+      // up to the one that decides that sweep go out before the first poll)
       const int nb = P->opts.check_every;
+      const int snb = std::max(1, nb / 4);
       launch_batch(kv, true);
-      cudaGraphExec_t gexec = nullptr;
+      cudaGraphExec_t gexec = nullptr, gsmall = nullptr;
       if (P->stream && P->opts.graphs != 1) {
         SweepGraph& G = P->batch_graph[prec];
         const uint64_t key = ((uint64_t)kv << 56) ^ ((uint64_t)nb << 32) ^ ((uint64_t)R << 8) ^
                              (uint64_t)(uintptr_t)P->d_bstate.p ^ ((uint64_t)(uintptr_t)bhist << 3) ^
                              ((uint64_t)bhist_len << 40);
         if (!G.exec || G.key != key) {
-          if (G.exec) cudaGraphExecDestroy(G.exec);
-          G.exec = nullptr;
-          cudaGraph_t graph = nullptr;
-          VTM_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-          for (int i = 0; i < nb; ++i) launch_batch(kv);
-          VTM_CUDA_TRY(cudaStreamEndCapture(s, &graph));
-          if (cudaGraphInstantiate(&G.exec, graph, 0) != cudaSuccess) {
-            G.exec = nullptr;
-            cudaGetLastError();
-          } else {
-            G.key = key;
+          G.reset();
+          for (int g = 0; g < 2; ++g) {
+            cudaGraph_t graph = nullptr;
+            VTM_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            for (int i = 0; i < (g ? snb : nb); ++i) launch_batch(kv);
+            VTM_CUDA_TRY(cudaStreamEndCapture(s, &graph));
+            cudaGraphExec_t& ex = g ? G.small : G.exec;
+            if (cudaGraphInstantiate(&ex, graph, 0) != cudaSuccess) {
+              ex = nullptr;
+              cudaGetLastError();
+            }
+            cudaGraphDestroy(graph);
           }
-          cudaGraphDestroy(graph);
+          if (G.exec) G.key = key;
         }
         gexec = G.exec;
+        gsmall = G.small;
+      }
+      const int step = std::min(outer, 7);
+      const int hint = P->batch_hint[prec][step];
+      int reps = 1, sreps = 0;
+      if (gexec && hint > 0) {
+        const int need = std::min(hint + 2, sweeps_left + 2);
+        reps = std::min(need / nb, 64);
+        sreps = gsmall ? (need - reps * nb + snb - 1) / snb : 0;
+        if (!gsmall && reps * nb < need) ++reps;
+        if (reps + sreps == 0) reps = 1;
       }
       int launched = 0;
       BatchCtrl hc{};
@@ -2508,20 +2530,24 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
         const int m = gexec ? nb : std::min(nb, sweeps_left + 1 - launched);
         VTM_CUDA_TRY(cudaEventRecord(P->evs0, s));
         if (gexec) {
-          VTM_CUDA_TRY(cudaGraphLaunch(gexec, s));
+          for (int i = 0; i < reps; ++i) VTM_CUDA_TRY(cudaGraphLaunch(gexec, s));
+          for (int i = 0; i < sreps; ++i) VTM_CUDA_TRY(cudaGraphLaunch(gsmall, s));
         } else {
           for (int i = 0; i < m; ++i) launch_batch(kv);
         }
         VTM_CUDA_TRY(cudaGetLastError());
-        launched += m;
+        const int went = gexec ? reps * nb + sreps * snb : m;
+        launched += went;
         VTM_CUDA_TRY(cudaEventRecord(P->evs1, s));
         VTM_CUDA_TRY(cudaMemcpyAsync(&hc, P->d_bctrl.p, sizeof(hc), cudaMemcpyDeviceToHost, s));
         VTM_CUDA_TRY(cudaStreamSynchronize(s));
         float bms = 0.f;
         VTM_CUDA_TRY(cudaEventElapsedTime(&bms, P->evs0, P->evs1));
         P->sweep_ms += bms;
-        P->sweep_launch_count += m;
-        P->launch_count += m;
+        P->sweep_launch_count += went;
+        P->launch_count += went;
+        reps = 1;
+        sreps = 0;
         if (hc.flag || launched > sweeps_left) break;
       }
       flag = hc.flag;
@@ -2530,6 +2556,7 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
         return VTM_ETIMEOUT;
       }
       kc = (flag == 1 || flag == 4) ? hc.conv_sweep : std::min(hc.k - 1, sweeps_left);
+      P->batch_hint[prec][step] = kc;
       if (bhist) {
         std::vector<double> hh(bhist_len);
         VTM_CUDA_TRY(cudaMemcpyAsync(hh.data(), bhist, bhist_len * sizeof(double), cudaMemcpyDeviceToHost, s));

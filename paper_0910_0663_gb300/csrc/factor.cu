@@ -839,11 +839,9 @@ extern "C" vtm_status vtm_factor(vtm_plan_t P) {
   cudaSetDevice(P->device);
   P->factored = false;
   // captured sweep batches refer to the operator buffers: rebuild them
-  for (int i = 0; i < 3; ++i) {
-    if (P->sweep_graph[i].exec) cudaGraphExecDestroy(P->sweep_graph[i].exec);
-    if (P->batch_graph[i].exec) cudaGraphExecDestroy(P->batch_graph[i].exec);
-    P->sweep_graph[i] = SweepGraph{};
-    P->batch_graph[i] = SweepGraph{};
+  for (int i = 0; i < 4; ++i) {
+    P->sweep_graph[i].reset();
+    P->batch_graph[i].reset();
   }
   // the tiled copy of the tcgen05 batched sweep follows the factors
   dev_free(P->d_Ttc);

@@ -1191,9 +1191,9 @@ extern "C" vtm_status vtm_get_ports(vtm_plan_t P, int32_t* node, int32_t* remote
 extern "C" void vtm_destroy(vtm_plan_t P) {
   if (!P) return;
   if (P->transposed) vtm_destroy(P->transposed);
-  for (int i = 0; i < 3; ++i) {
-    if (P->sweep_graph[i].exec) cudaGraphExecDestroy(P->sweep_graph[i].exec);
-    if (P->batch_graph[i].exec) cudaGraphExecDestroy(P->batch_graph[i].exec);
+  for (int i = 0; i < 4; ++i) {
+    P->sweep_graph[i].reset();
+    P->batch_graph[i].reset();
   }
   for (DevBuf* b : P->all_bufs()) dev_free(*b);
   if (P->h_ctrl) cudaFreeHost(P->h_ctrl);

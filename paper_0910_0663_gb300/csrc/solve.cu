@@ -3140,46 +3140,60 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   }
   // Batches of check_every launches, captured once into a CUDA graph when the
   // plan has its own stream (launches past convergence or the sweep limit
-  // return at once, so full batches are always safe).
+  // return at once, so full batches are always safe), and a graph of a
+  // quarter batch for the tail up to a hinted count.
   const int batch = P->opts.check_every;
-  cudaGraphExec_t gexec = nullptr;
+  const int sbatch = std::max(1, batch / 4);
+  cudaGraphExec_t gexec = nullptr, gsmall = nullptr;
   if (P->stream && P->opts.graphs != 1) {
     SweepGraph& G = P->sweep_graph[prec];
     const uint64_t key = ((uint64_t)kern << 56) ^ ((uint64_t)(P->opts.pdl == 1) << 52) ^
                          ((uint64_t)batch << 32) ^ (uint64_t)(uintptr_t)hist ^ ((uint64_t)hist_len << 16);
     if (!G.exec || G.key != key) {
-      if (G.exec) cudaGraphExecDestroy(G.exec);
-      G.exec = nullptr;
-      cudaGraph_t graph = nullptr;
-      VTM_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      for (int i = 0; i < batch; ++i) launch_one(kern);
-      VTM_CUDA_TRY(cudaStreamEndCapture(s, &graph));
-      cudaError_t e = cudaGraphInstantiate(&G.exec, graph, 0);
-      cudaGraphDestroy(graph);
-      if (e != cudaSuccess) {
-        G.exec = nullptr;
-        cudaGetLastError();
-      } else {
-        G.key = key;
+      G.reset();
+      for (int g = 0; g < 2; ++g) {
+        cudaGraph_t graph = nullptr;
+        VTM_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        for (int i = 0; i < (g ? sbatch : batch); ++i) launch_one(kern);
+        VTM_CUDA_TRY(cudaStreamEndCapture(s, &graph));
+        cudaGraphExec_t& ex = g ? G.small : G.exec;
+        cudaError_t e = cudaGraphInstantiate(&ex, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+          ex = nullptr;
+          cudaGetLastError();
+        }
       }
+      if (G.exec) G.key = key;
     }
     gexec = G.exec;
+    gsmall = G.small;
   }
-  // hint: the sweeps the same refinement step took last time.  That many
-  // launches (whole batches) go out before the first poll of the flag: a
-  // poll costs a host round trip with the GPU idle, a launch that finds the
-  // solve converged returns at once.
+  // hint: the sweeps the same refinement step took last time.  The launches
+  // up to the one that decides that sweep (whole batches, then quarter
+  // batches; the dataflow kernels decide one launch later) go out before the
+  // first poll of the flag: a poll costs a host round trip with the GPU
+  // idle, a launch that finds the solve converged returns at once.
   int launched = 0;
-  int reps = gexec ? std::min(std::max(1, (hint + batch - 1) / batch), 64) : 1;
+  int reps = 1, sreps = 0;
+  if (gexec && hint > 0) {
+    const int need = std::min(hint + 2, budget + 2);
+    reps = std::min(need / batch, 64);
+    sreps = gsmall ? (need - reps * batch + sbatch - 1) / sbatch : 0;
+    if (!gsmall && reps * batch < need) ++reps;
+    if (reps + sreps == 0) reps = 1;
+  }
   while (true) {
     const int m = gexec ? batch : std::min(batch, budget + 1 - launched);
     VTM_CUDA_TRY(cudaEventRecord(P->evs0, s));
     if (gexec) {
       for (int i = 0; i < reps; ++i) VTM_CUDA_TRY(cudaGraphLaunch(gexec, s));
+      for (int i = 0; i < sreps; ++i) VTM_CUDA_TRY(cudaGraphLaunch(gsmall, s));
     } else {
       for (int i = 0; i < m; ++i) launch_one(kern);
     }
-    launched += m * reps;
+    const int went = gexec ? reps * batch + sreps * sbatch : m;
+    launched += went;
     VTM_CUDA_TRY(cudaGetLastError());
     VTM_CUDA_TRY(cudaEventRecord(P->evs1, s));
     VTM_CUDA_TRY(cudaMemcpyAsync(P->h_ctrl, P->d_ctrl.p, sizeof(SweepCtrl), cudaMemcpyDeviceToHost, s));
@@ -3187,9 +3201,10 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
     float bms = 0.f;
     VTM_CUDA_TRY(cudaEventElapsedTime(&bms, P->evs0, P->evs1));
     P->sweep_ms += bms;
-    P->sweep_launch_count += m * reps;
-    P->launch_count += m * reps;
+    P->sweep_launch_count += went;
+    P->launch_count += went;
     reps = 1;
+    sreps = 0;
     if (P->h_ctrl->flag || launched > budget) break;
   }
   const SweepCtrl& r = *P->h_ctrl;

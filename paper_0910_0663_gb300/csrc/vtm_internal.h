@@ -133,9 +133,18 @@ struct TileTables {
 
 namespace vtm {
 // A captured batch of sweep launches (CUDA graph) and what it was made for.
+// Captured sweep launches: `exec` replays check_every launches, `small` a
+// quarter of that (the tail up to a hinted sweep count)
 struct SweepGraph {
   cudaGraphExec_t exec = nullptr;
+  cudaGraphExec_t small = nullptr;
   uint64_t key = 0;
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (small) cudaGraphExecDestroy(small);
+    exec = small = nullptr;
+    key = 0;
+  }
 };
 }  // namespace vtm
 
@@ -241,6 +250,7 @@ struct vtm_plan_s {
   int dataflow_kernel = 8;  // kernel of the last sweeps run (8 or 10 for asynchronous VTM)
   float tuned_ms[4] = {0.f, 0.f, 0.f, 0.f};
   int sweep_hint[4][8] = {};  // sweeps of refinement step i of the last solve, per precision
+  int batch_hint[4][8] = {};  // the same for the batched solves
   vtm::SweepGraph sweep_graph[4];
   vtm::SweepGraph batch_graph[4];
   // per-call accounting (reset by each solve)
