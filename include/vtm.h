@@ -87,10 +87,11 @@ typedef struct {
   int precision;     /* VTM_PREC_*; default VTM_PREC_FP64 */
   int max_sweeps;    /* sweeps per vtm_solve call, all refinement steps together; default 200000 */
   int check_every;   /* sweeps launched between two host polls of the convergence flag; default 32.
-                        An inner solve (single-column or batched) first launches as many sweeps
-                        as the same refinement step took in the plan's previous solve, plus up
-                        to one decision launch, in groups of check_every and then of
-                        check_every / 4, then polls (launches past convergence return at once) */
+                        An inner solve (single-column or batched) first launches the sweeps
+                        the same refinement step took in the plan's previous solve and the
+                        launch that decides the last of them (with graphs: in groups of
+                        check_every, then of check_every / 4), then polls (launches past
+                        convergence return at once) */
   double inner_tol;  /* relative tolerance of each inner solve in the refinement modes;
                         0 -> 1e-5 (FP32) / 1e-3 (FP16) / 3e-3 (BF16).  An inner solve that can finish
                         the job (inner_tol x its right-hand side <= 4 tol ||b||) aims at

@@ -2266,7 +2266,9 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
   if (f32_solves) VTM_TRY(dev_alloc(P->d_bV32, (size_t)n * R * sizeof(float)));
   // ... and the residuals in double-float when A's nonzeros allow it
   if (f32_solves) VTM_TRY(ensure_vals_df(P));
-  const bool dfres = f32_solves && P->vals_df_state == 1;
+  // (a solve that stalls on the double-float residual's floor goes on with
+  // FP64 residuals: dfres changes once, between refinement steps)
+  bool dfres = f32_solves && P->vals_df_state == 1;
   if (dfres) {
     VTM_TRY(dev_alloc(P->d_bdf, (size_t)n * R * sizeof(float2)));
     VTM_TRY(dev_alloc(P->d_rdf, (size_t)n * R * sizeof(float2)));
@@ -2277,7 +2279,7 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
   }
   float* V32 = P->d_bV32.as<float>();
   double* xacc = P->d_xacc.as<double>();
-  double* r = P->d_r.as<double>();
+  double* r = P->d_r.as<double>();  // set again when a double-float solve switches to FP64
   float2* bdf = P->d_bdf.as<float2>();
   float2* rdf = P->d_rdf.as<float2>();
   float2* xdf = P->d_xdf.as<float2>();
@@ -2517,17 +2519,20 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
       const int step = std::min(outer, 7);
       const int hint = P->batch_hint[prec][step];
       int reps = 1, sreps = 0;
-      if (gexec && hint > 0) {
-        const int need = std::min(hint + 2, sweeps_left + 2);
+      const int need = hint > 0 ? std::min(hint + 1, sweeps_left + 1) : 0;  // launch k decides sweep k - 1
+      if (gexec && need > 0) {
         reps = std::min(need / nb, 64);
         sreps = gsmall ? (need - reps * nb + snb - 1) / snb : 0;
         if (!gsmall && reps * nb < need) ++reps;
         if (reps + sreps == 0) reps = 1;
       }
+      // without graphs the first round is the hinted count of single launches
+      int first = need;
       int launched = 0;
       BatchCtrl hc{};
       while (true) {
-        const int m = gexec ? nb : std::min(nb, sweeps_left + 1 - launched);
+        const int m = gexec ? nb : std::min(first > 0 ? first : nb, sweeps_left + 1 - launched);
+        first = 0;
         VTM_CUDA_TRY(cudaEventRecord(P->evs0, s));
         if (gexec) {
           for (int i = 0; i < reps; ++i) VTM_CUDA_TRY(cudaGraphLaunch(gexec, s));
@@ -2618,6 +2623,29 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
       worst = std::max(worst, rel[c]);
       if (!std::isfinite(rr)) bad = true;
       if (rnorm[c] > tol * bnorm[c]) all_ok = false;
+    }
+    if (stall && dfres && !all_ok && !bad) {
+      // the double-float residual resolves ||r|| only down to about
+      // 2^-48 || |A| |x| ||, and corrections formed from it stop there: the
+      // iterate's residual is measured in FP64, and unless that one meets the
+      // tolerance the next steps take their right-hand sides from FP64
+      // residuals (unscaled columns; the stall test restarts from this norm)
+      VTM_TRY(dev_alloc(P->d_r, (size_t)n * R * sizeof(double)));
+      r = P->d_r.as<double>();
+      std::vector<double> rr64, bb64;
+      VTM_TRY(batch_norms(P, xacc, d_b, r, R, rr64, bb64));
+      all_ok = true;
+      worst = 0.0;
+      for (int c = 0; c < R; ++c) {
+        rnorm[c] = std::sqrt(rr64[c]);
+        if (!(rnorm[c] <= tol * bnorm[c])) all_ok = false;
+        if (!std::isfinite(rr64[c])) bad = true;
+        worst = std::max(worst, bnorm[c] > 0 ? rnorm[c] / bnorm[c] : rnorm[c]);
+        fexp[c] = 0;
+        sc[c] = 1.0;
+      }
+      dfres = false;
+      stall = false;
     }
     info->relres = worst;
     if (flag == 3 || bad) {

@@ -3170,21 +3170,26 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
     gsmall = G.small;
   }
   // hint: the sweeps the same refinement step took last time.  The launches
-  // up to the one that decides that sweep (whole batches, then quarter
-  // batches; the dataflow kernels decide one launch later) go out before the
-  // first poll of the flag: a poll costs a host round trip with the GPU
-  // idle, a launch that finds the solve converged returns at once.
+  // up to the one that decides that sweep (launch k decides sweep k - 1; the
+  // dataflow kernels decide one launch later), as whole batches and then
+  // quarter batches, go out before the first poll of the flag: a poll costs a
+  // host round trip with the GPU idle, a launch that finds the solve
+  // converged returns at once.
   int launched = 0;
   int reps = 1, sreps = 0;
-  if (gexec && hint > 0) {
-    const int need = std::min(hint + 2, budget + 2);
+  const int lag = (kern == 9 || kern == 11) ? 2 : 1;  // launches past the hinted sweep
+  const int need = hint > 0 ? std::min(hint + lag, budget + lag) : 0;
+  if (gexec && need > 0) {
     reps = std::min(need / batch, 64);
     sreps = gsmall ? (need - reps * batch + sbatch - 1) / sbatch : 0;
     if (!gsmall && reps * batch < need) ++reps;
     if (reps + sreps == 0) reps = 1;
   }
+  // without graphs the first round is the hinted count of single launches
+  int first = need;
   while (true) {
-    const int m = gexec ? batch : std::min(batch, budget + 1 - launched);
+    const int m = gexec ? batch : std::min(first > 0 ? first : batch, budget + 1 - launched);
+    first = 0;
     VTM_CUDA_TRY(cudaEventRecord(P->evs0, s));
     if (gexec) {
       for (int i = 0; i < reps; ++i) VTM_CUDA_TRY(cudaGraphLaunch(gexec, s));
