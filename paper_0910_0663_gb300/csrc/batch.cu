@@ -227,21 +227,27 @@ __global__ void batch_split_kernel(const double* __restrict__ src, float2* __res
 // registers, two).  Squares: FP32 per thread and across the lanes of a column, FP64 from
 // the warp sums on, blocks added in a fixed order by the last block.
 // out[2 c] = ||r'_c||^2, out[2 c + 1] = ||b'_c||^2; counter 0 on entry, left 0.
+// r', rounded to FP32 (h + l), goes to the rows iperm[i] of v1 and v2 (when
+// given): the right-hand sides of the step's two band solves in the band
+// order.
 template <int CG, int MINB>
 __global__ void __launch_bounds__(256, MINB) batch_residual_rows_kernel(
     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
     const float2* __restrict__ vdf, const float2* __restrict__ xdf, const float2* __restrict__ bdf,
-    float2* __restrict__ rdf, int64_t n, int R, int gx, double* __restrict__ partials,
+    const int32_t* __restrict__ iperm, float* __restrict__ v1,
+    float* __restrict__ v2, int64_t n, int R, int gx, double* __restrict__ partials,
     unsigned* __restrict__ counter, double* __restrict__ out) {
   constexpr int NP = CG / 2, LPR = 64 / CG, RPW = 32 / LPR;  // lanes per row, rows per warp
+  static_assert(CG % 4 == 0, "column group of whole 16-byte FP32 groups");
   __shared__ float red[128][8];
   __shared__ bool last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int c0 = CG * (lane % LPR);
   const int nc = max(0, min(CG, R - c0));
   const bool vec = nc == CG && (R & 1) == 0;
-  // STREAM: b', read once, marked evict-first (with the stores of r'), so
-  // that the rows of x' the neighbouring rows reuse stay in L2
+  const bool vec4 = nc == CG && (R & 3) == 0;  // 16-byte FP32 row stores
+  // STREAM: b', read once, marked evict-first, so that the rows of x' the
+  // neighbouring rows reuse stay in L2
   auto ld_row = [&](const float2* p, float2 (&o)[CG], bool stream) {
     if (vec) {
 #pragma unroll
@@ -262,6 +268,7 @@ __global__ void __launch_bounds__(256, MINB) batch_residual_rows_kernel(
   for (int64_t i = (int64_t)blockIdx.x * (8 * RPW) + warp * RPW + lane / LPR; i < n;
        i += (int64_t)gx * (8 * RPW)) {
     dacc2 acc[NP];
+    const int pos = v1 ? iperm[i] : 0;
     {
       float2 bv[CG];
       ld_row(bdf + i * R + c0, bv, true);
@@ -320,15 +327,25 @@ __global__ void __launch_bounds__(256, MINB) batch_residual_rows_kernel(
         rr[2 * p + h] += v.h * v.h;
       }
     }
-    float2* rp = rdf + i * R + c0;
-    if (vec) {
+    if (v1) {
+      float o[CG];
 #pragma unroll
-      for (int c = 0; c < CG; c += 2)
-        __stcs(reinterpret_cast<float4*>(rp + c), make_float4(rv[c].x, rv[c].y, rv[c + 1].x, rv[c + 1].y));
-    } else {
+      for (int c = 0; c < CG; ++c) o[c] = rv[c].x + rv[c].y;
 #pragma unroll
-      for (int c = 0; c < CG; ++c)
-        if (c < nc) rp[c] = rv[c];
+      for (int k = 0; k < 2; ++k) {
+        float* vp = (k ? v2 : v1);
+        if (!vp) continue;
+        vp += (int64_t)pos * R + c0;
+        if (vec4) {
+#pragma unroll
+          for (int c = 0; c < CG; c += 4)
+            *reinterpret_cast<float4*>(vp + c) = make_float4(o[c], o[c + 1], o[c + 2], o[c + 3]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < CG; ++c)
+            if (c < nc) vp[c] = o[c];
+        }
+      }
     }
   }
   // per column: the row slots of the warp (lanes l, l + LPR, ...)
@@ -377,20 +394,6 @@ __global__ void __launch_bounds__(256, MINB) batch_residual_rows_kernel(
 // tile of 32 positions x R.
 __device__ __forceinline__ float to_f32(double v) { return (float)v; }
 __device__ __forceinline__ float to_f32(float2 v) { return v.x + v.y; }
-
-// dst[pos][r] = src[perm[pos]][r] rounded to FP32, both row-major (the
-// double-float residual h + l)
-__global__ void batch_gather_rr_kernel(const int32_t* __restrict__ perm, const float2* __restrict__ src,
-                                       float* __restrict__ dst, int64_t n, int R) {
-  const int64_t total = n * R;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t pos = i / R;
-    const int r = (int)(i % R);
-    const float2 v = src[(int64_t)perm[pos] * R + r];
-    dst[i] = v.x + v.y;
-  }
-}
 
 // dst[pos][r] = src[r][perm[pos]] rounded to FP32 (src FP64, or a
 // double-float pair h + l)
@@ -2099,7 +2102,7 @@ static vtm_status batch_band_solve(vtm_plan_s* P, FT* V, int R, const FT* Lc, co
 static vtm_status batch_norms(vtm_plan_s* P, const double* x, const double* b, double* r, int R,
                               std::vector<double>& rr, std::vector<double>& bb,
                               const float2* dfx = nullptr, const float2* dfb = nullptr,
-                              float2* dfr = nullptr) {
+                              float* v1 = nullptr, float* v2 = nullptr) {
   const int gx = (int)std::max<int64_t>(1, std::min<int64_t>((P->n + 255) / 256, 152 * 2));
   const int gy = (R + 7) / 8;
   // fixed layout for up to 8 column groups: partials | out[128] | counters
@@ -2123,8 +2126,8 @@ static vtm_status batch_norms(vtm_plan_s* P, const double* x, const double* b, d
       P->bres2_init = true;
     }
     batch_residual_rows_kernel<4, 4><<<gr, 256, 0, P->stream>>>(
-        P->d_rowptr.as<int64_t>(), P->d_colidx.as<int32_t>(), P->d_vals_df.as<float2>(), dfx, dfb, dfr,
-        P->n, R, gr, part2, cnt2, out2);
+        P->d_rowptr.as<int64_t>(), P->d_colidx.as<int32_t>(), P->d_vals_df.as<float2>(), dfx, dfb,
+        P->d_iperm.as<int32_t>(), v1, v2, P->n, R, gr, part2, cnt2, out2);
     out = out2;
   } else
     batch_residual_norms_kernel<<<gx * gy, 256, 0, P->stream>>>(
@@ -2270,8 +2273,10 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
   // FP64 residuals: dfres changes once, between refinement steps)
   bool dfres = f32_solves && P->vals_df_state == 1;
   if (dfres) {
+    // the residual kernel writes the step's two right-hand sides (FP32, band
+    // order) itself: V32 for the first band solve, V32b for the recovery
     VTM_TRY(dev_alloc(P->d_bdf, (size_t)n * R * sizeof(float2)));
-    VTM_TRY(dev_alloc(P->d_rdf, (size_t)n * R * sizeof(float2)));
+    VTM_TRY(dev_alloc(P->d_bV32b, (size_t)n * R * sizeof(float)));
     VTM_TRY(dev_alloc(P->d_xdf, (size_t)n * R * sizeof(float2)));
     VTM_TRY(dev_alloc(P->d_bexp, 2 * 64 * sizeof(int)));
   } else {
@@ -2281,7 +2286,7 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
   double* xacc = P->d_xacc.as<double>();
   double* r = P->d_r.as<double>();  // set again when a double-float solve switches to FP64
   float2* bdf = P->d_bdf.as<float2>();
-  float2* rdf = P->d_rdf.as<float2>();
+  float* V32b = P->d_bV32b.as<float>();
   float2* xdf = P->d_xdf.as<float2>();
   int* d_emax = P->d_bexp.as<int>();
   int* d_f = d_emax + 64;
@@ -2305,7 +2310,7 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
     VTM_CUDA_TRY(cudaMemcpyAsync(d_f, fexp.data(), R * sizeof(int), cudaMemcpyHostToDevice, s));
     batch_split_rm_kernel<<<(unsigned)((n + 31) / 32), 256, 0, s>>>(d_b, d_f, bdf, n, R);
     P->launch_count += 2;
-    VTM_TRY(batch_norms(P, nullptr, nullptr, nullptr, R, rr2, bb2, nullptr, bdf, rdf));
+    VTM_TRY(batch_norms(P, nullptr, nullptr, nullptr, R, rr2, bb2, nullptr, bdf, V32, V32b));
     for (int c = 0; c < R; ++c) bnorm[c] = std::ldexp(std::sqrt(bb2[c]), fexp[c]);
   } else {
     VTM_TRY(batch_norms(P, xacc, d_b, r, R, rr2, bb2));
@@ -2329,10 +2334,13 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
   const int gt = (int)std::max<int64_t>(1, (n + 31) / 32), gp = grid_n(std::max<int64_t>(npt, 1) * R);
   for (int outer = 0; outer < max_outer; ++outer) {
     const double* rhs = outer == 0 ? d_b : r;
+    float* Vx = V32;  // the FP32 vector the step's correction ends in
     if (f32_solves) {
-      if (dfres) batch_gather_rr_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rdf, V32, n, R);
-      else batch_gather_rm_kernel<double><<<gt, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, V32, n, R);
-      P->launch_count++;
+      // (double-float residuals: V32 already holds r' in the band order)
+      if (!dfres) {
+        batch_gather_rm_kernel<double><<<gt, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, V32, n, R);
+        P->launch_count++;
+      }
       VTM_TRY(batch_band_solve<float>(P, V32, R, P->d_Lc32.as<float>(), P->d_Uc32.as<float>()));
     } else {
       batch_gather_kernel<double><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, V, n, R);
@@ -2575,12 +2583,14 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
       const int slot = kc & 1;
       P->launch_count += 2;
       if (f32_solves) {
-        if (dfres) batch_gather_rr_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rdf, V32, n, R);
+        // the recovery's right-hand side: r' again (V32b from the residual
+        // kernel, or gathered) plus the ports' injections
+        if (dfres) Vx = V32b;
         else batch_gather_rm_kernel<double><<<gt, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, V32, n, R);
         batch_inject_rm_kernel<<<gp, 256, 0, s>>>(P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(),
                                                   P->d_beta32.as<float>(),
-                                                  P->d_bstate.as<float>() + (size_t)slot * npt * 2 * R, V32, npt, R);
-        VTM_TRY(batch_band_solve<float>(P, V32, R, P->d_Lc32.as<float>(), P->d_Uc32.as<float>()));
+                                                  P->d_bstate.as<float>() + (size_t)slot * npt * 2 * R, Vx, npt, R);
+        VTM_TRY(batch_band_solve<float>(P, Vx, R, P->d_Lc32.as<float>(), P->d_Uc32.as<float>()));
       } else {
         batch_gather_kernel<double><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, V, n, R);
         if (lowp)
@@ -2598,10 +2608,10 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
       if (outer == 0) info->first_sweep_converged = 1;
     }
     if (dfres)
-      batch_scatter_rm_kernel<true><<<gt, 256, 0, s>>>(P->d_iperm.as<int32_t>(), V32, xacc, xdf, d_f, n, R,
+      batch_scatter_rm_kernel<true><<<gt, 256, 0, s>>>(P->d_iperm.as<int32_t>(), Vx, xacc, xdf, d_f, n, R,
                                                        outer > 0);
     else if (f32_solves)
-      batch_scatter_rm_kernel<false><<<gt, 256, 0, s>>>(P->d_iperm.as<int32_t>(), V32, xacc, nullptr, nullptr, n,
+      batch_scatter_rm_kernel<false><<<gt, 256, 0, s>>>(P->d_iperm.as<int32_t>(), Vx, xacc, nullptr, nullptr, n,
                                                         R, outer > 0);
     else
       batch_scatter_kernel<double><<<g1, 256, 0, s>>>(P->d_iperm.as<int32_t>(), V, xacc, n, R, outer > 0);
@@ -2610,7 +2620,7 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
     info->outer_steps = outer + 1;
     bool all_ok = true, bad = false, stall = false;
     double worst = 0.0;
-    if (dfres) VTM_TRY(batch_norms(P, nullptr, nullptr, nullptr, R, rr2, bb2, xdf, bdf, rdf));
+    if (dfres) VTM_TRY(batch_norms(P, nullptr, nullptr, nullptr, R, rr2, bb2, xdf, bdf, V32, V32b));
     else VTM_TRY(batch_norms(P, xacc, d_b, r, R, rr2, bb2));
     for (int c = 0; c < R; ++c) {
       const double rr = rr2[c];

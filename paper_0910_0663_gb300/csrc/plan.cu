@@ -799,7 +799,7 @@ std::vector<DevBuf*> vtm_plan_s::all_bufs() {
           &d_err, &d_red, &d_in_off, &d_out_off, &d_in_src, &d_in_kind, &d_in_twin,
           &d_in_own_out, &d_in_loc, &d_res_perm, &d_res_run, &d_out_loc, &d_in_coef, &d_in_d,
           &d_in_sigma, &d_out_scale, &d_out_diag, &d_E_off, &d_E_ld, &d_E, &d_cg, &d_gin,
-          &d_gout, &d_in_tile, &d_item_tile, &d_item_m0, &d_item_order, &d_tc_items, &d_tc_off, &d_tc_order, &d_Ttc, &d_bk_W, &d_bk_goff, &d_bk_order, &d_bk_blk, &d_bk_Gf, &d_bk_Gb, &d_vals_df, &d_bdf, &d_rdf, &d_xdf, &d_bexp, &d_bres2, &d_bV, &d_bV32, &d_bstate,
+          &d_gout, &d_in_tile, &d_item_tile, &d_item_m0, &d_item_order, &d_tc_items, &d_tc_off, &d_tc_order, &d_Ttc, &d_bk_W, &d_bk_goff, &d_bk_order, &d_bk_blk, &d_bk_Gf, &d_bk_Gb, &d_vals_df, &d_bdf, &d_xdf, &d_bexp, &d_bres2, &d_bV, &d_bV32, &d_bV32b, &d_bstate,
           &d_bc, &d_bpart,
           &d_btol2, &d_bctrl, &d_bres, &d_stage_in[0], &d_stage_in[1], &d_stage_in[2],
           &d_stage_out[0], &d_stage_out[1], &d_stage_out[2]};

@@ -286,7 +286,7 @@ struct vtm_plan_s {
 
   // batched right-hand sides (batch.cu)
   std::vector<int32_t> item_tile, item_m0;
-  vtm::DevBuf d_item_tile, d_item_m0, d_item_order, d_bV, d_bV32, d_bstate, d_bc, d_bpart, d_btol2,
+  vtm::DevBuf d_item_tile, d_item_m0, d_item_order, d_bV, d_bV32, d_bV32b, d_bstate, d_bc, d_bpart, d_btol2,
       d_bctrl, d_bres;
   bool bres_init = false;
   vtm::DevBuf d_bres2;  // the double-float residual's partials | out[128] | counter
@@ -307,7 +307,7 @@ struct vtm_plan_s {
   // (h, l) pairs (state 0 not built, 1 built, 2 values out of range), the
   // scaled b, residual and iterate, per-column exponents
   int vals_df_state = 0;
-  vtm::DevBuf d_vals_df, d_bdf, d_rdf, d_xdf, d_bexp;
+  vtm::DevBuf d_vals_df, d_bdf, d_xdf, d_bexp;
   vtm::DevBuf d_bk_W, d_bk_goff, d_bk_order, d_bk_blk, d_bk_Gf, d_bk_Gb;
 
   // adjoint of an unsymmetric system
