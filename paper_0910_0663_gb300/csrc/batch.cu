@@ -1020,6 +1020,37 @@ __device__ __forceinline__ void ld4_smem(const double* p, double (&o)[4]) {
   o[0] = v0.x; o[1] = v0.y; o[2] = v1.x; o[3] = v1.y;
 }
 
+// four consecutive values from global memory (16-byte aligned for FP32 and
+// FP64, 8-byte for the 16-bit types), converted to the accumulate type
+__device__ __forceinline__ void ld4_cvt(const float* p, float (&o)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void ld4_cvt(const double* p, double (&o)[4]) {
+  const double2 v0 = *reinterpret_cast<const double2*>(p), v1 = *reinterpret_cast<const double2*>(p + 2);
+  o[0] = v0.x; o[1] = v0.y; o[2] = v1.x; o[3] = v1.y;
+}
+__device__ __forceinline__ void ld4_cvt(const __half* p, float (&o)[4]) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ void ld4_cvt(const __nv_bfloat16* p, float (&o)[4]) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+// four consecutive shared-memory values (16-byte aligned) as vector stores
+__device__ __forceinline__ void st4_smem(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4_smem(double* p, const double (&v)[4]) {
+  *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+}
+
 __device__ __forceinline__ float to_acc(float v) { return v; }
 __device__ __forceinline__ double to_acc(double v) { return v; }
 __device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162float(v); }
@@ -1224,58 +1255,8 @@ __global__ void __launch_bounds__(1024 / TM) batch_sweep_kernel(
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0;
   if (k > 1) {
-    // chunk loads are staged in registers one chunk ahead (NT threads x
-    // PT, PW elements of T and of W_in), so their latency hides behind the
-    // FMAs; the twin rows that W_in is read through are loaded one chunk
-    // earlier still, so that no load waits on another inside the loop
-    constexpr int PT = kKC * kMB / NT, PW = kKC * 64 / NT;
-    static_assert(PT * NT == kKC * kMB && PW * NT == kKC * 64, "chunk shape");
-    AT tv[PT], wv[PW];
-    int twv[PW];
-    auto fetch_twin = [&](int t0) {
-#pragma unroll
-      for (int e = 0; e < PW; ++e) {
-        const int t = t0 + (tid + e * NT) / 64;
-        twv[e] = t < p ? twin[p0 + t] : 0;
-      }
-    };
-    auto fetch = [&](int t0) {
-#pragma unroll
-      for (int e = 0; e < PT; ++e) {
-        const int i = tid + e * NT;
-        const int kk = i / kMB, mm = i % kMB;
-        const int t = t0 + kk, s = m0 + mm;
-        tv[e] = (t < p && s < m1) ? to_acc(Tb[(size_t)t * ld + s]) : AT(0);
-      }
-#pragma unroll
-      for (int e = 0; e < PW; ++e) {
-        const int i = tid + e * NT;
-        const int kk = i / 64, r = i % 64;
-        const int t = t0 + kk;
-        wv[e] = (t < p && r < R) ? (AT)prev[(size_t)twv[e] * 2 * R + R + r] : AT(0);
-      }
-    };
-    fetch_twin(0);
-    fetch(0);
-    fetch_twin(kKC);
-    // one barrier per chunk: buffer b is rewritten two chunks after it was
-    // read, and every thread has passed the barrier of the chunk between
-    for (int t0 = 0, b = 0; t0 < p; t0 += kKC, b ^= 1) {
-#pragma unroll
-      for (int e = 0; e < PT; ++e) {
-        const int i = tid + e * NT;
-        Ts[b][i / kMB][i % kMB] = tv[e];
-      }
-#pragma unroll
-      for (int e = 0; e < PW; ++e) {
-        const int i = tid + e * NT;
-        Ws[b][i / 64][i % 64] = wv[e];
-      }
-      __syncthreads();
-      if (t0 + kKC < p) {
-        fetch(t0 + kKC);
-        fetch_twin(t0 + 2 * kKC);
-      }
+    // acc += T(:, chunk)^T-block x W_in(chunk, :) from shared buffer b
+    auto fma_chunk = [&](int b) {
 #pragma unroll
       for (int kk = 0; kk < kKC; ++kk) {
         AT a[TM], bw[4];
@@ -1287,6 +1268,115 @@ __global__ void __launch_bounds__(1024 / TM) batch_sweep_kernel(
         for (int i = 0; i < TM; ++i)
 #pragma unroll
           for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bw[j];
+      }
+    };
+    // Chunk loads are staged in registers one chunk ahead, so their latency
+    // hides behind the FMAs; the twin rows that W_in is read through are
+    // loaded one chunk earlier still, so that no load waits on another inside
+    // the loop.  One barrier per chunk: buffer b is rewritten two chunks after
+    // it was read, and every thread has passed the barrier of the chunk
+    // between.  With R a multiple of 4 (and T's rows of whole 4-element
+    // groups, as the layout pads them to 8) every load and shared store moves
+    // a group of 4 consecutive outputs or right-hand sides: group g = tid +
+    // e NT of a chunk is row g / 16, elements 4 (g % 16) .. + 3.
+    const bool vec = (R & 3) == 0 && ((T_off[tile] | (int64_t)ld) & 3) == 0;
+    if (vec) {
+      constexpr int GT = kKC * 16 / NT;  // groups of T and of W_in per thread and chunk
+      static_assert(GT * NT == kKC * 16, "chunk groups");
+      AT tv[GT][4], wv[GT][4];
+      int twv[GT];
+      auto fetch_twin = [&](int t0) {
+#pragma unroll
+        for (int e = 0; e < GT; ++e) {
+          const int t = t0 + (tid + e * NT) / 16;
+          twv[e] = t < p ? twin[p0 + t] : 0;
+        }
+      };
+      auto fetch = [&](int t0) {
+#pragma unroll
+        for (int e = 0; e < GT; ++e) {
+          const int g = tid + e * NT;
+          const int t = t0 + g / 16, c4 = 4 * (g % 16);
+          if (t < p && m0 + c4 < m1) {
+            ld4_cvt(Tb + (size_t)t * ld + m0 + c4, tv[e]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) tv[e][j] = AT(0);
+          }
+          if (t < p && c4 < R) {
+            ld4_cvt(prev + (size_t)twv[e] * 2 * R + R + c4, wv[e]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) wv[e][j] = AT(0);
+          }
+        }
+      };
+      fetch_twin(0);
+      fetch(0);
+      fetch_twin(kKC);
+      for (int t0 = 0, b = 0; t0 < p; t0 += kKC, b ^= 1) {
+#pragma unroll
+        for (int e = 0; e < GT; ++e) {
+          const int g = tid + e * NT;
+          st4_smem(&Ts[b][g / 16][4 * (g % 16)], tv[e]);
+          st4_smem(&Ws[b][g / 16][4 * (g % 16)], wv[e]);
+        }
+        __syncthreads();
+        if (t0 + kKC < p) {
+          fetch(t0 + kKC);
+          fetch_twin(t0 + 2 * kKC);
+        }
+        fma_chunk(b);
+      }
+    } else {
+      // one element per load (NT threads x PT, PW elements of T and of W_in)
+      constexpr int PT = kKC * kMB / NT, PW = kKC * 64 / NT;
+      static_assert(PT * NT == kKC * kMB && PW * NT == kKC * 64, "chunk shape");
+      AT tv[PT], wv[PW];
+      int twv[PW];
+      auto fetch_twin = [&](int t0) {
+#pragma unroll
+        for (int e = 0; e < PW; ++e) {
+          const int t = t0 + (tid + e * NT) / 64;
+          twv[e] = t < p ? twin[p0 + t] : 0;
+        }
+      };
+      auto fetch = [&](int t0) {
+#pragma unroll
+        for (int e = 0; e < PT; ++e) {
+          const int i = tid + e * NT;
+          const int kk = i / kMB, mm = i % kMB;
+          const int t = t0 + kk, s = m0 + mm;
+          tv[e] = (t < p && s < m1) ? to_acc(Tb[(size_t)t * ld + s]) : AT(0);
+        }
+#pragma unroll
+        for (int e = 0; e < PW; ++e) {
+          const int i = tid + e * NT;
+          const int kk = i / 64, r = i % 64;
+          const int t = t0 + kk;
+          wv[e] = (t < p && r < R) ? (AT)prev[(size_t)twv[e] * 2 * R + R + r] : AT(0);
+        }
+      };
+      fetch_twin(0);
+      fetch(0);
+      fetch_twin(kKC);
+      for (int t0 = 0, b = 0; t0 < p; t0 += kKC, b ^= 1) {
+#pragma unroll
+        for (int e = 0; e < PT; ++e) {
+          const int i = tid + e * NT;
+          Ts[b][i / kMB][i % kMB] = tv[e];
+        }
+#pragma unroll
+        for (int e = 0; e < PW; ++e) {
+          const int i = tid + e * NT;
+          Ws[b][i / 64][i % 64] = wv[e];
+        }
+        __syncthreads();
+        if (t0 + kKC < p) {
+          fetch(t0 + kKC);
+          fetch_twin(t0 + 2 * kKC);
+        }
+        fma_chunk(b);
       }
     }
   }
@@ -2433,16 +2523,16 @@ vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, d
         if (prec == VTM_PREC_BF16 && (kv & 1))
           go(batch_sweep_mma_kernel, 128, P->d_T16.as<__nv_bfloat16>(), P->d_bc.as<float>(),
              P->d_bstate.as<float>());
+        // the 16-bit and FP32 CUDA-core sweeps: 8 x 4 outputs per thread (thermal
+        // grid, 64 columns: FP32 28.2 against 29.7 ms with 4 x 4, FP16 36.0
+        // against 38.4, BF16 36.5 against 38.9)
         else if (prec == VTM_PREC_BF16)
-          go(batch_sweep_kernel<__nv_bfloat16, float, float>, 256, P->d_T16.as<__nv_bfloat16>(),
+          go(batch_sweep_kernel<__nv_bfloat16, float, float, 8>, 128, P->d_T16.as<__nv_bfloat16>(),
              P->d_bc.as<float>(), P->d_bstate.as<float>());
-        else if (prec == VTM_PREC_FP16 && getenv("VTM_BTM") && atoi(getenv("VTM_BTM")) == 8)
+        else if (prec == VTM_PREC_FP16)
           go(batch_sweep_kernel<__half, float, float, 8>, 128, P->d_T16.as<__half>(), P->d_bc.as<float>(),
              P->d_bstate.as<float>());
-        else if (prec == VTM_PREC_FP16)
-          go(batch_sweep_kernel<__half, float, float>, 256, P->d_T16.as<__half>(), P->d_bc.as<float>(),
-             P->d_bstate.as<float>());
-        else if (prec == VTM_PREC_FP32)  // 8 x 4 outputs per thread: 32.8 vs 34.1 ms (4 x 4), thermal grid
+        else if (prec == VTM_PREC_FP32)
           go(batch_sweep_kernel<float, float, float, 8>, 128, P->d_T32.as<float>(), P->d_bc.as<float>(),
              P->d_bstate.as<float>());
         else
