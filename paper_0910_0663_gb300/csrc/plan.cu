@@ -792,7 +792,7 @@ using namespace vtm;
 
 std::vector<DevBuf*> vtm_plan_s::all_bufs() {
   return {&tabs.node_off, &tabs.bw, &tabs.band_off, &tabs.port_off, &tabs.T_off, &tabs.T_ld,
-          &tabs.order, &d_rowptr, &d_colidx, &d_vals, &d_perm, &d_iperm, &d_Lc, &d_Uc, &d_Lc32, &d_Uc32, &d_v32,
+          &tabs.order, &d_rowptr, &d_colidx, &d_vals, &d_perm, &d_iperm, &d_Lc, &d_Uc, &d_Lc32, &d_Uc32, &d_v32, &d_v32b, &d_ell_val, &d_ell_col, &d_ell_len,
           &d_port_loc, &d_port_pos, &d_tdesc,
           &d_twin, &d_beta, &d_bout, &d_beta32, &d_bout32, &d_rho, &d_kd, &d_kd32, &d_run, &d_T64, &d_T32, &d_T16, &d_Tp32, &d_Tp16, &d_Tpdf, &d_dfstate, &d_cdf, &d_kddf, &d_nbr_off, &d_nbr, &d_done, &d_flow, &d_part4, &d_fstate32, &d_c64, &d_c32, &d_state64,
           &d_state32, &d_v, &d_v2, &d_xacc, &d_r, &d_bcol, &d_partials, &d_ctrl, &d_hist,
@@ -1145,6 +1145,7 @@ extern "C" vtm_status vtm_set_values(vtm_plan_t P, const double* vals) {
   P->factored = false;
   dev_free(P->d_vals_df);
   P->vals_df_state = 0;
+  P->ell_state = 0;  // the ELL copy of A follows the values
   if (P->transposed) {
     vtm_destroy(P->transposed);
     P->transposed = nullptr;

@@ -233,27 +233,11 @@ __device__ void sweep_decide(SweepCtrl* ctrl, int k, double tot, double* hist, i
   if (ctrl->flag == 0) ctrl->flag = flag;
 }
 
-// r = b - A x (global order, FP64), ||r||^2 and ||b||^2 reduced in a fixed
-// order; out[0] = ||r||^2, out[1] = ||b||^2.  counter must be 0 on entry and
-// is left 0.
-__global__ void __launch_bounds__(256) residual_kernel(const int64_t* __restrict__ rowptr,
-                                                       const int32_t* __restrict__ col,
-                                                       const double* __restrict__ val,
-                                                       const double* __restrict__ x,
-                                                       const double* __restrict__ b,
-                                                       double* __restrict__ r, int64_t n,
-                                                       double* __restrict__ partials,
-                                                       unsigned* __restrict__ counter,
-                                                       double* __restrict__ out) {
-  double rr = 0.0, bb = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    double acc = b[i];
-    for (int64_t q = rowptr[i]; q < rowptr[i + 1]; ++q) acc -= val[q] * x[col[q]];
-    if (r) r[i] = acc;
-    rr += acc * acc;
-    bb += b[i] * b[i];
-  }
+// The norms of the residual kernels: per-thread sums rr, bb reduced per
+// block, then the last block adds the block partials in a fixed order into
+// out[0], out[1] and leaves the counter 0.
+__device__ void residual_norms_tail(double rr, double bb, double* __restrict__ partials,
+                                    unsigned* __restrict__ counter, double* __restrict__ out) {
   double trr = block_sum_value(rr);
   double tbb = block_sum_value(bb);
   __shared__ bool last;
@@ -276,6 +260,82 @@ __global__ void __launch_bounds__(256) residual_kernel(const int64_t* __restrict
   }
 }
 
+// r = b - A x (global order, FP64), ||r||^2 and ||b||^2 reduced in a fixed
+// order; out[0] = ||r||^2, out[1] = ||b||^2.  counter must be 0 on entry and
+// is left 0.
+__global__ void __launch_bounds__(256) residual_kernel(const int64_t* __restrict__ rowptr,
+                                                       const int32_t* __restrict__ col,
+                                                       const double* __restrict__ val,
+                                                       const double* __restrict__ x,
+                                                       const double* __restrict__ b,
+                                                       double* __restrict__ r, int64_t n,
+                                                       double* __restrict__ partials,
+                                                       unsigned* __restrict__ counter,
+                                                       double* __restrict__ out) {
+  double rr = 0.0, bb = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = b[i];
+    for (int64_t q = rowptr[i]; q < rowptr[i + 1]; ++q) acc -= val[q] * x[col[q]];
+    if (r) r[i] = acc;
+    rr += acc * acc;
+    bb += b[i] * b[i];
+  }
+  residual_norms_tail(rr, bb, partials, counter, out);
+}
+
+// The same residual with A in ELL form: entry k of row i at [k n + i]
+// (coalesced along the rows), rows shorter than K padded with (0, i).  The
+// products are taken in the row's CSR order and a padding entry subtracts an
+// exact zero, so r matches the CSR kernel bit for bit (for finite x).  With
+// v1 (and v2) r rounded to FP32 also goes to position iperm[i] of those
+// vectors: the band-order right-hand sides of an inner solve's two FP32 band
+// solves.
+template <int K>
+__global__ void __launch_bounds__(256) residual_ell_kernel(
+    const double* __restrict__ ev, const int32_t* __restrict__ ec, const double* __restrict__ x,
+    const double* __restrict__ b, double* __restrict__ r, int64_t n, const int32_t* __restrict__ iperm,
+    float* __restrict__ v1, float* __restrict__ v2, double* __restrict__ partials,
+    unsigned* __restrict__ counter, double* __restrict__ out) {
+  double rr = 0.0, bb = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double bi = b[i];
+    double av[K];
+    int cv[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      av[k] = ev[(int64_t)k * n + i];
+      cv[k] = ec[(int64_t)k * n + i];
+    }
+    double acc = bi;
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc -= av[k] * x[cv[k]];
+    if (r) r[i] = acc;
+    if (v1) {
+      const int pos = iperm[i];
+      v1[pos] = (float)acc;
+      if (v2) v2[pos] = (float)acc;
+    }
+    rr += acc * acc;
+    bb += bi * bi;
+  }
+  residual_norms_tail(rr, bb, partials, counter, out);
+}
+
+// A in ELL form ([k][n], K entries per row, short rows padded with (0, i))
+__global__ void ell_build_kernel(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                 const double* __restrict__ val, int64_t n, int K, double* __restrict__ ev,
+                                 int32_t* __restrict__ ec) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q0 = rowptr[i], len = rowptr[i + 1] - q0;
+    for (int k = 0; k < K; ++k) {
+      ev[(int64_t)k * n + i] = k < len ? val[q0 + k] : 0.0;
+      ec[(int64_t)k * n + i] = k < len ? col[q0 + k] : (int32_t)i;
+    }
+  }
+}
 // Host-side launcher of residual_kernel for other translation units; the
 // caller provides partials[2*grid], the counter word (0 on entry, left 0)
 // and out[2].  Returns the grid it used.
@@ -3236,23 +3296,64 @@ static vtm_status run_sweeps(vtm_plan_s* P, double bnorm2, double target2, int b
   return VTM_OK;
 }
 
-vtm_status residual_pair(vtm_plan_s* P, const double* x, const double* b, double* r, double* rr,
-                         double* bb);
 static vtm_status norms(vtm_plan_s* P, const double* x, const double* b, double* r, double* rr,
-                        double* bb) {
-  return residual_pair(P, x, b, r, rr, bb);
+                        double* bb, float* v1 = nullptr, float* v2 = nullptr) {
+  return residual_pair(P, x, b, r, rr, bb, v1, v2);
+}
+
+// The ELL copy of A for the single-column residual, built on first use after
+// each set of values when every row has at most 8 entries and the padding
+// stays under half of the nonzeros (else the CSR kernel serves)
+static vtm_status ensure_ell(vtm_plan_s* P) {
+  if (P->ell_state != 0) return VTM_OK;
+  int64_t maxlen = 0;
+  for (int64_t i = 0; i < P->n; ++i) maxlen = std::max(maxlen, P->h_rowptr[i + 1] - P->h_rowptr[i]);
+  if (maxlen < 1 || maxlen > 8 || P->n * maxlen > P->nnz + P->nnz / 2) {
+    P->ell_state = 2;
+    return VTM_OK;
+  }
+  P->ell_k = (int)maxlen;
+  VTM_TRY(dev_alloc(P->d_ell_val, (size_t)P->n * maxlen * sizeof(double)));
+  VTM_TRY(dev_alloc(P->d_ell_col, (size_t)P->n * maxlen * sizeof(int32_t)));
+  ell_build_kernel<<<grid_for(P->n), 256, 0, P->stream>>>(P->d_rowptr.as<int64_t>(), P->d_colidx.as<int32_t>(),
+                                                           P->d_vals.as<double>(), P->n, P->ell_k,
+                                                           P->d_ell_val.as<double>(), P->d_ell_col.as<int32_t>());
+  VTM_CUDA_TRY(cudaGetLastError());
+  P->launch_count++;
+  P->ell_state = 1;
+  return VTM_OK;
 }
 
 vtm_status residual_pair(vtm_plan_s* P, const double* x, const double* b, double* r, double* rr,
-                         double* bb) {
+                         double* bb, float* v1, float* v2) {
   cudaStream_t s = P->stream;
   const int grid = grid_for(P->n);
   double* out = P->d_red.as<double>() + 2;
   unsigned* counter = reinterpret_cast<unsigned*>(P->d_red.p);
+  VTM_TRY(ensure_ell(P));
+  if (v1 && P->ell_state != 1) return VTM_EINTERNAL;  // callers ask for v1 only with the ELL copy
+  if (v1 && !P->d_iperm.p) VTM_TRY(upload(P->d_iperm, P->iperm, s));
   P->launch_count++;
-  residual_kernel<<<grid, 256, 0, s>>>(P->d_rowptr.as<int64_t>(), P->d_colidx.as<int32_t>(),
-                                       P->d_vals.as<double>(), x, b, r, P->n,
-                                       P->d_partials.as<double>(), counter, out);
+  if (P->ell_state == 1) {
+    auto go = [&](auto kern) {
+      kern<<<grid, 256, 0, s>>>(P->d_ell_val.as<double>(), P->d_ell_col.as<int32_t>(), x, b, r, P->n,
+                                P->d_iperm.as<int32_t>(), v1, v2, P->d_partials.as<double>(), counter, out);
+    };
+    switch (P->ell_k) {
+      case 1: go(residual_ell_kernel<1>); break;
+      case 2: go(residual_ell_kernel<2>); break;
+      case 3: go(residual_ell_kernel<3>); break;
+      case 4: go(residual_ell_kernel<4>); break;
+      case 5: go(residual_ell_kernel<5>); break;
+      case 6: go(residual_ell_kernel<6>); break;
+      case 7: go(residual_ell_kernel<7>); break;
+      default: go(residual_ell_kernel<8>); break;
+    }
+  } else {
+    residual_kernel<<<grid, 256, 0, s>>>(P->d_rowptr.as<int64_t>(), P->d_colidx.as<int32_t>(),
+                                         P->d_vals.as<double>(), x, b, r, P->n,
+                                         P->d_partials.as<double>(), counter, out);
+  }
   VTM_CUDA_TRY(cudaGetLastError());
   double h[2];
   VTM_CUDA_TRY(cudaMemcpyAsync(h, out, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -3280,13 +3381,27 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
     VTM_TRY(dev_alloc(P->d_state32, 4 * std::max<int64_t>(npt, 1) * sizeof(float)));
   }
   double rr0, bb;
+  // BF16/FP16 steps run both band solves in FP32; with the ELL residual the
+  // residual kernel writes their right-hand sides (r rounded to FP32, band
+  // order) itself: v32 for the first solve, v32b for the recovery
+  VTM_TRY(ensure_ell(P));
+  const bool fuse = (prec == VTM_PREC_BF16 || prec == VTM_PREC_FP16) && !P->general && npt > 0 &&
+                    P->d_Lc32.p && P->ell_state == 1;
+  float* v32 = nullptr;
+  float* v32b = nullptr;
+  if (fuse) {
+    VTM_TRY(dev_alloc(P->d_v32, (size_t)n * sizeof(float)));
+    VTM_TRY(dev_alloc(P->d_v32b, (size_t)n * sizeof(float)));
+    v32 = P->d_v32.as<float>();
+    v32b = P->d_v32b.as<float>();
+  }
   // ||b||^2 and r = b - A x (x = 0 gives r = b)
   const bool warm = d_x0 != nullptr;
   if (warm)
     VTM_CUDA_TRY(cudaMemcpyAsync(xacc, d_x0, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   else
     VTM_CUDA_TRY(cudaMemsetAsync(xacc, 0, n * sizeof(double), s));
-  VTM_TRY(norms(P, xacc, d_b, r, &rr0, &bb));
+  VTM_TRY(norms(P, xacc, d_b, fuse ? nullptr : r, &rr0, &bb, v32, v32b));
   const double bnorm = std::sqrt(bb);
   info->sweeps = 0;
   info->outer_steps = 0;
@@ -3322,8 +3437,10 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
     const bool x0_f32 = prec != VTM_PREC_FP64 && !P->general && npt > 0 && P->d_Lc32.p;
     if (x0_f32) {
       VTM_TRY(dev_alloc(P->d_v32, (size_t)n * sizeof(float)));
-      gather_perm_f32_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, P->d_v32.as<float>(), n);
-      P->launch_count++;
+      if (!fuse) {
+        gather_perm_f32_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, P->d_v32.as<float>(), n);
+        P->launch_count++;
+      }
       launch_band_solve32(P, P->d_v32.as<float>(), 1, n, s);
     } else {
       gather_perm_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, v, n);
@@ -3394,11 +3511,11 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
       const float* slot32 = static_cast<const float*>(P->wave_slot);
       recovered_f32 = (prec == VTM_PREC_BF16 || prec == VTM_PREC_FP16) && x0_f32;
       if (recovered_f32) {
-        gather_perm_f32_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, P->d_v32.as<float>(), n);
+        float* vr = fuse ? v32b : P->d_v32.as<float>();
+        if (!fuse) gather_perm_f32_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, vr, n);
         inject_kernel<float, float><<<g2, 256, 0, s>>>(P->d_port_pos.as<int32_t>(), P->d_run.as<uint8_t>(),
-                                                      P->d_beta.as<double>(), slot32,
-                                                      P->d_v32.as<float>(), npt);
-        launch_band_solve32(P, P->d_v32.as<float>(), 1, n, s);
+                                                      P->d_beta.as<double>(), slot32, vr, npt);
+        launch_band_solve32(P, vr, 1, n, s);
       } else {
         gather_perm_kernel<<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), rhs, v, n);
         if (prec == VTM_PREC_FP64)
@@ -3415,15 +3532,15 @@ static vtm_status solve_one(vtm_plan_s* P, const double* d_b, double* d_x, doubl
       if (outer == 0) info->first_sweep_converged = 1;
     }
     if (recovered_f32)
-      scatter_perm_kernel<float><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), P->d_v32.as<float>(), xacc, n,
-                                                    accumulate);
+      scatter_perm_kernel<float><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), fuse ? v32b : P->d_v32.as<float>(),
+                                                    xacc, n, accumulate);
     else
       scatter_perm_kernel<double><<<g1, 256, 0, s>>>(P->d_perm.as<int32_t>(), v, xacc, n, accumulate);
     P->launch_count++;
     VTM_CUDA_TRY(cudaGetLastError());
     info->outer_steps = outer + 1;
     double rr;
-    VTM_TRY(norms(P, xacc, d_b, r, &rr, &bb));
+    VTM_TRY(norms(P, xacc, d_b, fuse ? nullptr : r, &rr, &bb, v32, v32b));
     const double rprev = rnorm;
     rnorm = std::sqrt(rr);
     info->relres = rnorm / bnorm;

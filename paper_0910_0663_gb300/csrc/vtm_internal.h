@@ -219,6 +219,11 @@ struct vtm_plan_s {
   vtm::DevBuf d_iperm;                     // int32[n] (batched solves)
   vtm::DevBuf d_Lc, d_Uc;                  // band factors (doubles)
   vtm::DevBuf d_Lc32, d_Uc32, d_v32;       // FP32 factor copies and work vector (inner solves)
+  vtm::DevBuf d_v32b;                      // second FP32 work vector (the recovery's right-hand side)
+  // A in ELL form for the single-column residual ([k][n] values and columns,
+  // row lengths): 0 not built, 1 built, 2 rows too uneven (CSR kernel)
+  vtm::DevBuf d_ell_val, d_ell_col, d_ell_len;
+  int ell_state = 0, ell_k = 0;
   vtm::DevBuf d_port_loc, d_port_pos, d_twin, d_beta, d_run, d_tdesc;  // d_beta: beta d
   vtm::DevBuf d_bout, d_rho, d_kd, d_kd32;  // per port: 2 W beta / d, reflection, (g/W, d)
   vtm::DevBuf d_beta32, d_bout32;           // FP32 copies of beta d and 2 W beta / d
@@ -350,7 +355,7 @@ vtm_status residual_norms(vtm_plan_s* P, const double* d_x, const double* d_b, i
                           double* rel);
 
 vtm_status residual_pair(vtm_plan_s* P, const double* x, const double* b, double* r, double* rr,
-                         double* bb);
+                         double* bb, float* v1 = nullptr, float* v2 = nullptr);
 vtm_status solve_batched(vtm_plan_s* P, const double* d_b, double* d_x, int R, double tol,
                          vtm_info* info, bool record_hist = false);
 vtm_status ensure_vals_df(vtm_plan_s* P);
