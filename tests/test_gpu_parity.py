@@ -213,6 +213,35 @@ def test_set_values_then_refactor(vtm):
     assert np.abs(x.cpu().numpy() - x_star).max() <= 1e-8 * np.abs(x_star).max()
 
 
+@pytest.mark.parametrize("hub", [False, True])
+@pytest.mark.parametrize("precision", ["fp64", "fp16"])
+def test_residual_in_both_matrix_forms(vtm, precision, hub):
+    # the single-column residual reads A in ELL form when every row has at
+    # most 8 entries (the 5-point grid) and in CSR form otherwise (a hub node
+    # tied to 12 more nodes, in its own tile and three others: a row of 15):
+    # in both the reported relative residual is the oracle's ||b - A x|| / ||b||
+    # of the returned x (up to the rounding of r at this level), and x solves
+    # A x = b
+    w = wl.grid2d(32, 32, 8, 8, seed=13)
+    edges, g = w.edges, w.g
+    if hub:
+        extra = np.array([[0, j] for j in (2, 3, 4, 5, 6, 7, 16, 24, 34, 40, 48, 56)], dtype=edges.dtype)
+        edges = np.concatenate([edges, extra])
+        g = np.concatenate([g, np.full(len(extra), 0.7)])
+    ip, ix, data = wl.assemble_nodal(w.n, edges, g, w.ground)
+    assert (np.diff(ip).max() > 8) == hub
+    plan = vtm.Plan(ip, ix, data, w.partition, w.nparts, Zc=1.0, precision=precision)
+    A = O.csr_matrix(ip, ix, data, w.n)
+    for _ in range(2):
+        x, info = plan.solve(torch.from_numpy(w.b[0]).cuda(), tol=1e-10)
+        xs = x.cpu().numpy()
+        rel = np.linalg.norm(w.b[0] - A @ xs) / np.linalg.norm(w.b[0])
+        assert rel <= 1e-10
+        assert abs(info["relres"] - rel) <= 0.1 * rel
+    x_star = np.linalg.solve(A.toarray(), w.b[0])
+    assert np.abs(xs - x_star).max() <= 1e-7 * np.abs(x_star).max()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16", "fp16"])
 def test_solves_before_and_after_a_refactor(vtm, precision):
     # the captured sweep graphs of every precision are rebuilt after a new
