@@ -46,6 +46,11 @@ def parse():
                          "64 RHS; vccs: 1024^2 grid with controlled sources, VTM and block Jacobi; "
                          "grad: 1024^2 grid, forward + adjoint solve + branch gradients")
     ap.add_argument("--grid", type=int, default=2048)
+    ap.add_argument("--thermal-grid", type=int, default=128,
+                    help="--workload thermal: the grid is N x N x 32 (a smaller case for profiling)")
+    ap.add_argument("--thermal-boxes", type=int, default=400, help="--workload thermal: the number of boxes")
+    ap.add_argument("--band-solve", type=int, default=0, choices=[0, 1],
+                    help="FP32 single-column band solve: 0 bulk-copy ring, 1 register prefetch (same bits)")
     ap.add_argument("--zc", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-kernel", type=int, default=0, choices=list(range(6)),
@@ -91,8 +96,9 @@ def admittance_config(args):
 def workload_config(args):
     l2 = "flushed (512 MB write) between timed steps"
     if args.workload == "thermal":
-        return {"workload": "RC thermal grid 128x128x32 (524288 unknowns), G + C/h, 400 random boxes "
-                            "(200-3000 nodes), Zc=1 ohm, 64 RHS", "n": 524288, "nrhs": 64, "tol": TOL,
+        tg, tb = args.thermal_grid, args.thermal_boxes
+        return {"workload": f"RC thermal grid {tg}x{tg}x32 ({tg * tg * 32} unknowns), G + C/h, {tb} random boxes "
+                            "(200-3000 nodes), Zc=1 ohm, 64 RHS", "n": tg * tg * 32, "nrhs": 64, "tol": TOL,
                 "seed": 0, "l2": l2}
     if args.workload == "vccs":
         return {"workload": "1024x1024 resistor grid + VCCS at 5% of nodes (unsymmetric), 256 tiles of 64x64, "
@@ -374,7 +380,9 @@ def gpu_arm(args):
     build.build()
     from paper_0910_0663_gb300 import workloads as wl
 
-    if args.workload == "thermal":
+    if args.workload == "thermal" and (args.thermal_grid, args.thermal_boxes) != (128, 400):
+        w = wl.thermal3d(32, args.thermal_grid, args.thermal_grid, args.thermal_boxes, nrhs=64, seed=0)
+    elif args.workload == "thermal":
         w = wl.c3_thermal(nrhs=64)
     elif args.workload == "vccs":
         w = wl.c4_vccs()
@@ -401,7 +409,8 @@ def gpu_arm(args):
             results[prec] = run_mode(prec, w, dev, stream, flush, world, args.steps, args.warmup,
                                      method="bj" if prec.startswith("bj_") else args.method, adm=adm,
                                      grad=args.workload == "grad", sweep_kernel=args.sweep_kernel,
-                                     l2_persist=args.l2_persist, e2e=True, batch_kernel=args.batch_kernel)
+                                     l2_persist=args.l2_persist, e2e=True, batch_kernel=args.batch_kernel,
+                                     band_solve=args.band_solve)
         except Exception as exc:  # a failing mode is reported, the others still run
             errors[prec] = repr(exc)
     if not results:
@@ -417,7 +426,7 @@ def gpu_arm(args):
 
 
 def run_mode(prec, w, dev, stream, flush, world, steps, warmup, method="vtm", adm=None, grad=False,
-             sweep_kernel=0, l2_persist=0, e2e=True, Zc=None, batch_kernel=0):
+             sweep_kernel=0, l2_persist=0, e2e=True, Zc=None, batch_kernel=0, band_solve=0):
     """Plan, factor and time one mode on workload w: `steps` solves after
     `warmup` untimed ones, L2 flushed before each; with e2e also the same
     solves through the C ABI with pinned host buffers.  The plan is closed
@@ -435,7 +444,7 @@ def run_mode(prec, w, dev, stream, flush, world, steps, warmup, method="vtm", ad
         plan = vtm.Plan(w.indptr, w.indices, w.data, w.partition, w.nparts, Zc=Zc,
                         precision=prec_name, device=dev, stream=stream, factor=False,
                         sweep_kernel=sweep_kernel, l2_persist=l2_persist, method=method,
-                        batch_kernel=batch_kernel)
+                        batch_kernel=batch_kernel, band_solve=band_solve)
         if adm is not None and method != "bj":
             plan.set_admittance(adm[0], alpha=adm[1], radius=adm[2], factor=False)
         t1 = time.perf_counter()
