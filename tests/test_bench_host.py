@@ -100,3 +100,20 @@ def test_reference_arm_prints_the_contract_line():
     assert line["config"]["workload"].startswith("power grid 512x512")
     assert line["config"]["sample_of"].startswith("power grid 2048x2048")
     assert line["config"]["n"] == bench.SAMPLE_N ** 2
+
+
+def test_profiling_options_name_their_workload(monkeypatch):
+    # the smaller thermal grid and the band-solve choice that the profile
+    # commands use reach the line's config; the defaults keep the benchmark's
+    # 128 x 128 x 32 grid with 400 boxes
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "thermal", "--thermal-grid", "96",
+                                      "--thermal-boxes", "225", "--band-solve", "1"])
+    args = bench.parse()
+    cfg = bench.workload_config(args)
+    assert args.band_solve == 1
+    assert cfg["n"] == 96 * 96 * 32 and "96x96x32" in cfg["workload"] and "225 random boxes" in cfg["workload"]
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "thermal"])
+    args = bench.parse()
+    cfg = bench.workload_config(args)
+    assert args.band_solve == 0
+    assert cfg["n"] == 524288 and "128x128x32" in cfg["workload"] and "400 random boxes" in cfg["workload"]
